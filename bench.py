@@ -1,0 +1,368 @@
+"""Benchmark: nonuniform SHT synthesis + adjoint at lmax = 4095 on the
+4096 x 8191 deflected Gauss-Legendre grid (33,550,336 points).
+
+One step = one type 2 transform (synthesis) plus one type 1 transform
+(adjoint) with inputs resident on the GPU.  The headline is the FP64 path at
+eps = 1e-10; the mixed path (FP64 recurrence, FP32 contraction / FFT / NUFFT)
+at eps = 1e-5 is measured in the same run and reported beside it.  Prints one
+JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 (under torchrun) every rank runs the same workload on its
+own GPU (replicas: a single transform does not shard without an exchange
+step); value = max-over-ranks time per step / N.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "nuSHT synth+adjoint ms at ℓmax 4095, 33.5M pts; FP64 1e-10 vs mixed 1e-5"
+WORKLOAD = "gl4095"
+LMAX = 4095
+EPS = {"fp64": 1e-10, "mixed": 1e-5}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 pipe peak: 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz
+# (the recipe's nominal 1.25 TFLOP/s; 1.19 measured with an FMA probe)
+FP64_PEAK_TFLOPS = 1.25
+
+
+def legendre_flops(lmax: int, M: int) -> float:
+    """Algorithmic work of one Legendre pass: T = ceil(N_r/2) (L+1)(L+2)/2 triples
+    (ring pair, l, m) x 8 FP64 flops (recurrence 4 + complex accumulation 4)."""
+    nr = M // 2 + 1
+    return 8.0 * ((nr + 1) // 2) * (lmax + 1) * (lmax + 2) / 2.0
+
+
+class Clocks:
+    """nvidia-smi sampler run during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for n, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(ngpus: int):
+    import torch
+
+    if ngpus > 1 or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed as dist
+
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return dist, dist.get_rank(), dist.get_world_size(), local
+    return None, 0, 1, 0
+
+
+def barrier(dist):
+    import torch
+
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(dist, x: float) -> float:
+    import torch
+
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(torch, fn, steps: int, warmup: int, dist):
+    for _ in range(warmup):
+        fn()
+    barrier(dist)
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        fn()
+    e1.record(s)
+    barrier(dist)
+    return e0.elapsed_time(e1) / steps
+
+
+def stage_breakdown(torch, plan, ad, y, reps: int = 3):
+    """Per-stage device times from the library's own stream events."""
+    acc = None
+    for _ in range(reps):
+        plan.synth(ad)
+        plan.adjoint(y)
+        st = plan.stage_times()
+        if acc is None:
+            acc = {k: {kk: [vv] for kk, vv in v.items()} for k, v in st.items()}
+        else:
+            for k, v in st.items():
+                for kk, vv in v.items():
+                    acc[k][kk].append(vv)
+    return {k: {kk: float(np.mean(vv)) for kk, vv in v.items()} for k, v in acc.items()}
+
+
+def cpu_oracle_step(a, pts, L, nsample: int, seed: int = 3):
+    """Oracle synthesis + adjoint (all orders) on a seeded sample of points;
+    returns (seconds, threads, sample indices)."""
+    import oracle
+
+    sel = W.subset(pts.shape[0], nsample, seed=seed)
+    y = np.random.default_rng(seed).standard_normal(sel.size)
+    t0 = time.perf_counter()
+    oracle.synth(a, pts[sel], L)
+    oracle.adjoint(y, pts[sel], L)
+    return time.perf_counter() - t0, oracle.num_threads(), sel
+
+
+def run_reference(args):
+    """The oracle (direct O(lmax^2 N) sums, C + OpenMP on the host cores) on a
+    bounded sample of the same workload, scaled to one full step."""
+    dist, rank, world, _ = (None, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0)
+    if rank != 0:
+        return
+    L, a, pts = W.workload(WORKLOAD)
+    nsample = int(os.environ.get("NUSHT_REF_SAMPLE", "200"))
+    times = []
+    for k in range(args.warmup + args.steps):
+        sec, threads, sel = cpu_oracle_step(a, pts, L, nsample, seed=100 + k)
+        if k >= args.warmup:
+            times.append(sec)
+    scale = pts.shape[0] / float(nsample)
+    ms = 1e3 * float(np.mean(times)) * scale
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "deflected GL grid 4096x8191 (33,550,336 pts), lmax=mmax=4095, "
+                                   "C_l=(l+1)^-2, 2.5 arcmin rms deflection"},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": threads, "kind": "oracle",
+                             "sample": "%d seeded points per step (synthesis + full adjoint), scaled by N/%d "
+                                       "(the direct sum is exactly linear in N)" % (nsample, nsample)},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["gl1023", "gl2047", "gl4095"],
+                    help="smaller deflected-grid cases for profiling; the benchmark is gl4095")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    import paper_2406_14542_gb300 as nu
+
+    dist, rank, world, local = dist_setup(args.gpus)
+    L, a, pts = W.workload(args.workload)
+    npts = pts.shape[0]
+    peaks, peak_src = load_peaks()
+    dpts = torch.from_numpy(pts).cuda()
+    results = {}
+    y_host = np.random.default_rng(5).standard_normal(npts)
+    for prec in (["fp64"] if args.no_mixed else ["fp64", "mixed"]):
+        cd = torch.complex128 if prec == "fp64" else torch.complex64
+        rd = torch.float64 if prec == "fp64" else torch.float32
+        t0 = time.perf_counter()
+        plan = nu.Plan(L, dpts, eps=EPS[prec], precision=prec, profile=True)
+        torch.cuda.synchronize()
+        t_plan = time.perf_counter() - t0
+        ad = torch.from_numpy(a).to(cd).cuda()
+        y = torch.from_numpy(y_host).to(rd).cuda()
+        fmap = torch.empty(npts, dtype=rd, device="cuda")
+        calm = torch.empty(plan.nalm, dtype=cd, device="cuda")
+
+        def step():
+            plan.synth(ad, out=fmap)
+            plan.adjoint(y, out=calm)
+
+        with Clocks(local) as clk:
+            ms = time_steps(torch, step, args.steps, args.warmup, dist)
+        ms = max_over_ranks(dist, ms)
+        stages = stage_breakdown(torch, plan, ad, y)
+        # parity on a seeded subset against the oracle (rank 0)
+        par = None
+        if rank == 0:
+            import oracle
+
+            sel = W.subset(npts, 300, seed=17)
+            f_ref = oracle.synth(a, pts[sel], L)
+            f = plan.synth(ad).double().cpu().numpy()
+            par = oracle.eps_eff(f_ref, f[sel])
+        results[prec] = {"ms": ms, "plan_s": t_plan, "stages": stages, "clocks": clk.summary(), "eps_eff": par,
+                         "info": plan.info()}
+        if prec == "fp64":
+            # end to end through the public API with host buffers (pinned),
+            # copies inside the timed region
+            a_pin = torch.from_numpy(a).pin_memory()
+            y_pin = torch.from_numpy(y_host).pin_memory()
+            f_pin = torch.empty(npts, dtype=torch.float64).pin_memory()
+            c_pin = torch.empty(plan.nalm, dtype=torch.complex128).pin_memory()
+            a_dev = torch.empty_like(ad)
+            y_dev = torch.empty_like(y)
+
+            def e2e_step():
+                a_dev.copy_(a_pin, non_blocking=True)
+                plan.synth(a_dev, out=fmap)
+                f_pin.copy_(fmap, non_blocking=True)
+                y_dev.copy_(y_pin, non_blocking=True)
+                plan.adjoint(y_dev, out=calm)
+                c_pin.copy_(calm, non_blocking=True)
+
+            e2e_ms = max_over_ranks(dist, time_steps(torch, e2e_step, args.steps, 1, dist))
+            h2d = a_pin.numel() * 16 + y_pin.numel() * 8
+            d2h = f_pin.numel() * 8 + c_pin.numel() * 16
+            results["e2e"] = {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d,
+                              "d2h_bytes_per_step": d2h}
+        plan.close()
+        del ad, y, fmap, calm
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    fp = results["fp64"]
+    M = fp["info"]["M"]
+    flops = legendre_flops(L, M)
+    t_leg = fp["stages"]["synth"]["legendre"] * 1e-3
+    achieved = flops / t_leg / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "legendre_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as fh:
+                tj = json.load(fh)
+            if tj.get("kernel_hash") == _kernel_hash():
+                traffic = tj.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "legendre_synth_k<double> (FP64 pipe; peak = 152 SMs x 2 FP64 FMA/clk x 2.07 GHz, "
+                          "nominal)", "flops_per_launch": flops}
+    cpu = None
+    if not args.no_cpu:
+        nsample = int(os.environ.get("NUSHT_CPU_SAMPLE", "200"))
+        sec, threads, _ = cpu_oracle_step(a, pts, L, nsample)
+        cpu = {"value": 1e3 * sec * npts / nsample, "unit": "ms", "cores": threads, "kind": "oracle",
+               "sample": "%d seeded points (synthesis + adjoint over all orders), scaled by N/%d; "
+                         "the direct sum is exactly linear in N" % (nsample, nsample)}
+    launches_per_step = 9  # scale_alm, legendre_synth, poles, deconv_pad, interp | spread, deconv_trunc, legendre_adj, reduce
+    line = {
+        "metric": METRIC, "value": fp["ms"] / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": fp["ms"], "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "deflected GL grid %dx%d (%d pts), lmax=mmax=%d, "
+                               "C_l=(l+1)^-2 Gaussian a_lm, 2.5 arcmin rms deflection" % (L + 1, 2 * L + 1, npts, L),
+                   "eps": 1e-10, "precision": "fp64", "sigma": fp["info"]["sigma"], "w": fp["info"]["w"],
+                   "fine_grid": [fp["info"]["n1"], fp["info"]["n2"]], "M": M,
+                   "l2": "inputs larger than L2 (%d^2 fine grid, %d points)" % (fp["info"]["n1"], npts),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "synth_ms": fp["stages"]["synth"]["total"], "adjoint_ms": fp["stages"]["adjoint"]["total"],
+        "stages_ms": fp["stages"], "eps_eff": fp["eps_eff"], "plan_s": fp["plan_s"],
+        "roofline": roofline, "e2e": results.get("e2e"),
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": fp["clocks"], "peak_source": peak_src,
+    }
+    if "mixed" in results:
+        mx = results["mixed"]
+        line["mixed"] = {"ms_per_step": mx["ms"], "eps": 1e-5, "eps_eff": mx["eps_eff"],
+                         "synth_ms": mx["stages"]["synth"]["total"], "adjoint_ms": mx["stages"]["adjoint"]["total"],
+                         "stages_ms": mx["stages"], "w": mx["info"]["w"], "sigma": mx["info"]["sigma"],
+                         "dtype": "f64 recurrence / f32 contraction, FFT, NUFFT", "clocks": mx["clocks"]}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _kernel_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha1()
+    with open(os.path.join(ROOT, "paper_2406_14542_gb300", "csrc", "legendre.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+if __name__ == "__main__":
+    main()

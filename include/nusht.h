@@ -1,0 +1,212 @@
+/*
+ * nusht.h -- C ABI of the GB300 (sm_103a) nonuniform spin-0 spherical
+ * harmonic transform library (method of cuNUSHT, arXiv 2406.14542).
+ *
+ * Transforms (Sec. 2.1):
+ *   type 2, "synthesis" (Eq. SHTbase):
+ *       f_i = sum_{l<=lmax} sum_{|m|<=min(l,mmax)} a_lm Y_l^m(theta_i, phi_i)
+ *   type 1, "adjoint" (Eq. adjointSHTbase), the exact adjoint of type 2:
+ *       c_lm = sum_i f_i conj(Y_l^m(theta_i, phi_i))
+ * with Y_l^m = P_l^m(theta) e^{i m phi} (Eq. Ylm) and the orthonormal
+ * P_l^m = d^l_{m0}(theta) sqrt((2l+1)/(4 pi)) of the footnote of Sec. 2.2,
+ * Condon-Shortley phase included (Y_1^1 = -sqrt(3/(8 pi)) sin(theta) e^{i phi}).
+ *
+ * Real fields.  Coefficients are stored for m >= 0 only; negative orders are
+ * implied by a_{l,-m} = (-1)^m conj(a_lm), so maps are real.  Im(a_l0) is
+ * ignored by synthesis and the adjoint returns Im(c_l0) = 0.  The adjoint is
+ * the adjoint under <c, a> = sum_l Re(conj(c_l0) a_l0)
+ *                           + 2 sum_{l, m>0} Re(conj(c_lm) a_lm).
+ *
+ * Coefficient layout ("m-major"): a_lm lives at index m (2 lmax + 1 - m)/2 + l
+ * for 0 <= m <= mmax, m <= l <= lmax; nalm = (mmax+1)(lmax+1) - mmax(mmax+1)/2
+ * complex numbers, interleaved (re, im).  Points: npts pairs (theta, phi) of
+ * doubles, interleaved, any finite reals (theta and phi are taken modulo 2 pi
+ * on the doubled torus of Fig. doubling, which names the same sphere point).
+ *
+ * Method (Sec. 2.2, Eq. SHTfast / adjointSHTfast): Y = N F D S.  S evaluates
+ * the Legendre sums on Clenshaw-Curtis rings, D doubles theta to [0, 2 pi),
+ * F is a uniform FFT (here a 1D theta FFT, the phi FFTs of S and F cancel,
+ * Sec. 3), N is a type 2 NUFFT with the exponential-of-semicircle kernel.
+ *
+ * Precision modes:
+ *   NUSHT_FP64   all arithmetic in double; coefficients complex128, maps double.
+ *   NUSHT_MIXED  Legendre recurrence, its rescaling and the DFS fold in double;
+ *                Legendre contraction, FFTs and spreading/interpolation in
+ *                float; coefficients complex64, maps float.  Point coordinates
+ *                stay double in both modes (the cell index and offset are
+ *                reduced in double, Sec. 4 on single-precision pointing).
+ *
+ * Memory and streams.  Every d_* pointer is DEVICE memory owned by the caller
+ * and must stay valid for the duration of the call's stream work.  A plan owns
+ * all of its workspace, allocated in nusht_plan; the execute calls
+ * (nusht_synth, nusht_adjoint, nusht_synth_grad) allocate nothing, copy
+ * nothing to or from the host and do not synchronise: they enqueue kernels and
+ * cuFFT work on `stream` (NULL = the legacy default stream) and return.  A plan
+ * may be used by one stream at a time.  Plans are bound to the device that was
+ * current when they were created.
+ *
+ * Errors.  Every call returns NUSHT_OK (0) or a code below; nusht_strerror
+ * names it and nusht_last_error returns the message of the calling thread's
+ * most recent failure.  Invalid arguments are rejected before any GPU work.
+ */
+#ifndef NUSHT_H
+#define NUSHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NUSHT_API __attribute__((visibility("default")))
+#else
+#define NUSHT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* CUDA stream handle (identical to cudaStream_t). */
+typedef struct CUstream_st* nusht_stream_t;
+
+/* Opaque plan: sizes, recurrence tables, sorted points, fine-grid and cuFFT
+ * workspaces for one (lmax, mmax, point set, eps, precision). */
+typedef struct nusht_plan_s* nusht_plan_t;
+
+enum {
+  NUSHT_OK = 0,
+  NUSHT_EINVAL = 1,      /* bad argument: sizes, null pointers, eps range */
+  NUSHT_ENOMEM = 2,      /* device or host allocation failed */
+  NUSHT_ECUDA = 3,       /* CUDA runtime or cuFFT error */
+  NUSHT_EUNSUPPORTED = 4, /* valid but unsupported combination */
+  NUSHT_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+  NUSHT_EDEVICE = 6      /* no usable CUDA device / wrong architecture */
+};
+
+enum { NUSHT_FP64 = 0, NUSHT_MIXED = 1 };
+
+/* Options; a zeroed struct (or NULL) selects the defaults. */
+typedef struct {
+  double sigma;      /* fine-grid up-sampling factor; 0 = default (2.0) */
+  int kernel_width;  /* ES kernel width w override; 0 = from eps and sigma */
+  int profile;       /* 1 = record per-stage CUDA-event times (nusht_stage_times) */
+  int deterministic; /* reserved; synthesis is bit-reproducible, the adjoint's spreading
+                        flush adds tile halos with atomics (rounding-level order effects) */
+  int tune;          /* reserved (0) */
+  int reserved[7];
+} nusht_opts;
+
+/* Sizes a plan uses; filled by nusht_plan_sizes (no GPU needed) and nusht_info. */
+typedef struct {
+  int lmax, mmax;
+  int nrings;        /* Clenshaw-Curtis rings on [0, pi], = M/2 + 1 (>= lmax + 2) */
+  int M;             /* doubled theta length (multiple of 4, >= 2 lmax + 2) */
+  int n1, n2;        /* fine grid (theta, phi) of the NUFFT */
+  int w;             /* ES kernel width in fine-grid cells */
+  double beta;       /* ES kernel shape parameter */
+  double sigma;      /* up-sampling factor used */
+  int precision;
+  int nitems;        /* Legendre work items (order, ring block) kept after the polar skip */
+  int nitems_total;  /* Legendre work items before the polar skip */
+  int64_t npts;
+  int64_t bytes_device; /* device memory held by the plan */
+} nusht_sizes;
+
+/*
+ * nusht_plan -- create a plan (Sec. 3: plans are made once and reused; the
+ * NUFFT point set-up is the costly step and happens here, not in execute).
+ *   out        receives the plan handle (set to NULL on failure)
+ *   lmax       band limit, 0 <= lmax <= 16383
+ *   mmax       order limit, 0 <= mmax <= lmax
+ *   npts       number of points, >= 0 (< 2^31)
+ *   d_pts      device double[2*npts] (theta, phi) pairs; may be NULL if npts == 0
+ *   eps        requested relative accuracy, 1e-14 <= eps <= 1e-1
+ *              (NUSHT_MIXED requires eps >= 1e-6: NUSHT_EUNSUPPORTED otherwise)
+ *   precision  NUSHT_FP64 or NUSHT_MIXED
+ *   opts       options or NULL
+ *   stream     stream for the set-up kernels; the call synchronises it before
+ *              returning (planning is not asynchronous)
+ */
+NUSHT_API int nusht_plan(nusht_plan_t* out, int lmax, int mmax, int64_t npts, const double* d_pts, double eps,
+               int precision, const nusht_opts* opts, nusht_stream_t stream);
+
+/*
+ * nusht_setpts -- replace the point set of a plan (re-sort, recompute kernel
+ * tables).  npts may differ from the plan's; buffers are reallocated only if
+ * it grows beyond the capacity reserved so far.  Synchronises `stream`.
+ */
+NUSHT_API int nusht_setpts(nusht_plan_t p, int64_t npts, const double* d_pts, nusht_stream_t stream);
+
+/*
+ * nusht_synth -- type 2 (Eq. SHTbase, through Eq. SHTfast).
+ *   d_alm  device complex (FP64: double[2*nalm]; MIXED: float[2*nalm]), packed m-major
+ *   d_map  device FP64: double[npts] / MIXED: float[npts], in the caller's point order
+ * Asynchronous on `stream`; allocates nothing.
+ */
+NUSHT_API int nusht_synth(nusht_plan_t p, const void* d_alm, void* d_map, nusht_stream_t stream);
+
+/*
+ * nusht_adjoint -- type 1 (Eq. adjointSHTbase, through Eq. adjointSHTfast).
+ *   d_map  device FP64: double[npts] / MIXED: float[npts], caller's point order
+ *   d_alm  device complex, overwritten with c_lm (all nalm entries)
+ * Asynchronous on `stream`; allocates nothing.
+ */
+NUSHT_API int nusht_adjoint(nusht_plan_t p, const void* d_map, void* d_alm, nusht_stream_t stream);
+
+/*
+ * nusht_synth_grad -- gradient of the synthesised map with respect to the
+ * point coordinates: d_dtheta[i] = d f_i / d theta_i, d_dphi[i] = d f_i / d phi_i,
+ * evaluated by interpolating with the derivative of the ES kernel on the same
+ * fine grid (Sec. 2.2: the torus function is differentiable term by term).
+ * Either output pointer may be NULL.  Asynchronous; allocates nothing.
+ */
+NUSHT_API int nusht_synth_grad(nusht_plan_t p, const void* d_alm, void* d_dtheta, void* d_dphi, nusht_stream_t stream);
+
+/* nusht_destroy -- free the plan and its device memory (NULL-safe). */
+NUSHT_API int nusht_destroy(nusht_plan_t p);
+
+/* nusht_info -- sizes of an existing plan. */
+NUSHT_API int nusht_info(nusht_plan_t p, nusht_sizes* out);
+
+/*
+ * nusht_plan_sizes -- the sizes nusht_plan would choose, computed on the host
+ * only (no CUDA call): theta length, fine grid, ES kernel width and shape.
+ * nitems* and bytes_device are left 0.
+ */
+NUSHT_API int nusht_plan_sizes(int lmax, int mmax, double eps, int precision, const nusht_opts* opts, nusht_sizes* out);
+
+/*
+ * nusht_kernel_ft -- host-side Fourier transform of the ES kernel used for
+ * deconvolution: out[k] = integral over |y| <= alpha of psi(y/alpha) cos(k y) dy,
+ * alpha = w pi / n, psi(z) = exp(beta (sqrt(1 - z^2) - 1)), for k = 0..nk-1.
+ * Exposed for tests of the planner; no CUDA call.
+ */
+NUSHT_API int nusht_kernel_ft(int w, double beta, int n, int nk, double* out);
+
+/*
+ * nusht_good_size -- smallest n >= nmin that is a multiple of `multiple` and
+ * whose prime factors are all <= maxprime (App. B "good numbers").  Host only.
+ */
+NUSHT_API int64_t nusht_good_size(int64_t nmin, int multiple, int maxprime);
+
+/*
+ * nusht_stage_times -- per-stage device times (ms) of the last synth and
+ * adjoint calls made with opts.profile = 1: out[0..5] synth
+ * (legendre, theta_fft, deconv_pad, grid_fft, interp, total),
+ * out[6..11] adjoint (spread, grid_fft, deconv_trunc, theta_fft, legendre, total).
+ * Synchronises the plan's last stream.
+ */
+NUSHT_API int nusht_stage_times(nusht_plan_t p, double* out12);
+
+/* nusht_strerror -- static name of a status code. */
+NUSHT_API const char* nusht_strerror(int code);
+
+/* nusht_last_error -- message of this thread's most recent failure ("" if none). */
+NUSHT_API const char* nusht_last_error(void);
+
+/* nusht_version -- library version string. */
+NUSHT_API const char* nusht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NUSHT_H */

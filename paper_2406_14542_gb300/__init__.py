@@ -1,0 +1,342 @@
+"""Python binding of the GB300 nuSHT library (include/nusht.h).
+
+Argument marshalling only: every step of the transform runs in the CUDA
+library ``_lib/libnusht.so`` (built by ``paper_2406_14542_gb300.build``).
+There is no CPU fallback; if the library is missing or the device is not a
+GB300 (sm_103a) the calls raise.  PyTorch provides device memory and streams.
+
+    import torch, paper_2406_14542_gb300 as nu
+    plan = nu.Plan(lmax, pts_cuda_f64_Nx2, eps=1e-10, precision="fp64")
+    f = plan.synth(alm_cuda_complex128)          # type 2 (Eq. SHTbase)
+    c = plan.adjoint(f)                          # type 1 (Eq. adjointSHTbase)
+    f = nu.nusht(alm, pts, plan)                 # differentiable in alm and pts
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libnusht.so")
+
+NUSHT_OK, NUSHT_EINVAL, NUSHT_ENOMEM, NUSHT_ECUDA, NUSHT_EUNSUPPORTED, NUSHT_ETIMEOUT, NUSHT_EDEVICE = range(7)
+FP64, MIXED = 0, 1
+
+EXPORTS = ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_synth_grad", "nusht_destroy",
+           "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_good_size", "nusht_stage_times",
+           "nusht_strerror", "nusht_last_error", "nusht_version")
+
+
+class NushtError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__("%s failed: %s (%s)" % (where, msg, _name(code)))
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("kernel_width", ctypes.c_int), ("profile", ctypes.c_int),
+                ("deterministic", ctypes.c_int), ("tune", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("lmax", ctypes.c_int), ("mmax", ctypes.c_int), ("nrings", ctypes.c_int), ("M", ctypes.c_int),
+                ("n1", ctypes.c_int), ("n2", ctypes.c_int), ("w", ctypes.c_int), ("beta", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("precision", ctypes.c_int), ("nitems", ctypes.c_int),
+                ("nitems_total", ctypes.c_int), ("npts", ctypes.c_int64), ("bytes_device", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError("nuSHT CUDA library not built: %s (run python -m paper_2406_14542_gb300.build)" % p)
+        lib = ctypes.CDLL(p)
+        vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        lib.nusht_plan.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, i64, vp, ctypes.c_double,
+                                   ctypes.c_int, ctypes.POINTER(Opts), vp]
+        lib.nusht_setpts.argtypes = [vp, i64, vp, vp]
+        lib.nusht_synth.argtypes = [vp, vp, vp, vp]
+        lib.nusht_adjoint.argtypes = [vp, vp, vp, vp]
+        lib.nusht_synth_grad.argtypes = [vp, vp, vp, vp, vp]
+        lib.nusht_destroy.argtypes = [vp]
+        lib.nusht_info.argtypes = [vp, ctypes.POINTER(Sizes)]
+        lib.nusht_plan_sizes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                         ctypes.POINTER(Opts), ctypes.POINTER(Sizes)]
+        lib.nusht_kernel_ft.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
+        lib.nusht_good_size.argtypes = [i64, ctypes.c_int, ctypes.c_int]
+        lib.nusht_good_size.restype = i64
+        lib.nusht_stage_times.argtypes = [vp, dp]
+        lib.nusht_strerror.argtypes = [ctypes.c_int]
+        lib.nusht_strerror.restype = ctypes.c_char_p
+        lib.nusht_last_error.restype = ctypes.c_char_p
+        lib.nusht_version.restype = ctypes.c_char_p
+        for name in ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_synth_grad",
+                     "nusht_destroy", "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_stage_times"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _name(code: int) -> str:
+    try:
+        return load().nusht_strerror(code).decode()
+    except Exception:
+        return "status %d" % code
+
+
+def _check(code: int, where: str):
+    if code != NUSHT_OK:
+        raise NushtError(code, where, load().nusht_last_error().decode())
+
+
+def _opts(sigma=0.0, kernel_width=0, profile=False) -> Opts:
+    o = Opts()
+    o.sigma = float(sigma)
+    o.kernel_width = int(kernel_width)
+    o.profile = 1 if profile else 0
+    return o
+
+
+def _prec(precision) -> int:
+    if precision in (FP64, "fp64", "double"):
+        return FP64
+    if precision in (MIXED, "mixed"):
+        return MIXED
+    raise ValueError("precision must be 'fp64' or 'mixed'")
+
+
+def nalm(lmax: int, mmax: int | None = None) -> int:
+    mmax = lmax if mmax is None else mmax
+    return (mmax + 1) * (lmax + 1) - mmax * (mmax + 1) // 2
+
+
+def plan_sizes(lmax: int, eps: float, precision="fp64", mmax: int | None = None, sigma=0.0, kernel_width=0) -> dict:
+    """Sizes a plan would use (host-only computation, no GPU)."""
+    mmax = lmax if mmax is None else mmax
+    z = Sizes()
+    o = _opts(sigma, kernel_width)
+    _check(load().nusht_plan_sizes(lmax, mmax, eps, _prec(precision), ctypes.byref(o), ctypes.byref(z)),
+           "nusht_plan_sizes")
+    return z.as_dict()
+
+
+def kernel_ft(w: int, beta: float, n: int, nk: int):
+    """Fourier transform of the ES kernel as the planner computes it (host only)."""
+    import numpy as np
+
+    out = np.zeros(nk, dtype=np.float64)
+    _check(load().nusht_kernel_ft(w, beta, n, nk, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "nusht_kernel_ft")
+    return out
+
+
+def good_size(nmin: int, multiple: int = 1, maxprime: int = 7) -> int:
+    return int(load().nusht_good_size(int(nmin), int(multiple), int(maxprime)))
+
+
+def version() -> str:
+    return load().nusht_version().decode()
+
+
+def _stream_ptr(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(int(s.cuda_stream))
+
+
+class Plan:
+    """A planned transform for one band limit, point set, accuracy and precision.
+
+    ``pts``: CUDA float64 tensor of shape (N, 2) holding (theta, phi).
+    ``precision``: 'fp64' (complex128 a_lm, float64 maps) or 'mixed'
+    (complex64 a_lm, float32 maps; recurrence and fold stay FP64).
+    """
+
+    def __init__(self, lmax: int, pts, eps: float = 1e-10, precision="fp64", mmax: int | None = None,
+                 sigma: float = 0.0, kernel_width: int = 0, profile: bool = False, stream=None):
+        import torch
+
+        self.lib = load()
+        self.lmax = int(lmax)
+        self.mmax = self.lmax if mmax is None else int(mmax)
+        self.precision = _prec(precision)
+        self.eps = float(eps)
+        self.cdtype = torch.complex128 if self.precision == FP64 else torch.complex64
+        self.rdtype = torch.float64 if self.precision == FP64 else torch.float32
+        pts = self._check_pts(pts)
+        self.npts = int(pts.shape[0])
+        self.device = pts.device
+        h = ctypes.c_void_p()
+        o = _opts(sigma, kernel_width, profile)
+        _check(self.lib.nusht_plan(ctypes.byref(h), self.lmax, self.mmax, self.npts,
+                                   ctypes.c_void_p(pts.data_ptr() if self.npts else 0), self.eps, self.precision,
+                                   ctypes.byref(o), _stream_ptr(stream)), "nusht_plan")
+        self._h = h
+
+    @staticmethod
+    def _check_pts(pts):
+        import torch
+
+        if not (isinstance(pts, torch.Tensor) and pts.is_cuda and pts.dtype == torch.float64 and pts.dim() == 2
+                and pts.shape[1] == 2):
+            raise ValueError("pts must be a CUDA float64 tensor of shape (N, 2)")
+        return pts.contiguous()
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan is closed")
+        return self._h
+
+    @property
+    def nalm(self) -> int:
+        return nalm(self.lmax, self.mmax)
+
+    def info(self) -> dict:
+        z = Sizes()
+        _check(self.lib.nusht_info(self.handle, ctypes.byref(z)), "nusht_info")
+        return z.as_dict()
+
+    def setpts(self, pts, stream=None):
+        pts = self._check_pts(pts)
+        _check(self.lib.nusht_setpts(self.handle, int(pts.shape[0]), ctypes.c_void_p(pts.data_ptr()),
+                                     _stream_ptr(stream)), "nusht_setpts")
+        self.npts = int(pts.shape[0])
+
+    def _alm(self, alm):
+        import torch
+
+        if not (isinstance(alm, torch.Tensor) and alm.is_cuda and alm.dtype == self.cdtype
+                and alm.shape == (self.nalm,)):
+            raise ValueError("alm must be a CUDA %s tensor of shape (%d,)" % (self.cdtype, self.nalm))
+        return alm.contiguous()
+
+    def _map(self, m):
+        import torch
+
+        if not (isinstance(m, torch.Tensor) and m.is_cuda and m.dtype == self.rdtype and m.shape == (self.npts,)):
+            raise ValueError("map must be a CUDA %s tensor of shape (%d,)" % (self.rdtype, self.npts))
+        return m.contiguous()
+
+    def synth(self, alm, out=None, stream=None):
+        """Type 2 nuSHT: values at the plan's points (caller's order)."""
+        import torch
+
+        alm = self._alm(alm)
+        if out is None:
+            out = torch.empty(self.npts, dtype=self.rdtype, device=self.device)
+        out = self._map(out)
+        _check(self.lib.nusht_synth(self.handle, ctypes.c_void_p(alm.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                    _stream_ptr(stream)), "nusht_synth")
+        return out
+
+    def adjoint(self, m, out=None, stream=None):
+        """Type 1 nuSHT (adjoint): c_lm = sum_i f_i conj(Y_lm(theta_i, phi_i))."""
+        import torch
+
+        m = self._map(m)
+        if out is None:
+            out = torch.empty(self.nalm, dtype=self.cdtype, device=self.device)
+        out = self._alm(out)
+        _check(self.lib.nusht_adjoint(self.handle, ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      _stream_ptr(stream)), "nusht_adjoint")
+        return out
+
+    def synth_grad(self, alm, stream=None):
+        """(d f_i / d theta_i, d f_i / d phi_i) by derivative-of-kernel interpolation."""
+        import torch
+
+        alm = self._alm(alm)
+        dth = torch.empty(self.npts, dtype=self.rdtype, device=self.device)
+        dph = torch.empty(self.npts, dtype=self.rdtype, device=self.device)
+        _check(self.lib.nusht_synth_grad(self.handle, ctypes.c_void_p(alm.data_ptr()),
+                                         ctypes.c_void_p(dth.data_ptr()), ctypes.c_void_p(dph.data_ptr()),
+                                         _stream_ptr(stream)), "nusht_synth_grad")
+        return dth, dph
+
+    def stage_times(self) -> dict:
+        import numpy as np
+
+        out = np.zeros(12, dtype=np.float64)
+        _check(self.lib.nusht_stage_times(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "nusht_stage_times")
+        names = ["legendre", "theta_fft", "deconv_pad", "grid_fft", "interp", "total"]
+        anames = ["spread", "grid_fft", "deconv_trunc", "theta_fft", "legendre", "total"]
+        return {"synth": dict(zip(names, out[:6].tolist())), "adjoint": dict(zip(anames, out[6:].tolist()))}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self.lib.nusht_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _autograd():
+    import torch
+
+    class NuSHT(torch.autograd.Function):
+        """f = Y a (type 2) with gradients in a_lm (through the adjoint, type 1)
+        and in the point coordinates (derivative-of-kernel interpolation).
+
+        For a real loss, torch's complex gradient is dL/dRe(a) + i dL/dIm(a)
+        = w_m (Y^dagger g)_lm with w_0 = 1, w_{m>0} = 2 (the real-field map
+        counts each m > 0 twice, once through a_{l,-m}).
+        """
+
+        @staticmethod
+        def forward(ctx, alm, pts, plan):
+            ctx.plan = plan
+            ctx.save_for_backward(alm)
+            return plan.synth(alm.detach())
+
+        @staticmethod
+        def backward(ctx, g):
+            plan = ctx.plan
+            (alm,) = ctx.saved_tensors
+            g = g.contiguous().to(plan.rdtype)
+            ga = gp = None
+            if ctx.needs_input_grad[0]:
+                ga = plan.adjoint(g)
+                ga[plan.lmax + 1:] *= 2.0
+            if ctx.needs_input_grad[1]:
+                dth, dph = plan.synth_grad(alm.detach())
+                gp = torch.stack([g * dth, g * dph], dim=1).to(torch.float64)
+            return ga, gp, None
+
+    return NuSHT
+
+
+_NuSHT = None
+
+
+def nusht(alm, pts, plan: Plan):
+    """Differentiable type 2 nuSHT at ``plan``'s points; ``pts`` must hold the
+    same coordinates the plan was made with (it carries their gradient)."""
+    global _NuSHT
+    if _NuSHT is None:
+        _NuSHT = _autograd()
+    return _NuSHT.apply(alm, pts, plan)

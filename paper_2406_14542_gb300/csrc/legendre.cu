@@ -1,0 +1,725 @@
+// legendre.cu -- the iso-latitude step S and its adjoint S^dagger (Sec. 2.2,
+// Sec. 3) on Clenshaw-Curtis rings, with the doubling D fused into the
+// synthesis store and the fold D^dagger fused into the adjoint load.
+//
+// Recurrence.  For a fixed order m the orthonormal functions obey
+//   Pbar_l = alpha_l x Pbar_{l-1} - alpha_l b_l Pbar_{l-2},  x = cos(theta),
+//   alpha_l^2 = (4l^2-1)/(l^2-m^2),  b_l^2 = ((l-1)^2-m^2)/(4(l-1)^2-1).
+// Writing Pbar_l = Ahat_l q_l with Ahat_l = 2^-sigma_l prod_{k=m+1}^{l} alpha_k
+// (a theta-independent table) turns it into
+//   q_l = x q_{l-1} - c_l q_{l-2},  c_l = b_l / alpha_{l-1}
+//       = (l-1-m)(l-1+m) / ((2l-3)(2l-1))            (a rational number),
+// two FP64 operations per step instead of three; Ahat_l is folded into the
+// coefficients once per call (atilde = a Ahat).  sigma_l grows by
+// LEG_SEG_BITS whenever Ahat would leave [1, 2^48); those steps first scale
+// (q_{l-1}, q_{l-2}) by 2^LEG_SEG_BITS (table dshift).  The start value is
+// Pbar_mm = c_m sin^m(theta), with sin^m by binary powering and an integer
+// exponent.  While the value is below 2^-300 it is carried with a separate
+// exponent E (the scaled-exponent phase; checks are integer operations) and
+// not accumulated; ring blocks of an order whose every ring stays below that
+// threshold up to lmax are dropped from the work list at plan time.
+//
+// Parallel layout: one warp per work item (order m, block of 128 ring pairs),
+// four ring pairs (theta_j, pi - theta_j) per lane that share the recurrence
+// through Pbar_l(pi - theta) = (-1)^(l+m) Pbar_l(theta).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "nusht_internal.cuh"
+
+namespace nusht {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct LegArgs {
+  int lmax, mmax, M, npairs, bpm;
+  const int* items;
+  const double* c;
+  const int8_t* dshift;
+  const double* cm;
+  const double* ring_x;
+  const double* ring_s;
+};
+
+__device__ __forceinline__ int mbase_of(int L, int m) { return m * (2 * L + 1 - m) / 2; }
+
+__device__ __forceinline__ double exp2i(int e) {
+  // 2^e for -1022 <= e <= 1023, built from the exponent field
+  return __hiloint2double((e + 1023) << 20, 0);
+}
+
+// v = mant * 2^k with mant in [0.5, 1); v must be a positive normal number
+__device__ __forceinline__ void renorm(double& v, int& e) {
+  int hi = __double2hiint(v);
+  int lo = __double2loint(v);
+  int k = ((hi >> 20) & 0x7ff) - 1022;
+  hi = (hi & 0x800fffff) | (1022 << 20);
+  v = __hiloint2double(hi, lo);
+  e += k;
+}
+
+// s^m = mant * 2^ex (s in (0, 1]), by binary powering with integer exponents
+__device__ __forceinline__ void pow_scaled(double s, int m, double& mant, int& ex) {
+  double b = s;
+  int be = 0;
+  renorm(b, be);
+  double r = 1.0;
+  int re = 0;
+  renorm(r, re);
+  while (m) {
+    if (m & 1) {
+      r *= b;
+      re += be;
+      renorm(r, re);
+    }
+    m >>= 1;
+    if (m) {
+      b *= b;
+      be *= 2;
+      renorm(b, be);
+    }
+  }
+  mant = r;
+  ex = re;
+}
+
+// Float from a double known to lie in (-2^64, 2^64), by truncation of the
+// mantissa with integer operations (keeps the conversion off the FP64 pipe);
+// values below 2^-126 become 0.
+__device__ __forceinline__ float to_f32(double q) {
+  int hi = __double2hiint(q);
+  unsigned lo = (unsigned)__double2loint(q);
+  int e = ((hi >> 20) & 0x7ff) - 1023;
+  unsigned mant = ((unsigned)(hi & 0xfffff) << 3) | (lo >> 29);
+  unsigned bits = ((unsigned)hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | mant;
+  return (e < -126) ? 0.0f : __uint_as_float(bits);
+}
+
+template <typename T>
+struct V2;
+template <>
+struct V2<double> {
+  using t = double2;
+};
+template <>
+struct V2<float> {
+  using t = float2;
+};
+
+template <typename T>
+__device__ __forceinline__ T conv(double q);
+template <>
+__device__ __forceinline__ double conv<double>(double q) {
+  return q;
+}
+template <>
+__device__ __forceinline__ float conv<float>(double q) {
+  return to_f32(q);
+}
+
+// One recurrence chain (a ring pair).
+struct Chain {
+  double x, q1, q2;
+  int E;      // > 0: scaled phase, value = q * 2^-E; 0: ordinary values
+  bool valid;
+};
+
+__device__ __forceinline__ void chain_init(Chain& ch, const LegArgs& a, int m, int j) {
+  ch.valid = (j >= 1 && j <= a.npairs);
+  ch.q2 = 0.0;
+  if (!ch.valid) {
+    ch.x = 0.0;
+    ch.q1 = 0.0;
+    ch.E = 0;
+    return;
+  }
+  ch.x = __ldg(a.ring_x + (j - 1));
+  double s = __ldg(a.ring_s + (j - 1));
+  double mant;
+  int ex;
+  pow_scaled(s, m, mant, ex);
+  double q0 = __ldg(a.cm + m) * mant;
+  if (ex >= LEG_TINY_EXP) {
+    ch.q1 = q0 * exp2i(ex);
+    ch.E = 0;
+  } else {
+    int E = LEG_STEP_EXP * ((LEG_TINY_EXP - ex + LEG_STEP_EXP - 1) / LEG_STEP_EXP);
+    ch.q1 = q0 * exp2i(ex + E);
+    ch.E = E;
+  }
+}
+
+// v * 2^k through the exponent field (integer operations only); zero and
+// subnormal inputs are returned unchanged.  Used for the power-of-two
+// rescalings so that they never occupy the FP64 pipe (on sm_103a the FP64
+// pipe is 1/64 of the FP32 rate, and warp-uniform branches around FP64
+// multiplies are if-converted into predicated instructions that still issue).
+__device__ __forceinline__ double scale_pow2(double v, int k) {
+  int hi = __double2hiint(v);
+  const int lo = __double2loint(v);
+  hi = (hi & 0x7ff00000) ? hi + (k << 20) : hi;
+  return __hiloint2double(hi, lo);
+}
+
+// Advance to degree l: optional segment rescale (q_{l-1}, q_{l-2}) *= 2^48,
+// then q_l = x q_{l-1} - c q_{l-2}: two FP64 operations.  In the scaled phase
+// the exponent check and the 2^-256 step are integer operations.
+__device__ __forceinline__ void chain_step(Chain& ch, double c, bool do_rescale) {
+  if (do_rescale) {
+    ch.q1 = scale_pow2(ch.q1, LEG_SEG_BITS);
+    ch.q2 = scale_pow2(ch.q2, LEG_SEG_BITS);
+  }
+  double t = c * ch.q2;
+  double q = fma(ch.x, ch.q1, -t);
+  ch.q2 = ch.q1;
+  ch.q1 = q;
+  if (ch.E != 0) {
+    int expo = (__double2hiint(q) >> 20) & 0x7ff;
+    if (expo >= 1023 - 44) {
+      ch.q1 = scale_pow2(ch.q1, -LEG_STEP_EXP);
+      ch.q2 = scale_pow2(ch.q2, -LEG_STEP_EXP);
+      ch.E -= LEG_STEP_EXP;
+    }
+  }
+}
+
+__device__ __forceinline__ void item_of(const LegArgs& a, int it, int& m, int& blk) {
+  int v = __ldg(a.items + it);
+  m = v >> 16;
+  blk = v & 0xffff;
+}
+
+// ---------------------------------------------------------------------------
+// synthesis: G[m][*] (doubled, theta-contiguous) from atilde
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) legendre_synth_k(LegArgs a, const typename V2<T>::t* __restrict__ at,
+                                                        typename V2<T>::t* __restrict__ G, int nitems) {
+  using T2 = typename V2<T>::t;
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  int m, blk;
+  item_of(a, it, m, blk);
+  const int L = a.lmax;
+  const int mb = mbase_of(L, m);
+  Chain ch[LEG_K];
+  T2 accE[LEG_K], accO[LEG_K];
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) {
+    chain_init(ch[k], a, m, 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane);
+    accE[k].x = accE[k].y = accO[k].x = accO[k].y = (T)0;
+  }
+  // l = m (even parity)
+  {
+    T2 av = at[mb + m];
+#pragma unroll
+    for (int k = 0; k < LEG_K; ++k)
+      if (ch[k].E == 0) {
+        T q = conv<T>(ch[k].q1);
+        accE[k].x = fma(av.x, q, accE[k].x);
+        accE[k].y = fma(av.y, q, accE[k].y);
+      }
+  }
+  // degrees in pairs (l - m odd, l - m even) so that the parity is static
+  int l = m + 1;
+  for (; l + 1 <= L; l += 2) {
+    {
+      const double c = __ldg(a.c + mb + l);
+      const bool rs = __ldg(a.dshift + mb + l) != 0;
+      const T2 av = at[mb + l];
+#pragma unroll
+      for (int k = 0; k < LEG_K; ++k) {
+        chain_step(ch[k], c, rs);
+        if (ch[k].E == 0) {
+          T q = conv<T>(ch[k].q1);
+          accO[k].x = fma(av.x, q, accO[k].x);
+          accO[k].y = fma(av.y, q, accO[k].y);
+        }
+      }
+    }
+    {
+      const double c = __ldg(a.c + mb + l + 1);
+      const bool rs = __ldg(a.dshift + mb + l + 1) != 0;
+      const T2 av = at[mb + l + 1];
+#pragma unroll
+      for (int k = 0; k < LEG_K; ++k) {
+        chain_step(ch[k], c, rs);
+        if (ch[k].E == 0) {
+          T q = conv<T>(ch[k].q1);
+          accE[k].x = fma(av.x, q, accE[k].x);
+          accE[k].y = fma(av.y, q, accE[k].y);
+        }
+      }
+    }
+  }
+  if (l <= L) {
+    const double c = __ldg(a.c + mb + l);
+    const bool rs = __ldg(a.dshift + mb + l) != 0;
+    const T2 av = at[mb + l];
+#pragma unroll
+    for (int k = 0; k < LEG_K; ++k) {
+      chain_step(ch[k], c, rs);
+      if (ch[k].E == 0) {
+        T q = conv<T>(ch[k].q1);
+        accO[k].x = fma(av.x, q, accO[k].x);
+        accO[k].y = fma(av.y, q, accO[k].y);
+      }
+    }
+  }
+  // F(theta_j) = E + O, F(pi - theta_j) = E - O, then the doubling
+  // G(theta) = (-1)^m F(2 pi - theta) for theta in (pi, 2 pi)  (Fig. doubling)
+  const int M = a.M;
+  const T sg = (m & 1) ? (T)-1 : (T)1;
+  T2* row = G + (size_t)m * M;
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) {
+    if (!ch[k].valid) continue;
+    const int jn = 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane;
+    const int js = M / 2 - jn;
+    T2 fn, fs;
+    fn.x = accE[k].x + accO[k].x;
+    fn.y = accE[k].y + accO[k].y;
+    fs.x = accE[k].x - accO[k].x;
+    fs.y = accE[k].y - accO[k].y;
+    row[jn] = fn;
+    T2 t;
+    t.x = sg * fn.x;
+    t.y = sg * fn.y;
+    row[M - jn] = t;
+    if (js != jn) {
+      row[js] = fs;
+      t.x = sg * fs.x;
+      t.y = sg * fs.y;
+      row[M - js] = t;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint: partial[blk][l,m] = sum over the block's rings of q_l(theta) S(theta)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ typename V2<T>::t shfl2(typename V2<T>::t v, int mask) {
+  typename V2<T>::t r;
+  r.x = __shfl_xor_sync(FULL, v.x, mask);
+  r.y = __shfl_xor_sync(FULL, v.y, mask);
+  return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) legendre_adj_k(LegArgs a, const typename V2<T>::t* __restrict__ Gt,
+                                                      typename V2<T>::t* __restrict__ partial, int nitems,
+                                                      int64_t nalm) {
+  using T2 = typename V2<T>::t;
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  int m, blk;
+  item_of(a, it, m, blk);
+  const int L = a.lmax;
+  const int M = a.M;
+  const int mb = mbase_of(L, m);
+  const T sg = (m & 1) ? (T)-1 : (T)1;
+  const T2* row = Gt + (size_t)m * M;
+  Chain ch[LEG_K];
+  T2 SE[LEG_K], SO[LEG_K];
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) {
+    const int jn = 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane;
+    chain_init(ch[k], a, m, jn);
+    T2 fn, fs;
+    fn.x = fn.y = fs.x = fs.y = (T)0;
+    if (ch[k].valid) {
+      // D^dagger: F(theta_j) = G(theta_j) + (-1)^m G(2 pi - theta_j)
+      const int js = M / 2 - jn;
+      T2 g0 = row[jn], g1 = row[M - jn];
+      fn.x = g0.x + sg * g1.x;
+      fn.y = g0.y + sg * g1.y;
+      if (js != jn) {
+        T2 h0 = row[js], h1 = row[M - js];
+        fs.x = h0.x + sg * h1.x;
+        fs.y = h0.y + sg * h1.y;
+      }
+    }
+    SE[k].x = fn.x + fs.x;
+    SE[k].y = fn.y + fs.y;
+    SO[k].x = fn.x - fs.x;
+    SO[k].y = fn.y - fs.y;
+  }
+  T2* out = partial + (size_t)blk * nalm + mb;
+  for (int base = m; base <= L; base += 8) {
+    T2 v[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      v[s].x = v[s].y = (T)0;
+      const int l = base + s;
+      if (l <= L) {
+        if (l > m) {
+          const double c = __ldg(a.c + mb + l);
+          const bool rs = __ldg(a.dshift + mb + l) != 0;
+#pragma unroll
+          for (int k = 0; k < LEG_K; ++k) chain_step(ch[k], c, rs);
+        }
+#pragma unroll
+        for (int k = 0; k < LEG_K; ++k) {
+          if (ch[k].E == 0) {
+            T q = conv<T>(ch[k].q1);
+            const T2 S = (s & 1) ? SO[k] : SE[k];
+            v[s].x = fma(q, S.x, v[s].x);
+            v[s].y = fma(q, S.y, v[s].y);
+          }
+        }
+      }
+    }
+    // reduce-scatter the 8 degrees over the 32 lanes (warp-level reduction)
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    T2 w4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      T2 send = u16 ? v[i] : v[i + 4];
+      T2 keep = u16 ? v[i + 4] : v[i];
+      T2 r = shfl2<T>(send, 16);
+      w4[i].x = keep.x + r.x;
+      w4[i].y = keep.y + r.y;
+    }
+    T2 w2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      T2 send = u8 ? w4[i] : w4[i + 2];
+      T2 keep = u8 ? w4[i + 2] : w4[i];
+      T2 r = shfl2<T>(send, 8);
+      w2[i].x = keep.x + r.x;
+      w2[i].y = keep.y + r.y;
+    }
+    T2 z;
+    {
+      T2 send = u4 ? w2[0] : w2[1];
+      T2 keep = u4 ? w2[1] : w2[0];
+      T2 r = shfl2<T>(send, 4);
+      z.x = keep.x + r.x;
+      z.y = keep.y + r.y;
+    }
+    T2 r = shfl2<T>(z, 2);
+    z.x += r.x;
+    z.y += r.y;
+    r = shfl2<T>(z, 1);
+    z.x += r.x;
+    z.y += r.y;
+    const int l = base + ((lane >> 2) & 7);
+    if ((lane & 3) == 0 && l <= L) out[l] = z;
+  }
+}
+
+// Sum of the ring-block partials in a fixed order, times Ahat; the poles
+// (theta = 0, pi) contribute to m = 0 only: Pbar_l0(0) = sqrt((2l+1)/4pi),
+// Pbar_l0(pi) = (-1)^l sqrt((2l+1)/4pi).
+template <typename T>
+__global__ void adj_reduce_k(const typename V2<T>::t* __restrict__ partial, int bpm, int64_t nalm,
+                             const double* __restrict__ ahat, const double* __restrict__ pole_norm,
+                             const typename V2<T>::t* __restrict__ Gt, int lmax, int M, typename V2<T>::t* out) {
+  using T2 = typename V2<T>::t;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nalm) return;
+  double sx = 0.0, sy = 0.0;
+  for (int b = 0; b < bpm; ++b) {
+    T2 v = partial[(size_t)b * nalm + i];
+    sx += (double)v.x;
+    sy += (double)v.y;
+  }
+  const double ah = ahat[i];
+  sx *= ah;
+  sy *= ah;
+  T2 r;
+  if (i <= lmax) {  // m = 0 block: real
+    const int l = (int)i;
+    double np = (double)Gt[0].x, sp = (double)Gt[M / 2].x;
+    sx += pole_norm[l] * (np + ((l & 1) ? -sp : sp));
+    sy = 0.0;
+  }
+  r.x = (T)sx;
+  r.y = (T)sy;
+  out[i] = r;
+}
+
+// atilde_lm = a_lm Ahat_lm, with Im(a_l0) dropped
+template <typename Tin, typename T>
+__global__ void scale_alm_k(const Tin* __restrict__ alm, const double* __restrict__ ahat, int64_t nalm, int lmax,
+                            typename V2<T>::t* __restrict__ at) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nalm) return;
+  double re = (double)alm[2 * i], im = (double)alm[2 * i + 1];
+  if (i <= lmax) im = 0.0;
+  const double ah = ahat[i];
+  typename V2<T>::t r;
+  r.x = (T)(re * ah);
+  r.y = (T)(im * ah);
+  at[i] = r;
+}
+
+// F_0 at the poles: G[0][0] and G[0][M/2] (all m > 0 pole entries stay 0)
+template <typename Tin, typename T>
+__global__ void poles_synth_k(const Tin* __restrict__ alm, const double* __restrict__ pole_norm, int lmax, int M,
+                              typename V2<T>::t* G) {
+  __shared__ double sn[256], ss[256];
+  double n = 0.0, s = 0.0;
+  for (int l = threadIdx.x; l <= lmax; l += blockDim.x) {
+    double v = (double)alm[2 * l] * pole_norm[l];
+    n += v;
+    s += (l & 1) ? -v : v;
+  }
+  sn[threadIdx.x] = n;
+  ss[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sn[threadIdx.x] += sn[threadIdx.x + h];
+      ss[threadIdx.x] += ss[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    typename V2<T>::t a, b;
+    a.x = (T)sn[0];
+    a.y = (T)0;
+    b.x = (T)ss[0];
+    b.y = (T)0;
+    G[0] = a;
+    G[M / 2] = b;
+  }
+}
+
+// Plan-time probe: does any ring of the item leave the scaled phase by lmax?
+__global__ void __launch_bounds__(128) legendre_probe_k(LegArgs a, int ntotal, int* __restrict__ flags) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= ntotal) return;
+  const int m = it / a.bpm, blk = it % a.bpm;
+  const int L = a.lmax;
+  const int mb = mbase_of(L, m);
+  Chain ch[LEG_K];
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) chain_init(ch[k], a, m, 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane);
+  auto significant = [&]() {
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < LEG_K; ++k) any |= (ch[k].valid && ch[k].E == 0);
+    return any;
+  };
+  bool sig = __any_sync(FULL, significant());
+  for (int l = m + 1; l <= L && !sig; ++l) {
+    const double c = __ldg(a.c + mb + l);
+    const bool rs = __ldg(a.dshift + mb + l) != 0;
+#pragma unroll
+    for (int k = 0; k < LEG_K; ++k) chain_step(ch[k], c, rs);
+    sig = __any_sync(FULL, significant());
+  }
+  if (lane == 0) flags[it] = sig ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// host: tables in double-double, then the probe and the work list
+// ---------------------------------------------------------------------------
+struct dd {
+  double hi, lo;
+};
+
+inline dd two_sum(double a, double b) {
+  double s = a + b;
+  double bb = s - a;
+  double e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+inline dd dd_norm(double hi, double lo) { return two_sum(hi, lo); }
+inline dd dd_mul_d(dd a, double b) {
+  double p = a.hi * b;
+  double e = std::fma(a.hi, b, -p);
+  e += a.lo * b;
+  return dd_norm(p, e);
+}
+inline dd dd_div_d(dd a, double b) {
+  double q1 = a.hi / b;
+  dd p = dd_mul_d({q1, 0.0}, b);
+  double r = ((a.hi - p.hi) - p.lo + a.lo) / b;
+  return dd_norm(q1, r);
+}
+inline double dd_sqrt(dd a) {
+  if (a.hi <= 0.0) return 0.0;
+  double s = std::sqrt(a.hi);
+  // one Newton step in double-double: s + (a - s^2) / (2 s)
+  double p = s * s;
+  double e = std::fma(s, s, -p);
+  double r = ((a.hi - p) - e + a.lo) / (2.0 * s);
+  return s + r;
+}
+
+}  // namespace
+
+static LegArgs make_args(nusht_plan_t p) {
+  LegArgs a;
+  a.lmax = p->lmax;
+  a.mmax = p->mmax;
+  a.M = p->sz.M;
+  a.npairs = p->leg.npairs;
+  a.bpm = p->leg.blocks_per_m;
+  a.items = p->leg.items;
+  a.c = p->leg.c;
+  a.dshift = p->leg.dshift;
+  a.cm = p->leg.cm;
+  a.ring_x = p->leg.ring_x;
+  a.ring_s = p->leg.ring_s;
+  return a;
+}
+
+int legendre_build_tables(nusht_plan_t p, cudaStream_t s) {
+  const int L = p->lmax, mmax = p->mmax, M = p->sz.M;
+  const int64_t nalm = p->nalm;
+  std::vector<double> c(nalm), ah(nalm);
+  std::vector<int8_t> dsh(nalm, 0);
+  for (int m = 0; m <= mmax; ++m) {
+    const int64_t mb = (int64_t)m * (2 * L + 1 - m) / 2;
+    dd a2 = {1.0, 0.0};  // Ahat^2 (scaled)
+    for (int l = m; l <= L; ++l) {
+      if (l == m) {
+        c[mb + l] = 0.0;
+        ah[mb + l] = 1.0;
+        continue;
+      }
+      const double dl = l, dm = m;
+      // alpha_l^2 = (4 l^2 - 1) / (l^2 - m^2), exact integers
+      a2 = dd_mul_d(a2, 4.0 * dl * dl - 1.0);
+      a2 = dd_div_d(a2, dl * dl - dm * dm);
+      int e2 = 0;
+      std::frexp(a2.hi, &e2);
+      if (e2 > 2 * LEG_SEG_BITS) {  // Ahat >= 2^48: next segment
+        a2.hi = std::ldexp(a2.hi, -2 * LEG_SEG_BITS);
+        a2.lo = std::ldexp(a2.lo, -2 * LEG_SEG_BITS);
+        dsh[mb + l] = (int8_t)LEG_SEG_BITS;
+      }
+      ah[mb + l] = dd_sqrt(a2);
+      c[mb + l] = (l == m + 1) ? 0.0 : ((dl - 1.0 - dm) * (dl - 1.0 + dm)) / ((2.0 * dl - 3.0) * (2.0 * dl - 1.0));
+    }
+  }
+  // c_m = Pbar_mm / sin^m(theta) = (-1)^m sqrt(prod_{i<=m} (2i+1)/(2i) / (4 pi))
+  std::vector<double> cm(mmax + 1);
+  {
+    dd c2 = {1.0 / (4.0 * M_PI), 0.0};
+    // 1/(4 pi) to double-double accuracy
+    c2.lo = std::fma(-c2.hi, 4.0 * M_PI, 1.0) / (4.0 * M_PI);
+    for (int m = 0; m <= mmax; ++m) {
+      if (m > 0) {
+        c2 = dd_mul_d(c2, 2.0 * m + 1.0);
+        c2 = dd_div_d(c2, 2.0 * m);
+      }
+      double v = dd_sqrt(c2);
+      cm[m] = (m & 1) ? -v : v;
+    }
+  }
+  const int npairs = M / 4;
+  std::vector<double> rx(npairs), rs(npairs), pn(L + 1);
+  for (int j = 1; j <= npairs; ++j) {
+    const double th = M_PI * (double)j / (double)(M / 2);
+    rx[j - 1] = std::cos(th);
+    rs[j - 1] = std::sin(th);
+  }
+  for (int l = 0; l <= L; ++l) pn[l] = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+
+  LegTables& t = p->leg;
+  t.npairs = npairs;
+  t.blocks_per_m = (npairs + LEG_PAIRS_PER_WARP - 1) / LEG_PAIRS_PER_WARP;
+  NUSHT_TRY(dev_alloc((void**)&t.c, nalm * 8, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&t.ahat, nalm * 8, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&t.dshift, nalm, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&t.cm, (mmax + 1) * 8, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&t.ring_x, npairs * 8, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&t.ring_s, npairs * 8, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&t.pole_norm, (L + 1) * 8, &p->bytes));
+  NUSHT_CUDA(cudaMemcpyAsync(t.c, c.data(), nalm * 8, cudaMemcpyHostToDevice, s));
+  NUSHT_CUDA(cudaMemcpyAsync(t.ahat, ah.data(), nalm * 8, cudaMemcpyHostToDevice, s));
+  NUSHT_CUDA(cudaMemcpyAsync(t.dshift, dsh.data(), nalm, cudaMemcpyHostToDevice, s));
+  NUSHT_CUDA(cudaMemcpyAsync(t.cm, cm.data(), (mmax + 1) * 8, cudaMemcpyHostToDevice, s));
+  NUSHT_CUDA(cudaMemcpyAsync(t.ring_x, rx.data(), npairs * 8, cudaMemcpyHostToDevice, s));
+  NUSHT_CUDA(cudaMemcpyAsync(t.ring_s, rs.data(), npairs * 8, cudaMemcpyHostToDevice, s));
+  NUSHT_CUDA(cudaMemcpyAsync(t.pole_norm, pn.data(), (L + 1) * 8, cudaMemcpyHostToDevice, s));
+
+  // probe every (order, ring block), keep the significant ones (m ascending:
+  // the longest recurrences are issued first)
+  const int ntotal = (mmax + 1) * t.blocks_per_m;
+  t.nitems_total = ntotal;
+  int* dflags = nullptr;
+  NUSHT_TRY(dev_alloc((void**)&dflags, (size_t)ntotal * 4, nullptr));
+  LegArgs a = make_args(p);
+  a.items = nullptr;
+  legendre_probe_k<<<(ntotal + 3) / 4, 128, 0, s>>>(a, ntotal, dflags);
+  cudaError_t e = cudaGetLastError();
+  std::vector<int> flags(ntotal);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flags.data(), dflags, (size_t)ntotal * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(dflags);
+  if (e != cudaSuccess) return cuda_status(e, "legendre probe");
+  std::vector<int> items;
+  items.reserve(ntotal);
+  for (int i = 0; i < ntotal; ++i)
+    if (flags[i]) items.push_back(((i / t.blocks_per_m) << 16) | (i % t.blocks_per_m));
+  t.nitems = (int)items.size();
+  NUSHT_TRY(dev_alloc((void**)&t.items, std::max<size_t>(1, items.size()) * 4, &p->bytes));
+  if (!items.empty())
+    NUSHT_CUDA(cudaMemcpyAsync(t.items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s));
+  NUSHT_CUDA(cudaStreamSynchronize(s));
+  return NUSHT_OK;
+}
+
+int legendre_synth(nusht_plan_t p, const void* d_alm, cudaStream_t s) {
+  const int64_t nalm = p->nalm;
+  const int tb = 256;
+  const int nb = (int)((nalm + tb - 1) / tb);
+  LegArgs a = make_args(p);
+  const int nitems = p->leg.nitems;
+  if (p->precision == NUSHT_FP64) {
+    scale_alm_k<double, double><<<nb, tb, 0, s>>>((const double*)d_alm, p->leg.ahat, nalm, p->lmax,
+                                                  (double2*)p->atilde);
+    if (nitems > 0)
+      legendre_synth_k<double><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const double2*)p->atilde, (double2*)p->G, nitems);
+    poles_synth_k<double, double><<<1, 256, 0, s>>>((const double*)d_alm, p->leg.pole_norm, p->lmax, p->sz.M,
+                                                    (double2*)p->G);
+  } else {
+    scale_alm_k<float, float><<<nb, tb, 0, s>>>((const float*)d_alm, p->leg.ahat, nalm, p->lmax, (float2*)p->atilde);
+    if (nitems > 0)
+      legendre_synth_k<float><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float2*)p->atilde, (float2*)p->G, nitems);
+    poles_synth_k<float, float><<<1, 256, 0, s>>>((const float*)d_alm, p->leg.pole_norm, p->lmax, p->sz.M,
+                                                  (float2*)p->G);
+  }
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
+  const int64_t nalm = p->nalm;
+  LegArgs a = make_args(p);
+  const int nitems = p->leg.nitems;
+  const int tb = 256;
+  const int nb = (int)((nalm + tb - 1) / tb);
+  if (p->precision == NUSHT_FP64) {
+    if (nitems > 0)
+      legendre_adj_k<double><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const double2*)p->Ghat, (double2*)p->partial, nitems,
+                                                              nalm);
+    adj_reduce_k<double><<<nb, tb, 0, s>>>((const double2*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
+                                           p->leg.pole_norm, (const double2*)p->Ghat, p->lmax, p->sz.M,
+                                           (double2*)d_alm);
+  } else {
+    if (nitems > 0)
+      legendre_adj_k<float><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float2*)p->Ghat, (float2*)p->partial, nitems,
+                                                             nalm);
+    adj_reduce_k<float><<<nb, tb, 0, s>>>((const float2*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
+                                          p->leg.pole_norm, (const float2*)p->Ghat, p->lmax, p->sz.M, (float2*)d_alm);
+  }
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+}  // namespace nusht

@@ -1,0 +1,559 @@
+// nufft.cu -- the type 2 / type 1 NUFFT steps N and N^dagger (Sec. 2.2,
+// Sec. 3) on the doubled torus, with the exponential-of-semicircle kernel
+// psi(z) = exp(beta (sqrt(1 - z^2) - 1)), |z| <= 1, of width w fine-grid cells:
+//   * point set-up: fold (theta, phi) onto [0, 2 pi)^2, first tap and
+//     fractional offset in double, bin sort (tiles of BIN x BIN cells),
+//     FP64 kernel values per point;
+//   * deconv_pad / deconv_trunc: divide by the kernel's Fourier transform,
+//     zero-pad / truncate between the theta spectrum [m][k] and the fine
+//     spectrum [k][m] (a tiled transpose through shared memory);
+//   * interp: f_i = sum_{a,b} psi1_a psi2_b u[i1 + a, i2 + b]  (type 2);
+//   * spread: u[i1 + a, i2 + b] += f_i psi1_a psi2_b  (type 1), accumulated
+//     in a shared-memory tile per bin and flushed once with atomics.
+// Spreading and interpolation read the same kernel values, so the fast
+// adjoint is the exact transpose of the fast synthesis.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "nusht_internal.cuh"
+
+namespace nusht {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int BIN = 32;       // bin edge in fine-grid cells
+constexpr int SUBMAX = 256;   // points per spreading subproblem
+constexpr int WMAX = 16;
+
+template <typename T>
+struct V2;
+template <>
+struct V2<double> {
+  using t = double2;
+};
+template <>
+struct V2<float> {
+  using t = float2;
+};
+
+__device__ __forceinline__ double es_psi(double z, double beta) {
+  double r = 1.0 - z * z;
+  return r > 0.0 ? exp(beta * (sqrt(r) - 1.0)) : 0.0;
+}
+__device__ __forceinline__ float es_psif(float z, float beta) {
+  float r = 1.0f - z * z;
+  return r > 0.0f ? expf(beta * (sqrtf(r) - 1.0f)) : 0.0f;
+}
+// d psi / dz
+__device__ __forceinline__ double es_dpsi(double z, double beta) {
+  double r = 1.0 - z * z;
+  if (!(r > 0.0)) return 0.0;
+  double sr = sqrt(r);
+  return exp(beta * (sr - 1.0)) * beta * (-z) / sr;
+}
+__device__ __forceinline__ float es_dpsif(float z, float beta) {
+  float r = 1.0f - z * z;
+  if (!(r > 0.0f)) return 0.0f;
+  float sr = sqrtf(r);
+  return expf(beta * (sr - 1.0f)) * beta * (-z) / sr;
+}
+
+// fold a coordinate onto [0, 2 pi) and split it into the first kernel tap
+// (wrapped to [0, n)) and the offset t - i0 in (w/2 - 1, w/2]
+__device__ __forceinline__ void tap(double x, int n, int w, int& i0w, double& off) {
+  const double twopi = 6.283185307179586476925286766559;
+  double xr = x - twopi * floor(x * (1.0 / twopi));
+  if (xr >= twopi || xr < 0.0) xr = 0.0;
+  double t = xr * ((double)n / twopi);
+  double i0 = ceil(t - 0.5 * w);
+  off = t - i0;
+  int i = (int)i0;
+  if (i < 0) i += n;
+  if (i >= n) i -= n;
+  i0w = i;
+}
+
+__global__ void prep_k(const double* __restrict__ pts, int64_t npts, int n1, int n2, int w, int nb2,
+                       int* __restrict__ binid) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npts) return;
+  int i1, i2;
+  double o1, o2;
+  tap(pts[2 * i], n1, w, i1, o1);
+  tap(pts[2 * i + 1], n2, w, i2, o2);
+  binid[i] = (i1 / BIN) * nb2 + (i2 / BIN);
+}
+
+// sorted point s <- caller's point perm[s]: first taps, and kernel values
+// (FP64: psi[s][0..w) along theta then psi[s][w..2w) along phi) or the
+// offsets (MIXED, kernel evaluated on the fly in float)
+__global__ void gather_k(const double* __restrict__ pts, const int* __restrict__ perm, int64_t npts, int n1, int n2,
+                         int w, double beta, int* __restrict__ cell, double* __restrict__ psi,
+                         float* __restrict__ offf, double* __restrict__ xy) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= npts) return;
+  const int i = perm[s];
+  int i1, i2;
+  double o1, o2;
+  const double th = pts[2 * (int64_t)i], ph = pts[2 * (int64_t)i + 1];
+  xy[2 * s] = th;
+  xy[2 * s + 1] = ph;
+  tap(th, n1, w, i1, o1);
+  tap(ph, n2, w, i2, o2);
+  cell[2 * s] = i1;
+  cell[2 * s + 1] = i2;
+  const double sc = 2.0 / w;
+  if (psi) {
+    double* ps = psi + s * 2 * w;
+    for (int a = 0; a < w; ++a) ps[a] = es_psi((o1 - a) * sc, beta);
+    for (int b = 0; b < w; ++b) ps[w + b] = es_psi((o2 - b) * sc, beta);
+  }
+  if (offf) {
+    offf[2 * s] = (float)o1;
+    offf[2 * s + 1] = (float)o2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// deconvolution with transpose
+// ---------------------------------------------------------------------------
+// fine spectrum H[k1][m] (n1 x n2h) from the theta spectrum Ghat[m][kk] (M)
+template <typename T>
+__global__ void deconv_pad_k(const typename V2<T>::t* __restrict__ Gh, typename V2<T>::t* __restrict__ H, int lmax,
+                             int mmax, int M, int n1, int n2h, const double* __restrict__ d1,
+                             const double* __restrict__ d2) {
+  using T2 = typename V2<T>::t;
+  __shared__ T2 tile[32][33];
+  const int k0 = blockIdx.y * 32, m0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  // is this row tile entirely in the zero band lmax < k1 < n1 - lmax?
+  const bool zero_rows = (k0 > lmax) && (k0 + 31 < n1 - lmax);
+  const bool zero_cols = m0 > mmax;
+  if (!zero_rows && !zero_cols) {
+    // load Ghat[m0 + r][kk(k0 + tx)] for r = ty, ty + 8, ...
+    const int k1 = k0 + tx;
+    int k = 0;
+    bool kv = false;
+    if (k1 < n1) {
+      if (k1 <= lmax) {
+        k = k1;
+        kv = true;
+      } else if (k1 >= n1 - lmax) {
+        k = k1 - n1;
+        kv = true;
+      }
+    }
+    const int kk = kv ? (k < 0 ? k + M : k) : 0;
+    const double f1 = kv ? d1[k + lmax] : 0.0;
+    for (int r = ty; r < 32; r += 8) {
+      const int m = m0 + r;
+      T2 v;
+      v.x = v.y = (T)0;
+      if (kv && m <= mmax) {
+        T2 g = Gh[(size_t)m * M + kk];
+        const double f = f1 * d2[m];
+        v.x = (T)(g.x * f);
+        v.y = (T)(g.y * f);
+      }
+      tile[r][tx] = v;
+    }
+    __syncthreads();
+  }
+  for (int r = ty; r < 32; r += 8) {
+    const int k1 = k0 + r, m = m0 + tx;
+    if (k1 >= n1 || m >= n2h) continue;
+    T2 v;
+    if (zero_rows || zero_cols) {
+      v.x = v.y = (T)0;
+    } else {
+      v = tile[tx][r];
+    }
+    H[(size_t)k1 * n2h + m] = v;
+  }
+}
+
+// theta spectrum Gt[m][kk] from the fine spectrum H[k1][m] (after the r2c FFT)
+template <typename T>
+__global__ void deconv_trunc_k(const typename V2<T>::t* __restrict__ H, typename V2<T>::t* __restrict__ Gt, int lmax,
+                               int mmax, int M, int n1, int n2h, const double* __restrict__ d1,
+                               const double* __restrict__ d2) {
+  using T2 = typename V2<T>::t;
+  __shared__ T2 tile[32][33];
+  const int kk0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  // load H[k1(kk0 + r)][m0 + tx]
+  for (int r = ty; r < 32; r += 8) {
+    const int kk = kk0 + r, m = m0 + tx;
+    T2 v;
+    v.x = v.y = (T)0;
+    if (kk < M && m <= mmax) {
+      const int k = (kk <= M / 2) ? kk : kk - M;
+      if (k >= -lmax && k <= lmax) {
+        const int k1 = k < 0 ? k + n1 : k;
+        T2 h = H[(size_t)k1 * n2h + m];
+        const double f = d1[k + lmax] * d2[m];
+        v.x = (T)(h.x * f);
+        v.y = (T)(h.y * f);
+      }
+    }
+    tile[r][tx] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int m = m0 + r, kk = kk0 + tx;
+    if (m <= mmax && kk < M) Gt[(size_t)m * M + kk] = tile[tx][r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// interpolation (type 2): one thread per sorted point
+// ---------------------------------------------------------------------------
+template <typename T, bool GRAD>
+__global__ void __launch_bounds__(128) interp_k(const T* __restrict__ grid, int64_t stride, int n1, int n2, int w,
+                                                float betaf, double beta, const int* __restrict__ cell,
+                                                const double* __restrict__ psi, const float* __restrict__ offf,
+                                                const double* __restrict__ xy, const int* __restrict__ perm,
+                                                int64_t npts, T* __restrict__ out, T* __restrict__ dth,
+                                                T* __restrict__ dph) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= npts) return;
+  const int i1 = cell[2 * s], i2 = cell[2 * s + 1];
+  T p1[WMAX], p2[WMAX], q1[WMAX], q2[WMAX];
+  if (GRAD) {
+    // kernel values and derivatives on the fly (not the hot path)
+    int j1, j2;
+    double o1, o2;
+    tap(xy[2 * s], n1, w, j1, o1);
+    tap(xy[2 * s + 1], n2, w, j2, o2);
+    const double sc = 2.0 / w;
+#pragma unroll
+    for (int a = 0; a < WMAX; ++a) {
+      if (a < w) {
+        if (sizeof(T) == 8) {
+          p1[a] = (T)es_psi((o1 - a) * sc, beta);
+          p2[a] = (T)es_psi((o2 - a) * sc, beta);
+          q1[a] = (T)es_dpsi((o1 - a) * sc, beta);
+          q2[a] = (T)es_dpsi((o2 - a) * sc, beta);
+        } else {
+          const float scf = 2.0f / w;
+          p1[a] = (T)es_psif(((float)o1 - a) * scf, betaf);
+          p2[a] = (T)es_psif(((float)o2 - a) * scf, betaf);
+          q1[a] = (T)es_dpsif(((float)o1 - a) * scf, betaf);
+          q2[a] = (T)es_dpsif(((float)o2 - a) * scf, betaf);
+        }
+      }
+    }
+  } else if (psi) {
+    const double* ps = psi + s * 2 * w;
+#pragma unroll
+    for (int a = 0; a < WMAX; ++a)
+      if (a < w) {
+        p1[a] = (T)ps[a];
+        p2[a] = (T)ps[w + a];
+      }
+  } else {
+    const float o1 = offf[2 * s], o2 = offf[2 * s + 1];
+    const float scf = 2.0f / w;
+#pragma unroll
+    for (int a = 0; a < WMAX; ++a)
+      if (a < w) {
+        p1[a] = (T)es_psif((o1 - a) * scf, betaf);
+        p2[a] = (T)es_psif((o2 - a) * scf, betaf);
+      }
+  }
+  const bool wrap2 = i2 + w > n2;
+  T acc = 0, g1 = 0, g2 = 0;
+#pragma unroll
+  for (int a = 0; a < WMAX; ++a) {
+    if (a < w) {
+      int r = i1 + a;
+      if (r >= n1) r -= n1;
+      const T* row = grid + (int64_t)r * stride;
+      T in = 0, ind = 0;
+      if (!wrap2) {
+#pragma unroll
+        for (int b = 0; b < WMAX; ++b)
+          if (b < w) {
+            const T u = row[i2 + b];
+            in = fma(p2[b], u, in);
+            if (GRAD) ind = fma(q2[b], u, ind);
+          }
+      } else {
+#pragma unroll
+        for (int b = 0; b < WMAX; ++b)
+          if (b < w) {
+            int c = i2 + b;
+            if (c >= n2) c -= n2;
+            const T u = row[c];
+            in = fma(p2[b], u, in);
+            if (GRAD) ind = fma(q2[b], u, ind);
+          }
+      }
+      acc = fma(p1[a], in, acc);
+      if (GRAD) {
+        g1 = fma(q1[a], in, g1);
+        g2 = fma(p1[a], ind, g2);
+      }
+    }
+  }
+  const int i = perm[s];
+  if (!GRAD) {
+    out[i] = acc;
+  } else {
+    // d/dx psi((x - x_j)/alpha) = psi'(z) / alpha, alpha = w pi / n
+    const T a1 = (T)((double)n1 / (w * 3.14159265358979323846));
+    const T a2 = (T)((double)n2 / (w * 3.14159265358979323846));
+    if (dth) dth[i] = g1 * a1;
+    if (dph) dph[i] = g2 * a2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// spreading (type 1): one warp per subproblem, one point at a time, the
+// w x w cells of a point spread over the lanes (no two lanes share a cell),
+// accumulated in a shared-memory tile with halo, flushed once with atomics
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(32) spread_k(T* __restrict__ grid, int64_t stride, int n1, int n2, int w, int nb2,
+                                               float betaf, const int* __restrict__ sub, const int* __restrict__ cell,
+                                               const double* __restrict__ psi, const float* __restrict__ offf,
+                                               const int* __restrict__ perm, const T* __restrict__ f) {
+  extern __shared__ unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  const int lane = threadIdx.x;
+  const int tw = BIN + w - 1;
+  const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
+  const int r0 = (bin / nb2) * BIN, c0 = (bin % nb2) * BIN;
+  for (int t = lane; t < tw * tw; t += 32) tile[t] = (T)0;
+  __syncwarp();
+  // this lane's cells of a point: (a, b) for idx = lane + 32 t < w^2
+  const int nc = w * w;
+  int ca[8], cb[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    int idx = lane + 32 * t;
+    ca[t] = idx < nc ? idx / w : 0;
+    cb[t] = idx < nc ? idx % w : 0;
+  }
+  const float scf = 2.0f / w;
+  for (int q = 0; q < cnt; ++q) {
+    const int64_t s = (int64_t)start + q;
+    const int lr = cell[2 * s] - r0, lc = cell[2 * s + 1] - c0;
+    const T fv = f[perm[s]];
+    // lanes 0..w-1: f psi1_a ; lanes w..2w-1: psi2_b
+    T kv = 0;
+    if (lane < 2 * w) {
+      if (psi) {
+        kv = (T)psi[s * 2 * w + lane];
+      } else {
+        const int d = lane < w ? 0 : 1;
+        const int a = lane < w ? lane : lane - w;
+        kv = (T)es_psif((offf[2 * s + d] - a) * scf, betaf);
+      }
+      if (lane < w) kv *= fv;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (32 * t < nc) {
+        const T va = __shfl_sync(FULL, kv, ca[t]);
+        const T vb = __shfl_sync(FULL, kv, w + cb[t]);
+        if (lane + 32 * t < nc) {
+          T* cellp = tile + (lr + ca[t]) * tw + (lc + cb[t]);
+          *cellp = fma(va, vb, *cellp);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  __syncwarp();
+  for (int t = lane; t < tw * tw; t += 32) {
+    const T v = tile[t];
+    if (v != (T)0) {
+      int r = r0 + t / tw, c = c0 + t % tw;
+      while (r >= n1) r -= n1;
+      while (c >= n2) c -= n2;
+      atomicAdd(grid + (int64_t)r * stride + c, v);
+    }
+  }
+}
+
+}  // namespace
+
+void free_points(nusht_plan_t p) {
+  PointData& d = p->pts;
+  dev_free(d.perm);
+  dev_free(d.cell);
+  dev_free(d.psi);
+  dev_free(d.xy);
+  dev_free(d.off);
+  dev_free(d.sub);
+  d = PointData();
+}
+
+int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  PointData& d = p->pts;
+  const int nb1 = (z.n1 + BIN - 1) / BIN, nb2 = (z.n2 + BIN - 1) / BIN;
+  const bool dbl = p->precision == NUSHT_FP64;
+  if (npts > d.cap) {
+    size_t before = p->bytes;
+    dev_free(d.perm);
+    dev_free(d.cell);
+    dev_free(d.psi);
+    dev_free(d.off);
+    dev_free(d.xy);
+    d.perm = nullptr;
+    d.cell = nullptr;
+    d.psi = nullptr;
+    d.off = nullptr;
+    d.xy = nullptr;
+    p->bytes = before - std::min(before, d.bytes);
+    d.bytes = 0;
+    NUSHT_TRY(dev_alloc((void**)&d.perm, (size_t)npts * 4, &d.bytes));
+    NUSHT_TRY(dev_alloc((void**)&d.cell, (size_t)npts * 8, &d.bytes));
+    NUSHT_TRY(dev_alloc((void**)&d.xy, (size_t)npts * 16, &d.bytes));
+    if (dbl)
+      NUSHT_TRY(dev_alloc((void**)&d.psi, (size_t)npts * 2 * z.w * 8, &d.bytes));
+    else
+      NUSHT_TRY(dev_alloc((void**)&d.off, (size_t)npts * 8, &d.bytes));
+    p->bytes += d.bytes;
+    d.cap = npts;
+  }
+  d.npts = npts;
+  d.nbins1 = nb1;
+  d.nbins2 = nb2;
+  dev_free(d.sub);
+  d.sub = nullptr;
+  d.nsub = 0;
+  if (npts == 0) return NUSHT_OK;
+  // bin ids on the device, counting sort on the host (stable, so that the
+  // order inside a bin, and with it every summation order, is deterministic)
+  int* dbin = nullptr;
+  NUSHT_TRY(dev_alloc((void**)&dbin, (size_t)npts * 4, nullptr));
+  const int tb = 256;
+  const int nblk = (int)((npts + tb - 1) / tb);
+  prep_k<<<nblk, tb, 0, s>>>(d_pts, npts, z.n1, z.n2, z.w, nb2, dbin);
+  std::vector<int> bins(npts);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bins.data(), dbin, (size_t)npts * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(dbin);
+  if (e != cudaSuccess) return cuda_status(e, "point binning");
+  const int nbins = nb1 * nb2;
+  std::vector<int64_t> off(nbins + 1, 0);
+  for (int64_t i = 0; i < npts; ++i) off[bins[i] + 1]++;
+  for (int b = 0; b < nbins; ++b) off[b + 1] += off[b];
+  std::vector<int> perm(npts);
+  {
+    std::vector<int64_t> cur(off.begin(), off.end() - 1);
+    for (int64_t i = 0; i < npts; ++i) perm[cur[bins[i]]++] = (int)i;
+  }
+  std::vector<int> sub;
+  for (int b = 0; b < nbins; ++b)
+    for (int64_t st = off[b]; st < off[b + 1]; st += SUBMAX) {
+      sub.push_back(b);
+      sub.push_back((int)st);
+      sub.push_back((int)std::min<int64_t>(SUBMAX, off[b + 1] - st));
+    }
+  d.nsub = (int)(sub.size() / 3);
+  NUSHT_TRY(dev_alloc((void**)&d.sub, std::max<size_t>(1, sub.size()) * 4, &p->bytes));
+  NUSHT_CUDA(cudaMemcpyAsync(d.perm, perm.data(), (size_t)npts * 4, cudaMemcpyHostToDevice, s));
+  if (!sub.empty()) NUSHT_CUDA(cudaMemcpyAsync(d.sub, sub.data(), sub.size() * 4, cudaMemcpyHostToDevice, s));
+  gather_k<<<nblk, tb, 0, s>>>(d_pts, d.perm, npts, z.n1, z.n2, z.w, z.beta, d.cell, dbl ? d.psi : nullptr,
+                               dbl ? nullptr : d.off, d.xy);
+  NUSHT_CUDA(cudaGetLastError());
+  NUSHT_CUDA(cudaStreamSynchronize(s));
+  return NUSHT_OK;
+}
+
+int deconv_pad(nusht_plan_t p, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  const int n2h = z.n2 / 2 + 1;
+  dim3 blk(32, 8), grd((n2h + 31) / 32, (z.n1 + 31) / 32);
+  if (p->precision == NUSHT_FP64)
+    deconv_pad_k<double><<<grd, blk, 0, s>>>((const double2*)p->Ghat, (double2*)p->fine, z.lmax, z.mmax, z.M, z.n1,
+                                             n2h, p->deconv1, p->deconv2);
+  else
+    deconv_pad_k<float><<<grd, blk, 0, s>>>((const float2*)p->Ghat, (float2*)p->fine, z.lmax, z.mmax, z.M, z.n1, n2h,
+                                            p->deconv1, p->deconv2);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int deconv_trunc(nusht_plan_t p, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  const int n2h = z.n2 / 2 + 1;
+  dim3 blk(32, 8), grd((z.M + 31) / 32, (z.mmax + 1 + 31) / 32);
+  if (p->precision == NUSHT_FP64)
+    deconv_trunc_k<double><<<grd, blk, 0, s>>>((const double2*)p->fine, (double2*)p->Ghat, z.lmax, z.mmax, z.M, z.n1,
+                                               n2h, p->deconv1, p->deconv2);
+  else
+    deconv_trunc_k<float><<<grd, blk, 0, s>>>((const float2*)p->fine, (float2*)p->Ghat, z.lmax, z.mmax, z.M, z.n1, n2h,
+                                              p->deconv1, p->deconv2);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int interp(nusht_plan_t p, void* d_map, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  const int64_t n = p->pts.npts;
+  if (n == 0) return NUSHT_OK;
+  const int64_t stride = 2 * (z.n2 / 2 + 1);
+  const int tb = 128;
+  const int nb = (int)((n + tb - 1) / tb);
+  if (p->precision == NUSHT_FP64)
+    interp_k<double, false><<<nb, tb, 0, s>>>((const double*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
+                                              p->pts.cell, p->pts.psi, nullptr, nullptr, p->pts.perm, n,
+                                              (double*)d_map, nullptr, nullptr);
+  else
+    interp_k<float, false><<<nb, tb, 0, s>>>((const float*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
+                                             p->pts.cell, nullptr, p->pts.off, nullptr, p->pts.perm, n,
+                                             (float*)d_map, nullptr, nullptr);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  const int64_t n = p->pts.npts;
+  if (n == 0) return NUSHT_OK;
+  const int64_t stride = 2 * (z.n2 / 2 + 1);
+  const int tb = 128;
+  const int nb = (int)((n + tb - 1) / tb);
+  if (p->precision == NUSHT_FP64)
+    interp_k<double, true><<<nb, tb, 0, s>>>((const double*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
+                                             p->pts.cell, nullptr, nullptr, p->pts.xy, p->pts.perm, n, nullptr,
+                                             (double*)d_dth, (double*)d_dph);
+  else
+    interp_k<float, true><<<nb, tb, 0, s>>>((const float*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
+                                            p->pts.cell, nullptr, nullptr, p->pts.xy, p->pts.perm, n, nullptr,
+                                            (float*)d_dth, (float*)d_dph);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  const int64_t stride = 2 * (z.n2 / 2 + 1);
+  const size_t es = p->precision == NUSHT_FP64 ? 8 : 4;
+  NUSHT_CUDA(cudaMemsetAsync(p->fine, 0, (size_t)z.n1 * stride * es, s));
+  if (p->pts.nsub == 0) return NUSHT_OK;
+  const int tw = BIN + z.w - 1;
+  const size_t sm = (size_t)tw * tw * es;
+  if (p->precision == NUSHT_FP64)
+    spread_k<double><<<p->pts.nsub, 32, sm, s>>>((double*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2,
+                                                 (float)z.beta, p->pts.sub, p->pts.cell, p->pts.psi, nullptr,
+                                                 p->pts.perm, (const double*)d_map);
+  else
+    spread_k<float><<<p->pts.nsub, 32, sm, s>>>((float*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, (float)z.beta,
+                                                p->pts.sub, p->pts.cell, nullptr, p->pts.off, p->pts.perm,
+                                                (const float*)d_map);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+}  // namespace nusht

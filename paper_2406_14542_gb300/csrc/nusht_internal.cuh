@@ -1,0 +1,156 @@
+// nusht_internal.cuh -- plan layout and shared declarations of the CUDA
+// library (not part of the public ABI; see include/nusht.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nusht.h"
+
+namespace nusht {
+
+// ---------------------------------------------------------------------------
+// Error plumbing: every host entry point returns a status and records a
+// thread-local message.
+// ---------------------------------------------------------------------------
+int set_error(int code, const std::string& msg);
+int cuda_status(cudaError_t e, const char* what);
+int cufft_status(cufftResult r, const char* what);
+
+#define NUSHT_CUDA(call)                                                  \
+  do {                                                                    \
+    cudaError_t _e = (call);                                              \
+    if (_e != cudaSuccess) return ::nusht::cuda_status(_e, #call);        \
+  } while (0)
+#define NUSHT_CUFFT(call)                                                 \
+  do {                                                                    \
+    cufftResult _r = (call);                                              \
+    if (_r != CUFFT_SUCCESS) return ::nusht::cufft_status(_r, #call);     \
+  } while (0)
+#define NUSHT_TRY(call)                                                   \
+  do {                                                                    \
+    int _s = (call);                                                      \
+    if (_s != NUSHT_OK) return _s;                                        \
+  } while (0)
+
+// Device allocation through one place so that tests can inject failures.
+int dev_alloc(void** p, size_t bytes, size_t* counter);
+void dev_free(void* p);
+
+// ---------------------------------------------------------------------------
+// Legendre work decomposition.
+// Ring pairs (theta_j, pi - theta_j) for j = 1..M/4 (the poles are handled
+// apart).  One warp owns RINGS_PER_WARP = 32*K consecutive pairs of one
+// order m: a "work item".
+// ---------------------------------------------------------------------------
+constexpr int LEG_K = 4;                 // ring pairs per lane
+constexpr int LEG_PAIRS_PER_WARP = 32 * LEG_K;
+constexpr int LEG_SEG_BITS = 48;         // rescaled normalisation kept in [1, 2^(48+8))
+
+// Start exponent threshold of the scaled phase: values below 2^-300 (relative
+// to the rescaled normalisation) are not accumulated (Sec. 3: on-the-fly
+// recurrence with scaled exponents so that high-l values do not underflow).
+constexpr int LEG_TINY_EXP = -300;
+constexpr int LEG_STEP_EXP = 256;        // scaled-phase exponent step
+
+struct LegTables {
+  // per (l, m) packed m-major, nalm entries
+  double* c = nullptr;        // c_lm = (l-1-m)(l-1+m)/((2l-3)(2l-1)) (0 for l = m, m+1)
+  double* ahat = nullptr;     // rescaled normalisation Ahat_lm (>= 1)
+  int8_t* dshift = nullptr;   // rescale exponent applied before step l (0 = none)
+  // per m
+  double* cm = nullptr;       // Pbar_mm / sin^m(theta) = signed c_m
+  // per ring pair j = 1..M/4 (index j-1)
+  double* ring_x = nullptr;   // cos(theta_j)
+  double* ring_s = nullptr;   // sin(theta_j)
+  double* pole_norm = nullptr; // sqrt((2l+1)/(4 pi)), l = 0..lmax
+  int* items = nullptr;       // work list: (m << 16) | block
+  int nitems = 0;
+  int nitems_total = 0;
+  int blocks_per_m = 0;       // ring blocks per order
+  int npairs = 0;             // M/4
+};
+
+struct PointData {
+  int64_t npts = 0;
+  int64_t cap = 0;
+  int* perm = nullptr;        // sorted index -> caller index
+  int* cell = nullptr;        // sorted: first tap (i1, i2) interleaved, wrapped to [0, n)
+  double* psi = nullptr;      // FP64: kernel values [npts][2w] (w along theta, then w along phi)
+  double* xy = nullptr;       // sorted coordinates (theta, phi), for the position gradient
+  float* off = nullptr;       // MIXED: fractional offsets (t - i) per dim, [2][npts]
+  // subproblems for spreading: (bin index, first sorted point, count)
+  int* sub = nullptr;
+  int nsub = 0;
+  int nbins1 = 0, nbins2 = 0;
+  size_t bytes = 0;           // device bytes held for points (part of the plan's total)
+};
+
+struct StageEvents {
+  cudaEvent_t ev[8] = {};
+  bool ready = false;
+};
+
+}  // namespace nusht
+
+struct nusht_plan_s {
+  int device = 0;
+  int lmax = 0, mmax = 0, precision = NUSHT_FP64;
+  double eps = 0.0;
+  nusht_sizes sz{};
+  nusht_opts opts{};
+  int64_t nalm = 0;
+
+  nusht::LegTables leg;
+  nusht::PointData pts;
+
+  // kernel Fourier factors: d1[k + lmax] (k = -lmax..lmax), d2[m] (m = 0..mmax)
+  double* deconv1 = nullptr;
+  double* deconv2 = nullptr;
+
+  // work buffers
+  void* atilde = nullptr;     // per-call rescaled coefficients (complex, nalm)
+  void* G = nullptr;          // doubled ring map [mmax+1][M] complex
+  void* Ghat = nullptr;       // theta spectrum [mmax+1][M] complex
+  void* fine = nullptr;       // fine spectrum / grid, n1 x (n2/2+1) complex == n1 x (n2+2) real
+  void* partial = nullptr;    // adjoint Legendre partial sums [blocks_per_m][nalm] complex
+
+  cufftHandle fft_theta = 0;  // batched 1D, length M, batch mmax+1
+  cufftHandle fft_c2r = 0;    // 2D n1 x n2 complex-to-real (in place)
+  cufftHandle fft_r2c = 0;    // 2D n1 x n2 real-to-complex (in place)
+  bool have_theta = false, have_c2r = false, have_r2c = false;
+
+  size_t bytes = 0;
+
+  // profiling
+  nusht::StageEvents ev_synth, ev_adj;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace nusht {
+
+// sizes / host math (plan.cu)
+int choose_sizes(int lmax, int mmax, double eps, int precision, const nusht_opts* o, nusht_sizes* out);
+void kernel_ft(int w, double beta, int n, int nk, double* out);
+
+// point set-up (nufft.cu)
+int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s);
+void free_points(nusht_plan_t p);
+
+// Legendre (legendre.cu)
+int legendre_build_tables(nusht_plan_t p, cudaStream_t s);
+int legendre_synth(nusht_plan_t p, const void* d_alm, cudaStream_t s);
+int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s);
+
+// NUFFT steps (nufft.cu)
+int deconv_pad(nusht_plan_t p, cudaStream_t s);
+int deconv_trunc(nusht_plan_t p, cudaStream_t s);
+int interp(nusht_plan_t p, void* d_map, cudaStream_t s);
+int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, cudaStream_t s);
+int spread(nusht_plan_t p, const void* d_map, cudaStream_t s);
+
+}  // namespace nusht

@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA path (through the C ABI) against the direct-sum oracle
+on the same seeded inputs.
+
+Tolerances (relative l2 error eps_eff of Sec. 4): 1e-10 in FP64 mode, 1e-5 in
+mixed mode (the targets of the requested accuracies); the adjoint dot test
+<y, S a> = <S^H y, a> holds to 1e-12 in FP64 because spreading and
+interpolation use the same kernel values (exact transposes), whatever eps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_14542_gb300 import build
+
+    build.build()
+    import paper_2406_14542_gb300 as nu
+
+    return torch, nu
+
+
+def dev(torch, a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def run_synth(torch, nu, L, alm, pts, prec, eps=None, mmax=None, **kw):
+    eps = eps if eps is not None else TOL[prec]
+    cd = torch.complex128 if prec == "fp64" else torch.complex64
+    plan = nu.Plan(L, dev(torch, pts), eps=eps, precision=prec, mmax=mmax, **kw)
+    f = plan.synth(dev(torch, alm, cd))
+    torch.cuda.synchronize()
+    return plan, f.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_synth_uniform63(env, prec):
+    torch, nu = env
+    L, a, pts = W.workload("uniform63")
+    _, f = run_synth(torch, nu, L, a, pts, prec)
+    ref = oracle.synth(a, pts, L)
+    e = oracle.eps_eff(ref, f)
+    assert e <= TOL[prec], e
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_adjoint_uniform63(env, prec):
+    torch, nu = env
+    L, a, pts = W.workload("uniform63")
+    y = np.random.default_rng(7).standard_normal(pts.shape[0])
+    cd = torch.complex128 if prec == "fp64" else torch.complex64
+    rd = torch.float64 if prec == "fp64" else torch.float32
+    plan = nu.Plan(L, dev(torch, pts), eps=TOL[prec], precision=prec)
+    c = plan.adjoint(dev(torch, y, rd)).cpu().numpy().astype(np.complex128)
+    ref = oracle.adjoint(y, pts, L)
+    e = oracle.eps_eff(ref, c)
+    assert e <= TOL[prec], e
+    assert np.all(c[: L + 1].imag == 0)
+
+
+@pytest.mark.parametrize("eps", [1e-10, 1e-6, 1e-3])
+def test_dot_product_fp64_any_eps(env, eps):
+    """Exact adjointness of the fast path (independent of the NUFFT tolerance)."""
+    torch, nu = env
+    L, a, pts = W.workload("uniform63")
+    y = np.random.default_rng(8).standard_normal(pts.shape[0])
+    plan, f = run_synth(torch, nu, L, a, pts, "fp64", eps=eps)
+    c = plan.adjoint(dev(torch, y)).cpu().numpy()
+    lhs = float(np.dot(y, f))
+    rhs = oracle.alm_dot(c, a, L)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("L,mmax,npts", [(0, 0, 100), (1, 1, 37), (2, 1, 500), (5, 5, 1), (100, 60, 12345),
+                                         (129, 129, 3001), (300, 17, 2000)])
+def test_small_and_ragged_fp64(env, L, mmax, npts):
+    torch, nu = env
+    a = W.alm_gaussian(L, seed=L + 1, mmax=mmax)
+    pts = W.points_uniform(npts, seed=npts)
+    _, f = run_synth(torch, nu, L, a, pts, "fp64", mmax=mmax)
+    ref = oracle.synth(a, pts, L, mmax)
+    assert oracle.eps_eff(ref, f) <= 1e-10
+    y = np.random.default_rng(1).standard_normal(npts)
+    plan = nu.Plan(L, dev(torch, pts), eps=1e-10, mmax=mmax)
+    c = plan.adjoint(dev(torch, y)).cpu().numpy()
+    cref = oracle.adjoint(y, pts, L, mmax)
+    assert oracle.eps_eff(cref, c) <= 1e-10
+
+
+def test_poles_and_any_real_coordinates(env):
+    """Points on the poles, theta outside [0, pi], negative and large phi."""
+    torch, nu = env
+    L = 40
+    a = W.alm_gaussian(L, seed=3)
+    rng = np.random.default_rng(4)
+    th = np.concatenate([[0.0, math.pi, 0.0, math.pi, 1e-9, math.pi - 1e-9],
+                         rng.uniform(-7.0, 13.0, 300)])
+    ph = np.concatenate([[0.0, 0.0, 2.0, -1.0, 0.3, 6.2], rng.uniform(-20.0, 20.0, 300)])
+    pts = np.stack([th, ph], 1)
+    _, f = run_synth(torch, nu, L, a, pts, "fp64")
+    ref = oracle.synth(a, pts, L)
+    assert oracle.eps_eff(ref, f) <= 1e-10
+    assert np.max(np.abs(f - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def test_empty_point_set(env):
+    torch, nu = env
+    L = 10
+    plan = nu.Plan(L, torch.zeros((0, 2), dtype=torch.float64, device="cuda"), eps=1e-8)
+    a = dev(torch, W.alm_gaussian(L, seed=1))
+    f = plan.synth(a)
+    assert f.numel() == 0
+    c = plan.adjoint(torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert torch.count_nonzero(c).item() == 0
+
+
+def test_repeated_calls_are_identical(env):
+    """Synthesis is bit-reproducible (no atomics); the adjoint's halo flush adds
+    tiles with atomics, so two calls agree to rounding only."""
+    torch, nu = env
+    L, a, pts = W.workload("uniform63")
+    plan = nu.Plan(L, dev(torch, pts), eps=1e-10)
+    ad = dev(torch, a)
+    f1 = plan.synth(ad).clone()
+    f2 = plan.synth(ad).clone()
+    assert torch.equal(f1, f2)
+    c1 = plan.adjoint(f1).clone()
+    c2 = plan.adjoint(f1).clone()
+    assert (torch.linalg.norm(c1 - c2) / torch.linalg.norm(c1)).item() <= 1e-14
+
+
+def test_setpts_replaces_points(env):
+    torch, nu = env
+    L = 30
+    a = W.alm_gaussian(L, seed=2)
+    p1 = W.points_uniform(1000, seed=1)
+    p2 = W.points_uniform(3000, seed=2)
+    plan = nu.Plan(L, dev(torch, p1), eps=1e-10)
+    plan.setpts(dev(torch, p2))
+    f = plan.synth(dev(torch, a)).cpu().numpy()
+    assert oracle.eps_eff(oracle.synth(a, p2, L), f) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_gl1023_subset(env, prec):
+    """lmax = 1023 on the 1024 x 2047 deflected GL grid; 10^4-point oracle subset."""
+    torch, nu = env
+    L, a, pts = W.workload("gl1023")
+    _, f = run_synth(torch, nu, L, a, pts, prec)
+    sel = W.subset(pts.shape[0], 10000)
+    ref = oracle.synth(a, pts[sel], L)
+    e = oracle.eps_eff(ref, f[sel])
+    assert e <= TOL[prec], e
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_gl1023_adjoint_msubset(env, prec):
+    torch, nu = env
+    L, _, pts = W.workload("gl1023")
+    y = np.random.default_rng(9).standard_normal(pts.shape[0])
+    rd = torch.float64 if prec == "fp64" else torch.float32
+    plan = nu.Plan(L, dev(torch, pts), eps=TOL[prec], precision=prec)
+    c = plan.adjoint(dev(torch, y, rd)).cpu().numpy().astype(np.complex128)
+    rng = np.random.default_rng(10)
+    ms = sorted({0, 1, *rng.integers(2, L + 1, 4).tolist()})
+    ref = oracle.adjoint(y, pts, L, mlist=ms)
+    idx = np.concatenate([np.arange(oracle.lm_index(L, m, m), oracle.lm_index(L, L, m) + 1) for m in ms])
+    e = oracle.eps_eff(ref[idx], c[idx])
+    assert e <= TOL[prec], e
+
+
+def test_gl1023_dot_product_full(env):
+    torch, nu = env
+    L, a, pts = W.workload("gl1023")
+    y = np.random.default_rng(11).standard_normal(pts.shape[0])
+    plan, f = run_synth(torch, nu, L, a, pts, "fp64")
+    c = plan.adjoint(dev(torch, y)).cpu().numpy()
+    lhs = float(np.dot(y, f))
+    rhs = oracle.alm_dot(c, a, L)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
