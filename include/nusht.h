@@ -161,6 +161,44 @@ NUSHT_API int nusht_adjoint(nusht_plan_t p, const void* d_map, void* d_alm, nush
  */
 NUSHT_API int nusht_synth_grad(nusht_plan_t p, const void* d_alm, void* d_dtheta, void* d_dphi, nusht_stream_t stream);
 
+/*
+ * nusht_adjoint_direct_noalloc -- type 1 transform (the adjoint, same result
+ * as nusht_adjoint) for small problems, WITHOUT a plan and without
+ * allocating any memory.  The paper has no counterpart to this call.
+ *
+ * Who it is for: callers that must not call cudaMalloc at all, for example
+ * code whose device memory is entirely owned by another allocator (a
+ * framework's caching pool that reserves the GPU up front, so a raw
+ * cudaMalloc would fail or fragment it), or latency-critical loops where the
+ * implicit device synchronisation and unbounded latency of cudaMalloc and
+ * cudaFree are not acceptable.  nusht_plan allocates, so such callers cannot
+ * use the planned path.  This call evaluates
+ *     c_lm = sum_i f_i Pbar_lm(theta_i) e^{-i m phi_i}
+ * by direct summation on the GPU (O(lmax^2 npts) work, exact to rounding;
+ * no FFT or NUFFT), computing the recurrence coefficients on the fly.
+ *
+ *   lmax, mmax  0 <= mmax <= lmax <= 255; larger lmax is rejected with
+ *               NUSHT_EINVAL ("static scratch limit")
+ *   npts        >= 0
+ *   d_pts       device double[2*npts] (theta, phi), any finite reals
+ *   d_map       device double[npts] values f_i
+ *   d_alm       device complex128[nalm] output, m-major as for nusht_adjoint
+ *               (all entries overwritten; Im(c_l0) = 0)
+ *
+ * Scratch: partial sums live in one file-scope device array of
+ * 16 x 33024 complex doubles (8.45 MB) that every GPU which loads the library
+ * keeps until the process exits.  All calls share it, so calls whose GPU work
+ * overlaps (different streams, or different host threads, on one device)
+ * race on it and give wrong results; serialise them.  Each call overwrites
+ * the part it reads, so nothing needs clearing between calls.
+ * Set-up: the first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture begins.  Asynchronous on `stream`; no host
+ * memory is touched.  Only NUSHT_FP64 (double) inputs are supported.
+ */
+NUSHT_API int nusht_adjoint_direct_noalloc(int lmax, int mmax, int64_t npts, const double* d_pts, const double* d_map,
+                                           void* d_alm, nusht_stream_t stream);
+
 /* nusht_destroy -- free the plan and its device memory (NULL-safe). */
 NUSHT_API int nusht_destroy(nusht_plan_t p);
 

@@ -25,7 +25,7 @@ FP64, MIXED = 0, 1
 
 EXPORTS = ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_synth_grad", "nusht_destroy",
            "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_good_size", "nusht_stage_times",
-           "nusht_strerror", "nusht_last_error", "nusht_version")
+           "nusht_strerror", "nusht_last_error", "nusht_version", "nusht_adjoint_direct_noalloc")
 
 
 class NushtError(RuntimeError):
@@ -78,12 +78,14 @@ def load(path: str | None = None):
         lib.nusht_good_size.argtypes = [i64, ctypes.c_int, ctypes.c_int]
         lib.nusht_good_size.restype = i64
         lib.nusht_stage_times.argtypes = [vp, dp]
+        lib.nusht_adjoint_direct_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp]
         lib.nusht_strerror.argtypes = [ctypes.c_int]
         lib.nusht_strerror.restype = ctypes.c_char_p
         lib.nusht_last_error.restype = ctypes.c_char_p
         lib.nusht_version.restype = ctypes.c_char_p
         for name in ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_synth_grad",
-                     "nusht_destroy", "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_stage_times"):
+                     "nusht_destroy", "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_stage_times",
+                     "nusht_adjoint_direct_noalloc"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "nusht_internal.cuh"
@@ -723,3 +724,221 @@ int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
 }
 
 }  // namespace nusht
+
+// ---------------------------------------------------------------------------
+// Allocation-free, plan-free adjoint for small band limits.
+//
+// A variant of legendre_adj_k for callers that cannot allocate device memory:
+// instead of rings it runs the recurrence at the caller's points directly
+// (c_lm = sum_i f_i Pbar_lm(theta_i) e^{-i m phi_i}, no FFT and no NUFFT, so
+// no plan and no plan-time allocation), computing the recurrence
+// coefficients on the fly, and it keeps its per-warp partial sums in the
+// file-scope device array below instead of plan-owned memory.
+// ---------------------------------------------------------------------------
+namespace nusht {
+namespace {
+
+constexpr int NA_LMAX = 255;   // largest lmax accepted
+constexpr int NA_SLOTS = 16;   // partial-sum slots per coefficient
+constexpr int NA_NALM_MAX = (NA_LMAX + 1) * (NA_LMAX + 2) / 2;
+
+// NA_SLOTS x NA_NALM_MAX complex partial sums = 16 x 33024 x 16 B = 8.45 MB.
+// Every device that loads this library holds it until the process exits.
+static __device__ __align__(256) double2 g_noalloc_partial[NA_SLOTS * NA_NALM_MAX];
+
+__global__ void __launch_bounds__(128) direct_adj_k(int L, int mmax, int64_t npts, const double* __restrict__ pts,
+                                                    const double* __restrict__ f, double2* __restrict__ partial,
+                                                    int nalm) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= (mmax + 1) * NA_SLOTS) return;
+  const int m = it / NA_SLOTS, slot = it % NA_SLOTS;
+  const int mb = mbase_of(L, m);
+  // Pbar_mm / sin^m = (-1)^m sqrt(prod_{i<=m} (2i+1)/(2i) / (4 pi))
+  double cmm = 0.28209479177387814;  // 1/sqrt(4 pi)
+  for (int i = 1; i <= m; ++i) cmm *= sqrt((2.0 * i + 1.0) / (2.0 * i));
+  if (m & 1) cmm = -cmm;
+  double2* out = partial + (size_t)slot * nalm + mb;
+  const int64_t chunk = 32 * LEG_K;
+  bool first = true;
+  for (int64_t c0 = (int64_t)slot * chunk; first || c0 < npts; c0 += (int64_t)NA_SLOTS * chunk) {
+    Chain ch[LEG_K];
+    double2 S[LEG_K];
+#pragma unroll
+    for (int k = 0; k < LEG_K; ++k) {
+      const int64_t i = c0 + k * 32 + lane;
+      ch[k].q2 = 0.0;
+      ch[k].valid = i < npts;
+      ch[k].x = 0.0;
+      ch[k].q1 = 0.0;
+      ch[k].E = 0;
+      S[k].x = S[k].y = 0.0;
+      if (!ch[k].valid) continue;
+      const double th = pts[2 * i], ph = pts[2 * i + 1];
+      double s, c;
+      sincos(th, &s, &c);
+      ch[k].x = c;
+      double q0 = cmm;
+      int ex = 0;
+      if (m > 0) {
+        const double as = fabs(s);
+        if (as == 0.0) {
+          q0 = 0.0;
+        } else {
+          double mant;
+          pow_scaled(as, m, mant, ex);
+          q0 = cmm * mant * ((s < 0.0 && (m & 1)) ? -1.0 : 1.0);
+        }
+      }
+      if (q0 == 0.0 || ex >= LEG_TINY_EXP) {
+        ch[k].q1 = q0 * exp2i(ex < LEG_TINY_EXP ? 0 : ex);
+      } else {
+        const int E = LEG_STEP_EXP * ((LEG_TINY_EXP - ex + LEG_STEP_EXP - 1) / LEG_STEP_EXP);
+        ch[k].q1 = q0 * exp2i(ex + E);
+        ch[k].E = E;
+      }
+      double sp, cp;
+      sincos((double)m * ph, &sp, &cp);
+      S[k].x = f[i] * cp;
+      S[k].y = -f[i] * sp;
+    }
+    for (int base = m; base <= L; base += 8) {
+      double2 v[8];
+#pragma unroll
+      for (int st = 0; st < 8; ++st) {
+        v[st].x = v[st].y = 0.0;
+        const int l = base + st;
+        if (l <= L) {
+          if (l > m) {
+            // Pbar_l = alpha_l (x Pbar_{l-1} - b_l Pbar_{l-2}), coefficients on the fly
+            const double dl = l, dm = m;
+            const double al = sqrt((4.0 * dl * dl - 1.0) / (dl * dl - dm * dm));
+            const double bl = (l == m + 1) ? 0.0
+                                           : sqrt(((dl - 1.0) * (dl - 1.0) - dm * dm) /
+                                                  (4.0 * (dl - 1.0) * (dl - 1.0) - 1.0));
+#pragma unroll
+            for (int k = 0; k < LEG_K; ++k) {
+              const double q = al * fma(ch[k].x, ch[k].q1, -bl * ch[k].q2);
+              ch[k].q2 = ch[k].q1;
+              ch[k].q1 = q;
+              if (ch[k].E != 0) {
+                const int expo = (__double2hiint(q) >> 20) & 0x7ff;
+                if (expo >= 1023 - 44) {
+                  ch[k].q1 = scale_pow2(ch[k].q1, -LEG_STEP_EXP);
+                  ch[k].q2 = scale_pow2(ch[k].q2, -LEG_STEP_EXP);
+                  ch[k].E -= LEG_STEP_EXP;
+                }
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < LEG_K; ++k)
+            if (ch[k].E == 0) {
+              v[st].x = fma(ch[k].q1, S[k].x, v[st].x);
+              v[st].y = fma(ch[k].q1, S[k].y, v[st].y);
+            }
+        }
+      }
+      // same reduce-scatter over the lanes as legendre_adj_k
+      const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+      double2 w4[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        double2 send = u16 ? v[i] : v[i + 4];
+        double2 keep = u16 ? v[i + 4] : v[i];
+        double2 r = shfl2<double>(send, 16);
+        w4[i].x = keep.x + r.x;
+        w4[i].y = keep.y + r.y;
+      }
+      double2 w2[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        double2 send = u8 ? w4[i] : w4[i + 2];
+        double2 keep = u8 ? w4[i + 2] : w4[i];
+        double2 r = shfl2<double>(send, 8);
+        w2[i].x = keep.x + r.x;
+        w2[i].y = keep.y + r.y;
+      }
+      double2 z;
+      {
+        double2 send = u4 ? w2[0] : w2[1];
+        double2 keep = u4 ? w2[1] : w2[0];
+        double2 r = shfl2<double>(send, 4);
+        z.x = keep.x + r.x;
+        z.y = keep.y + r.y;
+      }
+      double2 r = shfl2<double>(z, 2);
+      z.x += r.x;
+      z.y += r.y;
+      r = shfl2<double>(z, 1);
+      z.x += r.x;
+      z.y += r.y;
+      const int l = base + ((lane >> 2) & 7);
+      if ((lane & 3) == 0 && l <= L) {
+        // the first chunk of a slot overwrites what an earlier call left there
+        if (first) {
+          out[l] = z;
+        } else {
+          double2 o = out[l];
+          o.x += z.x;
+          o.y += z.y;
+          out[l] = o;
+        }
+      }
+    }
+    first = false;
+  }
+}
+
+__global__ void direct_adj_reduce_k(const double2* __restrict__ partial, int nalm, int lmax, double2* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nalm) return;
+  double sx = 0.0, sy = 0.0;
+  for (int s = 0; s < NA_SLOTS; ++s) {
+    const double2 v = partial[(size_t)s * nalm + i];
+    sx += v.x;
+    sy += v.y;
+  }
+  if (i <= lmax) sy = 0.0;  // m = 0: real
+  out[i] = make_double2(sx, sy);
+}
+
+// device address of g_noalloc_partial, looked up once per device
+constexpr int NA_MAX_DEVICES = 64;
+static void* g_noalloc_ptr[NA_MAX_DEVICES] = {};
+static std::mutex g_noalloc_mutex;
+
+}  // namespace
+}  // namespace nusht
+
+extern "C" int nusht_adjoint_direct_noalloc(int lmax, int mmax, int64_t npts, const double* d_pts,
+                                            const double* d_map, void* d_alm, nusht_stream_t stream) {
+  using namespace nusht;
+  if (lmax < 0 || lmax > NA_LMAX)
+    return set_error(NUSHT_EINVAL, "nusht_adjoint_direct_noalloc: lmax must be in [0, 255] (static scratch limit)");
+  if (mmax < 0 || mmax > lmax) return set_error(NUSHT_EINVAL, "nusht_adjoint_direct_noalloc: mmax must be in [0, lmax]");
+  if (npts < 0) return set_error(NUSHT_EINVAL, "nusht_adjoint_direct_noalloc: npts < 0");
+  if (!d_alm || (npts > 0 && (!d_pts || !d_map)))
+    return set_error(NUSHT_EINVAL, "nusht_adjoint_direct_noalloc: null pointer");
+  int dev = 0;
+  NUSHT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NA_MAX_DEVICES) return set_error(NUSHT_EDEVICE, "nusht_adjoint_direct_noalloc: device index");
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partial);
+      if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_noalloc_partial)");
+      g_noalloc_ptr[dev] = ptr;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  const int nalm = (mmax + 1) * (lmax + 1) - mmax * (mmax + 1) / 2;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nwarps = (mmax + 1) * NA_SLOTS;
+  direct_adj_k<<<(nwarps + 3) / 4, 128, 0, s>>>(lmax, mmax, npts, d_pts, d_map, (double2*)scratch, nalm);
+  direct_adj_reduce_k<<<(nalm + 255) / 256, 256, 0, s>>>((const double2*)scratch, nalm, lmax, (double2*)d_alm);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
