@@ -92,7 +92,10 @@ typedef struct {
   int deterministic; /* reserved; synthesis is bit-reproducible, the adjoint's spreading
                         flush adds tile halos with atomics (rounding-level order effects) */
   int tune;          /* reserved (0) */
-  int reserved[7];
+  int fp64_contraction; /* FP64 mode only: 1 = Legendre sums with FP64 instructions;
+                           0 (default) = FP64 recurrence, sums as float pairs on the FP32
+                           pipe (~2^-48 relative per operation; a_lm magnitudes below 1e20) */
+  int reserved[6];
 } nusht_opts;
 
 /* Sizes a plan uses; filled by nusht_plan_sizes (no GPU needed) and nusht_info. */
@@ -109,6 +112,7 @@ typedef struct {
   int nitems_total;  /* Legendre work items before the polar skip */
   int64_t npts;
   int64_t bytes_device; /* device memory held by the plan */
+  int64_t leg_triples;  /* (ring pair, l, m) triples the Legendre kernels run per call */
 } nusht_sizes;
 
 /*

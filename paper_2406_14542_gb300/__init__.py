@@ -36,14 +36,16 @@ class NushtError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("kernel_width", ctypes.c_int), ("profile", ctypes.c_int),
-                ("deterministic", ctypes.c_int), ("tune", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("deterministic", ctypes.c_int), ("tune", ctypes.c_int), ("fp64_contraction", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class Sizes(ctypes.Structure):
     _fields_ = [("lmax", ctypes.c_int), ("mmax", ctypes.c_int), ("nrings", ctypes.c_int), ("M", ctypes.c_int),
                 ("n1", ctypes.c_int), ("n2", ctypes.c_int), ("w", ctypes.c_int), ("beta", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("precision", ctypes.c_int), ("nitems", ctypes.c_int),
-                ("nitems_total", ctypes.c_int), ("npts", ctypes.c_int64), ("bytes_device", ctypes.c_int64)]
+                ("nitems_total", ctypes.c_int), ("npts", ctypes.c_int64), ("bytes_device", ctypes.c_int64),
+                ("leg_triples", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,11 +105,12 @@ def _check(code: int, where: str):
         raise NushtError(code, where, load().nusht_last_error().decode())
 
 
-def _opts(sigma=0.0, kernel_width=0, profile=False) -> Opts:
+def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False) -> Opts:
     o = Opts()
     o.sigma = float(sigma)
     o.kernel_width = int(kernel_width)
     o.profile = 1 if profile else 0
+    o.fp64_contraction = 1 if fp64_contraction else 0
     return o
 
 
@@ -168,7 +171,8 @@ class Plan:
     """
 
     def __init__(self, lmax: int, pts, eps: float = 1e-10, precision="fp64", mmax: int | None = None,
-                 sigma: float = 0.0, kernel_width: int = 0, profile: bool = False, stream=None):
+                 sigma: float = 0.0, kernel_width: int = 0, profile: bool = False, fp64_contraction: bool = False,
+                 stream=None):
         import torch
 
         self.lib = load()
@@ -182,7 +186,7 @@ class Plan:
         self.npts = int(pts.shape[0])
         self.device = pts.device
         h = ctypes.c_void_p()
-        o = _opts(sigma, kernel_width, profile)
+        o = _opts(sigma, kernel_width, profile, fp64_contraction)
         _check(self.lib.nusht_plan(ctypes.byref(h), self.lmax, self.mmax, self.npts,
                                    ctypes.c_void_p(pts.data_ptr() if self.npts else 0), self.eps, self.precision,
                                    ctypes.byref(o), _stream_ptr(stream)), "nusht_plan")

@@ -495,6 +495,290 @@ __global__ void poles_synth_k(const Tin* __restrict__ alm, const double* __restr
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 mode with the contraction on the FP32 pipe.  The recurrence is the
+// FP64 one above; only the sums  sum_l atilde_l q_l  (synthesis) and
+// sum_rings q_l S (adjoint) are carried as unevaluated float pairs
+// hi + lo ("double-float": ~48-bit significand):
+//   * q (double) is split into qh + ql with integer bit operations;
+//   * each product is formed exactly (p = ah*qh, its error by an FMA) plus
+//     the cross terms ah*ql + al*qh;
+//   * sums use the two-sum error-free transformation.
+// Relative error per operation ~2^-48; the FP64 pipe then carries only the
+// two recurrence operations per step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_q(double q, float& qh, float& ql) {
+  const int hi = __double2hiint(q);
+  const unsigned lo = (unsigned)__double2loint(q);
+  const int eb = (hi >> 20) & 0x7ff;  // biased exponent
+  const unsigned sign = (unsigned)hi & 0x80000000u;
+  if (eb < 1023 - 126) {  // |q| < 2^-126 (or zero): negligible, flushed
+    qh = 0.0f;
+    ql = 0.0f;
+    return;
+  }
+  // leading 24 significant bits, exactly representable as a float
+  const unsigned mh = ((unsigned)(hi & 0xfffff) << 3) | (lo >> 29);
+  qh = __uint_as_float(sign | ((unsigned)(eb - 1023 + 127) << 23) | mh);
+  // remaining 29 bits r: value r * 2^(e - 52), rounded to 24 bits
+  const float r = __uint2float_rn(lo & 0x1fffffffu);
+  const int ef = eb - 1023 - 52 + 127;
+  const float sc = ef >= 1 ? __uint_as_float((unsigned)ef << 23) : 0.0f;
+  ql = __uint_as_float(__float_as_uint(__fmul_rn(r, sc)) | sign);
+}
+
+// (sh + sl) += (ah + al) * (qh + ql)
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float qh, float ql) {
+  const float p = __fmul_rn(ah, qh);
+  const float e = __fmaf_rn(ah, qh, -p);
+  const float t = __fmaf_rn(ah, ql, __fmaf_rn(al, qh, e));
+  const float s = __fadd_rn(sh, p);
+  const float bp = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  sl = __fadd_rn(sl, __fadd_rn(err, t));
+  sh = s;
+}
+
+// (ah + al) += (bh + bl)
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  const float s = __fadd_rn(ah, bh);
+  const float bp = __fsub_rn(s, ah);
+  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bp)), __fsub_rn(bh, bp));
+  al = __fadd_rn(__fadd_rn(al, bl), err);
+  ah = s;
+}
+
+__device__ __forceinline__ double df_value(float h, float l) { return (double)h + (double)l; }
+
+// float pair of a double: h = rn(v), l = rn(v - h)
+__device__ __forceinline__ void df_of(double v, float& h, float& l) {
+  h = __double2float_rn(v);
+  l = __double2float_rn(v - (double)h);
+}
+
+// atilde as double-float complex: (hi_re, lo_re, hi_im, lo_im)
+__global__ void scale_alm_df_k(const double* __restrict__ alm, const double* __restrict__ ahat, int64_t nalm, int lmax,
+                               float4* __restrict__ at) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nalm) return;
+  double re = alm[2 * i], im = alm[2 * i + 1];
+  if (i <= lmax) im = 0.0;
+  const double ah = ahat[i];
+  float4 r;
+  df_of(re * ah, r.x, r.y);
+  df_of(im * ah, r.z, r.w);
+  at[i] = r;
+}
+
+__device__ __forceinline__ void df_acc_step(float4& acc, const float4 av, double q) {
+  float qh, ql;
+  split_q(q, qh, ql);
+  df_mac(acc.x, acc.y, av.x, av.y, qh, ql);
+  df_mac(acc.z, acc.w, av.z, av.w, qh, ql);
+}
+
+__global__ void __launch_bounds__(128) legendre_synth_df_k(LegArgs a, const float4* __restrict__ at,
+                                                           double2* __restrict__ G, int nitems) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  int m, blk;
+  item_of(a, it, m, blk);
+  const int L = a.lmax;
+  const int mb = mbase_of(L, m);
+  Chain ch[LEG_K];
+  float4 accE[LEG_K], accO[LEG_K];
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) {
+    chain_init(ch[k], a, m, 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane);
+    accE[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    accO[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  {
+    const float4 av = at[mb + m];
+#pragma unroll
+    for (int k = 0; k < LEG_K; ++k)
+      if (ch[k].E == 0) df_acc_step(accE[k], av, ch[k].q1);
+  }
+  int l = m + 1;
+  for (; l + 1 <= L; l += 2) {
+    {
+      const double c = __ldg(a.c + mb + l);
+      const bool rs = __ldg(a.dshift + mb + l) != 0;
+      const float4 av = at[mb + l];
+#pragma unroll
+      for (int k = 0; k < LEG_K; ++k) {
+        chain_step(ch[k], c, rs);
+        if (ch[k].E == 0) df_acc_step(accO[k], av, ch[k].q1);
+      }
+    }
+    {
+      const double c = __ldg(a.c + mb + l + 1);
+      const bool rs = __ldg(a.dshift + mb + l + 1) != 0;
+      const float4 av = at[mb + l + 1];
+#pragma unroll
+      for (int k = 0; k < LEG_K; ++k) {
+        chain_step(ch[k], c, rs);
+        if (ch[k].E == 0) df_acc_step(accE[k], av, ch[k].q1);
+      }
+    }
+  }
+  if (l <= L) {
+    const double c = __ldg(a.c + mb + l);
+    const bool rs = __ldg(a.dshift + mb + l) != 0;
+    const float4 av = at[mb + l];
+#pragma unroll
+    for (int k = 0; k < LEG_K; ++k) {
+      chain_step(ch[k], c, rs);
+      if (ch[k].E == 0) df_acc_step(accO[k], av, ch[k].q1);
+    }
+  }
+  const int M = a.M;
+  const double sg = (m & 1) ? -1.0 : 1.0;
+  double2* row = G + (size_t)m * M;
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) {
+    if (!ch[k].valid) continue;
+    const int jn = 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane;
+    const int js = M / 2 - jn;
+    const double er = df_value(accE[k].x, accE[k].y), ei = df_value(accE[k].z, accE[k].w);
+    const double orr = df_value(accO[k].x, accO[k].y), oi = df_value(accO[k].z, accO[k].w);
+    const double2 fn = make_double2(er + orr, ei + oi);
+    const double2 fs = make_double2(er - orr, ei - oi);
+    row[jn] = fn;
+    row[M - jn] = make_double2(sg * fn.x, sg * fn.y);
+    if (js != jn) {
+      row[js] = fs;
+      row[M - js] = make_double2(sg * fs.x, sg * fs.y);
+    }
+  }
+}
+
+__device__ __forceinline__ float4 shfl4(float4 v, int mask) {
+  float4 r;
+  r.x = __shfl_xor_sync(FULL, v.x, mask);
+  r.y = __shfl_xor_sync(FULL, v.y, mask);
+  r.z = __shfl_xor_sync(FULL, v.z, mask);
+  r.w = __shfl_xor_sync(FULL, v.w, mask);
+  return r;
+}
+
+__device__ __forceinline__ void df4_add(float4& a4, const float4 b4) {
+  df_add(a4.x, a4.y, b4.x, b4.y);
+  df_add(a4.z, a4.w, b4.z, b4.w);
+}
+
+__global__ void __launch_bounds__(128) legendre_adj_df_k(LegArgs a, const double2* __restrict__ Gt,
+                                                         float4* __restrict__ partial, int nitems, int64_t nalm) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  int m, blk;
+  item_of(a, it, m, blk);
+  const int L = a.lmax;
+  const int M = a.M;
+  const int mb = mbase_of(L, m);
+  const double sg = (m & 1) ? -1.0 : 1.0;
+  const double2* row = Gt + (size_t)m * M;
+  Chain ch[LEG_K];
+  float4 SE[LEG_K], SO[LEG_K];  // double-float (hi_re, lo_re, hi_im, lo_im)
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) {
+    const int jn = 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane;
+    chain_init(ch[k], a, m, jn);
+    double2 fn = make_double2(0.0, 0.0), fs = make_double2(0.0, 0.0);
+    if (ch[k].valid) {
+      const int js = M / 2 - jn;
+      const double2 g0 = row[jn], g1 = row[M - jn];
+      fn = make_double2(g0.x + sg * g1.x, g0.y + sg * g1.y);
+      if (js != jn) {
+        const double2 h0 = row[js], h1 = row[M - js];
+        fs = make_double2(h0.x + sg * h1.x, h0.y + sg * h1.y);
+      }
+    }
+    df_of(fn.x + fs.x, SE[k].x, SE[k].y);
+    df_of(fn.y + fs.y, SE[k].z, SE[k].w);
+    df_of(fn.x - fs.x, SO[k].x, SO[k].y);
+    df_of(fn.y - fs.y, SO[k].z, SO[k].w);
+  }
+  float4* out = partial + (size_t)blk * nalm + mb;
+  for (int base = m; base <= L; base += 8) {
+    float4 v[8];
+#pragma unroll
+    for (int st = 0; st < 8; ++st) {
+      v[st] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int l = base + st;
+      if (l <= L) {
+        if (l > m) {
+          const double c = __ldg(a.c + mb + l);
+          const bool rs = __ldg(a.dshift + mb + l) != 0;
+#pragma unroll
+          for (int k = 0; k < LEG_K; ++k) chain_step(ch[k], c, rs);
+        }
+#pragma unroll
+        for (int k = 0; k < LEG_K; ++k) {
+          if (ch[k].E == 0) {
+            float qh, ql;
+            split_q(ch[k].q1, qh, ql);
+            const float4 S = (st & 1) ? SO[k] : SE[k];
+            df_mac(v[st].x, v[st].y, S.x, S.y, qh, ql);
+            df_mac(v[st].z, v[st].w, S.z, S.w, qh, ql);
+          }
+        }
+      }
+    }
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    float4 w4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 send = u16 ? v[i] : v[i + 4];
+      w4[i] = u16 ? v[i + 4] : v[i];
+      df4_add(w4[i], shfl4(send, 16));
+    }
+    float4 w2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float4 send = u8 ? w4[i] : w4[i + 2];
+      w2[i] = u8 ? w4[i + 2] : w4[i];
+      df4_add(w2[i], shfl4(send, 8));
+    }
+    float4 z;
+    {
+      const float4 send = u4 ? w2[0] : w2[1];
+      z = u4 ? w2[1] : w2[0];
+      df4_add(z, shfl4(send, 4));
+    }
+    df4_add(z, shfl4(z, 2));
+    df4_add(z, shfl4(z, 1));
+    const int l = base + ((lane >> 2) & 7);
+    if ((lane & 3) == 0 && l <= L) out[l] = z;  // float pairs; adj_reduce_df_k converts
+  }
+}
+
+// c_lm = Ahat sum_blocks (hi + lo) in double, plus the poles (m = 0)
+__global__ void adj_reduce_df_k(const float4* __restrict__ partial, int bpm, int64_t nalm,
+                                const double* __restrict__ ahat, const double* __restrict__ pole_norm,
+                                const double2* __restrict__ Gt, int lmax, int M, double2* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nalm) return;
+  double sx = 0.0, sy = 0.0;
+  for (int b = 0; b < bpm; ++b) {
+    const float4 v = partial[(size_t)b * nalm + i];
+    sx += (double)v.x + (double)v.y;
+    sy += (double)v.z + (double)v.w;
+  }
+  const double ah = ahat[i];
+  sx *= ah;
+  sy *= ah;
+  if (i <= lmax) {
+    const int l = (int)i;
+    const double np = Gt[0].x, sp = Gt[M / 2].x;
+    sx += pole_norm[l] * (np + ((l & 1) ? -sp : sp));
+    sy = 0.0;
+  }
+  out[i] = make_double2(sx, sy);
+}
+
 // Plan-time probe: does any ring of the item leave the scaled phase by lmax?
 __global__ void __launch_bounds__(128) legendre_probe_k(LegArgs a, int ntotal, int* __restrict__ flags) {
   const int lane = threadIdx.x & 31;
@@ -668,6 +952,15 @@ int legendre_build_tables(nusht_plan_t p, cudaStream_t s) {
   for (int i = 0; i < ntotal; ++i)
     if (flags[i]) items.push_back(((i / t.blocks_per_m) << 16) | (i % t.blocks_per_m));
   t.nitems = (int)items.size();
+  // triples (ring pair, l, m) processed per call: the roofline's unit of work
+  int64_t tri = 0;
+  for (int v : items) {
+    const int m = v >> 16, blk = v & 0xffff;
+    const int j0 = 1 + blk * LEG_PAIRS_PER_WARP;
+    const int nvalid = std::max(0, std::min(LEG_PAIRS_PER_WARP, npairs - j0 + 1));
+    tri += (int64_t)nvalid * (L - m + 1);
+  }
+  t.triples = tri;
   NUSHT_TRY(dev_alloc((void**)&t.items, std::max<size_t>(1, items.size()) * 4, &p->bytes));
   if (!items.empty())
     NUSHT_CUDA(cudaMemcpyAsync(t.items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s));
@@ -681,7 +974,13 @@ int legendre_synth(nusht_plan_t p, const void* d_alm, cudaStream_t s) {
   const int nb = (int)((nalm + tb - 1) / tb);
   LegArgs a = make_args(p);
   const int nitems = p->leg.nitems;
-  if (p->precision == NUSHT_FP64) {
+  if (p->precision == NUSHT_FP64 && !p->opts.fp64_contraction) {
+    scale_alm_df_k<<<nb, tb, 0, s>>>((const double*)d_alm, p->leg.ahat, nalm, p->lmax, (float4*)p->atilde);
+    if (nitems > 0)
+      legendre_synth_df_k<<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float4*)p->atilde, (double2*)p->G, nitems);
+    poles_synth_k<double, double><<<1, 256, 0, s>>>((const double*)d_alm, p->leg.pole_norm, p->lmax, p->sz.M,
+                                                    (double2*)p->G);
+  } else if (p->precision == NUSHT_FP64) {
     scale_alm_k<double, double><<<nb, tb, 0, s>>>((const double*)d_alm, p->leg.ahat, nalm, p->lmax,
                                                   (double2*)p->atilde);
     if (nitems > 0)
@@ -705,7 +1004,13 @@ int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
   const int nitems = p->leg.nitems;
   const int tb = 256;
   const int nb = (int)((nalm + tb - 1) / tb);
-  if (p->precision == NUSHT_FP64) {
+  if (p->precision == NUSHT_FP64 && !p->opts.fp64_contraction) {
+    if (nitems > 0)
+      legendre_adj_df_k<<<(nitems + 3) / 4, 128, 0, s>>>(a, (const double2*)p->Ghat, (float4*)p->partial, nitems,
+                                                         nalm);
+    adj_reduce_df_k<<<nb, tb, 0, s>>>((const float4*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
+                                      p->leg.pole_norm, (const double2*)p->Ghat, p->lmax, p->sz.M, (double2*)d_alm);
+  } else if (p->precision == NUSHT_FP64) {
     if (nitems > 0)
       legendre_adj_k<double><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const double2*)p->Ghat, (double2*)p->partial, nitems,
                                                               nalm);

@@ -71,6 +71,7 @@ struct LegTables {
   int* items = nullptr;       // work list: (m << 16) | block
   int nitems = 0;
   int nitems_total = 0;
+  int64_t triples = 0;        // (ring pair, l, m) triples of the kept items
   int blocks_per_m = 0;       // ring blocks per order
   int npairs = 0;             // M/4
 };

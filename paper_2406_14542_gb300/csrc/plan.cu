@@ -292,6 +292,7 @@ static int plan_body(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStre
   NUSHT_CUDA(cudaStreamSynchronize(s));
   p->sz.nitems = p->leg.nitems;
   p->sz.nitems_total = p->leg.nitems_total;
+  p->sz.leg_triples = p->leg.triples;
   p->sz.npts = p->pts.npts;
   return NUSHT_OK;
 }
