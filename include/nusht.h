@@ -203,6 +203,55 @@ NUSHT_API int nusht_synth_grad(nusht_plan_t p, const void* d_alm, void* d_dtheta
 NUSHT_API int nusht_adjoint_direct_noalloc(int lmax, int mmax, int64_t npts, const double* d_pts, const double* d_map,
                                            void* d_alm, nusht_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batched transforms: many independent transforms of uneven lmax and point
+ * count in one plan (NUSHT_MIXED only; each lmax <= 4095).  Members are
+ * grouped into buckets of up to 64 that share one Clenshaw-Curtis ring set,
+ * so one FP64 recurrence per (ring pair, l, m) serves every member of a
+ * bucket (Sec. 3: the recurrence is the O(lmax^3) part); the contraction
+ * over l (synthesis) or rings (adjoint) runs for all members at once in
+ * FP32.  The grouping minimises a cost model of recurrence and contraction
+ * work.  Each direction's whole stage sequence is captured once into a CUDA
+ * graph and replayed; it is re-captured when the buffer pointers change.
+ * ------------------------------------------------------------------------ */
+typedef struct nusht_batch_s* nusht_batch_t;
+
+/*
+ * nusht_plan_many -- plan nbatch transforms.
+ *   lmax[b]   band limit of member b (mmax = lmax), 0 <= lmax[b] <= 4095
+ *   npts[b]   its number of points; d_pts[b] its device (theta, phi) pairs
+ *   eps       accuracy, >= 1e-6 (mixed precision); precision must be NUSHT_MIXED
+ * The host arrays lmax, npts, d_pts are read during the call only.
+ * Synchronises `stream`.
+ */
+NUSHT_API int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64_t* npts,
+                              const double* const* d_pts, double eps, int precision, const nusht_opts* opts,
+                              nusht_stream_t stream);
+
+/*
+ * nusht_synth_many / nusht_adjoint_many -- all members at once.
+ *   d_alm[b]  device complex64 coefficients of member b (its own m-major layout)
+ *   d_map[b]  device float[npts[b]] values in member b's point order
+ * The pointer arrays are host arrays read during the call.  The first call
+ * with a given set of buffers captures a CUDA graph (this synchronises the
+ * stream and writes the plan's device pointer tables); later calls with the
+ * same buffers only launch it on `stream`.
+ */
+NUSHT_API int nusht_synth_many(nusht_batch_t p, const void* const* d_alm, void* const* d_map, nusht_stream_t stream);
+NUSHT_API int nusht_adjoint_many(nusht_batch_t p, const void* const* d_map, void* const* d_alm,
+                                 nusht_stream_t stream);
+
+/* nusht_destroy_many -- free a batch plan (NULL-safe). */
+NUSHT_API int nusht_destroy_many(nusht_batch_t p);
+
+/*
+ * nusht_batch_info -- grouping chosen by the planner: number of buckets,
+ * bucket index of each member (bucket_of[nbatch]), band limit of each
+ * bucket (bucket_lmax[nbuckets]) and device bytes; any output may be NULL.
+ */
+NUSHT_API int nusht_batch_info(nusht_batch_t p, int* nbuckets, int* bucket_of, int* bucket_lmax,
+                               int64_t* bytes_device);
+
 /* nusht_destroy -- free the plan and its device memory (NULL-safe). */
 NUSHT_API int nusht_destroy(nusht_plan_t p);
 

@@ -25,7 +25,8 @@ FP64, MIXED = 0, 1
 
 EXPORTS = ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_synth_grad", "nusht_destroy",
            "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_good_size", "nusht_stage_times",
-           "nusht_strerror", "nusht_last_error", "nusht_version", "nusht_adjoint_direct_noalloc")
+           "nusht_strerror", "nusht_last_error", "nusht_version", "nusht_adjoint_direct_noalloc",
+           "nusht_plan_many", "nusht_synth_many", "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info")
 
 
 class NushtError(RuntimeError):
@@ -81,13 +82,22 @@ def load(path: str | None = None):
         lib.nusht_good_size.restype = i64
         lib.nusht_stage_times.argtypes = [vp, dp]
         lib.nusht_adjoint_direct_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, i64, vp, vp, vp, vp]
+        lib.nusht_plan_many.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(Opts), vp]
+        lib.nusht_synth_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        lib.nusht_adjoint_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        lib.nusht_destroy_many.argtypes = [vp]
+        lib.nusht_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64)]
         lib.nusht_strerror.argtypes = [ctypes.c_int]
         lib.nusht_strerror.restype = ctypes.c_char_p
         lib.nusht_last_error.restype = ctypes.c_char_p
         lib.nusht_version.restype = ctypes.c_char_p
         for name in ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_synth_grad",
                      "nusht_destroy", "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_stage_times",
-                     "nusht_adjoint_direct_noalloc"):
+                     "nusht_adjoint_direct_noalloc", "nusht_plan_many", "nusht_synth_many",
+                     "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -299,6 +309,79 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+class BatchPlan:
+    """Many transforms of uneven lmax and point count in one plan (mixed
+    precision): complex64 a_lm, float32 maps.  ``pts_list[b]`` is a CUDA
+    float64 (N_b, 2) tensor; each lmax <= 4095."""
+
+    def __init__(self, lmaxs, pts_list, eps: float = 1e-5, sigma: float = 0.0, stream=None):
+        import torch
+
+        self.lib = load()
+        self.lmaxs = [int(l) for l in lmaxs]
+        n = len(self.lmaxs)
+        if len(pts_list) != n:
+            raise ValueError("one point array per transform")
+        self.pts = [Plan._check_pts(p) for p in pts_list]
+        self.npts = [int(p.shape[0]) for p in self.pts]
+        self.device = self.pts[0].device
+        larr = (ctypes.c_int * n)(*self.lmaxs)
+        narr = (ctypes.c_int64 * n)(*self.npts)
+        parr = (ctypes.c_void_p * n)(*[p.data_ptr() if p.numel() else 0 for p in self.pts])
+        o = _opts(sigma)
+        h = ctypes.c_void_p()
+        _check(self.lib.nusht_plan_many(ctypes.byref(h), n, larr, narr, parr, float(eps), MIXED, ctypes.byref(o),
+                                        _stream_ptr(stream)), "nusht_plan_many")
+        self._h = h
+        self.n = n
+
+    def info(self) -> dict:
+        nb = ctypes.c_int()
+        of = (ctypes.c_int * self.n)()
+        bl = (ctypes.c_int * self.n)()
+        by = ctypes.c_int64()
+        _check(self.lib.nusht_batch_info(self._h, ctypes.byref(nb), of, bl, ctypes.byref(by)), "nusht_batch_info")
+        return {"nbuckets": nb.value, "bucket_of": list(of), "bucket_lmax": list(bl)[: nb.value],
+                "bytes_device": by.value}
+
+    def synth(self, alms, outs=None, stream=None):
+        import torch
+
+        if outs is None:
+            outs = [torch.empty(n, dtype=torch.float32, device=self.device) for n in self.npts]
+        for a, l in zip(alms, self.lmaxs):
+            if not (a.is_cuda and a.dtype == torch.complex64 and a.shape == (nalm(l),) and a.is_contiguous()):
+                raise ValueError("alm must be contiguous CUDA complex64 of length nalm(lmax)")
+        ia = (ctypes.c_void_p * self.n)(*[a.data_ptr() for a in alms])
+        oa = (ctypes.c_void_p * self.n)(*[o.data_ptr() for o in outs])
+        _check(self.lib.nusht_synth_many(self._h, ia, oa, _stream_ptr(stream)), "nusht_synth_many")
+        return outs
+
+    def adjoint(self, maps, outs=None, stream=None):
+        import torch
+
+        if outs is None:
+            outs = [torch.empty(nalm(l), dtype=torch.complex64, device=self.device) for l in self.lmaxs]
+        for m, n in zip(maps, self.npts):
+            if not (m.is_cuda and m.dtype == torch.float32 and m.shape == (n,) and m.is_contiguous()):
+                raise ValueError("maps must be contiguous CUDA float32 of length npts")
+        ia = (ctypes.c_void_p * self.n)(*[m.data_ptr() for m in maps])
+        oa = (ctypes.c_void_p * self.n)(*[o.data_ptr() for o in outs])
+        _check(self.lib.nusht_adjoint_many(self._h, ia, oa, _stream_ptr(stream)), "nusht_adjoint_many")
+        return outs
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self.lib.nusht_destroy_many(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _autograd():

@@ -1,0 +1,767 @@
+// batch.cu -- many transforms of uneven lmax and point counts in one plan
+// (mixed precision: FP64 recurrence, FP32 contraction / FFT / NUFFT).
+//
+// Members are grouped into buckets of up to 64 transforms that share one
+// Clenshaw-Curtis ring set (the one of the bucket's largest lmax: more rings
+// than a member needs keep its DFS coefficients exact, Sec. 2.2).  Within a
+// bucket the FP64 recurrence is run once per (ring pair, l, m) and contracted
+// with every member's coefficients at once, i.e. per order m a dense product
+//   synthesis: F[ring][member] = sum_l P[ring][l] A[l][member]
+//   adjoint:   C[l][member]    = sum_rings P[ring][l] S[ring][member]
+// tiled through shared memory (CUDA-core FP32 FMA, FP32 accumulation).
+// Each member keeps its own NUFFT state (points, fine grid, 2D FFTs) and its
+// theta spectrum lives in a slice of the bucket's buffer, so the theta FFT is
+// one batched cuFFT call per bucket.  The grouping minimises a cost model of
+// the recurrence (per triple of the bucket's largest lmax) plus the
+// contraction (per triple and member column).
+//
+// The whole stage sequence of one direction is captured once into a CUDA
+// graph (re-captured when the caller's buffers change) and replayed.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "nusht_internal.cuh"
+#include "recurrence.cuh"
+
+struct nusht_batch_s;
+
+namespace nusht {
+namespace {
+
+using namespace rec;
+
+constexpr int BK_MAXB = 64;          // members per bucket
+constexpr int BK_COLS = 2 * BK_MAXB; // (re, im) columns of the contraction
+constexpr int BS_PAIRS = 64;         // synthesis: ring pairs per block
+constexpr int BS_LC = 16;            // synthesis: degrees per chunk
+constexpr int BA_TILE = 256;         // adjoint: ring pairs per recurrence tile (one per thread)
+constexpr int BA_LC = 32;            // adjoint: degrees per chunk
+constexpr int BA_SUB = 32;           // adjoint: ring pairs per staged S tile
+
+struct BucketArgs {
+  int lmax, M, npairs, B;
+  const double* c;
+  const int8_t* dshift;
+  const double* cm;
+  const double* ring_x;
+  const double* ring_s;
+  const int* memberL;
+};
+
+__device__ __forceinline__ int idx_lm(int L, int l, int m) { return m * (2 * L + 1 - m) / 2 + l; }
+
+// atb[(l,m)][slot] = a_slot(l, m) * Ahat(l, m) (zero where the member has no such (l, m))
+__global__ void bucket_scale_k(int L, int B, const int* __restrict__ memberL, const float2* const* __restrict__ alm,
+                               const double* __restrict__ ahat, float2* __restrict__ atb) {
+  const int m = blockIdx.y;
+  const int slot = threadIdx.x & (BK_MAXB - 1);
+  const int l = m + blockIdx.x * 4 + (threadIdx.x >> 6);
+  if (l > L) return;
+  const int i = idx_lm(L, l, m);
+  float2 v = make_float2(0.f, 0.f);
+  if (slot < B) {
+    const int Lb = memberL[slot];
+    if (l <= Lb && m <= Lb) {
+      const float2 a = alm[slot][idx_lm(Lb, l, m)];
+      const double ah = ahat[i];
+      v.x = (float)((double)a.x * ah);
+      v.y = m == 0 ? 0.f : (float)((double)a.y * ah);
+    }
+  }
+  atb[(size_t)i * BK_MAXB + slot] = v;
+}
+
+// synthesis: block = (order m, 64 ring pairs); 64 owner threads run the FP64
+// recurrence chunk by chunk into shared memory, all 256 threads contract
+// (64 pairs x 16 degrees) x (16 degrees x 128 columns) with even/odd degree
+// parities kept apart (north = E + O, south = E - O).
+__global__ void __launch_bounds__(256) bucket_synth_k(BucketArgs a, const int* __restrict__ items, int nitems,
+                                                      const float2* __restrict__ atb, float2* __restrict__ G) {
+  __shared__ __align__(16) float Ps[BS_LC][BS_PAIRS];
+  __shared__ __align__(16) float As[BS_LC][BK_COLS];
+  const int it = blockIdx.x;
+  if (it >= nitems) return;
+  const int v = items[it];
+  const int m = v >> 16, tile = v & 0xffff;
+  const int L = a.lmax;
+  const int mb = idx_lm(L, 0, m);  // packed base of order m
+  const int t = threadIdx.x;
+  Chain ch;
+  ch.valid = false;
+  ch.E = 0;
+  ch.q1 = ch.q2 = ch.x = 0.0;
+  if (t < BS_PAIRS) chain_init(ch, a, m, 1 + tile * BS_PAIRS + t);
+  const int pg = t >> 4, cg = t & 15;
+  float accE[4][8], accO[4][8];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) accE[r][c] = accO[r][c] = 0.f;
+  for (int l0 = m; l0 <= L; l0 += BS_LC) {
+    if (t < BS_PAIRS) {
+#pragma unroll
+      for (int j = 0; j < BS_LC; ++j) {
+        const int l = l0 + j;
+        float q = 0.f;
+        if (l <= L) {
+          if (l > m) chain_step(ch, __ldg(a.c + mb + l), __ldg(a.dshift + mb + l) != 0);
+          if (ch.valid && ch.E == 0) q = to_f32(ch.q1);
+        }
+        Ps[j][t] = q;
+      }
+    }
+    for (int e = t; e < BS_LC * BK_COLS / 4; e += 256) {
+      const int r = e >> 5, c4 = e & 31;
+      const int l = l0 + r;
+      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (l <= L) val = reinterpret_cast<const float4*>(atb + (size_t)(mb + l) * BK_MAXB)[c4];
+      reinterpret_cast<float4*>(&As[r][0])[c4] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < BS_LC; ++j) {
+      const float4 p = *reinterpret_cast<const float4*>(&Ps[j][pg * 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[j][cg * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[j][cg * 8 + 4]);
+      const float pr[4] = {p.x, p.y, p.z, p.w};
+      const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (j & 1)
+            accO[r][c] = fmaf(pr[r], ar[c], accO[r][c]);
+          else
+            accE[r][c] = fmaf(pr[r], ar[c], accE[r][c]);
+        }
+    }
+    __syncthreads();
+  }
+  const int M = a.M;
+  const float sg = (m & 1) ? -1.f : 1.f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int jn = 1 + tile * BS_PAIRS + pg * 4 + r;
+    if (jn > a.npairs) continue;
+    const int js = M / 2 - jn;
+#pragma unroll
+    for (int ss = 0; ss < 4; ++ss) {
+      const int slot = cg * 4 + ss;
+      if (slot >= a.B || m > a.memberL[slot]) continue;
+      const float2 fn = make_float2(accE[r][2 * ss] + accO[r][2 * ss], accE[r][2 * ss + 1] + accO[r][2 * ss + 1]);
+      const float2 fs = make_float2(accE[r][2 * ss] - accO[r][2 * ss], accE[r][2 * ss + 1] - accO[r][2 * ss + 1]);
+      float2* row = G + ((size_t)slot * (L + 1) + m) * M;
+      row[jn] = fn;
+      row[M - jn] = make_float2(sg * fn.x, sg * fn.y);
+      if (js != jn) {
+        row[js] = fs;
+        row[M - js] = make_float2(sg * fs.x, sg * fs.y);
+      }
+    }
+  }
+}
+
+// F_0 at the poles for every member (m > 0 pole entries stay 0)
+__global__ void bucket_poles_k(int L, int M, const int* __restrict__ memberL, const float2* const* __restrict__ alm,
+                               const double* __restrict__ pole_norm, float2* __restrict__ G) {
+  __shared__ double sn[256], ss[256];
+  const int slot = blockIdx.x;
+  const int Lb = memberL[slot];
+  double n = 0.0, s = 0.0;
+  for (int l = threadIdx.x; l <= Lb; l += blockDim.x) {
+    const double v = (double)alm[slot][l].x * pole_norm[l];
+    n += v;
+    s += (l & 1) ? -v : v;
+  }
+  sn[threadIdx.x] = n;
+  ss[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sn[threadIdx.x] += sn[threadIdx.x + h];
+      ss[threadIdx.x] += ss[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    float2* row = G + (size_t)slot * (L + 1) * M;
+    row[0] = make_float2((float)sn[0], 0.f);
+    row[M / 2] = make_float2((float)ss[0], 0.f);
+  }
+}
+
+// adjoint, first step: D^dagger fold into S[m][pair][E|O][slot (re, im)]
+__global__ void bucket_fold_k(int L, int M, int npairs, int B, const int* __restrict__ memberL,
+                              const float2* __restrict__ Gt, float* __restrict__ S) {
+  const int p = blockIdx.x, m = blockIdx.y, slot = threadIdx.x;  // 64 threads
+  const int jn = p + 1, js = M / 2 - jn;
+  float2 se = make_float2(0.f, 0.f), so = make_float2(0.f, 0.f);
+  if (slot < B && m <= memberL[slot]) {
+    const float sg = (m & 1) ? -1.f : 1.f;
+    const float2* row = Gt + ((size_t)slot * (L + 1) + m) * M;
+    const float2 g0 = row[jn], g1 = row[M - jn];
+    const float2 fn = make_float2(g0.x + sg * g1.x, g0.y + sg * g1.y);
+    float2 fs = make_float2(0.f, 0.f);
+    if (js != jn) {
+      const float2 h0 = row[js], h1 = row[M - js];
+      fs = make_float2(h0.x + sg * h1.x, h0.y + sg * h1.y);
+    }
+    se = make_float2(fn.x + fs.x, fn.y + fs.y);
+    so = make_float2(fn.x - fs.x, fn.y - fs.y);
+  }
+  float2* out = reinterpret_cast<float2*>(S + ((size_t)m * npairs + p) * 2 * BK_COLS);
+  out[slot] = se;
+  out[BK_MAXB + slot] = so;
+}
+
+// adjoint: block = order m with all its ring pairs; each thread owns NT
+// chains (pairs t, t+256, ...) kept in registers across degree chunks; per
+// chunk of 32 degrees the recurrence tile P[32][256] goes to shared memory
+// and C[32 degrees][128 columns] += P S is accumulated over the pairs with S
+// staged 32 pairs at a time.  The block owns its outputs: no atomics.
+template <int NT>
+__global__ void __launch_bounds__(256) bucket_adj_k(BucketArgs a, const int* __restrict__ mlist, int nm,
+                                                    const float* __restrict__ S, float* __restrict__ cacc) {
+  extern __shared__ __align__(16) float smem[];
+  float* Ps = smem;                    // [BA_LC][BA_TILE]
+  float* Ss = smem + BA_LC * BA_TILE;  // [BA_SUB][2 * BK_COLS]
+  if ((int)blockIdx.x >= nm) return;
+  const int m = mlist[blockIdx.x];
+  const int L = a.lmax;
+  const int mb = idx_lm(L, 0, m);  // packed base of order m
+  const int t = threadIdx.x;
+  const int npairs = a.npairs;
+  Chain ch[NT];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) {
+    ch[k].valid = false;
+    ch[k].E = 0;
+    ch[k].q1 = ch[k].q2 = ch[k].x = 0.0;
+    if (k * BA_TILE < npairs) chain_init(ch[k], a, m, 1 + k * BA_TILE + t);
+  }
+  const int jj = t >> 4, cg = t & 15;  // rows 2jj (even) and 2jj+1 (odd), columns cg*8..cg*8+7
+  for (int l0 = m; l0 <= L; l0 += BA_LC) {
+    float acc0[8], acc1[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc0[c] = acc1[c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      if (k * BA_TILE >= npairs) continue;
+#pragma unroll 4
+      for (int j = 0; j < BA_LC; ++j) {
+        const int l = l0 + j;
+        float q = 0.f;
+        if (l <= L) {
+          if (l > m) chain_step(ch[k], __ldg(a.c + mb + l), __ldg(a.dshift + mb + l) != 0);
+          if (ch[k].valid && ch[k].E == 0) q = to_f32(ch[k].q1);
+        }
+        Ps[j * BA_TILE + t] = q;
+      }
+      __syncthreads();
+      for (int sub = 0; sub < BA_TILE / BA_SUB; ++sub) {
+        const int pb = k * BA_TILE + sub * BA_SUB;
+        if (pb >= npairs) break;
+        // stage S[m][pb .. pb+31][256 floats]
+        const float4* src = reinterpret_cast<const float4*>(S + ((size_t)m * npairs + pb) * 2 * BK_COLS);
+        for (int e = t; e < BA_SUB * 2 * BK_COLS / 4; e += 256) {
+          const int r = e / (2 * BK_COLS / 4);
+          float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (pb + r < npairs) val = src[e];
+          reinterpret_cast<float4*>(Ss)[e] = val;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < BA_SUB; ++r) {
+          const float pe = Ps[(2 * jj) * BA_TILE + sub * BA_SUB + r];
+          const float po = Ps[(2 * jj + 1) * BA_TILE + sub * BA_SUB + r];
+          const float* srow = Ss + r * 2 * BK_COLS;
+          const float4 e0 = *reinterpret_cast<const float4*>(srow + cg * 8);
+          const float4 e1 = *reinterpret_cast<const float4*>(srow + cg * 8 + 4);
+          const float4 o0 = *reinterpret_cast<const float4*>(srow + BK_COLS + cg * 8);
+          const float4 o1 = *reinterpret_cast<const float4*>(srow + BK_COLS + cg * 8 + 4);
+          acc0[0] = fmaf(pe, e0.x, acc0[0]);
+          acc0[1] = fmaf(pe, e0.y, acc0[1]);
+          acc0[2] = fmaf(pe, e0.z, acc0[2]);
+          acc0[3] = fmaf(pe, e0.w, acc0[3]);
+          acc0[4] = fmaf(pe, e1.x, acc0[4]);
+          acc0[5] = fmaf(pe, e1.y, acc0[5]);
+          acc0[6] = fmaf(pe, e1.z, acc0[6]);
+          acc0[7] = fmaf(pe, e1.w, acc0[7]);
+          acc1[0] = fmaf(po, o0.x, acc1[0]);
+          acc1[1] = fmaf(po, o0.y, acc1[1]);
+          acc1[2] = fmaf(po, o0.z, acc1[2]);
+          acc1[3] = fmaf(po, o0.w, acc1[3]);
+          acc1[4] = fmaf(po, o1.x, acc1[4]);
+          acc1[5] = fmaf(po, o1.y, acc1[5]);
+          acc1[6] = fmaf(po, o1.z, acc1[6]);
+          acc1[7] = fmaf(po, o1.w, acc1[7]);
+        }
+        __syncthreads();
+      }
+    }
+    const int le = l0 + 2 * jj, lo = le + 1;
+    if (le <= L) {
+      float4* dst = reinterpret_cast<float4*>(cacc + (size_t)(mb + le) * BK_COLS + cg * 8);
+      dst[0] = make_float4(acc0[0], acc0[1], acc0[2], acc0[3]);
+      dst[1] = make_float4(acc0[4], acc0[5], acc0[6], acc0[7]);
+    }
+    if (lo <= L) {
+      float4* dst = reinterpret_cast<float4*>(cacc + (size_t)(mb + lo) * BK_COLS + cg * 8);
+      dst[0] = make_float4(acc1[0], acc1[1], acc1[2], acc1[3]);
+      dst[1] = make_float4(acc1[4], acc1[5], acc1[6], acc1[7]);
+    }
+  }
+}
+
+// member outputs: c_slot(l, m) = Ahat * C + poles (m = 0)
+__global__ void bucket_final_k(int L, int M, int B, const int* __restrict__ memberL, const float* __restrict__ cacc,
+                               const double* __restrict__ ahat, const double* __restrict__ pole_norm,
+                               const float2* __restrict__ Gt, float2* const* __restrict__ out) {
+  const int m = blockIdx.y;
+  const int slot = threadIdx.x & (BK_MAXB - 1);
+  const int l = m + blockIdx.x * 4 + (threadIdx.x >> 6);
+  if (l > L || slot >= B) return;
+  const int Lb = memberL[slot];
+  if (l > Lb || m > Lb) return;
+  const int i = idx_lm(L, l, m);
+  const float2 v = reinterpret_cast<const float2*>(cacc + (size_t)i * BK_COLS)[slot];
+  const double ah = ahat[i];
+  double re = (double)v.x * ah, im = (double)v.y * ah;
+  if (m == 0) {
+    const float2* row = Gt + (size_t)slot * (L + 1) * M;
+    re += pole_norm[l] * ((double)row[0].x + ((l & 1) ? -(double)row[M / 2].x : (double)row[M / 2].x));
+    im = 0.0;
+  }
+  out[slot][idx_lm(Lb, l, m)] = make_float2((float)re, (float)im);
+}
+
+struct Bucket {
+  int L = 0, M = 0, B = 0, npairs = 0, nt = 1;
+  std::vector<int> members;
+  nusht_plan_t leg = nullptr;
+  int* items = nullptr;
+  int nitems = 0;
+  int* mlist = nullptr;
+  int nm = 0;
+  int* memberL = nullptr;
+  float2* atb = nullptr;
+  float2* G = nullptr;
+  float2* Ghat = nullptr;
+  float* S = nullptr;
+  float* cacc = nullptr;
+  const float2** alm_ptrs = nullptr;  // device [BK_MAXB]
+  float2** out_ptrs = nullptr;        // device [BK_MAXB]
+  cufftHandle theta = 0;
+  bool have_theta = false;
+};
+
+int64_t tri_count(int L, int M) { return (int64_t)(M / 4) * (int64_t)(L + 1) * (L + 2) / 2; }
+
+}  // namespace
+}  // namespace nusht
+
+struct nusht_batch_s {
+  int device = 0, nbatch = 0, precision = NUSHT_MIXED;
+  double eps = 0;
+  nusht_opts opts{};
+  std::vector<int> L;
+  std::vector<int64_t> npts;
+  std::vector<nusht_plan_t> sub;
+  std::vector<nusht::Bucket> buckets;
+  std::vector<int> bucket_of, slot_of;
+  size_t bytes = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gs = nullptr, ga = nullptr;
+  std::vector<const void*> gs_in;
+  std::vector<void*> gs_out;
+  std::vector<const void*> ga_in;
+  std::vector<void*> ga_out;
+};
+
+namespace nusht {
+namespace {
+
+void bucket_free(Bucket& b) {
+  if (b.leg) plan_destroy(b.leg);
+  dev_free(b.items);
+  dev_free(b.mlist);
+  dev_free(b.memberL);
+  dev_free(b.atb);
+  dev_free(b.G);
+  dev_free(b.Ghat);
+  dev_free(b.S);
+  dev_free(b.cacc);
+  dev_free(b.alm_ptrs);
+  dev_free(b.out_ptrs);
+  if (b.have_theta) cufftDestroy(b.theta);
+  b = Bucket();
+}
+
+void batch_free(nusht_batch_t p) {
+  if (!p) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(p->device);
+  if (p->gs) cudaGraphExecDestroy(p->gs);
+  if (p->ga) cudaGraphExecDestroy(p->ga);
+  for (auto* s : p->sub)
+    if (s) plan_destroy(s);
+  for (auto& b : p->buckets) bucket_free(b);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  cudaSetDevice(cur);
+  delete p;
+}
+
+// Grouping of the members (sorted by lmax) into contiguous buckets of at most
+// 64 that minimises  sum over buckets of T(L_max) (c_rec + 128 c_col) + c_fix,
+// T = (ring pairs) x (l, m) triples of the bucket's lmax.  The constants are
+// per-triple costs of the FP64 recurrence and of the 128-column FP32
+// contraction on GB300 and a per-bucket overhead (launches, theta FFT).
+std::vector<std::vector<int>> group_members(const std::vector<int>& L, double c_rec, double c_col, double c_fix) {
+  const int n = (int)L.size();
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return L[x] < L[y]; });
+  std::vector<double> best(n + 1, 1e300);
+  std::vector<int> cut(n + 1, 0);
+  best[0] = 0.0;
+  for (int j = 1; j <= n; ++j) {
+    for (int i = std::max(0, j - BK_MAXB); i < j; ++i) {
+      nusht_sizes z;
+      const int Lb = L[order[j - 1]];
+      if (choose_sizes(Lb, Lb, 1e-5, NUSHT_MIXED, nullptr, &z) != NUSHT_OK) continue;
+      const double cost = best[i] + (double)tri_count(Lb, z.M) * (c_rec + BK_COLS * c_col) + c_fix;
+      if (cost < best[j]) {
+        best[j] = cost;
+        cut[j] = i;
+      }
+    }
+  }
+  std::vector<std::vector<int>> groups;
+  for (int j = n; j > 0; j = cut[j]) {
+    std::vector<int> g(order.begin() + cut[j], order.begin() + j);
+    groups.push_back(g);
+  }
+  std::reverse(groups.begin(), groups.end());
+  return groups;
+}
+
+int bucket_build(nusht_batch_t p, Bucket& b, cudaStream_t s) {
+  const int L = b.L;
+  nusht_sizes z;
+  NUSHT_TRY(choose_sizes(L, L, p->eps, NUSHT_MIXED, &p->opts, &z));
+  b.M = z.M;
+  b.npairs = b.M / 4;
+  b.nt = 1;
+  while (b.nt * BA_TILE < b.npairs) b.nt *= 2;
+  if (b.nt > 8) return set_error(NUSHT_EUNSUPPORTED, "batched transforms support lmax <= 4095");
+  PlanRole role;
+  role.nufft = false;
+  role.legendre = true;
+  NUSHT_TRY(plan_create(&b.leg, L, L, 0, nullptr, p->eps, NUSHT_MIXED, &p->opts, s, role));
+  // 64-pair synthesis tiles from the 128-pair work items kept by the probe
+  std::vector<int> items(b.leg->leg.nitems);
+  NUSHT_CUDA(cudaMemcpy(items.data(), b.leg->leg.items, items.size() * 4, cudaMemcpyDeviceToHost));
+  std::vector<int> tiles, ms;
+  for (int v : items) {
+    const int m = v >> 16, blk = v & 0xffff;
+    for (int h = 0; h < 2; ++h) {
+      const int tile = 2 * blk + h;
+      if (1 + tile * BS_PAIRS <= b.npairs) tiles.push_back((m << 16) | tile);
+    }
+    if (ms.empty() || ms.back() != m) ms.push_back(m);
+  }
+  b.nitems = (int)tiles.size();
+  b.nm = (int)ms.size();
+  NUSHT_TRY(dev_alloc((void**)&b.items, std::max<size_t>(1, tiles.size()) * 4, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.mlist, std::max<size_t>(1, ms.size()) * 4, &p->bytes));
+  if (!tiles.empty()) NUSHT_CUDA(cudaMemcpy(b.items, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice));
+  if (!ms.empty()) NUSHT_CUDA(cudaMemcpy(b.mlist, ms.data(), ms.size() * 4, cudaMemcpyHostToDevice));
+  std::vector<int> ml(BK_MAXB, -1);
+  for (int k = 0; k < b.B; ++k) ml[k] = p->L[b.members[k]];
+  NUSHT_TRY(dev_alloc((void**)&b.memberL, BK_MAXB * 4, &p->bytes));
+  NUSHT_CUDA(cudaMemcpy(b.memberL, ml.data(), BK_MAXB * 4, cudaMemcpyHostToDevice));
+  const int64_t nalm = b.leg->nalm;
+  const size_t gbytes = (size_t)b.B * (L + 1) * b.M * sizeof(float2);
+  NUSHT_TRY(dev_alloc((void**)&b.atb, (size_t)nalm * BK_MAXB * sizeof(float2), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.G, gbytes, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.Ghat, gbytes, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.S, (size_t)(L + 1) * b.npairs * 2 * BK_COLS * sizeof(float), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.cacc, (size_t)nalm * BK_COLS * sizeof(float), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.alm_ptrs, BK_MAXB * sizeof(void*), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.out_ptrs, BK_MAXB * sizeof(void*), &p->bytes));
+  NUSHT_CUDA(cudaMemsetAsync(b.G, 0, gbytes, s));
+  NUSHT_CUDA(cudaMemsetAsync(b.Ghat, 0, gbytes, s));
+  NUSHT_CUDA(cudaMemsetAsync(b.cacc, 0, (size_t)nalm * BK_COLS * sizeof(float), s));
+  NUSHT_CUFFT(cufftCreate(&b.theta));
+  b.have_theta = true;
+  int M = b.M;
+  size_t ws = 0;
+  NUSHT_CUFFT(cufftMakePlanMany(b.theta, 1, &M, nullptr, 1, M, nullptr, 1, M, CUFFT_C2C, b.B * (L + 1), &ws));
+  NUSHT_CUDA(cudaStreamSynchronize(s));
+  return NUSHT_OK;
+}
+
+BucketArgs bucket_args(const Bucket& b) {
+  BucketArgs a;
+  a.lmax = b.L;
+  a.M = b.M;
+  a.npairs = b.npairs;
+  a.B = b.B;
+  a.c = b.leg->leg.c;
+  a.dshift = b.leg->leg.dshift;
+  a.cm = b.leg->leg.cm;
+  a.ring_x = b.leg->leg.ring_x;
+  a.ring_s = b.leg->leg.ring_s;
+  a.memberL = b.memberL;
+  return a;
+}
+
+int launch_adj(const Bucket& b, cudaStream_t s) {
+  const BucketArgs a = bucket_args(b);
+  const size_t sm = (size_t)(BA_LC * BA_TILE + BA_SUB * 2 * BK_COLS) * sizeof(float);
+  switch (b.nt) {
+    case 1:
+      bucket_adj_k<1><<<b.nm, 256, sm, s>>>(a, b.mlist, b.nm, b.S, b.cacc);
+      break;
+    case 2:
+      bucket_adj_k<2><<<b.nm, 256, sm, s>>>(a, b.mlist, b.nm, b.S, b.cacc);
+      break;
+    case 4:
+      bucket_adj_k<4><<<b.nm, 256, sm, s>>>(a, b.mlist, b.nm, b.S, b.cacc);
+      break;
+    default:
+      bucket_adj_k<8><<<b.nm, 256, sm, s>>>(a, b.mlist, b.nm, b.S, b.cacc);
+      break;
+  }
+  return NUSHT_OK;
+}
+
+int set_adj_smem() {
+  const int sm = (BA_LC * BA_TILE + BA_SUB * 2 * BK_COLS) * (int)sizeof(float);
+  NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_k<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_k<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_k<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_k<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  return NUSHT_OK;
+}
+
+int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
+  for (auto& b : p->buckets) {
+    const BucketArgs a = bucket_args(b);
+    dim3 g((b.L + 1 + 3) / 4, b.L + 1);
+    bucket_scale_k<<<g, 256, 0, s>>>(b.L, b.B, b.memberL, b.alm_ptrs, b.leg->leg.ahat, b.atb);
+    if (b.nitems > 0) bucket_synth_k<<<b.nitems, 256, 0, s>>>(a, b.items, b.nitems, b.atb, b.G);
+    bucket_poles_k<<<b.B, 256, 0, s>>>(b.L, b.M, b.memberL, b.alm_ptrs, b.leg->leg.pole_norm, b.G);
+    NUSHT_CUDA(cudaGetLastError());
+    NUSHT_CUFFT(cufftSetStream(b.theta, s));
+    NUSHT_CUFFT(cufftExecC2C(b.theta, (cufftComplex*)b.G, (cufftComplex*)b.Ghat, CUFFT_FORWARD));
+  }
+  for (int i = 0; i < p->nbatch; ++i) {
+    nusht_plan_t q = p->sub[i];
+    NUSHT_TRY(deconv_pad(q, s));
+    NUSHT_CUFFT(cufftSetStream(q->fft_c2r, s));
+    NUSHT_CUFFT(cufftExecC2R(q->fft_c2r, (cufftComplex*)q->fine, (cufftReal*)q->fine));
+    NUSHT_TRY(interp(q, d_map[i], s));
+  }
+  return NUSHT_OK;
+}
+
+int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
+  for (int i = 0; i < p->nbatch; ++i) {
+    nusht_plan_t q = p->sub[i];
+    NUSHT_TRY(spread(q, d_map[i], s));
+    NUSHT_CUFFT(cufftSetStream(q->fft_r2c, s));
+    NUSHT_CUFFT(cufftExecR2C(q->fft_r2c, (cufftReal*)q->fine, (cufftComplex*)q->fine));
+    NUSHT_TRY(deconv_trunc(q, s));
+  }
+  for (auto& b : p->buckets) {
+    NUSHT_CUFFT(cufftSetStream(b.theta, s));
+    NUSHT_CUFFT(cufftExecC2C(b.theta, (cufftComplex*)b.Ghat, (cufftComplex*)b.Ghat, CUFFT_INVERSE));
+    dim3 gf(b.npairs, b.L + 1);
+    bucket_fold_k<<<gf, BK_MAXB, 0, s>>>(b.L, b.M, b.npairs, b.B, b.memberL, b.Ghat, b.S);
+    NUSHT_TRY(launch_adj(b, s));
+    dim3 g((b.L + 1 + 3) / 4, b.L + 1);
+    bucket_final_k<<<g, 256, 0, s>>>(b.L, b.M, b.B, b.memberL, b.cacc, b.leg->leg.ahat, b.leg->leg.pole_norm,
+                                     b.Ghat, b.out_ptrs);
+    NUSHT_CUDA(cudaGetLastError());
+  }
+  return NUSHT_OK;
+}
+
+// pointer tables of every bucket (plan-owned device arrays, written before a
+// capture; the captured kernels read them)
+int set_tables(nusht_batch_t p, const void* const* in, void* const* out, bool synth) {
+  for (auto& b : p->buckets) {
+    std::vector<const void*> vin(BK_MAXB, nullptr);
+    std::vector<void*> vout(BK_MAXB, nullptr);
+    for (int k = 0; k < b.B; ++k) {
+      if (synth)
+        vin[k] = in[b.members[k]];
+      else
+        vout[k] = out[b.members[k]];
+    }
+    if (synth)
+      NUSHT_CUDA(cudaMemcpy(b.alm_ptrs, vin.data(), BK_MAXB * sizeof(void*), cudaMemcpyHostToDevice));
+    else
+      NUSHT_CUDA(cudaMemcpy(b.out_ptrs, vout.data(), BK_MAXB * sizeof(void*), cudaMemcpyHostToDevice));
+  }
+  return NUSHT_OK;
+}
+
+}  // namespace
+}  // namespace nusht
+
+using namespace nusht;
+
+extern "C" {
+
+int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64_t* npts, const double* const* d_pts,
+                    double eps, int precision, const nusht_opts* opts, nusht_stream_t stream) {
+  if (!out) return set_error(NUSHT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nbatch < 1 || nbatch > 4096) return set_error(NUSHT_EINVAL, "nbatch must be in [1, 4096]");
+  if (!lmax || !npts || !d_pts) return set_error(NUSHT_EINVAL, "null array argument");
+  if (precision != NUSHT_MIXED)
+    return set_error(NUSHT_EUNSUPPORTED, "batched transforms run in NUSHT_MIXED precision");
+  for (int i = 0; i < nbatch; ++i) {
+    nusht_sizes z;
+    NUSHT_TRY(choose_sizes(lmax[i], lmax[i], eps, precision, opts, &z));
+    if (lmax[i] > 4095) return set_error(NUSHT_EUNSUPPORTED, "batched transforms support lmax <= 4095");
+    if (npts[i] < 0 || npts[i] > 0x7fffffffLL) return set_error(NUSHT_EINVAL, "npts must be in [0, 2^31)");
+    if (npts[i] > 0 && !d_pts[i]) return set_error(NUSHT_EINVAL, "null point array");
+  }
+  nusht_batch_t p = new (std::nothrow) nusht_batch_s();
+  if (!p) return set_error(NUSHT_ENOMEM, "host allocation failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = NUSHT_OK;
+  do {
+    {
+      cudaError_t e = cudaGetDevice(&p->device);
+      if (e != cudaSuccess) {
+        st = cuda_status(e, "cudaGetDevice");
+        break;
+      }
+    }
+    p->nbatch = nbatch;
+    p->precision = precision;
+    p->eps = eps;
+    if (opts) p->opts = *opts;
+    p->L.assign(lmax, lmax + nbatch);
+    p->npts.assign(npts, npts + nbatch);
+    if ((st = set_adj_smem()) != NUSHT_OK) break;
+    // per-triple costs on GB300: FP64 recurrence (2 FP64 instructions at
+    // ~70 % of 0.6e12/s), one FP32 FMA per column at ~50 % of 37e12/s, and a
+    // fixed cost per bucket
+    const auto groups = group_members(p->L, 4.6e-12, 5.4e-14, 2e-4);
+    p->bucket_of.assign(nbatch, -1);
+    p->slot_of.assign(nbatch, -1);
+    p->buckets.resize(groups.size());
+    for (size_t g = 0; g < groups.size() && st == NUSHT_OK; ++g) {
+      Bucket& b = p->buckets[g];
+      b.members = groups[g];
+      b.B = (int)b.members.size();
+      for (int k = 0; k < b.B; ++k) {
+        b.L = std::max(b.L, p->L[b.members[k]]);
+        p->bucket_of[b.members[k]] = (int)g;
+        p->slot_of[b.members[k]] = k;
+      }
+      st = bucket_build(p, b, s);
+    }
+    if (st != NUSHT_OK) break;
+    p->sub.assign(nbatch, nullptr);
+    for (int i = 0; i < nbatch && st == NUSHT_OK; ++i) {
+      const Bucket& b = p->buckets[p->bucket_of[i]];
+      PlanRole role;
+      role.legendre = false;
+      role.nufft = true;
+      role.M_override = b.M;
+      role.ghat_external = b.Ghat + (size_t)p->slot_of[i] * (b.L + 1) * b.M;
+      st = plan_create(&p->sub[i], p->L[i], p->L[i], p->npts[i], d_pts[i], eps, precision, opts, s, role);
+      if (st == NUSHT_OK) p->bytes += p->sub[i]->bytes;
+    }
+    if (st != NUSHT_OK) break;
+    {
+      cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+      if (e != cudaSuccess) st = cuda_status(e, "cudaStreamCreateWithFlags");
+    }
+  } while (false);
+  if (st != NUSHT_OK) {
+    cudaStreamSynchronize(s);
+    batch_free(p);
+    return st;
+  }
+  *out = p;
+  return NUSHT_OK;
+}
+
+static int run_many(nusht_batch_t p, const void* const* in, void* const* out, nusht_stream_t stream, bool synth) {
+  if (!p) return set_error(NUSHT_EINVAL, "batch plan is NULL");
+  if (!in || !out) return set_error(NUSHT_EINVAL, "null pointer array");
+  for (int i = 0; i < p->nbatch; ++i)
+    if (!in[i] || (!out[i] && p->npts[i] > 0)) return set_error(NUSHT_EINVAL, "null member buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<const void*> vin(in, in + p->nbatch);
+  std::vector<void*> vout(out, out + p->nbatch);
+  cudaGraphExec_t& ex = synth ? p->gs : p->ga;
+  std::vector<const void*>& kin = synth ? p->gs_in : p->ga_in;
+  std::vector<void*>& kout = synth ? p->gs_out : p->ga_out;
+  if (!ex || kin != vin || kout != vout) {
+    if (ex) {
+      NUSHT_CUDA(cudaStreamSynchronize(s));
+      cudaGraphExecDestroy(ex);
+      ex = nullptr;
+    }
+    NUSHT_TRY(set_tables(p, in, out, synth));
+    cudaGraph_t g = nullptr;
+    NUSHT_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    int st = synth ? enqueue_synth(p, out, p->cap) : enqueue_adjoint(p, in, p->cap);
+    cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+    if (st != NUSHT_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      ex = nullptr;
+      return cuda_status(e, "cudaGraphInstantiate");
+    }
+    kin = vin;
+    kout = vout;
+  }
+  NUSHT_CUDA(cudaGraphLaunch(ex, s));
+  return NUSHT_OK;
+}
+
+int nusht_synth_many(nusht_batch_t p, const void* const* d_alm, void* const* d_map, nusht_stream_t stream) {
+  return run_many(p, d_alm, d_map, stream, true);
+}
+
+int nusht_adjoint_many(nusht_batch_t p, const void* const* d_map, void* const* d_alm, nusht_stream_t stream) {
+  return run_many(p, d_map, d_alm, stream, false);
+}
+
+int nusht_destroy_many(nusht_batch_t p) {
+  batch_free(p);
+  return NUSHT_OK;
+}
+
+int nusht_batch_info(nusht_batch_t p, int* nbuckets, int* bucket_of, int* bucket_lmax, int64_t* bytes_device) {
+  if (!p) return set_error(NUSHT_EINVAL, "batch plan is NULL");
+  if (nbuckets) *nbuckets = (int)p->buckets.size();
+  if (bucket_of)
+    for (int i = 0; i < p->nbatch; ++i) bucket_of[i] = p->bucket_of[i];
+  if (bucket_lmax)
+    for (size_t g = 0; g < p->buckets.size(); ++g) bucket_lmax[g] = p->buckets[g].L;
+  if (bytes_device) *bytes_device = (int64_t)p->bytes;
+  return NUSHT_OK;
+}
+
+}  // extern "C"

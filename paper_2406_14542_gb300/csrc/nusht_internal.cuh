@@ -127,12 +127,29 @@ struct nusht_plan_s {
 
   size_t bytes = 0;
 
+  // role inside a batch (see nusht::PlanRole); a standalone plan has all parts
+  bool has_legendre = true, has_nufft = true, ghat_owned = true;
+
   // profiling
   nusht::StageEvents ev_synth, ev_adj;
   cudaStream_t last_stream = nullptr;
 };
 
 namespace nusht {
+
+// What a plan builds.  A standalone plan has everything.  Inside a batch,
+// member plans carry only the NUFFT part (points, fine grid, deconvolution
+// factors, 2D FFTs) and read/write their theta spectrum in a slice of their
+// bucket's buffer; a bucket owns one Legendre-only plan for the tables.
+struct PlanRole {
+  int M_override = 0;         // theta length shared by a bucket (0 = own choice)
+  bool legendre = true;
+  bool nufft = true;
+  void* ghat_external = nullptr;
+};
+int plan_create(nusht_plan_t* out, int lmax, int mmax, int64_t npts, const double* d_pts, double eps, int precision,
+                const nusht_opts* opts, cudaStream_t s, const PlanRole& role);
+void plan_destroy(nusht_plan_t p);
 
 // sizes / host math (plan.cu)
 int choose_sizes(int lmax, int mmax, double eps, int precision, const nusht_opts* o, nusht_sizes* out);

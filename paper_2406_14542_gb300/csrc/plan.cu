@@ -213,7 +213,7 @@ static void plan_free(nusht_plan_t p) {
   dev_free(p->deconv2);
   dev_free(p->atilde);
   dev_free(p->G);
-  dev_free(p->Ghat);
+  if (p->ghat_owned) dev_free(p->Ghat);
   dev_free(p->fine);
   dev_free(p->partial);
   if (p->have_theta) cufftDestroy(p->fft_theta);
@@ -230,11 +230,14 @@ static int make_ffts(nusht_plan_t p) {
   const nusht_sizes& z = p->sz;
   const bool dbl = p->precision == NUSHT_FP64;
   int M = z.M;
-  NUSHT_CUFFT(cufftCreate(&p->fft_theta));
-  p->have_theta = true;
   size_t ws = 0;
-  NUSHT_CUFFT(cufftMakePlanMany(p->fft_theta, 1, &M, nullptr, 1, M, nullptr, 1, M, dbl ? CUFFT_Z2Z : CUFFT_C2C,
-                                z.mmax + 1, &ws));
+  if (p->has_legendre) {
+    NUSHT_CUFFT(cufftCreate(&p->fft_theta));
+    p->have_theta = true;
+    NUSHT_CUFFT(cufftMakePlanMany(p->fft_theta, 1, &M, nullptr, 1, M, nullptr, 1, M, dbl ? CUFFT_Z2Z : CUFFT_C2C,
+                                  z.mmax + 1, &ws));
+  }
+  if (!p->has_nufft) return NUSHT_OK;
   NUSHT_CUFFT(cufftCreate(&p->fft_c2r));
   p->have_c2r = true;
   NUSHT_CUFFT(cufftMakePlan2d(p->fft_c2r, z.n1, z.n2, dbl ? CUFFT_Z2D : CUFFT_C2R, &ws));
@@ -259,9 +262,18 @@ static int check_device(int* dev) {
   return NUSHT_OK;
 }
 
-static int plan_body(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s) {
+static int plan_body(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s, const PlanRole& role) {
   const nusht_sizes& z = p->sz;
   const size_t cplx = (p->precision == NUSHT_FP64) ? 16 : 8;
+  const size_t gbytes = (size_t)(z.mmax + 1) * z.M * cplx;
+  if (!role.nufft) {
+    // bucket tables only: recurrence coefficients and the polar-skip work list
+    NUSHT_TRY(legendre_build_tables(p, s));
+    p->sz.nitems = p->leg.nitems;
+    p->sz.nitems_total = p->leg.nitems_total;
+    p->sz.leg_triples = p->leg.triples;
+    return NUSHT_OK;
+  }
   // Fourier factors of the ES kernel (deconvolution, Sec. 3 on the NUFFT):
   // d1[k] = h1 / (M psihat1(k)) folds the 1/M of the theta DFT, d2[m] = h2 / psihat2(m).
   {
@@ -278,15 +290,23 @@ static int plan_body(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStre
     NUSHT_CUDA(cudaMemcpyAsync(p->deconv2, d2.data(), d2.size() * 8, cudaMemcpyHostToDevice, s));
     NUSHT_CUDA(cudaStreamSynchronize(s));
   }
-  const size_t gbytes = (size_t)(z.mmax + 1) * z.M * cplx;
-  NUSHT_TRY(dev_alloc(&p->atilde, (size_t)p->nalm * cplx, &p->bytes));
-  NUSHT_TRY(dev_alloc(&p->G, gbytes, &p->bytes));
-  NUSHT_TRY(dev_alloc(&p->Ghat, gbytes, &p->bytes));
-  NUSHT_CUDA(cudaMemsetAsync(p->G, 0, gbytes, s));
+  if (role.legendre) {
+    NUSHT_TRY(dev_alloc(&p->atilde, (size_t)p->nalm * cplx, &p->bytes));
+    NUSHT_TRY(dev_alloc(&p->G, gbytes, &p->bytes));
+    NUSHT_CUDA(cudaMemsetAsync(p->G, 0, gbytes, s));
+  }
+  if (role.ghat_external) {
+    p->Ghat = role.ghat_external;
+    p->ghat_owned = false;
+  } else {
+    NUSHT_TRY(dev_alloc(&p->Ghat, gbytes, &p->bytes));
+  }
   NUSHT_TRY(dev_alloc(&p->fine, (size_t)z.n1 * (z.n2 / 2 + 1) * cplx, &p->bytes));
-  NUSHT_TRY(legendre_build_tables(p, s));
-  NUSHT_TRY(dev_alloc(&p->partial, (size_t)p->leg.blocks_per_m * p->nalm * cplx, &p->bytes));
-  NUSHT_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)p->leg.blocks_per_m * p->nalm * cplx, s));
+  if (role.legendre) {
+    NUSHT_TRY(legendre_build_tables(p, s));
+    NUSHT_TRY(dev_alloc(&p->partial, (size_t)p->leg.blocks_per_m * p->nalm * cplx, &p->bytes));
+    NUSHT_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)p->leg.blocks_per_m * p->nalm * cplx, s));
+  }
   NUSHT_TRY(make_ffts(p));
   NUSHT_TRY(setpts_impl(p, npts, d_pts, s));
   NUSHT_CUDA(cudaStreamSynchronize(s));
@@ -301,10 +321,23 @@ extern "C" {
 
 int nusht_plan(nusht_plan_t* out, int lmax, int mmax, int64_t npts, const double* d_pts, double eps, int precision,
                const nusht_opts* opts, nusht_stream_t stream) {
+  return nusht::plan_create(out, lmax, mmax, npts, d_pts, eps, precision, opts, (cudaStream_t)stream,
+                            nusht::PlanRole());
+}
+
+}  // extern "C"
+
+int nusht::plan_create(nusht_plan_t* out, int lmax, int mmax, int64_t npts, const double* d_pts, double eps,
+                       int precision, const nusht_opts* opts, cudaStream_t stream, const PlanRole& role) {
   if (!out) return set_error(NUSHT_EINVAL, "out is NULL");
   *out = nullptr;
   nusht_sizes z;
   NUSHT_TRY(choose_sizes(lmax, mmax, eps, precision, opts, &z));
+  if (role.M_override) {
+    if (role.M_override < z.M || role.M_override % 4) return set_error(NUSHT_EINVAL, "bad theta length override");
+    z.M = role.M_override;
+    z.nrings = z.M / 2 + 1;
+  }
   if (npts < 0 || npts > 0x7fffffffLL) return set_error(NUSHT_EINVAL, "npts must be in [0, 2^31)");
   if (npts > 0 && !d_pts) return set_error(NUSHT_EINVAL, "d_pts is NULL");
   int dev = 0;
@@ -322,8 +355,10 @@ int nusht_plan(nusht_plan_t* out, int lmax, int mmax, int64_t npts, const double
   p->sz = z;
   if (opts) p->opts = *opts;
   p->nalm = (int64_t)(mmax + 1) * (lmax + 1) - (int64_t)mmax * (mmax + 1) / 2;
-  cudaStream_t s = (cudaStream_t)stream;
-  int st = plan_body(p, npts, d_pts, s);
+  p->has_legendre = role.legendre;
+  p->has_nufft = role.nufft;
+  cudaStream_t s = stream;
+  int st = plan_body(p, npts, d_pts, s, role);
   g_fail_after = -1;
   if (st != NUSHT_OK) {
     cudaStreamSynchronize(s);
@@ -334,6 +369,10 @@ int nusht_plan(nusht_plan_t* out, int lmax, int mmax, int64_t npts, const double
   *out = p;
   return NUSHT_OK;
 }
+
+void nusht::plan_destroy(nusht_plan_t p) { plan_free(p); }
+
+extern "C" {
 
 int nusht_setpts(nusht_plan_t p, int64_t npts, const double* d_pts, nusht_stream_t stream) {
   if (!p) return set_error(NUSHT_EINVAL, "plan is NULL");

@@ -1,0 +1,99 @@
+"""Batched transforms (many uneven lmax and point counts in one plan, mixed
+precision) against the oracle, member by member, at the mixed tolerance
+eps_eff <= 1e-5; plus graph re-capture when the buffers change and the
+adjoint dot test."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_14542_gb300 import build
+
+    build.build()
+    import paper_2406_14542_gb300 as nu
+
+    return torch, nu
+
+
+def make_batch(torch, nu, ls, seed=0):
+    alms = [W.alm_gaussian(l, seed=seed + 10 * i, dtype=np.complex64) for i, l in enumerate(ls)]
+    pts = [W.points_uniform(max(1, 2 * l * l), seed=seed + 10 * i + 1) for i, l in enumerate(ls)]
+    bp = nu.BatchPlan(ls, [torch.from_numpy(p).cuda() for p in pts], eps=1e-5)
+    return bp, alms, pts
+
+
+def test_batch_small_against_oracle(env):
+    torch, nu = env
+    ls = [0, 3, 16, 40, 63, 100, 130, 7]
+    bp, alms, pts = make_batch(torch, nu, ls)
+    info = bp.info()
+    assert info["nbuckets"] >= 1 and max(info["bucket_lmax"]) == max(ls)
+    outs = bp.synth([torch.from_numpy(a).cuda() for a in alms])
+    torch.cuda.synchronize()
+    for l, a, p, f in zip(ls, alms, pts, outs):
+        sel = W.subset(p.shape[0], 3000, seed=l)
+        ref = oracle.synth(a.astype(np.complex128), p[sel], l)
+        assert oracle.eps_eff(ref, f.double().cpu().numpy()[sel]) <= TOL, l
+    ys = [np.random.default_rng(i).standard_normal(p.shape[0]) for i, p in enumerate(pts)]
+    cs = bp.adjoint([torch.from_numpy(y).float().cuda() for y in ys])
+    for l, p, y, c in zip(ls, pts, ys, cs):
+        ref = oracle.adjoint(y.astype(np.float32).astype(np.float64), p, l)
+        assert oracle.eps_eff(ref, c.cpu().numpy().astype(np.complex128)) <= TOL, l
+
+
+def test_batch_recapture_and_dot(env):
+    """New buffers force a new graph; results and the dot test hold."""
+    torch, nu = env
+    ls = [20, 31, 47]
+    bp, alms, pts = make_batch(torch, nu, ls, seed=5)
+    ad = [torch.from_numpy(a).cuda() for a in alms]
+    f1 = [x.clone() for x in bp.synth(ad)]
+    f2 = bp.synth(ad)  # fresh output buffers -> re-capture
+    for x, y in zip(f1, f2):
+        assert torch.equal(x, y)
+    ys = [torch.randn(p.shape[0], device="cuda") for p in pts]
+    cs = bp.adjoint(ys)
+    for l, a, f, y, c in zip(ls, alms, f1, ys, cs):
+        lhs = float(torch.dot(y.double(), f.double()))
+        rhs = oracle.alm_dot(c.cpu().numpy().astype(np.complex128), a.astype(np.complex128), l)
+        assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_batch64_members_against_oracle(env):
+    """64 transforms, lmax ~ U{64..511}, N_b = 2 lmax_b^2 uniform points: the
+    batch structure of the 64-transform workload at a size the oracle can
+    check; members sampled across buckets."""
+    torch, nu = env
+    rng = np.random.default_rng(0)
+    ls = [int(x) for x in rng.integers(64, 512, 64)]
+    bp, alms, pts = make_batch(torch, nu, ls, seed=100)
+    info = bp.info()
+    outs = bp.synth([torch.from_numpy(a).cuda() for a in alms])
+    torch.cuda.synchronize()
+    order = np.argsort(ls)
+    check = sorted({int(order[0]), int(order[len(ls) // 2]), int(order[-1])} |
+                   {int(np.argmax(np.array(info["bucket_of"]) == b)) for b in range(info["nbuckets"])})
+    for i in check:
+        sel = W.subset(pts[i].shape[0], 1500, seed=i)
+        ref = oracle.synth(alms[i].astype(np.complex128), pts[i][sel], ls[i])
+        assert oracle.eps_eff(ref, outs[i].double().cpu().numpy()[sel]) <= TOL, (i, ls[i])
+    ys = [torch.randn(p.shape[0], device="cuda") for p in pts]
+    cs = bp.adjoint(ys)
+    torch.cuda.synchronize()
+    for i in check[:3]:
+        l = ls[i]
+        ms = [0, 1, l // 2, l]
+        ref = oracle.adjoint(ys[i].double().cpu().numpy(), pts[i], l, mlist=ms)
+        idx = np.concatenate([np.arange(oracle.lm_index(l, m, m), oracle.lm_index(l, l, m) + 1) for m in ms])
+        got = cs[i].cpu().numpy().astype(np.complex128)
+        assert oracle.eps_eff(ref[idx], got[idx]) <= TOL, (i, l)
