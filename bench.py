@@ -218,6 +218,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-transform batched measurement")
+    ap.add_argument("--only-batch", action="store_true", help="run only the 64-transform batched measurement")
+    ap.add_argument("--batch-n", type=int, default=64, help="transforms in the batched workload")
+    ap.add_argument("--batch-lmax", type=int, default=2047, help="largest lmax of the batched workload")
     ap.add_argument("--workload", default=WORKLOAD, choices=["gl1023", "gl2047", "gl4095"],
                     help="smaller deflected-grid cases for profiling; the benchmark is gl4095")
     args = ap.parse_args()
@@ -231,6 +235,11 @@ def main():
     import paper_2406_14542_gb300 as nu
 
     dist, rank, world, local = dist_setup(args.gpus)
+    if args.only_batch:
+        b = run_batch64(torch, nu, args, dist, rank, sequential=False)
+        if rank == 0:
+            print(json.dumps({"batch64": b}), flush=True)
+        return
     L, a, pts = W.workload(args.workload)
     npts = pts.shape[0]
     peaks, peak_src = load_peaks()
@@ -295,6 +304,10 @@ def main():
         del ad, y, fmap, calm
         torch.cuda.empty_cache()
 
+    batch = None
+    if not args.no_batch and args.workload == WORKLOAD:
+        batch = run_batch64(torch, nu, args, dist, rank)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -351,11 +364,74 @@ def main():
                          "synth_ms": mx["stages"]["synth"]["total"], "adjoint_ms": mx["stages"]["adjoint"]["total"],
                          "stages_ms": mx["stages"], "w": mx["info"]["w"], "sigma": mx["info"]["sigma"],
                          "dtype": "f64 recurrence / f32 contraction, FFT, NUFFT", "clocks": mx["clocks"]}
+    if batch is not None:
+        line["batch64"] = batch
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_batch64(torch, nu, args, dist, rank, sequential=True):
+    """64 independent transforms, lmax_b ~ U{256..2047}, N_b = 2 lmax_b^2 uniform
+    points, complex64 a_lm, eps 1e-5: one batched plan (shared-ring buckets,
+    graph replay) against the same transforms run one by one through
+    standalone mixed-precision plans."""
+    members = W.batch64(nbatch=args.batch_n, lmax=args.batch_lmax)
+    ls = [m[0] for m in members]
+    dpts = [torch.from_numpy(m[2]).cuda() for m in members]
+    alms = [torch.from_numpy(m[1]).cuda() for m in members]
+    ys = [torch.randn(d.shape[0], dtype=torch.float32, device="cuda") for d in dpts]
+    t0 = time.perf_counter()
+    bp = nu.BatchPlan(ls, dpts, eps=1e-5)
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t0
+    fo = [torch.empty(d.shape[0], dtype=torch.float32, device="cuda") for d in dpts]
+    co = [torch.empty(nu.nalm(l), dtype=torch.complex64, device="cuda") for l in ls]
+
+    def step():
+        bp.synth(alms, fo)
+        bp.adjoint(ys, co)
+
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ms = max_over_ranks(dist, time_steps(torch, step, args.steps, args.warmup, dist))
+    info = bp.info()
+    # parity on sampled members (largest, smallest, median lmax)
+    par = None
+    if rank == 0:
+        import oracle
+
+        order = np.argsort(ls)
+        errs = []
+        for i in [int(order[-1]), int(order[0]), int(order[len(ls) // 2])]:
+            sel = W.subset(dpts[i].shape[0], 200, seed=i)
+            ref = oracle.synth(members[i][1].astype(np.complex128), members[i][2][sel], ls[i])
+            errs.append(oracle.eps_eff(ref, fo[i].double().cpu().numpy()[sel]))
+        par = max(errs)
+    bp.close()
+    torch.cuda.synchronize()
+    # the same transforms one by one (standalone plans, same eps / precision)
+    seq = 0.0
+    for i in range(len(ls) if sequential else 0):
+        pl = nu.Plan(ls[i], dpts[i], eps=1e-5, precision="mixed")
+        f = torch.empty_like(fo[i])
+        c = torch.empty_like(co[i])
+
+        def one():
+            pl.synth(alms[i], out=f)
+            pl.adjoint(ys[i], out=c)
+
+        seq += time_steps(torch, one, 2, 3, None)
+        pl.close()
+    torch.cuda.empty_cache()
+    return {"workload": "%d transforms, lmax ~ U{256..%d} (seed 0), N_b = 2 lmax_b^2 uniform points "
+                        "(%d total), complex64, eps 1e-5" % (args.batch_n, args.batch_lmax,
+                                                             sum(int(d.shape[0]) for d in dpts)),
+            "ms_per_step": ms, "sequential_ms_per_step": seq if sequential else None,
+            "speedup_vs_sequential": seq / ms if sequential else None,
+            "buckets": info["nbuckets"], "bucket_lmax": info["bucket_lmax"], "plan_s": t_plan,
+            "eps_eff_max_sampled": par, "clocks": clk.summary()}
 
 
 def _kernel_hash() -> str:

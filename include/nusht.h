@@ -95,7 +95,10 @@ typedef struct {
   int fp64_contraction; /* FP64 mode only: 1 = Legendre sums with FP64 instructions;
                            0 (default) = FP64 recurrence, sums as float pairs on the FP32
                            pipe (~2^-48 relative per operation; a_lm magnitudes below 1e20) */
-  int reserved[6];
+  int legendre_table; /* batched plans: 0 = run the FP64 recurrence once at plan time and keep
+                         its values in device memory when they fit (half the free memory),
+                         -1 = run the recurrence on every call */
+  int reserved[5];
 } nusht_opts;
 
 /* Sizes a plan uses; filled by nusht_plan_sizes (no GPU needed) and nusht_info. */

@@ -38,7 +38,7 @@ class NushtError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("kernel_width", ctypes.c_int), ("profile", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("tune", ctypes.c_int), ("fp64_contraction", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("legendre_table", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class Sizes(ctypes.Structure):
@@ -115,8 +115,9 @@ def _check(code: int, where: str):
         raise NushtError(code, where, load().nusht_last_error().decode())
 
 
-def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False) -> Opts:
+def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False, legendre_table=0) -> Opts:
     o = Opts()
+    o.legendre_table = int(legendre_table)
     o.sigma = float(sigma)
     o.kernel_width = int(kernel_width)
     o.profile = 1 if profile else 0
@@ -316,7 +317,8 @@ class BatchPlan:
     precision): complex64 a_lm, float32 maps.  ``pts_list[b]`` is a CUDA
     float64 (N_b, 2) tensor; each lmax <= 4095."""
 
-    def __init__(self, lmaxs, pts_list, eps: float = 1e-5, sigma: float = 0.0, stream=None):
+    def __init__(self, lmaxs, pts_list, eps: float = 1e-5, sigma: float = 0.0, legendre_table: int = 0,
+                 stream=None):
         import torch
 
         self.lib = load()
@@ -330,7 +332,7 @@ class BatchPlan:
         larr = (ctypes.c_int * n)(*self.lmaxs)
         narr = (ctypes.c_int64 * n)(*self.npts)
         parr = (ctypes.c_void_p * n)(*[p.data_ptr() if p.numel() else 0 for p in self.pts])
-        o = _opts(sigma)
+        o = _opts(sigma, legendre_table=legendre_table)
         h = ctypes.c_void_p()
         _check(self.lib.nusht_plan_many(ctypes.byref(h), n, larr, narr, parr, float(eps), MIXED, ctypes.byref(o),
                                         _stream_ptr(stream)), "nusht_plan_many")

@@ -318,6 +318,224 @@ __global__ void __launch_bounds__(256) bucket_adj_k(BucketArgs a, const int* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// Table path.  The recurrence values depend only on the bucket's rings, not
+// on the coefficients or the points, so the plan runs the FP64 recurrence
+// once and keeps q = Pbar / Ahat (as float, 0 in the scaled phase) in HBM:
+// P[item][l - m][64 pairs] for every kept (order, 64-pair tile).  Each call
+// is then a pure FP32 contraction streaming that table (synthesis) or its
+// transpose (adjoint); the double-buffered tiles arrive by cp.async.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) bucket_ptab_k(BucketArgs a, const int* __restrict__ items,
+                                                     const int64_t* __restrict__ offs, int nitems,
+                                                     float* __restrict__ P) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  const int v = items[it];
+  const int m = v >> 16, tile = v & 0xffff;
+  const int L = a.lmax;
+  const int mb = idx_lm(L, 0, m);
+  Chain ch[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) chain_init(ch[k], a, m, 1 + tile * BS_PAIRS + k * 32 + lane);
+  float* out = P + offs[it];
+  for (int l = m; l <= L; ++l) {
+    const bool step = l > m;
+    const double c = step ? __ldg(a.c + mb + l) : 0.0;
+    const bool rs = step && __ldg(a.dshift + mb + l) != 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (step) chain_step(ch[k], c, rs);
+      out[(size_t)(l - m) * BS_PAIRS + k * 32 + lane] = (ch[k].valid && ch[k].E == 0) ? to_f32(ch[k].q1) : 0.f;
+    }
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const int n = valid ? 16 : 0;  // 0 source bytes: the 16 destination bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// synthesis from the table: block = kept item (m, 64 pairs)
+__global__ void __launch_bounds__(256) bucket_synth_tab_k(BucketArgs a, const int* __restrict__ items,
+                                                          const int64_t* __restrict__ offs, int nitems,
+                                                          const float* __restrict__ P, const float2* __restrict__ atb,
+                                                          float2* __restrict__ G) {
+  __shared__ __align__(16) float Ps[2][BS_LC][BS_PAIRS];
+  __shared__ __align__(16) float As[2][BS_LC][BK_COLS];
+  const int it = blockIdx.x;
+  if (it >= nitems) return;
+  const int v = items[it];
+  const int m = v >> 16, tile = v & 0xffff;
+  const int L = a.lmax;
+  const int mb = idx_lm(L, 0, m);
+  const int t = threadIdx.x;
+  const float* Pi = P + offs[it];
+  const int nrow = L - m + 1;
+  const int nchunk = (nrow + BS_LC - 1) / BS_LC;
+  auto load = [&](int ck, int buf) {
+    // P rows: 16 x 64 floats = 256 x 16 B; A rows: 16 x 128 floats = 512 x 16 B
+    {
+      const int r = t >> 4, c4 = t & 15;
+      const int row = ck * BS_LC + r;
+      const bool ok = row < nrow;
+      cp_async16(&Ps[buf][r][c4 * 4], Pi + (size_t)(ok ? row : 0) * BS_PAIRS + c4 * 4, ok);
+    }
+    for (int e = t; e < BS_LC * BK_COLS / 4; e += 256) {
+      const int r = e >> 5, c4 = e & 31;
+      const int row = ck * BS_LC + r;
+      const bool ok = row < nrow;
+      cp_async16(&As[buf][r][c4 * 4],
+                 reinterpret_cast<const float*>(atb + (size_t)(mb + m + (ok ? row : 0)) * BK_MAXB) + c4 * 4, ok);
+    }
+    cp_async_commit();
+  };
+  // thread tile: 8 pairs (warp-uniform, so P reads broadcast) x 4 columns
+  const int pg = t >> 5, cg = t & 31;
+  float accE[8][4], accO[8][4];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) accE[r][c] = accO[r][c] = 0.f;
+  load(0, 0);
+  for (int ck = 0; ck < nchunk; ++ck) {
+    const int buf = ck & 1;
+    if (ck + 1 < nchunk) {
+      load(ck + 1, buf ^ 1);
+      cp_async_wait1();
+    } else {
+      cp_async_wait0();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < BS_LC; ++j) {
+      const float4 p0 = *reinterpret_cast<const float4*>(&Ps[buf][j][pg * 8]);
+      const float4 p1 = *reinterpret_cast<const float4*>(&Ps[buf][j][pg * 8 + 4]);
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][j][cg * 4]);
+      const float pr[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+      const float ar[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (j & 1)
+            accO[r][c] = fmaf(pr[r], ar[c], accO[r][c]);
+          else
+            accE[r][c] = fmaf(pr[r], ar[c], accE[r][c]);
+        }
+    }
+    __syncthreads();
+  }
+  const int M = a.M;
+  const float sg = (m & 1) ? -1.f : 1.f;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int jn = 1 + tile * BS_PAIRS + pg * 8 + r;
+    if (jn > a.npairs) continue;
+    const int js = M / 2 - jn;
+#pragma unroll
+    for (int ss = 0; ss < 2; ++ss) {
+      const int slot = cg * 2 + ss;
+      if (slot >= a.B || m > a.memberL[slot]) continue;
+      const float2 fn = make_float2(accE[r][2 * ss] + accO[r][2 * ss], accE[r][2 * ss + 1] + accO[r][2 * ss + 1]);
+      const float2 fs = make_float2(accE[r][2 * ss] - accO[r][2 * ss], accE[r][2 * ss + 1] - accO[r][2 * ss + 1]);
+      float2* row = G + ((size_t)slot * (L + 1) + m) * M;
+      row[jn] = fn;
+      row[M - jn] = make_float2(sg * fn.x, sg * fn.y);
+      if (js != jn) {
+        row[js] = fs;
+        row[M - js] = make_float2(sg * fs.x, sg * fs.y);
+      }
+    }
+  }
+}
+
+// adjoint from the table: block = (order m, 128 degrees); loops over the
+// order's kept tiles (items[mfirst[m] .. mfirst[m+1]) ), staging P
+// transposed (Pt[pair][degree]) and S[64 pairs][E|O x 128]; thread tile =
+// 16 consecutive degrees (warp-uniform) x 4 columns; the block owns its
+// 128 x 128 outputs
+constexpr int AT_LC = 128;
+constexpr int AT_PAD = AT_LC + 4;  // Pt row stride (floats), 16-byte aligned rows
+__global__ void __launch_bounds__(256) bucket_adj_tab_k(BucketArgs a, const int* __restrict__ items,
+                                                        const int64_t* __restrict__ offs,
+                                                        const int* __restrict__ mfirst, const int2* __restrict__ work,
+                                                        int nwork, const float* __restrict__ P,
+                                                        const float* __restrict__ S, float* __restrict__ cacc) {
+  extern __shared__ __align__(16) float smem[];
+  float* Pt = smem;                       // [64 pairs][AT_PAD]
+  float* Ss = smem + BS_PAIRS * AT_PAD;   // [64 pairs][2 * BK_COLS]
+  if ((int)blockIdx.x >= nwork) return;
+  const int2 wk = work[blockIdx.x];
+  const int m = wk.x, l0 = wk.y;  // degrees l0 .. l0 + 127
+  const int L = a.lmax;
+  const int mb = idx_lm(L, 0, m);
+  const int t = threadIdx.x;
+  const int jr = t >> 5, cg = t & 31;  // degrees jr*16 .. +15, columns cg*4 .. +3
+  float acc[16][4];
+#pragma unroll
+  for (int i = 0; i < 16; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+  const int i0 = mfirst[m], i1 = mfirst[m + 1];
+  const int nrow = L - m + 1;
+  for (int it = i0; it < i1; ++it) {
+    const int tile = items[it] & 0xffff;
+    const float* Pi = P + offs[it];
+    const float* Sp = S + ((size_t)m * a.npairs + (size_t)tile * BS_PAIRS) * 2 * BK_COLS;
+    for (int e = t; e < BS_PAIRS * 2 * BK_COLS / 4; e += 256) {
+      const int pr = e >> 6;
+      const bool ok = tile * BS_PAIRS + pr < a.npairs;
+      cp_async16(Ss + e * 4, Sp + (ok ? e * 4 : 0), ok);
+    }
+    cp_async_commit();
+    // P rows (l0 - m) .. +127, transposed into Pt[pair][row]
+    {
+      const int pair = t & 63;
+#pragma unroll 4
+      for (int r = t >> 6; r < AT_LC; r += 4) {
+        const int row = l0 - m + r;
+        Pt[pair * AT_PAD + r] = row < nrow ? Pi[(size_t)row * BS_PAIRS + pair] : 0.f;
+      }
+    }
+    cp_async_wait0();
+    __syncthreads();
+#pragma unroll 4
+    for (int pr = 0; pr < BS_PAIRS; ++pr) {
+      const float* prow = Pt + pr * AT_PAD + jr * 16;
+      const float4 q0 = *reinterpret_cast<const float4*>(prow);
+      const float4 q1 = *reinterpret_cast<const float4*>(prow + 4);
+      const float4 q2 = *reinterpret_cast<const float4*>(prow + 8);
+      const float4 q3 = *reinterpret_cast<const float4*>(prow + 12);
+      const float q[16] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
+                           q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
+      const float* srow = Ss + pr * 2 * BK_COLS;
+      const float4 se = *reinterpret_cast<const float4*>(srow + cg * 4);
+      const float4 so = *reinterpret_cast<const float4*>(srow + BK_COLS + cg * 4);
+      const float e4[4] = {se.x, se.y, se.z, se.w};
+      const float o4[4] = {so.x, so.y, so.z, so.w};
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(q[i], (i & 1) ? o4[c] : e4[c], acc[i][c]);
+    }
+    __syncthreads();
+  }
+  // degree l0 + jr*16 + i has parity i & 1 (l0 - m is a multiple of 128)
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int l = l0 + jr * 16 + i;
+    if (l <= L)
+      *reinterpret_cast<float4*>(cacc + (size_t)(mb + l) * BK_COLS + cg * 4) =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  }
+}
+
 // member outputs: c_slot(l, m) = Ahat * C + poles (m = 0)
 __global__ void bucket_final_k(int L, int M, int B, const int* __restrict__ memberL, const float* __restrict__ cacc,
                                const double* __restrict__ ahat, const double* __restrict__ pole_norm,
@@ -356,6 +574,14 @@ struct Bucket {
   float* cacc = nullptr;
   const float2** alm_ptrs = nullptr;  // device [BK_MAXB]
   float2** out_ptrs = nullptr;        // device [BK_MAXB]
+  // table path
+  bool table = false;
+  float* P = nullptr;                 // recurrence table, [item][l - m][64]
+  int64_t* offs = nullptr;            // item offsets into P
+  int* mfirst = nullptr;              // items of order m: [mfirst[m], mfirst[m+1])
+  int2* work = nullptr;               // adjoint blocks (m, first degree)
+  int nwork = 0;
+  size_t table_bytes = 0;
   cufftHandle theta = 0;
   bool have_theta = false;
 };
@@ -398,6 +624,10 @@ void bucket_free(Bucket& b) {
   dev_free(b.cacc);
   dev_free(b.alm_ptrs);
   dev_free(b.out_ptrs);
+  dev_free(b.P);
+  dev_free(b.offs);
+  dev_free(b.mfirst);
+  dev_free(b.work);
   if (b.have_theta) cufftDestroy(b.theta);
   b = Bucket();
 }
@@ -451,6 +681,21 @@ std::vector<std::vector<int>> group_members(const std::vector<int>& L, double c_
   return groups;
 }
 
+BucketArgs bucket_args(const Bucket& b) {
+  BucketArgs a;
+  a.lmax = b.L;
+  a.M = b.M;
+  a.npairs = b.npairs;
+  a.B = b.B;
+  a.c = b.leg->leg.c;
+  a.dshift = b.leg->leg.dshift;
+  a.cm = b.leg->leg.cm;
+  a.ring_x = b.leg->leg.ring_x;
+  a.ring_s = b.leg->leg.ring_s;
+  a.memberL = b.memberL;
+  return a;
+}
+
 int bucket_build(nusht_batch_t p, Bucket& b, cudaStream_t s) {
   const int L = b.L;
   nusht_sizes z;
@@ -498,6 +743,37 @@ int bucket_build(nusht_batch_t p, Bucket& b, cudaStream_t s) {
   NUSHT_CUDA(cudaMemsetAsync(b.G, 0, gbytes, s));
   NUSHT_CUDA(cudaMemsetAsync(b.Ghat, 0, gbytes, s));
   NUSHT_CUDA(cudaMemsetAsync(b.cacc, 0, (size_t)nalm * BK_COLS * sizeof(float), s));
+  // recurrence table when it fits (the on-the-fly kernels otherwise)
+  {
+    std::vector<int64_t> off(tiles.size() + 1, 0);
+    for (size_t k = 0; k < tiles.size(); ++k) off[k + 1] = off[k] + (int64_t)(L - (tiles[k] >> 16) + 1) * BS_PAIRS;
+    const size_t need = (size_t)off.back() * sizeof(float);
+    size_t freeb = 0, totalb = 0;
+    cudaMemGetInfo(&freeb, &totalb);
+    if (p->opts.legendre_table >= 0 && need > 0 && need < freeb / 2) {
+      b.table = true;
+      b.table_bytes = need;
+      NUSHT_TRY(dev_alloc((void**)&b.P, need, &p->bytes));
+      NUSHT_TRY(dev_alloc((void**)&b.offs, off.size() * 8, &p->bytes));
+      NUSHT_CUDA(cudaMemcpy(b.offs, off.data(), off.size() * 8, cudaMemcpyHostToDevice));
+      std::vector<int> mf(L + 2, 0);
+      for (size_t k = 0; k < tiles.size(); ++k) mf[(tiles[k] >> 16) + 1]++;
+      for (int m = 0; m <= L; ++m) mf[m + 1] += mf[m];
+      NUSHT_TRY(dev_alloc((void**)&b.mfirst, mf.size() * 4, &p->bytes));
+      NUSHT_CUDA(cudaMemcpy(b.mfirst, mf.data(), mf.size() * 4, cudaMemcpyHostToDevice));
+      std::vector<int2> wk;
+      for (int m = 0; m <= L; ++m)
+        if (mf[m + 1] > mf[m])
+          for (int l0 = m; l0 <= L; l0 += AT_LC) wk.push_back(make_int2(m, l0));
+      b.nwork = (int)wk.size();
+      NUSHT_TRY(dev_alloc((void**)&b.work, std::max<size_t>(1, wk.size()) * sizeof(int2), &p->bytes));
+      if (!wk.empty())
+        NUSHT_CUDA(cudaMemcpy(b.work, wk.data(), wk.size() * sizeof(int2), cudaMemcpyHostToDevice));
+      const BucketArgs a = bucket_args(b);
+      if (b.nitems > 0) bucket_ptab_k<<<(b.nitems + 3) / 4, 128, 0, s>>>(a, b.items, b.offs, b.nitems, b.P);
+      NUSHT_CUDA(cudaGetLastError());
+    }
+  }
   NUSHT_CUFFT(cufftCreate(&b.theta));
   b.have_theta = true;
   int M = b.M;
@@ -507,20 +783,6 @@ int bucket_build(nusht_batch_t p, Bucket& b, cudaStream_t s) {
   return NUSHT_OK;
 }
 
-BucketArgs bucket_args(const Bucket& b) {
-  BucketArgs a;
-  a.lmax = b.L;
-  a.M = b.M;
-  a.npairs = b.npairs;
-  a.B = b.B;
-  a.c = b.leg->leg.c;
-  a.dshift = b.leg->leg.dshift;
-  a.cm = b.leg->leg.cm;
-  a.ring_x = b.leg->leg.ring_x;
-  a.ring_s = b.leg->leg.ring_s;
-  a.memberL = b.memberL;
-  return a;
-}
 
 int launch_adj(const Bucket& b, cudaStream_t s) {
   const BucketArgs a = bucket_args(b);
@@ -548,6 +810,8 @@ int set_adj_smem() {
   NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_k<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_k<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_k<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  const int smt = (BS_PAIRS * AT_PAD + BS_PAIRS * 2 * BK_COLS) * (int)sizeof(float);
+  NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_tab_k, cudaFuncAttributeMaxDynamicSharedMemorySize, smt));
   return NUSHT_OK;
 }
 
@@ -556,7 +820,10 @@ int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
     const BucketArgs a = bucket_args(b);
     dim3 g((b.L + 1 + 3) / 4, b.L + 1);
     bucket_scale_k<<<g, 256, 0, s>>>(b.L, b.B, b.memberL, b.alm_ptrs, b.leg->leg.ahat, b.atb);
-    if (b.nitems > 0) bucket_synth_k<<<b.nitems, 256, 0, s>>>(a, b.items, b.nitems, b.atb, b.G);
+    if (b.nitems > 0 && b.table)
+      bucket_synth_tab_k<<<b.nitems, 256, 0, s>>>(a, b.items, b.offs, b.nitems, b.P, b.atb, b.G);
+    else if (b.nitems > 0)
+      bucket_synth_k<<<b.nitems, 256, 0, s>>>(a, b.items, b.nitems, b.atb, b.G);
     bucket_poles_k<<<b.B, 256, 0, s>>>(b.L, b.M, b.memberL, b.alm_ptrs, b.leg->leg.pole_norm, b.G);
     NUSHT_CUDA(cudaGetLastError());
     NUSHT_CUFFT(cufftSetStream(b.theta, s));
@@ -585,7 +852,14 @@ int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
     NUSHT_CUFFT(cufftExecC2C(b.theta, (cufftComplex*)b.Ghat, (cufftComplex*)b.Ghat, CUFFT_INVERSE));
     dim3 gf(b.npairs, b.L + 1);
     bucket_fold_k<<<gf, BK_MAXB, 0, s>>>(b.L, b.M, b.npairs, b.B, b.memberL, b.Ghat, b.S);
-    NUSHT_TRY(launch_adj(b, s));
+    if (b.table) {
+      const size_t sm = (size_t)(BS_PAIRS * AT_PAD + BS_PAIRS * 2 * BK_COLS) * sizeof(float);
+      if (b.nwork > 0)
+        bucket_adj_tab_k<<<b.nwork, 256, sm, s>>>(bucket_args(b), b.items, b.offs, b.mfirst, b.work, b.nwork, b.P,
+                                                  b.S, b.cacc);
+    } else {
+      NUSHT_TRY(launch_adj(b, s));
+    }
     dim3 g((b.L + 1 + 3) / 4, b.L + 1);
     bucket_final_k<<<g, 256, 0, s>>>(b.L, b.M, b.B, b.memberL, b.cacc, b.leg->leg.ahat, b.leg->leg.pole_norm,
                                      b.Ghat, b.out_ptrs);

@@ -25,17 +25,20 @@ def env():
     return torch, nu
 
 
-def make_batch(torch, nu, ls, seed=0):
+def make_batch(torch, nu, ls, seed=0, table=0):
     alms = [W.alm_gaussian(l, seed=seed + 10 * i, dtype=np.complex64) for i, l in enumerate(ls)]
     pts = [W.points_uniform(max(1, 2 * l * l), seed=seed + 10 * i + 1) for i, l in enumerate(ls)]
-    bp = nu.BatchPlan(ls, [torch.from_numpy(p).cuda() for p in pts], eps=1e-5)
+    bp = nu.BatchPlan(ls, [torch.from_numpy(p).cuda() for p in pts], eps=1e-5, legendre_table=table)
     return bp, alms, pts
 
 
-def test_batch_small_against_oracle(env):
+@pytest.mark.parametrize("table", [0, -1])
+def test_batch_small_against_oracle(env, table):
+    """Both Legendre paths: the plan-time recurrence table (default) and the
+    recurrence on every call."""
     torch, nu = env
     ls = [0, 3, 16, 40, 63, 100, 130, 7]
-    bp, alms, pts = make_batch(torch, nu, ls)
+    bp, alms, pts = make_batch(torch, nu, ls, table=table)
     info = bp.info()
     assert info["nbuckets"] >= 1 and max(info["bucket_lmax"]) == max(ls)
     outs = bp.synth([torch.from_numpy(a).cuda() for a in alms])
