@@ -195,28 +195,45 @@ __global__ void bucket_poles_k(int L, int M, const int* __restrict__ memberL, co
   }
 }
 
-// adjoint, first step: D^dagger fold into S[m][pair][E|O][slot (re, im)]
-__global__ void bucket_fold_k(int L, int M, int npairs, int B, const int* __restrict__ memberL,
-                              const float2* __restrict__ Gt, float* __restrict__ S) {
-  const int p = blockIdx.x, m = blockIdx.y, slot = threadIdx.x;  // 64 threads
-  const int jn = p + 1, js = M / 2 - jn;
-  float2 se = make_float2(0.f, 0.f), so = make_float2(0.f, 0.f);
-  if (slot < B && m <= memberL[slot]) {
-    const float sg = (m & 1) ? -1.f : 1.f;
-    const float2* row = Gt + ((size_t)slot * (L + 1) + m) * M;
-    const float2 g0 = row[jn], g1 = row[M - jn];
-    const float2 fn = make_float2(g0.x + sg * g1.x, g0.y + sg * g1.y);
-    float2 fs = make_float2(0.f, 0.f);
-    if (js != jn) {
-      const float2 h0 = row[js], h1 = row[M - js];
-      fs = make_float2(h0.x + sg * h1.x, h0.y + sg * h1.y);
+// adjoint, first step: D^dagger fold into S[m][pair][E|O][slot (re, im)].
+// Block = (32 ring pairs, order m); each warp reads one member's spectrum
+// row for the 32 pairs contiguously (4 coalesced runs), the block transposes
+// through shared memory and writes 32 contiguous S rows.
+constexpr int FOLD_PAIRS = 32;
+__global__ void __launch_bounds__(256) bucket_fold_k(int L, int M, int npairs, int B,
+                                                     const int* __restrict__ memberL, const float2* __restrict__ Gt,
+                                                     float* __restrict__ S) {
+  __shared__ float2 sE[FOLD_PAIRS][BK_MAXB + 1], sO[FOLD_PAIRS][BK_MAXB + 1];
+  const int p0 = blockIdx.x * FOLD_PAIRS, m = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = p0 + lane;
+  const float sg = (m & 1) ? -1.f : 1.f;
+  for (int slot = warp; slot < BK_MAXB; slot += 8) {
+    float2 se = make_float2(0.f, 0.f), so = make_float2(0.f, 0.f);
+    if (slot < B && m <= memberL[slot] && p < npairs) {
+      const int jn = p + 1, js = M / 2 - jn;
+      const float2* row = Gt + ((size_t)slot * (L + 1) + m) * M;
+      const float2 g0 = row[jn], g1 = row[M - jn];
+      const float2 fn = make_float2(g0.x + sg * g1.x, g0.y + sg * g1.y);
+      float2 fs = make_float2(0.f, 0.f);
+      if (js != jn) {
+        const float2 h0 = row[js], h1 = row[M - js];
+        fs = make_float2(h0.x + sg * h1.x, h0.y + sg * h1.y);
+      }
+      se = make_float2(fn.x + fs.x, fn.y + fs.y);
+      so = make_float2(fn.x - fs.x, fn.y - fs.y);
     }
-    se = make_float2(fn.x + fs.x, fn.y + fs.y);
-    so = make_float2(fn.x - fs.x, fn.y - fs.y);
+    sE[lane][slot] = se;
+    sO[lane][slot] = so;
   }
-  float2* out = reinterpret_cast<float2*>(S + ((size_t)m * npairs + p) * 2 * BK_COLS);
-  out[slot] = se;
-  out[BK_MAXB + slot] = so;
+  __syncthreads();
+  // 32 rows of 2 x 64 float2
+  for (int e = threadIdx.x; e < FOLD_PAIRS * 2 * BK_MAXB; e += 256) {
+    const int r = e / (2 * BK_MAXB), c = e % (2 * BK_MAXB);
+    if (p0 + r >= npairs) continue;
+    float2* out = reinterpret_cast<float2*>(S + ((size_t)m * npairs + p0 + r) * 2 * BK_COLS);
+    out[c] = c < BK_MAXB ? sE[r][c] : sO[r][c - BK_MAXB];
+  }
 }
 
 // adjoint: block = order m with all its ring pairs; each thread owns NT
@@ -850,8 +867,8 @@ int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
   for (auto& b : p->buckets) {
     NUSHT_CUFFT(cufftSetStream(b.theta, s));
     NUSHT_CUFFT(cufftExecC2C(b.theta, (cufftComplex*)b.Ghat, (cufftComplex*)b.Ghat, CUFFT_INVERSE));
-    dim3 gf(b.npairs, b.L + 1);
-    bucket_fold_k<<<gf, BK_MAXB, 0, s>>>(b.L, b.M, b.npairs, b.B, b.memberL, b.Ghat, b.S);
+    dim3 gf((b.npairs + FOLD_PAIRS - 1) / FOLD_PAIRS, b.L + 1);
+    bucket_fold_k<<<gf, 256, 0, s>>>(b.L, b.M, b.npairs, b.B, b.memberL, b.Ghat, b.S);
     if (b.table) {
       const size_t sm = (size_t)(BS_PAIRS * AT_PAD + BS_PAIRS * 2 * BK_COLS) * sizeof(float);
       if (b.nwork > 0)

@@ -381,6 +381,55 @@ __global__ void __launch_bounds__(32) spread_k(T* __restrict__ grid, int64_t str
   }
 }
 
+// Spreading in float (mixed mode): one thread per point of the subproblem,
+// kernel values evaluated on the fly from the FP32 offsets, w x w native
+// shared-memory float atomics into the bin's tile, one atomic flush.
+__global__ void __launch_bounds__(128) spread_pt_k(float* __restrict__ grid, int64_t stride, int n1, int n2, int w,
+                                                   int nb2, float betaf, const int* __restrict__ sub,
+                                                   const int* __restrict__ cell, const float* __restrict__ offf,
+                                                   const int* __restrict__ perm, const float* __restrict__ f) {
+  extern __shared__ unsigned char smem_raw[];
+  float* tile = reinterpret_cast<float*>(smem_raw);
+  const int tw = BIN + w - 1;
+  const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
+  const int r0 = (bin / nb2) * BIN, c0 = (bin % nb2) * BIN;
+  for (int t = threadIdx.x; t < tw * tw; t += blockDim.x) tile[t] = 0.f;
+  __syncthreads();
+  const float scf = 2.0f / w;
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const int64_t s = (int64_t)start + q;
+    const int lr = cell[2 * s] - r0, lc = cell[2 * s + 1] - c0;
+    const float fv = f[perm[s]];
+    const float o1 = offf[2 * s], o2 = offf[2 * s + 1];
+    float p1[WMAX], p2[WMAX];
+#pragma unroll
+    for (int a = 0; a < WMAX; ++a)
+      if (a < w) {
+        p1[a] = fv * es_psif((o1 - a) * scf, betaf);
+        p2[a] = es_psif((o2 - a) * scf, betaf);
+      }
+#pragma unroll
+    for (int a = 0; a < WMAX; ++a) {
+      if (a < w) {
+        float* trow = tile + (lr + a) * tw + lc;
+#pragma unroll
+        for (int b = 0; b < WMAX; ++b)
+          if (b < w) atomicAdd(trow + b, p1[a] * p2[b]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < tw * tw; t += blockDim.x) {
+    const float v = tile[t];
+    if (v != 0.f) {
+      int r = r0 + t / tw, c = c0 + t % tw;
+      while (r >= n1) r -= n1;
+      while (c >= n2) c -= n2;
+      atomicAdd(grid + (int64_t)r * stride + c, v);
+    }
+  }
+}
+
 }  // namespace
 
 void free_points(nusht_plan_t p) {
@@ -549,9 +598,8 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
                                                  (float)z.beta, p->pts.sub, p->pts.cell, p->pts.psi, nullptr,
                                                  p->pts.perm, (const double*)d_map);
   else
-    spread_k<float><<<p->pts.nsub, 32, sm, s>>>((float*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, (float)z.beta,
-                                                p->pts.sub, p->pts.cell, nullptr, p->pts.off, p->pts.perm,
-                                                (const float*)d_map);
+    spread_pt_k<<<p->pts.nsub, 128, sm, s>>>((float*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, (float)z.beta,
+                                             p->pts.sub, p->pts.cell, p->pts.off, p->pts.perm, (const float*)d_map);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
