@@ -219,6 +219,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-transform batched measurement")
+    ap.add_argument("--no-table", action="store_true", help="skip the recurrence-table (legendre_table=1) runs")
     ap.add_argument("--only-batch", action="store_true", help="run only the 64-transform batched measurement")
     ap.add_argument("--batch-n", type=int, default=64, help="transforms in the batched workload")
     ap.add_argument("--batch-lmax", type=int, default=2047, help="largest lmax of the batched workload")
@@ -246,11 +247,15 @@ def main():
     dpts = torch.from_numpy(pts).cuda()
     results = {}
     y_host = np.random.default_rng(5).standard_normal(npts)
-    for prec in (["fp64"] if args.no_mixed else ["fp64", "mixed"]):
+    runs = [("fp64", 0)] + ([] if args.no_mixed else [("mixed", 0)])
+    if not args.no_table:
+        runs += [("fp64", 1)] + ([] if args.no_mixed else [("mixed", 1)])
+    for prec, table in runs:
+        key = prec if not table else prec + "_table"
         cd = torch.complex128 if prec == "fp64" else torch.complex64
         rd = torch.float64 if prec == "fp64" else torch.float32
         t0 = time.perf_counter()
-        plan = nu.Plan(L, dpts, eps=EPS[prec], precision=prec, profile=True)
+        plan = nu.Plan(L, dpts, eps=EPS[prec], precision=prec, profile=True, legendre_table=table)
         torch.cuda.synchronize()
         t_plan = time.perf_counter() - t0
         ad = torch.from_numpy(a).to(cd).cuda()
@@ -275,9 +280,9 @@ def main():
             f_ref = oracle.synth(a, pts[sel], L)
             f = plan.synth(ad).double().cpu().numpy()
             par = oracle.eps_eff(f_ref, f[sel])
-        results[prec] = {"ms": ms, "plan_s": t_plan, "stages": stages, "clocks": clk.summary(), "eps_eff": par,
-                         "info": plan.info()}
-        if prec == "fp64":
+        results[key] = {"ms": ms, "plan_s": t_plan, "stages": stages, "clocks": clk.summary(), "eps_eff": par,
+                        "info": plan.info()}
+        if key == "fp64":
             # end to end through the public API with host buffers (pinned),
             # copies inside the timed region
             a_pin = torch.from_numpy(a).pin_memory()
@@ -364,6 +369,15 @@ def main():
                          "synth_ms": mx["stages"]["synth"]["total"], "adjoint_ms": mx["stages"]["adjoint"]["total"],
                          "stages_ms": mx["stages"], "w": mx["info"]["w"], "sigma": mx["info"]["sigma"],
                          "dtype": "f64 recurrence / f32 contraction, FFT, NUFFT", "clocks": mx["clocks"]}
+    for key in ("fp64_table", "mixed_table"):
+        if key in results:
+            r = results[key]
+            line[key] = {"ms_per_step": r["ms"], "eps_eff": r["eps_eff"], "plan_s": r["plan_s"],
+                         "synth_ms": r["stages"]["synth"]["total"], "adjoint_ms": r["stages"]["adjoint"]["total"],
+                         "legendre_ms": [r["stages"]["synth"]["legendre"], r["stages"]["adjoint"]["legendre"]],
+                         "plan_GB": r["info"]["bytes_device"] / 1e9,
+                         "what": "opts.legendre_table=1: the FP64 recurrence runs once at plan time and its "
+                                 "values stay in HBM; each call streams them"}
     if batch is not None:
         line["batch64"] = batch
     if cpu is not None:

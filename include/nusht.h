@@ -95,9 +95,12 @@ typedef struct {
   int fp64_contraction; /* FP64 mode only: 1 = Legendre sums with FP64 instructions;
                            0 (default) = FP64 recurrence, sums as float pairs on the FP32
                            pipe (~2^-48 relative per operation; a_lm magnitudes below 1e20) */
-  int legendre_table; /* batched plans: 0 = run the FP64 recurrence once at plan time and keep
-                         its values in device memory when they fit (half the free memory),
-                         -1 = run the recurrence on every call */
+  int legendre_table; /* where the FP64 recurrence runs.  0 = the plan type's default:
+                         every call for nusht_plan, once at plan time for nusht_plan_many;
+                         1 = once at plan time, its values kept in device memory (float per
+                         (ring pair, l, m) in mixed mode, a float pair in FP64 mode: 59 / 118 GB
+                         at lmax 4095), when they fit in half the free memory;
+                         -1 = every call */
   int reserved[5];
 } nusht_opts;
 

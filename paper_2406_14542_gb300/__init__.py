@@ -183,7 +183,7 @@ class Plan:
 
     def __init__(self, lmax: int, pts, eps: float = 1e-10, precision="fp64", mmax: int | None = None,
                  sigma: float = 0.0, kernel_width: int = 0, profile: bool = False, fp64_contraction: bool = False,
-                 stream=None):
+                 legendre_table: int = 0, stream=None):
         import torch
 
         self.lib = load()
@@ -197,7 +197,7 @@ class Plan:
         self.npts = int(pts.shape[0])
         self.device = pts.device
         h = ctypes.c_void_p()
-        o = _opts(sigma, kernel_width, profile, fp64_contraction)
+        o = _opts(sigma, kernel_width, profile, fp64_contraction, legendre_table)
         _check(self.lib.nusht_plan(ctypes.byref(h), self.lmax, self.mmax, self.npts,
                                    ctypes.c_void_p(pts.data_ptr() if self.npts else 0), self.eps, self.precision,
                                    ctypes.byref(o), _stream_ptr(stream)), "nusht_plan")

@@ -639,6 +639,276 @@ __global__ void adj_reduce_df_k(const float4* __restrict__ partial, int bpm, int
   out[i] = make_double2(sx, sy);
 }
 
+// ---------------------------------------------------------------------------
+// Table mode (opts.legendre_table = 1).  The recurrence values at the rings
+// do not depend on the coefficients, so the plan can run the FP64 recurrence
+// once and keep them in HBM: per kept work item, [l - m][4 chains][32 lanes]
+// of q as float (mixed) or as a float pair qh + ql (FP64 mode, ~2^-48).
+// Each call then streams the table through the same contractions as above.
+// ---------------------------------------------------------------------------
+template <bool DF>
+struct TabT;
+template <>
+struct TabT<false> {
+  using v = float;
+};
+template <>
+struct TabT<true> {
+  using v = float2;
+};
+
+template <bool DF>
+__global__ void __launch_bounds__(128) legendre_tab_build_k(LegArgs a, const int64_t* __restrict__ off,
+                                                            typename TabT<DF>::v* __restrict__ tab, int nitems) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  int m, blk;
+  item_of(a, it, m, blk);
+  const int L = a.lmax;
+  const int mb = mbase_of(L, m);
+  Chain ch[LEG_K];
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) chain_init(ch[k], a, m, 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane);
+  typename TabT<DF>::v* out = tab + off[it];
+  for (int l = m; l <= L; ++l) {
+    const bool step = l > m;
+    const double c = step ? __ldg(a.c + mb + l) : 0.0;
+    const bool rs = step && __ldg(a.dshift + mb + l) != 0;
+#pragma unroll
+    for (int k = 0; k < LEG_K; ++k) {
+      if (step) chain_step(ch[k], c, rs);
+      const bool use = ch[k].valid && ch[k].E == 0;
+      typename TabT<DF>::v val;
+      if constexpr (DF) {
+        float qh = 0.f, ql = 0.f;
+        if (use) split_q(ch[k].q1, qh, ql);
+        val = make_float2(qh, ql);
+      } else {
+        val = use ? to_f32(ch[k].q1) : 0.f;
+      }
+      out[(size_t)(l - m) * LEG_PAIRS_PER_WARP + k * 32 + lane] = val;
+    }
+  }
+}
+
+// synthesis from the table; mixed: float2 atilde / float2 sums, FP64 mode:
+// float4 double-float atilde and sums
+template <bool DF>
+__global__ void __launch_bounds__(128) legendre_synth_tab_k(LegArgs a, const int64_t* __restrict__ off,
+                                                            const typename TabT<DF>::v* __restrict__ tab,
+                                                            const void* __restrict__ atv, void* __restrict__ Gv,
+                                                            int nitems) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  int m, blk;
+  item_of(a, it, m, blk);
+  const int L = a.lmax;
+  const int mb = mbase_of(L, m);
+  const typename TabT<DF>::v* tp = tab + off[it];
+  float4 accE[LEG_K], accO[LEG_K];  // DF: (hi_re, lo_re, hi_im, lo_im); mixed: (re, im, -, -)
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) accE[k] = accO[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // one degree into the sums of its parity (static: the loop runs in pairs)
+  auto deg = [&](int l, float4* acc) {
+    const typename TabT<DF>::v* row = tp + (size_t)(l - m) * LEG_PAIRS_PER_WARP + lane;
+    if constexpr (DF) {
+      const float4 av = reinterpret_cast<const float4*>(atv)[mb + l];
+#pragma unroll
+      for (int k = 0; k < LEG_K; ++k) {
+        const float2 q = row[k * 32];
+        df_mac(acc[k].x, acc[k].y, av.x, av.y, q.x, q.y);
+        df_mac(acc[k].z, acc[k].w, av.z, av.w, q.x, q.y);
+      }
+    } else {
+      const float2 av = reinterpret_cast<const float2*>(atv)[mb + l];
+#pragma unroll
+      for (int k = 0; k < LEG_K; ++k) {
+        const float q = row[k * 32];
+        acc[k].x = fmaf(av.x, q, acc[k].x);
+        acc[k].y = fmaf(av.y, q, acc[k].y);
+      }
+    }
+  };
+  int l = m;
+  for (; l + 1 <= L; l += 2) {
+    deg(l, accE);
+    deg(l + 1, accO);
+  }
+  if (l <= L) deg(l, accE);
+  const int M = a.M;
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) {
+    const int jn = 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane;
+    if (jn > a.npairs) continue;
+    const int js = M / 2 - jn;
+    double er, ei, orr, oi;
+    if constexpr (DF) {
+      er = df_value(accE[k].x, accE[k].y);
+      ei = df_value(accE[k].z, accE[k].w);
+      orr = df_value(accO[k].x, accO[k].y);
+      oi = df_value(accO[k].z, accO[k].w);
+    } else {
+      er = accE[k].x;
+      ei = accE[k].y;
+      orr = accO[k].x;
+      oi = accO[k].y;
+    }
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    if constexpr (DF) {
+      double2* row = reinterpret_cast<double2*>(Gv) + (size_t)m * M;
+      row[jn] = make_double2(er + orr, ei + oi);
+      row[M - jn] = make_double2(sg * (er + orr), sg * (ei + oi));
+      if (js != jn) {
+        row[js] = make_double2(er - orr, ei - oi);
+        row[M - js] = make_double2(sg * (er - orr), sg * (ei - oi));
+      }
+    } else {
+      float2* row = reinterpret_cast<float2*>(Gv) + (size_t)m * M;
+      row[jn] = make_float2((float)(er + orr), (float)(ei + oi));
+      row[M - jn] = make_float2((float)(sg * (er + orr)), (float)(sg * (ei + oi)));
+      if (js != jn) {
+        row[js] = make_float2((float)(er - orr), (float)(ei - oi));
+        row[M - js] = make_float2((float)(sg * (er - orr)), (float)(sg * (ei - oi)));
+      }
+    }
+  }
+}
+
+// adjoint from the table (same reduce-scatter as legendre_adj_k)
+template <bool DF>
+__global__ void __launch_bounds__(128) legendre_adj_tab_k(LegArgs a, const int64_t* __restrict__ off,
+                                                          const typename TabT<DF>::v* __restrict__ tab,
+                                                          const void* __restrict__ Gtv, void* __restrict__ partv,
+                                                          int nitems, int64_t nalm) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  int m, blk;
+  item_of(a, it, m, blk);
+  const int L = a.lmax;
+  const int M = a.M;
+  const int mb = mbase_of(L, m);
+  const typename TabT<DF>::v* tp = tab + off[it];
+  float4 SE[LEG_K], SO[LEG_K];  // DF: double-float pairs; mixed: (re, im, -, -)
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) {
+    const int jn = 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane;
+    double2 fn = make_double2(0.0, 0.0), fs = make_double2(0.0, 0.0);
+    if (jn <= a.npairs) {
+      const int js = M / 2 - jn;
+      const double sg = (m & 1) ? -1.0 : 1.0;
+      if constexpr (DF) {
+        const double2* row = reinterpret_cast<const double2*>(Gtv) + (size_t)m * M;
+        const double2 g0 = row[jn], g1 = row[M - jn];
+        fn = make_double2(g0.x + sg * g1.x, g0.y + sg * g1.y);
+        if (js != jn) {
+          const double2 h0 = row[js], h1 = row[M - js];
+          fs = make_double2(h0.x + sg * h1.x, h0.y + sg * h1.y);
+        }
+      } else {
+        const float2* row = reinterpret_cast<const float2*>(Gtv) + (size_t)m * M;
+        const float2 g0 = row[jn], g1 = row[M - jn];
+        fn = make_double2(g0.x + sg * g1.x, g0.y + sg * g1.y);
+        if (js != jn) {
+          const float2 h0 = row[js], h1 = row[M - js];
+          fs = make_double2(h0.x + sg * h1.x, h0.y + sg * h1.y);
+        }
+      }
+    }
+    if constexpr (DF) {
+      df_of(fn.x + fs.x, SE[k].x, SE[k].y);
+      df_of(fn.y + fs.y, SE[k].z, SE[k].w);
+      df_of(fn.x - fs.x, SO[k].x, SO[k].y);
+      df_of(fn.y - fs.y, SO[k].z, SO[k].w);
+    } else {
+      SE[k] = make_float4((float)(fn.x + fs.x), (float)(fn.y + fs.y), 0.f, 0.f);
+      SO[k] = make_float4((float)(fn.x - fs.x), (float)(fn.y - fs.y), 0.f, 0.f);
+    }
+  }
+  for (int base = m; base <= L; base += 8) {
+    float4 v[8];
+#pragma unroll
+    for (int st = 0; st < 8; ++st) {
+      v[st] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int l = base + st;
+      if (l <= L) {
+        const typename TabT<DF>::v* row = tp + (size_t)(l - m) * LEG_PAIRS_PER_WARP + lane;
+#pragma unroll
+        for (int k = 0; k < LEG_K; ++k) {
+          const float4 S = (st & 1) ? SO[k] : SE[k];
+          if constexpr (DF) {
+            const float2 q = row[k * 32];
+            df_mac(v[st].x, v[st].y, S.x, S.y, q.x, q.y);
+            df_mac(v[st].z, v[st].w, S.z, S.w, q.x, q.y);
+          } else {
+            const float q = row[k * 32];
+            v[st].x = fmaf(q, S.x, v[st].x);
+            v[st].y = fmaf(q, S.y, v[st].y);
+          }
+        }
+      }
+    }
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    float4 w4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 send = u16 ? v[i] : v[i + 4];
+      w4[i] = u16 ? v[i + 4] : v[i];
+      const float4 r = shfl4(send, 16);
+      if constexpr (DF) {
+        df4_add(w4[i], r);
+      } else {
+        w4[i].x += r.x;
+        w4[i].y += r.y;
+      }
+    }
+    float4 w2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float4 send = u8 ? w4[i] : w4[i + 2];
+      w2[i] = u8 ? w4[i + 2] : w4[i];
+      const float4 r = shfl4(send, 8);
+      if constexpr (DF) {
+        df4_add(w2[i], r);
+      } else {
+        w2[i].x += r.x;
+        w2[i].y += r.y;
+      }
+    }
+    float4 z;
+    {
+      const float4 send = u4 ? w2[0] : w2[1];
+      z = u4 ? w2[1] : w2[0];
+      const float4 r = shfl4(send, 4);
+      if constexpr (DF) {
+        df4_add(z, r);
+      } else {
+        z.x += r.x;
+        z.y += r.y;
+      }
+    }
+#pragma unroll
+    for (int msk = 2; msk >= 1; msk >>= 1) {
+      const float4 r = shfl4(z, msk);
+      if constexpr (DF) {
+        df4_add(z, r);
+      } else {
+        z.x += r.x;
+        z.y += r.y;
+      }
+    }
+    const int l = base + ((lane >> 2) & 7);
+    if ((lane & 3) == 0 && l <= L) {
+      if constexpr (DF)
+        reinterpret_cast<float4*>(partv)[(size_t)blk * nalm + mb + l] = z;
+      else
+        reinterpret_cast<float2*>(partv)[(size_t)blk * nalm + mb + l] = make_float2(z.x, z.y);
+    }
+  }
+}
+
 // Plan-time probe: does any ring of the item leave the scaled phase by lmax?
 __global__ void __launch_bounds__(128) legendre_probe_k(LegArgs a, int ntotal, int* __restrict__ flags) {
   const int lane = threadIdx.x & 31;
@@ -824,6 +1094,31 @@ int legendre_build_tables(nusht_plan_t p, cudaStream_t s) {
   NUSHT_TRY(dev_alloc((void**)&t.items, std::max<size_t>(1, items.size()) * 4, &p->bytes));
   if (!items.empty())
     NUSHT_CUDA(cudaMemcpyAsync(t.items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s));
+  // the work list is on the device now; the table kernel reads it
+  // recurrence table (opts.legendre_table = 1) when it fits in half the free memory
+  if (p->opts.legendre_table > 0 && t.nitems > 0) {
+    const bool df = p->precision == NUSHT_FP64;
+    const size_t es = df ? sizeof(float2) : sizeof(float);
+    std::vector<int64_t> off(items.size() + 1, 0);
+    for (size_t k = 0; k < items.size(); ++k)
+      off[k + 1] = off[k] + (int64_t)(L - (items[k] >> 16) + 1) * LEG_PAIRS_PER_WARP;
+    const size_t need = (size_t)off.back() * es;
+    size_t freeb = 0, totalb = 0;
+    cudaMemGetInfo(&freeb, &totalb);
+    if (need < freeb / 2) {
+      NUSHT_TRY(dev_alloc(&t.tab, need, &p->bytes));
+      NUSHT_TRY(dev_alloc((void**)&t.tab_off, off.size() * 8, &p->bytes));
+      NUSHT_CUDA(cudaMemcpyAsync(t.tab_off, off.data(), off.size() * 8, cudaMemcpyHostToDevice, s));
+      LegArgs ta = make_args(p);
+      if (df)
+        legendre_tab_build_k<true><<<(t.nitems + 3) / 4, 128, 0, s>>>(ta, t.tab_off, (float2*)t.tab, t.nitems);
+      else
+        legendre_tab_build_k<false><<<(t.nitems + 3) / 4, 128, 0, s>>>(ta, t.tab_off, (float*)t.tab, t.nitems);
+      NUSHT_CUDA(cudaGetLastError());
+      t.tab_bytes = need;
+    }
+  }
+
   NUSHT_CUDA(cudaStreamSynchronize(s));
   return NUSHT_OK;
 }
@@ -834,7 +1129,24 @@ int legendre_synth(nusht_plan_t p, const void* d_alm, cudaStream_t s) {
   const int nb = (int)((nalm + tb - 1) / tb);
   LegArgs a = make_args(p);
   const int nitems = p->leg.nitems;
-  if (p->precision == NUSHT_FP64 && !p->opts.fp64_contraction) {
+  if (p->leg.tab) {
+    if (p->precision == NUSHT_FP64) {
+      scale_alm_df_k<<<nb, tb, 0, s>>>((const double*)d_alm, p->leg.ahat, nalm, p->lmax, (float4*)p->atilde);
+      if (nitems > 0)
+        legendre_synth_tab_k<true><<<(nitems + 3) / 4, 128, 0, s>>>(a, p->leg.tab_off, (const float2*)p->leg.tab,
+                                                                     p->atilde, p->G, nitems);
+      poles_synth_k<double, double><<<1, 256, 0, s>>>((const double*)d_alm, p->leg.pole_norm, p->lmax, p->sz.M,
+                                                      (double2*)p->G);
+    } else {
+      scale_alm_k<float, float><<<nb, tb, 0, s>>>((const float*)d_alm, p->leg.ahat, nalm, p->lmax,
+                                                  (float2*)p->atilde);
+      if (nitems > 0)
+        legendre_synth_tab_k<false><<<(nitems + 3) / 4, 128, 0, s>>>(a, p->leg.tab_off, (const float*)p->leg.tab,
+                                                                      p->atilde, p->G, nitems);
+      poles_synth_k<float, float><<<1, 256, 0, s>>>((const float*)d_alm, p->leg.pole_norm, p->lmax, p->sz.M,
+                                                    (float2*)p->G);
+    }
+  } else if (p->precision == NUSHT_FP64 && !p->opts.fp64_contraction) {
     scale_alm_df_k<<<nb, tb, 0, s>>>((const double*)d_alm, p->leg.ahat, nalm, p->lmax, (float4*)p->atilde);
     if (nitems > 0)
       legendre_synth_df_k<<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float4*)p->atilde, (double2*)p->G, nitems);
@@ -864,7 +1176,22 @@ int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
   const int nitems = p->leg.nitems;
   const int tb = 256;
   const int nb = (int)((nalm + tb - 1) / tb);
-  if (p->precision == NUSHT_FP64 && !p->opts.fp64_contraction) {
+  if (p->leg.tab) {
+    if (p->precision == NUSHT_FP64) {
+      if (nitems > 0)
+        legendre_adj_tab_k<true><<<(nitems + 3) / 4, 128, 0, s>>>(a, p->leg.tab_off, (const float2*)p->leg.tab,
+                                                                   p->Ghat, p->partial, nitems, nalm);
+      adj_reduce_df_k<<<nb, tb, 0, s>>>((const float4*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
+                                        p->leg.pole_norm, (const double2*)p->Ghat, p->lmax, p->sz.M, (double2*)d_alm);
+    } else {
+      if (nitems > 0)
+        legendre_adj_tab_k<false><<<(nitems + 3) / 4, 128, 0, s>>>(a, p->leg.tab_off, (const float*)p->leg.tab,
+                                                                    p->Ghat, p->partial, nitems, nalm);
+      adj_reduce_k<float><<<nb, tb, 0, s>>>((const float2*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
+                                            p->leg.pole_norm, (const float2*)p->Ghat, p->lmax, p->sz.M,
+                                            (float2*)d_alm);
+    }
+  } else if (p->precision == NUSHT_FP64 && !p->opts.fp64_contraction) {
     if (nitems > 0)
       legendre_adj_df_k<<<(nitems + 3) / 4, 128, 0, s>>>(a, (const double2*)p->Ghat, (float4*)p->partial, nitems,
                                                          nalm);

@@ -72,6 +72,9 @@ struct LegTables {
   int nitems = 0;
   int nitems_total = 0;
   int64_t triples = 0;        // (ring pair, l, m) triples of the kept items
+  void* tab = nullptr;        // recurrence table (table mode): float or float2 per triple
+  int64_t* tab_off = nullptr; // per-item offsets into tab
+  size_t tab_bytes = 0;
   int blocks_per_m = 0;       // ring blocks per order
   int npairs = 0;             // M/4
 };

@@ -209,6 +209,8 @@ static void plan_free(nusht_plan_t p) {
   dev_free(p->leg.ring_s);
   dev_free(p->leg.pole_norm);
   dev_free(p->leg.items);
+  dev_free(p->leg.tab);
+  dev_free(p->leg.tab_off);
   dev_free(p->deconv1);
   dev_free(p->deconv2);
   dev_free(p->atilde);

@@ -193,3 +193,32 @@ def test_gl1023_dot_product_full(env):
     lhs = float(np.dot(y, f))
     rhs = oracle.alm_dot(c, a, L)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_legendre_table_mode(env, prec):
+    """Recurrence once at plan time (table mode): same parity, synthesis and
+    adjoint, and the same results as the per-call recurrence to rounding."""
+    torch, nu = env
+    L, a, pts = W.workload("uniform63")
+    cd = torch.complex128 if prec == "fp64" else torch.complex64
+    rd = torch.float64 if prec == "fp64" else torch.float32
+    dp = dev(torch, pts)
+    pt = nu.Plan(L, dp, eps=TOL[prec], precision=prec, legendre_table=1)
+    pr = nu.Plan(L, dp, eps=TOL[prec], precision=prec)
+    ad = dev(torch, a, cd)
+    f = pt.synth(ad).double().cpu().numpy()
+    assert oracle.eps_eff(oracle.synth(a, pts, L), f) <= TOL[prec]
+    assert oracle.eps_eff(pr.synth(ad).double().cpu().numpy(), f) <= (1e-13 if prec == "fp64" else 1e-6)
+    y = np.random.default_rng(3).standard_normal(pts.shape[0])
+    c = pt.adjoint(dev(torch, y, rd)).cpu().numpy().astype(np.complex128)
+    assert oracle.eps_eff(oracle.adjoint(y, pts, L), c) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_legendre_table_mode_gl1023(env, prec):
+    torch, nu = env
+    L, a, pts = W.workload("gl1023")
+    _, f = run_synth(torch, nu, L, a, pts, prec, legendre_table=1)
+    sel = W.subset(pts.shape[0], 5000)
+    assert oracle.eps_eff(oracle.synth(a, pts[sel], L), f[sel]) <= TOL[prec]
