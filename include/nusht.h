@@ -91,7 +91,9 @@ typedef struct {
   int profile;       /* 1 = record per-stage CUDA-event times (nusht_stage_times) */
   int deterministic; /* reserved; synthesis is bit-reproducible, the adjoint's spreading
                         flush adds tile halos with atomics (rounding-level order effects) */
-  int tune;          /* reserved (0) */
+  int tune;          /* spreading/interpolation bin size: 0 = 32 cells; 1 = search (time
+                        16/32/64 on the plan's own points at plan time, cache the winner);
+                        2 = the cached choice for this device/size when present */
   int fp64_contraction; /* FP64 mode only: 1 = Legendre sums with FP64 instructions;
                            0 (default) = FP64 recurrence, sums as float pairs on the FP32
                            pipe (~2^-48 relative per operation; a_lm magnitudes below 1e20) */
@@ -263,6 +265,10 @@ NUSHT_API int nusht_destroy(nusht_plan_t p);
 
 /* nusht_info -- sizes of an existing plan. */
 NUSHT_API int nusht_info(nusht_plan_t p, nusht_sizes* out);
+
+/* nusht_plan_bin -- spreading/interpolation bin edge (fine-grid cells) the plan
+ * uses: 32, or the autotuner's choice (opts.tune). */
+NUSHT_API int nusht_plan_bin(nusht_plan_t p, int* bin);
 
 /*
  * nusht_plan_sizes -- the sizes nusht_plan would choose, computed on the host

@@ -26,7 +26,8 @@ FP64, MIXED = 0, 1
 EXPORTS = ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_synth_grad", "nusht_destroy",
            "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_good_size", "nusht_stage_times",
            "nusht_strerror", "nusht_last_error", "nusht_version", "nusht_adjoint_direct_noalloc",
-           "nusht_plan_many", "nusht_synth_many", "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info")
+           "nusht_plan_many", "nusht_synth_many", "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info",
+           "nusht_plan_bin")
 
 
 class NushtError(RuntimeError):
@@ -88,6 +89,7 @@ def load(path: str | None = None):
         lib.nusht_synth_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         lib.nusht_adjoint_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         lib.nusht_destroy_many.argtypes = [vp]
+        lib.nusht_plan_bin.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         lib.nusht_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64)]
         lib.nusht_strerror.argtypes = [ctypes.c_int]
@@ -97,7 +99,7 @@ def load(path: str | None = None):
         for name in ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_synth_grad",
                      "nusht_destroy", "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_stage_times",
                      "nusht_adjoint_direct_noalloc", "nusht_plan_many", "nusht_synth_many",
-                     "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info"):
+                     "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info", "nusht_plan_bin"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -115,8 +117,9 @@ def _check(code: int, where: str):
         raise NushtError(code, where, load().nusht_last_error().decode())
 
 
-def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False, legendre_table=0) -> Opts:
+def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False, legendre_table=0, tune=0) -> Opts:
     o = Opts()
+    o.tune = int(tune)
     o.legendre_table = int(legendre_table)
     o.sigma = float(sigma)
     o.kernel_width = int(kernel_width)
@@ -183,7 +186,7 @@ class Plan:
 
     def __init__(self, lmax: int, pts, eps: float = 1e-10, precision="fp64", mmax: int | None = None,
                  sigma: float = 0.0, kernel_width: int = 0, profile: bool = False, fp64_contraction: bool = False,
-                 legendre_table: int = 0, stream=None):
+                 legendre_table: int = 0, tune: int = 0, stream=None):
         import torch
 
         self.lib = load()
@@ -197,7 +200,7 @@ class Plan:
         self.npts = int(pts.shape[0])
         self.device = pts.device
         h = ctypes.c_void_p()
-        o = _opts(sigma, kernel_width, profile, fp64_contraction, legendre_table)
+        o = _opts(sigma, kernel_width, profile, fp64_contraction, legendre_table, tune)
         _check(self.lib.nusht_plan(ctypes.byref(h), self.lmax, self.mmax, self.npts,
                                    ctypes.c_void_p(pts.data_ptr() if self.npts else 0), self.eps, self.precision,
                                    ctypes.byref(o), _stream_ptr(stream)), "nusht_plan")
@@ -221,6 +224,12 @@ class Plan:
     @property
     def nalm(self) -> int:
         return nalm(self.lmax, self.mmax)
+
+    def bin_size(self) -> int:
+        """Spreading/interpolation bin edge the plan uses (autotuned when tune=1/2)."""
+        v = ctypes.c_int()
+        _check(self.lib.nusht_plan_bin(self.handle, ctypes.byref(v)), "nusht_plan_bin")
+        return v.value
 
     def info(self) -> dict:
         z = Sizes()
@@ -318,7 +327,7 @@ class BatchPlan:
     float64 (N_b, 2) tensor; each lmax <= 4095."""
 
     def __init__(self, lmaxs, pts_list, eps: float = 1e-5, sigma: float = 0.0, legendre_table: int = 0,
-                 stream=None):
+                 tune: int = 0, stream=None):
         import torch
 
         self.lib = load()
@@ -332,7 +341,7 @@ class BatchPlan:
         larr = (ctypes.c_int * n)(*self.lmaxs)
         narr = (ctypes.c_int64 * n)(*self.npts)
         parr = (ctypes.c_void_p * n)(*[p.data_ptr() if p.numel() else 0 for p in self.pts])
-        o = _opts(sigma, legendre_table=legendre_table)
+        o = _opts(sigma, legendre_table=legendre_table, tune=tune)
         h = ctypes.c_void_p()
         _check(self.lib.nusht_plan_many(ctypes.byref(h), n, larr, narr, parr, float(eps), MIXED, ctypes.byref(o),
                                         _stream_ptr(stream)), "nusht_plan_many")

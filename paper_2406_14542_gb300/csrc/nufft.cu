@@ -2,7 +2,8 @@
 // Sec. 3) on the doubled torus, with the exponential-of-semicircle kernel
 // psi(z) = exp(beta (sqrt(1 - z^2) - 1)), |z| <= 1, of width w fine-grid cells:
 //   * point set-up: fold (theta, phi) onto [0, 2 pi)^2, first tap and
-//     fractional offset in double, bin sort (tiles of BIN x BIN cells),
+//     fractional offset in double, bin sort (tiles of bin x bin cells, bin chosen
+//     by the plan: 32 by default, or by the autotuner),
 //     FP64 kernel values per point;
 //   * deconv_pad / deconv_trunc: divide by the kernel's Fourier transform,
 //     zero-pad / truncate between the theta spectrum [m][k] and the fine
@@ -25,7 +26,6 @@ namespace nusht {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int BIN = 32;       // bin edge in fine-grid cells
 constexpr int SUBMAX = 256;   // points per spreading subproblem
 constexpr int WMAX = 16;
 
@@ -77,7 +77,7 @@ __device__ __forceinline__ void tap(double x, int n, int w, int& i0w, double& of
   i0w = i;
 }
 
-__global__ void prep_k(const double* __restrict__ pts, int64_t npts, int n1, int n2, int w, int nb2,
+__global__ void prep_k(const double* __restrict__ pts, int64_t npts, int n1, int n2, int w, int nb2, int binsz,
                        int* __restrict__ binid) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npts) return;
@@ -85,7 +85,7 @@ __global__ void prep_k(const double* __restrict__ pts, int64_t npts, int n1, int
   double o1, o2;
   tap(pts[2 * i], n1, w, i1, o1);
   tap(pts[2 * i + 1], n2, w, i2, o2);
-  binid[i] = (i1 / BIN) * nb2 + (i2 / BIN);
+  binid[i] = (i1 / binsz) * nb2 + (i2 / binsz);
 }
 
 // sorted point s <- caller's point perm[s]: first taps, and kernel values
@@ -319,15 +319,16 @@ __global__ void __launch_bounds__(128) interp_k(const T* __restrict__ grid, int6
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(32) spread_k(T* __restrict__ grid, int64_t stride, int n1, int n2, int w, int nb2,
-                                               float betaf, const int* __restrict__ sub, const int* __restrict__ cell,
+                                               int binsz, float betaf, const int* __restrict__ sub,
+                                               const int* __restrict__ cell,
                                                const double* __restrict__ psi, const float* __restrict__ offf,
                                                const int* __restrict__ perm, const T* __restrict__ f) {
   extern __shared__ unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
   const int lane = threadIdx.x;
-  const int tw = BIN + w - 1;
+  const int tw = binsz + w - 1;
   const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
-  const int r0 = (bin / nb2) * BIN, c0 = (bin % nb2) * BIN;
+  const int r0 = (bin / nb2) * binsz, c0 = (bin % nb2) * binsz;
   for (int t = lane; t < tw * tw; t += 32) tile[t] = (T)0;
   __syncwarp();
   // this lane's cells of a point: (a, b) for idx = lane + 32 t < w^2
@@ -385,14 +386,14 @@ __global__ void __launch_bounds__(32) spread_k(T* __restrict__ grid, int64_t str
 // kernel values evaluated on the fly from the FP32 offsets, w x w native
 // shared-memory float atomics into the bin's tile, one atomic flush.
 __global__ void __launch_bounds__(128) spread_pt_k(float* __restrict__ grid, int64_t stride, int n1, int n2, int w,
-                                                   int nb2, float betaf, const int* __restrict__ sub,
+                                                   int nb2, int binsz, float betaf, const int* __restrict__ sub,
                                                    const int* __restrict__ cell, const float* __restrict__ offf,
                                                    const int* __restrict__ perm, const float* __restrict__ f) {
   extern __shared__ unsigned char smem_raw[];
   float* tile = reinterpret_cast<float*>(smem_raw);
-  const int tw = BIN + w - 1;
+  const int tw = binsz + w - 1;
   const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
-  const int r0 = (bin / nb2) * BIN, c0 = (bin % nb2) * BIN;
+  const int r0 = (bin / nb2) * binsz, c0 = (bin % nb2) * binsz;
   for (int t = threadIdx.x; t < tw * tw; t += blockDim.x) tile[t] = 0.f;
   __syncthreads();
   const float scf = 2.0f / w;
@@ -432,6 +433,15 @@ __global__ void __launch_bounds__(128) spread_pt_k(float* __restrict__ grid, int
 
 }  // namespace
 
+int spread_smem_optin() {
+  // bins of up to 64 cells with w <= 16: (64 + 15)^2 x 8 B = 49.9 KB of tile
+  const int mx = 80 * 80 * 8;
+  NUSHT_CUDA(cudaFuncSetAttribute(spread_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  NUSHT_CUDA(cudaFuncSetAttribute(spread_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  NUSHT_CUDA(cudaFuncSetAttribute(spread_pt_k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  return NUSHT_OK;
+}
+
 void free_points(nusht_plan_t p) {
   PointData& d = p->pts;
   dev_free(d.perm);
@@ -446,7 +456,8 @@ void free_points(nusht_plan_t p) {
 int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   PointData& d = p->pts;
-  const int nb1 = (z.n1 + BIN - 1) / BIN, nb2 = (z.n2 + BIN - 1) / BIN;
+  const int binsz = d.bin > 0 ? d.bin : 32;
+  const int nb1 = (z.n1 + binsz - 1) / binsz, nb2 = (z.n2 + binsz - 1) / binsz;
   const bool dbl = p->precision == NUSHT_FP64;
   if (npts > d.cap) {
     size_t before = p->bytes;
@@ -485,7 +496,7 @@ int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t 
   NUSHT_TRY(dev_alloc((void**)&dbin, (size_t)npts * 4, nullptr));
   const int tb = 256;
   const int nblk = (int)((npts + tb - 1) / tb);
-  prep_k<<<nblk, tb, 0, s>>>(d_pts, npts, z.n1, z.n2, z.w, nb2, dbin);
+  prep_k<<<nblk, tb, 0, s>>>(d_pts, npts, z.n1, z.n2, z.w, nb2, binsz, dbin);
   std::vector<int> bins(npts);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(bins.data(), dbin, (size_t)npts * 4, cudaMemcpyDeviceToHost, s);
@@ -591,14 +602,16 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
   const size_t es = p->precision == NUSHT_FP64 ? 8 : 4;
   NUSHT_CUDA(cudaMemsetAsync(p->fine, 0, (size_t)z.n1 * stride * es, s));
   if (p->pts.nsub == 0) return NUSHT_OK;
-  const int tw = BIN + z.w - 1;
+  const int binsz = p->pts.bin > 0 ? p->pts.bin : 32;
+  const int tw = binsz + z.w - 1;
   const size_t sm = (size_t)tw * tw * es;
   if (p->precision == NUSHT_FP64)
-    spread_k<double><<<p->pts.nsub, 32, sm, s>>>((double*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2,
+    spread_k<double><<<p->pts.nsub, 32, sm, s>>>((double*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz,
                                                  (float)z.beta, p->pts.sub, p->pts.cell, p->pts.psi, nullptr,
                                                  p->pts.perm, (const double*)d_map);
   else
-    spread_pt_k<<<p->pts.nsub, 128, sm, s>>>((float*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, (float)z.beta,
+    spread_pt_k<<<p->pts.nsub, 128, sm, s>>>((float*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz,
+                                             (float)z.beta,
                                              p->pts.sub, p->pts.cell, p->pts.off, p->pts.perm, (const float*)d_map);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;

@@ -91,6 +91,7 @@ struct PointData {
   int* sub = nullptr;
   int nsub = 0;
   int nbins1 = 0, nbins2 = 0;
+  int bin = 32;               // bin edge in fine-grid cells (spreading tile = bin + w - 1)
   size_t bytes = 0;           // device bytes held for points (part of the plan's total)
 };
 
@@ -173,5 +174,9 @@ int deconv_trunc(nusht_plan_t p, cudaStream_t s);
 int interp(nusht_plan_t p, void* d_map, cudaStream_t s);
 int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, cudaStream_t s);
 int spread(nusht_plan_t p, const void* d_map, cudaStream_t s);
+int spread_smem_optin();
+
+// autotuner (tune.cu)
+int tune_points(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s);
 
 }  // namespace nusht

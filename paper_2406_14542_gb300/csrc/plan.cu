@@ -310,7 +310,8 @@ static int plan_body(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStre
     NUSHT_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)p->leg.blocks_per_m * p->nalm * cplx, s));
   }
   NUSHT_TRY(make_ffts(p));
-  NUSHT_TRY(setpts_impl(p, npts, d_pts, s));
+  NUSHT_TRY(spread_smem_optin());
+  NUSHT_TRY(tune_points(p, npts, d_pts, s));
   NUSHT_CUDA(cudaStreamSynchronize(s));
   p->sz.nitems = p->leg.nitems;
   p->sz.nitems_total = p->leg.nitems_total;
@@ -498,6 +499,12 @@ int nusht_info(nusht_plan_t p, nusht_sizes* out) {
   if (!p || !out) return set_error(NUSHT_EINVAL, "null argument");
   *out = p->sz;
   out->bytes_device = (int64_t)p->bytes;
+  return NUSHT_OK;
+}
+
+int nusht_plan_bin(nusht_plan_t p, int* bin) {
+  if (!p || !bin) return set_error(NUSHT_EINVAL, "null argument");
+  *bin = p->pts.bin;
   return NUSHT_OK;
 }
 

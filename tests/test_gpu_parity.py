@@ -222,3 +222,23 @@ def test_legendre_table_mode_gl1023(env, prec):
     _, f = run_synth(torch, nu, L, a, pts, prec, legendre_table=1)
     sel = W.subset(pts.shape[0], 5000)
     assert oracle.eps_eff(oracle.synth(a, pts[sel], L), f[sel]) <= TOL[prec]
+
+
+def test_autotuned_bin_size(env, tmp_path, monkeypatch):
+    """tune=1 times bin sizes on the plan's own points and caches the winner;
+    tune=2 reuses it; parity holds whichever bin is chosen."""
+    torch, nu = env
+    monkeypatch.setenv("NUSHT_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    L, a, pts = W.workload("uniform63")
+    dp = dev(torch, pts)
+    p1 = nu.Plan(L, dp, eps=1e-10, tune=1)
+    b = p1.bin_size()
+    assert b in (16, 32, 64)
+    assert (tmp_path / "tune.txt").read_text().strip().endswith(" %d" % b)
+    f = p1.synth(dev(torch, a)).cpu().numpy()
+    assert oracle.eps_eff(oracle.synth(a, pts, L), f) <= 1e-10
+    y = np.random.default_rng(4).standard_normal(pts.shape[0])
+    c = p1.adjoint(dev(torch, y)).cpu().numpy()
+    assert oracle.eps_eff(oracle.adjoint(y, pts, L), c) <= 1e-10
+    p2 = nu.Plan(L, dp, eps=1e-10, tune=2)
+    assert p2.bin_size() == b
