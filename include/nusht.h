@@ -103,7 +103,11 @@ typedef struct {
                          (ring pair, l, m) in mixed mode, a float pair in FP64 mode: 59 / 118 GB
                          at lmax 4095), when they fit in half the free memory;
                          -1 = every call */
-  int reserved[5];
+  int tensor_cores;   /* batched plans whose recurrence table fits: 0 (default) = the
+                         contraction on the tensor cores (tcgen05.mma, TF32 operands split
+                         into hi + lo, three products per term, FP32 accumulation;
+                         ~2^-21 relative per product); -1 = FP32 FMA on the CUDA cores */
+  int reserved[4];
 } nusht_opts;
 
 /* Sizes a plan uses; filled by nusht_plan_sizes (no GPU needed) and nusht_info. */
@@ -217,8 +221,9 @@ NUSHT_API int nusht_adjoint_direct_noalloc(int lmax, int mmax, int64_t npts, con
  * grouped into buckets of up to 64 that share one Clenshaw-Curtis ring set,
  * so one FP64 recurrence per (ring pair, l, m) serves every member of a
  * bucket (Sec. 3: the recurrence is the O(lmax^3) part); the contraction
- * over l (synthesis) or rings (adjoint) runs for all members at once in
- * FP32.  The grouping minimises a cost model of recurrence and contraction
+ * over l (synthesis) or rings (adjoint) runs for all members at once, on the
+ * tensor cores (Sec. 4's mixed-precision split: TF32 hi/lo operands, FP32
+ * accumulation) or in FP32 on the CUDA cores (opts.tensor_cores).  The grouping minimises a cost model of recurrence and contraction
  * work.  Each direction's whole stage sequence is captured once into a CUDA
  * graph and replayed; it is re-captured when the buffer pointers change.
  * ------------------------------------------------------------------------ */
@@ -259,6 +264,23 @@ NUSHT_API int nusht_destroy_many(nusht_batch_t p);
  */
 NUSHT_API int nusht_batch_info(nusht_batch_t p, int* nbuckets, int* bucket_of, int* bucket_lmax,
                                int64_t* bytes_device);
+
+/*
+ * nusht_batch_status -- synchronises `stream`, then reports whether a
+ * tensor-core contraction block of an earlier call gave up a bounded wait
+ * (one second of device time per wait) and skipped its MMAs:
+ * NUSHT_ETIMEOUT (that call's outputs are invalid; the flag is cleared),
+ * else NUSHT_OK.  No counterpart in the paper: a guard of this library.
+ */
+NUSHT_API int nusht_batch_status(nusht_batch_t p, nusht_stream_t stream);
+
+/*
+ * nusht_batch_path -- the contraction path of bucket `bucket`: 2 = tensor
+ * cores from the recurrence table, 1 = CUDA-core FP32 from the table,
+ * 0 = CUDA-core FP32 with the recurrence run every call; -1 for a bad
+ * argument.
+ */
+NUSHT_API int nusht_batch_path(nusht_batch_t p, int bucket);
 
 /* nusht_destroy -- free the plan and its device memory (NULL-safe). */
 NUSHT_API int nusht_destroy(nusht_plan_t p);

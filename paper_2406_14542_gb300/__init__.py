@@ -27,7 +27,7 @@ EXPORTS = ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_
            "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_good_size", "nusht_stage_times",
            "nusht_strerror", "nusht_last_error", "nusht_version", "nusht_adjoint_direct_noalloc",
            "nusht_plan_many", "nusht_synth_many", "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info",
-           "nusht_plan_bin")
+           "nusht_plan_bin", "nusht_batch_status", "nusht_batch_path")
 
 
 class NushtError(RuntimeError):
@@ -39,7 +39,8 @@ class NushtError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("kernel_width", ctypes.c_int), ("profile", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("tune", ctypes.c_int), ("fp64_contraction", ctypes.c_int),
-                ("legendre_table", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("legendre_table", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class Sizes(ctypes.Structure):
@@ -90,6 +91,8 @@ def load(path: str | None = None):
         lib.nusht_adjoint_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         lib.nusht_destroy_many.argtypes = [vp]
         lib.nusht_plan_bin.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        lib.nusht_batch_status.argtypes = [vp, vp]
+        lib.nusht_batch_path.argtypes = [vp, ctypes.c_int]
         lib.nusht_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64)]
         lib.nusht_strerror.argtypes = [ctypes.c_int]
@@ -99,7 +102,8 @@ def load(path: str | None = None):
         for name in ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_synth_grad",
                      "nusht_destroy", "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_stage_times",
                      "nusht_adjoint_direct_noalloc", "nusht_plan_many", "nusht_synth_many",
-                     "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info", "nusht_plan_bin"):
+                     "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info", "nusht_plan_bin",
+                     "nusht_batch_status", "nusht_batch_path"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -117,8 +121,10 @@ def _check(code: int, where: str):
         raise NushtError(code, where, load().nusht_last_error().decode())
 
 
-def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False, legendre_table=0, tune=0) -> Opts:
+def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False, legendre_table=0, tune=0,
+          tensor_cores=0) -> Opts:
     o = Opts()
+    o.tensor_cores = int(tensor_cores)
     o.tune = int(tune)
     o.legendre_table = int(legendre_table)
     o.sigma = float(sigma)
@@ -327,7 +333,7 @@ class BatchPlan:
     float64 (N_b, 2) tensor; each lmax <= 4095."""
 
     def __init__(self, lmaxs, pts_list, eps: float = 1e-5, sigma: float = 0.0, legendre_table: int = 0,
-                 tune: int = 0, stream=None):
+                 tune: int = 0, tensor_cores: int = 0, stream=None):
         import torch
 
         self.lib = load()
@@ -341,7 +347,7 @@ class BatchPlan:
         larr = (ctypes.c_int * n)(*self.lmaxs)
         narr = (ctypes.c_int64 * n)(*self.npts)
         parr = (ctypes.c_void_p * n)(*[p.data_ptr() if p.numel() else 0 for p in self.pts])
-        o = _opts(sigma, legendre_table=legendre_table, tune=tune)
+        o = _opts(sigma, legendre_table=legendre_table, tune=tune, tensor_cores=tensor_cores)
         h = ctypes.c_void_p()
         _check(self.lib.nusht_plan_many(ctypes.byref(h), n, larr, narr, parr, float(eps), MIXED, ctypes.byref(o),
                                         _stream_ptr(stream)), "nusht_plan_many")
@@ -355,7 +361,13 @@ class BatchPlan:
         by = ctypes.c_int64()
         _check(self.lib.nusht_batch_info(self._h, ctypes.byref(nb), of, bl, ctypes.byref(by)), "nusht_batch_info")
         return {"nbuckets": nb.value, "bucket_of": list(of), "bucket_lmax": list(bl)[: nb.value],
-                "bytes_device": by.value}
+                "bytes_device": by.value,
+                "paths": [self.lib.nusht_batch_path(self._h, g) for g in range(nb.value)]}
+
+    def status(self, stream=None):
+        """Synchronise and raise if a tensor-core block of an earlier call gave
+        up a bounded wait (its outputs are then invalid)."""
+        _check(self.lib.nusht_batch_status(self._h, _stream_ptr(stream)), "nusht_batch_status")
 
     def synth(self, alms, outs=None, stream=None):
         import torch

@@ -553,6 +553,377 @@ __global__ void __launch_bounds__(256) bucket_adj_tab_k(BucketArgs a, const int*
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core contractions (tcgen05.mma kind::tf32, accumulators in tensor
+// memory).  Both directions are D[128 x 128] += A[128 x 8] B[128 x 8]^T per
+// MMA into two accumulators: D_E collects the even l - m terms and D_O the
+// odd ones, so no MMA multiplies zeros.
+//   synthesis: rows = 128 ring pairs, K = 8 degrees of one parity,
+//              B columns = the bucket's (member, re/im) coefficients;
+//   adjoint:   rows = 128 degrees of one parity, K = 8 ring pairs,
+//              B columns = the folded spectrum S_E or S_O.
+// Precision.  Each FP32 operand is split into x = hi + lo, hi = x rounded to
+// TF32 (cvt.rna), lo = x - hi exactly (|lo| <= 2^-11 |x|); D accumulates
+// hi*hi + hi*lo + lo*hi, so a product keeps about 22 significant bits with
+// an unbiased error.  The tensor core's own accumulation adds with reduced,
+// truncating alignment, an error that grows with the number of MMAs folded
+// into one accumulator; so the chunks are taken in groups of TC_G, each group
+// into one of two partial accumulator sets (TMEM columns 0..255 and
+// 256..511, alternating), and every finished group is added in FP32 with
+// round-to-nearest into per-thread registers while the tensor core runs the
+// next group.
+// Data flow.  A chunk (one K step of both parities) is 8 operand tiles of
+// 4 KB in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per
+// core matrix; K-adjacent core matrices 128 B apart, 8-row groups 256 B
+// apart).  Four chunk buffers rotate; threads 0..127 split and store the A
+// rows, threads 128..255 the B rows, global loads run two chunks ahead in
+// registers; one thread issues the six MMAs of a chunk and commits them to
+// the buffer's mbarrier.  Registers: warps 0..3 own the E sums of their 32
+// TMEM lanes, warps 4..7 the O sums.  One block per SM (512 TMEM columns;
+// the shared-memory size admits no second block).  Every wait is bounded
+// (one second of device time); a block that gives up sets *status, issues
+// nothing more, and still frees its tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int TC_TILE = 128 * 8 * 4;              // one 128 x 8 fp32 operand tile
+constexpr int TC_CHUNK = 8 * TC_TILE;             // AEh AEl AOh AOl BEh BEl BOh BOl
+constexpr int TC_NBUF = 4;
+constexpr int TC_G = 4;                           // chunks per partial accumulation (>= TC_NBUF - 1)
+constexpr int TC_SMEM = TC_NBUF * TC_CHUNK + 64;  // + mbarriers, TMEM address
+constexpr int TC_THREADS = 256;
+constexpr uint32_t TC_COLS = 512;
+static_assert(TC_G + 1 >= TC_NBUF, "a partial set is refilled only after its fold");
+static_assert(128 * 129 * 4 <= TC_NBUF * TC_CHUNK, "epilogue exchange fits the chunk buffers");
+// instruction descriptor: D f32 (bits 4-5 = 1), A and B tf32 (bits 7-9,
+// 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+}
+
+// shared-memory matrix descriptor: start >> 4, leading byte offset (next core
+// matrix along K) 128 B, stride byte offset (next 8-row group) 256 B,
+// descriptor version 1 at bit 46, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)(256u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  for (int it = 0; it < (1 << 30); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 63 && gtimer() - t0 > TC_WAIT_NS) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+      : "memory");
+}
+
+// 32 consecutive columns of this warp's 32 TMEM lanes (no wait)
+__device__ __forceinline__ void tc_ld32(uint32_t addr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(addr)
+      : "memory");
+}
+
+// row `row` of two operand pairs (hi, lo) starting at tile `tile` of a chunk buffer
+__device__ __forceinline__ void tc_store(unsigned char* buf, int tile, int row, const float (&e)[8],
+                                         const float (&o)[8]) {
+  const int base = (row >> 3) * 256 + (row & 7) * 16;
+  auto put = [&](int tl, const float (&v)[8]) {
+    float h[8], l[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      uint32_t hb;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v[k]));
+      h[k] = __uint_as_float(hb);
+      l[k] = v[k] - h[k];
+    }
+    unsigned char* ph = buf + tl * TC_TILE + base;
+    unsigned char* pl = ph + TC_TILE;
+    *reinterpret_cast<float4*>(ph) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(ph + 128) = make_float4(h[4], h[5], h[6], h[7]);
+    *reinterpret_cast<float4*>(pl) = make_float4(l[0], l[1], l[2], l[3]);
+    *reinterpret_cast<float4*>(pl + 128) = make_float4(l[4], l[5], l[6], l[7]);
+  };
+  put(tile, e);
+  put(tile + 2, o);
+}
+
+// TMEM allocation + mbarrier setup; returns the accumulator base address
+__device__ __forceinline__ uint32_t tc_setup(unsigned char* smem) {
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_NBUF * TC_CHUNK);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + TC_NBUF);
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < TC_NBUF; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[k])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return *tslot;
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tmem) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS) : "memory");
+}
+
+// Main loop over `nchunk` chunks.  load(c, e, o) fills this thread's two
+// operand rows of chunk c (threads < 128: A rows; others: B rows).  On return
+// (true) acc[] holds this thread's 128 sums: E (warps 0..3) or O (warps 4..7)
+// of TMEM lane 32 (warp % 4) + lane.  False: a wait gave up.
+template <class Load>
+__device__ __forceinline__ bool tc_mainloop(unsigned char* smem, uint32_t tmem, int nchunk, Load load,
+                                            float (&acc)[128]) {
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_NBUF * TC_CHUNK);
+  const int t = threadIdx.x, warp = t >> 5;
+  const int row = t & 127, tile = t < 128 ? 0 : 4;
+  // this thread's TMEM view: lanes of its warp quarter, E or O columns
+  const uint32_t tview = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (warp < 4 ? 0u : 128u);
+#pragma unroll
+  for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+  bool ok = true;
+  int last = -1;  // last chunk whose MMAs were issued
+  int pg = 0;     // next group to fold
+  auto fold = [&](int g) {
+    const uint32_t src = tview + (uint32_t)((g & 1) * 256);
+#pragma unroll
+    for (int c0 = 0; c0 < 128; c0 += 32) {
+      uint32_t r[32];
+      tc_ld32(src + c0, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+    }
+  };
+  float e0[8], o0[8], e1[8], o1[8];
+  if (nchunk > 0) load(0, e0, o0);
+  if (nchunk > 1) load(1, e1, o1);
+  auto step = [&](int c, float (&e)[8], float (&o)[8]) {
+    const int buf = c % TC_NBUF;
+    unsigned char* bp = smem + buf * TC_CHUNK;
+    if (c >= TC_NBUF && ok) {  // chunk c - NBUF's MMAs (and all before them) have completed
+      ok = mbar_wait(smem_u32(&bars[buf]), (uint32_t)((c / TC_NBUF - 1) & 1));
+      if (ok && (c - TC_NBUF) % TC_G == TC_G - 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        fold(pg++);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      }
+    }
+    tc_store(bp, tile, row, e, o);
+    if (c + 2 < nchunk) load(c + 2, e, o);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    ok = __syncthreads_and(ok);
+    if (!ok) return;
+    last = c;
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sb = smem_u32(bp);
+      const uint32_t dE = tmem + (uint32_t)(((c / TC_G) & 1) * 256), dO = dE + 128;
+      const uint32_t a = (c % TC_G) != 0 ? 1u : 0u;
+      tc_mma(dE, tc_desc(sb + 0 * TC_TILE), tc_desc(sb + 4 * TC_TILE), a);
+      tc_mma(dE, tc_desc(sb + 0 * TC_TILE), tc_desc(sb + 5 * TC_TILE), 1u);
+      tc_mma(dE, tc_desc(sb + 1 * TC_TILE), tc_desc(sb + 4 * TC_TILE), 1u);
+      tc_mma(dO, tc_desc(sb + 2 * TC_TILE), tc_desc(sb + 6 * TC_TILE), a);
+      tc_mma(dO, tc_desc(sb + 2 * TC_TILE), tc_desc(sb + 7 * TC_TILE), 1u);
+      tc_mma(dO, tc_desc(sb + 3 * TC_TILE), tc_desc(sb + 6 * TC_TILE), 1u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bars[buf]))
+                   : "memory");
+    }
+  };
+  for (int c = 0; c < nchunk; c += 2) {
+    step(c, e0, o0);
+    if (c + 1 < nchunk) step(c + 1, e1, o1);
+  }
+  // the last commit covers every MMA issued before it
+  bool done = last >= 0 ? mbar_wait(smem_u32(&bars[last % TC_NBUF]), (uint32_t)((last / TC_NBUF) & 1)) : true;
+  done = __syncthreads_and(done);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool good = ok && done && last == nchunk - 1;
+  if (good)
+    while (pg * TC_G < nchunk) fold(pg++);
+  return good;
+}
+
+// synthesis: block = (order m, 128 ring pairs = table tiles 2u, 2u + 1);
+// tile offsets into P, -1 for a tile outside the kept range
+__global__ void __launch_bounds__(TC_THREADS, 1) bucket_synth_tc_k(BucketArgs a, const int* __restrict__ titems,
+                                                                   const longlong2* __restrict__ toffs, int nitems,
+                                                                   const float* __restrict__ P,
+                                                                   const float2* __restrict__ atb,
+                                                                   float2* __restrict__ G, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  if ((int)blockIdx.x >= nitems || *(volatile int*)status) return;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int v = titems[blockIdx.x];
+  const int m = v >> 16, u = v & 0xffff;
+  const longlong2 of = toffs[blockIdx.x];
+  const int L = a.lmax;
+  const int mb = idx_lm(L, 0, m);
+  const int nrow = L - m + 1;
+  const int nchunk = (nrow + 15) / 16;
+  const int r = t & 127;
+  // A rows: ring pair r of the two tiles; B rows: column r of the coefficients
+  const long long off = (r < 64) ? of.x : of.y;
+  const float* src = t < 128 ? (off >= 0 ? P + off + (r & 63) : nullptr)
+                             : reinterpret_cast<const float*>(atb + (size_t)(mb + m) * BK_MAXB) + r;
+  const size_t stride = t < 128 ? (size_t)BS_PAIRS : (size_t)BK_COLS;
+  const uint32_t tmem = tc_setup(tc_smem);
+  float acc[128];
+  const bool ok = tc_mainloop(
+      tc_smem, tmem, nchunk,
+      [&](int c, float (&e)[8], float (&o)[8]) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int re = 16 * c + 2 * k, ro = re + 1;
+          e[k] = (src && re < nrow) ? __ldg(src + (size_t)re * stride) : 0.f;
+          o[k] = (src && ro < nrow) ? __ldg(src + (size_t)ro * stride) : 0.f;
+        }
+      },
+      acc);
+  if (!ok) {
+    if (t == 0) atomicExch(status, 1);
+  } else {
+    // O sums through shared memory (row stride 129: conflict-free)
+    float* xs = reinterpret_cast<float*>(tc_smem);
+    if (warp >= 4)
+#pragma unroll
+      for (int j = 0; j < 128; ++j) xs[r * 129 + j] = acc[j];
+    __syncthreads();
+    if (warp < 4) {
+      const int M = a.M;
+      const float sg = (m & 1) ? -1.f : 1.f;
+      const int jn = 1 + u * 128 + r;
+      const int js = M / 2 - jn;
+      if (jn <= a.npairs) {
+#pragma unroll
+        for (int slot = 0; slot < BK_MAXB; ++slot) {  // static acc[] indices
+          if (slot >= a.B || m > a.memberL[slot]) continue;
+          const float oe = xs[r * 129 + 2 * slot], oi = xs[r * 129 + 2 * slot + 1];
+          float2* rowp = G + ((size_t)slot * (L + 1) + m) * M;
+          const float ee = acc[2 * slot], ei = acc[2 * slot + 1];
+          const float2 fn = make_float2(ee + oe, ei + oi);
+          rowp[jn] = fn;
+          rowp[M - jn] = make_float2(sg * fn.x, sg * fn.y);
+          if (js != jn) {
+            const float2 fs = make_float2(ee - oe, ei - oi);
+            rowp[js] = fs;
+            rowp[M - js] = make_float2(sg * fs.x, sg * fs.y);
+          }
+        }
+      }
+    }
+  }
+  tc_teardown(tmem);
+}
+
+// adjoint: block = (order m, rows r0 .. r0 + 255 of l - m, r0 a multiple of
+// 256); TMEM lane d holds the even row r0 + 2d and the odd row r0 + 2d + 1;
+// K runs over the order's kept table tiles (items[mfirst[m] .. mfirst[m + 1])),
+// 8 ring pairs per chunk
+__global__ void __launch_bounds__(TC_THREADS, 1) bucket_adj_tc_k(BucketArgs a, const int* __restrict__ items,
+                                                                 const int64_t* __restrict__ offs,
+                                                                 const int* __restrict__ mfirst,
+                                                                 const int2* __restrict__ work, int nwork,
+                                                                 const float* __restrict__ P,
+                                                                 const float* __restrict__ S, float* __restrict__ cacc,
+                                                                 int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  if ((int)blockIdx.x >= nwork || *(volatile int*)status) return;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int2 wk = work[blockIdx.x];
+  const int m = wk.x, r0 = wk.y;
+  const int L = a.lmax;
+  const int mb = idx_lm(L, 0, m);
+  const int nrow = L - m + 1;
+  const int i0 = mfirst[m], i1 = mfirst[m + 1];
+  const int nchunk = (i1 - i0) * (BS_PAIRS / 8);
+  const int r = t & 127;
+  const int re = r0 + 2 * r, ro = re + 1;
+  const uint32_t tmem = tc_setup(tc_smem);
+  float acc[128];
+  const bool ok = tc_mainloop(
+      tc_smem, tmem, nchunk,
+      [&](int c, float (&e)[8], float (&o)[8]) {
+        const int it = i0 + (c >> 3), j = c & 7;
+        if (t < 128) {  // A rows: degrees re (E) and ro (O), ring pairs 8j .. 8j + 7 of the tile
+          const float* Pi = P + offs[it] + 8 * j;
+          float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0, y0 = x0, y1 = x0;
+          if (re < nrow) {
+            x0 = __ldg(reinterpret_cast<const float4*>(Pi + (size_t)re * BS_PAIRS));
+            x1 = __ldg(reinterpret_cast<const float4*>(Pi + (size_t)re * BS_PAIRS + 4));
+          }
+          if (ro < nrow) {
+            y0 = __ldg(reinterpret_cast<const float4*>(Pi + (size_t)ro * BS_PAIRS));
+            y1 = __ldg(reinterpret_cast<const float4*>(Pi + (size_t)ro * BS_PAIRS + 4));
+          }
+          e[0] = x0.x; e[1] = x0.y; e[2] = x0.z; e[3] = x0.w;
+          e[4] = x1.x; e[5] = x1.y; e[6] = x1.z; e[7] = x1.w;
+          o[0] = y0.x; o[1] = y0.y; o[2] = y0.z; o[3] = y0.w;
+          o[4] = y1.x; o[5] = y1.y; o[6] = y1.z; o[7] = y1.w;
+        } else {  // B rows: column r of S_E and S_O for the same 8 ring pairs
+          const int p0 = (items[it] & 0xffff) * BS_PAIRS + 8 * j;
+          const float* Sp = S + ((size_t)m * a.npairs + p0) * 2 * BK_COLS + r;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const bool in = p0 + k < a.npairs;
+            e[k] = in ? __ldg(Sp + (size_t)k * 2 * BK_COLS) : 0.f;
+            o[k] = in ? __ldg(Sp + (size_t)k * 2 * BK_COLS + BK_COLS) : 0.f;
+          }
+        }
+      },
+      acc);
+  if (!ok) {
+    if (t == 0) atomicExch(status, 1);
+  } else {
+    const int l = m + re + (warp < 4 ? 0 : 1);
+    if (l <= L) {
+      float* dst = cacc + (size_t)(mb + l) * BK_COLS;
+#pragma unroll
+      for (int j = 0; j < 128; j += 4)
+        *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+    }
+  }
+  tc_teardown(tmem);
+}
+
 // member outputs: c_slot(l, m) = Ahat * C + poles (m = 0)
 __global__ void bucket_final_k(int L, int M, int B, const int* __restrict__ memberL, const float* __restrict__ cacc,
                                const double* __restrict__ ahat, const double* __restrict__ pole_norm,
@@ -599,6 +970,14 @@ struct Bucket {
   int2* work = nullptr;               // adjoint blocks (m, first degree)
   int nwork = 0;
   size_t table_bytes = 0;
+  // tensor-core path (table only): synthesis blocks of 128 ring pairs and
+  // adjoint blocks of 256 degrees
+  bool tc = false;
+  int* tc_items = nullptr;            // (m << 16) | u, table tiles 2u and 2u + 1
+  longlong2* tc_offs = nullptr;       // their offsets into P (-1: not kept)
+  int ntc = 0;
+  int2* tc_work = nullptr;            // (m, first row l - m)
+  int ntc_work = 0;
   cufftHandle theta = 0;
   bool have_theta = false;
 };
@@ -619,6 +998,7 @@ struct nusht_batch_s {
   std::vector<int> bucket_of, slot_of;
   size_t bytes = 0;
   cudaStream_t cap = nullptr;
+  int* status = nullptr;  // device flag: a bounded wait in a tensor-core kernel gave up
   cudaGraphExec_t gs = nullptr, ga = nullptr;
   std::vector<const void*> gs_in;
   std::vector<void*> gs_out;
@@ -645,6 +1025,9 @@ void bucket_free(Bucket& b) {
   dev_free(b.offs);
   dev_free(b.mfirst);
   dev_free(b.work);
+  dev_free(b.tc_items);
+  dev_free(b.tc_offs);
+  dev_free(b.tc_work);
   if (b.have_theta) cufftDestroy(b.theta);
   b = Bucket();
 }
@@ -659,6 +1042,7 @@ void batch_free(nusht_batch_t p) {
   for (auto* s : p->sub)
     if (s) plan_destroy(s);
   for (auto& b : p->buckets) bucket_free(b);
+  dev_free(p->status);
   if (p->cap) cudaStreamDestroy(p->cap);
   cudaSetDevice(cur);
   delete p;
@@ -789,6 +1173,43 @@ int bucket_build(nusht_batch_t p, Bucket& b, cudaStream_t s) {
       const BucketArgs a = bucket_args(b);
       if (b.nitems > 0) bucket_ptab_k<<<(b.nitems + 3) / 4, 128, 0, s>>>(a, b.items, b.offs, b.nitems, b.P);
       NUSHT_CUDA(cudaGetLastError());
+      if (p->opts.tensor_cores >= 0) {
+        // pairs of 64-pair tiles (2u, 2u + 1) of one order; tiles[] is
+        // ordered by m, then tile
+        std::vector<int> ti;
+        std::vector<longlong2> to;
+        for (size_t k = 0; k < tiles.size(); ++k) {
+          const int m = tiles[k] >> 16, tile = tiles[k] & 0xffff;
+          const int key = (m << 16) | (tile >> 1);
+          if (ti.empty() || ti.back() != key) {
+            ti.push_back(key);
+            longlong2 z2;
+            z2.x = -1;
+            z2.y = -1;
+            to.push_back(z2);
+          }
+          if (tile & 1)
+            to.back().y = off[k];
+          else
+            to.back().x = off[k];
+        }
+        std::vector<int2> tw;
+        for (int m = 0; m <= L; ++m)
+          if (mf[m + 1] > mf[m])
+            for (int r0 = 0; r0 <= L - m; r0 += 256) tw.push_back(make_int2(m, r0));
+        b.ntc = (int)ti.size();
+        b.ntc_work = (int)tw.size();
+        NUSHT_TRY(dev_alloc((void**)&b.tc_items, std::max<size_t>(1, ti.size()) * 4, &p->bytes));
+        NUSHT_TRY(dev_alloc((void**)&b.tc_offs, std::max<size_t>(1, to.size()) * sizeof(longlong2), &p->bytes));
+        NUSHT_TRY(dev_alloc((void**)&b.tc_work, std::max<size_t>(1, tw.size()) * sizeof(int2), &p->bytes));
+        if (!ti.empty()) {
+          NUSHT_CUDA(cudaMemcpy(b.tc_items, ti.data(), ti.size() * 4, cudaMemcpyHostToDevice));
+          NUSHT_CUDA(cudaMemcpy(b.tc_offs, to.data(), to.size() * sizeof(longlong2), cudaMemcpyHostToDevice));
+        }
+        if (!tw.empty())
+          NUSHT_CUDA(cudaMemcpy(b.tc_work, tw.data(), tw.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        b.tc = true;
+      }
     }
   }
   NUSHT_CUFFT(cufftCreate(&b.theta));
@@ -829,6 +1250,8 @@ int set_adj_smem() {
   NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_k<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   const int smt = (BS_PAIRS * AT_PAD + BS_PAIRS * 2 * BK_COLS) * (int)sizeof(float);
   NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_tab_k, cudaFuncAttributeMaxDynamicSharedMemorySize, smt));
+  NUSHT_CUDA(cudaFuncSetAttribute(bucket_synth_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
   return NUSHT_OK;
 }
 
@@ -837,7 +1260,9 @@ int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
     const BucketArgs a = bucket_args(b);
     dim3 g((b.L + 1 + 3) / 4, b.L + 1);
     bucket_scale_k<<<g, 256, 0, s>>>(b.L, b.B, b.memberL, b.alm_ptrs, b.leg->leg.ahat, b.atb);
-    if (b.nitems > 0 && b.table)
+    if (b.ntc > 0 && b.tc)
+      bucket_synth_tc_k<<<b.ntc, TC_THREADS, TC_SMEM, s>>>(a, b.tc_items, b.tc_offs, b.ntc, b.P, b.atb, b.G, p->status);
+    else if (b.nitems > 0 && b.table)
       bucket_synth_tab_k<<<b.nitems, 256, 0, s>>>(a, b.items, b.offs, b.nitems, b.P, b.atb, b.G);
     else if (b.nitems > 0)
       bucket_synth_k<<<b.nitems, 256, 0, s>>>(a, b.items, b.nitems, b.atb, b.G);
@@ -869,7 +1294,11 @@ int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
     NUSHT_CUFFT(cufftExecC2C(b.theta, (cufftComplex*)b.Ghat, (cufftComplex*)b.Ghat, CUFFT_INVERSE));
     dim3 gf((b.npairs + FOLD_PAIRS - 1) / FOLD_PAIRS, b.L + 1);
     bucket_fold_k<<<gf, 256, 0, s>>>(b.L, b.M, b.npairs, b.B, b.memberL, b.Ghat, b.S);
-    if (b.table) {
+    if (b.tc) {
+      if (b.ntc_work > 0)
+        bucket_adj_tc_k<<<b.ntc_work, TC_THREADS, TC_SMEM, s>>>(bucket_args(b), b.items, b.offs, b.mfirst, b.tc_work,
+                                                         b.ntc_work, b.P, b.S, b.cacc, p->status);
+    } else if (b.table) {
       const size_t sm = (size_t)(BS_PAIRS * AT_PAD + BS_PAIRS * 2 * BK_COLS) * sizeof(float);
       if (b.nwork > 0)
         bucket_adj_tab_k<<<b.nwork, 256, sm, s>>>(bucket_args(b), b.items, b.offs, b.mfirst, b.work, b.nwork, b.P,
@@ -946,6 +1375,14 @@ int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64
     p->L.assign(lmax, lmax + nbatch);
     p->npts.assign(npts, npts + nbatch);
     if ((st = set_adj_smem()) != NUSHT_OK) break;
+    if ((st = dev_alloc((void**)&p->status, sizeof(int), &p->bytes)) != NUSHT_OK) break;
+    {
+      cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
+      if (e != cudaSuccess) {
+        st = cuda_status(e, "cudaMemsetAsync");
+        break;
+      }
+    }
     // per-triple costs on GB300: FP64 recurrence (2 FP64 instructions at
     // ~70 % of 0.6e12/s), one FP32 FMA per column at ~50 % of 37e12/s, and a
     // fixed cost per bucket
@@ -1042,6 +1479,25 @@ int nusht_adjoint_many(nusht_batch_t p, const void* const* d_map, void* const* d
 int nusht_destroy_many(nusht_batch_t p) {
   batch_free(p);
   return NUSHT_OK;
+}
+
+int nusht_batch_status(nusht_batch_t p, nusht_stream_t stream) {
+  if (!p) return set_error(NUSHT_EINVAL, "batch plan is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  NUSHT_CUDA(cudaStreamSynchronize(s));
+  int flag = 0;
+  NUSHT_CUDA(cudaMemcpy(&flag, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    NUSHT_CUDA(cudaMemset(p->status, 0, sizeof(int)));
+    return set_error(NUSHT_ETIMEOUT, "a tensor-core contraction block gave up waiting for its MMAs");
+  }
+  return NUSHT_OK;
+}
+
+int nusht_batch_path(nusht_batch_t p, int bucket) {
+  if (!p || bucket < 0 || bucket >= (int)p->buckets.size()) return -1;
+  const nusht::Bucket& b = p->buckets[bucket];
+  return b.tc ? 2 : (b.table ? 1 : 0);
 }
 
 int nusht_batch_info(nusht_batch_t p, int* nbuckets, int* bucket_of, int* bucket_lmax, int64_t* bytes_device) {

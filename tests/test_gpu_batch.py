@@ -25,22 +25,28 @@ def env():
     return torch, nu
 
 
-def make_batch(torch, nu, ls, seed=0, table=0):
+def make_batch(torch, nu, ls, seed=0, table=0, tc=0):
     alms = [W.alm_gaussian(l, seed=seed + 10 * i, dtype=np.complex64) for i, l in enumerate(ls)]
     pts = [W.points_uniform(max(1, 2 * l * l), seed=seed + 10 * i + 1) for i, l in enumerate(ls)]
-    bp = nu.BatchPlan(ls, [torch.from_numpy(p).cuda() for p in pts], eps=1e-5, legendre_table=table)
+    bp = nu.BatchPlan(ls, [torch.from_numpy(p).cuda() for p in pts], eps=1e-5, legendre_table=table,
+                      tensor_cores=tc)
     return bp, alms, pts
 
 
-@pytest.mark.parametrize("table", [0, -1])
-def test_batch_small_against_oracle(env, table):
-    """Both Legendre paths: the plan-time recurrence table (default) and the
-    recurrence on every call."""
+# contraction paths: 2 = tensor cores (table), 1 = CUDA-core FP32 (table),
+# 0 = CUDA-core FP32 with the recurrence on every call
+PATHS = [(0, 0, 2), (0, -1, 1), (-1, 0, 0)]
+
+
+@pytest.mark.parametrize("table,tc,path", PATHS)
+def test_batch_small_against_oracle(env, table, tc, path):
+    """Every Legendre contraction path against the oracle."""
     torch, nu = env
     ls = [0, 3, 16, 40, 63, 100, 130, 7]
-    bp, alms, pts = make_batch(torch, nu, ls, table=table)
+    bp, alms, pts = make_batch(torch, nu, ls, table=table, tc=tc)
     info = bp.info()
     assert info["nbuckets"] >= 1 and max(info["bucket_lmax"]) == max(ls)
+    assert info["paths"] == [path] * info["nbuckets"]
     outs = bp.synth([torch.from_numpy(a).cuda() for a in alms])
     torch.cuda.synchronize()
     for l, a, p, f in zip(ls, alms, pts, outs):
@@ -49,6 +55,7 @@ def test_batch_small_against_oracle(env, table):
         assert oracle.eps_eff(ref, f.double().cpu().numpy()[sel]) <= TOL, l
     ys = [np.random.default_rng(i).standard_normal(p.shape[0]) for i, p in enumerate(pts)]
     cs = bp.adjoint([torch.from_numpy(y).float().cuda() for y in ys])
+    bp.status()
     for l, p, y, c in zip(ls, pts, ys, cs):
         ref = oracle.adjoint(y.astype(np.float32).astype(np.float64), p, l)
         assert oracle.eps_eff(ref, c.cpu().numpy().astype(np.complex128)) <= TOL, l
@@ -72,15 +79,18 @@ def test_batch_recapture_and_dot(env):
         assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
-def test_batch64_members_against_oracle(env):
+@pytest.mark.parametrize("tc,path", [(0, 2), (-1, 1)])
+def test_batch64_members_against_oracle(env, tc, path):
     """64 transforms, lmax ~ U{64..511}, N_b = 2 lmax_b^2 uniform points: the
     batch structure of the 64-transform workload at a size the oracle can
-    check; members sampled across buckets."""
+    check (several 128-pair synthesis blocks and 256-degree adjoint blocks
+    per order, polar-skipped tiles); members sampled across buckets."""
     torch, nu = env
     rng = np.random.default_rng(0)
     ls = [int(x) for x in rng.integers(64, 512, 64)]
-    bp, alms, pts = make_batch(torch, nu, ls, seed=100)
+    bp, alms, pts = make_batch(torch, nu, ls, seed=100, tc=tc)
     info = bp.info()
+    assert set(info["paths"]) == {path}
     outs = bp.synth([torch.from_numpy(a).cuda() for a in alms])
     torch.cuda.synchronize()
     order = np.argsort(ls)
@@ -92,7 +102,7 @@ def test_batch64_members_against_oracle(env):
         assert oracle.eps_eff(ref, outs[i].double().cpu().numpy()[sel]) <= TOL, (i, ls[i])
     ys = [torch.randn(p.shape[0], device="cuda") for p in pts]
     cs = bp.adjoint(ys)
-    torch.cuda.synchronize()
+    bp.status()
     for i in check[:3]:
         l = ls[i]
         ms = [0, 1, l // 2, l]
