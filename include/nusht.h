@@ -86,14 +86,19 @@ enum { NUSHT_FP64 = 0, NUSHT_MIXED = 1 };
 
 /* Options; a zeroed struct (or NULL) selects the defaults. */
 typedef struct {
-  double sigma;      /* fine-grid up-sampling factor; 0 = default (2.0) */
+  double sigma;      /* fine-grid up-sampling factor in [1.2, 4]; 0 = default: 1.5 for
+                        NUSHT_FP64 (the FP64 2D FFT dominates), 2.0 for NUSHT_MIXED; with
+                        tune = 1 nusht_plan times sigma in {2, 1.5, 1.25} instead (each one
+                        whose kernel width for eps fits the limit of 16) and caches the
+                        winner, tune = 2 takes the cached one */
   int kernel_width;  /* ES kernel width w override; 0 = from eps and sigma */
   int profile;       /* 1 = record per-stage CUDA-event times (nusht_stage_times) */
   int deterministic; /* reserved; synthesis is bit-reproducible, the adjoint's spreading
                         flush adds tile halos with atomics (rounding-level order effects) */
-  int tune;          /* spreading/interpolation bin size: 0 = 32 cells; 1 = search (time
-                        16/32/64 on the plan's own points at plan time, cache the winner);
-                        2 = the cached choice for this device/size when present */
+  int tune;          /* NUFFT autotuner: 0 = off (bin edge 32 cells); 1 = search at plan
+                        time on the plan's own points (bin edge 16/32/64 and, when sigma = 0,
+                        the up-sampling factor), caching the winners; 2 = the cached choices
+                        for this device/size when present */
   int fp64_contraction; /* FP64 mode only: 1 = Legendre sums with FP64 instructions;
                            0 (default) = FP64 recurrence, sums as float pairs on the FP32
                            pipe (~2^-48 relative per operation; a_lm magnitudes below 1e20) */

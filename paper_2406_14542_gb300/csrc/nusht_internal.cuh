@@ -150,6 +150,7 @@ struct PlanRole {
   bool legendre = true;
   bool nufft = true;
   void* ghat_external = nullptr;
+  int bin = 0;                // spreading bin edge chosen by the caller (0: opts.tune decides)
 };
 int plan_create(nusht_plan_t* out, int lmax, int mmax, int64_t npts, const double* d_pts, double eps, int precision,
                 const nusht_opts* opts, cudaStream_t s, const PlanRole& role);
@@ -178,5 +179,12 @@ int spread_smem_optin();
 
 // autotuner (tune.cu)
 int tune_points(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s);
+// ES kernel width the accuracy formula asks for at NUFFT tolerance eps and
+// up-sampling sigma (before the [2, 16] clamp)
+int es_width(double eps, double sigma);
+// opts.tune 1/2 with opts.sigma = 0: the up-sampling factor (and the bin edge
+// found with it) from timing, or from the cache; *sigma_out = 0 if none
+int tune_sigma(int lmax, int mmax, int64_t npts, const double* d_pts, double eps, int precision,
+               const nusht_opts* o, cudaStream_t s, double* sigma_out, int* bin_out);
 
 }  // namespace nusht

@@ -80,13 +80,13 @@ int64_t good_size(int64_t nmin, int multiple, int maxprime) {
 // af Klinteberg, SIAM J. Sci. Comput. 2019, the kernel of cuFINUFFT that the
 // paper's N and N^dagger use, Sec. 3): width w from the tolerance and the
 // up-sampling factor, shape beta proportional to w.
+int es_width(double eps, double sigma) {
+  if (std::fabs(sigma - 2.0) < 1e-12) return (int)std::ceil(std::log10(1.0 / eps)) + 1;
+  return (int)std::ceil(std::log(1.0 / eps) / (M_PI * std::sqrt(1.0 - 1.0 / sigma)));
+}
+
 static void es_params(double eps, double sigma, int w_override, int* w, double* beta) {
-  int ww;
-  if (std::fabs(sigma - 2.0) < 1e-12) {
-    ww = (int)std::ceil(std::log10(1.0 / eps)) + 1;
-  } else {
-    ww = (int)std::ceil(std::log(1.0 / eps) / (M_PI * std::sqrt(1.0 - 1.0 / sigma)));
-  }
+  int ww = es_width(eps, sigma);
   if (w_override > 0) ww = w_override;
   ww = std::max(2, std::min(16, ww));
   double b;
@@ -110,7 +110,9 @@ int choose_sizes(int lmax, int mmax, double eps, int precision, const nusht_opts
     return set_error(NUSHT_EUNSUPPORTED, "NUSHT_MIXED supports eps >= 1e-6 only (single-precision grid)");
   nusht_opts opt{};
   if (o) opt = *o;
-  double sigma = opt.sigma > 0.0 ? opt.sigma : 2.0;
+  // default up-sampling: FP64 grids are FFT-bound (the FP64 2D FFT costs more
+  // than the wider kernel sigma = 1.5 needs); FP32 grids are not
+  double sigma = opt.sigma > 0.0 ? opt.sigma : (precision == NUSHT_FP64 ? 1.5 : 2.0);
   if (!(sigma >= 1.2 && sigma <= 4.0)) return set_error(NUSHT_EINVAL, "sigma must be in [1.2, 4]");
   if (opt.kernel_width < 0 || opt.kernel_width > 16)
     return set_error(NUSHT_EINVAL, "kernel_width must be in [0, 16]");
@@ -311,7 +313,12 @@ static int plan_body(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStre
   }
   NUSHT_TRY(make_ffts(p));
   NUSHT_TRY(spread_smem_optin());
-  NUSHT_TRY(tune_points(p, npts, d_pts, s));
+  if (role.bin > 0) {
+    p->pts.bin = role.bin;
+    NUSHT_TRY(setpts_impl(p, npts, d_pts, s));
+  } else {
+    NUSHT_TRY(tune_points(p, npts, d_pts, s));
+  }
   NUSHT_CUDA(cudaStreamSynchronize(s));
   p->sz.nitems = p->leg.nitems;
   p->sz.nitems_total = p->leg.nitems_total;
@@ -324,8 +331,19 @@ extern "C" {
 
 int nusht_plan(nusht_plan_t* out, int lmax, int mmax, int64_t npts, const double* d_pts, double eps, int precision,
                const nusht_opts* opts, nusht_stream_t stream) {
-  return nusht::plan_create(out, lmax, mmax, npts, d_pts, eps, precision, opts, (cudaStream_t)stream,
-                            nusht::PlanRole());
+  nusht_opts o{};
+  if (opts) o = *opts;
+  nusht::PlanRole role;
+  if (out && o.sigma == 0.0 && (o.tune == 1 || o.tune == 2) && npts > 0 && d_pts) {
+    double sg = 0.0;
+    int bin = 0;
+    NUSHT_TRY(nusht::tune_sigma(lmax, mmax, npts, d_pts, eps, precision, &o, (cudaStream_t)stream, &sg, &bin));
+    if (sg > 0.0) {
+      o.sigma = sg;
+      role.bin = bin;
+    }
+  }
+  return nusht::plan_create(out, lmax, mmax, npts, d_pts, eps, precision, &o, (cudaStream_t)stream, role);
 }
 
 }  // extern "C"

@@ -1,4 +1,13 @@
-// tune.cu -- plan-time autotuner of the spreading / interpolation bin size.
+// tune.cu -- plan-time autotuner of the NUFFT: up-sampling factor sigma and
+// spreading / interpolation bin size.
+//
+// sigma (opts.sigma = 0 with opts.tune = 1): for each sigma in {2, 1.5, 1.25}
+// whose accuracy formula width fits the kernel's limit of 16, a NUFFT-only
+// trial plan (its own bin search included) times the sigma-dependent stages
+// of one synthesis + adjoint: deconvolution/padding, the 2D FFTs,
+// interpolation and spreading.  The fastest sigma is cached under the device,
+// precision, lmax, mmax, eps decade and point-count power of two;
+// opts.tune = 2 reuses the cached sigma.
 //
 // opts.tune = 0: bin edge 32 cells.  opts.tune = 1 (search): the plan sorts
 // its points for each candidate bin edge (16, 32, 64 cells), times one
@@ -33,14 +42,11 @@ std::string cache_path() {
   return d + "/nusht_tune.txt";
 }
 
+std::string device_name(int dev);
+
 std::string tune_key(nusht_plan_t p, int64_t npts) {
-  cudaDeviceProp prop;
-  std::string dev = "gpu";
-  if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) dev = prop.name;
-  for (auto& c : dev)
-    if (c == ' ') c = '_';
   std::ostringstream k;
-  k << dev << ":p" << p->precision << ":L" << p->lmax << ":w" << p->sz.w << ":n" << p->sz.n1 << "x" << p->sz.n2
+  k << device_name(p->device) << ":p" << p->precision << ":L" << p->lmax << ":w" << p->sz.w << ":n" << p->sz.n1 << "x" << p->sz.n2
     << ":N" << (npts > 0 ? (int)std::floor(std::log2((double)npts)) : 0);
   return k.str();
 }
@@ -59,7 +65,105 @@ void cache_store(const std::string& key, int bin) {
   if (f) f << key << " " << bin << "\n";
 }
 
+std::string device_name(int dev) {
+  cudaDeviceProp prop;
+  std::string d = "gpu";
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) d = prop.name;
+  for (auto& c : d)
+    if (c == ' ') c = '_';
+  return d;
+}
+
+// one synthesis + adjoint pass of the sigma-dependent stages of a NUFFT-only plan
+int nufft_roundtrip(nusht_plan_t q, void* map, cudaStream_t s) {
+  NUSHT_TRY(deconv_pad(q, s));
+  NUSHT_CUFFT(cufftSetStream(q->fft_c2r, s));
+  NUSHT_CUFFT(q->precision == NUSHT_FP64
+                  ? cufftExecZ2D(q->fft_c2r, (cufftDoubleComplex*)q->fine, (cufftDoubleReal*)q->fine)
+                  : cufftExecC2R(q->fft_c2r, (cufftComplex*)q->fine, (cufftReal*)q->fine));
+  NUSHT_TRY(interp(q, map, s));
+  NUSHT_TRY(spread(q, map, s));
+  NUSHT_CUFFT(cufftSetStream(q->fft_r2c, s));
+  NUSHT_CUFFT(q->precision == NUSHT_FP64
+                  ? cufftExecD2Z(q->fft_r2c, (cufftDoubleReal*)q->fine, (cufftDoubleComplex*)q->fine)
+                  : cufftExecR2C(q->fft_r2c, (cufftReal*)q->fine, (cufftComplex*)q->fine));
+  NUSHT_TRY(deconv_trunc(q, s));
+  return NUSHT_OK;
+}
+
 }  // namespace
+
+int tune_sigma(int lmax, int mmax, int64_t npts, const double* d_pts, double eps, int precision,
+               const nusht_opts* o, cudaStream_t s, double* sigma_out, int* bin_out) {
+  *sigma_out = 0.0;
+  *bin_out = 0;
+  int dev = 0;
+  NUSHT_CUDA(cudaGetDevice(&dev));
+  std::ostringstream k;
+  k << "S:" << device_name(dev) << ":p" << precision << ":L" << lmax << ":m" << mmax << ":e"
+    << (int)std::lround(std::log10(eps)) << ":N" << (int)std::floor(std::log2((double)npts));
+  const std::string key = k.str();
+  if (o->tune == 2) {
+    const int v = cache_lookup(key);
+    if (v >= 120 && v <= 400) *sigma_out = v / 100.0;
+    return NUSHT_OK;
+  }
+  const double cand[3] = {2.0, 1.5, 1.25};
+  const size_t es = precision == NUSHT_FP64 ? 8 : 4;
+  void* map = nullptr;
+  NUSHT_TRY(dev_alloc(&map, (size_t)npts * es, nullptr));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int st = NUSHT_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = set_error(NUSHT_ECUDA, "event");
+  if (st == NUSHT_OK && cudaMemsetAsync(map, 0, (size_t)npts * es, s) != cudaSuccess)
+    st = set_error(NUSHT_ECUDA, "memset");
+  double best_s = 0.0;
+  int best_bin = 0;
+  float best_ms = 1e30f;
+  for (int c = 0; c < 3 && st == NUSHT_OK; ++c) {
+    if (es_width(0.1 * eps, cand[c]) > 16) continue;  // accuracy not reachable within the width limit
+    nusht_opts oc = *o;
+    oc.sigma = cand[c];
+    oc.tune = 1;
+    PlanRole r;
+    r.legendre = false;
+    nusht_plan_t q = nullptr;
+    if ((st = plan_create(&q, lmax, mmax, npts, d_pts, eps, precision, &oc, s, r)) != NUSHT_OK) break;
+    const size_t gbytes = (size_t)(q->sz.mmax + 1) * q->sz.M * (precision == NUSHT_FP64 ? 16 : 8);
+    if (cudaMemsetAsync(q->Ghat, 0, gbytes, s) != cudaSuccess) st = set_error(NUSHT_ECUDA, "memset");
+    if (st == NUSHT_OK) st = nufft_roundtrip(q, map, s);  // warm-up
+    if (st == NUSHT_OK) {
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 2 && st == NUSHT_OK; ++rep) st = nufft_roundtrip(q, map, s);
+      cudaEventRecord(e1, s);
+    }
+    float ms = 0.f;
+    if (st == NUSHT_OK) {
+      if (cudaEventSynchronize(e1) != cudaSuccess)
+        st = set_error(NUSHT_ECUDA, "tuning timer");
+      else
+        cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (st == NUSHT_OK && ms < best_ms) {
+      best_ms = ms;
+      best_s = cand[c];
+      best_bin = q->pts.bin;
+    }
+    cudaStreamSynchronize(s);
+    plan_destroy(q);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  dev_free(map);
+  if (st != NUSHT_OK) return st;
+  if (best_s > 0.0) {
+    cache_store(key, (int)std::lround(best_s * 100.0));
+    *sigma_out = best_s;
+    *bin_out = best_bin;
+  }
+  return NUSHT_OK;
+}
 
 int tune_points(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s) {
   const int mode = p->opts.tune;

@@ -79,12 +79,16 @@ def test_kernel_ft_against_quadrature(nu, w, beta, n):
 
 
 def test_plan_sizes(nu):
-    z = nu.plan_sizes(4095, 1e-10, "fp64")
+    z = nu.plan_sizes(4095, 1e-10, "fp64")  # default sigma 1.5 in FP64
     assert z["M"] == 8192 and z["nrings"] == 4097
-    assert z["n1"] == z["n2"] == 16384
-    assert 10 <= z["w"] <= 13
+    assert z["sigma"] == 1.5 and z["n1"] == z["n2"] == 12288
+    assert 13 <= z["w"] <= 15
+    z = nu.plan_sizes(4095, 1e-10, "fp64", sigma=2.0)
+    assert z["n1"] == z["n2"] == 16384 and 10 <= z["w"] <= 13
+    z = nu.plan_sizes(4095, 1e-5, "mixed")  # default sigma 2 in mixed precision
+    assert z["sigma"] == 2.0 and z["n1"] == 16384 and z["w"] == 7
     z = nu.plan_sizes(63, 1e-10)
-    assert z["M"] % 4 == 0 and z["M"] >= 128 and z["n1"] >= 2 * 127
+    assert z["M"] % 4 == 0 and z["M"] >= 128 and z["n1"] >= 1.5 * 127
     z = nu.plan_sizes(0, 1e-5, "mixed")
     assert z["M"] == 4 and z["n1"] >= 2 * z["w"]
     z = nu.plan_sizes(1023, 1e-5, "mixed", sigma=1.25)

@@ -224,21 +224,30 @@ def test_legendre_table_mode_gl1023(env, prec):
     assert oracle.eps_eff(oracle.synth(a, pts[sel], L), f[sel]) <= TOL[prec]
 
 
-def test_autotuned_bin_size(env, tmp_path, monkeypatch):
-    """tune=1 times bin sizes on the plan's own points and caches the winner;
-    tune=2 reuses it; parity holds whichever bin is chosen."""
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_autotuned_sigma_and_bin_size(env, tmp_path, monkeypatch, prec):
+    """tune=1 times the up-sampling factor and the bin size on the plan's own
+    points and caches the winners; tune=2 reuses them; parity holds whichever
+    are chosen."""
     torch, nu = env
     monkeypatch.setenv("NUSHT_TUNE_CACHE", str(tmp_path / "tune.txt"))
     L, a, pts = W.workload("uniform63")
     dp = dev(torch, pts)
-    p1 = nu.Plan(L, dp, eps=1e-10, tune=1)
-    b = p1.bin_size()
-    assert b in (16, 32, 64)
-    assert (tmp_path / "tune.txt").read_text().strip().endswith(" %d" % b)
-    f = p1.synth(dev(torch, a)).cpu().numpy()
-    assert oracle.eps_eff(oracle.synth(a, pts, L), f) <= 1e-10
+    eps = 1e-10 if prec == "fp64" else 1e-5
+    cd = np.complex128 if prec == "fp64" else np.complex64
+    p1 = nu.Plan(L, dp, eps=eps, precision=prec, tune=1)
+    b, sg = p1.bin_size(), p1.info()["sigma"]
+    assert b in (16, 32, 64) and sg in (1.25, 1.5, 2.0)
+    if prec == "fp64":
+        assert sg != 1.25  # its kernel width for 1e-11 exceeds the limit
+    lines = (tmp_path / "tune.txt").read_text().split("\n")
+    assert any(l.startswith("S:") and l.endswith(" %d" % round(100 * sg)) for l in lines)
+    f = p1.synth(dev(torch, a.astype(cd))).cpu().numpy().astype(np.float64)
+    assert oracle.eps_eff(oracle.synth(a, pts, L), f) <= TOL[prec]
     y = np.random.default_rng(4).standard_normal(pts.shape[0])
-    c = p1.adjoint(dev(torch, y)).cpu().numpy()
-    assert oracle.eps_eff(oracle.adjoint(y, pts, L), c) <= 1e-10
-    p2 = nu.Plan(L, dp, eps=1e-10, tune=2)
-    assert p2.bin_size() == b
+    if prec == "mixed":
+        y = y.astype(np.float32)
+    c = p1.adjoint(dev(torch, y)).cpu().numpy().astype(np.complex128)
+    assert oracle.eps_eff(oracle.adjoint(y.astype(np.float64), pts, L), c) <= TOL[prec]
+    p2 = nu.Plan(L, dp, eps=eps, precision=prec, tune=2)
+    assert p2.bin_size() == b and p2.info()["sigma"] == sg
