@@ -452,8 +452,9 @@ def _kernel_hash() -> str:
     import hashlib
 
     h = hashlib.sha1()
-    with open(os.path.join(ROOT, "paper_2406_14542_gb300", "csrc", "legendre.cu"), "rb") as fh:
-        h.update(fh.read())
+    for f in ("legendre.cu", "recurrence.cuh", "dfloat.cuh", "nusht_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2406_14542_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:12]
 
 

@@ -31,6 +31,7 @@
 
 #include "nusht_internal.cuh"
 #include "recurrence.cuh"
+#include "dfloat.cuh"
 
 namespace nusht {
 
@@ -367,55 +368,6 @@ __global__ void poles_synth_k(const Tin* __restrict__ alm, const double* __restr
 // Relative error per operation ~2^-48; the FP64 pipe then carries only the
 // two recurrence operations per step.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void split_q(double q, float& qh, float& ql) {
-  const int hi = __double2hiint(q);
-  const unsigned lo = (unsigned)__double2loint(q);
-  const int eb = (hi >> 20) & 0x7ff;  // biased exponent
-  const unsigned sign = (unsigned)hi & 0x80000000u;
-  if (eb < 1023 - 126) {  // |q| < 2^-126 (or zero): negligible, flushed
-    qh = 0.0f;
-    ql = 0.0f;
-    return;
-  }
-  // leading 24 significant bits, exactly representable as a float
-  const unsigned mh = ((unsigned)(hi & 0xfffff) << 3) | (lo >> 29);
-  qh = __uint_as_float(sign | ((unsigned)(eb - 1023 + 127) << 23) | mh);
-  // remaining 29 bits r: value r * 2^(e - 52), rounded to 24 bits
-  const float r = __uint2float_rn(lo & 0x1fffffffu);
-  const int ef = eb - 1023 - 52 + 127;
-  const float sc = ef >= 1 ? __uint_as_float((unsigned)ef << 23) : 0.0f;
-  ql = __uint_as_float(__float_as_uint(__fmul_rn(r, sc)) | sign);
-}
-
-// (sh + sl) += (ah + al) * (qh + ql)
-__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float qh, float ql) {
-  const float p = __fmul_rn(ah, qh);
-  const float e = __fmaf_rn(ah, qh, -p);
-  const float t = __fmaf_rn(ah, ql, __fmaf_rn(al, qh, e));
-  const float s = __fadd_rn(sh, p);
-  const float bp = __fsub_rn(s, sh);
-  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-  sl = __fadd_rn(sl, __fadd_rn(err, t));
-  sh = s;
-}
-
-// (ah + al) += (bh + bl)
-__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
-  const float s = __fadd_rn(ah, bh);
-  const float bp = __fsub_rn(s, ah);
-  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bp)), __fsub_rn(bh, bp));
-  al = __fadd_rn(__fadd_rn(al, bl), err);
-  ah = s;
-}
-
-__device__ __forceinline__ double df_value(float h, float l) { return (double)h + (double)l; }
-
-// float pair of a double: h = rn(v), l = rn(v - h)
-__device__ __forceinline__ void df_of(double v, float& h, float& l) {
-  h = __double2float_rn(v);
-  l = __double2float_rn(v - (double)h);
-}
-
 // atilde as double-float complex: (hi_re, lo_re, hi_im, lo_im)
 __global__ void scale_alm_df_k(const double* __restrict__ alm, const double* __restrict__ ahat, int64_t nalm, int lmax,
                                float4* __restrict__ at) {

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "nusht_internal.cuh"
+#include "dfloat.cuh"
 
 namespace nusht {
 
@@ -93,7 +94,7 @@ __global__ void prep_k(const double* __restrict__ pts, int64_t npts, int n1, int
 // offsets (MIXED, kernel evaluated on the fly in float)
 __global__ void gather_k(const double* __restrict__ pts, const int* __restrict__ perm, int64_t npts, int n1, int n2,
                          int w, double beta, int* __restrict__ cell, double* __restrict__ psi,
-                         float* __restrict__ offf, double* __restrict__ xy) {
+                         float2* __restrict__ psid, float* __restrict__ offf, double* __restrict__ xy) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= npts) return;
   const int i = perm[s];
@@ -111,6 +112,19 @@ __global__ void gather_k(const double* __restrict__ pts, const int* __restrict__
     double* ps = psi + s * 2 * w;
     for (int a = 0; a < w; ++a) ps[a] = es_psi((o1 - a) * sc, beta);
     for (int b = 0; b < w; ++b) ps[w + b] = es_psi((o2 - b) * sc, beta);
+  }
+  if (psid) {
+    float2* ps = psid + s * 2 * w;
+    for (int a = 0; a < w; ++a) {
+      const double v = es_psi((o1 - a) * sc, beta);
+      const float h = __double2float_rn(v);
+      ps[a] = make_float2(h, __double2float_rn(v - (double)h));
+    }
+    for (int b = 0; b < w; ++b) {
+      const double v = es_psi((o2 - b) * sc, beta);
+      const float h = __double2float_rn(v);
+      ps[w + b] = make_float2(h, __double2float_rn(v - (double)h));
+    }
   }
   if (offf) {
     offf[2 * s] = (float)o1;
@@ -382,6 +396,135 @@ __global__ void __launch_bounds__(32) spread_k(T* __restrict__ grid, int64_t str
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 mode in double-float (FP32 pipe).  Both kernels work per spreading
+// subproblem (a bin of binsz x binsz first taps, up to SUBMAX points) with the
+// bin's fine-grid tile (bin + halo, wrapped) in shared memory as float pairs:
+//   interpolation: the tile is loaded with coalesced row reads, each double
+//     split once on the way in (integer operations); one thread per point
+//     then reads its w x w taps from shared memory;
+//   spreading: one warp per subproblem, the w x w cells of a point spread over
+//     the lanes (no two lanes share a cell); the subproblem's taps and values
+//     are staged in shared memory first and each point's kernel values are
+//     fetched one point ahead; the tile is flushed as doubles with FP64
+//     atomics, so the r2c FFT input stays FP64.
+// Products are exact float-pair products, sums two-sum accumulations.
+// ---------------------------------------------------------------------------
+constexpr int IDF_THREADS = 128;
+
+__global__ void __launch_bounds__(IDF_THREADS) interp_df_k(const double* __restrict__ grid, int64_t stride, int n1,
+                                                           int n2, int w, int nb2, int binsz,
+                                                           const int* __restrict__ sub, const int* __restrict__ cell,
+                                                           const float2* __restrict__ psi,
+                                                           const int* __restrict__ perm, double* __restrict__ out) {
+  extern __shared__ unsigned char smem_raw[];
+  float2* tile = reinterpret_cast<float2*>(smem_raw);
+  const int tw = binsz + w - 1;
+  const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
+  const int r0 = (bin / nb2) * binsz, c0 = (bin % nb2) * binsz;
+  for (int e = threadIdx.x; e < tw * tw; e += IDF_THREADS) {
+    const int r = e / tw, c = e - r * tw;
+    const int gr = (r0 + r) % n1, gc = (c0 + c) % n2;  // the halo may wrap more than once on tiny grids
+    float h, l;
+    df_split(grid[(int64_t)gr * stride + gc], h, l);
+    tile[e] = make_float2(h, l);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < cnt; q += IDF_THREADS) {
+    const int64_t s = (int64_t)start + q;
+    const int lr = cell[2 * s] - r0, lc = cell[2 * s + 1] - c0;
+    const float2* ps = psi + s * 2 * w;
+    float2 p2[WMAX];
+#pragma unroll
+    for (int b = 0; b < WMAX; ++b)
+      if (b < w) p2[b] = ps[w + b];
+    float ah = 0.f, al = 0.f;
+#pragma unroll
+    for (int a = 0; a < WMAX; ++a) {
+      if (a < w) {
+        const float2* trow = tile + (lr + a) * tw + lc;
+        float ih = 0.f, il = 0.f;
+#pragma unroll
+        for (int b = 0; b < WMAX; ++b)
+          if (b < w) {
+            const float2 u = trow[b];
+            df_mac(ih, il, p2[b].x, p2[b].y, u.x, u.y);
+          }
+        const float2 p1 = ps[a];
+        df_mac(ah, al, p1.x, p1.y, ih, il);
+      }
+    }
+    out[perm[s]] = df_value(ah, al);
+  }
+}
+
+__global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int64_t stride, int n1, int n2, int w,
+                                                  int nb2, int binsz, const int* __restrict__ sub,
+                                                  const int* __restrict__ cell, const float2* __restrict__ psi,
+                                                  const int* __restrict__ perm, const double* __restrict__ f) {
+  extern __shared__ unsigned char smem_raw[];
+  const int tw = binsz + w - 1;
+  float2* tile = reinterpret_cast<float2*>(smem_raw);
+  int2* sp_cell = reinterpret_cast<int2*>(tile + tw * tw);    // [SUBMAX] local first taps
+  float2* sp_f = reinterpret_cast<float2*>(sp_cell + SUBMAX);  // [SUBMAX] values as float pairs
+  const int lane = threadIdx.x;
+  const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
+  const int r0 = (bin / nb2) * binsz, c0 = (bin % nb2) * binsz;
+  for (int t = lane; t < tw * tw; t += 32) tile[t] = make_float2(0.f, 0.f);
+  for (int q = lane; q < cnt; q += 32) {
+    const int64_t s = (int64_t)start + q;
+    sp_cell[q] = make_int2(cell[2 * s] - r0, cell[2 * s + 1] - c0);
+    float2 fv;
+    df_split(f[perm[s]], fv.x, fv.y);
+    sp_f[q] = fv;
+  }
+  __syncwarp();
+  const int nc = w * w;
+  int ca[8], cb[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int idx = lane + 32 * t;
+    ca[t] = idx < nc ? idx / w : 0;
+    cb[t] = idx < nc ? idx % w : 0;
+  }
+  // lanes 0..w-1 hold psi1_a, lanes w..2w-1 psi2_b of the current point
+  float2 kn = make_float2(0.f, 0.f);
+  if (cnt > 0 && lane < 2 * w) kn = psi[(int64_t)start * 2 * w + lane];
+  for (int q = 0; q < cnt; ++q) {
+    float2 kv = kn;
+    if (q + 1 < cnt && lane < 2 * w) kn = psi[((int64_t)start + q + 1) * 2 * w + lane];
+    const int2 lrc = sp_cell[q];
+    if (lane < w) kv = df_mul(kv, sp_f[q]);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (32 * t < nc) {
+        float2 va, vb;
+        va.x = __shfl_sync(FULL, kv.x, ca[t]);
+        va.y = __shfl_sync(FULL, kv.y, ca[t]);
+        vb.x = __shfl_sync(FULL, kv.x, w + cb[t]);
+        vb.y = __shfl_sync(FULL, kv.y, w + cb[t]);
+        if (lane + 32 * t < nc) {
+          float2* cellp = tile + (lrc.x + ca[t]) * tw + (lrc.y + cb[t]);
+          float2 c = *cellp;
+          df_mac(c.x, c.y, va.x, va.y, vb.x, vb.y);
+          *cellp = c;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  __syncwarp();
+  for (int t = lane; t < tw * tw; t += 32) {
+    const float2 v = tile[t];
+    if (v.x != 0.f) {
+      int r = r0 + t / tw, c = c0 + t % tw;
+      while (r >= n1) r -= n1;
+      while (c >= n2) c -= n2;
+      atomicAdd(grid + (int64_t)r * stride + c, df_value(v.x, v.y));
+    }
+  }
+}
+
 // Spreading in float (mixed mode): one thread per point of the subproblem,
 // kernel values evaluated on the fly from the FP32 offsets, w x w native
 // shared-memory float atomics into the bin's tile, one atomic flush.
@@ -439,6 +582,8 @@ int spread_smem_optin() {
   NUSHT_CUDA(cudaFuncSetAttribute(spread_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   NUSHT_CUDA(cudaFuncSetAttribute(spread_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   NUSHT_CUDA(cudaFuncSetAttribute(spread_pt_k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  NUSHT_CUDA(cudaFuncSetAttribute(spread_df_k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx + SUBMAX * 16));
+  NUSHT_CUDA(cudaFuncSetAttribute(interp_df_k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   return NUSHT_OK;
 }
 
@@ -452,6 +597,10 @@ void free_points(nusht_plan_t p) {
   dev_free(d.sub);
   d = PointData();
 }
+
+// FP64 plans run interpolation and spreading in double-float unless the
+// caller asked for FP64 instructions (opts.fp64_contraction)
+static bool nufft_df(nusht_plan_t p) { return p->precision == NUSHT_FP64 && !p->opts.fp64_contraction; }
 
 int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
@@ -523,7 +672,9 @@ int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t 
   NUSHT_TRY(dev_alloc((void**)&d.sub, std::max<size_t>(1, sub.size()) * 4, &p->bytes));
   NUSHT_CUDA(cudaMemcpyAsync(d.perm, perm.data(), (size_t)npts * 4, cudaMemcpyHostToDevice, s));
   if (!sub.empty()) NUSHT_CUDA(cudaMemcpyAsync(d.sub, sub.data(), sub.size() * 4, cudaMemcpyHostToDevice, s));
-  gather_k<<<nblk, tb, 0, s>>>(d_pts, d.perm, npts, z.n1, z.n2, z.w, z.beta, d.cell, dbl ? d.psi : nullptr,
+  const bool dfm = nufft_df(p);
+  gather_k<<<nblk, tb, 0, s>>>(d_pts, d.perm, npts, z.n1, z.n2, z.w, z.beta, d.cell,
+                               dbl && !dfm ? d.psi : nullptr, dfm ? reinterpret_cast<float2*>(d.psi) : nullptr,
                                dbl ? nullptr : d.off, d.xy);
   NUSHT_CUDA(cudaGetLastError());
   NUSHT_CUDA(cudaStreamSynchronize(s));
@@ -565,7 +716,14 @@ int interp(nusht_plan_t p, void* d_map, cudaStream_t s) {
   const int64_t stride = 2 * (z.n2 / 2 + 1);
   const int tb = 128;
   const int nb = (int)((n + tb - 1) / tb);
-  if (p->precision == NUSHT_FP64)
+  if (nufft_df(p)) {
+    if (p->pts.nsub == 0) return NUSHT_OK;
+    const int binsz = p->pts.bin > 0 ? p->pts.bin : 32;
+    const int tw = binsz + z.w - 1;
+    interp_df_k<<<p->pts.nsub, IDF_THREADS, (size_t)tw * tw * 8, s>>>(
+        (const double*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz, p->pts.sub, p->pts.cell,
+        reinterpret_cast<const float2*>(p->pts.psi), p->pts.perm, (double*)d_map);
+  } else if (p->precision == NUSHT_FP64)
     interp_k<double, false><<<nb, tb, 0, s>>>((const double*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
                                               p->pts.cell, p->pts.psi, nullptr, nullptr, p->pts.perm, n,
                                               (double*)d_map, nullptr, nullptr);
@@ -605,7 +763,11 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
   const int binsz = p->pts.bin > 0 ? p->pts.bin : 32;
   const int tw = binsz + z.w - 1;
   const size_t sm = (size_t)tw * tw * es;
-  if (p->precision == NUSHT_FP64)
+  if (nufft_df(p))
+    spread_df_k<<<p->pts.nsub, 32, sm + (size_t)SUBMAX * 16, s>>>((double*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz,
+                                            p->pts.sub, p->pts.cell, reinterpret_cast<const float2*>(p->pts.psi),
+                                            p->pts.perm, (const double*)d_map);
+  else if (p->precision == NUSHT_FP64)
     spread_k<double><<<p->pts.nsub, 32, sm, s>>>((double*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz,
                                                  (float)z.beta, p->pts.sub, p->pts.cell, p->pts.psi, nullptr,
                                                  p->pts.perm, (const double*)d_map);

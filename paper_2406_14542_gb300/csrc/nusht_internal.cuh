@@ -84,7 +84,8 @@ struct PointData {
   int64_t cap = 0;
   int* perm = nullptr;        // sorted index -> caller index
   int* cell = nullptr;        // sorted: first tap (i1, i2) interleaved, wrapped to [0, n)
-  double* psi = nullptr;      // FP64: kernel values [npts][2w] (w along theta, then w along phi)
+  double* psi = nullptr;      // FP64: kernel values [npts][2w] (w along theta, then w along phi);
+                              // as float pairs (hi, lo) when the NUFFT runs in double-float
   double* xy = nullptr;       // sorted coordinates (theta, phi), for the position gradient
   float* off = nullptr;       // MIXED: fractional offsets (t - i) per dim, [2][npts]
   // subproblems for spreading: (bin index, first sorted point, count)

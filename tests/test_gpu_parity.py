@@ -251,3 +251,40 @@ def test_autotuned_sigma_and_bin_size(env, tmp_path, monkeypatch, prec):
     assert oracle.eps_eff(oracle.adjoint(y.astype(np.float64), pts, L), c) <= TOL[prec]
     p2 = nu.Plan(L, dp, eps=eps, precision=prec, tune=2)
     assert p2.bin_size() == b and p2.info()["sigma"] == sg
+
+
+@pytest.mark.parametrize("sigma", [1.5, 2.0])
+def test_fp64_instruction_path_gl1023(env, sigma):
+    """fp64_contraction=1: Legendre sums, interpolation and spreading with FP64
+    instructions (the default runs them as float pairs on the FP32 pipe).
+    Both paths against the oracle on a seeded subset, and against each other
+    on every point and coefficient."""
+    torch, nu = env
+    L, a, pts = W.workload("gl1023")
+    sel = W.subset(pts.shape[0], 3000, seed=11)
+    ref = oracle.synth(a, pts[sel], L)
+    dp = dev(torch, pts)
+    y = dev(torch, np.random.default_rng(12).standard_normal(pts.shape[0]))
+    out = {}
+    for fc in (True, False):
+        plan = nu.Plan(L, dp, eps=1e-10, sigma=sigma, fp64_contraction=fc)
+        f = plan.synth(dev(torch, a)).cpu().numpy()
+        assert oracle.eps_eff(ref, f[sel]) <= 1e-10, fc
+        out[fc] = (f, plan.adjoint(y).cpu().numpy())
+    (f1, c1), (f0, c0) = out[True], out[False]
+    assert np.linalg.norm(f1 - f0) <= 1e-12 * np.linalg.norm(f1)
+    assert np.linalg.norm(c1 - c0) <= 1e-12 * np.linalg.norm(c1)
+
+
+def test_fp64_large_dynamic_range(env):
+    """Float-pair arithmetic keeps FP64-class relative accuracy for coefficients
+    and maps scaled by 1e15 and 1e-15 (the float exponent range is not hit)."""
+    torch, nu = env
+    L, a, pts = W.workload("uniform63")
+    y = np.random.default_rng(13).standard_normal(pts.shape[0])
+    plan = nu.Plan(L, dev(torch, pts), eps=1e-10)
+    for sc in (1e15, 1e-15):
+        f = plan.synth(dev(torch, a * sc)).cpu().numpy()
+        assert oracle.eps_eff(oracle.synth(a * sc, pts, L), f) <= 1e-10, sc
+        c = plan.adjoint(dev(torch, y * sc)).cpu().numpy()
+        assert oracle.eps_eff(oracle.adjoint(y * sc, pts, L), c) <= 1e-10, sc
