@@ -175,6 +175,49 @@ def version() -> str:
     return load().nusht_version().decode()
 
 
+def _msign(lmax: int, mmax: int, like):
+    """(-1)^m for every packed (l, m) entry (m-major, the m = 0 block first),
+    as a real array of the kind of ``like`` (numpy array or torch tensor)."""
+    import numpy as np
+
+    s = np.concatenate([np.full(lmax + 1 - m, -1.0 if m & 1 else 1.0) for m in range(mmax + 1)])
+    try:
+        import torch
+
+        if isinstance(like, torch.Tensor):
+            return torch.as_tensor(s, device=like.device, dtype=like.real.dtype)
+    except ImportError:
+        pass
+    return s
+
+
+def complex_split(alm_pos, alm_neg, lmax: int, mmax: int | None = None):
+    """A complex field F = sum_{l, |m| <= l} a_lm Y_lm as two real fields,
+    F = R + i I (Sec. 2.1 treats real fields; a complex one is two of them).
+
+    ``alm_pos`` holds a_{l,m} and ``alm_neg`` holds a_{l,-m}, both in the packed
+    m-major layout of m >= 0 (the m = 0 entries of ``alm_neg`` are ignored).
+    Returns the real-field coefficients (r, i) in that layout:
+    r_lm = (a_lm + (-1)^m conj(a_{l,-m})) / 2,  i_lm = (a_lm - (-1)^m conj(a_{l,-m})) / (2i)
+    (so r_l0 = Re a_l0, i_l0 = Im a_l0).  Works on numpy arrays and torch tensors."""
+    mmax = lmax if mmax is None else mmax
+    s = _msign(lmax, mmax, alm_pos)
+    neg = alm_neg.copy() if hasattr(alm_neg, "copy") and not hasattr(alm_neg, "clone") else alm_neg.clone()
+    neg[: lmax + 1] = alm_pos[: lmax + 1]
+    t = s * neg.conj()
+    return (alm_pos + t) / 2, (alm_pos - t) / 2j
+
+
+def complex_merge_adjoint(cu, cv, lmax: int, mmax: int | None = None):
+    """Adjoint of a complex map F = u + i v from the real-field adjoints
+    cu = Y^H u and cv = Y^H v (m >= 0):  c_{l,m} = cu + i cv and
+    c_{l,-m} = (-1)^m (conj(cu) + i conj(cv)).  Returns (c_pos, c_neg) in the
+    packed layout of ``complex_split``."""
+    mmax = lmax if mmax is None else mmax
+    s = _msign(lmax, mmax, cu)
+    return cu + 1j * cv, s * (cu.conj() + 1j * cv.conj())
+
+
 def _stream_ptr(stream=None):
     import torch
 
@@ -286,6 +329,21 @@ class Plan:
         _check(self.lib.nusht_adjoint(self.handle, ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                       _stream_ptr(stream)), "nusht_adjoint")
         return out
+
+    def synth_complex(self, alm_pos, alm_neg, stream=None):
+        """Complex field F = sum_{l,|m|<=l} a_lm Y_lm at the points (two real
+        transforms, see ``complex_split``); returns a complex tensor."""
+        r, i = complex_split(alm_pos, alm_neg, self.lmax, self.mmax)
+        fr = self.synth(r.to(self.cdtype).contiguous(), stream=stream)
+        fi = self.synth(i.to(self.cdtype).contiguous(), stream=stream)
+        return fr + 1j * fi
+
+    def adjoint_complex(self, fmap, stream=None):
+        """Adjoint for a complex map: (c_pos, c_neg) with c_{l,+-m} =
+        sum_j F_j conj(Y_{l,+-m}(x_j)) (see ``complex_merge_adjoint``)."""
+        cu = self.adjoint(fmap.real.to(self.rdtype).contiguous(), stream=stream)
+        cv = self.adjoint(fmap.imag.to(self.rdtype).contiguous(), stream=stream)
+        return complex_merge_adjoint(cu, cv, self.lmax, self.mmax)
 
     def synth_grad(self, alm, stream=None):
         """(d f_i / d theta_i, d f_i / d phi_i) by derivative-of-kernel interpolation."""

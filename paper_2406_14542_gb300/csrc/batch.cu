@@ -588,8 +588,9 @@ constexpr int TC_TILE = 128 * 8 * 4;              // one 128 x 8 fp32 operand ti
 constexpr int TC_CHUNK = 8 * TC_TILE;             // AEh AEl AOh AOl BEh BEl BOh BOl
 constexpr int TC_NBUF = 4;
 constexpr int TC_G = 4;                           // chunks per partial accumulation (>= TC_NBUF - 1)
+constexpr int TC_DEPTH = 3;                       // chunks of global loads in flight per thread
 constexpr int TC_SMEM = TC_NBUF * TC_CHUNK + 64;  // + mbarriers, TMEM address
-constexpr int TC_THREADS = 256;
+constexpr int TC_THREADS = 512;
 constexpr uint32_t TC_COLS = 512;
 static_assert(TC_G + 1 >= TC_NBUF, "a partial set is refilled only after its fold");
 static_assert(128 * 129 * 4 <= TC_NBUF * TC_CHUNK, "epilogue exchange fits the chunk buffers");
@@ -639,41 +640,34 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
       : "memory");
 }
 
-// 32 consecutive columns of this warp's 32 TMEM lanes (no wait)
-__device__ __forceinline__ void tc_ld32(uint32_t addr, uint32_t (&r)[32]) {
+// 16 consecutive columns of this warp's 32 TMEM lanes (no wait)
+__device__ __forceinline__ void tc_ld16(uint32_t addr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(addr)
       : "memory");
 }
 
-// row `row` of two operand pairs (hi, lo) starting at tile `tile` of a chunk buffer
-__device__ __forceinline__ void tc_store(unsigned char* buf, int tile, int row, const float (&e)[8],
-                                         const float (&o)[8]) {
+// one operand row (8 values) of one tile pair (hi at `tile`, lo at tile + 1)
+__device__ __forceinline__ void tc_store(unsigned char* buf, int tile, int row, const float (&v)[8]) {
   const int base = (row >> 3) * 256 + (row & 7) * 16;
-  auto put = [&](int tl, const float (&v)[8]) {
-    float h[8], l[8];
+  float h[8], l[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      uint32_t hb;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v[k]));
-      h[k] = __uint_as_float(hb);
-      l[k] = v[k] - h[k];
-    }
-    unsigned char* ph = buf + tl * TC_TILE + base;
-    unsigned char* pl = ph + TC_TILE;
-    *reinterpret_cast<float4*>(ph) = make_float4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<float4*>(ph + 128) = make_float4(h[4], h[5], h[6], h[7]);
-    *reinterpret_cast<float4*>(pl) = make_float4(l[0], l[1], l[2], l[3]);
-    *reinterpret_cast<float4*>(pl + 128) = make_float4(l[4], l[5], l[6], l[7]);
-  };
-  put(tile, e);
-  put(tile + 2, o);
+  for (int k = 0; k < 8; ++k) {
+    uint32_t hb;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v[k]));
+    h[k] = __uint_as_float(hb);
+    l[k] = v[k] - h[k];
+  }
+  unsigned char* ph = buf + tile * TC_TILE + base;
+  unsigned char* pl = ph + TC_TILE;
+  *reinterpret_cast<float4*>(ph) = make_float4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<float4*>(ph + 128) = make_float4(h[4], h[5], h[6], h[7]);
+  *reinterpret_cast<float4*>(pl) = make_float4(l[0], l[1], l[2], l[3]);
+  *reinterpret_cast<float4*>(pl + 128) = make_float4(l[4], l[5], l[6], l[7]);
 }
 
 // TMEM allocation + mbarrier setup; returns the accumulator base address
@@ -704,38 +698,40 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS) : "memory");
 }
 
-// Main loop over `nchunk` chunks.  load(c, e, o) fills this thread's two
-// operand rows of chunk c (threads < 128: A rows; others: B rows).  On return
-// (true) acc[] holds this thread's 128 sums: E (warps 0..3) or O (warps 4..7)
-// of TMEM lane 32 (warp % 4) + lane.  False: a wait gave up.
+// Main loop over `nchunk` chunks.  Staging role: thread t stores operand row
+// t % 128 of tile pair t / 128 (0: A even, 1: A odd, 2: B even, 3: B odd);
+// load(c, v) fills its 8 values of chunk c.  Fold role: warp w owns TMEM
+// lanes 32 (w % 4) .. + 31 and accumulator columns 64 (w / 4) .. + 63
+// (columns 0..127 = E, 128..255 = O).  On return (true) acc[] holds those 64
+// sums; false: a wait gave up.
 template <class Load>
 __device__ __forceinline__ bool tc_mainloop(unsigned char* smem, uint32_t tmem, int nchunk, Load load,
-                                            float (&acc)[128]) {
+                                            float (&acc)[64]) {
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_NBUF * TC_CHUNK);
   const int t = threadIdx.x, warp = t >> 5;
-  const int row = t & 127, tile = t < 128 ? 0 : 4;
-  // this thread's TMEM view: lanes of its warp quarter, E or O columns
-  const uint32_t tview = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (warp < 4 ? 0u : 128u);
+  const int row = t & 127, tile = 2 * (t >> 7);
+  const uint32_t tview = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
 #pragma unroll
-  for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+  for (int j = 0; j < 64; ++j) acc[j] = 0.f;
   bool ok = true;
   int last = -1;  // last chunk whose MMAs were issued
   int pg = 0;     // next group to fold
   auto fold = [&](int g) {
     const uint32_t src = tview + (uint32_t)((g & 1) * 256);
 #pragma unroll
-    for (int c0 = 0; c0 < 128; c0 += 32) {
-      uint32_t r[32];
-      tc_ld32(src + c0, r);
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      uint32_t r[16];
+      tc_ld16(src + c0, r);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+      for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(r[j]);
     }
   };
-  float e0[8], o0[8], e1[8], o1[8];
-  if (nchunk > 0) load(0, e0, o0);
-  if (nchunk > 1) load(1, e1, o1);
-  auto step = [&](int c, float (&e)[8], float (&o)[8]) {
+  float v0[8], v1[8], v2[8];
+  if (nchunk > 0) load(0, v0);
+  if (nchunk > 1) load(1, v1);
+  if (nchunk > 2) load(2, v2);
+  auto step = [&](int c, float (&v)[8]) {
     const int buf = c % TC_NBUF;
     unsigned char* bp = smem + buf * TC_CHUNK;
     if (c >= TC_NBUF && ok) {  // chunk c - NBUF's MMAs (and all before them) have completed
@@ -746,8 +742,8 @@ __device__ __forceinline__ bool tc_mainloop(unsigned char* smem, uint32_t tmem, 
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       }
     }
-    tc_store(bp, tile, row, e, o);
-    if (c + 2 < nchunk) load(c + 2, e, o);
+    tc_store(bp, tile, row, v);
+    if (c + TC_DEPTH < nchunk) load(c + TC_DEPTH, v);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     ok = __syncthreads_and(ok);
     if (!ok) return;
@@ -768,9 +764,10 @@ __device__ __forceinline__ bool tc_mainloop(unsigned char* smem, uint32_t tmem, 
                    : "memory");
     }
   };
-  for (int c = 0; c < nchunk; c += 2) {
-    step(c, e0, o0);
-    if (c + 1 < nchunk) step(c + 1, e1, o1);
+  for (int c = 0; c < nchunk; c += 3) {
+    step(c, v0);
+    if (c + 1 < nchunk) step(c + 1, v1);
+    if (c + 2 < nchunk) step(c + 2, v2);
   }
   // the last commit covers every MMA issued before it
   bool done = last >= 0 ? mbar_wait(smem_u32(&bars[last % TC_NBUF]), (uint32_t)((last / TC_NBUF) & 1)) : true;
@@ -791,7 +788,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bucket_synth_tc_k(BucketArgs a,
                                                                    float2* __restrict__ G, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   if ((int)blockIdx.x >= nitems || *(volatile int*)status) return;
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int v = titems[blockIdx.x];
   const int m = v >> 16, u = v & 0xffff;
   const longlong2 of = toffs[blockIdx.x];
@@ -799,46 +796,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bucket_synth_tc_k(BucketArgs a,
   const int mb = idx_lm(L, 0, m);
   const int nrow = L - m + 1;
   const int nchunk = (nrow + 15) / 16;
-  const int r = t & 127;
-  // A rows: ring pair r of the two tiles; B rows: column r of the coefficients
+  const int r = t & 127, part = t >> 7, par = part & 1;
+  // A rows (parts 0, 1): ring pair r of the two tiles; B rows (parts 2, 3):
+  // coefficient column r; degrees of parity `par`
   const long long off = (r < 64) ? of.x : of.y;
-  const float* src = t < 128 ? (off >= 0 ? P + off + (r & 63) : nullptr)
-                             : reinterpret_cast<const float*>(atb + (size_t)(mb + m) * BK_MAXB) + r;
-  const size_t stride = t < 128 ? (size_t)BS_PAIRS : (size_t)BK_COLS;
+  const float* src = part < 2 ? (off >= 0 ? P + off + (r & 63) : nullptr)
+                              : reinterpret_cast<const float*>(atb + (size_t)(mb + m) * BK_MAXB) + r;
+  const size_t stride = part < 2 ? (size_t)BS_PAIRS : (size_t)BK_COLS;
   const uint32_t tmem = tc_setup(tc_smem);
-  float acc[128];
+  float acc[64];
   const bool ok = tc_mainloop(
       tc_smem, tmem, nchunk,
-      [&](int c, float (&e)[8], float (&o)[8]) {
+      [&](int c, float (&x)[8]) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const int re = 16 * c + 2 * k, ro = re + 1;
-          e[k] = (src && re < nrow) ? __ldg(src + (size_t)re * stride) : 0.f;
-          o[k] = (src && ro < nrow) ? __ldg(src + (size_t)ro * stride) : 0.f;
+          const int rr = 16 * c + 2 * k + par;
+          x[k] = (src && rr < nrow) ? __ldg(src + (size_t)rr * stride) : 0.f;
         }
       },
       acc);
   if (!ok) {
     if (t == 0) atomicExch(status, 1);
   } else {
-    // O sums through shared memory (row stride 129: conflict-free)
+    // warps 8..15 (O sums) hand theirs over through shared memory (row
+    // stride 129: conflict-free); warps 0..7 form north = E + O and
+    // south = E - O for their 32 members
     float* xs = reinterpret_cast<float*>(tc_smem);
-    if (warp >= 4)
+    const int lrow = (warp & 3) * 32 + lane;  // ring pair within the block
+    const int cb = warp >> 2;                 // column block of 64
+    if (cb >= 2)
 #pragma unroll
-      for (int j = 0; j < 128; ++j) xs[r * 129 + j] = acc[j];
+      for (int j = 0; j < 64; ++j) xs[lrow * 129 + (cb - 2) * 64 + j] = acc[j];
     __syncthreads();
-    if (warp < 4) {
+    if (cb < 2) {
       const int M = a.M;
       const float sg = (m & 1) ? -1.f : 1.f;
-      const int jn = 1 + u * 128 + r;
+      const int jn = 1 + u * 128 + lrow;
       const int js = M / 2 - jn;
       if (jn <= a.npairs) {
 #pragma unroll
-        for (int slot = 0; slot < BK_MAXB; ++slot) {  // static acc[] indices
+        for (int q = 0; q < 32; ++q) {  // static acc[] indices
+          const int slot = cb * 32 + q;
           if (slot >= a.B || m > a.memberL[slot]) continue;
-          const float oe = xs[r * 129 + 2 * slot], oi = xs[r * 129 + 2 * slot + 1];
+          const float oe = xs[lrow * 129 + 2 * slot], oi = xs[lrow * 129 + 2 * slot + 1];
           float2* rowp = G + ((size_t)slot * (L + 1) + m) * M;
-          const float ee = acc[2 * slot], ei = acc[2 * slot + 1];
+          const float ee = acc[2 * q], ei = acc[2 * q + 1];
           const float2 fn = make_float2(ee + oe, ei + oi);
           rowp[jn] = fn;
           rowp[M - jn] = make_float2(sg * fn.x, sg * fn.y);
@@ -855,9 +857,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bucket_synth_tc_k(BucketArgs a,
 }
 
 // adjoint: block = (order m, rows r0 .. r0 + 255 of l - m, r0 a multiple of
-// 256); TMEM lane d holds the even row r0 + 2d and the odd row r0 + 2d + 1;
-// K runs over the order's kept table tiles (items[mfirst[m] .. mfirst[m + 1])),
-// 8 ring pairs per chunk
+// 256); TMEM lane d holds the even row r0 + 2d (D_E) and the odd row
+// r0 + 2d + 1 (D_O); K runs over the order's kept table tiles
+// (items[mfirst[m] .. mfirst[m + 1])), 8 ring pairs per chunk
 __global__ void __launch_bounds__(TC_THREADS, 1) bucket_adj_tc_k(BucketArgs a, const int* __restrict__ items,
                                                                  const int64_t* __restrict__ offs,
                                                                  const int* __restrict__ mfirst,
@@ -867,7 +869,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bucket_adj_tc_k(BucketArgs a, c
                                                                  int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   if ((int)blockIdx.x >= nwork || *(volatile int*)status) return;
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int2 wk = work[blockIdx.x];
   const int m = wk.x, r0 = wk.y;
   const int L = a.lmax;
@@ -875,49 +877,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) bucket_adj_tc_k(BucketArgs a, c
   const int nrow = L - m + 1;
   const int i0 = mfirst[m], i1 = mfirst[m + 1];
   const int nchunk = (i1 - i0) * (BS_PAIRS / 8);
-  const int r = t & 127;
-  const int re = r0 + 2 * r, ro = re + 1;
+  const int r = t & 127, part = t >> 7, par = part & 1;
+  const int rr = r0 + 2 * r + par;  // A rows: this degree row (l - m)
   const uint32_t tmem = tc_setup(tc_smem);
-  float acc[128];
+  float acc[64];
   const bool ok = tc_mainloop(
       tc_smem, tmem, nchunk,
-      [&](int c, float (&e)[8], float (&o)[8]) {
+      [&](int c, float (&x)[8]) {
         const int it = i0 + (c >> 3), j = c & 7;
-        if (t < 128) {  // A rows: degrees re (E) and ro (O), ring pairs 8j .. 8j + 7 of the tile
-          const float* Pi = P + offs[it] + 8 * j;
-          float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0, y0 = x0, y1 = x0;
-          if (re < nrow) {
-            x0 = __ldg(reinterpret_cast<const float4*>(Pi + (size_t)re * BS_PAIRS));
-            x1 = __ldg(reinterpret_cast<const float4*>(Pi + (size_t)re * BS_PAIRS + 4));
+        if (part < 2) {  // A row: degree row rr, ring pairs 8j .. 8j + 7 of the tile
+          float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+          if (rr < nrow) {
+            const float* Pi = P + offs[it] + (size_t)rr * BS_PAIRS + 8 * j;
+            x0 = __ldg(reinterpret_cast<const float4*>(Pi));
+            x1 = __ldg(reinterpret_cast<const float4*>(Pi + 4));
           }
-          if (ro < nrow) {
-            y0 = __ldg(reinterpret_cast<const float4*>(Pi + (size_t)ro * BS_PAIRS));
-            y1 = __ldg(reinterpret_cast<const float4*>(Pi + (size_t)ro * BS_PAIRS + 4));
-          }
-          e[0] = x0.x; e[1] = x0.y; e[2] = x0.z; e[3] = x0.w;
-          e[4] = x1.x; e[5] = x1.y; e[6] = x1.z; e[7] = x1.w;
-          o[0] = y0.x; o[1] = y0.y; o[2] = y0.z; o[3] = y0.w;
-          o[4] = y1.x; o[5] = y1.y; o[6] = y1.z; o[7] = y1.w;
-        } else {  // B rows: column r of S_E and S_O for the same 8 ring pairs
+          x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
+          x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
+        } else {  // B row: column r of S_E (part 2) or S_O (part 3), same ring pairs
           const int p0 = (items[it] & 0xffff) * BS_PAIRS + 8 * j;
-          const float* Sp = S + ((size_t)m * a.npairs + p0) * 2 * BK_COLS + r;
+          const float* Sp = S + ((size_t)m * a.npairs + p0) * 2 * BK_COLS + par * BK_COLS + r;
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const bool in = p0 + k < a.npairs;
-            e[k] = in ? __ldg(Sp + (size_t)k * 2 * BK_COLS) : 0.f;
-            o[k] = in ? __ldg(Sp + (size_t)k * 2 * BK_COLS + BK_COLS) : 0.f;
-          }
+          for (int k = 0; k < 8; ++k) x[k] = p0 + k < a.npairs ? __ldg(Sp + (size_t)k * 2 * BK_COLS) : 0.f;
         }
       },
       acc);
   if (!ok) {
     if (t == 0) atomicExch(status, 1);
   } else {
-    const int l = m + re + (warp < 4 ? 0 : 1);
+    const int cb = warp >> 2;
+    const int l = m + r0 + 2 * ((warp & 3) * 32 + lane) + (cb >> 1);
     if (l <= L) {
-      float* dst = cacc + (size_t)(mb + l) * BK_COLS;
+      float* dst = cacc + (size_t)(mb + l) * BK_COLS + (cb & 1) * 64;
 #pragma unroll
-      for (int j = 0; j < 128; j += 4)
+      for (int j = 0; j < 64; j += 4)
         *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
     }
   }

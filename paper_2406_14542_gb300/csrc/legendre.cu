@@ -480,7 +480,7 @@ __device__ __forceinline__ void df4_add(float4& a4, const float4 b4) {
   df_add(a4.z, a4.w, b4.z, b4.w);
 }
 
-__global__ void __launch_bounds__(128) legendre_adj_df_k(LegArgs a, const double2* __restrict__ Gt,
+__global__ void __launch_bounds__(128, 5) legendre_adj_df_k(LegArgs a, const double2* __restrict__ Gt,
                                                          float4* __restrict__ partial, int nitems, int64_t nalm) {
   const int lane = threadIdx.x & 31;
   const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -493,7 +493,11 @@ __global__ void __launch_bounds__(128) legendre_adj_df_k(LegArgs a, const double
   const double sg = (m & 1) ? -1.0 : 1.0;
   const double2* row = Gt + (size_t)m * M;
   Chain ch[LEG_K];
-  float4 SE[LEG_K], SO[LEG_K];  // double-float (hi_re, lo_re, hi_im, lo_im)
+  // folded spectrum per chain as double-float (hi_re, lo_re, hi_im, lo_im),
+  // even / odd l - m; kept in shared memory to leave registers for occupancy
+  __shared__ float4 sS[2][LEG_K][128];
+  float4* SE = &sS[0][0][threadIdx.x];
+  float4* SO = &sS[1][0][threadIdx.x];
 #pragma unroll
   for (int k = 0; k < LEG_K; ++k) {
     const int jn = 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane;
@@ -508,10 +512,13 @@ __global__ void __launch_bounds__(128) legendre_adj_df_k(LegArgs a, const double
         fs = make_double2(h0.x + sg * h1.x, h0.y + sg * h1.y);
       }
     }
-    df_of(fn.x + fs.x, SE[k].x, SE[k].y);
-    df_of(fn.y + fs.y, SE[k].z, SE[k].w);
-    df_of(fn.x - fs.x, SO[k].x, SO[k].y);
-    df_of(fn.y - fs.y, SO[k].z, SO[k].w);
+    float4 e4, o4;
+    df_of(fn.x + fs.x, e4.x, e4.y);
+    df_of(fn.y + fs.y, e4.z, e4.w);
+    df_of(fn.x - fs.x, o4.x, o4.y);
+    df_of(fn.y - fs.y, o4.z, o4.w);
+    SE[k * 128] = e4;
+    SO[k * 128] = o4;
   }
   float4* out = partial + (size_t)blk * nalm + mb;
   for (int base = m; base <= L; base += 8) {
@@ -532,7 +539,7 @@ __global__ void __launch_bounds__(128) legendre_adj_df_k(LegArgs a, const double
           if (ch[k].E == 0) {
             float qh, ql;
             split_q(ch[k].q1, qh, ql);
-            const float4 S = (st & 1) ? SO[k] : SE[k];
+            const float4 S = (st & 1) ? SO[k * 128] : SE[k * 128];
             df_mac(v[st].x, v[st].y, S.x, S.y, qh, ql);
             df_mac(v[st].z, v[st].w, S.z, S.w, qh, ql);
           }

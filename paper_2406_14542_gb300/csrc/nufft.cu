@@ -412,14 +412,15 @@ __global__ void __launch_bounds__(32) spread_k(T* __restrict__ grid, int64_t str
 // ---------------------------------------------------------------------------
 constexpr int IDF_THREADS = 128;
 
+template <int W>
 __global__ void __launch_bounds__(IDF_THREADS) interp_df_k(const double* __restrict__ grid, int64_t stride, int n1,
-                                                           int n2, int w, int nb2, int binsz,
-                                                           const int* __restrict__ sub, const int* __restrict__ cell,
+                                                           int n2, int nb2, int binsz, const int* __restrict__ sub,
+                                                           const int* __restrict__ cell,
                                                            const float2* __restrict__ psi,
                                                            const int* __restrict__ perm, double* __restrict__ out) {
   extern __shared__ unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);
-  const int tw = binsz + w - 1;
+  const int tw = binsz + W - 1;
   const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
   const int r0 = (bin / nb2) * binsz, c0 = (bin % nb2) * binsz;
   for (int e = threadIdx.x; e < tw * tw; e += IDF_THREADS) {
@@ -433,37 +434,36 @@ __global__ void __launch_bounds__(IDF_THREADS) interp_df_k(const double* __restr
   for (int q = threadIdx.x; q < cnt; q += IDF_THREADS) {
     const int64_t s = (int64_t)start + q;
     const int lr = cell[2 * s] - r0, lc = cell[2 * s + 1] - c0;
-    const float2* ps = psi + s * 2 * w;
-    float2 p2[WMAX];
+    const float2* ps = psi + s * 2 * W;
+    float2 p2[W];
 #pragma unroll
-    for (int b = 0; b < WMAX; ++b)
-      if (b < w) p2[b] = ps[w + b];
+    for (int b = 0; b < W; ++b) p2[b] = ps[W + b];
     float ah = 0.f, al = 0.f;
+#pragma unroll 1
+    for (int a = 0; a < W; ++a) {
+      const float2* trow = tile + (lr + a) * tw + lc;
+      float ih = 0.f, il = 0.f;
 #pragma unroll
-    for (int a = 0; a < WMAX; ++a) {
-      if (a < w) {
-        const float2* trow = tile + (lr + a) * tw + lc;
-        float ih = 0.f, il = 0.f;
-#pragma unroll
-        for (int b = 0; b < WMAX; ++b)
-          if (b < w) {
-            const float2 u = trow[b];
-            df_mac(ih, il, p2[b].x, p2[b].y, u.x, u.y);
-          }
-        const float2 p1 = ps[a];
-        df_mac(ah, al, p1.x, p1.y, ih, il);
+      for (int b = 0; b < W; ++b) {
+        const float2 u = trow[b];
+        df_mac(ih, il, p2[b].x, p2[b].y, u.x, u.y);
       }
+      const float2 p1 = ps[a];
+      df_mac(ah, al, p1.x, p1.y, ih, il);
     }
     out[perm[s]] = df_value(ah, al);
   }
 }
 
-__global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int64_t stride, int n1, int n2, int w,
-                                                  int nb2, int binsz, const int* __restrict__ sub,
+template <int W>
+__global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int64_t stride, int n1, int n2, int nb2,
+                                                  int binsz, const int* __restrict__ sub,
                                                   const int* __restrict__ cell, const float2* __restrict__ psi,
                                                   const int* __restrict__ perm, const double* __restrict__ f) {
+  constexpr int NC = W * W;
+  constexpr int NR = (NC + 31) / 32;  // rounds of 32 cells per point
   extern __shared__ unsigned char smem_raw[];
-  const int tw = binsz + w - 1;
+  const int tw = binsz + W - 1;
   float2* tile = reinterpret_cast<float2*>(smem_raw);
   int2* sp_cell = reinterpret_cast<int2*>(tile + tw * tw);    // [SUBMAX] local first taps
   float2* sp_f = reinterpret_cast<float2*>(sp_cell + SUBMAX);  // [SUBMAX] values as float pairs
@@ -479,38 +479,41 @@ __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int
     sp_f[q] = fv;
   }
   __syncwarp();
-  const int nc = w * w;
-  int ca[8], cb[8];
+  // this lane's cells of a point: (ca, cb) = divmod(lane + 32 t, W); offset in the tile
+  int ca[NR], cb[NR], co[NR];
 #pragma unroll
-  for (int t = 0; t < 8; ++t) {
+  for (int t = 0; t < NR; ++t) {
     const int idx = lane + 32 * t;
-    ca[t] = idx < nc ? idx / w : 0;
-    cb[t] = idx < nc ? idx % w : 0;
+    ca[t] = idx < NC ? idx / W : 0;
+    cb[t] = idx < NC ? idx % W : 0;
+    co[t] = ca[t] * tw + cb[t];
   }
-  // lanes 0..w-1 hold psi1_a, lanes w..2w-1 psi2_b of the current point
+  // lanes 0..W-1 hold psi1_a, lanes W..2W-1 psi2_b of the current point
   float2 kn = make_float2(0.f, 0.f);
-  if (cnt > 0 && lane < 2 * w) kn = psi[(int64_t)start * 2 * w + lane];
+  if (cnt > 0 && lane < 2 * W) kn = psi[(int64_t)start * 2 * W + lane];
   for (int q = 0; q < cnt; ++q) {
     float2 kv = kn;
-    if (q + 1 < cnt && lane < 2 * w) kn = psi[((int64_t)start + q + 1) * 2 * w + lane];
+    if (q + 1 < cnt && lane < 2 * W) kn = psi[((int64_t)start + q + 1) * 2 * W + lane];
     const int2 lrc = sp_cell[q];
-    if (lane < w) kv = df_mul(kv, sp_f[q]);
+    if (lane < W) kv = df_mul(kv, sp_f[q]);
+    float2* base = tile + lrc.x * tw + lrc.y;
+    // a point's cells are distinct: read them all, update, write them all
+    float2 c[NR];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      if (32 * t < nc) {
-        float2 va, vb;
-        va.x = __shfl_sync(FULL, kv.x, ca[t]);
-        va.y = __shfl_sync(FULL, kv.y, ca[t]);
-        vb.x = __shfl_sync(FULL, kv.x, w + cb[t]);
-        vb.y = __shfl_sync(FULL, kv.y, w + cb[t]);
-        if (lane + 32 * t < nc) {
-          float2* cellp = tile + (lrc.x + ca[t]) * tw + (lrc.y + cb[t]);
-          float2 c = *cellp;
-          df_mac(c.x, c.y, va.x, va.y, vb.x, vb.y);
-          *cellp = c;
-        }
-      }
+    for (int t = 0; t < NR; ++t)
+      if (lane + 32 * t < NC) c[t] = base[co[t]];
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {
+      float2 va, vb;
+      va.x = __shfl_sync(FULL, kv.x, ca[t]);
+      va.y = __shfl_sync(FULL, kv.y, ca[t]);
+      vb.x = __shfl_sync(FULL, kv.x, W + cb[t]);
+      vb.y = __shfl_sync(FULL, kv.y, W + cb[t]);
+      if (lane + 32 * t < NC) df_mac(c[t].x, c[t].y, va.x, va.y, vb.x, vb.y);
     }
+#pragma unroll
+    for (int t = 0; t < NR; ++t)
+      if (lane + 32 * t < NC) base[co[t]] = c[t];
     __syncwarp();
   }
   __syncwarp();
@@ -523,6 +526,49 @@ __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int
       atomicAdd(grid + (int64_t)r * stride + c, df_value(v.x, v.y));
     }
   }
+}
+
+// launch f<W> for the runtime width w (2 <= w <= WMAX)
+#define NUSHT_W_DISPATCH(w, F, ...) \
+  switch (w) {                      \
+    case 2: F<2>(__VA_ARGS__); break;   \
+    case 3: F<3>(__VA_ARGS__); break;   \
+    case 4: F<4>(__VA_ARGS__); break;   \
+    case 5: F<5>(__VA_ARGS__); break;   \
+    case 6: F<6>(__VA_ARGS__); break;   \
+    case 7: F<7>(__VA_ARGS__); break;   \
+    case 8: F<8>(__VA_ARGS__); break;   \
+    case 9: F<9>(__VA_ARGS__); break;   \
+    case 10: F<10>(__VA_ARGS__); break; \
+    case 11: F<11>(__VA_ARGS__); break; \
+    case 12: F<12>(__VA_ARGS__); break; \
+    case 13: F<13>(__VA_ARGS__); break; \
+    case 14: F<14>(__VA_ARGS__); break; \
+    case 15: F<15>(__VA_ARGS__); break; \
+    default: F<16>(__VA_ARGS__); break; \
+  }
+
+template <int W>
+void launch_interp_df(int nsub, size_t sm, cudaStream_t s, const double* grid, int64_t stride, int n1, int n2,
+                      int nb2, int binsz, const int* sub, const int* cell, const float2* psi, const int* perm,
+                      double* out) {
+  interp_df_k<W><<<nsub, IDF_THREADS, sm, s>>>(grid, stride, n1, n2, nb2, binsz, sub, cell, psi, perm, out);
+}
+
+template <int W>
+void launch_spread_df(int nsub, size_t sm, cudaStream_t s, double* grid, int64_t stride, int n1, int n2, int nb2,
+                      int binsz, const int* sub, const int* cell, const float2* psi, const int* perm,
+                      const double* f) {
+  spread_df_k<W><<<nsub, 32, sm, s>>>(grid, stride, n1, n2, nb2, binsz, sub, cell, psi, perm, f);
+}
+
+template <int W>
+void optin_df(int* st) {
+  const int mx = 80 * 80 * 8;
+  if (cudaFuncSetAttribute(spread_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx + SUBMAX * 16) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(interp_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
+    *st = 1;
 }
 
 // Spreading in float (mixed mode): one thread per point of the subproblem,
@@ -582,8 +628,9 @@ int spread_smem_optin() {
   NUSHT_CUDA(cudaFuncSetAttribute(spread_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   NUSHT_CUDA(cudaFuncSetAttribute(spread_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   NUSHT_CUDA(cudaFuncSetAttribute(spread_pt_k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  NUSHT_CUDA(cudaFuncSetAttribute(spread_df_k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx + SUBMAX * 16));
-  NUSHT_CUDA(cudaFuncSetAttribute(interp_df_k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  int bad = 0;
+  for (int w = 2; w <= WMAX; ++w) NUSHT_W_DISPATCH(w, optin_df, &bad);
+  if (bad) return set_error(NUSHT_ECUDA, "shared-memory opt-in for the double-float NUFFT kernels");
   return NUSHT_OK;
 }
 
@@ -720,9 +767,9 @@ int interp(nusht_plan_t p, void* d_map, cudaStream_t s) {
     if (p->pts.nsub == 0) return NUSHT_OK;
     const int binsz = p->pts.bin > 0 ? p->pts.bin : 32;
     const int tw = binsz + z.w - 1;
-    interp_df_k<<<p->pts.nsub, IDF_THREADS, (size_t)tw * tw * 8, s>>>(
-        (const double*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz, p->pts.sub, p->pts.cell,
-        reinterpret_cast<const float2*>(p->pts.psi), p->pts.perm, (double*)d_map);
+    NUSHT_W_DISPATCH(z.w, launch_interp_df, p->pts.nsub, (size_t)tw * tw * 8, s, (const double*)p->fine, stride,
+                     z.n1, z.n2, p->pts.nbins2, binsz, p->pts.sub, p->pts.cell,
+                     reinterpret_cast<const float2*>(p->pts.psi), p->pts.perm, (double*)d_map);
   } else if (p->precision == NUSHT_FP64)
     interp_k<double, false><<<nb, tb, 0, s>>>((const double*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
                                               p->pts.cell, p->pts.psi, nullptr, nullptr, p->pts.perm, n,
@@ -763,11 +810,11 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
   const int binsz = p->pts.bin > 0 ? p->pts.bin : 32;
   const int tw = binsz + z.w - 1;
   const size_t sm = (size_t)tw * tw * es;
-  if (nufft_df(p))
-    spread_df_k<<<p->pts.nsub, 32, sm + (size_t)SUBMAX * 16, s>>>((double*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz,
-                                            p->pts.sub, p->pts.cell, reinterpret_cast<const float2*>(p->pts.psi),
-                                            p->pts.perm, (const double*)d_map);
-  else if (p->precision == NUSHT_FP64)
+  if (nufft_df(p)) {
+    NUSHT_W_DISPATCH(z.w, launch_spread_df, p->pts.nsub, sm + (size_t)SUBMAX * 16, s, (double*)p->fine, stride, z.n1,
+                     z.n2, p->pts.nbins2, binsz, p->pts.sub, p->pts.cell,
+                     reinterpret_cast<const float2*>(p->pts.psi), p->pts.perm, (const double*)d_map);
+  } else if (p->precision == NUSHT_FP64)
     spread_k<double><<<p->pts.nsub, 32, sm, s>>>((double*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz,
                                                  (float)z.beta, p->pts.sub, p->pts.cell, p->pts.psi, nullptr,
                                                  p->pts.perm, (const double*)d_map);

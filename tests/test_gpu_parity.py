@@ -288,3 +288,39 @@ def test_fp64_large_dynamic_range(env):
         assert oracle.eps_eff(oracle.synth(a * sc, pts, L), f) <= 1e-10, sc
         c = plan.adjoint(dev(torch, y * sc)).cpu().numpy()
         assert oracle.eps_eff(oracle.adjoint(y * sc, pts, L), c) <= 1e-10, sc
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_execute_calls_capture_into_cuda_graph(env, prec):
+    """nusht_synth / nusht_adjoint are stream-ordered, allocate nothing and do
+    not synchronise, so they can be captured into a CUDA graph; replaying it
+    gives the eager results."""
+    torch, nu = env
+    L, a, pts = W.workload("uniform63")
+    cd = torch.complex128 if prec == "fp64" else torch.complex64
+    rd = torch.float64 if prec == "fp64" else torch.float32
+    plan = nu.Plan(L, dev(torch, pts), eps=TOL[prec], precision=prec)
+    ad = dev(torch, a, cd)
+    y = dev(torch, np.random.default_rng(9).standard_normal(pts.shape[0]), rd)
+    f = torch.empty(pts.shape[0], dtype=rd, device="cuda")
+    c = torch.empty(plan.nalm, dtype=cd, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.synth(ad, out=f)
+        plan.adjoint(y, out=c)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    f_eager, c_eager = f.clone(), c.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.synth(ad, out=f)
+        plan.adjoint(y, out=c)
+    f.zero_()
+    c.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(f, f_eager)
+    rel = (torch.linalg.norm(c - c_eager) / torch.linalg.norm(c_eager)).item()
+    # the adjoint's spreading adds with atomics: equal to rounding in the plan's precision
+    assert rel <= (1e-12 if prec == "fp64" else 1e-6)
