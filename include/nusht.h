@@ -89,9 +89,9 @@ typedef struct {
   double sigma;      /* fine-grid up-sampling factor in [1.2, 4]; 0 = default: 1.5 for
                         NUSHT_FP64 (the FP64 2D FFT dominates), 2.0 for NUSHT_MIXED; with
                         tune = 1 nusht_plan times sigma in {2, 1.5, 1.25} instead (each one
-                        whose kernel width for eps fits the limit of 16) and caches the
+                        whose kernel width for eps fits the limit of 20) and caches the
                         winner, tune = 2 takes the cached one */
-  int kernel_width;  /* ES kernel width w override; 0 = from eps and sigma */
+  int kernel_width;  /* ES kernel width w override in [2, 20]; 0 = from eps and sigma */
   int profile;       /* 1 = record per-stage CUDA-event times (nusht_stage_times) */
   int deterministic; /* reserved; synthesis is bit-reproducible, the adjoint's spreading
                         flush adds tile halos with atomics (rounding-level order effects) */

@@ -43,8 +43,12 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al,
   const float s = __fadd_rn(sh, p);
   const float bp = __fsub_rn(s, sh);
   const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-  sl = __fadd_rn(sl, __fadd_rn(err, t));
-  sh = s;
+  const float l = __fadd_rn(sl, __fadd_rn(err, t));
+  // renormalise (fast two-sum, |s| >= |l|): lo stays within half an ulp of
+  // hi, so its rounding error per step is ~2^-48 of the sum and does not
+  // grow with the number of accumulated terms
+  sh = __fadd_rn(s, l);
+  sl = __fsub_rn(l, __fsub_rn(sh, s));
 }
 
 // (ah + al) += (bh + bl)
@@ -52,8 +56,9 @@ __device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl)
   const float s = __fadd_rn(ah, bh);
   const float bp = __fsub_rn(s, ah);
   const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bp)), __fsub_rn(bh, bp));
-  al = __fadd_rn(__fadd_rn(al, bl), err);
-  ah = s;
+  const float l = __fadd_rn(__fadd_rn(al, bl), err);
+  ah = __fadd_rn(s, l);  // renormalise, as in df_mac
+  al = __fsub_rn(l, __fsub_rn(ah, s));
 }
 
 __device__ __forceinline__ double df_value(float h, float l) { return (double)h + (double)l; }

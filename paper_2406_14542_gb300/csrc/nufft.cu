@@ -28,7 +28,8 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int SUBMAX = 256;   // points per spreading subproblem
-constexpr int WMAX = 16;
+constexpr int WMAX = ES_WMAX;
+constexpr int NRMAX = (WMAX * WMAX + 31) / 32;  // rounds of 32 cells for a w x w footprint
 
 template <typename T>
 struct V2;
@@ -347,9 +348,9 @@ __global__ void __launch_bounds__(32) spread_k(T* __restrict__ grid, int64_t str
   __syncwarp();
   // this lane's cells of a point: (a, b) for idx = lane + 32 t < w^2
   const int nc = w * w;
-  int ca[8], cb[8];
+  int ca[NRMAX], cb[NRMAX];
 #pragma unroll
-  for (int t = 0; t < 8; ++t) {
+  for (int t = 0; t < NRMAX; ++t) {
     int idx = lane + 32 * t;
     ca[t] = idx < nc ? idx / w : 0;
     cb[t] = idx < nc ? idx % w : 0;
@@ -359,23 +360,23 @@ __global__ void __launch_bounds__(32) spread_k(T* __restrict__ grid, int64_t str
     const int64_t s = (int64_t)start + q;
     const int lr = cell[2 * s] - r0, lc = cell[2 * s + 1] - c0;
     const T fv = f[perm[s]];
-    // lanes 0..w-1: f psi1_a ; lanes w..2w-1: psi2_b
-    T kv = 0;
-    if (lane < 2 * w) {
+    // lane a < w: f psi1_a (k1) and psi2_a (k2)
+    T k1 = 0, k2 = 0;
+    if (lane < w) {
       if (psi) {
-        kv = (T)psi[s * 2 * w + lane];
+        k1 = (T)psi[s * 2 * w + lane];
+        k2 = (T)psi[s * 2 * w + w + lane];
       } else {
-        const int d = lane < w ? 0 : 1;
-        const int a = lane < w ? lane : lane - w;
-        kv = (T)es_psif((offf[2 * s + d] - a) * scf, betaf);
+        k1 = (T)es_psif((offf[2 * s] - lane) * scf, betaf);
+        k2 = (T)es_psif((offf[2 * s + 1] - lane) * scf, betaf);
       }
-      if (lane < w) kv *= fv;
+      k1 *= fv;
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < NRMAX; ++t) {
       if (32 * t < nc) {
-        const T va = __shfl_sync(FULL, kv, ca[t]);
-        const T vb = __shfl_sync(FULL, kv, w + cb[t]);
+        const T va = __shfl_sync(FULL, k1, ca[t]);
+        const T vb = __shfl_sync(FULL, k2, cb[t]);
         if (lane + 32 * t < nc) {
           T* cellp = tile + (lr + ca[t]) * tw + (lc + cb[t]);
           *cellp = fma(va, vb, *cellp);
@@ -488,14 +489,21 @@ __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int
     cb[t] = idx < NC ? idx % W : 0;
     co[t] = ca[t] * tw + cb[t];
   }
-  // lanes 0..W-1 hold psi1_a, lanes W..2W-1 psi2_b of the current point
-  float2 kn = make_float2(0.f, 0.f);
-  if (cnt > 0 && lane < 2 * W) kn = psi[(int64_t)start * 2 * W + lane];
+  // lane a < W holds psi1_a (k1, times f) and psi2_a (k2) of the current point
+  float2 n1v = make_float2(0.f, 0.f), n2v = n1v;
+  if (cnt > 0 && lane < W) {
+    n1v = psi[(int64_t)start * 2 * W + lane];
+    n2v = psi[(int64_t)start * 2 * W + W + lane];
+  }
   for (int q = 0; q < cnt; ++q) {
-    float2 kv = kn;
-    if (q + 1 < cnt && lane < 2 * W) kn = psi[((int64_t)start + q + 1) * 2 * W + lane];
+    float2 k1 = n1v;
+    const float2 k2 = n2v;
+    if (q + 1 < cnt && lane < W) {
+      n1v = psi[((int64_t)start + q + 1) * 2 * W + lane];
+      n2v = psi[((int64_t)start + q + 1) * 2 * W + W + lane];
+    }
     const int2 lrc = sp_cell[q];
-    if (lane < W) kv = df_mul(kv, sp_f[q]);
+    if (lane < W) k1 = df_mul(k1, sp_f[q]);
     float2* base = tile + lrc.x * tw + lrc.y;
     // a point's cells are distinct: read them all, update, write them all
     float2 c[NR];
@@ -505,10 +513,10 @@ __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int
 #pragma unroll
     for (int t = 0; t < NR; ++t) {
       float2 va, vb;
-      va.x = __shfl_sync(FULL, kv.x, ca[t]);
-      va.y = __shfl_sync(FULL, kv.y, ca[t]);
-      vb.x = __shfl_sync(FULL, kv.x, W + cb[t]);
-      vb.y = __shfl_sync(FULL, kv.y, W + cb[t]);
+      va.x = __shfl_sync(FULL, k1.x, ca[t]);
+      va.y = __shfl_sync(FULL, k1.y, ca[t]);
+      vb.x = __shfl_sync(FULL, k2.x, cb[t]);
+      vb.y = __shfl_sync(FULL, k2.y, cb[t]);
       if (lane + 32 * t < NC) df_mac(c[t].x, c[t].y, va.x, va.y, vb.x, vb.y);
     }
 #pragma unroll
@@ -545,7 +553,11 @@ __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int
     case 13: F<13>(__VA_ARGS__); break; \
     case 14: F<14>(__VA_ARGS__); break; \
     case 15: F<15>(__VA_ARGS__); break; \
-    default: F<16>(__VA_ARGS__); break; \
+    case 16: F<16>(__VA_ARGS__); break; \
+    case 17: F<17>(__VA_ARGS__); break; \
+    case 18: F<18>(__VA_ARGS__); break; \
+    case 19: F<19>(__VA_ARGS__); break; \
+    default: F<20>(__VA_ARGS__); break; \
   }
 
 template <int W>
@@ -564,7 +576,7 @@ void launch_spread_df(int nsub, size_t sm, cudaStream_t s, double* grid, int64_t
 
 template <int W>
 void optin_df(int* st) {
-  const int mx = 80 * 80 * 8;
+  const int mx = 84 * 84 * 8;
   if (cudaFuncSetAttribute(spread_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx + SUBMAX * 16) !=
           cudaSuccess ||
       cudaFuncSetAttribute(interp_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
@@ -574,38 +586,35 @@ void optin_df(int* st) {
 // Spreading in float (mixed mode): one thread per point of the subproblem,
 // kernel values evaluated on the fly from the FP32 offsets, w x w native
 // shared-memory float atomics into the bin's tile, one atomic flush.
-__global__ void __launch_bounds__(128) spread_pt_k(float* __restrict__ grid, int64_t stride, int n1, int n2, int w,
-                                                   int nb2, int binsz, float betaf, const int* __restrict__ sub,
+template <int W>
+__global__ void __launch_bounds__(128) spread_pt_k(float* __restrict__ grid, int64_t stride, int n1, int n2, int nb2,
+                                                   int binsz, float betaf, const int* __restrict__ sub,
                                                    const int* __restrict__ cell, const float* __restrict__ offf,
                                                    const int* __restrict__ perm, const float* __restrict__ f) {
   extern __shared__ unsigned char smem_raw[];
   float* tile = reinterpret_cast<float*>(smem_raw);
-  const int tw = binsz + w - 1;
+  const int tw = binsz + W - 1;
   const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
   const int r0 = (bin / nb2) * binsz, c0 = (bin % nb2) * binsz;
   for (int t = threadIdx.x; t < tw * tw; t += blockDim.x) tile[t] = 0.f;
   __syncthreads();
-  const float scf = 2.0f / w;
+  const float scf = 2.0f / W;
   for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
     const int64_t s = (int64_t)start + q;
     const int lr = cell[2 * s] - r0, lc = cell[2 * s + 1] - c0;
     const float fv = f[perm[s]];
     const float o1 = offf[2 * s], o2 = offf[2 * s + 1];
-    float p1[WMAX], p2[WMAX];
+    float p1[W], p2[W];
 #pragma unroll
-    for (int a = 0; a < WMAX; ++a)
-      if (a < w) {
-        p1[a] = fv * es_psif((o1 - a) * scf, betaf);
-        p2[a] = es_psif((o2 - a) * scf, betaf);
-      }
+    for (int a = 0; a < W; ++a) {
+      p1[a] = fv * es_psif((o1 - a) * scf, betaf);
+      p2[a] = es_psif((o2 - a) * scf, betaf);
+    }
 #pragma unroll
-    for (int a = 0; a < WMAX; ++a) {
-      if (a < w) {
-        float* trow = tile + (lr + a) * tw + lc;
+    for (int a = 0; a < W; ++a) {
+      float* trow = tile + (lr + a) * tw + lc;
 #pragma unroll
-        for (int b = 0; b < WMAX; ++b)
-          if (b < w) atomicAdd(trow + b, p1[a] * p2[b]);
-      }
+      for (int b = 0; b < W; ++b) atomicAdd(trow + b, p1[a] * p2[b]);
     }
   }
   __syncthreads();
@@ -620,16 +629,75 @@ __global__ void __launch_bounds__(128) spread_pt_k(float* __restrict__ grid, int
   }
 }
 
+// interpolation in float (mixed mode): one thread per point, kernel values
+// evaluated on the fly from the FP32 offsets
+template <int W>
+__global__ void __launch_bounds__(128) interp_f_k(const float* __restrict__ grid, int64_t stride, int n1, int n2,
+                                                  float betaf, const int* __restrict__ cell,
+                                                  const float* __restrict__ offf, const int* __restrict__ perm,
+                                                  int64_t npts, float* __restrict__ out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= npts) return;
+  const int i1 = cell[2 * s], i2 = cell[2 * s + 1];
+  const float o1 = offf[2 * s], o2 = offf[2 * s + 1];
+  const float scf = 2.0f / W;
+  float p1[W], p2[W];
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    p1[a] = es_psif((o1 - a) * scf, betaf);
+    p2[a] = es_psif((o2 - a) * scf, betaf);
+  }
+  const bool wrap2 = i2 + W > n2;
+  float acc = 0.f;
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    int r = i1 + a;
+    if (r >= n1) r -= n1;
+    const float* row = grid + (int64_t)r * stride;
+    float in = 0.f;
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      int c = i2 + b;
+      if (wrap2 && c >= n2) c -= n2;
+      in = fmaf(p2[b], row[c], in);
+    }
+    acc = fmaf(p1[a], in, acc);
+  }
+  out[perm[s]] = acc;
+}
+
+template <int W>
+void launch_spread_f(int nsub, size_t sm, cudaStream_t s, float* grid, int64_t stride, int n1, int n2, int nb2,
+                     int binsz, float betaf, const int* sub, const int* cell, const float* offf, const int* perm,
+                     const float* f) {
+  spread_pt_k<W><<<nsub, 128, sm, s>>>(grid, stride, n1, n2, nb2, binsz, betaf, sub, cell, offf, perm, f);
+}
+
+template <int W>
+void launch_interp_f(int nb, cudaStream_t s, const float* grid, int64_t stride, int n1, int n2, float betaf,
+                     const int* cell, const float* offf, const int* perm, int64_t npts, float* out) {
+  interp_f_k<W><<<nb, 128, 0, s>>>(grid, stride, n1, n2, betaf, cell, offf, perm, npts, out);
+}
+
+template <int W>
+void optin_f(int* st) {
+  if (cudaFuncSetAttribute(spread_pt_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 84 * 84 * 8) != cudaSuccess)
+    *st = 1;
+}
+
 }  // namespace
 
 int spread_smem_optin() {
-  // bins of up to 64 cells with w <= 16: (64 + 15)^2 x 8 B = 49.9 KB of tile
-  const int mx = 80 * 80 * 8;
+  // bins of up to 64 cells with w <= 20: (64 + 19)^2 x 8 B = 55.1 KB of tile
+  const int mx = 84 * 84 * 8;
   NUSHT_CUDA(cudaFuncSetAttribute(spread_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   NUSHT_CUDA(cudaFuncSetAttribute(spread_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  NUSHT_CUDA(cudaFuncSetAttribute(spread_pt_k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+
   int bad = 0;
-  for (int w = 2; w <= WMAX; ++w) NUSHT_W_DISPATCH(w, optin_df, &bad);
+  for (int w = 2; w <= WMAX; ++w) {
+    NUSHT_W_DISPATCH(w, optin_df, &bad);
+    NUSHT_W_DISPATCH(w, optin_f, &bad);
+  }
   if (bad) return set_error(NUSHT_ECUDA, "shared-memory opt-in for the double-float NUFFT kernels");
   return NUSHT_OK;
 }
@@ -775,9 +843,8 @@ int interp(nusht_plan_t p, void* d_map, cudaStream_t s) {
                                               p->pts.cell, p->pts.psi, nullptr, nullptr, p->pts.perm, n,
                                               (double*)d_map, nullptr, nullptr);
   else
-    interp_k<float, false><<<nb, tb, 0, s>>>((const float*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
-                                             p->pts.cell, nullptr, p->pts.off, nullptr, p->pts.perm, n,
-                                             (float*)d_map, nullptr, nullptr);
+    NUSHT_W_DISPATCH(z.w, launch_interp_f, nb, s, (const float*)p->fine, stride, z.n1, z.n2, (float)z.beta,
+                     p->pts.cell, p->pts.off, p->pts.perm, n, (float*)d_map);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
@@ -819,9 +886,8 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
                                                  (float)z.beta, p->pts.sub, p->pts.cell, p->pts.psi, nullptr,
                                                  p->pts.perm, (const double*)d_map);
   else
-    spread_pt_k<<<p->pts.nsub, 128, sm, s>>>((float*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz,
-                                             (float)z.beta,
-                                             p->pts.sub, p->pts.cell, p->pts.off, p->pts.perm, (const float*)d_map);
+    NUSHT_W_DISPATCH(z.w, launch_spread_f, p->pts.nsub, sm, s, (float*)p->fine, stride, z.n1, z.n2, p->pts.nbins2,
+                     binsz, (float)z.beta, p->pts.sub, p->pts.cell, p->pts.off, p->pts.perm, (const float*)d_map);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }

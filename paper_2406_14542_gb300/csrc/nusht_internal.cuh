@@ -180,8 +180,10 @@ int spread_smem_optin();
 
 // autotuner (tune.cu)
 int tune_points(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s);
+// largest ES kernel width the spreading / interpolation kernels support
+constexpr int ES_WMAX = 20;
 // ES kernel width the accuracy formula asks for at NUFFT tolerance eps and
-// up-sampling sigma (before the [2, 16] clamp)
+// up-sampling sigma (before the [2, ES_WMAX] clamp)
 int es_width(double eps, double sigma);
 // opts.tune 1/2 with opts.sigma = 0: the up-sampling factor (and the bin edge
 // found with it) from timing, or from the cache; *sigma_out = 0 if none

@@ -88,7 +88,7 @@ int es_width(double eps, double sigma) {
 static void es_params(double eps, double sigma, int w_override, int* w, double* beta) {
   int ww = es_width(eps, sigma);
   if (w_override > 0) ww = w_override;
-  ww = std::max(2, std::min(16, ww));
+  ww = std::max(2, std::min(ES_WMAX, ww));
   double b;
   if (std::fabs(sigma - 2.0) < 1e-12) {
     b = 2.30 * ww;
@@ -114,8 +114,8 @@ int choose_sizes(int lmax, int mmax, double eps, int precision, const nusht_opts
   // than the wider kernel sigma = 1.5 needs); FP32 grids are not
   double sigma = opt.sigma > 0.0 ? opt.sigma : (precision == NUSHT_FP64 ? 1.5 : 2.0);
   if (!(sigma >= 1.2 && sigma <= 4.0)) return set_error(NUSHT_EINVAL, "sigma must be in [1.2, 4]");
-  if (opt.kernel_width < 0 || opt.kernel_width > 16)
-    return set_error(NUSHT_EINVAL, "kernel_width must be in [0, 16]");
+  if (opt.kernel_width < 0 || opt.kernel_width > ES_WMAX)
+    return set_error(NUSHT_EINVAL, "kernel_width must be in [0, 20]");
   std::memset(out, 0, sizeof(*out));
   out->lmax = lmax;
   out->mmax = mmax;
@@ -531,7 +531,7 @@ int nusht_plan_sizes(int lmax, int mmax, double eps, int precision, const nusht_
 }
 
 int nusht_kernel_ft(int w, double beta, int n, int nk, double* out) {
-  if (w < 2 || w > 16 || !(beta > 0) || n < 2 * w || nk < 0 || (nk > 0 && !out))
+  if (w < 2 || w > ES_WMAX || !(beta > 0) || n < 2 * w || nk < 0 || (nk > 0 && !out))
     return set_error(NUSHT_EINVAL, "bad kernel_ft arguments");
   kernel_ft(w, beta, n, nk, out);
   return NUSHT_OK;

@@ -2,7 +2,7 @@
 // spreading / interpolation bin size.
 //
 // sigma (opts.sigma = 0 with opts.tune = 1): for each sigma in {2, 1.5, 1.25}
-// whose accuracy formula width fits the kernel's limit of 16, a NUFFT-only
+// whose accuracy formula width fits the kernel's limit of 20, a NUFFT-only
 // trial plan (its own bin search included) times the sigma-dependent stages
 // of one synthesis + adjoint: deconvolution/padding, the 2D FFTs,
 // interpolation and spreading.  The fastest sigma is cached under the device,
@@ -121,7 +121,7 @@ int tune_sigma(int lmax, int mmax, int64_t npts, const double* d_pts, double eps
   int best_bin = 0;
   float best_ms = 1e30f;
   for (int c = 0; c < 3 && st == NUSHT_OK; ++c) {
-    if (es_width(0.1 * eps, cand[c]) > 16) continue;  // accuracy not reachable within the width limit
+    if (es_width(0.1 * eps, cand[c]) > ES_WMAX) continue;  // accuracy not reachable within the width limit
     nusht_opts oc = *o;
     oc.sigma = cand[c];
     oc.tune = 1;

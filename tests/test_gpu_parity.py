@@ -324,3 +324,31 @@ def test_execute_calls_capture_into_cuda_graph(env, prec):
     rel = (torch.linalg.norm(c - c_eager) / torch.linalg.norm(c_eager)).item()
     # the adjoint's spreading adds with atomics: equal to rounding in the plan's precision
     assert rel <= (1e-12 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec,sigma,kw,fc", [("fp64", 1.25, 0, False), ("fp64", 1.25, 0, True),
+                                              ("fp64", 2.0, 17, False), ("mixed", 2.0, 20, False)])
+def test_kernel_widths_above_16(env, prec, sigma, kw, fc):
+    """Widths 17..20 (sigma = 1.25 at eps 1e-10 needs w = 19): synthesis and
+    adjoint against the oracle, and the dot test, on every spreading and
+    interpolation path (double-float, FP64 instructions, float)."""
+    torch, nu = env
+    L, a, pts = W.workload("uniform63")
+    cd = torch.complex128 if prec == "fp64" else torch.complex64
+    rd = torch.float64 if prec == "fp64" else torch.float32
+    plan = nu.Plan(L, dev(torch, pts), eps=TOL[prec], precision=prec, sigma=sigma, kernel_width=kw,
+                   fp64_contraction=fc)
+    assert plan.info()["w"] >= 17
+    f = plan.synth(dev(torch, a, cd)).double().cpu().numpy()
+    assert oracle.eps_eff(oracle.synth(a, pts, L), f) <= TOL[prec]
+    y = np.random.default_rng(14).standard_normal(pts.shape[0])
+    if prec == "mixed":
+        y = y.astype(np.float32).astype(np.float64)
+    c = plan.adjoint(dev(torch, y, rd)).cpu().numpy().astype(np.complex128)
+    assert oracle.eps_eff(oracle.adjoint(y, pts, L), c) <= TOL[prec]
+    lhs = float(np.dot(y, f))
+    rhs = oracle.alm_dot(c, a, L)
+    # at sigma = 1.25 the deconvolution factors 1 / psihat near the band edge
+    # are large and amplify rounding in both directions alike: 1e-11 there
+    dtol = 1e-5 if prec == "mixed" else (1e-11 if sigma < 1.4 else 1e-12)
+    assert abs(lhs - rhs) <= dtol * abs(lhs)
