@@ -93,8 +93,11 @@ typedef struct {
                         winner, tune = 2 takes the cached one */
   int kernel_width;  /* ES kernel width w override in [2, 20]; 0 = from eps and sigma */
   int profile;       /* 1 = record per-stage CUDA-event times (nusht_stage_times) */
-  int deterministic; /* reserved; synthesis is bit-reproducible, the adjoint's spreading
-                        flush adds tile halos with atomics (rounding-level order effects) */
+  int deterministic; /* 1 = bit-reproducible adjoint: each spreading subproblem writes its
+                        tile (bin + halo) to a plan-owned scratch buffer and every fine-grid
+                        cell sums the tiles covering it in a fixed order, instead of adding
+                        halos with atomics (FP64 at lmax 4095: 2.4 GB of scratch).  0 = atomics
+                        (rounding-level order effects).  Synthesis is always reproducible. */
   int tune;          /* NUFFT autotuner: 0 = off (bin edge 32 cells); 1 = search at plan
                         time on the plan's own points (bin edge 16/32/64 and, when sigma = 0,
                         the up-sampling factor), caching the winners; 2 = the cached choices

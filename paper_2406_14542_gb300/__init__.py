@@ -122,8 +122,9 @@ def _check(code: int, where: str):
 
 
 def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False, legendre_table=0, tune=0,
-          tensor_cores=0) -> Opts:
+          tensor_cores=0, deterministic=False) -> Opts:
     o = Opts()
+    o.deterministic = 1 if deterministic else 0
     o.tensor_cores = int(tensor_cores)
     o.tune = int(tune)
     o.legendre_table = int(legendre_table)
@@ -235,7 +236,7 @@ class Plan:
 
     def __init__(self, lmax: int, pts, eps: float = 1e-10, precision="fp64", mmax: int | None = None,
                  sigma: float = 0.0, kernel_width: int = 0, profile: bool = False, fp64_contraction: bool = False,
-                 legendre_table: int = 0, tune: int = 0, stream=None):
+                 legendre_table: int = 0, tune: int = 0, deterministic: bool = False, stream=None):
         import torch
 
         self.lib = load()
@@ -249,7 +250,8 @@ class Plan:
         self.npts = int(pts.shape[0])
         self.device = pts.device
         h = ctypes.c_void_p()
-        o = _opts(sigma, kernel_width, profile, fp64_contraction, legendre_table, tune)
+        o = _opts(sigma, kernel_width, profile, fp64_contraction, legendre_table, tune,
+                  deterministic=deterministic)
         _check(self.lib.nusht_plan(ctypes.byref(h), self.lmax, self.mmax, self.npts,
                                    ctypes.c_void_p(pts.data_ptr() if self.npts else 0), self.eps, self.precision,
                                    ctypes.byref(o), _stream_ptr(stream)), "nusht_plan")
@@ -391,7 +393,7 @@ class BatchPlan:
     float64 (N_b, 2) tensor; each lmax <= 4095."""
 
     def __init__(self, lmaxs, pts_list, eps: float = 1e-5, sigma: float = 0.0, legendre_table: int = 0,
-                 tune: int = 0, tensor_cores: int = 0, stream=None):
+                 tune: int = 0, tensor_cores: int = 0, deterministic: bool = False, stream=None):
         import torch
 
         self.lib = load()
@@ -405,7 +407,8 @@ class BatchPlan:
         larr = (ctypes.c_int * n)(*self.lmaxs)
         narr = (ctypes.c_int64 * n)(*self.npts)
         parr = (ctypes.c_void_p * n)(*[p.data_ptr() if p.numel() else 0 for p in self.pts])
-        o = _opts(sigma, legendre_table=legendre_table, tune=tune, tensor_cores=tensor_cores)
+        o = _opts(sigma, legendre_table=legendre_table, tune=tune, tensor_cores=tensor_cores,
+                  deterministic=deterministic)
         h = ctypes.c_void_p()
         _check(self.lib.nusht_plan_many(ctypes.byref(h), n, larr, narr, parr, float(eps), MIXED, ctypes.byref(o),
                                         _stream_ptr(stream)), "nusht_plan_many")

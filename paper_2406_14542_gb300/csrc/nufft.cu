@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(32) spread_k(T* __restrict__ grid, int64_t str
                                                int binsz, float betaf, const int* __restrict__ sub,
                                                const int* __restrict__ cell,
                                                const double* __restrict__ psi, const float* __restrict__ offf,
-                                               const int* __restrict__ perm, const T* __restrict__ f) {
+                                               const int* __restrict__ perm, const T* __restrict__ f,
+                                               T* __restrict__ scratch) {
   extern __shared__ unsigned char smem_raw[];
   T* tile = reinterpret_cast<T*>(smem_raw);
   const int lane = threadIdx.x;
@@ -386,6 +387,11 @@ __global__ void __launch_bounds__(32) spread_k(T* __restrict__ grid, int64_t str
     __syncwarp();
   }
   __syncwarp();
+  if (scratch) {  // deterministic: the whole tile to this subproblem's slot
+    T* dst = scratch + (size_t)blockIdx.x * tw * tw;
+    for (int t = lane; t < tw * tw; t += 32) dst[t] = tile[t];
+    return;
+  }
   for (int t = lane; t < tw * tw; t += 32) {
     const T v = tile[t];
     if (v != (T)0) {
@@ -460,7 +466,8 @@ template <int W>
 __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int64_t stride, int n1, int n2, int nb2,
                                                   int binsz, const int* __restrict__ sub,
                                                   const int* __restrict__ cell, const float2* __restrict__ psi,
-                                                  const int* __restrict__ perm, const double* __restrict__ f) {
+                                                  const int* __restrict__ perm, const double* __restrict__ f,
+                                                  float2* __restrict__ scratch) {
   constexpr int NC = W * W;
   constexpr int NR = (NC + 31) / 32;  // rounds of 32 cells per point
   extern __shared__ unsigned char smem_raw[];
@@ -525,6 +532,11 @@ __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int
     __syncwarp();
   }
   __syncwarp();
+  if (scratch) {  // deterministic: the whole tile to this subproblem's slot
+    float2* dst = scratch + (size_t)blockIdx.x * tw * tw;
+    for (int t = lane; t < tw * tw; t += 32) dst[t] = tile[t];
+    return;
+  }
   for (int t = lane; t < tw * tw; t += 32) {
     const float2 v = tile[t];
     if (v.x != 0.f) {
@@ -570,8 +582,61 @@ void launch_interp_df(int nsub, size_t sm, cudaStream_t s, const double* grid, i
 template <int W>
 void launch_spread_df(int nsub, size_t sm, cudaStream_t s, double* grid, int64_t stride, int n1, int n2, int nb2,
                       int binsz, const int* sub, const int* cell, const float2* psi, const int* perm,
-                      const double* f) {
-  spread_df_k<W><<<nsub, 32, sm, s>>>(grid, stride, n1, n2, nb2, binsz, sub, cell, psi, perm, f);
+                      const double* f, float2* scratch) {
+  spread_df_k<W><<<nsub, 32, sm, s>>>(grid, stride, n1, n2, nb2, binsz, sub, cell, psi, perm, f, scratch);
+}
+
+__device__ __forceinline__ double tile_value(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ double tile_value(double v) { return v; }
+__device__ __forceinline__ float tile_value(float v) { return v; }
+
+// Deterministic type 1: grid cell (r, c) = the sum, in a fixed order, of the
+// tile entries of every subproblem whose tile covers it.  A tile of bin
+// (R', C') covers rows r0' .. r0' + bin + w - 2 (mod n1); with w - 1 <= bin
+// these lie in the bins R - 2, R - 1, R (R - 2 only when a partial last bin
+// lets footprints of the bin before it wrap into bin 0); all bins are taken
+// when there are at most four per dimension, where tiles can wrap around the
+// whole grid; likewise columns.  Bins whose tile misses the cell add nothing.
+template <typename T, typename A, typename S>
+__global__ void grid_gather_k(T* __restrict__ grid, int64_t stride, int n1, int n2, int binsz, int tw, int nb1,
+                              int nb2, const int* __restrict__ binsub, const S* __restrict__ tiles) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n1 * n2) return;
+  const int r = (int)(e / n2), c = (int)(e - (int64_t)r * n2);
+  const int R = r / binsz, C = c / binsz;
+  int rb[4], cb[4];
+  int nr = 0, nc = 0;
+  if (nb1 <= 4) {
+    for (int b = 0; b < nb1; ++b) rb[nr++] = b;
+  } else {
+    rb[nr++] = (R + nb1 - 2) % nb1;
+    rb[nr++] = (R + nb1 - 1) % nb1;
+    rb[nr++] = R;
+  }
+  if (nb2 <= 4) {
+    for (int b = 0; b < nb2; ++b) cb[nc++] = b;
+  } else {
+    cb[nc++] = (C + nb2 - 2) % nb2;
+    cb[nc++] = (C + nb2 - 1) % nb2;
+    cb[nc++] = C;
+  }
+  A acc = 0;
+  auto val = [](const S& v) -> A { return tile_value(v); };
+  for (int i = 0; i < nr; ++i) {
+    const int r0 = rb[i] * binsz;
+    for (int tr = ((r - r0) % n1 + n1) % n1; tr < tw; tr += n1) {
+      for (int j = 0; j < nc; ++j) {
+        const int c0 = cb[j] * binsz;
+        const int bin = rb[i] * nb2 + cb[j];
+        for (int tc = ((c - c0) % n2 + n2) % n2; tc < tw; tc += n2) {
+          for (int k = binsub[bin]; k < binsub[bin + 1]; ++k) {
+            acc += val(tiles[(size_t)k * tw * tw + tr * tw + tc]);
+          }
+        }
+      }
+    }
+  }
+  grid[(int64_t)r * stride + c] = (T)acc;
 }
 
 template <int W>
@@ -710,6 +775,8 @@ void free_points(nusht_plan_t p) {
   dev_free(d.xy);
   dev_free(d.off);
   dev_free(d.sub);
+  dev_free(d.tiles);
+  dev_free(d.binsub);
   d = PointData();
 }
 
@@ -720,6 +787,9 @@ static bool nufft_df(nusht_plan_t p) { return p->precision == NUSHT_FP64 && !p->
 int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   PointData& d = p->pts;
+  // the deterministic gather takes the tiles of the bins R and R - 1 per
+  // dimension, which needs w - 1 <= bin
+  if (p->opts.deterministic && d.bin > 0 && d.bin < z.w) d.bin = 32;
   const int binsz = d.bin > 0 ? d.bin : 32;
   const int nb1 = (z.n1 + binsz - 1) / binsz, nb2 = (z.n2 + binsz - 1) / binsz;
   const bool dbl = p->precision == NUSHT_FP64;
@@ -785,6 +855,24 @@ int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t 
     }
   d.nsub = (int)(sub.size() / 3);
   NUSHT_TRY(dev_alloc((void**)&d.sub, std::max<size_t>(1, sub.size()) * 4, &p->bytes));
+  if (p->opts.deterministic) {
+    std::vector<int> bs(nbins + 1, 0);
+    for (size_t k = 0; k < sub.size() / 3; ++k) bs[sub[3 * k] + 1]++;
+    for (int b = 0; b < nbins; ++b) bs[b + 1] += bs[b];
+    dev_free(d.binsub);
+    d.binsub = nullptr;
+    NUSHT_TRY(dev_alloc((void**)&d.binsub, bs.size() * 4, &p->bytes));
+    NUSHT_CUDA(cudaMemcpyAsync(d.binsub, bs.data(), bs.size() * 4, cudaMemcpyHostToDevice, s));
+    const int tw = binsz + z.w - 1;
+    const size_t need = std::max<size_t>(1, (size_t)d.nsub) * tw * tw * (dbl ? 8 : 4);
+    if (need > d.tiles_cap) {
+      dev_free(d.tiles);
+      d.tiles = nullptr;
+      d.tiles_cap = 0;
+      NUSHT_TRY(dev_alloc(&d.tiles, need, &p->bytes));
+      d.tiles_cap = need;
+    }
+  }
   NUSHT_CUDA(cudaMemcpyAsync(d.perm, perm.data(), (size_t)npts * 4, cudaMemcpyHostToDevice, s));
   if (!sub.empty()) NUSHT_CUDA(cudaMemcpyAsync(d.sub, sub.data(), sub.size() * 4, cudaMemcpyHostToDevice, s));
   const bool dfm = nufft_df(p);
@@ -872,7 +960,8 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const int64_t stride = 2 * (z.n2 / 2 + 1);
   const size_t es = p->precision == NUSHT_FP64 ? 8 : 4;
-  NUSHT_CUDA(cudaMemsetAsync(p->fine, 0, (size_t)z.n1 * stride * es, s));
+  const bool det = p->opts.deterministic != 0 && p->pts.tiles != nullptr;
+  if (p->pts.nsub == 0 || !det) NUSHT_CUDA(cudaMemsetAsync(p->fine, 0, (size_t)z.n1 * stride * es, s));
   if (p->pts.nsub == 0) return NUSHT_OK;
   const int binsz = p->pts.bin > 0 ? p->pts.bin : 32;
   const int tw = binsz + z.w - 1;
@@ -880,15 +969,39 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
   if (nufft_df(p)) {
     NUSHT_W_DISPATCH(z.w, launch_spread_df, p->pts.nsub, sm + (size_t)SUBMAX * 16, s, (double*)p->fine, stride, z.n1,
                      z.n2, p->pts.nbins2, binsz, p->pts.sub, p->pts.cell,
-                     reinterpret_cast<const float2*>(p->pts.psi), p->pts.perm, (const double*)d_map);
-  } else if (p->precision == NUSHT_FP64)
+                     reinterpret_cast<const float2*>(p->pts.psi), p->pts.perm, (const double*)d_map,
+                     det ? (float2*)p->pts.tiles : nullptr);
+  } else if (p->precision == NUSHT_FP64) {
     spread_k<double><<<p->pts.nsub, 32, sm, s>>>((double*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz,
                                                  (float)z.beta, p->pts.sub, p->pts.cell, p->pts.psi, nullptr,
-                                                 p->pts.perm, (const double*)d_map);
-  else
+                                                 p->pts.perm, (const double*)d_map,
+                                                 det ? (double*)p->pts.tiles : nullptr);
+  } else if (det) {
+    // one warp per subproblem, points in order, lanes own distinct cells: no
+    // atomics, so the tile is reproducible
+    spread_k<float><<<p->pts.nsub, 32, sm, s>>>((float*)p->fine, stride, z.n1, z.n2, z.w, p->pts.nbins2, binsz,
+                                                (float)z.beta, p->pts.sub, p->pts.cell, nullptr, p->pts.off,
+                                                p->pts.perm, (const float*)d_map, (float*)p->pts.tiles);
+  } else {
     NUSHT_W_DISPATCH(z.w, launch_spread_f, p->pts.nsub, sm, s, (float*)p->fine, stride, z.n1, z.n2, p->pts.nbins2,
                      binsz, (float)z.beta, p->pts.sub, p->pts.cell, p->pts.off, p->pts.perm, (const float*)d_map);
+  }
   NUSHT_CUDA(cudaGetLastError());
+  if (det) {
+    const int64_t ncell = (int64_t)z.n1 * z.n2;
+    const unsigned nb = (unsigned)((ncell + 255) / 256);
+    const int nb1 = p->pts.nbins1, nb2 = p->pts.nbins2;
+    if (nufft_df(p))
+      grid_gather_k<double, double, float2><<<nb, 256, 0, s>>>((double*)p->fine, stride, z.n1, z.n2, binsz, tw, nb1,
+                                                              nb2, p->pts.binsub, (const float2*)p->pts.tiles);
+    else if (p->precision == NUSHT_FP64)
+      grid_gather_k<double, double, double><<<nb, 256, 0, s>>>((double*)p->fine, stride, z.n1, z.n2, binsz, tw, nb1,
+                                                              nb2, p->pts.binsub, (const double*)p->pts.tiles);
+    else
+      grid_gather_k<float, float, float><<<nb, 256, 0, s>>>((float*)p->fine, stride, z.n1, z.n2, binsz, tw, nb1, nb2,
+                                                           p->pts.binsub, (const float*)p->pts.tiles);
+    NUSHT_CUDA(cudaGetLastError());
+  }
   return NUSHT_OK;
 }
 

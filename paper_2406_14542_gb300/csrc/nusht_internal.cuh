@@ -94,6 +94,11 @@ struct PointData {
   int nbins1 = 0, nbins2 = 0;
   int bin = 32;               // bin edge in fine-grid cells (spreading tile = bin + w - 1)
   size_t bytes = 0;           // device bytes held for points (part of the plan's total)
+  // opts.deterministic: every subproblem's tile is written here ([nsub][tile]),
+  // then summed per grid cell in a fixed order (no atomics)
+  void* tiles = nullptr;
+  size_t tiles_cap = 0;
+  int* binsub = nullptr;      // subproblems of bin b: [binsub[b], binsub[b + 1])
 };
 
 struct StageEvents {

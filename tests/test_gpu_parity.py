@@ -352,3 +352,30 @@ def test_kernel_widths_above_16(env, prec, sigma, kw, fc):
     # are large and amplify rounding in both directions alike: 1e-11 there
     dtol = 1e-5 if prec == "mixed" else (1e-11 if sigma < 1.4 else 1e-12)
     assert abs(lhs - rhs) <= dtol * abs(lhs)
+
+
+@pytest.mark.parametrize("prec,fc,n", [("fp64", False, 20000), ("fp64", True, 20000), ("mixed", False, 20000),
+                                       ("fp64", False, 3001)])
+def test_deterministic_adjoint(env, prec, fc, n):
+    """opts.deterministic: the adjoint is bit-reproducible (tiles summed per
+    grid cell in a fixed order, no atomics) and agrees with the oracle and
+    with the atomic path to rounding; includes a grid whose last bin is
+    partial (lmax 129 -> n = 392 at sigma 1.5)."""
+    torch, nu = env
+    L = 63 if n == 20000 else 129
+    a = W.alm_gaussian(L, seed=1)
+    pts = W.points_uniform(n, seed=n + 1)
+    rd = torch.float64 if prec == "fp64" else torch.float32
+    y = np.random.default_rng(15).standard_normal(n)
+    if prec == "mixed":
+        y = y.astype(np.float32).astype(np.float64)
+    dy = dev(torch, y, rd)
+    pd = nu.Plan(L, dev(torch, pts), eps=TOL[prec], precision=prec, fp64_contraction=fc, deterministic=True)
+    c1 = pd.adjoint(dy).clone()
+    c2 = pd.adjoint(dy).clone()
+    assert torch.equal(c1, c2)
+    got = c1.cpu().numpy().astype(np.complex128)
+    assert oracle.eps_eff(oracle.adjoint(y, pts, L), got) <= TOL[prec]
+    pa = nu.Plan(L, dev(torch, pts), eps=TOL[prec], precision=prec, fp64_contraction=fc)
+    ca = pa.adjoint(dy).cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ca) <= (1e-12 if prec == "fp64" else 1e-5) * np.linalg.norm(ca)
