@@ -1267,8 +1267,7 @@ int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
   for (int i = 0; i < p->nbatch; ++i) {
     nusht_plan_t q = p->sub[i];
     NUSHT_TRY(deconv_pad(q, s));
-    NUSHT_CUFFT(cufftSetStream(q->fft_c2r, s));
-    NUSHT_CUFFT(cufftExecC2R(q->fft_c2r, (cufftComplex*)q->fine, (cufftReal*)q->fine));
+    NUSHT_TRY(fine_fft_c2r(q, s));
     NUSHT_TRY(interp(q, d_map[i], s));
   }
   return NUSHT_OK;
@@ -1278,8 +1277,7 @@ int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
   for (int i = 0; i < p->nbatch; ++i) {
     nusht_plan_t q = p->sub[i];
     NUSHT_TRY(spread(q, d_map[i], s));
-    NUSHT_CUFFT(cufftSetStream(q->fft_r2c, s));
-    NUSHT_CUFFT(cufftExecR2C(q->fft_r2c, (cufftReal*)q->fine, (cufftComplex*)q->fine));
+    NUSHT_TRY(fine_fft_r2c(q, s));
     NUSHT_TRY(deconv_trunc(q, s));
   }
   for (auto& b : p->buckets) {

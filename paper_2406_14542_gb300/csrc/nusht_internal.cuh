@@ -131,9 +131,13 @@ struct nusht_plan_s {
   void* partial = nullptr;    // adjoint Legendre partial sums [blocks_per_m][nalm] complex
 
   cufftHandle fft_theta = 0;  // batched 1D, length M, batch mmax+1
-  cufftHandle fft_c2r = 0;    // 2D n1 x n2 complex-to-real (in place)
-  cufftHandle fft_r2c = 0;    // 2D n1 x n2 real-to-complex (in place)
-  bool have_theta = false, have_c2r = false, have_r2c = false;
+  // fine-grid FFT, in place on [n1][n2/2 + 1] complex = [n1][n2 + 2] real.
+  // FP64: along the first dimension only the columns m <= mmax (the others
+  // are zero), then the real transform along every row; FP32: 2D plans.
+  cufftHandle fft_cols = 0;   // FP64: C2C along n1, columns 0..mmax (stride n2/2 + 1)
+  cufftHandle fft_c2r = 0;    // FP64: rows complex-to-real along n2; FP32: 2D
+  cufftHandle fft_r2c = 0;    // FP64: rows real-to-complex along n2; FP32: 2D
+  bool have_theta = false, have_c2r = false, have_r2c = false, have_cols = false;
 
   size_t bytes = 0;
 
@@ -185,6 +189,9 @@ int spread_smem_optin();
 
 // autotuner (tune.cu)
 int tune_points(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s);
+// fine spectrum -> fine grid (inverse, both dimensions) and back (forward)
+int fine_fft_c2r(nusht_plan_t p, cudaStream_t s);
+int fine_fft_r2c(nusht_plan_t p, cudaStream_t s);
 // largest ES kernel width the spreading / interpolation kernels support
 constexpr int ES_WMAX = 20;
 // ES kernel width the accuracy formula asks for at NUFFT tolerance eps and

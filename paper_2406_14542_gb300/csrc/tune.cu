@@ -77,16 +77,10 @@ std::string device_name(int dev) {
 // one synthesis + adjoint pass of the sigma-dependent stages of a NUFFT-only plan
 int nufft_roundtrip(nusht_plan_t q, void* map, cudaStream_t s) {
   NUSHT_TRY(deconv_pad(q, s));
-  NUSHT_CUFFT(cufftSetStream(q->fft_c2r, s));
-  NUSHT_CUFFT(q->precision == NUSHT_FP64
-                  ? cufftExecZ2D(q->fft_c2r, (cufftDoubleComplex*)q->fine, (cufftDoubleReal*)q->fine)
-                  : cufftExecC2R(q->fft_c2r, (cufftComplex*)q->fine, (cufftReal*)q->fine));
+  NUSHT_TRY(fine_fft_c2r(q, s));
   NUSHT_TRY(interp(q, map, s));
   NUSHT_TRY(spread(q, map, s));
-  NUSHT_CUFFT(cufftSetStream(q->fft_r2c, s));
-  NUSHT_CUFFT(q->precision == NUSHT_FP64
-                  ? cufftExecD2Z(q->fft_r2c, (cufftDoubleReal*)q->fine, (cufftDoubleComplex*)q->fine)
-                  : cufftExecR2C(q->fft_r2c, (cufftReal*)q->fine, (cufftComplex*)q->fine));
+  NUSHT_TRY(fine_fft_r2c(q, s));
   NUSHT_TRY(deconv_trunc(q, s));
   return NUSHT_OK;
 }
