@@ -115,7 +115,12 @@ typedef struct {
                          contraction on the tensor cores (tcgen05.mma, TF32 operands split
                          into hi + lo, three products per term, FP32 accumulation;
                          ~2^-21 relative per product); -1 = FP32 FMA on the CUDA cores */
-  int reserved[4];
+  int fast_recurrence; /* 1 = run the P_lm recurrence of single-transform per-call plans in
+                          double-float on the FP32 pipe (x, q_l, c_l as float pairs, ~2^-47
+                          relative per step instead of FP64's 2^-53; about 2.5x faster Legendre
+                          stages on GB300).  Opt-in: the default recurrence is FP64.  Ignored
+                          with fp64_contraction = 1 and in recurrence-table mode. */
+  int reserved[3];
 } nusht_opts;
 
 /* Sizes a plan uses; filled by nusht_plan_sizes (no GPU needed) and nusht_info. */

@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("kernel_width", ctypes.c_int), ("profile", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("tune", ctypes.c_int), ("fp64_contraction", ctypes.c_int),
                 ("legendre_table", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("fast_recurrence", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class Sizes(ctypes.Structure):
@@ -122,8 +122,9 @@ def _check(code: int, where: str):
 
 
 def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False, legendre_table=0, tune=0,
-          tensor_cores=0, deterministic=False) -> Opts:
+          tensor_cores=0, deterministic=False, fast_recurrence=False) -> Opts:
     o = Opts()
+    o.fast_recurrence = 1 if fast_recurrence else 0
     o.deterministic = 1 if deterministic else 0
     o.tensor_cores = int(tensor_cores)
     o.tune = int(tune)
@@ -236,7 +237,8 @@ class Plan:
 
     def __init__(self, lmax: int, pts, eps: float = 1e-10, precision="fp64", mmax: int | None = None,
                  sigma: float = 0.0, kernel_width: int = 0, profile: bool = False, fp64_contraction: bool = False,
-                 legendre_table: int = 0, tune: int = 0, deterministic: bool = False, stream=None):
+                 legendre_table: int = 0, tune: int = 0, deterministic: bool = False,
+                 fast_recurrence: bool = False, stream=None):
         import torch
 
         self.lib = load()
@@ -251,7 +253,7 @@ class Plan:
         self.device = pts.device
         h = ctypes.c_void_p()
         o = _opts(sigma, kernel_width, profile, fp64_contraction, legendre_table, tune,
-                  deterministic=deterministic)
+                  deterministic=deterministic, fast_recurrence=fast_recurrence)
         _check(self.lib.nusht_plan(ctypes.byref(h), self.lmax, self.mmax, self.npts,
                                    ctypes.c_void_p(pts.data_ptr() if self.npts else 0), self.eps, self.precision,
                                    ctypes.byref(o), _stream_ptr(stream)), "nusht_plan")

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) bucket_synth_k(BucketArgs a, const int* _
         const int l = l0 + j;
         float q = 0.f;
         if (l <= L) {
-          if (l > m) chain_step(ch, __ldg(a.c + mb + l), __ldg(a.dshift + mb + l) != 0);
+          if (l > m) chain_step(ch, __ldg(a.c + mb + l), (int)__ldg(a.dshift + mb + l));
           if (ch.valid && ch.E == 0) q = to_f32(ch.q1);
         }
         Ps[j][t] = q;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(256) bucket_adj_k(BucketArgs a, const int* __r
         const int l = l0 + j;
         float q = 0.f;
         if (l <= L) {
-          if (l > m) chain_step(ch[k], __ldg(a.c + mb + l), __ldg(a.dshift + mb + l) != 0);
+          if (l > m) chain_step(ch[k], __ldg(a.c + mb + l), (int)__ldg(a.dshift + mb + l));
           if (ch[k].valid && ch[k].E == 0) q = to_f32(ch[k].q1);
         }
         Ps[j * BA_TILE + t] = q;
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(128) bucket_ptab_k(BucketArgs a, const int* __
   for (int l = m; l <= L; ++l) {
     const bool step = l > m;
     const double c = step ? __ldg(a.c + mb + l) : 0.0;
-    const bool rs = step && __ldg(a.dshift + mb + l) != 0;
+    const int rs = step ? (int)__ldg(a.dshift + mb + l) : 0;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       if (step) chain_step(ch[k], c, rs);

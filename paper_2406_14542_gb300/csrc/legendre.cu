@@ -44,11 +44,23 @@ struct LegArgs {
   int lmax, mmax, M, npairs, bpm;
   const int* items;
   const double* c;
+  const float2* cdf;
   const int8_t* dshift;
   const double* cm;
   const double* ring_x;
   const double* ring_s;
 };
+
+// the recurrence value in the contraction's type: float (mixed) or a float
+// pair split off the double (FP64 chain) / taken as is (double-float chain)
+template <typename T>
+__device__ __forceinline__ T qconv(const Chain& ch) {
+  return conv<T>(ch.q1);
+}
+template <typename T>
+__device__ __forceinline__ T qconv(const DfChain& ch) {
+  return (T)ch.q1.x;
+}
 
 __device__ __forceinline__ void item_of(const LegArgs& a, int it, int& m, int& blk) {
   int v = __ldg(a.items + it);
@@ -59,7 +71,7 @@ __device__ __forceinline__ void item_of(const LegArgs& a, int it, int& m, int& b
 // ---------------------------------------------------------------------------
 // synthesis: G[m][*] (doubled, theta-contiguous) from atilde
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, class CH = Chain>
 __global__ void __launch_bounds__(128) legendre_synth_k(LegArgs a, const typename V2<T>::t* __restrict__ at,
                                                         typename V2<T>::t* __restrict__ G, int nitems) {
   using T2 = typename V2<T>::t;
@@ -70,7 +82,7 @@ __global__ void __launch_bounds__(128) legendre_synth_k(LegArgs a, const typenam
   item_of(a, it, m, blk);
   const int L = a.lmax;
   const int mb = mbase_of(L, m);
-  Chain ch[LEG_K];
+  CH ch[LEG_K];
   T2 accE[LEG_K], accO[LEG_K];
 #pragma unroll
   for (int k = 0; k < LEG_K; ++k) {
@@ -83,7 +95,7 @@ __global__ void __launch_bounds__(128) legendre_synth_k(LegArgs a, const typenam
 #pragma unroll
     for (int k = 0; k < LEG_K; ++k)
       if (ch[k].E == 0) {
-        T q = conv<T>(ch[k].q1);
+        T q = qconv<T>(ch[k]);
         accE[k].x = fma(av.x, q, accE[k].x);
         accE[k].y = fma(av.y, q, accE[k].y);
       }
@@ -92,28 +104,28 @@ __global__ void __launch_bounds__(128) legendre_synth_k(LegArgs a, const typenam
   int l = m + 1;
   for (; l + 1 <= L; l += 2) {
     {
-      const double c = __ldg(a.c + mb + l);
-      const bool rs = __ldg(a.dshift + mb + l) != 0;
+      const auto c = coef(a, mb + l, ch[0]);
+      const int rs = __ldg(a.dshift + mb + l);
       const T2 av = at[mb + l];
 #pragma unroll
       for (int k = 0; k < LEG_K; ++k) {
         chain_step(ch[k], c, rs);
         if (ch[k].E == 0) {
-          T q = conv<T>(ch[k].q1);
+          T q = qconv<T>(ch[k]);
           accO[k].x = fma(av.x, q, accO[k].x);
           accO[k].y = fma(av.y, q, accO[k].y);
         }
       }
     }
     {
-      const double c = __ldg(a.c + mb + l + 1);
-      const bool rs = __ldg(a.dshift + mb + l + 1) != 0;
+      const auto c = coef(a, mb + l + 1, ch[0]);
+      const int rs = __ldg(a.dshift + mb + l + 1);
       const T2 av = at[mb + l + 1];
 #pragma unroll
       for (int k = 0; k < LEG_K; ++k) {
         chain_step(ch[k], c, rs);
         if (ch[k].E == 0) {
-          T q = conv<T>(ch[k].q1);
+          T q = qconv<T>(ch[k]);
           accE[k].x = fma(av.x, q, accE[k].x);
           accE[k].y = fma(av.y, q, accE[k].y);
         }
@@ -121,14 +133,14 @@ __global__ void __launch_bounds__(128) legendre_synth_k(LegArgs a, const typenam
     }
   }
   if (l <= L) {
-    const double c = __ldg(a.c + mb + l);
-    const bool rs = __ldg(a.dshift + mb + l) != 0;
+    const auto c = coef(a, mb + l, ch[0]);
+    const int rs = __ldg(a.dshift + mb + l);
     const T2 av = at[mb + l];
 #pragma unroll
     for (int k = 0; k < LEG_K; ++k) {
       chain_step(ch[k], c, rs);
       if (ch[k].E == 0) {
-        T q = conv<T>(ch[k].q1);
+        T q = qconv<T>(ch[k]);
         accO[k].x = fma(av.x, q, accO[k].x);
         accO[k].y = fma(av.y, q, accO[k].y);
       }
@@ -174,7 +186,7 @@ __device__ __forceinline__ typename V2<T>::t shfl2(typename V2<T>::t v, int mask
   return r;
 }
 
-template <typename T>
+template <typename T, class CH = Chain>
 __global__ void __launch_bounds__(128) legendre_adj_k(LegArgs a, const typename V2<T>::t* __restrict__ Gt,
                                                       typename V2<T>::t* __restrict__ partial, int nitems,
                                                       int64_t nalm) {
@@ -189,7 +201,7 @@ __global__ void __launch_bounds__(128) legendre_adj_k(LegArgs a, const typename 
   const int mb = mbase_of(L, m);
   const T sg = (m & 1) ? (T)-1 : (T)1;
   const T2* row = Gt + (size_t)m * M;
-  Chain ch[LEG_K];
+  CH ch[LEG_K];
   T2 SE[LEG_K], SO[LEG_K];
 #pragma unroll
   for (int k = 0; k < LEG_K; ++k) {
@@ -223,15 +235,15 @@ __global__ void __launch_bounds__(128) legendre_adj_k(LegArgs a, const typename 
       const int l = base + s;
       if (l <= L) {
         if (l > m) {
-          const double c = __ldg(a.c + mb + l);
-          const bool rs = __ldg(a.dshift + mb + l) != 0;
+          const auto c = coef(a, mb + l, ch[0]);
+          const int rs = __ldg(a.dshift + mb + l);
 #pragma unroll
           for (int k = 0; k < LEG_K; ++k) chain_step(ch[k], c, rs);
         }
 #pragma unroll
         for (int k = 0; k < LEG_K; ++k) {
           if (ch[k].E == 0) {
-            T q = conv<T>(ch[k].q1);
+            T q = qconv<T>(ch[k]);
             const T2 S = (s & 1) ? SO[k] : SE[k];
             v[s].x = fma(q, S.x, v[s].x);
             v[s].y = fma(q, S.y, v[s].y);
@@ -382,13 +394,23 @@ __global__ void scale_alm_df_k(const double* __restrict__ alm, const double* __r
   at[i] = r;
 }
 
-__device__ __forceinline__ void df_acc_step(float4& acc, const float4 av, double q) {
+// q as a float pair: split off the FP64 chain's double, or the double-float
+// chain's own pair
+__device__ __forceinline__ void qsplit(const Chain& ch, float& qh, float& ql) { split_q(ch.q1, qh, ql); }
+__device__ __forceinline__ void qsplit(const DfChain& ch, float& qh, float& ql) {
+  qh = ch.q1.x;
+  ql = ch.q1.y;
+}
+
+template <class CH>
+__device__ __forceinline__ void df_acc_step(float4& acc, const float4 av, const CH& ch) {
   float qh, ql;
-  split_q(q, qh, ql);
+  qsplit(ch, qh, ql);
   df_mac(acc.x, acc.y, av.x, av.y, qh, ql);
   df_mac(acc.z, acc.w, av.z, av.w, qh, ql);
 }
 
+template <class CH>
 __global__ void __launch_bounds__(128) legendre_synth_df_k(LegArgs a, const float4* __restrict__ at,
                                                            double2* __restrict__ G, int nitems) {
   const int lane = threadIdx.x & 31;
@@ -398,7 +420,7 @@ __global__ void __launch_bounds__(128) legendre_synth_df_k(LegArgs a, const floa
   item_of(a, it, m, blk);
   const int L = a.lmax;
   const int mb = mbase_of(L, m);
-  Chain ch[LEG_K];
+  CH ch[LEG_K];
   float4 accE[LEG_K], accO[LEG_K];
 #pragma unroll
   for (int k = 0; k < LEG_K; ++k) {
@@ -410,39 +432,39 @@ __global__ void __launch_bounds__(128) legendre_synth_df_k(LegArgs a, const floa
     const float4 av = at[mb + m];
 #pragma unroll
     for (int k = 0; k < LEG_K; ++k)
-      if (ch[k].E == 0) df_acc_step(accE[k], av, ch[k].q1);
+      if (ch[k].E == 0) df_acc_step(accE[k], av, ch[k]);
   }
   int l = m + 1;
   for (; l + 1 <= L; l += 2) {
     {
-      const double c = __ldg(a.c + mb + l);
-      const bool rs = __ldg(a.dshift + mb + l) != 0;
+      const auto c = coef(a, mb + l, ch[0]);
+      const int rs = __ldg(a.dshift + mb + l);
       const float4 av = at[mb + l];
 #pragma unroll
       for (int k = 0; k < LEG_K; ++k) {
         chain_step(ch[k], c, rs);
-        if (ch[k].E == 0) df_acc_step(accO[k], av, ch[k].q1);
+        if (ch[k].E == 0) df_acc_step(accO[k], av, ch[k]);
       }
     }
     {
-      const double c = __ldg(a.c + mb + l + 1);
-      const bool rs = __ldg(a.dshift + mb + l + 1) != 0;
+      const auto c = coef(a, mb + l + 1, ch[0]);
+      const int rs = __ldg(a.dshift + mb + l + 1);
       const float4 av = at[mb + l + 1];
 #pragma unroll
       for (int k = 0; k < LEG_K; ++k) {
         chain_step(ch[k], c, rs);
-        if (ch[k].E == 0) df_acc_step(accE[k], av, ch[k].q1);
+        if (ch[k].E == 0) df_acc_step(accE[k], av, ch[k]);
       }
     }
   }
   if (l <= L) {
-    const double c = __ldg(a.c + mb + l);
-    const bool rs = __ldg(a.dshift + mb + l) != 0;
+    const auto c = coef(a, mb + l, ch[0]);
+    const int rs = __ldg(a.dshift + mb + l);
     const float4 av = at[mb + l];
 #pragma unroll
     for (int k = 0; k < LEG_K; ++k) {
       chain_step(ch[k], c, rs);
-      if (ch[k].E == 0) df_acc_step(accO[k], av, ch[k].q1);
+      if (ch[k].E == 0) df_acc_step(accO[k], av, ch[k]);
     }
   }
   const int M = a.M;
@@ -480,6 +502,7 @@ __device__ __forceinline__ void df4_add(float4& a4, const float4 b4) {
   df_add(a4.z, a4.w, b4.z, b4.w);
 }
 
+template <class CH>
 __global__ void __launch_bounds__(128, 5) legendre_adj_df_k(LegArgs a, const double2* __restrict__ Gt,
                                                          float4* __restrict__ partial, int nitems, int64_t nalm) {
   const int lane = threadIdx.x & 31;
@@ -492,7 +515,7 @@ __global__ void __launch_bounds__(128, 5) legendre_adj_df_k(LegArgs a, const dou
   const int mb = mbase_of(L, m);
   const double sg = (m & 1) ? -1.0 : 1.0;
   const double2* row = Gt + (size_t)m * M;
-  Chain ch[LEG_K];
+  CH ch[LEG_K];
   // folded spectrum per chain as double-float (hi_re, lo_re, hi_im, lo_im),
   // even / odd l - m; kept in shared memory to leave registers for occupancy
   __shared__ float4 sS[2][LEG_K][128];
@@ -529,8 +552,8 @@ __global__ void __launch_bounds__(128, 5) legendre_adj_df_k(LegArgs a, const dou
       const int l = base + st;
       if (l <= L) {
         if (l > m) {
-          const double c = __ldg(a.c + mb + l);
-          const bool rs = __ldg(a.dshift + mb + l) != 0;
+          const auto c = coef(a, mb + l, ch[0]);
+          const int rs = __ldg(a.dshift + mb + l);
 #pragma unroll
           for (int k = 0; k < LEG_K; ++k) chain_step(ch[k], c, rs);
         }
@@ -538,7 +561,7 @@ __global__ void __launch_bounds__(128, 5) legendre_adj_df_k(LegArgs a, const dou
         for (int k = 0; k < LEG_K; ++k) {
           if (ch[k].E == 0) {
             float qh, ql;
-            split_q(ch[k].q1, qh, ql);
+            qsplit(ch[k], qh, ql);
             const float4 S = (st & 1) ? SO[k * 128] : SE[k * 128];
             df_mac(v[st].x, v[st].y, S.x, S.y, qh, ql);
             df_mac(v[st].z, v[st].w, S.z, S.w, qh, ql);
@@ -633,7 +656,7 @@ __global__ void __launch_bounds__(128) legendre_tab_build_k(LegArgs a, const int
   for (int l = m; l <= L; ++l) {
     const bool step = l > m;
     const double c = step ? __ldg(a.c + mb + l) : 0.0;
-    const bool rs = step && __ldg(a.dshift + mb + l) != 0;
+    const int rs = step ? (int)__ldg(a.dshift + mb + l) : 0;
 #pragma unroll
     for (int k = 0; k < LEG_K; ++k) {
       if (step) chain_step(ch[k], c, rs);
@@ -888,7 +911,7 @@ __global__ void __launch_bounds__(128) legendre_probe_k(LegArgs a, int ntotal, i
   bool sig = __any_sync(FULL, significant());
   for (int l = m + 1; l <= L && !sig; ++l) {
     const double c = __ldg(a.c + mb + l);
-    const bool rs = __ldg(a.dshift + mb + l) != 0;
+    const int rs = __ldg(a.dshift + mb + l);
 #pragma unroll
     for (int k = 0; k < LEG_K; ++k) chain_step(ch[k], c, rs);
     sig = __any_sync(FULL, significant());
@@ -943,6 +966,7 @@ static LegArgs make_args(nusht_plan_t p) {
   a.bpm = p->leg.blocks_per_m;
   a.items = p->leg.items;
   a.c = p->leg.c;
+  a.cdf = p->leg.cdf;
   a.dshift = p->leg.dshift;
   a.cm = p->leg.cm;
   a.ring_x = p->leg.ring_x;
@@ -955,6 +979,11 @@ int legendre_build_tables(nusht_plan_t p, cudaStream_t s) {
   const int64_t nalm = p->nalm;
   std::vector<double> c(nalm), ah(nalm);
   std::vector<int8_t> dsh(nalm, 0);
+  // the double-float recurrence applies to the per-call kernels of mixed
+  // plans and of FP64 plans with float-pair sums; it needs narrower segments
+  const bool fastrec = p->opts.fast_recurrence && !(p->precision == NUSHT_FP64 && p->opts.fp64_contraction) &&
+                       p->opts.legendre_table <= 0 && p->has_nufft;
+  const int seg = fastrec ? LEG_SEG_BITS_DF : LEG_SEG_BITS;
   for (int m = 0; m <= mmax; ++m) {
     const int64_t mb = (int64_t)m * (2 * L + 1 - m) / 2;
     dd a2 = {1.0, 0.0};  // Ahat^2 (scaled)
@@ -970,10 +999,10 @@ int legendre_build_tables(nusht_plan_t p, cudaStream_t s) {
       a2 = dd_div_d(a2, dl * dl - dm * dm);
       int e2 = 0;
       std::frexp(a2.hi, &e2);
-      if (e2 > 2 * LEG_SEG_BITS) {  // Ahat >= 2^48: next segment
-        a2.hi = std::ldexp(a2.hi, -2 * LEG_SEG_BITS);
-        a2.lo = std::ldexp(a2.lo, -2 * LEG_SEG_BITS);
-        dsh[mb + l] = (int8_t)LEG_SEG_BITS;
+      if (e2 > 2 * seg) {  // Ahat >= 2^seg: next segment
+        a2.hi = std::ldexp(a2.hi, -2 * seg);
+        a2.lo = std::ldexp(a2.lo, -2 * seg);
+        dsh[mb + l] = (int8_t)seg;
       }
       ah[mb + l] = dd_sqrt(a2);
       c[mb + l] = (l == m + 1) ? 0.0 : ((dl - 1.0 - dm) * (dl - 1.0 + dm)) / ((2.0 * dl - 3.0) * (2.0 * dl - 1.0));
@@ -1014,6 +1043,16 @@ int legendre_build_tables(nusht_plan_t p, cudaStream_t s) {
   NUSHT_TRY(dev_alloc((void**)&t.ring_s, npairs * 8, &p->bytes));
   NUSHT_TRY(dev_alloc((void**)&t.pole_norm, (L + 1) * 8, &p->bytes));
   NUSHT_CUDA(cudaMemcpyAsync(t.c, c.data(), nalm * 8, cudaMemcpyHostToDevice, s));
+  if (fastrec) {
+    std::vector<float2> cd(nalm);
+    for (int64_t i = 0; i < nalm; ++i) {
+      const float h = (float)c[i];
+      cd[i] = make_float2(h, (float)(c[i] - (double)h));
+    }
+    NUSHT_TRY(dev_alloc((void**)&t.cdf, nalm * sizeof(float2), &p->bytes));
+    NUSHT_CUDA(cudaMemcpyAsync(t.cdf, cd.data(), nalm * sizeof(float2), cudaMemcpyHostToDevice, s));
+    NUSHT_CUDA(cudaStreamSynchronize(s));
+  }
   NUSHT_CUDA(cudaMemcpyAsync(t.ahat, ah.data(), nalm * 8, cudaMemcpyHostToDevice, s));
   NUSHT_CUDA(cudaMemcpyAsync(t.dshift, dsh.data(), nalm, cudaMemcpyHostToDevice, s));
   NUSHT_CUDA(cudaMemcpyAsync(t.cm, cm.data(), (mmax + 1) * 8, cudaMemcpyHostToDevice, s));
@@ -1084,6 +1123,7 @@ int legendre_build_tables(nusht_plan_t p, cudaStream_t s) {
 
 int legendre_synth(nusht_plan_t p, const void* d_alm, cudaStream_t s) {
   const int64_t nalm = p->nalm;
+  const bool fastrec = p->leg.cdf != nullptr;  // opts.fast_recurrence (built when it applies)
   const int tb = 256;
   const int nb = (int)((nalm + tb - 1) / tb);
   LegArgs a = make_args(p);
@@ -1108,7 +1148,14 @@ int legendre_synth(nusht_plan_t p, const void* d_alm, cudaStream_t s) {
   } else if (p->precision == NUSHT_FP64 && !p->opts.fp64_contraction) {
     scale_alm_df_k<<<nb, tb, 0, s>>>((const double*)d_alm, p->leg.ahat, nalm, p->lmax, (float4*)p->atilde);
     if (nitems > 0)
-      legendre_synth_df_k<<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float4*)p->atilde, (double2*)p->G, nitems);
+    {
+      if (fastrec)
+        legendre_synth_df_k<DfChain><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float4*)p->atilde, (double2*)p->G,
+                                                                      nitems);
+      else
+        legendre_synth_df_k<Chain><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float4*)p->atilde, (double2*)p->G,
+                                                                    nitems);
+    }
     poles_synth_k<double, double><<<1, 256, 0, s>>>((const double*)d_alm, p->leg.pole_norm, p->lmax, p->sz.M,
                                                     (double2*)p->G);
   } else if (p->precision == NUSHT_FP64) {
@@ -1121,7 +1168,13 @@ int legendre_synth(nusht_plan_t p, const void* d_alm, cudaStream_t s) {
   } else {
     scale_alm_k<float, float><<<nb, tb, 0, s>>>((const float*)d_alm, p->leg.ahat, nalm, p->lmax, (float2*)p->atilde);
     if (nitems > 0)
-      legendre_synth_k<float><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float2*)p->atilde, (float2*)p->G, nitems);
+    {
+      if (fastrec)
+        legendre_synth_k<float, DfChain><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float2*)p->atilde,
+                                                                          (float2*)p->G, nitems);
+      else
+        legendre_synth_k<float><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float2*)p->atilde, (float2*)p->G, nitems);
+    }
     poles_synth_k<float, float><<<1, 256, 0, s>>>((const float*)d_alm, p->leg.pole_norm, p->lmax, p->sz.M,
                                                   (float2*)p->G);
   }
@@ -1131,6 +1184,7 @@ int legendre_synth(nusht_plan_t p, const void* d_alm, cudaStream_t s) {
 
 int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
   const int64_t nalm = p->nalm;
+  const bool fastrec = p->leg.cdf != nullptr;
   LegArgs a = make_args(p);
   const int nitems = p->leg.nitems;
   const int tb = 256;
@@ -1152,8 +1206,14 @@ int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
     }
   } else if (p->precision == NUSHT_FP64 && !p->opts.fp64_contraction) {
     if (nitems > 0)
-      legendre_adj_df_k<<<(nitems + 3) / 4, 128, 0, s>>>(a, (const double2*)p->Ghat, (float4*)p->partial, nitems,
-                                                         nalm);
+    {
+      if (fastrec)
+        legendre_adj_df_k<DfChain><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const double2*)p->Ghat, (float4*)p->partial,
+                                                                    nitems, nalm);
+      else
+        legendre_adj_df_k<Chain><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const double2*)p->Ghat, (float4*)p->partial,
+                                                                  nitems, nalm);
+    }
     adj_reduce_df_k<<<nb, tb, 0, s>>>((const float4*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
                                       p->leg.pole_norm, (const double2*)p->Ghat, p->lmax, p->sz.M, (double2*)d_alm);
   } else if (p->precision == NUSHT_FP64) {
@@ -1165,8 +1225,14 @@ int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
                                            (double2*)d_alm);
   } else {
     if (nitems > 0)
-      legendre_adj_k<float><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float2*)p->Ghat, (float2*)p->partial, nitems,
-                                                             nalm);
+    {
+      if (fastrec)
+        legendre_adj_k<float, DfChain><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float2*)p->Ghat,
+                                                                        (float2*)p->partial, nitems, nalm);
+      else
+        legendre_adj_k<float><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const float2*)p->Ghat, (float2*)p->partial,
+                                                               nitems, nalm);
+    }
     adj_reduce_k<float><<<nb, tb, 0, s>>>((const float2*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
                                           p->leg.pole_norm, (const float2*)p->Ghat, p->lmax, p->sz.M, (float2*)d_alm);
   }

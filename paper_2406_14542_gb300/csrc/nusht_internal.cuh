@@ -50,6 +50,7 @@ void dev_free(void* p);
 constexpr int LEG_K = 4;                 // ring pairs per lane
 constexpr int LEG_PAIRS_PER_WARP = 32 * LEG_K;
 constexpr int LEG_SEG_BITS = 48;         // rescaled normalisation kept in [1, 2^(48+8))
+constexpr int LEG_SEG_BITS_DF = 24;      // the same with the double-float recurrence
 
 // Start exponent threshold of the scaled phase: values below 2^-300 (relative
 // to the rescaled normalisation) are not accumulated (Sec. 3: on-the-fly
@@ -60,6 +61,7 @@ constexpr int LEG_STEP_EXP = 256;        // scaled-phase exponent step
 struct LegTables {
   // per (l, m) packed m-major, nalm entries
   double* c = nullptr;        // c_lm = (l-1-m)(l-1+m)/((2l-3)(2l-1)) (0 for l = m, m+1)
+  float2* cdf = nullptr;      // c_lm as a float pair (opts.fast_recurrence only)
   double* ahat = nullptr;     // rescaled normalisation Ahat_lm (>= 1)
   int8_t* dshift = nullptr;   // rescale exponent applied before step l (0 = none)
   // per m

@@ -204,6 +204,7 @@ static void plan_free(nusht_plan_t p) {
   cudaSetDevice(p->device);
   free_points(p);
   dev_free(p->leg.c);
+  dev_free(p->leg.cdf);
   dev_free(p->leg.ahat);
   dev_free(p->leg.dshift);
   dev_free(p->leg.cm);

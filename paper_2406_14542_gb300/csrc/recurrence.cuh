@@ -132,13 +132,14 @@ __device__ __forceinline__ double scale_pow2(double v, int k) {
   return __hiloint2double(hi, lo);
 }
 
-// Advance to degree l: optional segment rescale (q_{l-1}, q_{l-2}) *= 2^48,
-// then q_l = x q_{l-1} - c q_{l-2}: two FP64 operations.  In the scaled phase
-// the exponent check and the 2^-256 step are integer operations.
-__device__ __forceinline__ void chain_step(Chain& ch, double c, bool do_rescale) {
-  if (do_rescale) {
-    ch.q1 = scale_pow2(ch.q1, LEG_SEG_BITS);
-    ch.q2 = scale_pow2(ch.q2, LEG_SEG_BITS);
+// Advance to degree l: optional segment rescale (q_{l-1}, q_{l-2}) *= 2^shift
+// (shift from the plan's table: its segment width, or 0), then
+// q_l = x q_{l-1} - c q_{l-2}: two FP64 operations.  In the scaled phase the
+// exponent check and the 2^-256 step are integer operations.
+__device__ __forceinline__ void chain_step(Chain& ch, double c, int shift) {
+  if (shift) {
+    ch.q1 = scale_pow2(ch.q1, shift);
+    ch.q2 = scale_pow2(ch.q2, shift);
   }
   double t = c * ch.q2;
   double q = fma(ch.x, ch.q1, -t);
@@ -153,6 +154,107 @@ __device__ __forceinline__ void chain_step(Chain& ch, double c, bool do_rescale)
     }
   }
 }
+
+// ---------------------------------------------------------------------------
+// The same recurrence in double-float (opt-in, opts.fast_recurrence): x, q_l
+// and c_l are float pairs hi + lo, one step is two exact float-pair products
+// and a two-sum difference, renormalised (~20 FP32 operations, ~2^-47
+// relative per step, against two FP64 operations on a pipe 62x slower).
+// The float exponent range changes two things.  The plan's normalisation
+// segments are LEG_SEG_BITS_DF = 24 bits wide (so q = Pbar / Ahat varies by at
+// most 2^24 against Pbar inside a segment), and values below 2^-76 are
+// carried as q * 2^E (E a multiple of 64): an ordinary value then stays above
+// 2^-100 with a normal lo word, and a scaled one has |Pbar| < 2^-52.
+// ---------------------------------------------------------------------------
+constexpr int DF_TINY_EXP = -76;
+constexpr int DF_STEP_EXP = 64;
+
+struct DfChain {
+  float2 x, q1, q2;
+  int E;  // > 0: scaled phase, value = q * 2^-E; 0: ordinary values
+  bool valid;
+};
+
+// float pair of a double (plan/initialisation only: FP64 conversions)
+__device__ __forceinline__ float2 df2_of(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+// v * 2^k, -126 <= k <= 127: one FP32 multiply by an exact power of two
+// (correct for zero and subnormal inputs as well)
+__device__ __forceinline__ float scale_pow2f(float v, int k) {
+  return __fmul_rn(v, __uint_as_float((unsigned)(k + 127) << 23));
+}
+
+template <class A>
+__device__ __forceinline__ void chain_init(DfChain& ch, const A& a, int m, int j) {
+  ch.valid = (j >= 1 && j <= a.npairs);
+  ch.q2 = make_float2(0.f, 0.f);
+  if (!ch.valid) {
+    ch.x = make_float2(0.f, 0.f);
+    ch.q1 = make_float2(0.f, 0.f);
+    ch.E = 0;
+    return;
+  }
+  ch.x = df2_of(__ldg(a.ring_x + (j - 1)));
+  const double s = __ldg(a.ring_s + (j - 1));
+  double mant;
+  int ex;
+  pow_scaled(s, m, mant, ex);
+  const double q0 = __ldg(a.cm + m) * mant;
+  if (ex >= DF_TINY_EXP) {
+    ch.q1 = df2_of(q0 * exp2i(ex));
+    ch.E = 0;
+  } else {
+    const int E = DF_STEP_EXP * ((DF_TINY_EXP - ex + DF_STEP_EXP - 1) / DF_STEP_EXP);
+    ch.q1 = df2_of(q0 * exp2i(ex + E));
+    ch.E = E;
+  }
+}
+
+__device__ __forceinline__ void chain_step(DfChain& ch, float2 c, int shift) {
+  if (shift) {
+    ch.q1 = make_float2(scale_pow2f(ch.q1.x, shift), scale_pow2f(ch.q1.y, shift));
+    ch.q2 = make_float2(scale_pow2f(ch.q2.x, shift), scale_pow2f(ch.q2.y, shift));
+  }
+  // x q1 and c q2, each exact product plus cross terms
+  const float p1 = __fmul_rn(ch.x.x, ch.q1.x);
+  float e1 = __fmaf_rn(ch.x.x, ch.q1.x, -p1);
+  e1 = __fmaf_rn(ch.x.x, ch.q1.y, __fmaf_rn(ch.x.y, ch.q1.x, e1));
+  const float p2 = __fmul_rn(c.x, ch.q2.x);
+  float e2 = __fmaf_rn(c.x, ch.q2.x, -p2);
+  e2 = __fmaf_rn(c.x, ch.q2.y, __fmaf_rn(c.y, ch.q2.x, e2));
+  // (p1 - p2) by two-sum, then the error terms, then renormalise
+  const float sd = __fsub_rn(p1, p2);
+  const float bp = __fsub_rn(sd, p1);
+  const float err = __fadd_rn(__fsub_rn(p1, __fsub_rn(sd, bp)), __fsub_rn(-p2, bp));
+  const float t = __fadd_rn(err, __fsub_rn(e1, e2));
+  const float hi = __fadd_rn(sd, t);
+  ch.q2 = ch.q1;
+  ch.q1 = make_float2(hi, __fsub_rn(t, __fsub_rn(hi, sd)));
+  if (ch.E != 0) {
+    const int expo = (int)((__float_as_uint(ch.q1.x) >> 23) & 0xff);
+    if (expo >= 127 + DF_TINY_EXP + DF_STEP_EXP) {
+      ch.q1 = make_float2(scale_pow2f(ch.q1.x, -DF_STEP_EXP), scale_pow2f(ch.q1.y, -DF_STEP_EXP));
+      ch.q2 = make_float2(scale_pow2f(ch.q2.x, -DF_STEP_EXP), scale_pow2f(ch.q2.y, -DF_STEP_EXP));
+      ch.E -= DF_STEP_EXP;
+    }
+  }
+}
+
+// per-chain-type access: the step coefficient and the current value as a
+// float pair or a single float
+template <class A>
+__device__ __forceinline__ double coef(const A& a, int i, const Chain&) {
+  return __ldg(a.c + i);
+}
+template <class A>
+__device__ __forceinline__ float2 coef(const A& a, int i, const DfChain&) {
+  return __ldg(a.cdf + i);
+}
+__device__ __forceinline__ float qf(const Chain& ch) { return to_f32(ch.q1); }
+__device__ __forceinline__ float qf(const DfChain& ch) { return ch.q1.x; }
 
 }  // namespace rec
 }  // namespace nusht

@@ -379,3 +379,37 @@ def test_deterministic_adjoint(env, prec, fc, n):
     pa = nu.Plan(L, dev(torch, pts), eps=TOL[prec], precision=prec, fp64_contraction=fc)
     ca = pa.adjoint(dy).cpu().numpy().astype(np.complex128)
     assert np.linalg.norm(got - ca) <= (1e-12 if prec == "fp64" else 1e-5) * np.linalg.norm(ca)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fast_recurrence(env, prec):
+    """opts.fast_recurrence: the P_lm recurrence in double-float on the FP32
+    pipe.  Synthesis on a seeded subset and the adjoint on an order subset
+    against the oracle at the plan's tolerance (lmax 1023 on the deflected
+    grid, where orders run into the scaled-exponent phase), the dot test, and
+    agreement with the FP64 recurrence."""
+    torch, nu = env
+    L, a, pts = W.workload("gl1023")
+    cd = torch.complex128 if prec == "fp64" else torch.complex64
+    rd = torch.float64 if prec == "fp64" else torch.float32
+    dp = dev(torch, pts)
+    plan = nu.Plan(L, dp, eps=TOL[prec], precision=prec, fast_recurrence=True)
+    ref_plan = nu.Plan(L, dp, eps=TOL[prec], precision=prec)
+    ad = dev(torch, a, cd)
+    f = plan.synth(ad).double().cpu().numpy()
+    sel = W.subset(pts.shape[0], 3000, seed=16)
+    assert oracle.eps_eff(oracle.synth(a, pts[sel], L), f[sel]) <= TOL[prec]
+    f0 = ref_plan.synth(ad).double().cpu().numpy()
+    assert np.linalg.norm(f - f0) <= (1e-11 if prec == "fp64" else 3e-6) * np.linalg.norm(f0)
+    y = np.random.default_rng(17).standard_normal(pts.shape[0])
+    if prec == "mixed":
+        y = y.astype(np.float32).astype(np.float64)
+    c = plan.adjoint(dev(torch, y, rd)).cpu().numpy().astype(np.complex128)
+    ms = [0, 1, 300, 700, 1023]
+    ref = oracle.adjoint(y, pts, L, mlist=ms)
+    idx = np.concatenate([np.arange(oracle.lm_index(L, m, m), oracle.lm_index(L, L, m) + 1) for m in ms])
+    assert oracle.eps_eff(ref[idx], c[idx]) <= TOL[prec]
+    if prec == "fp64":
+        lhs = float(np.dot(y, f))
+        rhs = oracle.alm_dot(c, a, L)
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
