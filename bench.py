@@ -220,6 +220,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-transform batched measurement")
     ap.add_argument("--no-table", action="store_true", help="skip the recurrence-table (legendre_table=1) runs")
+    ap.add_argument("--no-fast", action="store_true",
+                    help="skip the opt-in double-float recurrence (fast_recurrence=1) runs")
     ap.add_argument("--only-batch", action="store_true", help="run only the 64-transform batched measurement")
     ap.add_argument("--batch-n", type=int, default=64, help="transforms in the batched workload")
     ap.add_argument("--batch-lmax", type=int, default=2047, help="largest lmax of the batched workload")
@@ -247,15 +249,19 @@ def main():
     dpts = torch.from_numpy(pts).cuda()
     results = {}
     y_host = np.random.default_rng(5).standard_normal(npts)
-    runs = [("fp64", 0)] + ([] if args.no_mixed else [("mixed", 0)])
+    # (precision, recurrence table, double-float recurrence)
+    runs = [("fp64", 0, False)] + ([] if args.no_mixed else [("mixed", 0, False)])
     if not args.no_table:
-        runs += [("fp64", 1)] + ([] if args.no_mixed else [("mixed", 1)])
-    for prec, table in runs:
-        key = prec if not table else prec + "_table"
+        runs += [("fp64", 1, False)] + ([] if args.no_mixed else [("mixed", 1, False)])
+    if not args.no_fast:
+        runs += [("fp64", 0, True)] + ([] if args.no_mixed else [("mixed", 0, True)])
+    for prec, table, fastrec in runs:
+        key = prec + ("_table" if table else "") + ("_fast_recurrence" if fastrec else "")
         cd = torch.complex128 if prec == "fp64" else torch.complex64
         rd = torch.float64 if prec == "fp64" else torch.float32
         t0 = time.perf_counter()
-        plan = nu.Plan(L, dpts, eps=EPS[prec], precision=prec, profile=True, legendre_table=table)
+        plan = nu.Plan(L, dpts, eps=EPS[prec], precision=prec, profile=True, legendre_table=table,
+                       fast_recurrence=fastrec)
         torch.cuda.synchronize()
         t_plan = time.perf_counter() - t0
         ad = torch.from_numpy(a).to(cd).cuda()
@@ -378,6 +384,14 @@ def main():
                          "plan_GB": r["info"]["bytes_device"] / 1e9,
                          "what": "opts.legendre_table=1: the FP64 recurrence runs once at plan time and its "
                                  "values stay in HBM; each call streams them"}
+    for key in ("fp64_fast_recurrence", "mixed_fast_recurrence"):
+        if key in results:
+            r = results[key]
+            line[key] = {"ms_per_step": r["ms"], "eps_eff": r["eps_eff"],
+                         "synth_ms": r["stages"]["synth"]["total"], "adjoint_ms": r["stages"]["adjoint"]["total"],
+                         "legendre_ms": [r["stages"]["synth"]["legendre"], r["stages"]["adjoint"]["legendre"]],
+                         "what": "opts.fast_recurrence=1 (opt-in): the P_lm recurrence in double-float on the FP32 "
+                                 "pipe instead of FP64"}
     if batch is not None:
         line["batch64"] = batch
     if cpu is not None:
