@@ -66,11 +66,11 @@ __global__ void bucket_scale_k(int L, int B, const int* __restrict__ memberL, co
   float2 v = make_float2(0.f, 0.f);
   if (slot < B) {
     const int Lb = memberL[slot];
-    if (l <= Lb && m <= Lb) {
+    if (l <= Lb && m <= Lb) {  // single precision suffices for complex64 coefficients
       const float2 a = alm[slot][idx_lm(Lb, l, m)];
-      const double ah = ahat[i];
-      v.x = (float)((double)a.x * ah);
-      v.y = m == 0 ? 0.f : (float)((double)a.y * ah);
+      const float ah = (float)ahat[i];
+      v.x = a.x * ah;
+      v.y = m == 0 ? 0.f : a.y * ah;
     }
   }
   atb[(size_t)i * BK_MAXB + slot] = v;
@@ -929,14 +929,15 @@ __global__ void bucket_final_k(int L, int M, int B, const int* __restrict__ memb
   if (l > Lb || m > Lb) return;
   const int i = idx_lm(L, l, m);
   const float2 v = reinterpret_cast<const float2*>(cacc + (size_t)i * BK_COLS)[slot];
-  const double ah = ahat[i];
-  double re = (double)v.x * ah, im = (double)v.y * ah;
+  const float ah = (float)ahat[i];
+  float re = v.x * ah, im = v.y * ah;
   if (m == 0) {
     const float2* row = Gt + (size_t)slot * (L + 1) * M;
-    re += pole_norm[l] * ((double)row[0].x + ((l & 1) ? -(double)row[M / 2].x : (double)row[M / 2].x));
-    im = 0.0;
+    const float pn = (float)pole_norm[l];
+    re += pn * (row[0].x + ((l & 1) ? -row[M / 2].x : row[M / 2].x));
+    im = 0.f;
   }
-  out[slot][idx_lm(Lb, l, m)] = make_float2((float)re, (float)im);
+  out[slot][idx_lm(Lb, l, m)] = make_float2(re, im);
 }
 
 struct Bucket {

@@ -603,12 +603,15 @@ __global__ void adj_reduce_df_k(const float4* __restrict__ partial, int bpm, int
                                 const double2* __restrict__ Gt, int lmax, int M, double2* out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nalm) return;
-  double sx = 0.0, sy = 0.0;
+  // the block partials summed as float pairs (FP32 pipe), in a fixed order,
+  // then one conversion to double
+  float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
   for (int b = 0; b < bpm; ++b) {
     const float4 v = partial[(size_t)b * nalm + i];
-    sx += (double)v.x + (double)v.y;
-    sy += (double)v.z + (double)v.w;
+    df_add(xh, xl, v.x, v.y);
+    df_add(yh, yl, v.z, v.w);
   }
+  double sx = df_value(xh, xl), sy = df_value(yh, yl);
   const double ah = ahat[i];
   sx *= ah;
   sy *= ah;
