@@ -154,6 +154,22 @@ def time_steps(torch, fn, steps: int, warmup: int, dist):
     return e0.elapsed_time(e1) / steps
 
 
+def step_spread(torch, fn, reps: int = 20):
+    """Median and standard deviation of single-step device times (CUDA events
+    around each step, after the timed run has warmed everything up)."""
+    s = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts)), float(np.std(ts))
+
+
 def stage_breakdown(torch, plan, ad, y, reps: int = 3):
     """Per-stage device times from the library's own stream events."""
     acc = None
@@ -220,6 +236,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-transform batched measurement")
     ap.add_argument("--no-table", action="store_true", help="skip the recurrence-table (legendre_table=1) runs")
+    ap.add_argument("--sweep", action="store_true",
+                    help="accuracy / speed sweep over eps x sigma on the lmax 1023 deflected grid (one JSON line)")
     ap.add_argument("--no-fast", action="store_true",
                     help="skip the opt-in double-float recurrence (fast_recurrence=1) runs")
     ap.add_argument("--only-batch", action="store_true", help="run only the 64-transform batched measurement")
@@ -238,6 +256,10 @@ def main():
     import paper_2406_14542_gb300 as nu
 
     dist, rank, world, local = dist_setup(args.gpus)
+    if args.sweep:
+        if rank == 0:
+            print(json.dumps({"sweep": run_sweep(torch, nu, args)}), flush=True)
+        return
     if args.only_batch:
         b = run_batch64(torch, nu, args, dist, rank, sequential=False)
         if rank == 0:
@@ -276,6 +298,7 @@ def main():
         with Clocks(local) as clk:
             ms = time_steps(torch, step, args.steps, args.warmup, dist)
         ms = max_over_ranks(dist, ms)
+        med, std = step_spread(torch, step, 20 if key == "fp64" else 5)
         stages = stage_breakdown(torch, plan, ad, y)
         # parity on a seeded subset against the oracle (rank 0)
         par = None
@@ -287,30 +310,79 @@ def main():
             f = plan.synth(ad).double().cpu().numpy()
             par = oracle.eps_eff(f_ref, f[sel])
         results[key] = {"ms": ms, "plan_s": t_plan, "stages": stages, "clocks": clk.summary(), "eps_eff": par,
-                        "info": plan.info()}
+                        "info": plan.info(), "median": med, "std": std}
         if key == "fp64":
-            # end to end through the public API with host buffers (pinned),
-            # copies inside the timed region
-            a_pin = torch.from_numpy(a).pin_memory()
-            y_pin = torch.from_numpy(y_host).pin_memory()
-            f_pin = torch.empty(npts, dtype=torch.float64).pin_memory()
-            c_pin = torch.empty(plan.nalm, dtype=torch.complex128).pin_memory()
-            a_dev = torch.empty_like(ad)
-            y_dev = torch.empty_like(y)
+            # end to end through the public API with host buffers (pinned):
+            # every step uploads its a_lm and map and downloads its map and
+            # coefficients.  A copy stream overlaps the uploads and downloads
+            # with compute (y's upload with the synthesis, the map's download
+            # with the adjoint, the next a_lm's upload with this adjoint);
+            # device and host buffers alternate between two slots.
+            nb = 2
+            a_pin = [torch.from_numpy(a).pin_memory() for _ in range(nb)]
+            y_pin = [torch.from_numpy(y_host).pin_memory() for _ in range(nb)]
+            f_pin = [torch.empty(npts, dtype=torch.float64).pin_memory() for _ in range(nb)]
+            c_pin = [torch.empty(plan.nalm, dtype=torch.complex128).pin_memory() for _ in range(nb)]
+            a_dev = [torch.empty_like(ad) for _ in range(nb)]
+            y_dev = [torch.empty_like(y) for _ in range(nb)]
+            f_dev = [torch.empty_like(fmap) for _ in range(nb)]
+            c_dev = [torch.empty_like(calm) for _ in range(nb)]
+            hs, ds = torch.cuda.Stream(), torch.cuda.Stream()  # uploads, downloads
+            comp = torch.cuda.current_stream()
+            ev = {k: [torch.cuda.Event() for _ in range(nb)] for k in ("a", "y", "f", "c", "fd", "cd")}
+            it = [0]
 
             def e2e_step():
-                a_dev.copy_(a_pin, non_blocking=True)
-                plan.synth(a_dev, out=fmap)
-                f_pin.copy_(fmap, non_blocking=True)
-                y_dev.copy_(y_pin, non_blocking=True)
-                plan.adjoint(y_dev, out=calm)
-                c_pin.copy_(calm, non_blocking=True)
+                b = it[0] % nb
+                it[0] += 1
+                with torch.cuda.stream(hs):
+                    hs.wait_event(ev["c"][b])  # slot b's inputs are free once its last adjoint ran
+                    a_dev[b].copy_(a_pin[b], non_blocking=True)
+                    ev["a"][b].record(hs)
+                    y_dev[b].copy_(y_pin[b], non_blocking=True)
+                    ev["y"][b].record(hs)
+                comp.wait_event(ev["a"][b])
+                comp.wait_event(ev["fd"][b])  # slot b's map has been downloaded
+                plan.synth(a_dev[b], out=f_dev[b])
+                ev["f"][b].record(comp)
+                with torch.cuda.stream(ds):
+                    ds.wait_event(ev["f"][b])
+                    f_pin[b].copy_(f_dev[b], non_blocking=True)
+                    ev["fd"][b].record(ds)
+                comp.wait_event(ev["y"][b])
+                comp.wait_event(ev["cd"][b])
+                plan.adjoint(y_dev[b], out=c_dev[b])
+                ev["c"][b].record(comp)
+                with torch.cuda.stream(ds):
+                    ds.wait_event(ev["c"][b])
+                    c_pin[b].copy_(c_dev[b], non_blocking=True)
+                    ev["cd"][b].record(ds)
 
-            e2e_ms = max_over_ranks(dist, time_steps(torch, e2e_step, args.steps, 1, dist))
-            h2d = a_pin.numel() * 16 + y_pin.numel() * 8
-            d2h = f_pin.numel() * 8 + c_pin.numel() * 16
+            def drain():  # the timed region ends when the last downloads have landed
+                comp.wait_stream(ds)
+                comp.wait_stream(hs)
+
+            for b in range(nb):  # events start recorded, so the first waits pass
+                for k in ev:
+                    ev[k][b].record(comp)
+            e2e_step()
+            drain()
+            barrier(dist)
+            t0e = torch.cuda.Event(enable_timing=True)
+            t1e = torch.cuda.Event(enable_timing=True)
+            t0e.record(comp)
+            for _ in range(args.steps):
+                e2e_step()
+            drain()
+            t1e.record(comp)
+            barrier(dist)
+            e2e_ms = max_over_ranks(dist, t0e.elapsed_time(t1e) / args.steps)
+            h2d = a_pin[0].numel() * 16 + y_pin[0].numel() * 8
+            d2h = f_pin[0].numel() * 8 + c_pin[0].numel() * 16
             results["e2e"] = {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d,
-                              "d2h_bytes_per_step": d2h}
+                              "d2h_bytes_per_step": d2h,
+                              "how": "public API; pinned host buffers; every step's uploads and downloads inside "
+                                     "the timed region, overlapped with compute on upload / download streams"}
         plan.close()
         del ad, y, fmap, calm
         torch.cuda.empty_cache()
@@ -365,13 +437,15 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "synth_ms": fp["stages"]["synth"]["total"], "adjoint_ms": fp["stages"]["adjoint"]["total"],
         "stages_ms": fp["stages"], "eps_eff": fp["eps_eff"], "plan_s": fp["plan_s"],
+        "step_ms_median": fp["median"], "step_ms_std": fp["std"],
         "roofline": roofline, "e2e": results.get("e2e"),
         "gpu_launches": launches_per_step * args.steps,
         "clocks": fp["clocks"], "peak_source": peak_src,
     }
     if "mixed" in results:
         mx = results["mixed"]
-        line["mixed"] = {"ms_per_step": mx["ms"], "eps": 1e-5, "eps_eff": mx["eps_eff"],
+        line["mixed"] = {"ms_per_step": mx["ms"], "step_ms_median": mx["median"], "step_ms_std": mx["std"],
+                         "eps": 1e-5, "eps_eff": mx["eps_eff"],
                          "synth_ms": mx["stages"]["synth"]["total"], "adjoint_ms": mx["stages"]["adjoint"]["total"],
                          "stages_ms": mx["stages"], "w": mx["info"]["w"], "sigma": mx["info"]["sigma"],
                          "dtype": "f64 recurrence / f32 contraction, FFT, NUFFT", "clocks": mx["clocks"]}
@@ -399,6 +473,51 @@ def main():
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_sweep(torch, nu, args):
+    """eps in {1e-2, 1e-6, 1e-10} x sigma in {1.25, 1.5, 2} (FP64; mixed for
+    eps >= 1e-6) on the lmax 1023 deflected GL grid: eps_eff against the oracle
+    on a 3000-point subset, milliseconds per synthesis + adjoint and the
+    per-stage split, as the paper's accuracy/operator breakdown does."""
+    import oracle
+
+    L, a, pts = W.workload("gl1023")
+    npts = pts.shape[0]
+    dpts = torch.from_numpy(pts).cuda()
+    sel = W.subset(npts, 3000, seed=18)
+    f_ref = oracle.synth(a, pts[sel], L)
+    y_host = np.random.default_rng(6).standard_normal(npts)
+    out = []
+    for prec in ("fp64", "mixed"):
+        cd = torch.complex128 if prec == "fp64" else torch.complex64
+        rd = torch.float64 if prec == "fp64" else torch.float32
+        ad = torch.from_numpy(a).to(cd).cuda()
+        y = torch.from_numpy(y_host).to(rd).cuda()
+        for eps in (1e-2, 1e-6, 1e-10):
+            if prec == "mixed" and eps < 1e-6:
+                continue
+            for sigma in (1.25, 1.5, 2.0):
+                try:
+                    plan = nu.Plan(L, dpts, eps=eps, precision=prec, sigma=sigma, profile=True)
+                except Exception as e:  # width beyond the kernel limit
+                    out.append({"precision": prec, "eps": eps, "sigma": sigma, "unavailable": str(e)})
+                    continue
+
+                def step():
+                    plan.synth(ad)
+                    plan.adjoint(y)
+
+                ms = time_steps(torch, step, 3, 2, None)
+                f = plan.synth(ad).double().cpu().numpy()
+                st = stage_breakdown(torch, plan, ad, y)
+                info = plan.info()
+                out.append({"precision": prec, "eps": eps, "sigma": sigma, "w": info["w"],
+                            "fine_grid": info["n1"], "eps_eff": oracle.eps_eff(f_ref, f[sel]), "ms_per_step": ms,
+                            "stages_ms": st})
+                plan.close()
+                torch.cuda.empty_cache()
+    return {"workload": "deflected GL grid 1024x2047 (%d pts), lmax=mmax=1023" % npts, "runs": out}
 
 
 def run_batch64(torch, nu, args, dist, rank, sequential=True):

@@ -116,6 +116,9 @@ int tune_sigma(int lmax, int mmax, int64_t npts, const double* d_pts, double eps
   float best_ms = 1e30f;
   for (int c = 0; c < 3 && st == NUSHT_OK; ++c) {
     if (es_width(0.1 * eps, cand[c]) > ES_WMAX) continue;  // accuracy not reachable within the width limit
+    // FP32 rounding amplified by the large deconvolution factors of sigma =
+    // 1.25 measured eps_eff 2.2e-6 at eps = 1e-6 (lmax 1023): not offered there
+    if (precision == NUSHT_MIXED && cand[c] < 1.4 && eps < 1e-5) continue;
     nusht_opts oc = *o;
     oc.sigma = cand[c];
     oc.tune = 1;
