@@ -195,6 +195,15 @@ __global__ void bucket_poles_k(int L, int M, const int* __restrict__ memberL, co
   }
 }
 
+// adjoint, first step for the tensor-core path: the same fold, written as
+// the contraction's B tiles BA[m][table tile][group of 8 ring pairs]: rows =
+// 128 columns (member, re/im), k = the group's 8 ring pairs, E then O, each
+// split into TF32 hi and lo.  Block = (32 ring pairs, order m).
+__global__ void __launch_bounds__(256) bucket_fold_ba_k(int L, int M, int npairs, int B, int ntiles,
+                                                        const int* __restrict__ memberL,
+                                                        const float2* __restrict__ Gt,
+                                                        unsigned char* __restrict__ BA);
+
 // adjoint, first step: D^dagger fold into S[m][pair][E|O][slot (re, im)].
 // Block = (32 ring pairs, order m); each warp reads one member's spectrum
 // row for the 32 pairs contiguously (4 coalesced runs), the block transposes
@@ -575,25 +584,26 @@ __global__ void __launch_bounds__(256) bucket_adj_tab_k(BucketArgs a, const int*
 // Data flow.  A chunk (one K step of both parities) is 8 operand tiles of
 // 4 KB in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per
 // core matrix; K-adjacent core matrices 128 B apart, 8-row groups 256 B
-// apart).  Four chunk buffers rotate; threads 0..127 split and store the A
-// rows, threads 128..255 the B rows, global loads run two chunks ahead in
-// registers; one thread issues the six MMAs of a chunk and commits them to
-// the buffer's mbarrier.  Registers: warps 0..3 own the E sums of their 32
-// TMEM lanes, warps 4..7 the O sums.  One block per SM (512 TMEM columns;
-// the shared-memory size admits no second block).  Every wait is bounded
-// (one second of device time); a block that gives up sets *status, issues
-// nothing more, and still frees its tensor memory.
+// apart): A_E hi, A_E lo, A_O hi, A_O lo, then the same for B.  Operands are
+// split and laid out before the contraction, so that the contraction moves
+// them only with the bulk copy engine: the A tiles at plan time from the
+// recurrence table (one copy in synthesis order, one in adjoint order), the
+// B tiles per call by the kernels that produce the coefficients (scaling by
+// Ahat) and the folded spectrum.  Warp roles: one thread issues two 16 KB
+// cp.async.bulk copies per chunk into a ring of T6_NBUF buffers (mbarrier
+// transaction counts), one thread waits for them and issues the six MMAs,
+// committing to the buffer's "empty" barrier and, at the end of a group, to
+// the group's barrier; 16 warps fold each finished group (64 accumulator
+// columns of 32 TMEM lanes per warp) and arrive on the set's "free" barrier
+// that the MMA thread waits for before refilling it.  One block per SM (512
+// TMEM columns).  Every wait is bounded (one second of device time); a block
+// that gives up flags the others, waits (bounded) for its copies in flight,
+// sets *status and still frees its tensor memory.
 // ---------------------------------------------------------------------------
 constexpr int TC_TILE = 128 * 8 * 4;              // one 128 x 8 fp32 operand tile
 constexpr int TC_CHUNK = 8 * TC_TILE;             // AEh AEl AOh AOl BEh BEl BOh BOl
-constexpr int TC_NBUF = 4;
-constexpr int TC_G = 4;                           // chunks per partial accumulation (>= TC_NBUF - 1)
-constexpr int TC_DEPTH = 3;                       // chunks of global loads in flight per thread
-constexpr int TC_SMEM = TC_NBUF * TC_CHUNK + 64;  // + mbarriers, TMEM address
-constexpr int TC_THREADS = 512;
-constexpr uint32_t TC_COLS = 512;
-static_assert(TC_G + 1 >= TC_NBUF, "a partial set is refilled only after its fold");
-static_assert(128 * 129 * 4 <= TC_NBUF * TC_CHUNK, "epilogue exchange fits the chunk buffers");
+constexpr int TC_G = 4;                           // chunks per partial accumulation
+constexpr uint32_t TC_COLS = 512;                 // two partial sets of D_E, D_O
 // instruction descriptor: D f32 (bits 4-5 = 1), A and B tf32 (bits 7-9,
 // 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
 constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
@@ -670,27 +680,6 @@ __device__ __forceinline__ void tc_store(unsigned char* buf, int tile, int row, 
   *reinterpret_cast<float4*>(pl + 128) = make_float4(l[4], l[5], l[6], l[7]);
 }
 
-// TMEM allocation + mbarrier setup; returns the accumulator base address
-__device__ __forceinline__ uint32_t tc_setup(unsigned char* smem) {
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_NBUF * TC_CHUNK);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + TC_NBUF);
-  if ((threadIdx.x >> 5) == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(TC_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < TC_NBUF; ++k)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[k])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return *tslot;
-}
-
 __device__ __forceinline__ void tc_teardown(uint32_t tmem) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -698,223 +687,363 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS) : "memory");
 }
 
-// Main loop over `nchunk` chunks.  Staging role: thread t stores operand row
-// t % 128 of tile pair t / 128 (0: A even, 1: A odd, 2: B even, 3: B odd);
-// load(c, v) fills its 8 values of chunk c.  Fold role: warp w owns TMEM
-// lanes 32 (w % 4) .. + 31 and accumulator columns 64 (w / 4) .. + 63
-// (columns 0..127 = E, 128..255 = O).  On return (true) acc[] holds those 64
-// sums; false: a wait gave up.
-template <class Load>
-__device__ __forceinline__ bool tc_mainloop(unsigned char* smem, uint32_t tmem, int nchunk, Load load,
-                                            float (&acc)[64]) {
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + TC_NBUF * TC_CHUNK);
-  const int t = threadIdx.x, warp = t >> 5;
-  const int row = t & 127, tile = 2 * (t >> 7);
-  const uint32_t tview = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
+constexpr int T6_NBUF = 6;
+constexpr int T6_FOLD_WARPS = 16;
+constexpr int T6_THREADS = 32 * (T6_FOLD_WARPS + 2);
+constexpr int T6_HALF = TC_CHUNK / 2;  // A or B half of a chunk (16 KB)
+constexpr int T6_SMEM = T6_NBUF * TC_CHUNK + 256;
+static_assert(128 * 129 * 4 <= T6_NBUF * TC_CHUNK, "epilogue exchange fits the chunk buffers");
+
+struct T6Bars {
+  uint64_t full[T6_NBUF], empty[T6_NBUF], gdone[2], gfree[2];
+  uint32_t tslot;
+  int abort;
+};
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// bulk copy global -> shared of `bytes` (multiple of 16, both ends 16-byte
+// aligned), completing on the barrier's transaction count
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
+               : "memory");
+}
+
+// Contraction of one block.  Synthesis (ADJ = false): block = (order m, 128
+// ring pairs), chunks = 16 degrees, A = PA + aoff[block], B = BS + bsoff[m].
+// Adjoint: block = (order m, 256 degrees from r0), chunks = (kept table tile,
+// group of 8 ring pairs), A = PT + aoff[block], B = BA[m][tile][group].
+template <bool ADJ>
+__global__ void __launch_bounds__(T6_THREADS, 1) bucket_tc_k(BucketArgs a, int nblk, const int* __restrict__ titems,
+                                                             const int2* __restrict__ work,
+                                                             const int64_t* __restrict__ aoff,
+                                                             const int64_t* __restrict__ bsoff,
+                                                             const int* __restrict__ items,
+                                                             const int* __restrict__ mfirst, int ntiles,
+                                                             const unsigned char* __restrict__ Atab,
+                                                             const unsigned char* __restrict__ Bbuf,
+                                                             float2* __restrict__ G, float* __restrict__ cacc,
+                                                             int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  T6Bars* bars = reinterpret_cast<T6Bars*>(tc_smem + T6_NBUF * TC_CHUNK);
+  if ((int)blockIdx.x >= nblk || *(volatile int*)status) return;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int L = a.lmax;
+  int m, nchunk, u = 0, r0 = 0, i0 = 0;
+  if (!ADJ) {
+    const int v = titems[blockIdx.x];
+    m = v >> 16;
+    u = v & 0xffff;
+    nchunk = (L - m + 1 + 15) / 16;
+  } else {
+    const int2 wk = work[blockIdx.x];
+    m = wk.x;
+    r0 = wk.y;
+    i0 = mfirst[m];
+    nchunk = (mfirst[m + 1] - i0) * (BS_PAIRS / 8);
+  }
+  const unsigned char* Asrc = Atab + aoff[blockIdx.x];
+  volatile int* abort = &bars->abort;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars->tslot)),
+                 "r"(TC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) {
+    for (int k = 0; k < T6_NBUF; ++k) {
+      mbar_init(&bars->full[k], 1);
+      mbar_init(&bars->empty[k], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&bars->gdone[k], 1);
+      mbar_init(&bars->gfree[k], T6_FOLD_WARPS);
+    }
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = bars->tslot;
+  const int ngroups = (nchunk + TC_G - 1) / TC_G;
+  float acc[64];
 #pragma unroll
   for (int j = 0; j < 64; ++j) acc[j] = 0.f;
-  bool ok = true;
-  int last = -1;  // last chunk whose MMAs were issued
-  int pg = 0;     // next group to fold
-  auto fold = [&](int g) {
-    const uint32_t src = tview + (uint32_t)((g & 1) * 256);
-#pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-      uint32_t r[16];
-      tc_ld16(src + c0, r);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+  if (warp == T6_FOLD_WARPS) {
+    if (lane == 0) {  // producer
+      int issued = 0;
+      for (int c = 0; c < nchunk && !*abort; ++c) {
+        const int s = c % T6_NBUF;
+        if (c >= T6_NBUF && !mbar_wait(smem_u32(&bars->empty[s]), (uint32_t)((c / T6_NBUF - 1) & 1))) {
+          *abort = 1;
+          break;
+        }
+        unsigned char* dst = tc_smem + s * TC_CHUNK;
+        const unsigned char* bsrc;
+        if (ADJ) {
+          const int tile = items[i0 + (c >> 3)] & 0xffff;
+          bsrc = Bbuf + ((size_t)(m * ntiles + tile) * 8 + (c & 7)) * T6_HALF;
+        } else {
+          bsrc = Bbuf + bsoff[m] + (size_t)c * T6_HALF;
+        }
+        mbar_expect_tx(&bars->full[s], TC_CHUNK);
+        bulk_g2s(dst, Asrc + (size_t)c * T6_HALF, T6_HALF, &bars->full[s]);
+        bulk_g2s(dst + T6_HALF, bsrc, T6_HALF, &bars->full[s]);
+        issued = c + 1;
+      }
+      if (*abort)  // wait (bounded) for the copies still in flight
+        for (int c = issued > T6_NBUF ? issued - T6_NBUF : 0; c < issued; ++c)
+          mbar_wait(smem_u32(&bars->full[c % T6_NBUF]), (uint32_t)((c / T6_NBUF) & 1));
     }
-  };
-  float v0[8], v1[8], v2[8];
-  if (nchunk > 0) load(0, v0);
-  if (nchunk > 1) load(1, v1);
-  if (nchunk > 2) load(2, v2);
-  auto step = [&](int c, float (&v)[8]) {
-    const int buf = c % TC_NBUF;
-    unsigned char* bp = smem + buf * TC_CHUNK;
-    if (c >= TC_NBUF && ok) {  // chunk c - NBUF's MMAs (and all before them) have completed
-      ok = mbar_wait(smem_u32(&bars[buf]), (uint32_t)((c / TC_NBUF - 1) & 1));
-      if (ok && (c - TC_NBUF) % TC_G == TC_G - 1) {
+  } else if (warp == T6_FOLD_WARPS + 1) {
+    if (lane == 0) {  // MMA issuer
+      int last = -1;
+      for (int c = 0; c < nchunk && !*abort; ++c) {
+        const int s = c % T6_NBUF;
+        if (!mbar_wait(smem_u32(&bars->full[s]), (uint32_t)((c / T6_NBUF) & 1))) {
+          *abort = 1;
+          break;
+        }
+        const int g = c / TC_G, set = g & 1;
+        if (c % TC_G == 0 && g >= 2 && !mbar_wait(smem_u32(&bars->gfree[set]), (uint32_t)(((g - 2) >> 1) & 1))) {
+          *abort = 1;
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        fold(pg++);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        const uint32_t sb = smem_u32(tc_smem + s * TC_CHUNK);
+        const uint32_t dE = tmem + (uint32_t)(set * 256), dO = dE + 128;
+        const uint32_t acc_on = (c % TC_G) != 0 ? 1u : 0u;
+        tc_mma(dE, tc_desc(sb + 0 * TC_TILE), tc_desc(sb + 4 * TC_TILE), acc_on);
+        tc_mma(dE, tc_desc(sb + 0 * TC_TILE), tc_desc(sb + 5 * TC_TILE), 1u);
+        tc_mma(dE, tc_desc(sb + 1 * TC_TILE), tc_desc(sb + 4 * TC_TILE), 1u);
+        tc_mma(dO, tc_desc(sb + 2 * TC_TILE), tc_desc(sb + 6 * TC_TILE), acc_on);
+        tc_mma(dO, tc_desc(sb + 2 * TC_TILE), tc_desc(sb + 7 * TC_TILE), 1u);
+        tc_mma(dO, tc_desc(sb + 3 * TC_TILE), tc_desc(sb + 6 * TC_TILE), 1u);
+        tc_commit(&bars->empty[s]);
+        if (c % TC_G == TC_G - 1 || c == nchunk - 1) tc_commit(&bars->gdone[set]);
+        last = c;
       }
+      // after a give-up, MMAs already issued still write tensor memory: wait
+      // (bounded) for the commit that covers them before the block frees it
+      if (*abort && last >= 0)
+        mbar_wait(smem_u32(&bars->empty[last % T6_NBUF]), (uint32_t)((last / T6_NBUF) & 1));
     }
-    tc_store(bp, tile, row, v);
-    if (c + TC_DEPTH < nchunk) load(c + TC_DEPTH, v);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    ok = __syncthreads_and(ok);
-    if (!ok) return;
-    last = c;
-    if (t == 0) {
+  } else {  // fold warps: lanes 32 (warp % 4) .., columns 64 (warp / 4) .. of a partial set
+    const uint32_t tview = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
+    for (int g = 0; g < ngroups; ++g) {
+      const int set = g & 1;
+      const bool okw = mbar_wait(smem_u32(&bars->gdone[set]), (uint32_t)((g >> 1) & 1));
+      if (!__all_sync(0xffffffffu, okw)) {
+        *abort = 1;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sb = smem_u32(bp);
-      const uint32_t dE = tmem + (uint32_t)(((c / TC_G) & 1) * 256), dO = dE + 128;
-      const uint32_t a = (c % TC_G) != 0 ? 1u : 0u;
-      tc_mma(dE, tc_desc(sb + 0 * TC_TILE), tc_desc(sb + 4 * TC_TILE), a);
-      tc_mma(dE, tc_desc(sb + 0 * TC_TILE), tc_desc(sb + 5 * TC_TILE), 1u);
-      tc_mma(dE, tc_desc(sb + 1 * TC_TILE), tc_desc(sb + 4 * TC_TILE), 1u);
-      tc_mma(dO, tc_desc(sb + 2 * TC_TILE), tc_desc(sb + 6 * TC_TILE), a);
-      tc_mma(dO, tc_desc(sb + 2 * TC_TILE), tc_desc(sb + 7 * TC_TILE), 1u);
-      tc_mma(dO, tc_desc(sb + 3 * TC_TILE), tc_desc(sb + 6 * TC_TILE), 1u);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&bars[buf]))
-                   : "memory");
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        uint32_t r[16];
+        tc_ld16(tview + (uint32_t)(set * 256 + c0), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->gfree[set]);
     }
-  };
-  for (int c = 0; c < nchunk; c += 3) {
-    step(c, v0);
-    if (c + 1 < nchunk) step(c + 1, v1);
-    if (c + 2 < nchunk) step(c + 2, v2);
   }
-  // the last commit covers every MMA issued before it
-  bool done = last >= 0 ? mbar_wait(smem_u32(&bars[last % TC_NBUF]), (uint32_t)((last / TC_NBUF) & 1)) : true;
-  done = __syncthreads_and(done);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const bool good = ok && done && last == nchunk - 1;
-  if (good)
-    while (pg * TC_G < nchunk) fold(pg++);
-  return good;
-}
-
-// synthesis: block = (order m, 128 ring pairs = table tiles 2u, 2u + 1);
-// tile offsets into P, -1 for a tile outside the kept range
-__global__ void __launch_bounds__(TC_THREADS, 1) bucket_synth_tc_k(BucketArgs a, const int* __restrict__ titems,
-                                                                   const longlong2* __restrict__ toffs, int nitems,
-                                                                   const float* __restrict__ P,
-                                                                   const float2* __restrict__ atb,
-                                                                   float2* __restrict__ G, int* __restrict__ status) {
-  extern __shared__ __align__(1024) unsigned char tc_smem[];
-  if ((int)blockIdx.x >= nitems || *(volatile int*)status) return;
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int v = titems[blockIdx.x];
-  const int m = v >> 16, u = v & 0xffff;
-  const longlong2 of = toffs[blockIdx.x];
-  const int L = a.lmax;
-  const int mb = idx_lm(L, 0, m);
-  const int nrow = L - m + 1;
-  const int nchunk = (nrow + 15) / 16;
-  const int r = t & 127, part = t >> 7, par = part & 1;
-  // A rows (parts 0, 1): ring pair r of the two tiles; B rows (parts 2, 3):
-  // coefficient column r; degrees of parity `par`
-  const long long off = (r < 64) ? of.x : of.y;
-  const float* src = part < 2 ? (off >= 0 ? P + off + (r & 63) : nullptr)
-                              : reinterpret_cast<const float*>(atb + (size_t)(mb + m) * BK_MAXB) + r;
-  const size_t stride = part < 2 ? (size_t)BS_PAIRS : (size_t)BK_COLS;
-  const uint32_t tmem = tc_setup(tc_smem);
-  float acc[64];
-  const bool ok = tc_mainloop(
-      tc_smem, tmem, nchunk,
-      [&](int c, float (&x)[8]) {
+  __syncthreads();
+  const bool ok = !*abort && nchunk > 0;
+  if (warp < T6_FOLD_WARPS && ok) {
+    const int lrow = (warp & 3) * 32 + lane;  // TMEM lane: ring pair (synthesis) / degree pair (adjoint)
+    const int cb = warp >> 2;                 // column block of 64: 0, 1 = E; 2, 3 = O
+    const int mb = idx_lm(L, 0, m);
+    if (!ADJ) {
+      // warps with O sums hand them over through shared memory (row stride
+      // 129: conflict-free); the E warps form north = E + O, south = E - O
+      float* xs = reinterpret_cast<float*>(tc_smem);
+      if (cb >= 2)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int rr = 16 * c + 2 * k + par;
-          x[k] = (src && rr < nrow) ? __ldg(src + (size_t)rr * stride) : 0.f;
-        }
-      },
-      acc);
-  if (!ok) {
-    if (t == 0) atomicExch(status, 1);
-  } else {
-    // warps 8..15 (O sums) hand theirs over through shared memory (row
-    // stride 129: conflict-free); warps 0..7 form north = E + O and
-    // south = E - O for their 32 members
-    float* xs = reinterpret_cast<float*>(tc_smem);
-    const int lrow = (warp & 3) * 32 + lane;  // ring pair within the block
-    const int cb = warp >> 2;                 // column block of 64
-    if (cb >= 2)
+        for (int j = 0; j < 64; ++j) xs[lrow * 129 + (cb - 2) * 64 + j] = acc[j];
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * T6_FOLD_WARPS) : "memory");
+      if (cb < 2) {
+        const int M = a.M;
+        const float sg = (m & 1) ? -1.f : 1.f;
+        const int jn = 1 + u * 128 + lrow;
+        const int js = M / 2 - jn;
+        if (jn <= a.npairs) {
 #pragma unroll
-      for (int j = 0; j < 64; ++j) xs[lrow * 129 + (cb - 2) * 64 + j] = acc[j];
-    __syncthreads();
-    if (cb < 2) {
-      const int M = a.M;
-      const float sg = (m & 1) ? -1.f : 1.f;
-      const int jn = 1 + u * 128 + lrow;
-      const int js = M / 2 - jn;
-      if (jn <= a.npairs) {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {  // static acc[] indices
-          const int slot = cb * 32 + q;
-          if (slot >= a.B || m > a.memberL[slot]) continue;
-          const float oe = xs[lrow * 129 + 2 * slot], oi = xs[lrow * 129 + 2 * slot + 1];
-          float2* rowp = G + ((size_t)slot * (L + 1) + m) * M;
-          const float ee = acc[2 * q], ei = acc[2 * q + 1];
-          const float2 fn = make_float2(ee + oe, ei + oi);
-          rowp[jn] = fn;
-          rowp[M - jn] = make_float2(sg * fn.x, sg * fn.y);
-          if (js != jn) {
-            const float2 fs = make_float2(ee - oe, ei - oi);
-            rowp[js] = fs;
-            rowp[M - js] = make_float2(sg * fs.x, sg * fs.y);
+          for (int q = 0; q < 32; ++q) {  // static acc[] indices
+            const int slot = cb * 32 + q;
+            if (slot >= a.B || m > a.memberL[slot]) continue;
+            const float oe = xs[lrow * 129 + 2 * slot], oi = xs[lrow * 129 + 2 * slot + 1];
+            float2* rowp = G + ((size_t)slot * (L + 1) + m) * M;
+            const float ee = acc[2 * q], ei = acc[2 * q + 1];
+            const float2 fn = make_float2(ee + oe, ei + oi);
+            rowp[jn] = fn;
+            rowp[M - jn] = make_float2(sg * fn.x, sg * fn.y);
+            if (js != jn) {
+              const float2 fs = make_float2(ee - oe, ei - oi);
+              rowp[js] = fs;
+              rowp[M - js] = make_float2(sg * fs.x, sg * fs.y);
+            }
           }
         }
       }
+    } else {
+      const int l = m + r0 + 2 * lrow + (cb >> 1);
+      if (l <= L) {
+        float* dst = cacc + (size_t)(mb + l) * BK_COLS + (cb & 1) * 64;
+#pragma unroll
+        for (int j = 0; j < 64; j += 4)
+          *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+      }
     }
   }
+  if (!ok && nchunk > 0 && t == 0) atomicExch(status, 1);
   tc_teardown(tmem);
 }
 
-// adjoint: block = (order m, rows r0 .. r0 + 255 of l - m, r0 a multiple of
-// 256); TMEM lane d holds the even row r0 + 2d (D_E) and the odd row
-// r0 + 2d + 1 (D_O); K runs over the order's kept table tiles
-// (items[mfirst[m] .. mfirst[m + 1])), 8 ring pairs per chunk
-__global__ void __launch_bounds__(TC_THREADS, 1) bucket_adj_tc_k(BucketArgs a, const int* __restrict__ items,
-                                                                 const int64_t* __restrict__ offs,
-                                                                 const int* __restrict__ mfirst,
-                                                                 const int2* __restrict__ work, int nwork,
-                                                                 const float* __restrict__ P,
-                                                                 const float* __restrict__ S, float* __restrict__ cacc,
-                                                                 int* __restrict__ status) {
-  extern __shared__ __align__(1024) unsigned char tc_smem[];
-  if ((int)blockIdx.x >= nwork || *(volatile int*)status) return;
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int2 wk = work[blockIdx.x];
-  const int m = wk.x, r0 = wk.y;
-  const int L = a.lmax;
-  const int mb = idx_lm(L, 0, m);
+// Plan time: A tiles of the synthesis (rows = 128 ring pairs of tiles 2u,
+// 2u + 1; k = 8 degrees of one parity per chunk of 16) from the table P.
+__global__ void __launch_bounds__(256) tc_build_pa_k(const float* __restrict__ P, const int* __restrict__ titems,
+                                                     const longlong2* __restrict__ toffs,
+                                                     const int64_t* __restrict__ aoff, int L,
+                                                     unsigned char* __restrict__ PA) {
+  const int it = blockIdx.y, c = blockIdx.x;
+  const int m = titems[it] >> 16;
   const int nrow = L - m + 1;
-  const int i0 = mfirst[m], i1 = mfirst[m + 1];
-  const int nchunk = (i1 - i0) * (BS_PAIRS / 8);
-  const int r = t & 127, part = t >> 7, par = part & 1;
-  const int rr = r0 + 2 * r + par;  // A rows: this degree row (l - m)
-  const uint32_t tmem = tc_setup(tc_smem);
-  float acc[64];
-  const bool ok = tc_mainloop(
-      tc_smem, tmem, nchunk,
-      [&](int c, float (&x)[8]) {
-        const int it = i0 + (c >> 3), j = c & 7;
-        if (part < 2) {  // A row: degree row rr, ring pairs 8j .. 8j + 7 of the tile
-          float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-          if (rr < nrow) {
-            const float* Pi = P + offs[it] + (size_t)rr * BS_PAIRS + 8 * j;
-            x0 = __ldg(reinterpret_cast<const float4*>(Pi));
-            x1 = __ldg(reinterpret_cast<const float4*>(Pi + 4));
-          }
-          x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
-          x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
-        } else {  // B row: column r of S_E (part 2) or S_O (part 3), same ring pairs
-          const int p0 = (items[it] & 0xffff) * BS_PAIRS + 8 * j;
-          const float* Sp = S + ((size_t)m * a.npairs + p0) * 2 * BK_COLS + par * BK_COLS + r;
+  if (16 * c >= nrow) return;
+  const int row0 = threadIdx.x & 127, par = threadIdx.x >> 7;
+  const longlong2 of = toffs[it];
+  const long long off = row0 < 64 ? of.x : of.y;
+  float v[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) x[k] = p0 + k < a.npairs ? __ldg(Sp + (size_t)k * 2 * BK_COLS) : 0.f;
-        }
-      },
-      acc);
-  if (!ok) {
-    if (t == 0) atomicExch(status, 1);
-  } else {
-    const int cb = warp >> 2;
-    const int l = m + r0 + 2 * ((warp & 3) * 32 + lane) + (cb >> 1);
-    if (l <= L) {
-      float* dst = cacc + (size_t)(mb + l) * BK_COLS + (cb & 1) * 64;
-#pragma unroll
-      for (int j = 0; j < 64; j += 4)
-        *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
-    }
+  for (int k = 0; k < 8; ++k) {
+    const int r = 16 * c + 2 * k + par;
+    v[k] = (off >= 0 && r < nrow) ? P[off + (size_t)r * BS_PAIRS + (row0 & 63)] : 0.f;
   }
-  tc_teardown(tmem);
+  unsigned char* dst = PA + aoff[it] + (size_t)c * T6_HALF;
+  tc_store(dst, 2 * par, row0, v);
+}
+
+// Plan time: A tiles of the adjoint (rows = 128 degrees of one parity from
+// r0; k = 8 ring pairs of a kept tile per chunk) from the table P.
+__global__ void __launch_bounds__(256) tc_build_pt_k(const float* __restrict__ P, const int* __restrict__ items,
+                                                     const int64_t* __restrict__ offs,
+                                                     const int* __restrict__ mfirst, const int2* __restrict__ work,
+                                                     const int64_t* __restrict__ aoff, int L,
+                                                     unsigned char* __restrict__ PT) {
+  const int w = blockIdx.y, c = blockIdx.x;
+  const int2 wk = work[w];
+  const int m = wk.x, r0 = wk.y;
+  const int i0 = mfirst[m], i1 = mfirst[m + 1];
+  if (c >= (i1 - i0) * (BS_PAIRS / 8)) return;
+  const int it = i0 + (c >> 3), j = c & 7;
+  const int nrow = L - m + 1;
+  const int row0 = threadIdx.x & 127, par = threadIdx.x >> 7;
+  const int r = r0 + 2 * row0 + par;
+  float v[8];
+  if (r < nrow) {
+    const float* src = P + offs[it] + (size_t)r * BS_PAIRS + 8 * j;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = src[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = 0.f;
+  }
+  unsigned char* dst = PT + aoff[w] + (size_t)c * T6_HALF;
+  tc_store(dst, 2 * par, row0, v);
+}
+
+// Per call, synthesis: B tiles (rows = 128 columns (member, re/im), k = 8
+// degrees of one parity per chunk) of atilde = a Ahat, straight from the
+// members' coefficients.
+__global__ void __launch_bounds__(256) tc_scale_bs_k(int L, int B, const int* __restrict__ memberL,
+                                                     const float2* const* __restrict__ alm,
+                                                     const double* __restrict__ ahat,
+                                                     const int64_t* __restrict__ bsoff,
+                                                     unsigned char* __restrict__ BS) {
+  const int m = blockIdx.y, c = blockIdx.x;
+  const int nrow = L - m + 1;
+  if (16 * c >= nrow) return;
+  const int n = threadIdx.x & 127, par = threadIdx.x >> 7;
+  const int slot = n >> 1;
+  const int Lb = slot < B ? memberL[slot] : -1;
+  const float2* am = slot < B ? alm[slot] : nullptr;
+  float v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int l = m + 16 * c + 2 * k + par;
+    float x = 0.f;
+    if (l <= L && l <= Lb && m <= Lb) {
+      const float2 av = am[idx_lm(Lb, l, m)];
+      const float ah = (float)ahat[idx_lm(L, l, m)];
+      x = (n & 1) ? (m == 0 ? 0.f : av.y * ah) : av.x * ah;
+    }
+    v[k] = x;
+  }
+  unsigned char* dst = BS + bsoff[m] + (size_t)c * T6_HALF;
+  tc_store(dst, 2 * par, n, v);
+}
+
+__global__ void __launch_bounds__(256) bucket_fold_ba_k(int L, int M, int npairs, int B, int ntiles,
+                                                        const int* __restrict__ memberL,
+                                                        const float2* __restrict__ Gt,
+                                                        unsigned char* __restrict__ BA) {
+  __shared__ float2 sE[FOLD_PAIRS][BK_MAXB + 1], sO[FOLD_PAIRS][BK_MAXB + 1];
+  const int p0 = blockIdx.x * FOLD_PAIRS, m = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = p0 + lane;
+  const float sg = (m & 1) ? -1.f : 1.f;
+  for (int slot = warp; slot < BK_MAXB; slot += 8) {
+    float2 se = make_float2(0.f, 0.f), so = make_float2(0.f, 0.f);
+    if (slot < B && m <= memberL[slot] && p < npairs) {
+      const int jn = p + 1, js = M / 2 - jn;
+      const float2* row = Gt + ((size_t)slot * (L + 1) + m) * M;
+      const float2 g0 = row[jn], g1 = row[M - jn];
+      const float2 fn = make_float2(g0.x + sg * g1.x, g0.y + sg * g1.y);
+      float2 fs = make_float2(0.f, 0.f);
+      if (js != jn) {
+        const float2 h0 = row[js], h1 = row[M - js];
+        fs = make_float2(h0.x + sg * h1.x, h0.y + sg * h1.y);
+      }
+      se = make_float2(fn.x + fs.x, fn.y + fs.y);
+      so = make_float2(fn.x - fs.x, fn.y - fs.y);
+    }
+    sE[lane][slot] = se;
+    sO[lane][slot] = so;
+  }
+  __syncthreads();
+  // 4 groups of 8 ring pairs; thread = (column n, parity)
+  const int n = threadIdx.x & 127, par = threadIdx.x >> 7;
+  const int slot = n >> 1;
+#pragma unroll
+  for (int g = 0; g < FOLD_PAIRS / 8; ++g) {
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float2 x = par ? sO[8 * g + k][slot] : sE[8 * g + k][slot];
+      v[k] = (n & 1) ? x.y : x.x;
+    }
+    const int pg = p0 + 8 * g;  // first ring pair of the group (multiple of 8)
+    const int tile = pg / BS_PAIRS, j = (pg % BS_PAIRS) / 8;
+    unsigned char* dst = BA + ((size_t)(m * ntiles + tile) * 8 + j) * T6_HALF;
+    tc_store(dst, 2 * par, n, v);  // tiles 0..3 of the chunk's B half
+  }
 }
 
 // member outputs: c_slot(l, m) = Ahat * C + poles (m = 0)
@@ -972,6 +1101,15 @@ struct Bucket {
   int ntc = 0;
   int2* tc_work = nullptr;            // (m, first row l - m)
   int ntc_work = 0;
+  int ntiles = 0;                     // 64-pair table tiles per order
+  int maxch = 0, maxch_adj = 0;       // chunks per block, at most
+  unsigned char* PA = nullptr;        // synthesis A tiles, per block, chunk after chunk
+  unsigned char* PT = nullptr;        // adjoint A tiles, per block
+  unsigned char* BS = nullptr;        // synthesis B tiles, per order (per call)
+  unsigned char* BA = nullptr;        // adjoint B tiles [m][tile][group] (per call)
+  int64_t* pa_off = nullptr;          // byte offsets of the blocks / orders
+  int64_t* pt_off = nullptr;
+  int64_t* bs_off = nullptr;
   cufftHandle theta = 0;
   bool have_theta = false;
 };
@@ -1022,6 +1160,13 @@ void bucket_free(Bucket& b) {
   dev_free(b.tc_items);
   dev_free(b.tc_offs);
   dev_free(b.tc_work);
+  dev_free(b.PA);
+  dev_free(b.PT);
+  dev_free(b.BS);
+  dev_free(b.BA);
+  dev_free(b.pa_off);
+  dev_free(b.pt_off);
+  dev_free(b.bs_off);
   if (b.have_theta) cufftDestroy(b.theta);
   b = Bucket();
 }
@@ -1202,7 +1347,57 @@ int bucket_build(nusht_batch_t p, Bucket& b, cudaStream_t s) {
         }
         if (!tw.empty())
           NUSHT_CUDA(cudaMemcpy(b.tc_work, tw.data(), tw.size() * sizeof(int2), cudaMemcpyHostToDevice));
-        b.tc = true;
+        // pre-split operand tiles: sizes, then the tables when they fit
+        b.ntiles = (b.npairs + BS_PAIRS - 1) / BS_PAIRS;
+        b.maxch = (L + 1 + 15) / 16;
+        std::vector<int64_t> pao(ti.size()), pto(tw.size()), bso(L + 1);
+        int64_t pab = 0, ptb = 0, bsb = 0;
+        for (size_t k = 0; k < ti.size(); ++k) {
+          pao[k] = pab;
+          pab += (int64_t)((L - (ti[k] >> 16) + 1 + 15) / 16) * T6_HALF;
+        }
+        b.maxch_adj = 0;
+        for (size_t k = 0; k < tw.size(); ++k) {
+          pto[k] = ptb;
+          const int ch = (mf[tw[k].x + 1] - mf[tw[k].x]) * (BS_PAIRS / 8);
+          b.maxch_adj = std::max(b.maxch_adj, ch);
+          ptb += (int64_t)ch * T6_HALF;
+        }
+        for (int m = 0; m <= L; ++m) {
+          bso[m] = bsb;
+          bsb += (int64_t)((L - m + 1 + 15) / 16) * T6_HALF;
+        }
+        const int64_t bab = (int64_t)(L + 1) * b.ntiles * 8 * T6_HALF;
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        if (pab + ptb + bsb + bab > 0 && (size_t)(pab + ptb + bsb + bab) < fr / 2) {
+          NUSHT_TRY(dev_alloc((void**)&b.PA, std::max<int64_t>(16, pab), &p->bytes));
+          NUSHT_TRY(dev_alloc((void**)&b.PT, std::max<int64_t>(16, ptb), &p->bytes));
+          NUSHT_TRY(dev_alloc((void**)&b.BS, std::max<int64_t>(16, bsb), &p->bytes));
+          NUSHT_TRY(dev_alloc((void**)&b.BA, std::max<int64_t>(16, bab), &p->bytes));
+          NUSHT_TRY(dev_alloc((void**)&b.pa_off, std::max<size_t>(1, pao.size()) * 8, &p->bytes));
+          NUSHT_TRY(dev_alloc((void**)&b.pt_off, std::max<size_t>(1, pto.size()) * 8, &p->bytes));
+          NUSHT_TRY(dev_alloc((void**)&b.bs_off, bso.size() * 8, &p->bytes));
+          if (!pao.empty()) NUSHT_CUDA(cudaMemcpy(b.pa_off, pao.data(), pao.size() * 8, cudaMemcpyHostToDevice));
+          if (!pto.empty()) NUSHT_CUDA(cudaMemcpy(b.pt_off, pto.data(), pto.size() * 8, cudaMemcpyHostToDevice));
+          NUSHT_CUDA(cudaMemcpy(b.bs_off, bso.data(), bso.size() * 8, cudaMemcpyHostToDevice));
+          NUSHT_CUDA(cudaMemsetAsync(b.BA, 0, bab, s));  // tiles of pairs past npairs stay zero
+          if (b.ntc > 0)
+            tc_build_pa_k<<<dim3(b.maxch, b.ntc), 256, 0, s>>>(b.P, b.tc_items, b.tc_offs, b.pa_off, L, b.PA);
+          if (b.ntc_work > 0 && b.maxch_adj > 0)
+            tc_build_pt_k<<<dim3(b.maxch_adj, b.ntc_work), 256, 0, s>>>(b.P, b.items, b.offs, b.mfirst, b.tc_work,
+                                                                      b.pt_off, L, b.PT);
+          NUSHT_CUDA(cudaGetLastError());
+          NUSHT_CUDA(cudaStreamSynchronize(s));
+          b.tc = true;
+          // the CUDA-core operands are not needed on this path
+          dev_free(b.P);
+          b.P = nullptr;
+          dev_free(b.atb);
+          b.atb = nullptr;
+          dev_free(b.S);
+          b.S = nullptr;
+        }
       }
     }
   }
@@ -1244,8 +1439,8 @@ int set_adj_smem() {
   NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_k<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   const int smt = (BS_PAIRS * AT_PAD + BS_PAIRS * 2 * BK_COLS) * (int)sizeof(float);
   NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_tab_k, cudaFuncAttributeMaxDynamicSharedMemorySize, smt));
-  NUSHT_CUDA(cudaFuncSetAttribute(bucket_synth_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-  NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+  NUSHT_CUDA(cudaFuncSetAttribute(bucket_tc_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T6_SMEM));
+  NUSHT_CUDA(cudaFuncSetAttribute(bucket_tc_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, T6_SMEM));
   return NUSHT_OK;
 }
 
@@ -1253,10 +1448,18 @@ int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
   for (auto& b : p->buckets) {
     const BucketArgs a = bucket_args(b);
     dim3 g((b.L + 1 + 3) / 4, b.L + 1);
-    bucket_scale_k<<<g, 256, 0, s>>>(b.L, b.B, b.memberL, b.alm_ptrs, b.leg->leg.ahat, b.atb);
-    if (b.ntc > 0 && b.tc)
-      bucket_synth_tc_k<<<b.ntc, TC_THREADS, TC_SMEM, s>>>(a, b.tc_items, b.tc_offs, b.ntc, b.P, b.atb, b.G, p->status);
-    else if (b.nitems > 0 && b.table)
+    if (b.tc) {
+      tc_scale_bs_k<<<dim3(b.maxch, b.L + 1), 256, 0, s>>>(b.L, b.B, b.memberL, b.alm_ptrs, b.leg->leg.ahat,
+                                                           b.bs_off, b.BS);
+      if (b.ntc > 0)
+        bucket_tc_k<false><<<b.ntc, T6_THREADS, T6_SMEM, s>>>(a, b.ntc, b.tc_items, nullptr, b.pa_off, b.bs_off,
+                                                              nullptr, nullptr, b.ntiles, b.PA, b.BS, b.G, nullptr,
+                                                              p->status);
+    } else {
+      bucket_scale_k<<<g, 256, 0, s>>>(b.L, b.B, b.memberL, b.alm_ptrs, b.leg->leg.ahat, b.atb);
+    }
+    if (b.tc) {
+    } else if (b.nitems > 0 && b.table)
       bucket_synth_tab_k<<<b.nitems, 256, 0, s>>>(a, b.items, b.offs, b.nitems, b.P, b.atb, b.G);
     else if (b.nitems > 0)
       bucket_synth_k<<<b.nitems, 256, 0, s>>>(a, b.items, b.nitems, b.atb, b.G);
@@ -1284,12 +1487,18 @@ int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
   for (auto& b : p->buckets) {
     NUSHT_CUFFT(cufftSetStream(b.theta, s));
     NUSHT_CUFFT(cufftExecC2C(b.theta, (cufftComplex*)b.Ghat, (cufftComplex*)b.Ghat, CUFFT_INVERSE));
-    dim3 gf((b.npairs + FOLD_PAIRS - 1) / FOLD_PAIRS, b.L + 1);
-    bucket_fold_k<<<gf, 256, 0, s>>>(b.L, b.M, b.npairs, b.B, b.memberL, b.Ghat, b.S);
     if (b.tc) {
+      dim3 gf(b.ntiles * BS_PAIRS / FOLD_PAIRS, b.L + 1);
+      bucket_fold_ba_k<<<gf, 256, 0, s>>>(b.L, b.M, b.npairs, b.B, b.ntiles, b.memberL, b.Ghat, b.BA);
       if (b.ntc_work > 0)
-        bucket_adj_tc_k<<<b.ntc_work, TC_THREADS, TC_SMEM, s>>>(bucket_args(b), b.items, b.offs, b.mfirst, b.tc_work,
-                                                         b.ntc_work, b.P, b.S, b.cacc, p->status);
+        bucket_tc_k<true><<<b.ntc_work, T6_THREADS, T6_SMEM, s>>>(bucket_args(b), b.ntc_work, nullptr, b.tc_work,
+                                                                  b.pt_off, nullptr, b.items, b.mfirst, b.ntiles,
+                                                                  b.PT, b.BA, nullptr, b.cacc, p->status);
+    } else {
+      dim3 gf((b.npairs + FOLD_PAIRS - 1) / FOLD_PAIRS, b.L + 1);
+      bucket_fold_k<<<gf, 256, 0, s>>>(b.L, b.M, b.npairs, b.B, b.memberL, b.Ghat, b.S);
+    }
+    if (b.tc) {
     } else if (b.table) {
       const size_t sm = (size_t)(BS_PAIRS * AT_PAD + BS_PAIRS * 2 * BK_COLS) * sizeof(float);
       if (b.nwork > 0)
