@@ -1130,6 +1130,11 @@ struct nusht_batch_s {
   std::vector<int> bucket_of, slot_of;
   size_t bytes = 0;
   cudaStream_t cap = nullptr;
+  // members' NUFFT stages run on NSIDE streams forked from the capture
+  // stream (graph branches), so that small members' kernels overlap
+  static constexpr int NSIDE = 4;
+  cudaStream_t side[NSIDE] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[NSIDE] = {};
   int* status = nullptr;  // device flag: a bounded wait in a tensor-core kernel gave up
   cudaGraphExec_t gs = nullptr, ga = nullptr;
   std::vector<const void*> gs_in;
@@ -1182,6 +1187,11 @@ void batch_free(nusht_batch_t p) {
     if (s) plan_destroy(s);
   for (auto& b : p->buckets) bucket_free(b);
   dev_free(p->status);
+  for (int k = 0; k < nusht_batch_s::NSIDE; ++k) {
+    if (p->side[k]) cudaStreamDestroy(p->side[k]);
+    if (p->ev_join[k]) cudaEventDestroy(p->ev_join[k]);
+  }
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->cap) cudaStreamDestroy(p->cap);
   cudaSetDevice(cur);
   delete p;
@@ -1444,6 +1454,22 @@ int set_adj_smem() {
   return NUSHT_OK;
 }
 
+// fork the side streams off `s` / join them back (inside a capture these
+// become graph branches)
+int fork(nusht_batch_t p, cudaStream_t s) {
+  NUSHT_CUDA(cudaEventRecord(p->ev_fork, s));
+  for (int k = 0; k < nusht_batch_s::NSIDE; ++k) NUSHT_CUDA(cudaStreamWaitEvent(p->side[k], p->ev_fork, 0));
+  return NUSHT_OK;
+}
+
+int join(nusht_batch_t p, cudaStream_t s) {
+  for (int k = 0; k < nusht_batch_s::NSIDE; ++k) {
+    NUSHT_CUDA(cudaEventRecord(p->ev_join[k], p->side[k]));
+    NUSHT_CUDA(cudaStreamWaitEvent(s, p->ev_join[k], 0));
+  }
+  return NUSHT_OK;
+}
+
 int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
   for (auto& b : p->buckets) {
     const BucketArgs a = bucket_args(b);
@@ -1468,22 +1494,28 @@ int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
     NUSHT_CUFFT(cufftSetStream(b.theta, s));
     NUSHT_CUFFT(cufftExecC2C(b.theta, (cufftComplex*)b.G, (cufftComplex*)b.Ghat, CUFFT_FORWARD));
   }
+  NUSHT_TRY(fork(p, s));
   for (int i = 0; i < p->nbatch; ++i) {
     nusht_plan_t q = p->sub[i];
-    NUSHT_TRY(deconv_pad(q, s));
-    NUSHT_TRY(fine_fft_c2r(q, s));
-    NUSHT_TRY(interp(q, d_map[i], s));
+    cudaStream_t ms = p->side[i % nusht_batch_s::NSIDE];
+    NUSHT_TRY(deconv_pad(q, ms));
+    NUSHT_TRY(fine_fft_c2r(q, ms));
+    NUSHT_TRY(interp(q, d_map[i], ms));
   }
+  NUSHT_TRY(join(p, s));
   return NUSHT_OK;
 }
 
 int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
+  NUSHT_TRY(fork(p, s));
   for (int i = 0; i < p->nbatch; ++i) {
     nusht_plan_t q = p->sub[i];
-    NUSHT_TRY(spread(q, d_map[i], s));
-    NUSHT_TRY(fine_fft_r2c(q, s));
-    NUSHT_TRY(deconv_trunc(q, s));
+    cudaStream_t ms = p->side[i % nusht_batch_s::NSIDE];
+    NUSHT_TRY(spread(q, d_map[i], ms));
+    NUSHT_TRY(fine_fft_r2c(q, ms));
+    NUSHT_TRY(deconv_trunc(q, ms));
   }
+  NUSHT_TRY(join(p, s));
   for (auto& b : p->buckets) {
     NUSHT_CUFFT(cufftSetStream(b.theta, s));
     NUSHT_CUFFT(cufftExecC2C(b.theta, (cufftComplex*)b.Ghat, (cufftComplex*)b.Ghat, CUFFT_INVERSE));
@@ -1617,7 +1649,12 @@ int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64
     if (st != NUSHT_OK) break;
     {
       cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
-      if (e != cudaSuccess) st = cuda_status(e, "cudaStreamCreateWithFlags");
+      for (int k = 0; k < nusht_batch_s::NSIDE && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join[k], cudaEventDisableTiming);
+      }
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+      if (e != cudaSuccess) st = cuda_status(e, "stream / event creation");
     }
   } while (false);
   if (st != NUSHT_OK) {
