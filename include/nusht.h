@@ -120,7 +120,12 @@ typedef struct {
                           relative per step instead of FP64's 2^-53; about 2.5x faster Legendre
                           stages on GB300).  Opt-in: the default recurrence is FP64.  Ignored
                           with fp64_contraction = 1 and in recurrence-table mode. */
-  int reserved[3];
+  int fft_kernels;    /* FP64 plans: 0 (default) = the theta FFT and the fine-grid 2D real FFT
+                         run as this library's double-float kernels (one line per CTA in
+                         shared memory, ~2^-47 relative per operation) when every length is
+                         at most 14336; longer lengths use cuFFT's FP64 transforms;
+                         -1 = cuFFT's FP64 transforms always.  Mixed plans use cuFFT FP32. */
+  int reserved[2];
 } nusht_opts;
 
 /* Sizes a plan uses; filled by nusht_plan_sizes (no GPU needed) and nusht_info. */

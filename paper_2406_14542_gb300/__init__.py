@@ -40,7 +40,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("kernel_width", ctypes.c_int), ("profile", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("tune", ctypes.c_int), ("fp64_contraction", ctypes.c_int),
                 ("legendre_table", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("fast_recurrence", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("fast_recurrence", ctypes.c_int), ("fft_kernels", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class Sizes(ctypes.Structure):
@@ -122,8 +123,9 @@ def _check(code: int, where: str):
 
 
 def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False, legendre_table=0, tune=0,
-          tensor_cores=0, deterministic=False, fast_recurrence=False) -> Opts:
+          tensor_cores=0, deterministic=False, fast_recurrence=False, fft_kernels=0) -> Opts:
     o = Opts()
+    o.fft_kernels = int(fft_kernels)
     o.fast_recurrence = 1 if fast_recurrence else 0
     o.deterministic = 1 if deterministic else 0
     o.tensor_cores = int(tensor_cores)
@@ -238,7 +240,7 @@ class Plan:
     def __init__(self, lmax: int, pts, eps: float = 1e-10, precision="fp64", mmax: int | None = None,
                  sigma: float = 0.0, kernel_width: int = 0, profile: bool = False, fp64_contraction: bool = False,
                  legendre_table: int = 0, tune: int = 0, deterministic: bool = False,
-                 fast_recurrence: bool = False, stream=None):
+                 fast_recurrence: bool = False, fft_kernels: int = 0, stream=None):
         import torch
 
         self.lib = load()
@@ -253,7 +255,7 @@ class Plan:
         self.device = pts.device
         h = ctypes.c_void_p()
         o = _opts(sigma, kernel_width, profile, fp64_contraction, legendre_table, tune,
-                  deterministic=deterministic, fast_recurrence=fast_recurrence)
+                  deterministic=deterministic, fast_recurrence=fast_recurrence, fft_kernels=fft_kernels)
         _check(self.lib.nusht_plan(ctypes.byref(h), self.lmax, self.mmax, self.npts,
                                    ctypes.c_void_p(pts.data_ptr() if self.npts else 0), self.eps, self.precision,
                                    ctypes.byref(o), _stream_ptr(stream)), "nusht_plan")

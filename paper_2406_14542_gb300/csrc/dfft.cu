@@ -1,0 +1,515 @@
+// dfft.cu -- double-float FFTs of FP64 plans: the theta transform (F in
+// Eq. SHTfast, the 1D DFT of the doubled ring map along theta) and the 2D
+// real transform of the NUFFT's fine grid (the uniform FFT step of the type 1
+// and type 2 NUFFT), each line transformed in shared memory.
+//
+// GB300 issues FP64 at 1/62 of its FP32 rate, and cuFFT's FP64 transforms are
+// bound by that pipe.  Here every complex value is an unevaluated pair of
+// floats per component (re.hi, re.lo, im.hi, im.lo; ~2^-47 relative per
+// operation, see dfloat.cuh), and the arithmetic runs on the FP32 pipe.
+//
+// One CTA owns one line of length N (N * 16 bytes of shared memory, N up to
+// DFFT_NMAX).  The transform is an in-place mixed-radix decimation in
+// frequency (radices 2, 3, 4, 5, 7): a pass of radix R over sub-blocks of
+// length L combines the R values b*L + j + r*(L/R) and multiplies output q by
+// W_L^(j q).  The result is left in digit-reversed order; `rev` maps an output
+// index to its shared-memory position and the store reads through it.
+//
+// Fine grid (n1 x n2 real, rows of stride n2 + 2 doubles):
+//   synthesis: dfft_cols_synth_k  (per order m <= mmax: deconvolve and
+//              zero-pad the theta spectrum to n1, inverse DFT along theta,
+//              store the column as row m of the order-major buffer T[m][j]);
+//              dfft_rows_c2r_k (per pair of rows j, j+1: the two Hermitian
+//              half spectra X_j[m], X_j+1[m] (m <= mmax) packed as
+//              C = X_j + i X_j+1 over the full length, one inverse DFT,
+//              x_j = Re, x_j+1 = Im).
+//   adjoint:   dfft_rows_r2c_k (the two real rows as one complex sequence,
+//              one forward DFT, spectra of each separated by the Hermitian
+//              symmetry, m <= mmax kept); dfft_cols_adj_k (forward DFT along
+//              theta per order, truncation to |k| <= lmax and deconvolution).
+// The DFT sign and scale match cuFFT's (unnormalised; "forward" = e^-i).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dfloat.cuh"
+#include "nusht_internal.cuh"
+
+namespace nusht {
+namespace {
+
+constexpr int DFFT_T = 512;  // threads per line
+
+// ---------------------------------------------------------------------------
+// float-pair complex arithmetic (float4 = re.hi, re.lo, im.hi, im.lo)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 dd_add(float ah, float al, float bh, float bl) {
+  const float s = __fadd_rn(ah, bh);
+  const float bp = __fsub_rn(s, ah);
+  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bp)), __fsub_rn(bh, bp));
+  const float l = __fadd_rn(__fadd_rn(al, bl), err);
+  const float h = __fadd_rn(s, l);
+  return make_float2(h, __fsub_rn(l, __fsub_rn(h, s)));
+}
+
+// x*y + u*v for float pairs, one renormalisation
+__device__ __forceinline__ float2 dd_dot2(float xh, float xl, float yh, float yl, float uh, float ul, float vh,
+                                          float vl) {
+  const float p1 = __fmul_rn(xh, yh);
+  const float e1 = __fmaf_rn(xh, yh, -p1);
+  const float p2 = __fmul_rn(uh, vh);
+  const float e2 = __fmaf_rn(uh, vh, -p2);
+  const float s = __fadd_rn(p1, p2);
+  const float bp = __fsub_rn(s, p1);
+  const float err = __fadd_rn(__fsub_rn(p1, __fsub_rn(s, bp)), __fsub_rn(p2, bp));
+  float t = __fadd_rn(e1, e2);
+  t = __fmaf_rn(xh, yl, t);
+  t = __fmaf_rn(xl, yh, t);
+  t = __fmaf_rn(uh, vl, t);
+  t = __fmaf_rn(ul, vh, t);
+  const float l = __fadd_rn(t, err);
+  const float h = __fadd_rn(s, l);
+  return make_float2(h, __fsub_rn(l, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ float4 c_add(float4 a, float4 b) {
+  const float2 r = dd_add(a.x, a.y, b.x, b.y), i = dd_add(a.z, a.w, b.z, b.w);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+__device__ __forceinline__ float4 c_sub(float4 a, float4 b) {
+  const float2 r = dd_add(a.x, a.y, -b.x, -b.y), i = dd_add(a.z, a.w, -b.z, -b.w);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+// a * (SG i)
+template <int SG>
+__device__ __forceinline__ float4 c_mul_i(float4 a) {
+  return SG > 0 ? make_float4(-a.z, -a.w, a.x, a.y) : make_float4(a.z, a.w, -a.x, -a.y);
+}
+// a * (c + SG i s), w = (c.hi, c.lo, s.hi, s.lo)
+template <int SG>
+__device__ __forceinline__ float4 c_mul_tw(float4 a, float4 w) {
+  const float sh = SG > 0 ? w.z : -w.z, sl = SG > 0 ? w.w : -w.w;
+  const float2 re = dd_dot2(a.x, a.y, w.x, w.y, -a.z, -a.w, sh, sl);
+  const float2 im = dd_dot2(a.x, a.y, sh, sl, a.z, a.w, w.x, w.y);
+  return make_float4(re.x, re.y, im.x, im.y);
+}
+// a * (real pair c)
+__device__ __forceinline__ float4 c_scale(float4 a, float2 c) {
+  const float2 re = df_mul(make_float2(a.x, a.y), c), im = df_mul(make_float2(a.z, a.w), c);
+  return make_float4(re.x, re.y, im.x, im.y);
+}
+// acc += a * (real pair c)
+__device__ __forceinline__ void c_mac(float4& acc, float4 a, float2 c) {
+  df_mac(acc.x, acc.y, a.x, a.y, c.x, c.y);
+  df_mac(acc.z, acc.w, a.z, a.w, c.x, c.y);
+}
+
+__device__ __forceinline__ float4 c_of(double2 v) {
+  float4 r;
+  df_split(v.x, r.x, r.y);
+  df_split(v.y, r.z, r.w);
+  return r;
+}
+__device__ __forceinline__ double2 c_value(float4 c) { return make_double2(df_value(c.x, c.y), df_value(c.z, c.w)); }
+
+// ---------------------------------------------------------------------------
+// small DFTs of the butterflies (sign SG: +1 inverse, -1 forward)
+// ---------------------------------------------------------------------------
+template <int SG>
+__device__ __forceinline__ void dft4(float4* v) {
+  const float4 t0 = c_add(v[0], v[2]), t1 = c_sub(v[0], v[2]);
+  const float4 t2 = c_add(v[1], v[3]), t3 = c_mul_i<SG>(c_sub(v[1], v[3]));
+  v[0] = c_add(t0, t2);
+  v[2] = c_sub(t0, t2);
+  v[1] = c_add(t1, t3);
+  v[3] = c_sub(t1, t3);
+}
+
+// odd R: X_q = v0 + sum_r cos(2 pi r q / R) (v_r + v_R-r) + SG i sin(...) (v_r - v_R-r);
+// the constants are entries of the length-N twiddle table (R divides N)
+template <int R, int SG>
+__device__ __forceinline__ void dft_odd(float4* v, const float4* __restrict__ tw, int n_over_r) {
+  constexpr int H = R / 2;
+  float4 t[H], u[H];
+#pragma unroll
+  for (int r = 1; r <= H; ++r) {
+    t[r - 1] = c_add(v[r], v[R - r]);
+    u[r - 1] = c_sub(v[r], v[R - r]);
+  }
+  float4 out[R];
+  out[0] = v[0];
+#pragma unroll
+  for (int r = 0; r < H; ++r) out[0] = c_add(out[0], t[r]);
+#pragma unroll
+  for (int q = 1; q <= H; ++q) {
+    float4 a = v[0], b = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+      const float4 w = __ldg(tw + ((r * q) % R) * n_over_r);
+      c_mac(a, t[r - 1], make_float2(w.x, w.y));
+      c_mac(b, u[r - 1], make_float2(w.z, w.w));
+    }
+    const float4 ib = c_mul_i<SG>(b);
+    out[q] = c_add(a, ib);
+    out[R - q] = c_sub(a, ib);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = out[r];
+}
+
+template <int R, int SG>
+__device__ __forceinline__ void dif_pass(float4* X, const DfftLen& f, int L, int mul) {
+  const int S = L / R;
+  const int nb = f.N / R;
+  const bool pow2 = (S & (S - 1)) == 0;
+  const int sh = pow2 ? __ffs(S) - 1 : 0;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    const int b = pow2 ? (t >> sh) : t / S;
+    const int j = t - b * S;
+    float4* p = X + b * L + j;
+    float4 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = p[r * S];
+    if constexpr (R == 2) {
+      const float4 a = v[0];
+      v[0] = c_add(a, v[1]);
+      v[1] = c_sub(a, v[1]);
+    } else if constexpr (R == 4) {
+      dft4<SG>(v);
+    } else {
+      dft_odd<R, SG>(v, f.tw, f.N / R);
+    }
+    // output q times W_L^(j q) = W_N^(mul j q), mul = N / L
+#pragma unroll
+    for (int q = 1; q < R; ++q) v[q] = c_mul_tw<SG>(v[q], __ldg(f.tw + mul * j * q));
+#pragma unroll
+    for (int r = 0; r < R; ++r) p[r * S] = v[r];
+  }
+}
+
+// all passes; natural-order input in X, output k at X[f.rev[k]]
+template <int SG>
+__device__ void dif_line(float4* X, const DfftLen& f) {
+  int L = f.N;
+  for (int s = 0; s < f.npass; ++s) {
+    const int R = (int)((f.code >> (4 * s)) & 15u);
+    const int mul = f.N / L;
+    switch (R) {
+      case 4: dif_pass<4, SG>(X, f, L, mul); break;
+      case 2: dif_pass<2, SG>(X, f, L, mul); break;
+      case 3: dif_pass<3, SG>(X, f, L, mul); break;
+      case 5: dif_pass<5, SG>(X, f, L, mul); break;
+      default: dif_pass<7, SG>(X, f, L, mul); break;
+    }
+    __syncthreads();
+    L /= R;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// complex lines of length f.N (stride ld), in place allowed
+template <int SG>
+__global__ void __launch_bounds__(DFFT_T) dfft_lines_k(const double2* in, double2* out, int64_t ld, int nlines,
+                                                       DfftLen f) {
+  extern __shared__ float4 X[];
+  for (int line = blockIdx.x; line < nlines; line += gridDim.x) {
+    const double2* src = in + (int64_t)line * ld;
+    for (int k = threadIdx.x; k < f.N; k += blockDim.x) X[k] = c_of(src[k]);
+    __syncthreads();
+    dif_line<SG>(X, f);
+    double2* dst = out + (int64_t)line * ld;
+    for (int k = threadIdx.x; k < f.N; k += blockDim.x) dst[k] = c_value(X[__ldg(f.rev + k)]);
+    __syncthreads();
+  }
+}
+
+// synthesis, per order m: H[k1] = Ghat[m][k mod M] d1[k] d2[m] for |k| <= lmax
+// (k1 = k mod n1), zero elsewhere; inverse DFT along theta; T[m][j]
+__global__ void __launch_bounds__(DFFT_T) dfft_cols_synth_k(const double2* __restrict__ Gh, float4* __restrict__ T,
+                                                            int lmax, int M, const float2* __restrict__ d1,
+                                                            const float2* __restrict__ d2, DfftLen f) {
+  extern __shared__ float4 X[];
+  const int m = blockIdx.x, n1 = f.N;
+  const float2 dm = d2[m];
+  const double2* g = Gh + (int64_t)m * M;
+  for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    int k = k1;
+    bool keep = true;
+    if (k1 > lmax) {
+      k = k1 - n1;
+      keep = k >= -lmax;
+    }
+    if (keep) v = c_scale(c_of(g[k < 0 ? k + M : k]), df_mul(d1[k + lmax], dm));
+    X[k1] = v;
+  }
+  __syncthreads();
+  dif_line<1>(X, f);
+  float4* dst = T + (int64_t)m * n1;
+  for (int j = threadIdx.x; j < n1; j += blockDim.x) dst[j] = X[__ldg(f.rev + j)];
+}
+
+// synthesis, per row pair (j, j + 1): the real rows of the fine grid
+__global__ void __launch_bounds__(DFFT_T) dfft_rows_c2r_k(const float4* __restrict__ T, double* __restrict__ grid,
+                                                          int64_t stride, int n1, int mmax, DfftLen f) {
+  extern __shared__ float4 X[];
+  const int n2 = f.N;
+  const int j = 2 * blockIdx.x;
+  const bool two = j + 1 < n1;
+  for (int k = mmax + 1 + threadIdx.x; k < n2 - mmax; k += blockDim.x) X[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int m = threadIdx.x; m <= mmax; m += blockDim.x) {
+    const float4 a = T[(int64_t)m * n1 + j];
+    const float4 b = two ? T[(int64_t)m * n1 + j + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m == 0) {
+      // the imaginary parts of the m = 0 entries do not enter a real transform
+      X[0] = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+      // C[m] = a + i b, C[n2 - m] = conj(a) + i conj(b)
+      const float2 r1 = dd_add(a.x, a.y, -b.z, -b.w), i1 = dd_add(a.z, a.w, b.x, b.y);
+      const float2 r2 = dd_add(a.x, a.y, b.z, b.w), i2 = dd_add(b.x, b.y, -a.z, -a.w);
+      X[m] = make_float4(r1.x, r1.y, i1.x, i1.y);
+      X[n2 - m] = make_float4(r2.x, r2.y, i2.x, i2.y);
+    }
+  }
+  __syncthreads();
+  dif_line<1>(X, f);
+  double* r0 = grid + (int64_t)j * stride;
+  for (int n = threadIdx.x; n < n2; n += blockDim.x) {
+    const float4 c = X[__ldg(f.rev + n)];
+    r0[n] = df_value(c.x, c.y);
+    if (two) r0[stride + n] = df_value(c.z, c.w);
+  }
+}
+
+// adjoint, per row pair: spectra m <= mmax of rows j, j + 1 into T[m][j], T[m][j + 1]
+__global__ void __launch_bounds__(DFFT_T) dfft_rows_r2c_k(const double* __restrict__ grid, float4* __restrict__ T,
+                                                          int64_t stride, int n1, int mmax, DfftLen f) {
+  extern __shared__ float4 X[];
+  const int n2 = f.N;
+  const int j = 2 * blockIdx.x;
+  const bool two = j + 1 < n1;
+  const double* r0 = grid + (int64_t)j * stride;
+  for (int n = threadIdx.x; n < n2; n += blockDim.x) {
+    float4 v;
+    df_split(r0[n], v.x, v.y);
+    if (two) {
+      df_split(r0[stride + n], v.z, v.w);
+    } else {
+      v.z = v.w = 0.f;
+    }
+    X[n] = v;
+  }
+  __syncthreads();
+  dif_line<-1>(X, f);
+  for (int m = threadIdx.x; m <= mmax; m += blockDim.x) {
+    const float4 cm = X[__ldg(f.rev + m)];
+    const float4 cn = X[__ldg(f.rev + (m == 0 ? 0 : n2 - m))];
+    // X_j = (C[m] + conj C[n2-m]) / 2, X_j+1 = -i (C[m] - conj C[n2-m]) / 2
+    const float2 ar = dd_add(cm.x, cm.y, cn.x, cn.y), ai = dd_add(cm.z, cm.w, -cn.z, -cn.w);
+    const float2 br = dd_add(cm.z, cm.w, cn.z, cn.w), bi = dd_add(cn.x, cn.y, -cm.x, -cm.y);
+    T[(int64_t)m * n1 + j] = make_float4(0.5f * ar.x, 0.5f * ar.y, 0.5f * ai.x, 0.5f * ai.y);
+    if (two) T[(int64_t)m * n1 + j + 1] = make_float4(0.5f * br.x, 0.5f * br.y, 0.5f * bi.x, 0.5f * bi.y);
+  }
+}
+
+// adjoint, per order m: forward DFT of T[m][.] along theta, then
+// Ghat[m][kk] = H[k mod n1] d1[k] d2[m] for |k| <= lmax (k = kk or kk - M), else 0
+__global__ void __launch_bounds__(DFFT_T) dfft_cols_adj_k(const float4* __restrict__ T, double2* __restrict__ Gh,
+                                                          int lmax, int M, const float2* __restrict__ d1,
+                                                          const float2* __restrict__ d2, DfftLen f) {
+  extern __shared__ float4 X[];
+  const int m = blockIdx.x, n1 = f.N;
+  const float4* src = T + (int64_t)m * n1;
+  for (int k = threadIdx.x; k < n1; k += blockDim.x) X[k] = src[k];
+  __syncthreads();
+  dif_line<-1>(X, f);
+  const float2 dm = d2[m];
+  double2* g = Gh + (int64_t)m * M;
+  for (int kk = threadIdx.x; kk < M; kk += blockDim.x) {
+    const int k = kk <= M / 2 ? kk : kk - M;
+    double2 v = make_double2(0.0, 0.0);
+    if (k >= -lmax && k <= lmax) {
+      const float4 c = X[__ldg(f.rev + (k < 0 ? k + n1 : k))];
+      v = c_value(c_scale(c, df_mul(d1[k + lmax], dm)));
+    }
+    g[kk] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+bool factor(int n, DfftLen& f) {
+  std::vector<int> r;
+  for (int p : {7, 5, 3}) {
+    while (n % p == 0) {
+      r.push_back(p);
+      n /= p;
+    }
+  }
+  if (n % 2 == 0 && (n & (n - 1)) == 0) {
+    int e = 0;
+    while ((1 << e) < n) ++e;
+    if (e % 2) r.push_back(2);
+    for (int i = 0; i < e / 2; ++i) r.push_back(4);
+    n = 1;
+  }
+  if (n != 1 || (int)r.size() > DFFT_MAXPASS) return false;
+  f.npass = (int)r.size();
+  f.code = 0;
+  for (int i = 0; i < f.npass; ++i) f.code |= (unsigned long long)r[i] << (4 * i);
+  return true;
+}
+
+int make_len(int N, DfftLen& f, size_t* bytes) {
+  f.N = N;
+  if (!factor(N, f)) return set_error(NUSHT_EUNSUPPORTED, "double-float FFT: length has a prime factor above 7");
+  std::vector<float4> tw(N);
+  for (int k = 0; k < N; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)N;
+    const double c = std::cos(a), s = std::sin(a);
+    const float ch = (float)c, sh = (float)s;
+    tw[k] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
+  }
+  // output k = k_1 + R_1 (k_2 + R_2 (...)) sits at sum_s k_s N / (R_1 ... R_s)
+  std::vector<int> rev(N);
+  for (int k = 0; k < N; ++k) {
+    int kk = k, pos = 0, L = N;
+    for (int s = 0; s < f.npass; ++s) {
+      const int R = (int)((f.code >> (4 * s)) & 15u);
+      const int d = kk % R;
+      kk /= R;
+      L /= R;
+      pos += d * L;
+    }
+    rev[k] = pos;
+  }
+  NUSHT_TRY(dev_alloc((void**)&f.tw, (size_t)N * sizeof(float4), bytes));
+  NUSHT_TRY(dev_alloc((void**)&f.rev, (size_t)N * sizeof(int), bytes));
+  NUSHT_CUDA(cudaMemcpy(f.tw, tw.data(), (size_t)N * sizeof(float4), cudaMemcpyHostToDevice));
+  NUSHT_CUDA(cudaMemcpy(f.rev, rev.data(), (size_t)N * sizeof(int), cudaMemcpyHostToDevice));
+  return NUSHT_OK;
+}
+
+int smem_optin() {
+  static int done = 0;
+  if (done) return NUSHT_OK;
+  const int b = DFFT_NMAX * (int)sizeof(float4);
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_synth_k, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_c2r_k, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_r2c_k, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+  done = 1;
+  return NUSHT_OK;
+}
+
+std::vector<float2> pairs_of(const std::vector<double>& v) {
+  std::vector<float2> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    const float h = (float)v[i];
+    o[i] = make_float2(h, (float)(v[i] - (double)h));
+  }
+  return o;
+}
+
+}  // namespace
+
+bool dfft_fits(const nusht_sizes& z, bool theta, bool fine) {
+  auto ok = [](int n) {
+    DfftLen f;
+    return n >= 2 && n <= DFFT_NMAX && factor(n, f);
+  };
+  if (theta && !ok(z.M)) return false;
+  if (fine && (!ok(z.n1) || !ok(z.n2) || z.n2 % 2 || z.n1 <= 2 * z.lmax || 2 * z.mmax >= z.n2)) return false;
+  return true;
+}
+
+int dfft_setup(nusht_plan_t p, bool theta, bool fine, const double* d1, const double* d2) {
+  const nusht_sizes& z = p->sz;
+  NUSHT_TRY(smem_optin());
+  if (theta) {
+    NUSHT_TRY(make_len(z.M, p->dft_theta, &p->bytes));
+    p->dfft_theta = true;
+  }
+  if (fine) {
+    NUSHT_TRY(make_len(z.n1, p->dft_n1, &p->bytes));
+    NUSHT_TRY(make_len(z.n2, p->dft_n2, &p->bytes));
+    NUSHT_TRY(dev_alloc(&p->tcols, (size_t)(z.mmax + 1) * z.n1 * sizeof(float4), &p->bytes));
+    const std::vector<double> v1(d1, d1 + 2 * z.lmax + 1), v2(d2, d2 + z.mmax + 1);
+    const std::vector<float2> f1 = pairs_of(v1), f2 = pairs_of(v2);
+    NUSHT_TRY(dev_alloc((void**)&p->deconv1f, f1.size() * sizeof(float2), &p->bytes));
+    NUSHT_TRY(dev_alloc((void**)&p->deconv2f, f2.size() * sizeof(float2), &p->bytes));
+    NUSHT_CUDA(cudaMemcpy(p->deconv1f, f1.data(), f1.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    NUSHT_CUDA(cudaMemcpy(p->deconv2f, f2.data(), f2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    p->dfft_fine = true;
+  }
+  return NUSHT_OK;
+}
+
+void dfft_free(nusht_plan_t p) {
+  for (DfftLen* f : {&p->dft_theta, &p->dft_n1, &p->dft_n2}) {
+    dev_free(f->tw);
+    dev_free(f->rev);
+    f->tw = nullptr;
+    f->rev = nullptr;
+  }
+  dev_free(p->tcols);
+  dev_free(p->deconv1f);
+  dev_free(p->deconv2f);
+  p->tcols = nullptr;
+  p->deconv1f = p->deconv2f = nullptr;
+  p->dfft_theta = p->dfft_fine = false;
+}
+
+int dfft_theta_exec(nusht_plan_t p, const void* src, void* dst, int sign, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  const size_t sm = (size_t)z.M * sizeof(float4);
+  if (sign > 0)
+    dfft_lines_k<1><<<z.mmax + 1, DFFT_T, sm, s>>>((const double2*)src, (double2*)dst, z.M, z.mmax + 1, p->dft_theta);
+  else
+    dfft_lines_k<-1><<<z.mmax + 1, DFFT_T, sm, s>>>((const double2*)src, (double2*)dst, z.M, z.mmax + 1,
+                                                    p->dft_theta);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int dfft_cols_synth(nusht_plan_t p, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  dfft_cols_synth_k<<<z.mmax + 1, DFFT_T, (size_t)z.n1 * sizeof(float4), s>>>(
+      (const double2*)p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f, p->deconv2f, p->dft_n1);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int dfft_rows_c2r(nusht_plan_t p, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  const int64_t stride = 2 * (z.n2 / 2 + 1);
+  dfft_rows_c2r_k<<<(z.n1 + 1) / 2, DFFT_T, (size_t)z.n2 * sizeof(float4), s>>>(
+      (const float4*)p->tcols, (double*)p->fine, stride, z.n1, z.mmax, p->dft_n2);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int dfft_rows_r2c(nusht_plan_t p, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  const int64_t stride = 2 * (z.n2 / 2 + 1);
+  dfft_rows_r2c_k<<<(z.n1 + 1) / 2, DFFT_T, (size_t)z.n2 * sizeof(float4), s>>>(
+      (const double*)p->fine, (float4*)p->tcols, stride, z.n1, z.mmax, p->dft_n2);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int dfft_cols_adjoint(nusht_plan_t p, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  dfft_cols_adj_k<<<z.mmax + 1, DFFT_T, (size_t)z.n1 * sizeof(float4), s>>>(
+      (const float4*)p->tcols, (double2*)p->Ghat, z.lmax, z.M, p->deconv1f, p->deconv2f, p->dft_n1);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+}  // namespace nusht

@@ -885,6 +885,9 @@ int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t 
 }
 
 int deconv_pad(nusht_plan_t p, cudaStream_t s) {
+  // double-float FFT plans: deconvolution and zero-padding happen in the load
+  // of the column pass, which this stage then runs
+  if (p->dfft_fine) return dfft_cols_synth(p, s);
   const nusht_sizes& z = p->sz;
   const int n2h = z.n2 / 2 + 1;
   dim3 blk(32, 8), grd((n2h + 31) / 32, (z.n1 + 31) / 32);
@@ -899,6 +902,9 @@ int deconv_pad(nusht_plan_t p, cudaStream_t s) {
 }
 
 int deconv_trunc(nusht_plan_t p, cudaStream_t s) {
+  // double-float FFT plans: the column pass, with truncation and
+  // deconvolution in its store
+  if (p->dfft_fine) return dfft_cols_adjoint(p, s);
   const nusht_sizes& z = p->sz;
   const int n2h = z.n2 / 2 + 1;
   dim3 blk(32, 8), grd((z.M + 31) / 32, (z.mmax + 1 + 31) / 32);

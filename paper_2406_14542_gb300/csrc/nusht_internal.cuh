@@ -103,6 +103,19 @@ struct PointData {
   int* binsub = nullptr;      // subproblems of bin b: [binsub[b], binsub[b + 1])
 };
 
+// One transform length of the double-float FFT kernels (dfft.cu): radices
+// of the in-place decimation-in-frequency passes, the twiddle table
+// W_N^k = (cos hi, cos lo, sin hi, sin lo) and the shared-memory position of
+// each output index after the passes.
+constexpr int DFFT_NMAX = 14336;  // longest line: N float-pair complex values in shared memory
+constexpr int DFFT_MAXPASS = 16;
+struct DfftLen {
+  int N = 0, npass = 0;
+  unsigned long long code = 0;  // radix of pass s in bits [4s, 4s + 4)
+  float4* tw = nullptr;
+  int* rev = nullptr;
+};
+
 struct StageEvents {
   cudaEvent_t ev[8] = {};
   bool ready = false;
@@ -140,6 +153,15 @@ struct nusht_plan_s {
   cufftHandle fft_c2r = 0;    // FP64: rows complex-to-real along n2; FP32: 2D
   cufftHandle fft_r2c = 0;    // FP64: rows real-to-complex along n2; FP32: 2D
   bool have_theta = false, have_c2r = false, have_r2c = false, have_cols = false;
+
+  // FP64 plans: the theta and fine-grid FFTs as double-float kernels (dfft.cu)
+  // instead of cuFFT's FP64 transforms; tcols holds the fine spectrum order
+  // by order, [mmax + 1][n1] float-pair complex, between the column and row passes
+  bool dfft_theta = false, dfft_fine = false;
+  nusht::DfftLen dft_theta, dft_n1, dft_n2;
+  void* tcols = nullptr;
+  float2* deconv1f = nullptr;  // deconv1 / deconv2 as float pairs
+  float2* deconv2f = nullptr;
 
   size_t bytes = 0;
 
@@ -194,6 +216,15 @@ int tune_points(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t 
 // fine spectrum -> fine grid (inverse, both dimensions) and back (forward)
 int fine_fft_c2r(nusht_plan_t p, cudaStream_t s);
 int fine_fft_r2c(nusht_plan_t p, cudaStream_t s);
+// double-float FFTs (dfft.cu): whether every length fits, set-up, execution
+bool dfft_fits(const nusht_sizes& z, bool theta, bool fine);
+int dfft_setup(nusht_plan_t p, bool theta, bool fine, const double* d1, const double* d2);
+void dfft_free(nusht_plan_t p);
+int dfft_theta_exec(nusht_plan_t p, const void* src, void* dst, int sign, cudaStream_t s);
+int dfft_cols_synth(nusht_plan_t p, cudaStream_t s);
+int dfft_rows_c2r(nusht_plan_t p, cudaStream_t s);
+int dfft_rows_r2c(nusht_plan_t p, cudaStream_t s);
+int dfft_cols_adjoint(nusht_plan_t p, cudaStream_t s);
 // largest ES kernel width the spreading / interpolation kernels support
 constexpr int ES_WMAX = 20;
 // ES kernel width the accuracy formula asks for at NUFFT tolerance eps and

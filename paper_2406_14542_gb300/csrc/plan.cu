@@ -221,6 +221,7 @@ static void plan_free(nusht_plan_t p) {
   if (p->ghat_owned) dev_free(p->Ghat);
   dev_free(p->fine);
   dev_free(p->partial);
+  dfft_free(p);
   if (p->have_theta) cufftDestroy(p->fft_theta);
   if (p->have_cols) cufftDestroy(p->fft_cols);
   if (p->have_c2r) cufftDestroy(p->fft_c2r);
@@ -232,18 +233,23 @@ static void plan_free(nusht_plan_t p) {
   delete p;
 }
 
-static int make_ffts(nusht_plan_t p) {
+static int make_ffts(nusht_plan_t p, const double* d1, const double* d2) {
   const nusht_sizes& z = p->sz;
   const bool dbl = p->precision == NUSHT_FP64;
   int M = z.M;
   size_t ws = 0;
-  if (p->has_legendre) {
+  // FP64: double-float kernels for every length that fits in shared memory
+  const bool own = dbl && p->opts.fft_kernels >= 0;
+  const bool own_theta = own && p->has_legendre && dfft_fits(z, true, false);
+  const bool own_fine = own && p->has_nufft && dfft_fits(z, false, true);
+  if (own_theta || own_fine) NUSHT_TRY(dfft_setup(p, own_theta, own_fine, d1, d2));
+  if (p->has_legendre && !own_theta) {
     NUSHT_CUFFT(cufftCreate(&p->fft_theta));
     p->have_theta = true;
     NUSHT_CUFFT(cufftMakePlanMany(p->fft_theta, 1, &M, nullptr, 1, M, nullptr, 1, M, dbl ? CUFFT_Z2Z : CUFFT_C2C,
                                   z.mmax + 1, &ws));
   }
-  if (!p->has_nufft) return NUSHT_OK;
+  if (!p->has_nufft || own_fine) return NUSHT_OK;
   if (!dbl) {  // FP32: cuFFT's own 2D plans measured faster than the split below
     NUSHT_CUFFT(cufftCreate(&p->fft_c2r));
     p->have_c2r = true;
@@ -270,7 +276,21 @@ static int make_ffts(nusht_plan_t p) {
   return NUSHT_OK;
 }
 
+// theta DFT of the doubled ring map, [mmax + 1][M] complex: sign -1 forward
+// (synthesis), +1 inverse (adjoint); src == dst allowed
+static int theta_fft(nusht_plan_t p, const void* src, void* dst, int sign, cudaStream_t s) {
+  if (p->dfft_theta) return dfft_theta_exec(p, src, dst, sign, s);
+  const int dir = sign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE;
+  NUSHT_CUFFT(cufftSetStream(p->fft_theta, s));
+  if (p->precision == NUSHT_FP64)
+    NUSHT_CUFFT(cufftExecZ2Z(p->fft_theta, (cufftDoubleComplex*)src, (cufftDoubleComplex*)dst, dir));
+  else
+    NUSHT_CUFFT(cufftExecC2C(p->fft_theta, (cufftComplex*)src, (cufftComplex*)dst, dir));
+  return NUSHT_OK;
+}
+
 int nusht::fine_fft_c2r(nusht_plan_t p, cudaStream_t s) {
+  if (p->dfft_fine) return dfft_rows_c2r(p, s);
   NUSHT_CUFFT(cufftSetStream(p->fft_c2r, s));
   if (!p->have_cols) {
     NUSHT_CUFFT(cufftExecC2R(p->fft_c2r, (cufftComplex*)p->fine, (cufftReal*)p->fine));
@@ -288,6 +308,7 @@ int nusht::fine_fft_c2r(nusht_plan_t p, cudaStream_t s) {
 }
 
 int nusht::fine_fft_r2c(nusht_plan_t p, cudaStream_t s) {
+  if (p->dfft_fine) return dfft_rows_r2c(p, s);
   NUSHT_CUFFT(cufftSetStream(p->fft_r2c, s));
   if (!p->have_cols) {
     NUSHT_CUFFT(cufftExecR2C(p->fft_r2c, (cufftReal*)p->fine, (cufftComplex*)p->fine));
@@ -333,11 +354,11 @@ static int plan_body(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStre
   }
   // Fourier factors of the ES kernel (deconvolution, Sec. 3 on the NUFFT):
   // d1[k] = h1 / (M psihat1(k)) folds the 1/M of the theta DFT, d2[m] = h2 / psihat2(m).
+  std::vector<double> d1(2 * z.lmax + 1), d2(z.mmax + 1);
   {
     std::vector<double> f1(z.lmax + 1), f2(z.mmax + 1);
     kernel_ft(z.w, z.beta, z.n1, z.lmax + 1, f1.data());
     kernel_ft(z.w, z.beta, z.n2, z.mmax + 1, f2.data());
-    std::vector<double> d1(2 * z.lmax + 1), d2(z.mmax + 1);
     const double h1 = 2.0 * M_PI / z.n1, h2 = 2.0 * M_PI / z.n2;
     for (int k = -z.lmax; k <= z.lmax; ++k) d1[k + z.lmax] = h1 / ((double)z.M * f1[std::abs(k)]);
     for (int m = 0; m <= z.mmax; ++m) d2[m] = h2 / f2[m];
@@ -364,7 +385,7 @@ static int plan_body(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStre
     NUSHT_TRY(dev_alloc(&p->partial, (size_t)p->leg.blocks_per_m * p->nalm * cplx, &p->bytes));
     NUSHT_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)p->leg.blocks_per_m * p->nalm * cplx, s));
   }
-  NUSHT_TRY(make_ffts(p));
+  NUSHT_TRY(make_ffts(p, d1.data(), d2.data()));
   NUSHT_TRY(spread_smem_optin());
   if (role.bin > 0) {
     p->pts.bin = role.bin;
@@ -479,17 +500,12 @@ int nusht_synth(nusht_plan_t p, const void* d_alm, void* d_map, nusht_stream_t s
   const bool prof = p->opts.profile != 0;
   if (prof) NUSHT_TRY(ev_init(p->ev_synth));
   p->last_stream = s;
-  const bool dbl = p->precision == NUSHT_FP64;
   STAGE(p->ev_synth, 0);
   // S with D fused into its store: Legendre sums on the rings, written doubled
   NUSHT_TRY(legendre_synth(p, d_alm, s));
   STAGE(p->ev_synth, 1);
   // F along theta (the phi transforms of S and F cancel, Sec. 3)
-  NUSHT_CUFFT(cufftSetStream(p->fft_theta, s));
-  if (dbl)
-    NUSHT_CUFFT(cufftExecZ2Z(p->fft_theta, (cufftDoubleComplex*)p->G, (cufftDoubleComplex*)p->Ghat, CUFFT_FORWARD));
-  else
-    NUSHT_CUFFT(cufftExecC2C(p->fft_theta, (cufftComplex*)p->G, (cufftComplex*)p->Ghat, CUFFT_FORWARD));
+  NUSHT_TRY(theta_fft(p, p->G, p->Ghat, -1, s));
   STAGE(p->ev_synth, 2);
   // N: deconvolve and zero-pad onto the fine spectrum, FFT to the fine grid, interpolate
   NUSHT_TRY(deconv_pad(p, s));
@@ -508,7 +524,6 @@ int nusht_adjoint(nusht_plan_t p, const void* d_map, void* d_alm, nusht_stream_t
   const bool prof = p->opts.profile != 0;
   if (prof) NUSHT_TRY(ev_init(p->ev_adj));
   p->last_stream = s;
-  const bool dbl = p->precision == NUSHT_FP64;
   STAGE(p->ev_adj, 0);
   // N^dagger: spread onto the fine grid
   NUSHT_TRY(spread(p, d_map, s));
@@ -519,11 +534,7 @@ int nusht_adjoint(nusht_plan_t p, const void* d_map, void* d_alm, nusht_stream_t
   NUSHT_TRY(deconv_trunc(p, s));
   STAGE(p->ev_adj, 3);
   // F^dagger along theta
-  NUSHT_CUFFT(cufftSetStream(p->fft_theta, s));
-  if (dbl)
-    NUSHT_CUFFT(cufftExecZ2Z(p->fft_theta, (cufftDoubleComplex*)p->Ghat, (cufftDoubleComplex*)p->Ghat, CUFFT_INVERSE));
-  else
-    NUSHT_CUFFT(cufftExecC2C(p->fft_theta, (cufftComplex*)p->Ghat, (cufftComplex*)p->Ghat, CUFFT_INVERSE));
+  NUSHT_TRY(theta_fft(p, p->Ghat, p->Ghat, 1, s));
   STAGE(p->ev_adj, 4);
   // D^dagger fused into S^dagger's load: fold, then adjoint Legendre sums
   NUSHT_TRY(legendre_adjoint(p, d_alm, s));
@@ -536,13 +547,8 @@ int nusht_synth_grad(nusht_plan_t p, const void* d_alm, void* d_dtheta, void* d_
   if (!d_alm) return set_error(NUSHT_EINVAL, "null alm pointer");
   if (!d_dtheta && !d_dphi) return NUSHT_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  const bool dbl = p->precision == NUSHT_FP64;
   NUSHT_TRY(legendre_synth(p, d_alm, s));
-  NUSHT_CUFFT(cufftSetStream(p->fft_theta, s));
-  if (dbl)
-    NUSHT_CUFFT(cufftExecZ2Z(p->fft_theta, (cufftDoubleComplex*)p->G, (cufftDoubleComplex*)p->Ghat, CUFFT_FORWARD));
-  else
-    NUSHT_CUFFT(cufftExecC2C(p->fft_theta, (cufftComplex*)p->G, (cufftComplex*)p->Ghat, CUFFT_FORWARD));
+  NUSHT_TRY(theta_fft(p, p->G, p->Ghat, -1, s));
   NUSHT_TRY(deconv_pad(p, s));
   NUSHT_TRY(fine_fft_c2r(p, s));
   NUSHT_TRY(interp_grad(p, d_dtheta, d_dphi, s));
