@@ -104,13 +104,60 @@ __device__ __forceinline__ void c_mac(float4& acc, float4 a, float2 c) {
   df_mac(acc.z, acc.w, a.z, a.w, c.x, c.y);
 }
 
+// conversions with integer operations only (the FP64 pipe issues a warp's
+// conversion or add once per 64 cycles per SM sub-partition)
+// double -> float pair: leading 24 bits and the rounded rest; |v| below 2^-126
+// flushes to zero, above the float range saturates
+__device__ __forceinline__ void split_d(double v, float& h, float& l) {
+  const int hi = __double2hiint(v);
+  if (((hi >> 20) & 0x7ff) > 1023 + 127) {
+    h = __int_as_float(hi < 0 ? (int)0xff800000 : 0x7f800000);
+    l = 0.0f;
+    return;
+  }
+  split_q(v, h, l);
+}
+// renormalised float pair (|l| <= ulp(h)) -> double, within 2^-52 relative:
+// the two significands aligned and added as integers
+__device__ __forceinline__ double pair_to_double(float h, float l) {
+  const unsigned hb = __float_as_uint(h), lb = __float_as_uint(l);
+  const int eh = (int)((hb >> 23) & 0xffu);
+  if (eh == 0) return 0.0;
+  long long mh = (long long)((hb & 0x7fffffu) | 0x800000u) << 29;  // unit 2^(eh - 127 - 52)
+  int el = (int)((lb >> 23) & 0xffu);
+  long long ml = (long long)(lb & 0x7fffffu);
+  if (el != 0) {
+    ml |= 0x800000;
+  } else {
+    el = 1;  // subnormal l
+  }
+  if (ml != 0) {
+    const int sh = el - eh + 29;
+    ml = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> -sh) : 0);
+    mh = ((hb ^ lb) & 0x80000000u) ? mh - ml : mh + ml;
+  }
+  long long e = eh - 127 + 1023;
+  if (mh >= (1LL << 53)) {
+    mh >>= 1;
+    ++e;
+  } else if (mh < (1LL << 52)) {
+    mh <<= 1;
+    --e;
+  }
+  const unsigned long long bits = ((unsigned long long)(hb & 0x80000000u) << 32) | ((unsigned long long)e << 52) |
+                                  ((unsigned long long)mh & ((1ULL << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ float4 c_of(double2 v) {
   float4 r;
-  df_split(v.x, r.x, r.y);
-  df_split(v.y, r.z, r.w);
+  split_d(v.x, r.x, r.y);
+  split_d(v.y, r.z, r.w);
   return r;
 }
-__device__ __forceinline__ double2 c_value(float4 c) { return make_double2(df_value(c.x, c.y), df_value(c.z, c.w)); }
+__device__ __forceinline__ double2 c_value(float4 c) {
+  return make_double2(pair_to_double(c.x, c.y), pair_to_double(c.z, c.w));
+}
 
 // ---------------------------------------------------------------------------
 // small DFTs of the butterflies (sign SG: +1 inverse, -1 forward)
@@ -163,6 +210,15 @@ __device__ __forceinline__ void dif_pass(float4* X, const DfftLen& f, int L, int
   const int nb = f.N / R;
   const bool pow2 = (S & (S - 1)) == 0;
   const int sh = pow2 ? __ffs(S) - 1 : 0;
+  // the twiddles of the thread's next butterfly are fetched one butterfly
+  // ahead (they come from L2: the table does not fit in L1 next to the line)
+  float4 w[R - 1];
+  {
+    const int t = threadIdx.x < nb ? threadIdx.x : 0;
+    const int j = t - (pow2 ? (t >> sh) : t / S) * S;
+#pragma unroll
+    for (int q = 1; q < R; ++q) w[q - 1] = __ldg(f.tw + mul * j * q);
+  }
   for (int t = threadIdx.x; t < nb; t += blockDim.x) {
     const int b = pow2 ? (t >> sh) : t / S;
     const int j = t - b * S;
@@ -170,6 +226,13 @@ __device__ __forceinline__ void dif_pass(float4* X, const DfftLen& f, int L, int
     float4 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = p[r * S];
+    float4 wn[R - 1];
+    {
+      const int tn = t + blockDim.x < nb ? t + blockDim.x : t;
+      const int jn = tn - (pow2 ? (tn >> sh) : tn / S) * S;
+#pragma unroll
+      for (int q = 1; q < R; ++q) wn[q - 1] = __ldg(f.tw + mul * jn * q);
+    }
     if constexpr (R == 2) {
       const float4 a = v[0];
       v[0] = c_add(a, v[1]);
@@ -181,9 +244,11 @@ __device__ __forceinline__ void dif_pass(float4* X, const DfftLen& f, int L, int
     }
     // output q times W_L^(j q) = W_N^(mul j q), mul = N / L
 #pragma unroll
-    for (int q = 1; q < R; ++q) v[q] = c_mul_tw<SG>(v[q], __ldg(f.tw + mul * j * q));
+    for (int q = 1; q < R; ++q) v[q] = c_mul_tw<SG>(v[q], w[q - 1]);
 #pragma unroll
     for (int r = 0; r < R; ++r) p[r * S] = v[r];
+#pragma unroll
+    for (int q = 0; q < R - 1; ++q) w[q] = wn[q];
   }
 }
 
@@ -210,31 +275,38 @@ __device__ void dif_line(float4* X, const DfftLen& f) {
 // kernels
 // ---------------------------------------------------------------------------
 
-// complex lines of length f.N (stride ld), in place allowed
-template <int SG>
-__global__ void __launch_bounds__(DFFT_T) dfft_lines_k(const double2* in, double2* out, int64_t ld, int nlines,
-                                                       DfftLen f) {
+// complex lines of length f.N (stride ld), in place allowed; input and
+// output either double2 or float pairs (INP / OUTP), 16 bytes per value
+template <int SG, bool INP, bool OUTP>
+__global__ void __launch_bounds__(DFFT_T) dfft_lines_k(const void* in, void* out, int64_t ld, int nlines, DfftLen f) {
   extern __shared__ float4 X[];
   for (int line = blockIdx.x; line < nlines; line += gridDim.x) {
-    const double2* src = in + (int64_t)line * ld;
-    for (int k = threadIdx.x; k < f.N; k += blockDim.x) X[k] = c_of(src[k]);
+    const int64_t o = (int64_t)line * ld;
+    for (int k = threadIdx.x; k < f.N; k += blockDim.x)
+      X[k] = INP ? static_cast<const float4*>(in)[o + k] : c_of(static_cast<const double2*>(in)[o + k]);
     __syncthreads();
     dif_line<SG>(X, f);
-    double2* dst = out + (int64_t)line * ld;
-    for (int k = threadIdx.x; k < f.N; k += blockDim.x) dst[k] = c_value(X[__ldg(f.rev + k)]);
+    for (int k = threadIdx.x; k < f.N; k += blockDim.x) {
+      const float4 c = X[__ldg(f.rev + k)];
+      if (OUTP)
+        static_cast<float4*>(out)[o + k] = c;
+      else
+        static_cast<double2*>(out)[o + k] = c_value(c);
+    }
     __syncthreads();
   }
 }
 
 // synthesis, per order m: H[k1] = Ghat[m][k mod M] d1[k] d2[m] for |k| <= lmax
 // (k1 = k mod n1), zero elsewhere; inverse DFT along theta; T[m][j]
-__global__ void __launch_bounds__(DFFT_T) dfft_cols_synth_k(const double2* __restrict__ Gh, float4* __restrict__ T,
+template <bool INP>
+__global__ void __launch_bounds__(DFFT_T) dfft_cols_synth_k(const void* __restrict__ Gh, float4* __restrict__ T,
                                                             int lmax, int M, const float2* __restrict__ d1,
                                                             const float2* __restrict__ d2, DfftLen f) {
   extern __shared__ float4 X[];
   const int m = blockIdx.x, n1 = f.N;
   const float2 dm = d2[m];
-  const double2* g = Gh + (int64_t)m * M;
+  const int64_t o = (int64_t)m * M;
   for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     int k = k1;
@@ -243,7 +315,11 @@ __global__ void __launch_bounds__(DFFT_T) dfft_cols_synth_k(const double2* __res
       k = k1 - n1;
       keep = k >= -lmax;
     }
-    if (keep) v = c_scale(c_of(g[k < 0 ? k + M : k]), df_mul(d1[k + lmax], dm));
+    if (keep) {
+      const int64_t i = o + (k < 0 ? k + M : k);
+      const float4 gv = INP ? static_cast<const float4*>(Gh)[i] : c_of(static_cast<const double2*>(Gh)[i]);
+      v = c_scale(gv, df_mul(d1[k + lmax], dm));
+    }
     X[k1] = v;
   }
   __syncthreads();
@@ -279,8 +355,8 @@ __global__ void __launch_bounds__(DFFT_T) dfft_rows_c2r_k(const float4* __restri
   double* r0 = grid + (int64_t)j * stride;
   for (int n = threadIdx.x; n < n2; n += blockDim.x) {
     const float4 c = X[__ldg(f.rev + n)];
-    r0[n] = df_value(c.x, c.y);
-    if (two) r0[stride + n] = df_value(c.z, c.w);
+    r0[n] = pair_to_double(c.x, c.y);
+    if (two) r0[stride + n] = pair_to_double(c.z, c.w);
   }
 }
 
@@ -294,9 +370,9 @@ __global__ void __launch_bounds__(DFFT_T) dfft_rows_r2c_k(const double* __restri
   const double* r0 = grid + (int64_t)j * stride;
   for (int n = threadIdx.x; n < n2; n += blockDim.x) {
     float4 v;
-    df_split(r0[n], v.x, v.y);
+    split_d(r0[n], v.x, v.y);
     if (two) {
-      df_split(r0[stride + n], v.z, v.w);
+      split_d(r0[stride + n], v.z, v.w);
     } else {
       v.z = v.w = 0.f;
     }
@@ -317,7 +393,8 @@ __global__ void __launch_bounds__(DFFT_T) dfft_rows_r2c_k(const double* __restri
 
 // adjoint, per order m: forward DFT of T[m][.] along theta, then
 // Ghat[m][kk] = H[k mod n1] d1[k] d2[m] for |k| <= lmax (k = kk or kk - M), else 0
-__global__ void __launch_bounds__(DFFT_T) dfft_cols_adj_k(const float4* __restrict__ T, double2* __restrict__ Gh,
+template <bool OUTP>
+__global__ void __launch_bounds__(DFFT_T) dfft_cols_adj_k(const float4* __restrict__ T, void* __restrict__ Gh,
                                                           int lmax, int M, const float2* __restrict__ d1,
                                                           const float2* __restrict__ d2, DfftLen f) {
   extern __shared__ float4 X[];
@@ -327,15 +404,18 @@ __global__ void __launch_bounds__(DFFT_T) dfft_cols_adj_k(const float4* __restri
   __syncthreads();
   dif_line<-1>(X, f);
   const float2 dm = d2[m];
-  double2* g = Gh + (int64_t)m * M;
+  const int64_t o = (int64_t)m * M;
   for (int kk = threadIdx.x; kk < M; kk += blockDim.x) {
     const int k = kk <= M / 2 ? kk : kk - M;
-    double2 v = make_double2(0.0, 0.0);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k >= -lmax && k <= lmax) {
       const float4 c = X[__ldg(f.rev + (k < 0 ? k + n1 : k))];
-      v = c_value(c_scale(c, df_mul(d1[k + lmax], dm)));
+      v = c_scale(c, df_mul(d1[k + lmax], dm));
     }
-    g[kk] = v;
+    if (OUTP)
+      static_cast<float4*>(Gh)[o + kk] = v;
+    else
+      static_cast<double2*>(Gh)[o + kk] = c_value(v);
   }
 }
 
@@ -398,12 +478,17 @@ int smem_optin() {
   static int done = 0;
   if (done) return NUSHT_OK;
   const int b = DFFT_NMAX * (int)sizeof(float4);
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_synth_k, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_c2r_k, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_r2c_k, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k, cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<-1, false, false>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<-1, false, true>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1, false, false>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1, true, false>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_synth_k<false>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_synth_k<true>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_c2r_k, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_r2c_k, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k<false>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k<true>, a, b));
   done = 1;
   return NUSHT_OK;
 }
@@ -466,22 +551,38 @@ void dfft_free(nusht_plan_t p) {
   p->dfft_theta = p->dfft_fine = false;
 }
 
+// With both the theta and the fine-grid transforms here, the theta spectrum
+// passes between them as float pairs: synthesis writes Ghat as pairs for the
+// column pass, the adjoint's column pass writes pairs for the inverse theta
+// DFT; the ring map G and the adjoint's final Ghat stay double2.
 int dfft_theta_exec(nusht_plan_t p, const void* src, void* dst, int sign, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const size_t sm = (size_t)z.M * sizeof(float4);
-  if (sign > 0)
-    dfft_lines_k<1><<<z.mmax + 1, DFFT_T, sm, s>>>((const double2*)src, (double2*)dst, z.M, z.mmax + 1, p->dft_theta);
-  else
-    dfft_lines_k<-1><<<z.mmax + 1, DFFT_T, sm, s>>>((const double2*)src, (double2*)dst, z.M, z.mmax + 1,
-                                                    p->dft_theta);
+  const int nl = z.mmax + 1;
+  if (sign < 0) {
+    if (p->dfft_fine)
+      dfft_lines_k<-1, false, true><<<nl, DFFT_T, sm, s>>>(src, dst, z.M, nl, p->dft_theta);
+    else
+      dfft_lines_k<-1, false, false><<<nl, DFFT_T, sm, s>>>(src, dst, z.M, nl, p->dft_theta);
+  } else {
+    if (p->dfft_fine)
+      dfft_lines_k<1, true, false><<<nl, DFFT_T, sm, s>>>(src, dst, z.M, nl, p->dft_theta);
+    else
+      dfft_lines_k<1, false, false><<<nl, DFFT_T, sm, s>>>(src, dst, z.M, nl, p->dft_theta);
+  }
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
 
 int dfft_cols_synth(nusht_plan_t p, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
-  dfft_cols_synth_k<<<z.mmax + 1, DFFT_T, (size_t)z.n1 * sizeof(float4), s>>>(
-      (const double2*)p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f, p->deconv2f, p->dft_n1);
+  const size_t sm = (size_t)z.n1 * sizeof(float4);
+  if (p->dfft_theta)
+    dfft_cols_synth_k<true><<<z.mmax + 1, DFFT_T, sm, s>>>(p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f,
+                                                           p->deconv2f, p->dft_n1);
+  else
+    dfft_cols_synth_k<false><<<z.mmax + 1, DFFT_T, sm, s>>>(p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f,
+                                                            p->deconv2f, p->dft_n1);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
@@ -506,8 +607,13 @@ int dfft_rows_r2c(nusht_plan_t p, cudaStream_t s) {
 
 int dfft_cols_adjoint(nusht_plan_t p, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
-  dfft_cols_adj_k<<<z.mmax + 1, DFFT_T, (size_t)z.n1 * sizeof(float4), s>>>(
-      (const float4*)p->tcols, (double2*)p->Ghat, z.lmax, z.M, p->deconv1f, p->deconv2f, p->dft_n1);
+  const size_t sm = (size_t)z.n1 * sizeof(float4);
+  if (p->dfft_theta)
+    dfft_cols_adj_k<true><<<z.mmax + 1, DFFT_T, sm, s>>>((const float4*)p->tcols, p->Ghat, z.lmax, z.M, p->deconv1f,
+                                                         p->deconv2f, p->dft_n1);
+  else
+    dfft_cols_adj_k<false><<<z.mmax + 1, DFFT_T, sm, s>>>((const float4*)p->tcols, p->Ghat, z.lmax, z.M,
+                                                          p->deconv1f, p->deconv2f, p->dft_n1);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
