@@ -38,7 +38,9 @@
 namespace nusht {
 namespace {
 
-constexpr int DFFT_T = 512;  // threads per line
+// threads per line: 1024 for lengths whose radices are 2, 3, 4 (54 to 62
+// registers), 512 when a radix 5 or 7 pass is compiled in (up to 128)
+constexpr int DFFT_T_WIDE = 1024, DFFT_T_ODD = 512;
 
 // ---------------------------------------------------------------------------
 // float-pair complex arithmetic (float4 = re.hi, re.lo, im.hi, im.lo)
@@ -253,18 +255,23 @@ __device__ __forceinline__ void dif_pass(float4* X, const DfftLen& f, int L, int
 }
 
 // all passes; natural-order input in X, output k at X[f.rev[k]]
-template <int SG>
+template <int SG, int NT>
 __device__ void dif_line(float4* X, const DfftLen& f) {
   int L = f.N;
   for (int s = 0; s < f.npass; ++s) {
     const int R = (int)((f.code >> (4 * s)) & 15u);
     const int mul = f.N / L;
-    switch (R) {
-      case 4: dif_pass<4, SG>(X, f, L, mul); break;
-      case 2: dif_pass<2, SG>(X, f, L, mul); break;
-      case 3: dif_pass<3, SG>(X, f, L, mul); break;
-      case 5: dif_pass<5, SG>(X, f, L, mul); break;
-      default: dif_pass<7, SG>(X, f, L, mul); break;
+    if (R == 4) {
+      dif_pass<4, SG>(X, f, L, mul);
+    } else if (R == 2) {
+      dif_pass<2, SG>(X, f, L, mul);
+    } else if (R == 3) {
+      dif_pass<3, SG>(X, f, L, mul);
+    } else if constexpr (NT == DFFT_T_ODD) {
+      if (R == 5)
+        dif_pass<5, SG>(X, f, L, mul);
+      else
+        dif_pass<7, SG>(X, f, L, mul);
     }
     __syncthreads();
     L /= R;
@@ -277,15 +284,15 @@ __device__ void dif_line(float4* X, const DfftLen& f) {
 
 // complex lines of length f.N (stride ld), in place allowed; input and
 // output either double2 or float pairs (INP / OUTP), 16 bytes per value
-template <int SG, bool INP, bool OUTP>
-__global__ void __launch_bounds__(DFFT_T) dfft_lines_k(const void* in, void* out, int64_t ld, int nlines, DfftLen f) {
+template <int SG, bool INP, bool OUTP, int NT>
+__global__ void __launch_bounds__(NT) dfft_lines_k(const void* in, void* out, int64_t ld, int nlines, DfftLen f) {
   extern __shared__ float4 X[];
   for (int line = blockIdx.x; line < nlines; line += gridDim.x) {
     const int64_t o = (int64_t)line * ld;
     for (int k = threadIdx.x; k < f.N; k += blockDim.x)
       X[k] = INP ? static_cast<const float4*>(in)[o + k] : c_of(static_cast<const double2*>(in)[o + k]);
     __syncthreads();
-    dif_line<SG>(X, f);
+    dif_line<SG, NT>(X, f);
     for (int k = threadIdx.x; k < f.N; k += blockDim.x) {
       const float4 c = X[__ldg(f.rev + k)];
       if (OUTP)
@@ -299,8 +306,8 @@ __global__ void __launch_bounds__(DFFT_T) dfft_lines_k(const void* in, void* out
 
 // synthesis, per order m: H[k1] = Ghat[m][k mod M] d1[k] d2[m] for |k| <= lmax
 // (k1 = k mod n1), zero elsewhere; inverse DFT along theta; T[m][j]
-template <bool INP>
-__global__ void __launch_bounds__(DFFT_T) dfft_cols_synth_k(const void* __restrict__ Gh, float4* __restrict__ T,
+template <bool INP, int NT>
+__global__ void __launch_bounds__(NT) dfft_cols_synth_k(const void* __restrict__ Gh, float4* __restrict__ T,
                                                             int lmax, int M, const float2* __restrict__ d1,
                                                             const float2* __restrict__ d2, DfftLen f) {
   extern __shared__ float4 X[];
@@ -323,13 +330,14 @@ __global__ void __launch_bounds__(DFFT_T) dfft_cols_synth_k(const void* __restri
     X[k1] = v;
   }
   __syncthreads();
-  dif_line<1>(X, f);
+  dif_line<1, NT>(X, f);
   float4* dst = T + (int64_t)m * n1;
   for (int j = threadIdx.x; j < n1; j += blockDim.x) dst[j] = X[__ldg(f.rev + j)];
 }
 
 // synthesis, per row pair (j, j + 1): the real rows of the fine grid
-__global__ void __launch_bounds__(DFFT_T) dfft_rows_c2r_k(const float4* __restrict__ T, double* __restrict__ grid,
+template <int NT>
+__global__ void __launch_bounds__(NT) dfft_rows_c2r_k(const float4* __restrict__ T, double* __restrict__ grid,
                                                           int64_t stride, int n1, int mmax, DfftLen f) {
   extern __shared__ float4 X[];
   const int n2 = f.N;
@@ -351,7 +359,7 @@ __global__ void __launch_bounds__(DFFT_T) dfft_rows_c2r_k(const float4* __restri
     }
   }
   __syncthreads();
-  dif_line<1>(X, f);
+  dif_line<1, NT>(X, f);
   double* r0 = grid + (int64_t)j * stride;
   for (int n = threadIdx.x; n < n2; n += blockDim.x) {
     const float4 c = X[__ldg(f.rev + n)];
@@ -361,7 +369,8 @@ __global__ void __launch_bounds__(DFFT_T) dfft_rows_c2r_k(const float4* __restri
 }
 
 // adjoint, per row pair: spectra m <= mmax of rows j, j + 1 into T[m][j], T[m][j + 1]
-__global__ void __launch_bounds__(DFFT_T) dfft_rows_r2c_k(const double* __restrict__ grid, float4* __restrict__ T,
+template <int NT>
+__global__ void __launch_bounds__(NT) dfft_rows_r2c_k(const double* __restrict__ grid, float4* __restrict__ T,
                                                           int64_t stride, int n1, int mmax, DfftLen f) {
   extern __shared__ float4 X[];
   const int n2 = f.N;
@@ -379,7 +388,7 @@ __global__ void __launch_bounds__(DFFT_T) dfft_rows_r2c_k(const double* __restri
     X[n] = v;
   }
   __syncthreads();
-  dif_line<-1>(X, f);
+  dif_line<-1, NT>(X, f);
   for (int m = threadIdx.x; m <= mmax; m += blockDim.x) {
     const float4 cm = X[__ldg(f.rev + m)];
     const float4 cn = X[__ldg(f.rev + (m == 0 ? 0 : n2 - m))];
@@ -393,8 +402,8 @@ __global__ void __launch_bounds__(DFFT_T) dfft_rows_r2c_k(const double* __restri
 
 // adjoint, per order m: forward DFT of T[m][.] along theta, then
 // Ghat[m][kk] = H[k mod n1] d1[k] d2[m] for |k| <= lmax (k = kk or kk - M), else 0
-template <bool OUTP>
-__global__ void __launch_bounds__(DFFT_T) dfft_cols_adj_k(const float4* __restrict__ T, void* __restrict__ Gh,
+template <bool OUTP, int NT>
+__global__ void __launch_bounds__(NT) dfft_cols_adj_k(const float4* __restrict__ T, void* __restrict__ Gh,
                                                           int lmax, int M, const float2* __restrict__ d1,
                                                           const float2* __restrict__ d2, DfftLen f) {
   extern __shared__ float4 X[];
@@ -402,7 +411,7 @@ __global__ void __launch_bounds__(DFFT_T) dfft_cols_adj_k(const float4* __restri
   const float4* src = T + (int64_t)m * n1;
   for (int k = threadIdx.x; k < n1; k += blockDim.x) X[k] = src[k];
   __syncthreads();
-  dif_line<-1>(X, f);
+  dif_line<-1, NT>(X, f);
   const float2 dm = d2[m];
   const int64_t o = (int64_t)m * M;
   for (int kk = threadIdx.x; kk < M; kk += blockDim.x) {
@@ -474,21 +483,37 @@ int make_len(int N, DfftLen& f, size_t* bytes) {
   return NUSHT_OK;
 }
 
+template <int NT>
+int optin_all(int b) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<-1, false, false, NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<-1, false, true, NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1, false, false, NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1, true, false, NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_synth_k<false, NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_synth_k<true, NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_c2r_k<NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_r2c_k<NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k<false, NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k<true, NT>, a, b));
+  return NUSHT_OK;
+}
+
+// whether every pass of f has radix 2, 3 or 4 (the 1024-thread kernels)
+bool wide(const DfftLen& f) {
+  for (int i = 0; i < f.npass; ++i) {
+    const int R = (int)((f.code >> (4 * i)) & 15u);
+    if (R == 5 || R == 7) return false;
+  }
+  return true;
+}
+
 int smem_optin() {
   static int done = 0;
   if (done) return NUSHT_OK;
   const int b = DFFT_NMAX * (int)sizeof(float4);
-  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<-1, false, false>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<-1, false, true>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1, false, false>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1, true, false>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_synth_k<false>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_synth_k<true>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_c2r_k, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_r2c_k, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k<false>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k<true>, a, b));
+  NUSHT_TRY(optin_all<DFFT_T_WIDE>(b));
+  NUSHT_TRY(optin_all<DFFT_T_ODD>(b));
   done = 1;
   return NUSHT_OK;
 }
@@ -559,16 +584,23 @@ int dfft_theta_exec(nusht_plan_t p, const void* src, void* dst, int sign, cudaSt
   const nusht_sizes& z = p->sz;
   const size_t sm = (size_t)z.M * sizeof(float4);
   const int nl = z.mmax + 1;
+  const DfftLen& f = p->dft_theta;
+  auto go = [&](auto kw, auto ko) {
+    if (wide(f))
+      kw<<<nl, DFFT_T_WIDE, sm, s>>>(src, dst, z.M, nl, f);
+    else
+      ko<<<nl, DFFT_T_ODD, sm, s>>>(src, dst, z.M, nl, f);
+  };
   if (sign < 0) {
     if (p->dfft_fine)
-      dfft_lines_k<-1, false, true><<<nl, DFFT_T, sm, s>>>(src, dst, z.M, nl, p->dft_theta);
+      go(dfft_lines_k<-1, false, true, DFFT_T_WIDE>, dfft_lines_k<-1, false, true, DFFT_T_ODD>);
     else
-      dfft_lines_k<-1, false, false><<<nl, DFFT_T, sm, s>>>(src, dst, z.M, nl, p->dft_theta);
+      go(dfft_lines_k<-1, false, false, DFFT_T_WIDE>, dfft_lines_k<-1, false, false, DFFT_T_ODD>);
   } else {
     if (p->dfft_fine)
-      dfft_lines_k<1, true, false><<<nl, DFFT_T, sm, s>>>(src, dst, z.M, nl, p->dft_theta);
+      go(dfft_lines_k<1, true, false, DFFT_T_WIDE>, dfft_lines_k<1, true, false, DFFT_T_ODD>);
     else
-      dfft_lines_k<1, false, false><<<nl, DFFT_T, sm, s>>>(src, dst, z.M, nl, p->dft_theta);
+      go(dfft_lines_k<1, false, false, DFFT_T_WIDE>, dfft_lines_k<1, false, false, DFFT_T_ODD>);
   }
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
@@ -577,12 +609,17 @@ int dfft_theta_exec(nusht_plan_t p, const void* src, void* dst, int sign, cudaSt
 int dfft_cols_synth(nusht_plan_t p, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const size_t sm = (size_t)z.n1 * sizeof(float4);
+  const DfftLen& f = p->dft_n1;
+  auto go = [&](auto kw, auto ko) {
+    if (wide(f))
+      kw<<<z.mmax + 1, DFFT_T_WIDE, sm, s>>>(p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f, p->deconv2f, f);
+    else
+      ko<<<z.mmax + 1, DFFT_T_ODD, sm, s>>>(p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f, p->deconv2f, f);
+  };
   if (p->dfft_theta)
-    dfft_cols_synth_k<true><<<z.mmax + 1, DFFT_T, sm, s>>>(p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f,
-                                                           p->deconv2f, p->dft_n1);
+    go(dfft_cols_synth_k<true, DFFT_T_WIDE>, dfft_cols_synth_k<true, DFFT_T_ODD>);
   else
-    dfft_cols_synth_k<false><<<z.mmax + 1, DFFT_T, sm, s>>>(p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f,
-                                                            p->deconv2f, p->dft_n1);
+    go(dfft_cols_synth_k<false, DFFT_T_WIDE>, dfft_cols_synth_k<false, DFFT_T_ODD>);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
@@ -590,8 +627,14 @@ int dfft_cols_synth(nusht_plan_t p, cudaStream_t s) {
 int dfft_rows_c2r(nusht_plan_t p, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const int64_t stride = 2 * (z.n2 / 2 + 1);
-  dfft_rows_c2r_k<<<(z.n1 + 1) / 2, DFFT_T, (size_t)z.n2 * sizeof(float4), s>>>(
-      (const float4*)p->tcols, (double*)p->fine, stride, z.n1, z.mmax, p->dft_n2);
+  const size_t sm = (size_t)z.n2 * sizeof(float4);
+  const DfftLen& f = p->dft_n2;
+  if (wide(f))
+    dfft_rows_c2r_k<DFFT_T_WIDE><<<(z.n1 + 1) / 2, DFFT_T_WIDE, sm, s>>>((const float4*)p->tcols, (double*)p->fine,
+                                                                        stride, z.n1, z.mmax, f);
+  else
+    dfft_rows_c2r_k<DFFT_T_ODD><<<(z.n1 + 1) / 2, DFFT_T_ODD, sm, s>>>((const float4*)p->tcols, (double*)p->fine,
+                                                                      stride, z.n1, z.mmax, f);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
@@ -599,8 +642,14 @@ int dfft_rows_c2r(nusht_plan_t p, cudaStream_t s) {
 int dfft_rows_r2c(nusht_plan_t p, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const int64_t stride = 2 * (z.n2 / 2 + 1);
-  dfft_rows_r2c_k<<<(z.n1 + 1) / 2, DFFT_T, (size_t)z.n2 * sizeof(float4), s>>>(
-      (const double*)p->fine, (float4*)p->tcols, stride, z.n1, z.mmax, p->dft_n2);
+  const size_t sm = (size_t)z.n2 * sizeof(float4);
+  const DfftLen& f = p->dft_n2;
+  if (wide(f))
+    dfft_rows_r2c_k<DFFT_T_WIDE><<<(z.n1 + 1) / 2, DFFT_T_WIDE, sm, s>>>((const double*)p->fine, (float4*)p->tcols,
+                                                                        stride, z.n1, z.mmax, f);
+  else
+    dfft_rows_r2c_k<DFFT_T_ODD><<<(z.n1 + 1) / 2, DFFT_T_ODD, sm, s>>>((const double*)p->fine, (float4*)p->tcols,
+                                                                      stride, z.n1, z.mmax, f);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
@@ -608,12 +657,19 @@ int dfft_rows_r2c(nusht_plan_t p, cudaStream_t s) {
 int dfft_cols_adjoint(nusht_plan_t p, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const size_t sm = (size_t)z.n1 * sizeof(float4);
+  const DfftLen& f = p->dft_n1;
+  auto go = [&](auto kw, auto ko) {
+    if (wide(f))
+      kw<<<z.mmax + 1, DFFT_T_WIDE, sm, s>>>((const float4*)p->tcols, p->Ghat, z.lmax, z.M, p->deconv1f,
+                                             p->deconv2f, f);
+    else
+      ko<<<z.mmax + 1, DFFT_T_ODD, sm, s>>>((const float4*)p->tcols, p->Ghat, z.lmax, z.M, p->deconv1f,
+                                            p->deconv2f, f);
+  };
   if (p->dfft_theta)
-    dfft_cols_adj_k<true><<<z.mmax + 1, DFFT_T, sm, s>>>((const float4*)p->tcols, p->Ghat, z.lmax, z.M, p->deconv1f,
-                                                         p->deconv2f, p->dft_n1);
+    go(dfft_cols_adj_k<true, DFFT_T_WIDE>, dfft_cols_adj_k<true, DFFT_T_ODD>);
   else
-    dfft_cols_adj_k<false><<<z.mmax + 1, DFFT_T, sm, s>>>((const float4*)p->tcols, p->Ghat, z.lmax, z.M,
-                                                          p->deconv1f, p->deconv2f, p->dft_n1);
+    go(dfft_cols_adj_k<false, DFFT_T_WIDE>, dfft_cols_adj_k<false, DFFT_T_ODD>);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
