@@ -240,6 +240,7 @@ def main():
                     help="accuracy / speed sweep over eps x sigma on the lmax 1023 deflected grid (one JSON line)")
     ap.add_argument("--no-fast", action="store_true",
                     help="skip the opt-in double-float recurrence (fast_recurrence=1) runs")
+    ap.add_argument("--no-pointing", action="store_true", help="skip the lensing pointing measurement")
     ap.add_argument("--only-batch", action="store_true", help="run only the 64-transform batched measurement")
     ap.add_argument("--batch-n", type=int, default=64, help="transforms in the batched workload")
     ap.add_argument("--batch-lmax", type=int, default=2047, help="largest lmax of the batched workload")
@@ -387,6 +388,8 @@ def main():
         del ad, y, fmap, calm
         torch.cuda.empty_cache()
 
+    pointing = None if args.no_pointing else run_pointing(torch, nu, args, dist, L)
+
     batch = None
     if not args.no_batch and args.workload == WORKLOAD:
         batch = run_batch64(torch, nu, args, dist, rank)
@@ -466,6 +469,8 @@ def main():
                          "legendre_ms": [r["stages"]["synth"]["legendre"], r["stages"]["adjoint"]["legendre"]],
                          "what": "opts.fast_recurrence=1 (opt-in): the P_lm recurrence in double-float on the FP32 "
                                  "pipe instead of FP64"}
+    if pointing is not None:
+        line["pointing"] = pointing
     if batch is not None:
         line["batch64"] = batch
     if cpu is not None:
@@ -473,6 +478,40 @@ def main():
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_pointing(torch, nu, args, dist, L):
+    """CMB lensing pointing (App. C) on the undeflected Gauss-Legendre grid of
+    the workload's lmax, for a synthetic potential of 2.5 arcmin rms
+    deflection: milliseconds per call (synthesis of the potential to the fine
+    grid, derivative-of-kernel interpolation and the deflection per point),
+    FP64 at eps 1e-10."""
+    pts = W.gl_ring_grid(L + 1, 2 * L + 1)
+    phi = W.phi_lensing(L, seed=7)
+    dpts = torch.from_numpy(pts).cuda()
+    plan = nu.Plan(L, dpts, eps=EPS["fp64"], precision="fp64")
+    ph = torch.from_numpy(phi).cuda()
+    out = torch.empty((pts.shape[0], 2), dtype=torch.float64, device="cuda")
+
+    def step():
+        plan.pointing(ph, out=out)
+
+    ms = max_over_ranks(dist, time_steps(torch, step, args.steps, args.warmup, dist))
+    # angle between each sampled point and its deflected position
+    sub = pts[::997]
+    o = out[::997].cpu().numpy()
+
+    def unit(p):
+        return np.stack([np.sin(p[:, 0]) * np.cos(p[:, 1]), np.sin(p[:, 0]) * np.sin(p[:, 1]), np.cos(p[:, 0])], 1)
+
+    moved = np.arccos(np.clip(np.sum(unit(sub) * unit(o), 1), -1.0, 1.0))
+    plan.close()
+    del dpts, ph, out
+    torch.cuda.empty_cache()
+    return {"ms": ms, "lmax": L, "npts": int(pts.shape[0]),
+            "workload": "undeflected GL grid %dx%d, lensing potential C_l ~ [l(l+1)]^-1 (1+l/60)^-3, "
+                        "2.5 arcmin rms deflection (seed 7)" % (L + 1, 2 * L + 1),
+            "rms_deflection_arcmin": float(np.sqrt(np.mean(moved**2)) * 180 * 60 / np.pi)}
 
 
 def run_sweep(torch, nu, args):

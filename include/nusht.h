@@ -39,7 +39,7 @@
  * Memory and streams.  Every d_* pointer is DEVICE memory owned by the caller
  * and must stay valid for the duration of the call's stream work.  A plan owns
  * all of its workspace, allocated in nusht_plan; the execute calls
- * (nusht_synth, nusht_adjoint, nusht_synth_grad) allocate nothing, copy
+ * (nusht_synth, nusht_adjoint, nusht_synth_grad, nusht_pointing) allocate nothing, copy
  * nothing to or from the host and do not synchronise: they enqueue kernels and
  * cuFFT work on `stream` (NULL = the legacy default stream) and return.  A plan
  * may be used by one stream at a time.  Plans are bound to the device that was
@@ -194,6 +194,25 @@ NUSHT_API int nusht_adjoint(nusht_plan_t p, const void* d_map, void* d_alm, nush
  * Either output pointer may be NULL.  Asynchronous; allocates nothing.
  */
 NUSHT_API int nusht_synth_grad(nusht_plan_t p, const void* d_alm, void* d_dtheta, void* d_dphi, nusht_stream_t stream);
+
+/*
+ * nusht_pointing -- CMB lensing pointing (App. C): the deflected position of
+ * every point of the plan for the lensing potential Phi.
+ *   d_philm  the potential's coefficients in the plan's a_lm layout and
+ *            precision (packed m-major, complex128 for NUSHT_FP64, complex64
+ *            for NUSHT_MIXED; real field, Im(Phi_l0) ignored)
+ *   d_ptg    device double[2 * npts], caller's point order:
+ *            d_ptg[2i] = theta'_i in [0, pi], d_ptg[2i + 1] = phi'_i in [0, 2 pi)
+ * The gradient alpha_theta + i alpha_phi = (d/dtheta + (i / sin theta) d/dphi) Phi
+ * (Eq. spin1deriv) is interpolated at each point with the derivative of the ES
+ * kernel (as in nusht_synth_grad), and the point is moved along the geodesic
+ * that starts in that direction by the angle alpha = |alpha|:
+ * n' = cos(alpha) n + sin(alpha)/alpha (alpha_theta e_theta + alpha_phi e_phi)
+ * (Eq. pointing), in double.  A point with sin(theta) = 0 takes alpha_phi = 0.
+ * Plans made by nusht_plan only (NUSHT_EUNSUPPORTED otherwise).
+ * Asynchronous; allocates nothing; overwrites the plan's work buffers.
+ */
+NUSHT_API int nusht_pointing(nusht_plan_t p, const void* d_philm, double* d_ptg, nusht_stream_t stream);
 
 /*
  * nusht_adjoint_direct_noalloc -- type 1 transform (the adjoint, same result

@@ -61,6 +61,7 @@ def _load():
         lib.oracle_ring_sums.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp, dp]
         lib.oracle_adjoint_m.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, dp, ctypes.c_int, ip, dp]
         lib.oracle_synth_grad.argtypes = [ctypes.c_int, ctypes.c_int, dp, i64, dp, dp, dp]
+        lib.oracle_pointing.argtypes = [ctypes.c_int, ctypes.c_int, dp, i64, dp, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
         return lib
@@ -161,6 +162,19 @@ def synth_grad(alm: np.ndarray, pts: np.ndarray, lmax: int, mmax: int | None = N
     dph = np.empty(p.shape[0], dtype=np.float64)
     _load().oracle_synth_grad(lmax, mmax, _dp(a), p.shape[0], _dp(p), _dp(dth), _dp(dph))
     return dth, dph
+
+
+def pointing(philm: np.ndarray, pts: np.ndarray, lmax: int, mmax: int | None = None) -> np.ndarray:
+    """CMB lensing pointing (App. C, Eq. pointing and Eq. spin1deriv): the
+    deflected (theta', phi') of every point for the lensing potential philm
+    (packed real-field coefficients); shape (npts, 2), theta' in [0, pi],
+    phi' in [0, 2 pi)."""
+    mmax = lmax if mmax is None else mmax
+    a = _alm_pairs(philm, lmax, mmax)
+    p = _pts(pts)
+    out = np.empty((p.shape[0], 2), dtype=np.float64)
+    _load().oracle_pointing(lmax, mmax, _dp(a), p.shape[0], _dp(p), _dp(out))
+    return out
 
 
 def alm_dot(c: np.ndarray, a: np.ndarray, lmax: int, mmax: int | None = None) -> float:

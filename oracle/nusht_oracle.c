@@ -386,6 +386,46 @@ void oracle_synth_grad(int L, int mmax, const double* alm, int64_t npts, const d
   }
 }
 
+/*
+ * CMB lensing pointing (App. C): the deflected position of each point.
+ *   alpha_theta + i alpha_phi = (d/dtheta + (i / sin theta) d/dphi) Phi    (Eq. spin1deriv)
+ *   n' = cos(alpha) n + (sin(alpha) / alpha) (alpha_theta e_theta + alpha_phi e_phi),
+ *   alpha = sqrt(alpha_theta^2 + alpha_phi^2)                             (Eq. pointing)
+ * with n = (sin t cos p, sin t sin p, cos t), e_theta = (cos t cos p, cos t sin p,
+ * -sin t), e_phi = (-sin p, cos p, 0).  The derivatives of the potential Phi
+ * (real field, packed coefficients philm) are the analytic ones of
+ * oracle_synth_grad.  At a point with sin(theta) = 0 alpha_phi is taken as 0.
+ * Output: out[2i] = theta' in [0, pi], out[2i + 1] = phi' in [0, 2 pi).
+ */
+void oracle_pointing(int L, int mmax, const double* philm, int64_t npts, const double* pts, double* out) {
+  double* dth = (double*)malloc(sizeof(double) * (size_t)(npts > 0 ? npts : 1));
+  double* dph = (double*)malloc(sizeof(double) * (size_t)(npts > 0 ? npts : 1));
+  oracle_synth_grad(L, mmax, philm, npts, pts, dth, dph);
+  const double twopi = 2.0 * M_PI;
+  for (int64_t i = 0; i < npts; ++i) {
+    const double t = pts[2 * i], ph = pts[2 * i + 1];
+    const double st = sin(t), ct = cos(t), sp = sin(ph), cp = cos(ph);
+    const double n[3] = {st * cp, st * sp, ct};
+    const double et[3] = {ct * cp, ct * sp, -st};
+    const double ep[3] = {-sp, cp, 0.0};
+    const double at = dth[i];
+    const double ap = (st != 0.0) ? dph[i] / st : 0.0;
+    const double a = sqrt(at * at + ap * ap);
+    const double sinc = (a > 0.0) ? sin(a) / a : 1.0;
+    const double ca = cos(a);
+    double q[3];
+    for (int k = 0; k < 3; ++k) q[k] = ca * n[k] + sinc * (at * et[k] + ap * ep[k]);
+    const double tp = atan2(sqrt(q[0] * q[0] + q[1] * q[1]), q[2]);
+    double pp = atan2(q[1], q[0]);
+    if (pp < 0.0) pp += twopi;
+    if (pp >= twopi) pp -= twopi;
+    out[2 * i] = tp;
+    out[2 * i + 1] = pp;
+  }
+  free(dth);
+  free(dph);
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

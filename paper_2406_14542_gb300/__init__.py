@@ -27,7 +27,7 @@ EXPORTS = ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_
            "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_good_size", "nusht_stage_times",
            "nusht_strerror", "nusht_last_error", "nusht_version", "nusht_adjoint_direct_noalloc",
            "nusht_plan_many", "nusht_synth_many", "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info",
-           "nusht_plan_bin", "nusht_batch_status", "nusht_batch_path")
+           "nusht_plan_bin", "nusht_batch_status", "nusht_batch_path", "nusht_pointing")
 
 
 class NushtError(RuntimeError):
@@ -76,6 +76,7 @@ def load(path: str | None = None):
         lib.nusht_synth.argtypes = [vp, vp, vp, vp]
         lib.nusht_adjoint.argtypes = [vp, vp, vp, vp]
         lib.nusht_synth_grad.argtypes = [vp, vp, vp, vp, vp]
+        lib.nusht_pointing.argtypes = [vp, vp, vp, vp]
         lib.nusht_destroy.argtypes = [vp]
         lib.nusht_info.argtypes = [vp, ctypes.POINTER(Sizes)]
         lib.nusht_plan_sizes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -104,7 +105,7 @@ def load(path: str | None = None):
                      "nusht_destroy", "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_stage_times",
                      "nusht_adjoint_direct_noalloc", "nusht_plan_many", "nusht_synth_many",
                      "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info", "nusht_plan_bin",
-                     "nusht_batch_status", "nusht_batch_path"):
+                     "nusht_batch_status", "nusht_batch_path", "nusht_pointing"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -362,6 +363,21 @@ class Plan:
                                          ctypes.c_void_p(dth.data_ptr()), ctypes.c_void_p(dph.data_ptr()),
                                          _stream_ptr(stream)), "nusht_synth_grad")
         return dth, dph
+
+    def pointing(self, philm, out=None, stream=None):
+        """CMB lensing pointing (App. C): the deflected (theta', phi') of every
+        point for the lensing potential ``philm`` (the plan's a_lm layout and
+        precision); float64 tensor of shape (npts, 2), theta' in [0, pi],
+        phi' in [0, 2 pi), in the order of the plan's points."""
+        import torch
+
+        philm = self._alm(philm)
+        ptg = out if out is not None else torch.empty((self.npts, 2), dtype=torch.float64, device=self.device)
+        if ptg.dtype != torch.float64 or tuple(ptg.shape) != (self.npts, 2) or not ptg.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor of shape (npts, 2)")
+        _check(self.lib.nusht_pointing(self.handle, ctypes.c_void_p(philm.data_ptr()),
+                                       ctypes.c_void_p(ptg.data_ptr()), _stream_ptr(stream)), "nusht_pointing")
+        return ptg
 
     def stage_times(self) -> dict:
         import numpy as np

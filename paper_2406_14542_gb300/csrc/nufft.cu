@@ -225,7 +225,37 @@ __global__ void deconv_trunc_k(const typename V2<T>::t* __restrict__ H, typename
 }
 
 // ---------------------------------------------------------------------------
-// interpolation (type 2): one thread per sorted point
+// CMB lensing pointing (App. C): the point (theta, phi) moved along the
+// geodesic that starts in the direction of the potential's gradient, by its
+// length (Eq. pointing), with alpha_theta = dPhi/dtheta and
+// alpha_phi = dPhi/dphi / sin(theta) (Eq. spin1deriv).  Evaluated in the
+// frame turned by phi about the z axis, where n = (sin t, 0, cos t),
+// e_theta = (cos t, 0, -sin t), e_phi = (0, 1, 0).  Writes theta' in [0, pi]
+// and phi' in [0, 2 pi).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void deflect(double th, double ph, double gth, double gph, double* __restrict__ o) {
+  double st, ct;
+  sincos(th, &st, &ct);
+  const double at = gth, ap = st != 0.0 ? gph / st : 0.0;
+  const double a = sqrt(at * at + ap * ap);
+  double sa, ca;
+  sincos(a, &sa, &ca);
+  const double sinc = a > 0.0 ? sa / a : 1.0;
+  const double x = ca * st + sinc * at * ct;
+  const double y = sinc * ap;
+  const double z = ca * ct - sinc * at * st;
+  const double twopi = 6.283185307179586476925286766559;
+  double pp = ph + atan2(y, x);
+  pp -= twopi * floor(pp * (1.0 / twopi));
+  if (pp >= twopi || pp < 0.0) pp = 0.0;
+  o[0] = atan2(sqrt(x * x + y * y), z);
+  o[1] = pp;
+}
+
+// ---------------------------------------------------------------------------
+// interpolation (type 2): one thread per sorted point; with GRAD the
+// derivatives of the kernel give d/dtheta and d/dphi, written out or, with
+// ptg, turned into the deflected position (pointing)
 // ---------------------------------------------------------------------------
 template <typename T, bool GRAD>
 __global__ void __launch_bounds__(128) interp_k(const T* __restrict__ grid, int64_t stride, int n1, int n2, int w,
@@ -233,7 +263,7 @@ __global__ void __launch_bounds__(128) interp_k(const T* __restrict__ grid, int6
                                                 const double* __restrict__ psi, const float* __restrict__ offf,
                                                 const double* __restrict__ xy, const int* __restrict__ perm,
                                                 int64_t npts, T* __restrict__ out, T* __restrict__ dth,
-                                                T* __restrict__ dph) {
+                                                T* __restrict__ dph, double* __restrict__ ptg) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= npts) return;
   const int i1 = cell[2 * s], i2 = cell[2 * s + 1];
@@ -322,6 +352,10 @@ __global__ void __launch_bounds__(128) interp_k(const T* __restrict__ grid, int6
     // d/dx psi((x - x_j)/alpha) = psi'(z) / alpha, alpha = w pi / n
     const T a1 = (T)((double)n1 / (w * 3.14159265358979323846));
     const T a2 = (T)((double)n2 / (w * 3.14159265358979323846));
+    if (ptg) {
+      deflect(xy[2 * s], xy[2 * s + 1], (double)(g1 * a1), (double)(g2 * a2), ptg + 2 * (int64_t)i);
+      return;
+    }
     if (dth) dth[i] = g1 * a1;
     if (dph) dph[i] = g2 * a2;
   }
@@ -935,7 +969,7 @@ int interp(nusht_plan_t p, void* d_map, cudaStream_t s) {
   } else if (p->precision == NUSHT_FP64)
     interp_k<double, false><<<nb, tb, 0, s>>>((const double*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
                                               p->pts.cell, p->pts.psi, nullptr, nullptr, p->pts.perm, n,
-                                              (double*)d_map, nullptr, nullptr);
+                                              (double*)d_map, nullptr, nullptr, nullptr);
   else
     NUSHT_W_DISPATCH(z.w, launch_interp_f, nb, s, (const float*)p->fine, stride, z.n1, z.n2, (float)z.beta,
                      p->pts.cell, p->pts.off, p->pts.perm, n, (float*)d_map);
@@ -953,11 +987,30 @@ int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, cudaStream_t s) {
   if (p->precision == NUSHT_FP64)
     interp_k<double, true><<<nb, tb, 0, s>>>((const double*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
                                              p->pts.cell, nullptr, nullptr, p->pts.xy, p->pts.perm, n, nullptr,
-                                             (double*)d_dth, (double*)d_dph);
+                                             (double*)d_dth, (double*)d_dph, nullptr);
   else
     interp_k<float, true><<<nb, tb, 0, s>>>((const float*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
                                             p->pts.cell, nullptr, nullptr, p->pts.xy, p->pts.perm, n, nullptr,
-                                            (float*)d_dth, (float*)d_dph);
+                                            (float*)d_dth, (float*)d_dph, nullptr);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int interp_pointing(nusht_plan_t p, double* d_ptg, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  const int64_t n = p->pts.npts;
+  if (n == 0) return NUSHT_OK;
+  const int64_t stride = 2 * (z.n2 / 2 + 1);
+  const int tb = 128;
+  const int nb = (int)((n + tb - 1) / tb);
+  if (p->precision == NUSHT_FP64)
+    interp_k<double, true><<<nb, tb, 0, s>>>((const double*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
+                                             p->pts.cell, nullptr, nullptr, p->pts.xy, p->pts.perm, n, nullptr,
+                                             nullptr, nullptr, d_ptg);
+  else
+    interp_k<float, true><<<nb, tb, 0, s>>>((const float*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
+                                            p->pts.cell, nullptr, nullptr, p->pts.xy, p->pts.perm, n, nullptr,
+                                            nullptr, nullptr, d_ptg);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }

@@ -208,6 +208,7 @@ int deconv_pad(nusht_plan_t p, cudaStream_t s);
 int deconv_trunc(nusht_plan_t p, cudaStream_t s);
 int interp(nusht_plan_t p, void* d_map, cudaStream_t s);
 int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, cudaStream_t s);
+int interp_pointing(nusht_plan_t p, double* d_ptg, cudaStream_t s);
 int spread(nusht_plan_t p, const void* d_map, cudaStream_t s);
 int spread_smem_optin();
 

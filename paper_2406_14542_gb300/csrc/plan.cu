@@ -555,6 +555,21 @@ int nusht_synth_grad(nusht_plan_t p, const void* d_alm, void* d_dtheta, void* d_
   return NUSHT_OK;
 }
 
+int nusht_pointing(nusht_plan_t p, const void* d_philm, double* d_ptg, nusht_stream_t stream) {
+  if (!p) return set_error(NUSHT_EINVAL, "plan is NULL");
+  if (!d_philm || (!d_ptg && p->pts.npts > 0)) return set_error(NUSHT_EINVAL, "null potential or pointing pointer");
+  if (!p->has_legendre || !p->has_nufft) return set_error(NUSHT_EUNSUPPORTED, "pointing needs a standalone plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  // the potential's synthesis up to the fine grid, then the derivative-of-kernel
+  // interpolation with the deflection applied per point
+  NUSHT_TRY(legendre_synth(p, d_philm, s));
+  NUSHT_TRY(theta_fft(p, p->G, p->Ghat, -1, s));
+  NUSHT_TRY(deconv_pad(p, s));
+  NUSHT_TRY(fine_fft_c2r(p, s));
+  NUSHT_TRY(interp_pointing(p, d_ptg, s));
+  return NUSHT_OK;
+}
+
 int nusht_destroy(nusht_plan_t p) {
   plan_free(p);
   return NUSHT_OK;

@@ -341,3 +341,73 @@ def test_eps_eff_definition():
     t = np.array([3.0, 4.0])
     assert oracle.eps_eff(t, t) == 0.0
     assert abs(oracle.eps_eff(t, np.array([3.0, 3.0])) - 0.2) < 1e-15
+
+
+# --- CMB lensing pointing (App. C, Eq. pointing and Eq. spin1deriv) -------
+
+
+def _unit(th, ph):
+    return np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], -1)
+
+
+def test_pointing_y10_is_a_meridional_shift():
+    """Phi = a10 Y_10 = a10 sqrt(3/4pi) cos(theta): the gradient points along
+    e_theta only, so every point moves along its meridian by
+    alpha_theta = -a10 sqrt(3/4pi) sin(theta): theta' = theta + alpha_theta, phi' = phi."""
+    L = 3
+    a10 = 2e-3
+    phi = np.zeros(oracle.nalm(L), dtype=np.complex128)
+    phi[oracle.lm_index(L, 1, 0)] = a10
+    pts = W.points_uniform(200, seed=91)
+    pts = np.concatenate([pts, [[1e-3, 0.5], [math.pi - 1e-3, 4.0], [math.pi / 2, 6.2]]])
+    out = oracle.pointing(phi, pts, L)
+    th_ref = pts[:, 0] - a10 * math.sqrt(3.0 / FOURPI) * np.sin(pts[:, 0])
+    np.testing.assert_allclose(out[:, 0], th_ref, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(out[:, 1], np.mod(pts[:, 1], 2 * math.pi), rtol=0, atol=1e-14)
+
+
+def test_pointing_zero_potential_is_identity():
+    L = 5
+    pts = W.points_uniform(50, seed=92)
+    pts[:, 1] += 7.0  # any real phi: the output is reduced to [0, 2 pi)
+    out = oracle.pointing(np.zeros(oracle.nalm(L), dtype=np.complex128), pts, L)
+    np.testing.assert_allclose(out[:, 0], pts[:, 0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(out[:, 1], np.mod(pts[:, 1], 2 * math.pi), rtol=0, atol=1e-14)
+
+
+def test_pointing_moves_along_the_geodesic_of_the_gradient():
+    """n' lies at angular distance alpha = |grad Phi| from n, in the direction
+    of alpha_theta e_theta + alpha_phi e_phi (the geodesic the gradient starts)."""
+    L = 12
+    phi = W.alm_gaussian(L, seed=93) * 3e-3
+    pts = W.points_uniform(300, seed=94)
+    out = oracle.pointing(phi, pts, L)
+    dth, dph = oracle.synth_grad(phi, pts, L)
+    th, ph = pts[:, 0], pts[:, 1]
+    at, ap = dth, dph / np.sin(th)
+    alpha = np.hypot(at, ap)
+    n, n2 = _unit(th, ph), _unit(out[:, 0], out[:, 1])
+    dist = np.arctan2(np.linalg.norm(np.cross(n, n2), axis=1), np.sum(n * n2, axis=1))
+    np.testing.assert_allclose(dist, alpha, rtol=1e-12, atol=1e-16)
+    et = np.stack([np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)], -1)
+    ep = np.stack([-np.sin(ph), np.cos(ph), np.zeros_like(ph)], -1)
+    d = (at[:, None] * et + ap[:, None] * ep) / alpha[:, None]
+    t = n2 - np.sum(n * n2, axis=1)[:, None] * n
+    t /= np.linalg.norm(t, axis=1)[:, None]
+    np.testing.assert_allclose(t, d, rtol=0, atol=1e-9)
+
+
+def test_pointing_rotation_equivariance():
+    """Rotating the potential about the z axis by phi0 (c_lm -> c_lm e^{-i m phi0})
+    rotates the deflected positions by the same angle."""
+    L = 10
+    phi = W.alm_gaussian(L, seed=95) * 2e-3
+    ms = np.concatenate([np.full(L + 1 - m, m) for m in range(L + 1)])
+    phi0 = 0.7
+    rot = phi * np.exp(-1j * ms * phi0)
+    pts = W.points_uniform(100, seed=96)
+    out = oracle.pointing(phi, pts, L)
+    out_r = oracle.pointing(rot, pts + np.array([0.0, phi0]), L)
+    np.testing.assert_allclose(out_r[:, 0], out[:, 0], rtol=0, atol=1e-14)
+    dphi = np.mod(out_r[:, 1] - out[:, 1] - phi0 + math.pi, 2 * math.pi) - math.pi
+    np.testing.assert_allclose(dphi, 0.0, rtol=0, atol=1e-13)

@@ -65,6 +65,25 @@ def alm_gaussian(lmax: int, seed: int, mmax: int | None = None, spectrum: str | 
     return a.astype(dtype)
 
 
+def phi_lensing(lmax: int, seed: int, rms_arcmin: float = 2.5, dtype=np.complex128) -> np.ndarray:
+    """Packed m-major coefficients of a synthetic lensing potential Phi:
+    Gaussian with C_l proportional to [l(l+1)]^-1 (1 + l/60)^-3 for l >= 2
+    (zero for l < 2), scaled so that the rms deflection |grad Phi| over the
+    sphere is rms_arcmin: sum_l (2l+1) l(l+1) C_l / (4 pi) = rms^2.  The
+    stand-in for the paper's CMB lensing simulations (Sec. 4, App. C)."""
+    ls = np.arange(lmax + 1, dtype=np.float64)
+    cl = np.zeros(lmax + 1)
+    hi = ls >= 2
+    cl[hi] = 1.0 / (ls[hi] * (ls[hi] + 1.0)) / (1.0 + ls[hi] / 60.0) ** 3
+    var = np.sum((2.0 * ls + 1.0) * ls * (ls + 1.0) * cl) / (4.0 * np.pi)
+    rms = rms_arcmin * np.pi / (180.0 * 60.0)
+    if var > 0:
+        cl *= rms**2 / var
+    a = alm_gaussian(lmax, seed)
+    ells = np.concatenate([np.arange(m, lmax + 1) for m in range(lmax + 1)])
+    return (a * np.sqrt(cl[ells])).astype(dtype)
+
+
 def points_uniform(n: int, seed: int) -> np.ndarray:
     """n points uniform on the sphere: theta = arccos U[-1,1], phi ~ U[0, 2 pi)."""
     rng = np.random.default_rng(seed)
