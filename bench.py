@@ -241,6 +241,7 @@ def main():
     ap.add_argument("--no-fast", action="store_true",
                     help="skip the opt-in double-float recurrence (fast_recurrence=1) runs")
     ap.add_argument("--no-pointing", action="store_true", help="skip the lensing pointing measurement")
+    ap.add_argument("--no-autograd", action="store_true", help="skip the differentiable-transform measurement")
     ap.add_argument("--only-batch", action="store_true", help="run only the 64-transform batched measurement")
     ap.add_argument("--batch-n", type=int, default=64, help="transforms in the batched workload")
     ap.add_argument("--batch-lmax", type=int, default=2047, help="largest lmax of the batched workload")
@@ -389,6 +390,7 @@ def main():
         torch.cuda.empty_cache()
 
     pointing = None if args.no_pointing else run_pointing(torch, nu, args, dist, L)
+    autograd = None if args.no_autograd or args.workload != WORKLOAD else run_autograd(torch, nu, args, dist)
 
     batch = None
     if not args.no_batch and args.workload == WORKLOAD:
@@ -471,6 +473,8 @@ def main():
                                  "pipe instead of FP64"}
     if pointing is not None:
         line["pointing"] = pointing
+    if autograd is not None:
+        line["autograd"] = autograd
     if batch is not None:
         line["batch64"] = batch
     if cpu is not None:
@@ -512,6 +516,33 @@ def run_pointing(torch, nu, args, dist, L):
             "workload": "undeflected GL grid %dx%d, lensing potential C_l ~ [l(l+1)]^-1 (1+l/60)^-3, "
                         "2.5 arcmin rms deflection (seed 7)" % (L + 1, 2 * L + 1),
             "rms_deflection_arcmin": float(np.sqrt(np.mean(moved**2)) * 180 * 60 / np.pi)}
+
+
+def run_autograd(torch, nu, args, dist):
+    """The differentiable transform (autograd) on the lmax 2047 deflected GL
+    grid (8,386,560 points), FP64 at eps 1e-10: one forward synthesis and the
+    backward pass of L = sum_i w_i f_i^2 (the adjoint for dL/da_lm, the
+    derivative-of-kernel interpolation for dL/d(theta, phi)), ms per step."""
+    L, a, pts = W.workload("gl2047")
+    n = pts.shape[0]
+    w = torch.from_numpy(np.random.default_rng(1).uniform(0, 1, n)).cuda()
+    dpts = torch.from_numpy(pts).cuda()
+    plan = nu.Plan(L, dpts, eps=EPS["fp64"], precision="fp64")
+    ad = torch.from_numpy(a).cuda()
+
+    def step():
+        alm = ad.detach().requires_grad_(True)
+        dp = dpts.detach().requires_grad_(True)
+        f = nu.nusht(alm, dp, plan)
+        (w * f * f).sum().backward()
+
+    ms = max_over_ranks(dist, time_steps(torch, step, args.steps, args.warmup, dist))
+    plan.close()
+    del dpts, ad, w
+    torch.cuda.empty_cache()
+    return {"ms": ms, "lmax": L, "npts": int(n), "precision": "fp64", "eps": EPS["fp64"],
+            "workload": "deflected GL grid 2048x4095, L = sum_i w_i f_i^2, w_i ~ U[0, 1) (seed 1)",
+            "what": "forward synthesis + backward (grad a_lm and grad (theta, phi))"}
 
 
 def run_sweep(torch, nu, args):

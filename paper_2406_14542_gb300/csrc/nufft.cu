@@ -496,6 +496,119 @@ __global__ void __launch_bounds__(IDF_THREADS) interp_df_k(const double* __restr
   }
 }
 
+// d psi / dz over psi for the ES kernel, -beta z / sqrt(1 - z^2), as a float
+// pair at z = (o - a) 2 / W (o: the point's offset from its first tap);
+// 0 where 1 - z^2 <= 0 (psi is 0 there)
+template <int W>
+__device__ __forceinline__ float2 es_dfac(float oh, float ol, int a, float2 beta) {
+  // 2 / W as a float pair (folded at compile time)
+  constexpr double cw = 2.0 / W;
+  constexpr float cwh = (float)cw;
+  constexpr float cwl = (float)(cw - (double)cwh);
+  // o - a (a is an exact small integer), then z = (o - a) 2 / W
+  float dh = 0.f, dl = 0.f;
+  df_add(dh, dl, oh, ol);
+  df_add(dh, dl, (float)-a, 0.f);
+  const float2 z = df_mul(make_float2(dh, dl), make_float2(cwh, cwl));
+  // r = 1 - z^2
+  const float2 zz = df_mul(z, z);
+  float rh = 1.0f, rl = 0.0f;
+  df_add(rh, rl, -zz.x, -zz.y);
+  if (!(rh > 0.0f)) return make_float2(0.0f, 0.0f);
+  // s = sqrt(r): one Newton correction of the float root
+  const float s0 = sqrtf(rh);
+  const float e = __fadd_rn(__fmaf_rn(-s0, s0, rh), rl);
+  float sh = s0, sl = __fdiv_rn(e, 2.0f * s0);
+  {
+    const float t = __fadd_rn(sh, sl);
+    sl = __fsub_rn(sl, __fsub_rn(t, sh));
+    sh = t;
+  }
+  // -beta z / s
+  const float2 n = df_mul(beta, z);
+  const float g0 = __fdiv_rn(n.x, sh);
+  const float pr = __fmul_rn(g0, sh);
+  const float pe = __fmaf_rn(g0, sh, -pr);
+  const float rm = __fadd_rn(__fsub_rn(__fsub_rn(n.x, pr), pe), __fsub_rn(n.y, __fmul_rn(g0, sl)));
+  const float g1 = __fdiv_rn(rm, sh);
+  const float gh = __fadd_rn(g0, g1);
+  return make_float2(-gh, -__fsub_rn(g1, __fsub_rn(gh, g0)));
+}
+
+// FP64-mode gradient interpolation on the double-float tile (the tile and
+// the kernel values as in interp_df_k):
+//   d f / d theta = (n1 / (W pi)) sum_a psi1'_a sum_b psi2_b u_ab,
+//   d f / d phi   = (n2 / (W pi)) sum_a psi1_a sum_b psi2'_b u_ab,
+// psi' = psi * es_dfac.  Writes the derivatives, or with ptg the deflected
+// position (pointing, App. C).
+template <int W>
+__global__ void __launch_bounds__(IDF_THREADS) interp_grad_df_k(const double* __restrict__ grid, int64_t stride,
+                                                                int n1, int n2, int nb2, int binsz,
+                                                                const int* __restrict__ sub,
+                                                                const int* __restrict__ cell,
+                                                                const float2* __restrict__ psi,
+                                                                const double* __restrict__ xy,
+                                                                const int* __restrict__ perm, float2 beta,
+                                                                double* __restrict__ dth, double* __restrict__ dph,
+                                                                double* __restrict__ ptg) {
+  extern __shared__ unsigned char smem_raw[];
+  float2* tile = reinterpret_cast<float2*>(smem_raw);
+  const int tw = binsz + W - 1;
+  const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
+  const int r0 = (bin / nb2) * binsz, c0 = (bin % nb2) * binsz;
+  for (int e = threadIdx.x; e < tw * tw; e += IDF_THREADS) {
+    const int r = e / tw, c = e - r * tw;
+    const int gr = (r0 + r) % n1, gc = (c0 + c) % n2;
+    float h, l;
+    df_split(grid[(int64_t)gr * stride + gc], h, l);
+    tile[e] = make_float2(h, l);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < cnt; q += IDF_THREADS) {
+    const int64_t s = (int64_t)start + q;
+    const int lr = cell[2 * s] - r0, lc = cell[2 * s + 1] - c0;
+    const float2* ps = psi + s * 2 * W;
+    int j1, j2;
+    double o1, o2;
+    tap(xy[2 * s], n1, W, j1, o1);
+    tap(xy[2 * s + 1], n2, W, j2, o2);
+    float o1h, o1l, o2h, o2l;
+    df_split(o1, o1h, o1l);
+    df_split(o2, o2h, o2l);
+    float2 p2[W], q2[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      p2[b] = ps[W + b];
+      q2[b] = df_mul(p2[b], es_dfac<W>(o2h, o2l, b, beta));
+    }
+    float th = 0.f, tl = 0.f, fh = 0.f, fl = 0.f;
+#pragma unroll 1
+    for (int a = 0; a < W; ++a) {
+      const float2* trow = tile + (lr + a) * tw + lc;
+      float ih = 0.f, il = 0.f, jh = 0.f, jl = 0.f;
+#pragma unroll
+      for (int b = 0; b < W; ++b) {
+        const float2 u = trow[b];
+        df_mac(ih, il, p2[b].x, p2[b].y, u.x, u.y);
+        df_mac(jh, jl, q2[b].x, q2[b].y, u.x, u.y);
+      }
+      const float2 p1 = ps[a];
+      const float2 q1 = df_mul(p1, es_dfac<W>(o1h, o1l, a, beta));
+      df_mac(th, tl, q1.x, q1.y, ih, il);
+      df_mac(fh, fl, p1.x, p1.y, jh, jl);
+    }
+    const double gth = df_value(th, tl) * ((double)n1 / (W * 3.14159265358979323846));
+    const double gph = df_value(fh, fl) * ((double)n2 / (W * 3.14159265358979323846));
+    const int i = perm[s];
+    if (ptg) {
+      deflect(xy[2 * s], xy[2 * s + 1], gth, gph, ptg + 2 * (int64_t)i);
+    } else {
+      if (dth) dth[i] = gth;
+      if (dph) dph[i] = gph;
+    }
+  }
+}
+
 template <int W>
 __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int64_t stride, int n1, int n2, int nb2,
                                                   int binsz, const int* __restrict__ sub,
@@ -614,6 +727,14 @@ void launch_interp_df(int nsub, size_t sm, cudaStream_t s, const double* grid, i
 }
 
 template <int W>
+void launch_interp_grad_df(int nsub, size_t sm, cudaStream_t s, const double* grid, int64_t stride, int n1, int n2,
+                           int nb2, int binsz, const int* sub, const int* cell, const float2* psi, const double* xy,
+                           const int* perm, float2 beta, double* dth, double* dph, double* ptg) {
+  interp_grad_df_k<W><<<nsub, IDF_THREADS, sm, s>>>(grid, stride, n1, n2, nb2, binsz, sub, cell, psi, xy, perm, beta,
+                                                    dth, dph, ptg);
+}
+
+template <int W>
 void launch_spread_df(int nsub, size_t sm, cudaStream_t s, double* grid, int64_t stride, int n1, int n2, int nb2,
                       int binsz, const int* sub, const int* cell, const float2* psi, const int* perm,
                       const double* f, float2* scratch) {
@@ -678,7 +799,8 @@ void optin_df(int* st) {
   const int mx = 84 * 84 * 8;
   if (cudaFuncSetAttribute(spread_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx + SUBMAX * 16) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(interp_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
+      cudaFuncSetAttribute(interp_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
+      cudaFuncSetAttribute(interp_grad_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
     *st = 1;
 }
 
@@ -977,10 +1099,27 @@ int interp(nusht_plan_t p, void* d_map, cudaStream_t s) {
   return NUSHT_OK;
 }
 
+// FP64 plans with the double-float NUFFT: derivatives (or the pointing) from
+// the bin tiles and the plan's kernel-value table
+static int interp_grad_df(nusht_plan_t p, double* d_dth, double* d_dph, double* d_ptg, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  const int64_t stride = 2 * (z.n2 / 2 + 1);
+  const int binsz = p->pts.bin > 0 ? p->pts.bin : 32;
+  const int tw = binsz + z.w - 1;
+  const float bh = (float)z.beta;
+  const float2 beta = make_float2(bh, (float)(z.beta - (double)bh));
+  NUSHT_W_DISPATCH(z.w, launch_interp_grad_df, p->pts.nsub, (size_t)tw * tw * 8, s, (const double*)p->fine, stride,
+                   z.n1, z.n2, p->pts.nbins2, binsz, p->pts.sub, p->pts.cell,
+                   reinterpret_cast<const float2*>(p->pts.psi), p->pts.xy, p->pts.perm, beta, d_dth, d_dph, d_ptg);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
 int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const int64_t n = p->pts.npts;
   if (n == 0) return NUSHT_OK;
+  if (nufft_df(p) && p->pts.nsub > 0) return interp_grad_df(p, (double*)d_dth, (double*)d_dph, nullptr, s);
   const int64_t stride = 2 * (z.n2 / 2 + 1);
   const int tb = 128;
   const int nb = (int)((n + tb - 1) / tb);
@@ -1000,6 +1139,7 @@ int interp_pointing(nusht_plan_t p, double* d_ptg, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const int64_t n = p->pts.npts;
   if (n == 0) return NUSHT_OK;
+  if (nufft_df(p) && p->pts.nsub > 0) return interp_grad_df(p, nullptr, nullptr, d_ptg, s);
   const int64_t stride = 2 * (z.n2 / 2 + 1);
   const int tb = 128;
   const int nb = (int)((n + tb - 1) / tb);

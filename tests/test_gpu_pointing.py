@@ -42,14 +42,17 @@ def chord_error(got, ref, pts):
     return float(np.linalg.norm(unit(got) - unit(ref)) / np.linalg.norm(unit(ref) - unit(pts)))
 
 
-@pytest.mark.parametrize("prec,eps,tol", [("fp64", 1e-10, 1e-8), ("mixed", 1e-5, 1e-4)])
-def test_pointing_against_oracle(env, prec, eps, tol):
+@pytest.mark.parametrize("prec,eps,tol,fc", [("fp64", 1e-10, 1e-8, False), ("fp64", 1e-10, 1e-8, True),
+                                             ("mixed", 1e-5, 1e-4, False)])
+def test_pointing_against_oracle(env, prec, eps, tol, fc):
+    """fc: fp64_contraction = 1, the FP64-instruction derivative interpolation
+    (kernel values evaluated on the fly) instead of the double-float one."""
     torch, nu = env
     L = 63
     pts = W.points_uniform(20000, seed=41)
     phi = W.phi_lensing(L, seed=42)
     cd = torch.complex128 if prec == "fp64" else torch.complex64
-    plan = nu.Plan(L, torch.from_numpy(pts).cuda(), eps=eps, precision=prec)
+    plan = nu.Plan(L, torch.from_numpy(pts).cuda(), eps=eps, precision=prec, fp64_contraction=fc)
     got = plan.pointing(torch.from_numpy(phi).to(cd).cuda()).cpu().numpy()
     ref = oracle.pointing(phi, pts, L)
     assert np.all((got[:, 0] >= 0) & (got[:, 0] <= math.pi))
