@@ -447,3 +447,29 @@ def test_fp64_fft_kernels(env, L, npts):
     lhs = float(np.dot(y, f))
     rhs = oracle.alm_dot(c, a, L)
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1e-300)
+
+
+def test_fp64_fft_kernels_theta_only(env):
+    """A fine grid longer than a shared-memory line (sigma = 4 at lmax 2047:
+    n = 16384 > 14336) takes cuFFT FP64 for the 2D transform while the theta
+    DFT (M = 4096) stays on the double-float kernel, which then hands the
+    theta spectrum over as double2: against cuFFT throughout and the oracle."""
+    torch, nu = env
+    L = 2047
+    pts = W.points_uniform(100000, seed=61)
+    a = W.alm_gaussian(L, seed=62, spectrum="inv_l1_sq")
+    dp = dev(torch, pts)
+    own = nu.Plan(L, dp, eps=1e-10, precision="fp64", sigma=4.0)
+    assert own.info()["n1"] > 14336
+    cuf = nu.Plan(L, dp, eps=1e-10, precision="fp64", sigma=4.0, fft_kernels=-1)
+    ad = dev(torch, a, torch.complex128)
+    f = own.synth(ad).cpu().numpy()
+    f0 = cuf.synth(ad).cpu().numpy()
+    assert np.linalg.norm(f - f0) <= 1e-12 * np.linalg.norm(f0)
+    y = np.random.default_rng(63).standard_normal(pts.shape[0])
+    yd = dev(torch, y)
+    c = own.adjoint(yd).cpu().numpy()
+    c0 = cuf.adjoint(yd).cpu().numpy()
+    assert np.linalg.norm(c - c0) <= 1e-12 * np.linalg.norm(c0)
+    sel = W.subset(pts.shape[0], 200, seed=64)
+    assert oracle.eps_eff(oracle.synth(a, pts[sel], L), f[sel]) <= TOL["fp64"]
