@@ -98,7 +98,8 @@ typedef struct {
                         cell sums the tiles covering it in a fixed order, instead of adding
                         halos with atomics (FP64 at lmax 4095: 2.4 GB of scratch).  0 = atomics
                         (rounding-level order effects).  Synthesis is always reproducible. */
-  int tune;          /* NUFFT autotuner: 0 = off (bin edge 32 cells); 1 = search at plan
+  int tune;          /* NUFFT autotuner: 0 = off (bin edge 16 cells for FP64 plans with kernel
+                        width <= 17 and fp64_contraction = 0, else 32); 1 = search at plan
                         time on the plan's own points (bin edge 16/32/64 and, when sigma = 0,
                         the up-sampling factor), caching the winners; 2 = the cached choices
                         for this device/size when present */
