@@ -96,7 +96,7 @@ typedef struct {
   int deterministic; /* 1 = bit-reproducible adjoint: each spreading subproblem writes its
                         tile (bin + halo) to a plan-owned scratch buffer and every fine-grid
                         cell sums the tiles covering it in a fixed order, instead of adding
-                        halos with atomics (FP64 at lmax 4095: 2.4 GB of scratch).  0 = atomics
+                        halos with atomics (FP64 at lmax 4095: 4.0 GB of scratch).  0 = atomics
                         (rounding-level order effects).  Synthesis is always reproducible. */
   int tune;          /* NUFFT autotuner: 0 = off (bin edge 16 cells for FP64 plans with kernel
                         width <= 17 and fp64_contraction = 0, else 32); 1 = search at plan
