@@ -126,3 +126,14 @@ def test_plan_without_gpu_reports_device_error(nu):
     rc = lib.nusht_plan(ctypes.byref(h), 8, 9, 0, None, 1e-8, 0, None, None)
     assert rc == nu.NUSHT_EINVAL
     assert lib.nusht_destroy(None) == 0
+
+
+def test_execute_calls_reject_null_plan(nu):
+    """Every execute entry point rejects a NULL plan with NUSHT_EINVAL before
+    any GPU work (host-side validation; no device needed)."""
+    lib = nu.load()
+    assert lib.nusht_synth(None, None, None, None) == nu.NUSHT_EINVAL
+    assert lib.nusht_adjoint(None, None, None, None) == nu.NUSHT_EINVAL
+    assert lib.nusht_synth_grad(None, None, None, None, None) == nu.NUSHT_EINVAL
+    assert lib.nusht_pointing(None, None, None, None) == nu.NUSHT_EINVAL
+    assert b"NULL" in lib.nusht_last_error()
