@@ -609,6 +609,10 @@ __global__ void __launch_bounds__(IDF_THREADS) interp_grad_df_k(const double* __
   }
 }
 
+// padded row stride of the double-float spreading tile: the least ts >= tw
+// with ts = W (mod 16)
+__host__ __device__ __forceinline__ int spread_df_stride(int tw, int W) { return tw + (((W - tw) % 16) + 16) % 16; }
+
 template <int W>
 __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int64_t stride, int n1, int n2, int nb2,
                                                   int binsz, const int* __restrict__ sub,
@@ -619,13 +623,17 @@ __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int
   constexpr int NR = (NC + 31) / 32;  // rounds of 32 cells per point
   extern __shared__ unsigned char smem_raw[];
   const int tw = binsz + W - 1;
+  // tile rows padded to a stride ts = W (mod 16): the W x W cells of a point,
+  // taken in lane order, then sit on consecutive banks (conflict-free 64-bit
+  // read and write, as if the patch were stored packed)
+  const int ts = spread_df_stride(tw, W);
   float2* tile = reinterpret_cast<float2*>(smem_raw);
-  int2* sp_cell = reinterpret_cast<int2*>(tile + tw * tw);    // [SUBMAX] local first taps
+  int2* sp_cell = reinterpret_cast<int2*>(tile + tw * ts);    // [SUBMAX] local first taps
   float2* sp_f = reinterpret_cast<float2*>(sp_cell + SUBMAX);  // [SUBMAX] values as float pairs
   const int lane = threadIdx.x;
   const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
   const int r0 = (bin / nb2) * binsz, c0 = (bin % nb2) * binsz;
-  for (int t = lane; t < tw * tw; t += 32) tile[t] = make_float2(0.f, 0.f);
+  for (int t = lane; t < tw * ts; t += 32) tile[t] = make_float2(0.f, 0.f);
   for (int q = lane; q < cnt; q += 32) {
     const int64_t s = (int64_t)start + q;
     sp_cell[q] = make_int2(cell[2 * s] - r0, cell[2 * s + 1] - c0);
@@ -641,7 +649,7 @@ __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int
     const int idx = lane + 32 * t;
     ca[t] = idx < NC ? idx / W : 0;
     cb[t] = idx < NC ? idx % W : 0;
-    co[t] = ca[t] * tw + cb[t];
+    co[t] = ca[t] * ts + cb[t];
   }
   // lane a < W holds psi1_a (k1, times f) and psi2_a (k2) of the current point
   float2 n1v = make_float2(0.f, 0.f), n2v = n1v;
@@ -658,7 +666,7 @@ __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int
     }
     const int2 lrc = sp_cell[q];
     if (lane < W) k1 = df_mul(k1, sp_f[q]);
-    float2* base = tile + lrc.x * tw + lrc.y;
+    float2* base = tile + lrc.x * ts + lrc.y;
     // a point's cells are distinct: read them all, update, write them all
     float2 c[NR];
 #pragma unroll
@@ -679,15 +687,16 @@ __global__ void __launch_bounds__(32) spread_df_k(double* __restrict__ grid, int
     __syncwarp();
   }
   __syncwarp();
-  if (scratch) {  // deterministic: the whole tile to this subproblem's slot
+  if (scratch) {  // deterministic: the whole tile (packed, tw x tw) to this subproblem's slot
     float2* dst = scratch + (size_t)blockIdx.x * tw * tw;
-    for (int t = lane; t < tw * tw; t += 32) dst[t] = tile[t];
+    for (int t = lane; t < tw * tw; t += 32) dst[t] = tile[(t / tw) * ts + t % tw];
     return;
   }
   for (int t = lane; t < tw * tw; t += 32) {
-    const float2 v = tile[t];
+    const int tr = t / tw, tc = t - tr * tw;
+    const float2 v = tile[tr * ts + tc];
     if (v.x != 0.f) {
-      int r = r0 + t / tw, c = c0 + t % tw;
+      int r = r0 + tr, c = c0 + tc;
       while (r >= n1) r -= n1;
       while (c >= n2) c -= n2;
       atomicAdd(grid + (int64_t)r * stride + c, df_value(v.x, v.y));
@@ -797,7 +806,8 @@ __global__ void grid_gather_k(T* __restrict__ grid, int64_t stride, int n1, int 
 template <int W>
 void optin_df(int* st) {
   const int mx = 84 * 84 * 8;
-  if (cudaFuncSetAttribute(spread_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx + SUBMAX * 16) !=
+  const int mxs = 84 * spread_df_stride(84, W) * 8;
+  if (cudaFuncSetAttribute(spread_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mxs + SUBMAX * 16) !=
           cudaSuccess ||
       cudaFuncSetAttribute(interp_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess ||
       cudaFuncSetAttribute(interp_grad_df_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
@@ -1166,7 +1176,8 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
   const int tw = binsz + z.w - 1;
   const size_t sm = (size_t)tw * tw * es;
   if (nufft_df(p)) {
-    NUSHT_W_DISPATCH(z.w, launch_spread_df, p->pts.nsub, sm + (size_t)SUBMAX * 16, s, (double*)p->fine, stride, z.n1,
+    const size_t smd = (size_t)tw * spread_df_stride(tw, z.w) * 8 + (size_t)SUBMAX * 16;
+    NUSHT_W_DISPATCH(z.w, launch_spread_df, p->pts.nsub, smd, s, (double*)p->fine, stride, z.n1,
                      z.n2, p->pts.nbins2, binsz, p->pts.sub, p->pts.cell,
                      reinterpret_cast<const float2*>(p->pts.psi), p->pts.perm, (const double*)d_map,
                      det ? (float2*)p->pts.tiles : nullptr);
