@@ -10,6 +10,16 @@ GB300 (sm_103a) the calls raise.  PyTorch provides device memory and streams.
     f = plan.synth(alm_cuda_complex128)          # type 2 (Eq. SHTbase)
     c = plan.adjoint(f)                          # type 1 (Eq. adjointSHTbase)
     f = nu.nusht(alm, pts, plan)                 # differentiable in alm and pts
+    ptg = grid_plan.pointing(phi_lm)             # CMB lensing pointing (App. C):
+                                                 # (theta', phi') per point, (N, 2)
+    batch = nu.BatchPlan(lmaxs, pts_list, eps=1e-5)   # many transforms of uneven lmax
+    maps = batch.synth(alm_list)                 # one CUDA graph per direction
+
+Options (keyword arguments of Plan): sigma, kernel_width, tune (autotuner),
+deterministic (bit-reproducible adjoint), legendre_table (plan-time
+recurrence in HBM), fast_recurrence (double-float recurrence, opt-in),
+fp64_contraction, fft_kernels (-1: cuFFT FP64 instead of the double-float
+FFT kernels), profile (per-stage times, Plan.stage_times()).
 """
 from __future__ import annotations
 
