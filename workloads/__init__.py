@@ -3,9 +3,12 @@ oracle legs and bench.py).
 
 This module holds input generation only: random coefficients, point clouds,
 Gauss-Legendre ring grids and a lensing-style deflection of those grids.  It
-contains none of the transform's arithmetic (no Legendre functions, no FFTs,
-no spreading kernels), so that the oracle and the CUDA library can both take
-their inputs from here without sharing any of the method.
+shares no code with the oracle or the CUDA library and neither of them
+imports it; both take their inputs from here.  The one piece of spherical
+harmonic arithmetic in it, ``phi_gradient_rings``, only places the deflected
+grid points (the gradient of the synthetic lensing potential on the grid's
+rings, a plain numpy recurrence); parity of the transform is checked on
+whatever points it produces.
 
 Workloads (Sec. 4, benchmark set-up; sizes and distributions as named in the
 build's configuration list):
@@ -22,11 +25,10 @@ build's configuration list):
   uniform points each.
 
 The paper's CMB simulations (Sec. 4, Fig. benchmark_setup) are not available;
-the deflection here stands in for them.  It is the tangential gradient of a
-random potential Phi(n) = sum_q A_q cos(k_q . n + phase_q) (a sum of random 3D
-plane waves restricted to the unit sphere, |k_q| ~ U[kmin, kmax]), rescaled
-so that the rms deflection over a fixed sample of grid points is exactly the
-requested value, and applied with the lensing pointing relation of Appendix C:
+the deflection here stands in for them.  It is the gradient of a Gaussian
+random lensing potential Phi (``phi_lensing``: C_l ~ [l(l+1)]^-1 (1+l/60)^-3,
+2 <= l <= min(512, lmax), scaled to 2.5 arcmin rms deflection), evaluated on
+the grid's rings, applied with the lensing pointing relation of Appendix C:
 n' = cos(a) n + sin(a)/a (a_theta e_theta + a_phi e_phi).
 """
 from __future__ import annotations
@@ -106,67 +108,96 @@ def gl_ring_grid(nrings: int, nphi: int) -> np.ndarray:
     return out
 
 
-class _Waves:
-    """Random plane waves of the deflection potential."""
+def phi_gradient_rings(philm: np.ndarray, lphi: int, thetas: np.ndarray, nphi: int):
+    """Gradient of the real field Phi = sum_lm philm_lm Y_lm (packed m-major,
+    band limit lphi) on iso-latitude rings: returns (a_theta, a_phi), each of
+    shape (len(thetas), nphi), with a_theta = dPhi/dtheta and
+    a_phi = (1/sin theta) dPhi/dphi at phi_k = 2 pi k / nphi (the spin-1
+    gradient of App. C, Eq. spin1deriv).  Input generation only: the
+    orthonormal functions come from the textbook three-term recurrence in
+    numpy, vectorised over the rings, their theta derivative from
+    sin(theta) dP_lm = l cos(theta) P_lm - sqrt((2l+1)(l^2-m^2)/(2l-1)) P_{l-1,m},
+    and the sum over m from a real inverse FFT per ring.  The rings must not
+    touch the poles (Gauss-Legendre nodes never do)."""
+    th = np.asarray(thetas, dtype=np.float64)
+    x, s = np.cos(th), np.sin(th)
+    nr = th.size
+    A = np.zeros((nr, lphi + 1), dtype=np.complex128)  # sum_l phi_lm dP_lm/dtheta
+    B = np.zeros((nr, lphi + 1), dtype=np.complex128)  # sum_l phi_lm P_lm
+    pmm = np.full(nr, 1.0 / np.sqrt(4.0 * np.pi))
+    base = 0
+    with np.errstate(under="ignore"):
+        for m in range(lphi + 1):
+            if m > 0:
+                pmm = -np.sqrt((2.0 * m + 1.0) / (2.0 * m)) * s * pmm
+            col = philm[base:base + lphi + 1 - m]
+            base += lphi + 1 - m
+            p2 = np.zeros(nr)
+            p1 = pmm
+            for l in range(m, lphi + 1):
+                if l == m + 1:
+                    p = np.sqrt(2.0 * m + 3.0) * x * p1
+                elif l > m + 1:
+                    a = np.sqrt((4.0 * l * l - 1.0) / (l * l - m * m))
+                    b = np.sqrt(((l - 1.0) ** 2 - m * m) / (4.0 * (l - 1.0) ** 2 - 1.0))
+                    p = a * (x * p1 - b * p2)
+                else:
+                    p = p1
+                if l > m:
+                    p2, p1 = p1, p
+                    dp = (l * x * p1 - np.sqrt((2.0 * l + 1.0) * (l * l - m * m) / (2.0 * l - 1.0)) * p2) / s
+                else:
+                    dp = (l * x * p1) / s
+                c = col[l - m]
+                A[:, m] += c * dp
+                B[:, m] += c * p1
+    A[:, 0] = A[:, 0].real
+    # real field: g(phi) = c_0 + 2 Re sum_{m>0} c_m e^{i m phi} = nphi * irfft(c)
+    C = np.zeros((nr, nphi // 2 + 1), dtype=np.complex128)
+    C[:, : lphi + 1] = A
+    a_th = nphi * np.fft.irfft(C, n=nphi, axis=1)
+    C[:] = 0.0
+    C[:, : lphi + 1] = B * (1j * np.arange(lphi + 1))[None, :] / s[:, None]
+    a_ph = nphi * np.fft.irfft(C, n=nphi, axis=1)
+    return a_th, a_ph
 
-    def __init__(self, seed: int, nwaves: int, kmin: float, kmax: float):
-        rng = np.random.default_rng(seed)
-        d = rng.standard_normal((nwaves, 3))
-        d /= np.linalg.norm(d, axis=1, keepdims=True)
-        kmag = rng.uniform(kmin, kmax, nwaves)
-        self.k = d * kmag[:, None]
-        self.amp = rng.standard_normal(nwaves) / kmag  # equal power per wave in the gradient
-        self.phase = rng.uniform(0.0, 2.0 * np.pi, nwaves)
 
-    def gradient(self, th: np.ndarray, ph: np.ndarray):
-        """(a_theta, a_phi): 3D gradient of Phi projected on e_theta, e_phi."""
-        st, ct = np.sin(th), np.cos(th)
-        sp, cp = np.sin(ph), np.cos(ph)
-        nx, ny, nz = st * cp, st * sp, ct
-        gx = np.zeros_like(th)
-        gy = np.zeros_like(th)
-        gz = np.zeros_like(th)
-        for q in range(self.k.shape[0]):
-            kx, ky, kz = self.k[q]
-            s = -self.amp[q] * np.sin(kx * nx + ky * ny + kz * nz + self.phase[q])
-            gx += s * kx
-            gy += s * ky
-            gz += s * kz
-        a_th = gx * ct * cp + gy * ct * sp - gz * st
-        a_ph = -gx * sp + gy * cp
-        return a_th, a_ph
+def pointing_shift(th: np.ndarray, ph: np.ndarray, a_th: np.ndarray, a_ph: np.ndarray):
+    """Move each point along the great circle that starts in the direction
+    a_th e_theta + a_phi e_phi by the angle |a| (App. C, Eq. pointing):
+    n' = cos|a| n + sin|a|/|a| (a_th e_theta + a_phi e_phi); returns
+    (theta', phi') with theta' in [0, pi], phi' in [0, 2 pi)."""
+    a = np.sqrt(a_th**2 + a_ph**2)
+    sinc = np.where(a > 0, np.sin(a) / np.where(a > 0, a, 1.0), 1.0)
+    ca = np.cos(a)
+    st, ct = np.sin(th), np.cos(th)
+    sp, cp = np.sin(ph), np.cos(ph)
+    x = ca * st * cp + sinc * (a_th * ct * cp - a_ph * sp)
+    y = ca * st * sp + sinc * (a_th * ct * sp + a_ph * cp)
+    z = ca * ct + sinc * (-a_th * st)
+    return np.arctan2(np.sqrt(x * x + y * y), z), np.mod(np.arctan2(y, x), 2.0 * np.pi)
 
 
-def deflect(pts: np.ndarray, rms_arcmin: float, seed: int, nwaves: int = 24, kmin: float = 20.0,
-            kmax: float = 400.0, chunk: int = 1 << 18) -> np.ndarray:
-    """Displace points by the gradient deflection of a random potential with the
-    pointing relation of Appendix C; the rms deflection is ``rms_arcmin``."""
-    waves = _Waves(seed, nwaves, kmin, kmax)
-    n = pts.shape[0]
-    # scale: rms |a| over a fixed sample of the input points
-    rng = np.random.default_rng(seed + 7919)
-    sel = rng.choice(n, size=min(n, 20000), replace=False)
-    a_th, a_ph = waves.gradient(pts[sel, 0], pts[sel, 1])
-    scale = rms_arcmin * ARCMIN / np.sqrt(np.mean(a_th**2 + a_ph**2))
+LPHI_MAX = 512  # band limit of the synthetic lensing potential
+
+
+def deflect_gl_grid(lmax: int, rms_arcmin: float, seed: int, chunk: int = 1 << 18) -> np.ndarray:
+    """(lmax+1) x (2 lmax+1) Gauss-Legendre ring grid deflected by the
+    gradient of a Gaussian lensing potential (``phi_lensing`` with band limit
+    min(512, lmax), rms deflection ``rms_arcmin``), with the pointing
+    relation of Appendix C."""
+    nr, nphi = lmax + 1, 2 * lmax + 1
+    pts = gl_ring_grid(nr, nphi)
+    lphi = min(LPHI_MAX, lmax)
+    phi = phi_lensing(lphi, seed, rms_arcmin)
+    a_th, a_ph = phi_gradient_rings(phi, lphi, pts[::nphi, 0], nphi)
+    a_th = a_th.reshape(-1)
+    a_ph = a_ph.reshape(-1)
     out = np.empty_like(pts)
 
     def one(s0):
-        th = pts[s0:s0 + chunk, 0]
-        ph = pts[s0:s0 + chunk, 1]
-        a_th, a_ph = waves.gradient(th, ph)
-        a_th *= scale
-        a_ph *= scale
-        a = np.sqrt(a_th**2 + a_ph**2)
-        sinc = np.where(a > 0, np.sin(a) / np.where(a > 0, a, 1.0), 1.0)
-        ca = np.cos(a)
-        st, ct = np.sin(th), np.cos(th)
-        sp, cp = np.sin(ph), np.cos(ph)
-        # n' = cos(a) n + sin(a)/a (a_th e_th + a_ph e_ph)
-        x = ca * st * cp + sinc * (a_th * ct * cp - a_ph * sp)
-        y = ca * st * sp + sinc * (a_th * ct * sp + a_ph * cp)
-        z = ca * ct + sinc * (-a_th * st)
-        out[s0:s0 + chunk, 0] = np.arctan2(np.sqrt(x * x + y * y), z)
-        out[s0:s0 + chunk, 1] = np.mod(np.arctan2(y, x), 2.0 * np.pi)
+        sl = slice(s0, s0 + chunk)
+        out[sl, 0], out[sl, 1] = pointing_shift(pts[sl, 0], pts[sl, 1], a_th[sl], a_ph[sl])
 
     # numpy ufuncs release the GIL, so chunks run in parallel threads; every
     # chunk is a pure function of its own points, so the result is the same
@@ -174,7 +205,7 @@ def deflect(pts: np.ndarray, rms_arcmin: float, seed: int, nwaves: int = 24, kmi
     from concurrent.futures import ThreadPoolExecutor
 
     with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
-        list(ex.map(one, range(0, n, chunk)))
+        list(ex.map(one, range(0, pts.shape[0], chunk)))
     return out
 
 
@@ -202,11 +233,11 @@ def _cached(key: str, make):
 def deflected_gl_grid(lmax: int, seed: int = 1, rms_arcmin: float = 2.5, cache: bool = True) -> np.ndarray:
     """(lmax+1) x (2 lmax+1) Gauss-Legendre ring grid deflected by ``rms_arcmin``."""
     def make():
-        return deflect(gl_ring_grid(lmax + 1, 2 * lmax + 1), rms_arcmin, seed)
+        return deflect_gl_grid(lmax, rms_arcmin, seed)
 
     if not cache:
         return make()
-    return _cached("glgrid-v1-%d-%d-%r" % (lmax, seed, rms_arcmin), make)
+    return _cached("glgrid-v2-%d-%d-%r" % (lmax, seed, rms_arcmin), make)
 
 
 def subset(n: int, k: int, seed: int = 12345) -> np.ndarray:
