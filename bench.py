@@ -215,11 +215,12 @@ def run_reference(args):
     scale = pts.shape[0] / float(nsample)
     ms = 1e3 * float(np.mean(times)) * scale
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "extrapolated": True,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "deflected GL grid 4096x8191 (33,550,336 pts), lmax=mmax=4095, "
                                    "C_l=(l+1)^-2, 2.5 arcmin rms deflection"},
-            "cpu_baseline": {"value": ms, "unit": "ms", "cores": threads, "kind": "oracle",
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": threads, "kind": "oracle", "extrapolated": True,
                              "sample": "%d seeded points per step (synthesis + full adjoint), scaled by N/%d "
                                        "(the direct sum is exactly linear in N)" % (nsample, nsample)},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -235,7 +236,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-transform batched measurement")
-    ap.add_argument("--no-table", action="store_true", help="skip the recurrence-table (legendre_table=1) runs")
+    ap.add_argument("--no-table", action="store_true",
+                    help="skip the FP64 recurrence-table run and the mixed per-call-recurrence run")
+    ap.add_argument("--no-strict", action="store_true",
+                    help="skip the all-FP64-instruction run (fp64_contraction=1, fft_kernels=-1)")
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy / speed sweep over eps x sigma on the lmax 1023 deflected grid (one JSON line)")
     ap.add_argument("--no-fast", action="store_true",
@@ -273,19 +277,24 @@ def main():
     dpts = torch.from_numpy(pts).cuda()
     results = {}
     y_host = np.random.default_rng(5).standard_normal(npts)
-    # (precision, recurrence table, double-float recurrence)
-    runs = [("fp64", 0, False)] + ([] if args.no_mixed else [("mixed", 0, False)])
+    # (key, precision, plan options); "mixed" is the mixed default, which
+    # runs the FP64 recurrence once at plan time (recurrence table)
+    runs = [("fp64", "fp64", {})] + ([] if args.no_mixed else [("mixed", "mixed", {})])
+    if not args.no_strict:
+        runs += [("fp64_strict", "fp64", {"fp64_contraction": True, "fft_kernels": -1})]
     if not args.no_table:
-        runs += [("fp64", 1, False)] + ([] if args.no_mixed else [("mixed", 1, False)])
+        runs += [("fp64_table", "fp64", {"legendre_table": 1})]
+        runs += [] if args.no_mixed else [("mixed_percall", "mixed", {"legendre_table": -1})]
     if not args.no_fast:
-        runs += [("fp64", 0, True)] + ([] if args.no_mixed else [("mixed", 0, True)])
-    for prec, table, fastrec in runs:
-        key = prec + ("_table" if table else "") + ("_fast_recurrence" if fastrec else "")
+        runs += [("fp64_fast_recurrence", "fp64", {"fast_recurrence": True})]
+        runs += [] if args.no_mixed else [("mixed_fast_recurrence", "mixed", {"fast_recurrence": True})]
+    sel_par = W.subset(npts, 300, seed=17)
+    f_ref_par = None
+    for key, prec, popts in runs:
         cd = torch.complex128 if prec == "fp64" else torch.complex64
         rd = torch.float64 if prec == "fp64" else torch.float32
         t0 = time.perf_counter()
-        plan = nu.Plan(L, dpts, eps=EPS[prec], precision=prec, profile=True, legendre_table=table,
-                       fast_recurrence=fastrec)
+        plan = nu.Plan(L, dpts, eps=EPS[prec], precision=prec, profile=True, **popts)
         torch.cuda.synchronize()
         t_plan = time.perf_counter() - t0
         ad = torch.from_numpy(a).to(cd).cuda()
@@ -307,10 +316,10 @@ def main():
         if rank == 0:
             import oracle
 
-            sel = W.subset(npts, 300, seed=17)
-            f_ref = oracle.synth(a, pts[sel], L)
+            if f_ref_par is None:
+                f_ref_par = oracle.synth(a, pts[sel_par], L)
             f = plan.synth(ad).double().cpu().numpy()
-            par = oracle.eps_eff(f_ref, f[sel])
+            par = oracle.eps_eff(f_ref_par, f[sel_par])
         results[key] = {"ms": ms, "plan_s": t_plan, "stages": stages, "clocks": clk.summary(), "eps_eff": par,
                         "info": plan.info(), "median": med, "std": std}
         if key == "fp64":
@@ -404,39 +413,55 @@ def main():
     fp = results["fp64"]
     M = fp["info"]["M"]
     flops = legendre_fp64_work(fp["info"]["leg_triples"])
-    t_leg = fp["stages"]["synth"]["legendre"] * 1e-3
-    achieved = flops / t_leg / 1e12
     peak = FP64_PEAK_TFLOPS * 0.75
-    traffic = None
+    traffic = {}
     prof = os.path.join(ROOT, "profiles", "legendre_traffic.json")
     if os.path.exists(prof):
         try:
             with open(prof) as fh:
                 tj = json.load(fh)
             if tj.get("kernel_hash") == _kernel_hash():
-                traffic = tj.get("bytes_per_launch")
+                traffic = tj.get("bytes_per_launch", {})
         except Exception:
-            traffic = None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "legendre_synth_df_k: FP64 recurrence (1 DMUL + 1 DFMA = 3 flops per triple) on the FP64 "
-                          "pipe; peak = 152 SMs x 2 FP64 FMA lanes/clk x 2.07 GHz x 3 flops / 2 slots (nominal)",
-                "flops_per_launch": flops, "triples_per_launch": fp["info"]["leg_triples"]}
+            traffic = {}
+    # both Legendre kernels against the FP64 pipe; the top-level entry is the
+    # slower (dominant) one.  Stage times are the library's CUDA events on the
+    # launching stream (the adjoint stage includes the 0.3 ms partial-sum
+    # reduction kernel).
+    leg = {}
+    for kname, direction in (("legendre_synth_df_k", "synth"), ("legendre_adj_df_k", "adjoint")):
+        t_leg = fp["stages"][direction]["legendre"] * 1e-3
+        ach = flops / t_leg / 1e12
+        leg[kname] = {"ms": t_leg * 1e3, "achieved": ach, "frac": ach / peak, "traffic": traffic.get(kname)}
+    dom = max(leg, key=lambda k: leg[k]["ms"])
+    roofline = {"bound": "alu", "achieved": leg[dom]["achieved"], "peak": peak, "unit": "TFLOP/s",
+                "frac": leg[dom]["frac"], "traffic": leg[dom]["traffic"],
+                "kernel": dom + ": FP64 recurrence (1 DMUL + 1 DFMA = 3 flops per triple) on the FP64 pipe; "
+                                "peak = 152 SMs x 2 FP64 FMA lanes/clk x 2.07 GHz x 3 flops / 2 slots (nominal; "
+                                "no FP64 figure in the measured peaks)",
+                "flops_per_launch": flops, "triples_per_launch": fp["info"]["leg_triples"],
+                "per_kernel": leg}
     cpu = None
     if not args.no_cpu:
         nsample = int(os.environ.get("NUSHT_CPU_SAMPLE", "200"))
         sec, threads, _ = cpu_oracle_step(a, pts, L, nsample)
         cpu = {"value": 1e3 * sec * npts / nsample, "unit": "ms", "cores": threads, "kind": "oracle",
+               "extrapolated": True,
                "sample": "%d seeded points (synthesis + adjoint over all orders), scaled by N/%d; "
                          "the direct sum is exactly linear in N" % (nsample, nsample)}
-    launches_per_step = 9  # scale_alm, legendre_synth, poles, deconv_pad, interp | spread, deconv_trunc, legendre_adj, reduce
+    # synthesis: scale_alm_df, legendre_synth_df, poles_synth, theta DFT, column pass, row pass, interp_df;
+    # adjoint: spread_df, row pass, column pass, theta DFT, legendre_adj_df, adj_reduce_df
+    launches_per_step = 13
     line = {
         "metric": METRIC, "value": fp["ms"] / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": fp["ms"], "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": "f64 recurrence; double-float (float pairs, ~2^-47 per op) contraction, FFTs, NUFFT",
+        "data": "synthetic",
         "config": {"workload": "deflected GL grid %dx%d (%d pts), lmax=mmax=%d, "
                                "C_l=(l+1)^-2 Gaussian a_lm, 2.5 arcmin rms deflection" % (L + 1, 2 * L + 1, npts, L),
-                   "eps": 1e-10, "precision": "fp64", "sigma": fp["info"]["sigma"], "w": fp["info"]["w"],
+                   "eps": 1e-10, "precision": "NUSHT_FP64 (default options)", "sigma": fp["info"]["sigma"],
+                   "w": fp["info"]["w"],
                    "fine_grid": [fp["info"]["n1"], fp["info"]["n2"]], "M": M,
                    "l2": "inputs larger than L2 (%d^2 fine grid, %d points)" % (fp["info"]["n1"], npts),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -450,19 +475,31 @@ def main():
     if "mixed" in results:
         mx = results["mixed"]
         line["mixed"] = {"ms_per_step": mx["ms"], "step_ms_median": mx["median"], "step_ms_std": mx["std"],
-                         "eps": 1e-5, "eps_eff": mx["eps_eff"],
+                         "eps": 1e-5, "eps_eff": mx["eps_eff"], "plan_s": mx["plan_s"],
+                         "plan_GB": mx["info"]["bytes_device"] / 1e9,
                          "synth_ms": mx["stages"]["synth"]["total"], "adjoint_ms": mx["stages"]["adjoint"]["total"],
                          "stages_ms": mx["stages"], "w": mx["info"]["w"], "sigma": mx["info"]["sigma"],
-                         "dtype": "f64 recurrence / f32 contraction, FFT, NUFFT", "clocks": mx["clocks"]}
-    for key in ("fp64_table", "mixed_table"):
+                         "dtype": "f64 recurrence (once, at plan time: the mixed default) / f32 contraction, FFT, "
+                                  "NUFFT", "clocks": mx["clocks"],
+                         "nufft_roofline": mixed_nufft_roofline(mx, npts, peaks["hbm_gbs"])}
+    if "fp64_strict" in results:
+        r = results["fp64_strict"]
+        line["fp64_strict"] = {"ms_per_step": r["ms"], "eps_eff": r["eps_eff"],
+                               "synth_ms": r["stages"]["synth"]["total"],
+                               "adjoint_ms": r["stages"]["adjoint"]["total"], "stages_ms": r["stages"],
+                               "dtype": "f64 instructions in every stage",
+                               "what": "opts.fp64_contraction=1, opts.fft_kernels=-1: Legendre sums, spreading and "
+                                       "interpolation with FP64 instructions, cuFFT FP64 transforms"}
+    for key in ("fp64_table", "mixed_percall"):
         if key in results:
             r = results[key]
             line[key] = {"ms_per_step": r["ms"], "eps_eff": r["eps_eff"], "plan_s": r["plan_s"],
                          "synth_ms": r["stages"]["synth"]["total"], "adjoint_ms": r["stages"]["adjoint"]["total"],
                          "legendre_ms": [r["stages"]["synth"]["legendre"], r["stages"]["adjoint"]["legendre"]],
                          "plan_GB": r["info"]["bytes_device"] / 1e9,
-                         "what": "opts.legendre_table=1: the FP64 recurrence runs once at plan time and its "
-                                 "values stay in HBM; each call streams them"}
+                         "what": ("opts.legendre_table=1: the FP64 recurrence runs once at plan time and its "
+                                  "values stay in HBM; each call streams them") if key == "fp64_table" else
+                                 ("opts.legendre_table=-1: the FP64 recurrence runs in every call")}
     for key in ("fp64_fast_recurrence", "mixed_fast_recurrence"):
         if key in results:
             r = results[key]
@@ -482,6 +519,23 @@ def main():
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def mixed_nufft_roofline(r, npts: int, hbm_gbs: float) -> dict:
+    """HBM roofline of the mixed-mode interpolation (interp_f_k) and
+    spreading (spread_pt_k) stages: algorithmic bytes per launch = one pass
+    over the float fine grid (n1 x (n2 + 2) x 4 B) + 24 B per point (sorted
+    first taps 8 B, offsets 8 B, permutation 4 B, the value 4 B), divided by
+    the stage's CUDA-event time."""
+    z = r["info"]
+    grid = z["n1"] * (z["n2"] + 2) * 4
+    nbytes = grid + 24 * npts
+    out = {"bytes_per_launch": nbytes, "peak_gbs": hbm_gbs}
+    for kname, direction, stage in (("interp_f_k", "synth", "interp"), ("spread_pt_k", "adjoint", "spread")):
+        ms = r["stages"][direction][stage]
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[kname] = {"ms": ms, "achieved_gbs": gbs, "frac": gbs / hbm_gbs}
+    return out
 
 
 def run_pointing(torch, nu, args, dist, L):
@@ -655,7 +709,7 @@ def _kernel_hash() -> str:
     import hashlib
 
     h = hashlib.sha1()
-    for f in ("legendre.cu", "recurrence.cuh", "dfloat.cuh", "nusht_internal.cuh"):
+    for f in ("legendre.cu", "recurrence.cuh", "dfloat.cuh"):
         with open(os.path.join(ROOT, "paper_2406_14542_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]

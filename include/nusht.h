@@ -28,18 +28,35 @@
  * F is a uniform FFT (here a 1D theta FFT, the phi FFTs of S and F cancel,
  * Sec. 3), N is a type 2 NUFFT with the exponential-of-semicircle kernel.
  *
- * Precision modes:
- *   NUSHT_FP64   all arithmetic in double; coefficients complex128, maps double.
- *   NUSHT_MIXED  Legendre recurrence, its rescaling and the DFS fold in double;
- *                Legendre contraction, FFTs and spreading/interpolation in
- *                float; coefficients complex64, maps float.  Point coordinates
- *                stay double in both modes (the cell index and offset are
- *                reduced in double, Sec. 4 on single-precision pointing).
+ * Precision modes (what each stage computes in; Sec. 4 reads accuracy as the
+ * relative l2 error eps_eff against the exact sum):
+ *   NUSHT_FP64   coefficients complex128, maps double.  In double (FP64
+ *                instructions): the P_lm recurrence and its rescaling, the
+ *                DFS doubling and fold, the coordinate reduction (cell index
+ *                and offset), the kernel values and the deconvolution factors
+ *                (both computed at plan time).  In double-float (unevaluated
+ *                float pairs hi + lo on the FP32 pipe, ~2^-47 relative per
+ *                operation, float exponent range) by default: the Legendre
+ *                contraction (sum_l a_lm P_lm and its adjoint), the theta FFT
+ *                and the fine-grid 2D FFT (lengths up to 14336; longer ones use
+ *                cuFFT in double), spreading and interpolation; the kernel
+ *                values are stored as float pairs.  opts.fp64_contraction = 1
+ *                and opts.fft_kernels = -1 together select FP64 instructions
+ *                for every stage.  Measured eps_eff at lmax 4095 is ~6e-12
+ *                either way, against the 1e-10 target.
+ *   NUSHT_MIXED  coefficients complex64, maps float.  The Legendre recurrence,
+ *                its rescaling and the DFS fold in double (by default the
+ *                recurrence runs once at plan time, see opts.legendre_table);
+ *                the Legendre contraction, the FFTs and spreading /
+ *                interpolation in float.  Point coordinates stay double in
+ *                both modes (the cell index and offset are reduced in double,
+ *                Sec. 4 on single-precision pointing).
  *
  * Memory and streams.  Every d_* pointer is DEVICE memory owned by the caller
  * and must stay valid for the duration of the call's stream work.  A plan owns
  * all of its workspace, allocated in nusht_plan; the execute calls
- * (nusht_synth, nusht_adjoint, nusht_synth_grad, nusht_pointing) allocate nothing, copy
+ * (nusht_synth, nusht_adjoint, nusht_synth_grad, nusht_adjoint_grad,
+ * nusht_synth_grad_pts, nusht_pointing) allocate nothing, copy
  * nothing to or from the host and do not synchronise: they enqueue kernels and
  * cuFFT work on `stream` (NULL = the legacy default stream) and return.  A plan
  * may be used by one stream at a time.  Plans are bound to the device that was
@@ -107,11 +124,13 @@ typedef struct {
                            0 (default) = FP64 recurrence, sums as float pairs on the FP32
                            pipe (~2^-48 relative per operation; a_lm magnitudes below 1e20) */
   int legendre_table; /* where the FP64 recurrence runs.  0 = the plan type's default:
-                         every call for nusht_plan, once at plan time for nusht_plan_many;
-                         1 = once at plan time, its values kept in device memory (float per
-                         (ring pair, l, m) in mixed mode, a float pair in FP64 mode: 59 / 118 GB
-                         at lmax 4095), when they fit in half the free memory;
-                         -1 = every call */
+                         once at plan time for NUSHT_MIXED plans (nusht_plan, unless
+                         fast_recurrence = 1, and nusht_plan_many), every call for
+                         NUSHT_FP64 plans; 1 = once at plan time; -1 = every call.  At plan
+                         time the values are kept in device memory (a float per (ring pair,
+                         l, m) in mixed mode, a float pair in FP64 mode: 59 / 118 GB at lmax
+                         4095) when they fit in half the free memory, else the recurrence
+                         runs every call */
   int tensor_cores;   /* batched plans whose recurrence table fits: 0 (default) = the
                          contraction on the tensor cores (tcgen05.mma, TF32 operands split
                          into hi + lo, three products per term, FP32 accumulation;
@@ -197,6 +216,37 @@ NUSHT_API int nusht_adjoint(nusht_plan_t p, const void* d_map, void* d_alm, nush
 NUSHT_API int nusht_synth_grad(nusht_plan_t p, const void* d_alm, void* d_dtheta, void* d_dphi, nusht_stream_t stream);
 
 /*
+ * nusht_adjoint_grad -- gradient of a real loss L(f) with respect to the
+ * complex coefficients, given the cotangent g_i = dL/df_i of the synthesised
+ * map f = Y a (Eq. SHTbase; the backward pass of a differentiable transform).
+ * Because type 1 is the adjoint of type 2 (Sec. 2.1), the gradient is the
+ * adjoint applied to g, with the m > 0 entries doubled (each stands for
+ * a_{l,m} and a_{l,-m} = (-1)^m conj(a_lm) of the real field):
+ *     d_galm[l, m] = w_m (Y^dagger g)_lm,  w_0 = 1, w_{m>0} = 2,
+ * in the convention dL/dRe(a) + i dL/dIm(a) (Im of the m = 0 entries is 0).
+ *   d_cot   device FP64: double[npts] / MIXED: float[npts], caller's order
+ *   d_galm  device complex, nalm entries, overwritten
+ * Asynchronous; allocates nothing.
+ */
+NUSHT_API int nusht_adjoint_grad(nusht_plan_t p, const void* d_cot, void* d_galm, nusht_stream_t stream);
+
+/*
+ * nusht_synth_grad_pts -- gradient of a real loss L(f) with respect to the
+ * point coordinates, given the cotangent g_i = dL/df_i of f = Y a: since
+ * f_i depends only on point i,
+ *     d_gpts[2 i] = g_i d f_i / d theta_i,  d_gpts[2 i + 1] = g_i d f_i / d phi_i,
+ * with the derivatives from the derivative-of-kernel interpolation of
+ * nusht_synth_grad (the same layout as the points, (theta, phi) pairs).
+ *   d_alm   device complex coefficients (the plan's precision)
+ *   d_cot   device FP64: double[npts] / MIXED: float[npts], caller's order
+ *   d_gpts  device double[2 * npts], overwritten
+ * Plans made by nusht_plan only (NUSHT_EUNSUPPORTED otherwise).
+ * Asynchronous; allocates nothing; overwrites the plan's work buffers.
+ */
+NUSHT_API int nusht_synth_grad_pts(nusht_plan_t p, const void* d_alm, const void* d_cot, double* d_gpts,
+                                   nusht_stream_t stream);
+
+/*
  * nusht_pointing -- CMB lensing pointing (App. C): the deflected position of
  * every point of the plan for the lensing potential Phi.
  *   d_philm  the potential's coefficients in the plan's a_lm layout and
@@ -244,11 +294,14 @@ NUSHT_API int nusht_pointing(nusht_plan_t p, const void* d_philm, double* d_ptg,
  * keeps until the process exits.  All calls share it, so calls whose GPU work
  * overlaps (different streams, or different host threads, on one device)
  * race on it and give wrong results; serialise them.  Each call overwrites
- * the part it reads, so nothing needs clearing between calls.
- * Set-up: the first call on each device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture begins.  Asynchronous on `stream`; no host
- * memory is touched.  Only NUSHT_FP64 (double) inputs are supported.
+ * the part it reads, so nothing needs clearing between calls.  The number of
+ * partial-sum slots per coefficient is the array's capacity over nalm,
+ * capped by the number of 128-point chunks (and by 4096).
+ * Set-up: every call looks up that array's device address
+ * (cudaGetSymbolAddress) with the calling thread's current device; the first
+ * call on a device also loads the library's device code there, so make that
+ * first call before any stream capture begins.  Asynchronous on `stream`;
+ * no host memory is touched.  Only NUSHT_FP64 (double) inputs are supported.
  */
 NUSHT_API int nusht_adjoint_direct_noalloc(int lmax, int mmax, int64_t npts, const double* d_pts, const double* d_map,
                                            void* d_alm, nusht_stream_t stream);
@@ -327,7 +380,8 @@ NUSHT_API int nusht_destroy(nusht_plan_t p);
 NUSHT_API int nusht_info(nusht_plan_t p, nusht_sizes* out);
 
 /* nusht_plan_bin -- spreading/interpolation bin edge (fine-grid cells) the plan
- * uses: 32, or the autotuner's choice (opts.tune). */
+ * uses: without the autotuner 16 for FP64 plans with kernel width <= 17 and
+ * fp64_contraction = 0, else 32; with opts.tune the autotuner's choice. */
 NUSHT_API int nusht_plan_bin(nusht_plan_t p, int* bin);
 
 /*

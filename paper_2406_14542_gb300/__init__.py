@@ -37,7 +37,8 @@ EXPORTS = ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_
            "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_good_size", "nusht_stage_times",
            "nusht_strerror", "nusht_last_error", "nusht_version", "nusht_adjoint_direct_noalloc",
            "nusht_plan_many", "nusht_synth_many", "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info",
-           "nusht_plan_bin", "nusht_batch_status", "nusht_batch_path", "nusht_pointing")
+           "nusht_plan_bin", "nusht_batch_status", "nusht_batch_path", "nusht_pointing", "nusht_adjoint_grad",
+           "nusht_synth_grad_pts")
 
 
 class NushtError(RuntimeError):
@@ -87,6 +88,8 @@ def load(path: str | None = None):
         lib.nusht_adjoint.argtypes = [vp, vp, vp, vp]
         lib.nusht_synth_grad.argtypes = [vp, vp, vp, vp, vp]
         lib.nusht_pointing.argtypes = [vp, vp, vp, vp]
+        lib.nusht_adjoint_grad.argtypes = [vp, vp, vp, vp]
+        lib.nusht_synth_grad_pts.argtypes = [vp, vp, vp, vp, vp]
         lib.nusht_destroy.argtypes = [vp]
         lib.nusht_info.argtypes = [vp, ctypes.POINTER(Sizes)]
         lib.nusht_plan_sizes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -115,7 +118,8 @@ def load(path: str | None = None):
                      "nusht_destroy", "nusht_info", "nusht_plan_sizes", "nusht_kernel_ft", "nusht_stage_times",
                      "nusht_adjoint_direct_noalloc", "nusht_plan_many", "nusht_synth_many",
                      "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info", "nusht_plan_bin",
-                     "nusht_batch_status", "nusht_batch_path", "nusht_pointing"):
+                     "nusht_batch_status", "nusht_batch_path", "nusht_pointing", "nusht_adjoint_grad",
+                     "nusht_synth_grad_pts"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -374,6 +378,37 @@ class Plan:
                                          _stream_ptr(stream)), "nusht_synth_grad")
         return dth, dph
 
+    def adjoint_grad(self, g, out=None, stream=None):
+        """Gradient of a real loss in a_lm from the cotangent g = dL/df of the
+        synthesised map (nusht_adjoint_grad: the adjoint with the m > 0
+        entries doubled, torch's dL/dRe + i dL/dIm convention)."""
+        import torch
+
+        g = self._map(g)
+        if out is None:
+            out = torch.empty(self.nalm, dtype=self.cdtype, device=self.device)
+        out = self._alm(out)
+        _check(self.lib.nusht_adjoint_grad(self.handle, ctypes.c_void_p(g.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+               "nusht_adjoint_grad")
+        return out
+
+    def synth_grad_pts(self, alm, g, out=None, stream=None):
+        """Gradient of a real loss in the point coordinates from the cotangent
+        g = dL/df (nusht_synth_grad_pts): float64 (npts, 2) tensor of
+        (g_i df_i/dtheta_i, g_i df_i/dphi_i)."""
+        import torch
+
+        alm = self._alm(alm)
+        g = self._map(g)
+        gp = out if out is not None else torch.empty((self.npts, 2), dtype=torch.float64, device=self.device)
+        if gp.dtype != torch.float64 or tuple(gp.shape) != (self.npts, 2) or not gp.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor of shape (npts, 2)")
+        _check(self.lib.nusht_synth_grad_pts(self.handle, ctypes.c_void_p(alm.data_ptr()),
+                                             ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(gp.data_ptr()),
+                                             _stream_ptr(stream)), "nusht_synth_grad_pts")
+        return gp
+
     def pointing(self, philm, out=None, stream=None):
         """CMB lensing pointing (App. C): the deflected (theta', phi') of every
         point for the lensing potential ``philm`` (the plan's a_lm layout and
@@ -507,7 +542,9 @@ def _autograd():
 
         For a real loss, torch's complex gradient is dL/dRe(a) + i dL/dIm(a)
         = w_m (Y^dagger g)_lm with w_0 = 1, w_{m>0} = 2 (the real-field map
-        counts each m > 0 twice, once through a_{l,-m}).
+        counts each m > 0 twice, once through a_{l,-m}); the library applies
+        that weight (nusht_adjoint_grad) and the cotangent product of the
+        position gradient (nusht_synth_grad_pts), so backward only calls them.
         """
 
         @staticmethod
@@ -523,11 +560,9 @@ def _autograd():
             g = g.contiguous().to(plan.rdtype)
             ga = gp = None
             if ctx.needs_input_grad[0]:
-                ga = plan.adjoint(g)
-                ga[plan.lmax + 1:] *= 2.0
+                ga = plan.adjoint_grad(g)
             if ctx.needs_input_grad[1]:
-                dth, dph = plan.synth_grad(alm.detach())
-                gp = torch.stack([g * dth, g * dph], dim=1).to(torch.float64)
+                gp = plan.synth_grad_pts(alm.detach(), g)
             return ga, gp, None
 
     return NuSHT

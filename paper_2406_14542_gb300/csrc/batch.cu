@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -598,7 +599,10 @@ __global__ void __launch_bounds__(256) bucket_adj_tab_k(BucketArgs a, const int*
 // that the MMA thread waits for before refilling it.  One block per SM (512
 // TMEM columns).  Every wait is bounded (one second of device time); a block
 // that gives up flags the others, waits (bounded) for its copies in flight,
-// sets *status and still frees its tensor memory.
+// sets *status and still frees its tensor memory.  test_giveup = 1 (a test
+// hook, NUSHT_TEST_TC_GIVEUP=1 at plan time) gives the MMA thread's first
+// wait for data a limit of zero polls, so that it runs out before any MMA is
+// issued and the give-up path runs.
 // ---------------------------------------------------------------------------
 constexpr int TC_TILE = 128 * 8 * 4;              // one 128 x 8 fp32 operand tile
 constexpr int TC_CHUNK = 8 * TC_TILE;             // AEh AEl AOh AOl BEh BEl BOh BOl
@@ -628,9 +632,14 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase `parity` of an mbarrier: gives up (false) after
+// TC_WAIT_NS of device time or max_polls polls, or, when `stop` is given, as
+// soon as *stop is set (another role of the block gave up).  Waits that drain
+// asynchronous work before the block exits pass no `stop`.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* stop = nullptr,
+                                          int max_polls = 1 << 30) {
   const unsigned long long t0 = gtimer();
-  for (int it = 0; it < (1 << 30); ++it) {
+  for (int it = 0; it < max_polls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -638,7 +647,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 63) == 63 && gtimer() - t0 > TC_WAIT_NS) return false;
+    if ((it & 63) == 63 && (gtimer() - t0 > TC_WAIT_NS || (stop && *stop))) return false;
   }
   return false;
 }
@@ -736,7 +745,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) bucket_tc_k(BucketArgs a, int n
                                                              const unsigned char* __restrict__ Atab,
                                                              const unsigned char* __restrict__ Bbuf,
                                                              float2* __restrict__ G, float* __restrict__ cacc,
-                                                             int* __restrict__ status) {
+                                                             int* __restrict__ status, int test_giveup) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   T6Bars* bars = reinterpret_cast<T6Bars*>(tc_smem + T6_NBUF * TC_CHUNK);
   if ((int)blockIdx.x >= nblk || *(volatile int*)status) return;
@@ -788,7 +797,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) bucket_tc_k(BucketArgs a, int n
       int issued = 0;
       for (int c = 0; c < nchunk && !*abort; ++c) {
         const int s = c % T6_NBUF;
-        if (c >= T6_NBUF && !mbar_wait(smem_u32(&bars->empty[s]), (uint32_t)((c / T6_NBUF - 1) & 1))) {
+        if (c >= T6_NBUF && !mbar_wait(smem_u32(&bars->empty[s]), (uint32_t)((c / T6_NBUF - 1) & 1), abort)) {
           *abort = 1;
           break;
         }
@@ -814,12 +823,14 @@ __global__ void __launch_bounds__(T6_THREADS, 1) bucket_tc_k(BucketArgs a, int n
       int last = -1;
       for (int c = 0; c < nchunk && !*abort; ++c) {
         const int s = c % T6_NBUF;
-        if (!mbar_wait(smem_u32(&bars->full[s]), (uint32_t)((c / T6_NBUF) & 1))) {
+        if (!mbar_wait(smem_u32(&bars->full[s]), (uint32_t)((c / T6_NBUF) & 1), abort,
+                       (test_giveup && c == 0) ? 0 : (1 << 30))) {
           *abort = 1;
           break;
         }
         const int g = c / TC_G, set = g & 1;
-        if (c % TC_G == 0 && g >= 2 && !mbar_wait(smem_u32(&bars->gfree[set]), (uint32_t)(((g - 2) >> 1) & 1))) {
+        if (c % TC_G == 0 && g >= 2 &&
+            !mbar_wait(smem_u32(&bars->gfree[set]), (uint32_t)(((g - 2) >> 1) & 1), abort)) {
           *abort = 1;
           break;
         }
@@ -846,7 +857,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) bucket_tc_k(BucketArgs a, int n
     const uint32_t tview = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
     for (int g = 0; g < ngroups; ++g) {
       const int set = g & 1;
-      const bool okw = mbar_wait(smem_u32(&bars->gdone[set]), (uint32_t)((g >> 1) & 1));
+      const bool okw = mbar_wait(smem_u32(&bars->gdone[set]), (uint32_t)((g >> 1) & 1), abort);
       if (!__all_sync(0xffffffffu, okw)) {
         *abort = 1;
         break;
@@ -1136,6 +1147,7 @@ struct nusht_batch_s {
   cudaStream_t side[NSIDE] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[NSIDE] = {};
   int* status = nullptr;  // device flag: a bounded wait in a tensor-core kernel gave up
+  int test_giveup = 0;    // test hook (NUSHT_TEST_TC_GIVEUP=1): the first data wait runs out
   cudaGraphExec_t gs = nullptr, ga = nullptr;
   std::vector<const void*> gs_in;
   std::vector<void*> gs_out;
@@ -1480,7 +1492,7 @@ int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
       if (b.ntc > 0)
         bucket_tc_k<false><<<b.ntc, T6_THREADS, T6_SMEM, s>>>(a, b.ntc, b.tc_items, nullptr, b.pa_off, b.bs_off,
                                                               nullptr, nullptr, b.ntiles, b.PA, b.BS, b.G, nullptr,
-                                                              p->status);
+                                                              p->status, p->test_giveup);
     } else {
       bucket_scale_k<<<g, 256, 0, s>>>(b.L, b.B, b.memberL, b.alm_ptrs, b.leg->leg.ahat, b.atb);
     }
@@ -1525,7 +1537,8 @@ int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
       if (b.ntc_work > 0)
         bucket_tc_k<true><<<b.ntc_work, T6_THREADS, T6_SMEM, s>>>(bucket_args(b), b.ntc_work, nullptr, b.tc_work,
                                                                   b.pt_off, nullptr, b.items, b.mfirst, b.ntiles,
-                                                                  b.PT, b.BA, nullptr, b.cacc, p->status);
+                                                                  b.PT, b.BA, nullptr, b.cacc, p->status,
+                                                                  p->test_giveup);
     } else {
       dim3 gf((b.npairs + FOLD_PAIRS - 1) / FOLD_PAIRS, b.L + 1);
       bucket_fold_k<<<gf, 256, 0, s>>>(b.L, b.M, b.npairs, b.B, b.memberL, b.Ghat, b.S);
@@ -1607,6 +1620,10 @@ int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64
     if (opts) p->opts = *opts;
     p->L.assign(lmax, lmax + nbatch);
     p->npts.assign(npts, npts + nbatch);
+    {
+      const char* tg = std::getenv("NUSHT_TEST_TC_GIVEUP");
+      p->test_giveup = (tg && std::atoi(tg) == 1) ? 1 : 0;
+    }
     if ((st = set_adj_smem()) != NUSHT_OK) break;
     if ((st = dev_alloc((void**)&p->status, sizeof(int), &p->bytes)) != NUSHT_OK) break;
     {

@@ -26,7 +26,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <vector>
 
 #include "nusht_internal.cuh"
@@ -293,10 +292,13 @@ __global__ void __launch_bounds__(128) legendre_adj_k(LegArgs a, const typename 
 // Sum of the ring-block partials in a fixed order, times Ahat; the poles
 // (theta = 0, pi) contribute to m = 0 only: Pbar_l0(0) = sqrt((2l+1)/4pi),
 // Pbar_l0(pi) = (-1)^l sqrt((2l+1)/4pi).
+// wpos multiplies the m > 0 entries: 1 for the adjoint, 2 for the gradient of
+// a real loss with respect to the complex coefficients (nusht_adjoint_grad).
 template <typename T>
 __global__ void adj_reduce_k(const typename V2<T>::t* __restrict__ partial, int bpm, int64_t nalm,
                              const double* __restrict__ ahat, const double* __restrict__ pole_norm,
-                             const typename V2<T>::t* __restrict__ Gt, int lmax, int M, typename V2<T>::t* out) {
+                             const typename V2<T>::t* __restrict__ Gt, int lmax, int M, double wpos,
+                             typename V2<T>::t* out) {
   using T2 = typename V2<T>::t;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nalm) return;
@@ -306,7 +308,7 @@ __global__ void adj_reduce_k(const typename V2<T>::t* __restrict__ partial, int 
     sx += (double)v.x;
     sy += (double)v.y;
   }
-  const double ah = ahat[i];
+  const double ah = (i <= lmax) ? ahat[i] : ahat[i] * wpos;
   sx *= ah;
   sy *= ah;
   T2 r;
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(128, 5) legendre_adj_df_k(LegArgs a, const dou
 // c_lm = Ahat sum_blocks (hi + lo) in double, plus the poles (m = 0)
 __global__ void adj_reduce_df_k(const float4* __restrict__ partial, int bpm, int64_t nalm,
                                 const double* __restrict__ ahat, const double* __restrict__ pole_norm,
-                                const double2* __restrict__ Gt, int lmax, int M, double2* out) {
+                                const double2* __restrict__ Gt, int lmax, int M, double wpos, double2* out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nalm) return;
   // the block partials summed as float pairs (FP32 pipe), in a fixed order,
@@ -612,7 +614,7 @@ __global__ void adj_reduce_df_k(const float4* __restrict__ partial, int bpm, int
     df_add(yh, yl, v.z, v.w);
   }
   double sx = df_value(xh, xl), sy = df_value(yh, yl);
-  const double ah = ahat[i];
+  const double ah = (i <= lmax) ? ahat[i] : ahat[i] * wpos;
   sx *= ah;
   sy *= ah;
   if (i <= lmax) {
@@ -1095,9 +1097,15 @@ int legendre_build_tables(nusht_plan_t p, cudaStream_t s) {
   NUSHT_TRY(dev_alloc((void**)&t.items, std::max<size_t>(1, items.size()) * 4, &p->bytes));
   if (!items.empty())
     NUSHT_CUDA(cudaMemcpyAsync(t.items, items.data(), items.size() * 4, cudaMemcpyHostToDevice, s));
-  // the work list is on the device now; the table kernel reads it
-  // recurrence table (opts.legendre_table = 1) when it fits in half the free memory
-  if (p->opts.legendre_table > 0 && t.nitems > 0) {
+  // the work list is on the device now; the table kernel reads it.
+  // Recurrence table when it fits in half the free memory: with
+  // opts.legendre_table = 1, and by default for standalone mixed plans (the
+  // per-call FP64 recurrence is then most of a mixed call; its table is a
+  // float per triple, 59 GB at lmax 4095) unless the caller asked for the
+  // double-float per-call recurrence.
+  const bool want_tab = p->opts.legendre_table > 0 ||
+                        (p->opts.legendre_table == 0 && p->precision == NUSHT_MIXED && p->has_nufft && !fastrec);
+  if (want_tab && t.nitems > 0) {
     const bool df = p->precision == NUSHT_FP64;
     const size_t es = df ? sizeof(float2) : sizeof(float);
     std::vector<int64_t> off(items.size() + 1, 0);
@@ -1185,7 +1193,7 @@ int legendre_synth(nusht_plan_t p, const void* d_alm, cudaStream_t s) {
   return NUSHT_OK;
 }
 
-int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
+int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s, double wpos) {
   const int64_t nalm = p->nalm;
   const bool fastrec = p->leg.cdf != nullptr;
   LegArgs a = make_args(p);
@@ -1198,13 +1206,14 @@ int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
         legendre_adj_tab_k<true><<<(nitems + 3) / 4, 128, 0, s>>>(a, p->leg.tab_off, (const float2*)p->leg.tab,
                                                                    p->Ghat, p->partial, nitems, nalm);
       adj_reduce_df_k<<<nb, tb, 0, s>>>((const float4*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
-                                        p->leg.pole_norm, (const double2*)p->Ghat, p->lmax, p->sz.M, (double2*)d_alm);
+                                        p->leg.pole_norm, (const double2*)p->Ghat, p->lmax, p->sz.M, wpos,
+                                        (double2*)d_alm);
     } else {
       if (nitems > 0)
         legendre_adj_tab_k<false><<<(nitems + 3) / 4, 128, 0, s>>>(a, p->leg.tab_off, (const float*)p->leg.tab,
                                                                     p->Ghat, p->partial, nitems, nalm);
       adj_reduce_k<float><<<nb, tb, 0, s>>>((const float2*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
-                                            p->leg.pole_norm, (const float2*)p->Ghat, p->lmax, p->sz.M,
+                                            p->leg.pole_norm, (const float2*)p->Ghat, p->lmax, p->sz.M, wpos,
                                             (float2*)d_alm);
     }
   } else if (p->precision == NUSHT_FP64 && !p->opts.fp64_contraction) {
@@ -1218,13 +1227,14 @@ int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
                                                                   nitems, nalm);
     }
     adj_reduce_df_k<<<nb, tb, 0, s>>>((const float4*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
-                                      p->leg.pole_norm, (const double2*)p->Ghat, p->lmax, p->sz.M, (double2*)d_alm);
+                                      p->leg.pole_norm, (const double2*)p->Ghat, p->lmax, p->sz.M, wpos,
+                                      (double2*)d_alm);
   } else if (p->precision == NUSHT_FP64) {
     if (nitems > 0)
       legendre_adj_k<double><<<(nitems + 3) / 4, 128, 0, s>>>(a, (const double2*)p->Ghat, (double2*)p->partial, nitems,
                                                               nalm);
     adj_reduce_k<double><<<nb, tb, 0, s>>>((const double2*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
-                                           p->leg.pole_norm, (const double2*)p->Ghat, p->lmax, p->sz.M,
+                                           p->leg.pole_norm, (const double2*)p->Ghat, p->lmax, p->sz.M, wpos,
                                            (double2*)d_alm);
   } else {
     if (nitems > 0)
@@ -1237,7 +1247,8 @@ int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s) {
                                                                nitems, nalm);
     }
     adj_reduce_k<float><<<nb, tb, 0, s>>>((const float2*)p->partial, p->leg.blocks_per_m, nalm, p->leg.ahat,
-                                          p->leg.pole_norm, (const float2*)p->Ghat, p->lmax, p->sz.M, (float2*)d_alm);
+                                          p->leg.pole_norm, (const float2*)p->Ghat, p->lmax, p->sz.M, wpos,
+                                          (float2*)d_alm);
   }
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
@@ -1259,29 +1270,34 @@ namespace nusht {
 namespace {
 
 constexpr int NA_LMAX = 255;   // largest lmax accepted
-constexpr int NA_SLOTS = 16;   // partial-sum slots per coefficient
+constexpr int NA_SLOTS = 16;   // partial-sum slots per coefficient at the largest size
 constexpr int NA_NALM_MAX = (NA_LMAX + 1) * (NA_LMAX + 2) / 2;
+constexpr int NA_CAP = NA_SLOTS * NA_NALM_MAX;  // complex entries of the array
+constexpr int NA_CHUNK = 32 * LEG_K;            // points per warp pass
+constexpr int NA_SLOTS_MAX = 4096;              // bound on the slots of small problems
 
-// NA_SLOTS x NA_NALM_MAX complex partial sums = 16 x 33024 x 16 B = 8.45 MB.
-// Every device that loads this library holds it until the process exits.
-static __device__ __align__(256) double2 g_noalloc_partial[NA_SLOTS * NA_NALM_MAX];
+// NA_CAP complex partial sums = 16 x 33024 x 16 B = 8.45 MB.  Every device
+// that loads this library holds it until the process exits.
+static __device__ __align__(256) double2 g_noalloc_partial[NA_CAP];
 
+// One warp per (order m, slot); slot s takes the point chunks s, s + nslots,
+// ... and writes its partial sums to partial[s][l, m] (nslots x nalm <= NA_CAP).
 __global__ void __launch_bounds__(128) direct_adj_k(int L, int mmax, int64_t npts, const double* __restrict__ pts,
                                                     const double* __restrict__ f, double2* __restrict__ partial,
-                                                    int nalm) {
+                                                    int nalm, int nslots) {
   const int lane = threadIdx.x & 31;
   const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (it >= (mmax + 1) * NA_SLOTS) return;
-  const int m = it / NA_SLOTS, slot = it % NA_SLOTS;
+  if (it >= (mmax + 1) * nslots) return;
+  const int m = it / nslots, slot = it % nslots;
   const int mb = mbase_of(L, m);
   // Pbar_mm / sin^m = (-1)^m sqrt(prod_{i<=m} (2i+1)/(2i) / (4 pi))
   double cmm = 0.28209479177387814;  // 1/sqrt(4 pi)
   for (int i = 1; i <= m; ++i) cmm *= sqrt((2.0 * i + 1.0) / (2.0 * i));
   if (m & 1) cmm = -cmm;
   double2* out = partial + (size_t)slot * nalm + mb;
-  const int64_t chunk = 32 * LEG_K;
+  const int64_t chunk = NA_CHUNK;
   bool first = true;
-  for (int64_t c0 = (int64_t)slot * chunk; first || c0 < npts; c0 += (int64_t)NA_SLOTS * chunk) {
+  for (int64_t c0 = (int64_t)slot * chunk; first || c0 < npts; c0 += (int64_t)nslots * chunk) {
     Chain ch[LEG_K];
     double2 S[LEG_K];
 #pragma unroll
@@ -1410,11 +1426,12 @@ __global__ void __launch_bounds__(128) direct_adj_k(int L, int mmax, int64_t npt
   }
 }
 
-__global__ void direct_adj_reduce_k(const double2* __restrict__ partial, int nalm, int lmax, double2* __restrict__ out) {
+__global__ void direct_adj_reduce_k(const double2* __restrict__ partial, int nalm, int nslots, int lmax,
+                                    double2* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nalm) return;
   double sx = 0.0, sy = 0.0;
-  for (int s = 0; s < NA_SLOTS; ++s) {
+  for (int s = 0; s < nslots; ++s) {
     const double2 v = partial[(size_t)s * nalm + i];
     sx += v.x;
     sy += v.y;
@@ -1422,11 +1439,6 @@ __global__ void direct_adj_reduce_k(const double2* __restrict__ partial, int nal
   if (i <= lmax) sy = 0.0;  // m = 0: real
   out[i] = make_double2(sx, sy);
 }
-
-// device address of g_noalloc_partial, looked up once per device
-constexpr int NA_MAX_DEVICES = 64;
-static void* g_noalloc_ptr[NA_MAX_DEVICES] = {};
-static std::mutex g_noalloc_mutex;
 
 }  // namespace
 }  // namespace nusht
@@ -1440,25 +1452,27 @@ extern "C" int nusht_adjoint_direct_noalloc(int lmax, int mmax, int64_t npts, co
   if (npts < 0) return set_error(NUSHT_EINVAL, "nusht_adjoint_direct_noalloc: npts < 0");
   if (!d_alm || (npts > 0 && (!d_pts || !d_map)))
     return set_error(NUSHT_EINVAL, "nusht_adjoint_direct_noalloc: null pointer");
-  int dev = 0;
-  NUSHT_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= NA_MAX_DEVICES) return set_error(NUSHT_EDEVICE, "nusht_adjoint_direct_noalloc: device index");
+  // The array's device address in the current device's context.  Host code
+  // cannot use the symbol itself (it names a host-side shadow), so it is
+  // looked up here on every call, with the caller's device current: a cached
+  // address would go stale after cudaDeviceReset or under another context.
+  // The lookup is cheap once the library's device code is loaded; the first
+  // call on a device loads it.
   void* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> g(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-      void* ptr = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partial);
-      if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_noalloc_partial)");
-      g_noalloc_ptr[dev] = ptr;
-    }
-    scratch = g_noalloc_ptr[dev];
-  }
+  cudaError_t e = cudaGetSymbolAddress(&scratch, g_noalloc_partial);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_noalloc_partial)");
   const int nalm = (mmax + 1) * (lmax + 1) - mmax * (mmax + 1) / 2;
+  // slots: as many as the array holds for this nalm, no more than there are
+  // point chunks (at least one, whose first pass writes the zeros of an
+  // empty point set)
+  const int64_t nchunks = (npts + NA_CHUNK - 1) / NA_CHUNK;
+  const int nslots = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)NA_CAP / nalm, nchunks,
+                                                                   (int64_t)NA_SLOTS_MAX}));
   cudaStream_t s = (cudaStream_t)stream;
-  const int nwarps = (mmax + 1) * NA_SLOTS;
-  direct_adj_k<<<(nwarps + 3) / 4, 128, 0, s>>>(lmax, mmax, npts, d_pts, d_map, (double2*)scratch, nalm);
-  direct_adj_reduce_k<<<(nalm + 255) / 256, 256, 0, s>>>((const double2*)scratch, nalm, lmax, (double2*)d_alm);
+  const int nwarps = (mmax + 1) * nslots;
+  direct_adj_k<<<(nwarps + 3) / 4, 128, 0, s>>>(lmax, mmax, npts, d_pts, d_map, (double2*)scratch, nalm, nslots);
+  direct_adj_reduce_k<<<(nalm + 255) / 256, 256, 0, s>>>((const double2*)scratch, nalm, nslots, lmax,
+                                                          (double2*)d_alm);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }

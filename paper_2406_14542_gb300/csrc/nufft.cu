@@ -3,7 +3,8 @@
 // psi(z) = exp(beta (sqrt(1 - z^2) - 1)), |z| <= 1, of width w fine-grid cells:
 //   * point set-up: fold (theta, phi) onto [0, 2 pi)^2, first tap and
 //     fractional offset in double, bin sort (tiles of bin x bin cells, bin chosen
-//     by the plan: 32 by default, or by the autotuner),
+//     by the plan: 16 for FP64 plans with w <= 17 and float-pair arithmetic,
+//     32 otherwise, or by the autotuner),
 //     FP64 kernel values per point;
 //   * deconv_pad / deconv_trunc: divide by the kernel's Fourier transform,
 //     zero-pad / truncate between the theta spectrum [m][k] and the fine
@@ -254,8 +255,9 @@ __device__ __forceinline__ void deflect(double th, double ph, double gth, double
 
 // ---------------------------------------------------------------------------
 // interpolation (type 2): one thread per sorted point; with GRAD the
-// derivatives of the kernel give d/dtheta and d/dphi, written out or, with
-// ptg, turned into the deflected position (pointing)
+// derivatives of the kernel give d/dtheta and d/dphi, written out, or with
+// ptg turned into the deflected position (pointing), or with gpts multiplied
+// by the cotangent cot (the position gradient of a loss, interleaved)
 // ---------------------------------------------------------------------------
 template <typename T, bool GRAD>
 __global__ void __launch_bounds__(128) interp_k(const T* __restrict__ grid, int64_t stride, int n1, int n2, int w,
@@ -263,7 +265,8 @@ __global__ void __launch_bounds__(128) interp_k(const T* __restrict__ grid, int6
                                                 const double* __restrict__ psi, const float* __restrict__ offf,
                                                 const double* __restrict__ xy, const int* __restrict__ perm,
                                                 int64_t npts, T* __restrict__ out, T* __restrict__ dth,
-                                                T* __restrict__ dph, double* __restrict__ ptg) {
+                                                T* __restrict__ dph, double* __restrict__ ptg,
+                                                const T* __restrict__ cot, double* __restrict__ gpts) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= npts) return;
   const int i1 = cell[2 * s], i2 = cell[2 * s + 1];
@@ -354,6 +357,12 @@ __global__ void __launch_bounds__(128) interp_k(const T* __restrict__ grid, int6
     const T a2 = (T)((double)n2 / (w * 3.14159265358979323846));
     if (ptg) {
       deflect(xy[2 * s], xy[2 * s + 1], (double)(g1 * a1), (double)(g2 * a2), ptg + 2 * (int64_t)i);
+      return;
+    }
+    if (gpts) {
+      const double c = (double)cot[i];
+      gpts[2 * (int64_t)i] = c * (double)(g1 * a1);
+      gpts[2 * (int64_t)i + 1] = c * (double)(g2 * a2);
       return;
     }
     if (dth) dth[i] = g1 * a1;
@@ -540,7 +549,8 @@ __device__ __forceinline__ float2 es_dfac(float oh, float ol, int a, float2 beta
 //   d f / d theta = (n1 / (W pi)) sum_a psi1'_a sum_b psi2_b u_ab,
 //   d f / d phi   = (n2 / (W pi)) sum_a psi1_a sum_b psi2'_b u_ab,
 // psi' = psi * es_dfac.  Writes the derivatives, or with ptg the deflected
-// position (pointing, App. C).
+// position (pointing, App. C), or with gpts the derivatives times the
+// cotangent cot (interleaved, the position gradient of a loss).
 template <int W>
 __global__ void __launch_bounds__(IDF_THREADS) interp_grad_df_k(const double* __restrict__ grid, int64_t stride,
                                                                 int n1, int n2, int nb2, int binsz,
@@ -550,7 +560,9 @@ __global__ void __launch_bounds__(IDF_THREADS) interp_grad_df_k(const double* __
                                                                 const double* __restrict__ xy,
                                                                 const int* __restrict__ perm, float2 beta,
                                                                 double* __restrict__ dth, double* __restrict__ dph,
-                                                                double* __restrict__ ptg) {
+                                                                double* __restrict__ ptg,
+                                                                const double* __restrict__ cot,
+                                                                double* __restrict__ gpts) {
   extern __shared__ unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);
   const int tw = binsz + W - 1;
@@ -602,6 +614,10 @@ __global__ void __launch_bounds__(IDF_THREADS) interp_grad_df_k(const double* __
     const int i = perm[s];
     if (ptg) {
       deflect(xy[2 * s], xy[2 * s + 1], gth, gph, ptg + 2 * (int64_t)i);
+    } else if (gpts) {
+      const double c = cot[i];
+      gpts[2 * (int64_t)i] = c * gth;
+      gpts[2 * (int64_t)i + 1] = c * gph;
     } else {
       if (dth) dth[i] = gth;
       if (dph) dph[i] = gph;
@@ -738,9 +754,10 @@ void launch_interp_df(int nsub, size_t sm, cudaStream_t s, const double* grid, i
 template <int W>
 void launch_interp_grad_df(int nsub, size_t sm, cudaStream_t s, const double* grid, int64_t stride, int n1, int n2,
                            int nb2, int binsz, const int* sub, const int* cell, const float2* psi, const double* xy,
-                           const int* perm, float2 beta, double* dth, double* dph, double* ptg) {
+                           const int* perm, float2 beta, double* dth, double* dph, double* ptg, const double* cot,
+                           double* gpts) {
   interp_grad_df_k<W><<<nsub, IDF_THREADS, sm, s>>>(grid, stride, n1, n2, nb2, binsz, sub, cell, psi, xy, perm, beta,
-                                                    dth, dph, ptg);
+                                                    dth, dph, ptg, cot, gpts);
 }
 
 template <int W>
@@ -1101,7 +1118,7 @@ int interp(nusht_plan_t p, void* d_map, cudaStream_t s) {
   } else if (p->precision == NUSHT_FP64)
     interp_k<double, false><<<nb, tb, 0, s>>>((const double*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
                                               p->pts.cell, p->pts.psi, nullptr, nullptr, p->pts.perm, n,
-                                              (double*)d_map, nullptr, nullptr, nullptr);
+                                              (double*)d_map, nullptr, nullptr, nullptr, nullptr, nullptr);
   else
     NUSHT_W_DISPATCH(z.w, launch_interp_f, nb, s, (const float*)p->fine, stride, z.n1, z.n2, (float)z.beta,
                      p->pts.cell, p->pts.off, p->pts.perm, n, (float*)d_map);
@@ -1111,7 +1128,8 @@ int interp(nusht_plan_t p, void* d_map, cudaStream_t s) {
 
 // FP64 plans with the double-float NUFFT: derivatives (or the pointing) from
 // the bin tiles and the plan's kernel-value table
-static int interp_grad_df(nusht_plan_t p, double* d_dth, double* d_dph, double* d_ptg, cudaStream_t s) {
+static int interp_grad_df(nusht_plan_t p, double* d_dth, double* d_dph, double* d_ptg, const double* cot,
+                          double* gpts, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const int64_t stride = 2 * (z.n2 / 2 + 1);
   const int binsz = p->pts.bin > 0 ? p->pts.bin : 32;
@@ -1120,27 +1138,29 @@ static int interp_grad_df(nusht_plan_t p, double* d_dth, double* d_dph, double* 
   const float2 beta = make_float2(bh, (float)(z.beta - (double)bh));
   NUSHT_W_DISPATCH(z.w, launch_interp_grad_df, p->pts.nsub, (size_t)tw * tw * 8, s, (const double*)p->fine, stride,
                    z.n1, z.n2, p->pts.nbins2, binsz, p->pts.sub, p->pts.cell,
-                   reinterpret_cast<const float2*>(p->pts.psi), p->pts.xy, p->pts.perm, beta, d_dth, d_dph, d_ptg);
+                   reinterpret_cast<const float2*>(p->pts.psi), p->pts.xy, p->pts.perm, beta, d_dth, d_dph, d_ptg,
+                   cot, gpts);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
 
-int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, cudaStream_t s) {
+int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, const void* cot, double* gpts, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const int64_t n = p->pts.npts;
   if (n == 0) return NUSHT_OK;
-  if (nufft_df(p) && p->pts.nsub > 0) return interp_grad_df(p, (double*)d_dth, (double*)d_dph, nullptr, s);
+  if (nufft_df(p) && p->pts.nsub > 0)
+    return interp_grad_df(p, (double*)d_dth, (double*)d_dph, nullptr, (const double*)cot, gpts, s);
   const int64_t stride = 2 * (z.n2 / 2 + 1);
   const int tb = 128;
   const int nb = (int)((n + tb - 1) / tb);
   if (p->precision == NUSHT_FP64)
     interp_k<double, true><<<nb, tb, 0, s>>>((const double*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
                                              p->pts.cell, nullptr, nullptr, p->pts.xy, p->pts.perm, n, nullptr,
-                                             (double*)d_dth, (double*)d_dph, nullptr);
+                                             (double*)d_dth, (double*)d_dph, nullptr, (const double*)cot, gpts);
   else
     interp_k<float, true><<<nb, tb, 0, s>>>((const float*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
                                             p->pts.cell, nullptr, nullptr, p->pts.xy, p->pts.perm, n, nullptr,
-                                            (float*)d_dth, (float*)d_dph, nullptr);
+                                            (float*)d_dth, (float*)d_dph, nullptr, (const float*)cot, gpts);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
@@ -1149,18 +1169,18 @@ int interp_pointing(nusht_plan_t p, double* d_ptg, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const int64_t n = p->pts.npts;
   if (n == 0) return NUSHT_OK;
-  if (nufft_df(p) && p->pts.nsub > 0) return interp_grad_df(p, nullptr, nullptr, d_ptg, s);
+  if (nufft_df(p) && p->pts.nsub > 0) return interp_grad_df(p, nullptr, nullptr, d_ptg, nullptr, nullptr, s);
   const int64_t stride = 2 * (z.n2 / 2 + 1);
   const int tb = 128;
   const int nb = (int)((n + tb - 1) / tb);
   if (p->precision == NUSHT_FP64)
     interp_k<double, true><<<nb, tb, 0, s>>>((const double*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
                                              p->pts.cell, nullptr, nullptr, p->pts.xy, p->pts.perm, n, nullptr,
-                                             nullptr, nullptr, d_ptg);
+                                             nullptr, nullptr, d_ptg, nullptr, nullptr);
   else
     interp_k<float, true><<<nb, tb, 0, s>>>((const float*)p->fine, stride, z.n1, z.n2, z.w, (float)z.beta, z.beta,
                                             p->pts.cell, nullptr, nullptr, p->pts.xy, p->pts.perm, n, nullptr,
-                                            nullptr, nullptr, d_ptg);
+                                            nullptr, nullptr, d_ptg, nullptr, nullptr);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }

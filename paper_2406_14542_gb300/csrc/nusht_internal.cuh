@@ -201,13 +201,17 @@ void free_points(nusht_plan_t p);
 // Legendre (legendre.cu)
 int legendre_build_tables(nusht_plan_t p, cudaStream_t s);
 int legendre_synth(nusht_plan_t p, const void* d_alm, cudaStream_t s);
-int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s);
+// wpos: factor of the m > 0 coefficients (1: the adjoint; 2: the gradient of a
+// real loss with respect to complex a_lm)
+int legendre_adjoint(nusht_plan_t p, void* d_alm, cudaStream_t s, double wpos = 1.0);
 
 // NUFFT steps (nufft.cu)
 int deconv_pad(nusht_plan_t p, cudaStream_t s);
 int deconv_trunc(nusht_plan_t p, cudaStream_t s);
 int interp(nusht_plan_t p, void* d_map, cudaStream_t s);
-int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, cudaStream_t s);
+// d/dtheta and d/dphi at the points (either output may be NULL), or with
+// gpts = (cot_i d/dtheta, cot_i d/dphi) interleaved
+int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, const void* cot, double* gpts, cudaStream_t s);
 int interp_pointing(nusht_plan_t p, double* d_ptg, cudaStream_t s);
 int spread(nusht_plan_t p, const void* d_map, cudaStream_t s);
 int spread_smem_optin();

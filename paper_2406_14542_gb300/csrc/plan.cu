@@ -517,10 +517,13 @@ int nusht_synth(nusht_plan_t p, const void* d_alm, void* d_map, nusht_stream_t s
   return NUSHT_OK;
 }
 
-int nusht_adjoint(nusht_plan_t p, const void* d_map, void* d_alm, nusht_stream_t stream) {
+}  // extern "C"
+
+// N^dagger, F^dagger, D^dagger, S^dagger; the m > 0 coefficients are scaled
+// by wpos (1: the adjoint, 2: the gradient convention of nusht_adjoint_grad)
+static int adjoint_chain(nusht_plan_t p, const void* d_map, void* d_alm, cudaStream_t s, double wpos) {
   if (!p) return set_error(NUSHT_EINVAL, "plan is NULL");
   if (!d_alm || (!d_map && p->pts.npts > 0)) return set_error(NUSHT_EINVAL, "null alm or map pointer");
-  cudaStream_t s = (cudaStream_t)stream;
   const bool prof = p->opts.profile != 0;
   if (prof) NUSHT_TRY(ev_init(p->ev_adj));
   p->last_stream = s;
@@ -537,9 +540,19 @@ int nusht_adjoint(nusht_plan_t p, const void* d_map, void* d_alm, nusht_stream_t
   NUSHT_TRY(theta_fft(p, p->Ghat, p->Ghat, 1, s));
   STAGE(p->ev_adj, 4);
   // D^dagger fused into S^dagger's load: fold, then adjoint Legendre sums
-  NUSHT_TRY(legendre_adjoint(p, d_alm, s));
+  NUSHT_TRY(legendre_adjoint(p, d_alm, s, wpos));
   STAGE(p->ev_adj, 5);
   return NUSHT_OK;
+}
+
+extern "C" {
+
+int nusht_adjoint(nusht_plan_t p, const void* d_map, void* d_alm, nusht_stream_t stream) {
+  return adjoint_chain(p, d_map, d_alm, (cudaStream_t)stream, 1.0);
+}
+
+int nusht_adjoint_grad(nusht_plan_t p, const void* d_cot, void* d_galm, nusht_stream_t stream) {
+  return adjoint_chain(p, d_cot, d_galm, (cudaStream_t)stream, 2.0);
 }
 
 int nusht_synth_grad(nusht_plan_t p, const void* d_alm, void* d_dtheta, void* d_dphi, nusht_stream_t stream) {
@@ -551,7 +564,21 @@ int nusht_synth_grad(nusht_plan_t p, const void* d_alm, void* d_dtheta, void* d_
   NUSHT_TRY(theta_fft(p, p->G, p->Ghat, -1, s));
   NUSHT_TRY(deconv_pad(p, s));
   NUSHT_TRY(fine_fft_c2r(p, s));
-  NUSHT_TRY(interp_grad(p, d_dtheta, d_dphi, s));
+  NUSHT_TRY(interp_grad(p, d_dtheta, d_dphi, nullptr, nullptr, s));
+  return NUSHT_OK;
+}
+
+int nusht_synth_grad_pts(nusht_plan_t p, const void* d_alm, const void* d_cot, double* d_gpts,
+                         nusht_stream_t stream) {
+  if (!p) return set_error(NUSHT_EINVAL, "plan is NULL");
+  if (!d_alm || (p->pts.npts > 0 && (!d_cot || !d_gpts))) return set_error(NUSHT_EINVAL, "null pointer");
+  if (!p->has_legendre || !p->has_nufft) return set_error(NUSHT_EUNSUPPORTED, "needs a standalone plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  NUSHT_TRY(legendre_synth(p, d_alm, s));
+  NUSHT_TRY(theta_fft(p, p->G, p->Ghat, -1, s));
+  NUSHT_TRY(deconv_pad(p, s));
+  NUSHT_TRY(fine_fft_c2r(p, s));
+  NUSHT_TRY(interp_grad(p, nullptr, nullptr, d_cot, d_gpts, s));
   return NUSHT_OK;
 }
 

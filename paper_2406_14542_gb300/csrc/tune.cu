@@ -9,11 +9,13 @@
 // precision, lmax, mmax, eps decade and point-count power of two;
 // opts.tune = 2 reuses the cached sigma.
 //
-// opts.tune = 0: bin edge 32 cells.  opts.tune = 1 (search): the plan sorts
+// opts.tune = 0: bin edge 16 cells for FP64 plans with kernel width <= 17 and
+// float-pair arithmetic (fp64_contraction = 0), 32 cells otherwise.
+// opts.tune = 1 (search): the plan sorts
 // its points for each candidate bin edge (16, 32, 64 cells), times one
 // spreading + interpolation pass with CUDA events on the plan's own data, keeps
 // the fastest and records it in a cache file.  opts.tune = 2 (cached): the
-// cached choice for the same key when present, else 32.  Key: device name,
+// cached choice for the same key when present, else the untuned default.  Key: device name,
 // precision, lmax, kernel width, fine grid and the point count's power of two.
 // Cache: $NUSHT_TUNE_CACHE, else $HOME/.cache/nusht_tune.txt, one
 // "key bin" line per entry (the last entry of a key wins).

@@ -62,7 +62,7 @@ def test_autograd_alm_matches_adjoint_and_fd(env):
     assert (torch.linalg.norm(g - c) / torch.linalg.norm(c)).item() <= 1e-12
     # central differences along a random complex direction
     d = torch.from_numpy(W.alm_gaussian(L, seed=99)).cuda()
-    d[: L + 1] += 1j * torch.randn(L + 1, dtype=torch.float64, device="cuda")
+    d[: L + 1] += 1j * torch.from_numpy(np.random.default_rng(98).standard_normal(L + 1)).cuda()
     h = 1e-6
 
     def lossat(x):
@@ -144,3 +144,36 @@ def test_differentiable_gl2047(env):
     fd = (lossat(alm.detach() + hh * d) - lossat(alm.detach() - hh * d)) / (2 * hh)
     an = torch.sum((torch.conj(ga) * d).real).item()
     assert abs(fd - an) <= 1e-6 * abs(an)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_gradient_entry_points(env, prec, tol):
+    """nusht_adjoint_grad = the adjoint with the m > 0 entries doubled, and
+    nusht_synth_grad_pts = the cotangent times nusht_synth_grad, through the
+    C ABI (the autograd backward calls only these two)."""
+    torch, nu = env
+    L, a, pts = W.workload("uniform63")
+    cd = torch.complex128 if prec == "fp64" else torch.complex64
+    rd = torch.float64 if prec == "fp64" else torch.float32
+    plan = nu.Plan(L, torch.from_numpy(pts).cuda(), eps=1e-10 if prec == "fp64" else 1e-5, precision=prec,
+                   deterministic=True)
+    g = torch.from_numpy(np.random.default_rng(4).standard_normal(pts.shape[0])).to(rd).cuda()
+    ga = plan.adjoint_grad(g).cpu().numpy().astype(np.complex128)
+    c = plan.adjoint(g).cpu().numpy().astype(np.complex128)
+    c[L + 1:] *= 2.0
+    assert rel(ga, c) <= tol
+    assert np.all(ga[: L + 1].imag == 0)
+    alm = torch.from_numpy(a).to(cd).cuda()
+    gp = plan.synth_grad_pts(alm, g).cpu().numpy()
+    dth, dph = plan.synth_grad(alm)
+    gd = g.double().cpu().numpy()
+    assert rel(gp[:, 0], gd * dth.double().cpu().numpy()) <= tol
+    assert rel(gp[:, 1], gd * dph.double().cpu().numpy()) <= tol
+    # against the oracle: w_m (Y^dagger g) and g * analytic derivative
+    ref = oracle.adjoint(gd, pts, L)
+    ref[L + 1:] *= 2.0
+    assert rel(ga, ref) <= (1e-10 if prec == "fp64" else 1e-5)
+    rth, rph = oracle.synth_grad(a, pts, L)
+    assert rel(gp[:, 0], gd * rth) <= (1e-8 if prec == "fp64" else 1e-4)
+    assert rel(gp[:, 1], gd * rph) <= (1e-8 if prec == "fp64" else 1e-4)
+    plan.close()

@@ -71,12 +71,15 @@ def test_batch_recapture_and_dot(env):
     f2 = bp.synth(ad)  # fresh output buffers -> re-capture
     for x, y in zip(f1, f2):
         assert torch.equal(x, y)
-    ys = [torch.randn(p.shape[0], device="cuda") for p in pts]
+    gen = torch.Generator(device="cuda").manual_seed(6)
+    ys = [torch.randn(p.shape[0], device="cuda", generator=gen) for p in pts]
     cs = bp.adjoint(ys)
     for l, a, f, y, c in zip(ls, alms, f1, ys, cs):
         lhs = float(torch.dot(y.double(), f.double()))
         rhs = oracle.alm_dot(c.cpu().numpy().astype(np.complex128), a.astype(np.complex128), l)
-        assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+        # rounding in either side is bounded by ~eps |y| |f|; <y, f> itself
+        # can cancel to |y| |f| / sqrt(N), so the bound is not relative to it
+        assert abs(lhs - rhs) <= 1e-6 * float(torch.linalg.norm(y.double()) * torch.linalg.norm(f.double()))
 
 
 @pytest.mark.parametrize("tc,path", [(0, 2), (-1, 1)])
@@ -100,7 +103,8 @@ def test_batch64_members_against_oracle(env, tc, path):
         sel = W.subset(pts[i].shape[0], 1500, seed=i)
         ref = oracle.synth(alms[i].astype(np.complex128), pts[i][sel], ls[i])
         assert oracle.eps_eff(ref, outs[i].double().cpu().numpy()[sel]) <= TOL, (i, ls[i])
-    ys = [torch.randn(p.shape[0], device="cuda") for p in pts]
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    ys = [torch.randn(p.shape[0], device="cuda", generator=gen) for p in pts]
     cs = bp.adjoint(ys)
     bp.status()
     for i in check[:3]:
