@@ -144,7 +144,11 @@ typedef struct {
                          run as this library's double-float kernels (one line per CTA in
                          shared memory, ~2^-47 relative per operation) when every length is
                          at most 14336; longer lengths use cuFFT's FP64 transforms;
-                         -1 = cuFFT's FP64 transforms always.  Mixed plans use cuFFT FP32. */
+                         -1 = cuFFT's FP64 transforms always.  Mixed plans: 0 (default) or
+                         -1 = cuFFT FP32 (2D plans, separate deconvolution); 1 = this
+                         library's FP32 line kernels for the fine grid (deconvolution fused
+                         into the column pass; lengths up to 28672), slower than cuFFT on
+                         GB300 and kept for comparison. */
   int reserved[2];
 } nusht_opts;
 
@@ -372,6 +376,16 @@ NUSHT_API int nusht_batch_status(nusht_batch_t p, nusht_stream_t stream);
  * argument.
  */
 NUSHT_API int nusht_batch_path(nusht_batch_t p, int bucket);
+
+/*
+ * nusht_batch_schedule -- the tensor-core contraction schedule of bucket
+ * `bucket`: how many 16-degree chunks are accumulated into one tensor-memory
+ * partial set before they are folded into the FP32 register sums, for the
+ * synthesis and the adjoint (2, 4 or 8; 4 unless opts.tune chose, 0 for a
+ * bucket not on the tensor-core path).  Either output may be NULL.
+ * No counterpart in the paper: the schedule of this library's kernel.
+ */
+NUSHT_API int nusht_batch_schedule(nusht_batch_t p, int bucket, int* chunks_synth, int* chunks_adjoint);
 
 /* nusht_destroy -- free the plan and its device memory (NULL-safe). */
 NUSHT_API int nusht_destroy(nusht_plan_t p);

@@ -38,7 +38,7 @@ EXPORTS = ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_
            "nusht_strerror", "nusht_last_error", "nusht_version", "nusht_adjoint_direct_noalloc",
            "nusht_plan_many", "nusht_synth_many", "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info",
            "nusht_plan_bin", "nusht_batch_status", "nusht_batch_path", "nusht_pointing", "nusht_adjoint_grad",
-           "nusht_synth_grad_pts")
+           "nusht_synth_grad_pts", "nusht_batch_schedule")
 
 
 class NushtError(RuntimeError):
@@ -108,6 +108,8 @@ def load(path: str | None = None):
         lib.nusht_plan_bin.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         lib.nusht_batch_status.argtypes = [vp, vp]
         lib.nusht_batch_path.argtypes = [vp, ctypes.c_int]
+        lib.nusht_batch_schedule.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int)]
         lib.nusht_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64)]
         lib.nusht_strerror.argtypes = [ctypes.c_int]
@@ -119,7 +121,7 @@ def load(path: str | None = None):
                      "nusht_adjoint_direct_noalloc", "nusht_plan_many", "nusht_synth_many",
                      "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info", "nusht_plan_bin",
                      "nusht_batch_status", "nusht_batch_path", "nusht_pointing", "nusht_adjoint_grad",
-                     "nusht_synth_grad_pts"):
+                     "nusht_synth_grad_pts", "nusht_batch_schedule"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -458,7 +460,8 @@ class BatchPlan:
     float64 (N_b, 2) tensor; each lmax <= 4095."""
 
     def __init__(self, lmaxs, pts_list, eps: float = 1e-5, sigma: float = 0.0, legendre_table: int = 0,
-                 tune: int = 0, tensor_cores: int = 0, deterministic: bool = False, stream=None):
+                 tune: int = 0, tensor_cores: int = 0, deterministic: bool = False, fft_kernels: int = 0,
+                 stream=None):
         import torch
 
         self.lib = load()
@@ -473,7 +476,7 @@ class BatchPlan:
         narr = (ctypes.c_int64 * n)(*self.npts)
         parr = (ctypes.c_void_p * n)(*[p.data_ptr() if p.numel() else 0 for p in self.pts])
         o = _opts(sigma, legendre_table=legendre_table, tune=tune, tensor_cores=tensor_cores,
-                  deterministic=deterministic)
+                  deterministic=deterministic, fft_kernels=fft_kernels)
         h = ctypes.c_void_p()
         _check(self.lib.nusht_plan_many(ctypes.byref(h), n, larr, narr, parr, float(eps), MIXED, ctypes.byref(o),
                                         _stream_ptr(stream)), "nusht_plan_many")
@@ -486,9 +489,16 @@ class BatchPlan:
         bl = (ctypes.c_int * self.n)()
         by = ctypes.c_int64()
         _check(self.lib.nusht_batch_info(self._h, ctypes.byref(nb), of, bl, ctypes.byref(by)), "nusht_batch_info")
+        sched = []
+        for g in range(nb.value):
+            cs, ca = ctypes.c_int(), ctypes.c_int()
+            _check(self.lib.nusht_batch_schedule(self._h, g, ctypes.byref(cs), ctypes.byref(ca)),
+                   "nusht_batch_schedule")
+            sched.append((cs.value, ca.value))
         return {"nbuckets": nb.value, "bucket_of": list(of), "bucket_lmax": list(bl)[: nb.value],
                 "bytes_device": by.value,
-                "paths": [self.lib.nusht_batch_path(self._h, g) for g in range(nb.value)]}
+                "paths": [self.lib.nusht_batch_path(self._h, g) for g in range(nb.value)],
+                "schedule": sched}
 
     def status(self, stream=None):
         """Synchronise and raise if a tensor-core block of an earlier call gave

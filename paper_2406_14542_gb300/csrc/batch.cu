@@ -577,7 +577,9 @@ __global__ void __launch_bounds__(256) bucket_adj_tab_k(BucketArgs a, const int*
 // hi*hi + hi*lo + lo*hi, so a product keeps about 22 significant bits with
 // an unbiased error.  The tensor core's own accumulation adds with reduced,
 // truncating alignment, an error that grows with the number of MMAs folded
-// into one accumulator; so the chunks are taken in groups of TC_G, each group
+// into one accumulator; so the chunks are taken in groups of tcg (2, 4 or 8:
+// the bucket's degree chunks per partial accumulation, picked by the
+// autotuner with opts.tune, else 4), each group
 // into one of two partial accumulator sets (TMEM columns 0..255 and
 // 256..511, alternating), and every finished group is added in FP32 with
 // round-to-nearest into per-thread registers while the tensor core runs the
@@ -606,7 +608,7 @@ __global__ void __launch_bounds__(256) bucket_adj_tab_k(BucketArgs a, const int*
 // ---------------------------------------------------------------------------
 constexpr int TC_TILE = 128 * 8 * 4;              // one 128 x 8 fp32 operand tile
 constexpr int TC_CHUNK = 8 * TC_TILE;             // AEh AEl AOh AOl BEh BEl BOh BOl
-constexpr int TC_G = 4;                           // chunks per partial accumulation
+constexpr int TC_G = 4;                           // default chunks per partial accumulation
 constexpr uint32_t TC_COLS = 512;                 // two partial sets of D_E, D_O
 // instruction descriptor: D f32 (bits 4-5 = 1), A and B tf32 (bits 7-9,
 // 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
@@ -745,7 +747,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) bucket_tc_k(BucketArgs a, int n
                                                              const unsigned char* __restrict__ Atab,
                                                              const unsigned char* __restrict__ Bbuf,
                                                              float2* __restrict__ G, float* __restrict__ cacc,
-                                                             int* __restrict__ status, int test_giveup) {
+                                                             int* __restrict__ status, int test_giveup, int tcg) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   T6Bars* bars = reinterpret_cast<T6Bars*>(tc_smem + T6_NBUF * TC_CHUNK);
   if ((int)blockIdx.x >= nblk || *(volatile int*)status) return;
@@ -788,7 +790,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) bucket_tc_k(BucketArgs a, int n
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = bars->tslot;
-  const int ngroups = (nchunk + TC_G - 1) / TC_G;
+  const int ngroups = (nchunk + tcg - 1) / tcg;
   float acc[64];
 #pragma unroll
   for (int j = 0; j < 64; ++j) acc[j] = 0.f;
@@ -828,8 +830,8 @@ __global__ void __launch_bounds__(T6_THREADS, 1) bucket_tc_k(BucketArgs a, int n
           *abort = 1;
           break;
         }
-        const int g = c / TC_G, set = g & 1;
-        if (c % TC_G == 0 && g >= 2 &&
+        const int g = c / tcg, set = g & 1;
+        if (c % tcg == 0 && g >= 2 &&
             !mbar_wait(smem_u32(&bars->gfree[set]), (uint32_t)(((g - 2) >> 1) & 1), abort)) {
           *abort = 1;
           break;
@@ -837,7 +839,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) bucket_tc_k(BucketArgs a, int n
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t sb = smem_u32(tc_smem + s * TC_CHUNK);
         const uint32_t dE = tmem + (uint32_t)(set * 256), dO = dE + 128;
-        const uint32_t acc_on = (c % TC_G) != 0 ? 1u : 0u;
+        const uint32_t acc_on = (c % tcg) != 0 ? 1u : 0u;
         tc_mma(dE, tc_desc(sb + 0 * TC_TILE), tc_desc(sb + 4 * TC_TILE), acc_on);
         tc_mma(dE, tc_desc(sb + 0 * TC_TILE), tc_desc(sb + 5 * TC_TILE), 1u);
         tc_mma(dE, tc_desc(sb + 1 * TC_TILE), tc_desc(sb + 4 * TC_TILE), 1u);
@@ -845,7 +847,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1) bucket_tc_k(BucketArgs a, int n
         tc_mma(dO, tc_desc(sb + 2 * TC_TILE), tc_desc(sb + 7 * TC_TILE), 1u);
         tc_mma(dO, tc_desc(sb + 3 * TC_TILE), tc_desc(sb + 6 * TC_TILE), 1u);
         tc_commit(&bars->empty[s]);
-        if (c % TC_G == TC_G - 1 || c == nchunk - 1) tc_commit(&bars->gdone[set]);
+        if (c % tcg == tcg - 1 || c == nchunk - 1) tc_commit(&bars->gdone[set]);
         last = c;
       }
       // after a give-up, MMAs already issued still write tensor memory: wait
@@ -1118,6 +1120,7 @@ struct Bucket {
   unsigned char* PT = nullptr;        // adjoint A tiles, per block
   unsigned char* BS = nullptr;        // synthesis B tiles, per order (per call)
   unsigned char* BA = nullptr;        // adjoint B tiles [m][tile][group] (per call)
+  int tcg_s = TC_G, tcg_a = TC_G;     // degree chunks per partial accumulation (synthesis, adjoint)
   int64_t* pa_off = nullptr;          // byte offsets of the blocks / orders
   int64_t* pt_off = nullptr;
   int64_t* bs_off = nullptr;
@@ -1146,6 +1149,19 @@ struct nusht_batch_s {
   static constexpr int NSIDE = 4;
   cudaStream_t side[NSIDE] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[NSIDE] = {};
+  // members' NUFFT stages as one launch per stage for all members (mixed
+  // precision, FP32 fine-grid FFT kernels, atomics): the member tables, in
+  // table order (grouped by kernel width), and a per-call table of the
+  // members' map pointers in the same order
+  bool fused = false;
+  bool fused_sfft = false;             // fine-grid FFTs by the FP32 line kernels (else cuFFT per member)
+  std::vector<nusht::NufftBatch> nbw;  // one per kernel width
+  nusht::NufftBatch nball;             // every member (grid zero fill)
+  nusht::SfftLaunch sl;
+  nusht::NufftMember* d_nmem = nullptr;
+  nusht::SfftMember* d_smem = nullptr;
+  float** d_maps = nullptr;
+  std::vector<int> table_of;           // member -> position in the tables
   int* status = nullptr;  // device flag: a bounded wait in a tensor-core kernel gave up
   int test_giveup = 0;    // test hook (NUSHT_TEST_TC_GIVEUP=1): the first data wait runs out
   cudaGraphExec_t gs = nullptr, ga = nullptr;
@@ -1199,6 +1215,9 @@ void batch_free(nusht_batch_t p) {
     if (s) plan_destroy(s);
   for (auto& b : p->buckets) bucket_free(b);
   dev_free(p->status);
+  dev_free(p->d_nmem);
+  dev_free(p->d_smem);
+  dev_free(p->d_maps);
   for (int k = 0; k < nusht_batch_s::NSIDE; ++k) {
     if (p->side[k]) cudaStreamDestroy(p->side[k]);
     if (p->ev_join[k]) cudaEventDestroy(p->ev_join[k]);
@@ -1256,6 +1275,76 @@ BucketArgs bucket_args(const Bucket& b) {
   a.ring_s = b.leg->leg.ring_s;
   a.memberL = b.memberL;
   return a;
+}
+
+// Autotuner of the tensor-core contraction's schedule: the degree chunks per
+// partial accumulation (2, 4 or 8 chunks of 16 degrees into one TMEM partial
+// set before the fold into registers) for each direction, timed on the
+// bucket's own tables with zero operands (opts.tune = 1) and cached under the
+// device, the bucket lmax and member count; opts.tune = 2 takes the cached
+// choice.  Larger groups fold less often; smaller ones bound the tensor
+// core's truncating accumulation to fewer MMAs (eps_eff 1.2e-6 at 4 chunks,
+// lmax 2043).
+int tune_tc(nusht_batch_t p, Bucket& b, cudaStream_t s) {
+  std::string key = "C:" + tune_device(p->device) + ":L" + std::to_string(b.L) + ":B" + std::to_string(b.B);
+  if (p->opts.tune == 2) {
+    const int v = tune_cache_get(key);
+    const int vs = v / 10, va = v % 10;
+    if ((vs == 2 || vs == 4 || vs == 8) && (va == 2 || va == 4 || va == 8)) {
+      b.tcg_s = vs;
+      b.tcg_a = va;
+    }
+    return NUSHT_OK;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return set_error(NUSHT_ECUDA, "tuning events");
+  }
+  const BucketArgs a = bucket_args(b);
+  int st = NUSHT_OK;
+  for (int dir = 0; dir < 2 && st == NUSHT_OK; ++dir) {
+    float best = 1e30f;
+    int bestg = TC_G;
+    for (int g : {2, 4, 8}) {
+      auto launch = [&]() {
+        if (dir == 0 && b.ntc > 0)
+          bucket_tc_k<false><<<b.ntc, T6_THREADS, T6_SMEM, s>>>(a, b.ntc, b.tc_items, nullptr, b.pa_off, b.bs_off,
+                                                                nullptr, nullptr, b.ntiles, b.PA, b.BS, b.G, nullptr,
+                                                                p->status, 0, g);
+        if (dir == 1 && b.ntc_work > 0)
+          bucket_tc_k<true><<<b.ntc_work, T6_THREADS, T6_SMEM, s>>>(a, b.ntc_work, nullptr, b.tc_work, b.pt_off,
+                                                                    nullptr, b.items, b.mfirst, b.ntiles, b.PT, b.BA,
+                                                                    nullptr, b.cacc, p->status, 0, g);
+      };
+      launch();  // warm-up
+      cudaEventRecord(e0, s);
+      launch();
+      launch();
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = cuda_status(e, "tensor-core schedule tuning");
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        bestg = g;
+      }
+    }
+    if (dir == 0)
+      b.tcg_s = bestg;
+    else
+      b.tcg_a = bestg;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != NUSHT_OK) return st;
+  tune_cache_put(key, b.tcg_s * 10 + b.tcg_a);
+  return NUSHT_OK;
 }
 
 int bucket_build(nusht_batch_t p, Bucket& b, cudaStream_t s) {
@@ -1412,6 +1501,10 @@ int bucket_build(nusht_batch_t p, Bucket& b, cudaStream_t s) {
           NUSHT_CUDA(cudaGetLastError());
           NUSHT_CUDA(cudaStreamSynchronize(s));
           b.tc = true;
+          if (p->opts.tune == 1 || p->opts.tune == 2) {
+            NUSHT_CUDA(cudaMemsetAsync(b.BS, 0, std::max<int64_t>(16, bsb), s));
+            NUSHT_TRY(tune_tc(p, b, s));
+          }
           // the CUDA-core operands are not needed on this path
           dev_free(b.P);
           b.P = nullptr;
@@ -1492,7 +1585,7 @@ int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
       if (b.ntc > 0)
         bucket_tc_k<false><<<b.ntc, T6_THREADS, T6_SMEM, s>>>(a, b.ntc, b.tc_items, nullptr, b.pa_off, b.bs_off,
                                                               nullptr, nullptr, b.ntiles, b.PA, b.BS, b.G, nullptr,
-                                                              p->status, p->test_giveup);
+                                                              p->status, p->test_giveup, b.tcg_s);
     } else {
       bucket_scale_k<<<g, 256, 0, s>>>(b.L, b.B, b.memberL, b.alm_ptrs, b.leg->leg.ahat, b.atb);
     }
@@ -1505,6 +1598,22 @@ int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
     NUSHT_CUDA(cudaGetLastError());
     NUSHT_CUFFT(cufftSetStream(b.theta, s));
     NUSHT_CUFFT(cufftExecC2C(b.theta, (cufftComplex*)b.G, (cufftComplex*)b.Ghat, CUFFT_FORWARD));
+  }
+  if (p->fused) {
+    // every member at once: deconvolution and zero padding (fused into the
+    // column pass with the FP32 line kernels), the fine-grid FFT,
+    // interpolation; members' cuFFT calls on the forked streams
+    if (p->fused_sfft) {
+      NUSHT_TRY(sfft_cols_synth(p->sl, s));
+      NUSHT_TRY(sfft_rows_c2r(p->sl, s));
+    } else {
+      NUSHT_TRY(deconv_pad_many(p->nball, s));
+      NUSHT_TRY(fork(p, s));
+      for (int i = 0; i < p->nbatch; ++i) NUSHT_TRY(fine_fft_c2r(p->sub[i], p->side[i % nusht_batch_s::NSIDE]));
+      NUSHT_TRY(join(p, s));
+    }
+    for (const NufftBatch& g : p->nbw) NUSHT_TRY(interp_many(g, p->d_maps + g.map_base, s));
+    return NUSHT_OK;
   }
   NUSHT_TRY(fork(p, s));
   for (int i = 0; i < p->nbatch; ++i) {
@@ -1519,15 +1628,31 @@ int enqueue_synth(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
 }
 
 int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
-  NUSHT_TRY(fork(p, s));
-  for (int i = 0; i < p->nbatch; ++i) {
-    nusht_plan_t q = p->sub[i];
-    cudaStream_t ms = p->side[i % nusht_batch_s::NSIDE];
-    NUSHT_TRY(spread(q, d_map[i], ms));
-    NUSHT_TRY(fine_fft_r2c(q, ms));
-    NUSHT_TRY(deconv_trunc(q, ms));
+  if (p->fused) {
+    // every member at once: zero the grids, spread, row pass, column pass + truncation
+    NUSHT_TRY(zero_grids_many(p->nball, s));
+    for (const NufftBatch& g : p->nbw)
+      NUSHT_TRY(spread_many(g, const_cast<const float* const*>(p->d_maps) + g.map_base, s));
+    if (p->fused_sfft) {
+      NUSHT_TRY(sfft_rows_r2c(p->sl, s));
+      NUSHT_TRY(sfft_cols_adjoint(p->sl, s));
+    } else {
+      NUSHT_TRY(fork(p, s));
+      for (int i = 0; i < p->nbatch; ++i) NUSHT_TRY(fine_fft_r2c(p->sub[i], p->side[i % nusht_batch_s::NSIDE]));
+      NUSHT_TRY(join(p, s));
+      NUSHT_TRY(deconv_trunc_many(p->nball, s));
+    }
+  } else {
+    NUSHT_TRY(fork(p, s));
+    for (int i = 0; i < p->nbatch; ++i) {
+      nusht_plan_t q = p->sub[i];
+      cudaStream_t ms = p->side[i % nusht_batch_s::NSIDE];
+      NUSHT_TRY(spread(q, d_map[i], ms));
+      NUSHT_TRY(fine_fft_r2c(q, ms));
+      NUSHT_TRY(deconv_trunc(q, ms));
+    }
+    NUSHT_TRY(join(p, s));
   }
-  NUSHT_TRY(join(p, s));
   for (auto& b : p->buckets) {
     NUSHT_CUFFT(cufftSetStream(b.theta, s));
     NUSHT_CUFFT(cufftExecC2C(b.theta, (cufftComplex*)b.Ghat, (cufftComplex*)b.Ghat, CUFFT_INVERSE));
@@ -1538,7 +1663,7 @@ int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
         bucket_tc_k<true><<<b.ntc_work, T6_THREADS, T6_SMEM, s>>>(bucket_args(b), b.ntc_work, nullptr, b.tc_work,
                                                                   b.pt_off, nullptr, b.items, b.mfirst, b.ntiles,
                                                                   b.PT, b.BA, nullptr, b.cacc, p->status,
-                                                                  p->test_giveup);
+                                                                  p->test_giveup, b.tcg_a);
     } else {
       dim3 gf((b.npairs + FOLD_PAIRS - 1) / FOLD_PAIRS, b.L + 1);
       bucket_fold_k<<<gf, 256, 0, s>>>(b.L, b.M, b.npairs, b.B, b.memberL, b.Ghat, b.S);
@@ -1560,9 +1685,129 @@ int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
   return NUSHT_OK;
 }
 
+// Member tables of the fused NUFFT stages (plan time): zero fill, spreading,
+// interpolation and the deconvolution run as one launch each for every
+// member; the fine-grid FFTs are the FP32 line kernels' two passes (one
+// launch each) when every member uses them, else each member's cuFFT 2D
+// plan.  They apply with the atomic spreading (not opts.deterministic);
+// otherwise each member runs its own stages.
+int build_fused(nusht_batch_t p) {
+  p->fused = p->fused_sfft = false;
+  if (p->opts.deterministic) return NUSHT_OK;
+  int nsfft = 0;
+  for (auto* q : p->sub) {
+    if (q->pts.off == nullptr || q->dfft_fine) return NUSHT_OK;
+    nsfft += q->sfft_fine ? 1 : 0;
+  }
+  if (nsfft != 0 && nsfft != p->nbatch) return NUSHT_OK;
+  p->fused_sfft = nsfft == p->nbatch;
+  std::vector<int> order(p->nbatch);
+  for (int i = 0; i < p->nbatch; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p->sub[a]->sz.w < p->sub[b]->sz.w; });
+  std::vector<NufftMember> nm(p->nbatch);
+  std::vector<SfftMember> sm(p->nbatch);
+  p->table_of.assign(p->nbatch, 0);
+  p->nbw.clear();
+  SfftLaunch& sl = p->sl;
+  sl = SfftLaunch();
+  int blk = 0, sub = 0, zero = 0, cols = 0, rows = 0, pad = 0, trunc = 0;
+  for (int t = 0; t < p->nbatch; ++t) {
+    const int i = order[t];
+    nusht_plan_t q = p->sub[i];
+    const nusht_sizes& z = q->sz;
+    p->table_of[i] = t;
+    if (p->nbw.empty() || p->nbw.back().w != z.w) {
+      NufftBatch g;
+      g.w = z.w;
+      g.nm = t;  // first table position, turned into the count below
+      p->nbw.push_back(g);
+    }
+    NufftBatch& g = p->nbw.back();
+    NufftMember& a = nm[t];
+    a.grid = static_cast<float*>(q->fine);
+    a.cell = q->pts.cell;
+    a.off = q->pts.off;
+    a.perm = q->pts.perm;
+    a.sub = q->pts.sub;
+    a.stride = 2 * (z.n2 / 2 + 1);
+    a.npts = q->pts.npts;
+    a.n1 = z.n1;
+    a.n2 = z.n2;
+    a.nbins2 = q->pts.nbins2;
+    a.bin = q->pts.bin > 0 ? q->pts.bin : 32;
+    a.beta = (float)z.beta;
+    a.Gh = static_cast<float2*>(q->Ghat);
+    a.d1 = q->deconv1;
+    a.d2 = q->deconv2;
+    a.lmax = z.lmax;
+    a.mmax = z.mmax;
+    a.M = z.M;
+    a.blk0 = blk;
+    a.sub0 = sub;
+    a.zero0 = zero;
+    a.pad0 = pad;
+    a.trunc0 = trunc;
+    pad += ((z.n2 / 2 + 1 + 31) / 32) * ((z.n1 + 31) / 32);
+    trunc += ((z.M + 31) / 32) * ((z.mmax + 1 + 31) / 32);
+    blk += (int)((q->pts.npts + 127) / 128);
+    sub += q->pts.nsub;
+    zero += (int)((z.n1 * a.stride + ZERO_CHUNK - 1) / ZERO_CHUNK);
+    g.bin = std::max(g.bin, a.bin);
+    if (p->fused_sfft) {
+      SfftMember& f = sm[t];
+      sfft_member(q, f);
+      f.col0 = cols;
+      f.row0 = rows;
+      cols += z.mmax + 1;
+      rows += (z.n1 + 1) / 2;
+      sl.maxn1 = std::max(sl.maxn1, z.n1);
+      sl.maxn2 = std::max(sl.maxn2, z.n2);
+      sl.wide = sl.wide && sfft_launch_of(q).wide;
+    }
+  }
+  NUSHT_TRY(dev_alloc((void**)&p->d_nmem, nm.size() * sizeof(NufftMember), &p->bytes));
+  if (p->fused_sfft) NUSHT_TRY(dev_alloc((void**)&p->d_smem, sm.size() * sizeof(SfftMember), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&p->d_maps, p->nbatch * sizeof(float*), &p->bytes));
+  NUSHT_CUDA(cudaMemcpy(p->d_nmem, nm.data(), nm.size() * sizeof(NufftMember), cudaMemcpyHostToDevice));
+  if (p->fused_sfft)
+    NUSHT_CUDA(cudaMemcpy(p->d_smem, sm.data(), sm.size() * sizeof(SfftMember), cudaMemcpyHostToDevice));
+  // each width group: its slice of the member table; block counts relative to
+  // the group's first member (the kernels subtract blk0 / sub0 of members of
+  // the same table, so a group's launch starts at its first member's offsets)
+  for (size_t k = 0; k < p->nbw.size(); ++k) {
+    NufftBatch& g = p->nbw[k];
+    const int t0 = g.nm, t1 = k + 1 < p->nbw.size() ? p->nbw[k + 1].nm : p->nbatch;
+    g.mem = p->d_nmem + t0;
+    g.nm = t1 - t0;
+    g.nblk = (t1 < p->nbatch ? nm[t1].blk0 : blk) - nm[t0].blk0;
+    g.nsub = (t1 < p->nbatch ? nm[t1].sub0 : sub) - nm[t0].sub0;
+    g.nzero = 0;
+    g.blk_base = nm[t0].blk0;
+    g.sub_base = nm[t0].sub0;
+    g.map_base = t0;
+  }
+  p->nball.mem = p->d_nmem;
+  p->nball.nm = p->nbatch;
+  p->nball.nzero = zero;
+  p->nball.npad = pad;
+  p->nball.ntrunc = trunc;
+  sl.mem = p->d_smem;
+  sl.nm = p->nbatch;
+  sl.ncols = cols;
+  sl.nrows = rows;
+  p->fused = true;
+  return NUSHT_OK;
+}
+
 // pointer tables of every bucket (plan-owned device arrays, written before a
 // capture; the captured kernels read them)
 int set_tables(nusht_batch_t p, const void* const* in, void* const* out, bool synth) {
+  if (p->fused) {
+    std::vector<float*> maps(p->nbatch);
+    for (int i = 0; i < p->nbatch; ++i)
+      maps[p->table_of[i]] = static_cast<float*>(synth ? out[i] : const_cast<void*>(in[i]));
+    NUSHT_CUDA(cudaMemcpy(p->d_maps, maps.data(), p->nbatch * sizeof(float*), cudaMemcpyHostToDevice));
+  }
   for (auto& b : p->buckets) {
     std::vector<const void*> vin(BK_MAXB, nullptr);
     std::vector<void*> vout(BK_MAXB, nullptr);
@@ -1664,6 +1909,7 @@ int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64
       if (st == NUSHT_OK) p->bytes += p->sub[i]->bytes;
     }
     if (st != NUSHT_OK) break;
+    if ((st = build_fused(p)) != NUSHT_OK) break;
     {
       cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
       for (int k = 0; k < nusht_batch_s::NSIDE && e == cudaSuccess; ++k) {
@@ -1746,6 +1992,14 @@ int nusht_batch_status(nusht_batch_t p, nusht_stream_t stream) {
     NUSHT_CUDA(cudaMemset(p->status, 0, sizeof(int)));
     return set_error(NUSHT_ETIMEOUT, "a tensor-core contraction block gave up waiting for its MMAs");
   }
+  return NUSHT_OK;
+}
+
+int nusht_batch_schedule(nusht_batch_t p, int bucket, int* chunks_synth, int* chunks_adjoint) {
+  if (!p || bucket < 0 || bucket >= (int)p->buckets.size()) return set_error(NUSHT_EINVAL, "bad bucket");
+  const nusht::Bucket& b = p->buckets[bucket];
+  if (chunks_synth) *chunks_synth = b.tc ? b.tcg_s : 0;
+  if (chunks_adjoint) *chunks_adjoint = b.tc ? b.tcg_a : 0;
   return NUSHT_OK;
 }
 

@@ -162,52 +162,97 @@ __device__ __forceinline__ double2 c_value(float4 c) {
 }
 
 // ---------------------------------------------------------------------------
+// The line transform is written once for two complex types: CDF, the
+// float-pair complex above (FP64 plans), and CSF, plain float complex (mixed
+// plans; twiddles and odd-radix constants are the hi words of the table).
+// ---------------------------------------------------------------------------
+struct CDF {
+  using V = float4;
+  static __device__ __forceinline__ V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ V add(V a, V b) { return c_add(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return c_sub(a, b); }
+  template <int SG>
+  static __device__ __forceinline__ V mul_i(V a) {
+    return c_mul_i<SG>(a);
+  }
+  template <int SG>
+  static __device__ __forceinline__ V mul_tw(V a, float4 w) {
+    return c_mul_tw<SG>(a, w);
+  }
+  // acc += a * (h + l), a real float pair
+  static __device__ __forceinline__ void mac(V& acc, V a, float h, float l) { c_mac(acc, a, make_float2(h, l)); }
+};
+
+struct CSF {
+  using V = float2;
+  static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ V add(V a, V b) { return make_float2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ V sub(V a, V b) { return make_float2(a.x - b.x, a.y - b.y); }
+  template <int SG>
+  static __device__ __forceinline__ V mul_i(V a) {
+    return SG > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+  }
+  template <int SG>
+  static __device__ __forceinline__ V mul_tw(V a, float4 w) {
+    const float c = w.x, sn = SG > 0 ? w.z : -w.z;
+    return make_float2(fmaf(a.x, c, -a.y * sn), fmaf(a.x, sn, a.y * c));
+  }
+  static __device__ __forceinline__ void mac(V& acc, V a, float h, float) {
+    acc.x = fmaf(a.x, h, acc.x);
+    acc.y = fmaf(a.y, h, acc.y);
+  }
+};
+
+// ---------------------------------------------------------------------------
 // small DFTs of the butterflies (sign SG: +1 inverse, -1 forward)
 // ---------------------------------------------------------------------------
-template <int SG>
-__device__ __forceinline__ void dft4(float4* v) {
-  const float4 t0 = c_add(v[0], v[2]), t1 = c_sub(v[0], v[2]);
-  const float4 t2 = c_add(v[1], v[3]), t3 = c_mul_i<SG>(c_sub(v[1], v[3]));
-  v[0] = c_add(t0, t2);
-  v[2] = c_sub(t0, t2);
-  v[1] = c_add(t1, t3);
-  v[3] = c_sub(t1, t3);
+template <int SG, class C>
+__device__ __forceinline__ void dft4(typename C::V* v) {
+  using V = typename C::V;
+  const V t0 = C::add(v[0], v[2]), t1 = C::sub(v[0], v[2]);
+  const V t2 = C::add(v[1], v[3]), t3 = C::template mul_i<SG>(C::sub(v[1], v[3]));
+  v[0] = C::add(t0, t2);
+  v[2] = C::sub(t0, t2);
+  v[1] = C::add(t1, t3);
+  v[3] = C::sub(t1, t3);
 }
 
 // odd R: X_q = v0 + sum_r cos(2 pi r q / R) (v_r + v_R-r) + SG i sin(...) (v_r - v_R-r);
 // the constants are entries of the length-N twiddle table (R divides N)
-template <int R, int SG>
-__device__ __forceinline__ void dft_odd(float4* v, const float4* __restrict__ tw, int n_over_r) {
+template <int R, int SG, class C>
+__device__ __forceinline__ void dft_odd(typename C::V* v, const float4* __restrict__ tw, int n_over_r) {
+  using V = typename C::V;
   constexpr int H = R / 2;
-  float4 t[H], u[H];
+  V t[H], u[H];
 #pragma unroll
   for (int r = 1; r <= H; ++r) {
-    t[r - 1] = c_add(v[r], v[R - r]);
-    u[r - 1] = c_sub(v[r], v[R - r]);
+    t[r - 1] = C::add(v[r], v[R - r]);
+    u[r - 1] = C::sub(v[r], v[R - r]);
   }
-  float4 out[R];
+  V out[R];
   out[0] = v[0];
 #pragma unroll
-  for (int r = 0; r < H; ++r) out[0] = c_add(out[0], t[r]);
+  for (int r = 0; r < H; ++r) out[0] = C::add(out[0], t[r]);
 #pragma unroll
   for (int q = 1; q <= H; ++q) {
-    float4 a = v[0], b = make_float4(0.f, 0.f, 0.f, 0.f);
+    V a = v[0], b = C::zero();
 #pragma unroll
     for (int r = 1; r <= H; ++r) {
       const float4 w = __ldg(tw + ((r * q) % R) * n_over_r);
-      c_mac(a, t[r - 1], make_float2(w.x, w.y));
-      c_mac(b, u[r - 1], make_float2(w.z, w.w));
+      C::mac(a, t[r - 1], w.x, w.y);
+      C::mac(b, u[r - 1], w.z, w.w);
     }
-    const float4 ib = c_mul_i<SG>(b);
-    out[q] = c_add(a, ib);
-    out[R - q] = c_sub(a, ib);
+    const V ib = C::template mul_i<SG>(b);
+    out[q] = C::add(a, ib);
+    out[R - q] = C::sub(a, ib);
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = out[r];
 }
 
-template <int R, int SG>
-__device__ __forceinline__ void dif_pass(float4* X, const DfftLen& f, int L, int mul) {
+template <int R, int SG, class C>
+__device__ __forceinline__ void dif_pass(typename C::V* X, const DfftLen& f, int L, int mul) {
+  using V = typename C::V;
   const int S = L / R;
   const int nb = f.N / R;
   const bool pow2 = (S & (S - 1)) == 0;
@@ -224,8 +269,8 @@ __device__ __forceinline__ void dif_pass(float4* X, const DfftLen& f, int L, int
   for (int t = threadIdx.x; t < nb; t += blockDim.x) {
     const int b = pow2 ? (t >> sh) : t / S;
     const int j = t - b * S;
-    float4* p = X + b * L + j;
-    float4 v[R];
+    V* p = X + b * L + j;
+    V v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = p[r * S];
     float4 wn[R - 1];
@@ -236,17 +281,17 @@ __device__ __forceinline__ void dif_pass(float4* X, const DfftLen& f, int L, int
       for (int q = 1; q < R; ++q) wn[q - 1] = __ldg(f.tw + mul * jn * q);
     }
     if constexpr (R == 2) {
-      const float4 a = v[0];
-      v[0] = c_add(a, v[1]);
-      v[1] = c_sub(a, v[1]);
+      const V a = v[0];
+      v[0] = C::add(a, v[1]);
+      v[1] = C::sub(a, v[1]);
     } else if constexpr (R == 4) {
-      dft4<SG>(v);
+      dft4<SG, C>(v);
     } else {
-      dft_odd<R, SG>(v, f.tw, f.N / R);
+      dft_odd<R, SG, C>(v, f.tw, f.N / R);
     }
     // output q times W_L^(j q) = W_N^(mul j q), mul = N / L
 #pragma unroll
-    for (int q = 1; q < R; ++q) v[q] = c_mul_tw<SG>(v[q], w[q - 1]);
+    for (int q = 1; q < R; ++q) v[q] = C::template mul_tw<SG>(v[q], w[q - 1]);
 #pragma unroll
     for (int r = 0; r < R; ++r) p[r * S] = v[r];
 #pragma unroll
@@ -255,23 +300,23 @@ __device__ __forceinline__ void dif_pass(float4* X, const DfftLen& f, int L, int
 }
 
 // all passes; natural-order input in X, output k at X[f.rev[k]]
-template <int SG, int NT>
-__device__ void dif_line(float4* X, const DfftLen& f) {
+template <int SG, int NT, class C = CDF>
+__device__ void dif_line(typename C::V* X, const DfftLen& f) {
   int L = f.N;
   for (int s = 0; s < f.npass; ++s) {
     const int R = (int)((f.code >> (4 * s)) & 15u);
     const int mul = f.N / L;
     if (R == 4) {
-      dif_pass<4, SG>(X, f, L, mul);
+      dif_pass<4, SG, C>(X, f, L, mul);
     } else if (R == 2) {
-      dif_pass<2, SG>(X, f, L, mul);
+      dif_pass<2, SG, C>(X, f, L, mul);
     } else if (R == 3) {
-      dif_pass<3, SG>(X, f, L, mul);
+      dif_pass<3, SG, C>(X, f, L, mul);
     } else if constexpr (NT == DFFT_T_ODD) {
       if (R == 5)
-        dif_pass<5, SG>(X, f, L, mul);
+        dif_pass<5, SG, C>(X, f, L, mul);
       else
-        dif_pass<7, SG>(X, f, L, mul);
+        dif_pass<7, SG, C>(X, f, L, mul);
     }
     __syncthreads();
     L /= R;
@@ -429,6 +474,127 @@ __global__ void __launch_bounds__(NT) dfft_cols_adj_k(const float4* __restrict__
 }
 
 // ---------------------------------------------------------------------------
+// FP32 fine-grid transforms of mixed plans, for one plan or every member of a
+// batch in one launch per pass: CTA b finds its member (the last one whose
+// first CTA is <= b) and the line it owns.  Same passes as above with plain
+// float complex values (8 bytes per value in shared memory).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int member_of(const SfftMember* __restrict__ mem, int nm, int b, bool rows) {
+  int lo = 0, hi = nm - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((rows ? mem[mid].row0 : mem[mid].col0) <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// synthesis, per (member, order m): deconvolve and zero-pad the theta
+// spectrum to n1, inverse DFT along theta, store T[m][.]
+template <int NT>
+__global__ void __launch_bounds__(NT) sfft_cols_synth_k(const SfftMember* __restrict__ mem, int nm) {
+  extern __shared__ float2 Xs[];
+  const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, false)];
+  const int m = blockIdx.x - q.col0;
+  const int n1 = q.n1, lmax = q.lmax, M = q.M;
+  const float dm = q.d2[m];
+  const float2* g = q.Gh + (int64_t)m * M;
+  for (int k1 = threadIdx.x; k1 < n1; k1 += NT) {
+    float2 v = make_float2(0.f, 0.f);
+    const int k = k1 > lmax ? k1 - n1 : k1;
+    if (k >= -lmax) {
+      const float2 gv = g[k < 0 ? k + M : k];
+      const float d = q.d1[k + lmax] * dm;
+      v = make_float2(gv.x * d, gv.y * d);
+    }
+    Xs[k1] = v;
+  }
+  __syncthreads();
+  dif_line<1, NT, CSF>(Xs, q.f1);
+  float2* dst = q.T + (int64_t)m * n1;
+  for (int j = threadIdx.x; j < n1; j += NT) dst[j] = Xs[__ldg(q.f1.rev + j)];
+}
+
+// synthesis, per (member, row pair j, j + 1): the two Hermitian half spectra
+// packed as C = X_j + i X_j+1, one inverse DFT, x_j = Re, x_j+1 = Im
+template <int NT>
+__global__ void __launch_bounds__(NT) sfft_rows_c2r_k(const SfftMember* __restrict__ mem, int nm) {
+  extern __shared__ float2 Xs[];
+  const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, true)];
+  const int j = 2 * (blockIdx.x - q.row0);
+  const int n1 = q.n1, n2 = q.n2, mmax = q.mmax;
+  const bool two = j + 1 < n1;
+  for (int k = mmax + 1 + threadIdx.x; k < n2 - mmax; k += NT) Xs[k] = make_float2(0.f, 0.f);
+  for (int m = threadIdx.x; m <= mmax; m += NT) {
+    const float2 a = q.T[(int64_t)m * n1 + j];
+    const float2 b = two ? q.T[(int64_t)m * n1 + j + 1] : make_float2(0.f, 0.f);
+    if (m == 0) {
+      Xs[0] = make_float2(a.x, b.x);  // a real transform takes only Re of m = 0
+    } else {
+      Xs[m] = make_float2(a.x - b.y, a.y + b.x);
+      Xs[n2 - m] = make_float2(a.x + b.y, b.x - a.y);
+    }
+  }
+  __syncthreads();
+  dif_line<1, NT, CSF>(Xs, q.f2);
+  float* r0 = q.grid + (int64_t)j * q.stride;
+  for (int n = threadIdx.x; n < n2; n += NT) {
+    const float2 c = Xs[__ldg(q.f2.rev + n)];
+    r0[n] = c.x;
+    if (two) r0[q.stride + n] = c.y;
+  }
+}
+
+// adjoint, per (member, row pair): spectra m <= mmax of rows j, j + 1 into T
+template <int NT>
+__global__ void __launch_bounds__(NT) sfft_rows_r2c_k(const SfftMember* __restrict__ mem, int nm) {
+  extern __shared__ float2 Xs[];
+  const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, true)];
+  const int j = 2 * (blockIdx.x - q.row0);
+  const int n1 = q.n1, n2 = q.n2, mmax = q.mmax;
+  const bool two = j + 1 < n1;
+  const float* r0 = q.grid + (int64_t)j * q.stride;
+  for (int n = threadIdx.x; n < n2; n += NT) Xs[n] = make_float2(r0[n], two ? r0[q.stride + n] : 0.f);
+  __syncthreads();
+  dif_line<-1, NT, CSF>(Xs, q.f2);
+  for (int m = threadIdx.x; m <= mmax; m += NT) {
+    const float2 cm = Xs[__ldg(q.f2.rev + m)];
+    const float2 cn = Xs[__ldg(q.f2.rev + (m == 0 ? 0 : n2 - m))];
+    // X_j = (C[m] + conj C[n2-m]) / 2, X_j+1 = -i (C[m] - conj C[n2-m]) / 2
+    q.T[(int64_t)m * n1 + j] = make_float2(0.5f * (cm.x + cn.x), 0.5f * (cm.y - cn.y));
+    if (two) q.T[(int64_t)m * n1 + j + 1] = make_float2(0.5f * (cm.y + cn.y), 0.5f * (cn.x - cm.x));
+  }
+}
+
+// adjoint, per (member, order m): forward DFT of T[m][.] along theta, then
+// Gh[m][kk] = H[k mod n1] d1[k] d2[m] for |k| <= lmax (k = kk or kk - M), else 0
+template <int NT>
+__global__ void __launch_bounds__(NT) sfft_cols_adj_k(const SfftMember* __restrict__ mem, int nm) {
+  extern __shared__ float2 Xs[];
+  const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, false)];
+  const int m = blockIdx.x - q.col0;
+  const int n1 = q.n1, lmax = q.lmax, M = q.M;
+  const float2* src = q.T + (int64_t)m * n1;
+  for (int k = threadIdx.x; k < n1; k += NT) Xs[k] = src[k];
+  __syncthreads();
+  dif_line<-1, NT, CSF>(Xs, q.f1);
+  const float dm = q.d2[m];
+  float2* g = const_cast<float2*>(q.Gh) + (int64_t)m * M;
+  for (int kk = threadIdx.x; kk < M; kk += NT) {
+    const int k = kk <= M / 2 ? kk : kk - M;
+    float2 v = make_float2(0.f, 0.f);
+    if (k >= -lmax && k <= lmax) {
+      const float2 c = Xs[__ldg(q.f1.rev + (k < 0 ? k + n1 : k))];
+      const float d = q.d1[k + lmax] * dm;
+      v = make_float2(c.x * d, c.y * d);
+    }
+    g[kk] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 bool factor(int n, DfftLen& f) {
@@ -496,6 +662,10 @@ int optin_all(int b) {
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_r2c_k<NT>, a, b));
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k<false, NT>, a, b));
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k<true, NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_synth_k<NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_c2r_k<NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_r2c_k<NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_adj_k<NT>, a, b));
   return NUSHT_OK;
 }
 
@@ -571,9 +741,14 @@ void dfft_free(nusht_plan_t p) {
   dev_free(p->tcols);
   dev_free(p->deconv1f);
   dev_free(p->deconv2f);
+  dev_free(p->deconv1s);
+  dev_free(p->deconv2s);
+  dev_free(p->sfft_mem);
   p->tcols = nullptr;
   p->deconv1f = p->deconv2f = nullptr;
-  p->dfft_theta = p->dfft_fine = false;
+  p->deconv1s = p->deconv2s = nullptr;
+  p->sfft_mem = nullptr;
+  p->dfft_theta = p->dfft_fine = p->sfft_fine = false;
 }
 
 // With both the theta and the fine-grid transforms here, the theta spectrum
@@ -673,5 +848,81 @@ int dfft_cols_adjoint(nusht_plan_t p, cudaStream_t s) {
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
+
+bool sfft_fits(const nusht_sizes& z) {
+  auto ok = [](int n) {
+    DfftLen f;
+    return n >= 2 && n <= SFFT_NMAX && factor(n, f);
+  };
+  return ok(z.n1) && ok(z.n2) && z.n2 % 2 == 0 && z.n1 > 2 * z.lmax && 2 * z.mmax < z.n2;
+}
+
+int sfft_setup(nusht_plan_t p, const double* d1, const double* d2) {
+  const nusht_sizes& z = p->sz;
+  NUSHT_TRY(smem_optin());
+  NUSHT_TRY(make_len(z.n1, p->dft_n1, &p->bytes));
+  NUSHT_TRY(make_len(z.n2, p->dft_n2, &p->bytes));
+  NUSHT_TRY(dev_alloc(&p->tcols, (size_t)(z.mmax + 1) * z.n1 * sizeof(float2), &p->bytes));
+  std::vector<float> f1(2 * z.lmax + 1), f2(z.mmax + 1);
+  for (size_t i = 0; i < f1.size(); ++i) f1[i] = (float)d1[i];
+  for (size_t i = 0; i < f2.size(); ++i) f2[i] = (float)d2[i];
+  NUSHT_TRY(dev_alloc((void**)&p->deconv1s, f1.size() * sizeof(float), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&p->deconv2s, f2.size() * sizeof(float), &p->bytes));
+  NUSHT_CUDA(cudaMemcpy(p->deconv1s, f1.data(), f1.size() * sizeof(float), cudaMemcpyHostToDevice));
+  NUSHT_CUDA(cudaMemcpy(p->deconv2s, f2.data(), f2.size() * sizeof(float), cudaMemcpyHostToDevice));
+  p->sfft_fine = true;
+  SfftMember m;
+  sfft_member(p, m);
+  NUSHT_TRY(dev_alloc((void**)&p->sfft_mem, sizeof(SfftMember), &p->bytes));
+  NUSHT_CUDA(cudaMemcpy(p->sfft_mem, &m, sizeof(SfftMember), cudaMemcpyHostToDevice));
+  return NUSHT_OK;
+}
+
+void sfft_member(nusht_plan_t p, SfftMember& m) {
+  const nusht_sizes& z = p->sz;
+  m.Gh = static_cast<float2*>(p->Ghat);
+  m.T = static_cast<float2*>(p->tcols);
+  m.grid = static_cast<float*>(p->fine);
+  m.d1 = p->deconv1s;
+  m.d2 = p->deconv2s;
+  m.stride = 2 * (z.n2 / 2 + 1);
+  m.lmax = z.lmax;
+  m.mmax = z.mmax;
+  m.M = z.M;
+  m.n1 = z.n1;
+  m.n2 = z.n2;
+  m.col0 = m.row0 = 0;
+  m.f1 = p->dft_n1;
+  m.f2 = p->dft_n2;
+}
+
+SfftLaunch sfft_launch_of(nusht_plan_t p) {
+  SfftLaunch l;
+  l.mem = p->sfft_mem;
+  l.nm = 1;
+  l.ncols = p->sz.mmax + 1;
+  l.nrows = (p->sz.n1 + 1) / 2;
+  l.maxn1 = p->sz.n1;
+  l.maxn2 = p->sz.n2;
+  l.wide = wide(p->dft_n1) && wide(p->dft_n2);
+  return l;
+}
+
+#define NUSHT_SFFT_LAUNCH(KERNEL, NCTA, NMAXLEN)                                                       \
+  do {                                                                                                 \
+    if ((NCTA) <= 0) return NUSHT_OK;                                                                  \
+    const size_t sm = (size_t)(NMAXLEN) * sizeof(float2);                                              \
+    if (l.wide)                                                                                        \
+      KERNEL<DFFT_T_WIDE><<<(NCTA), DFFT_T_WIDE, sm, s>>>(l.mem, l.nm);                                \
+    else                                                                                               \
+      KERNEL<DFFT_T_ODD><<<(NCTA), DFFT_T_ODD, sm, s>>>(l.mem, l.nm);                                  \
+    NUSHT_CUDA(cudaGetLastError());                                                                    \
+    return NUSHT_OK;                                                                                   \
+  } while (0)
+
+int sfft_cols_synth(const SfftLaunch& l, cudaStream_t s) { NUSHT_SFFT_LAUNCH(sfft_cols_synth_k, l.ncols, l.maxn1); }
+int sfft_rows_c2r(const SfftLaunch& l, cudaStream_t s) { NUSHT_SFFT_LAUNCH(sfft_rows_c2r_k, l.nrows, l.maxn2); }
+int sfft_rows_r2c(const SfftLaunch& l, cudaStream_t s) { NUSHT_SFFT_LAUNCH(sfft_rows_r2c_k, l.nrows, l.maxn2); }
+int sfft_cols_adjoint(const SfftLaunch& l, cudaStream_t s) { NUSHT_SFFT_LAUNCH(sfft_cols_adj_k, l.ncols, l.maxn1); }
 
 }  // namespace nusht

@@ -504,11 +504,19 @@ __device__ __forceinline__ void df4_add(float4& a4, const float4 b4) {
   df_add(a4.z, a4.w, b4.z, b4.w);
 }
 
+// The adjoint's degree loop is rolled (two degrees, one of each parity, per
+// iteration) so that its body stays small: the unrolled eight-degree body
+// with register accumulators (and the shuffle reduce-scatter after it) ran
+// 12 % slower, stalled on instruction fetch.  Each degree's sum over the
+// lane's four chains goes to a shared-memory slot; every eight degrees the
+// warp reduces the slots over its 32 lanes through the transpose: lane t sums
+// one float pair (degree t / 4, re or im) over 16 lanes, and the two halves
+// are combined with one shuffle.
 template <class CH>
 __global__ void __launch_bounds__(128, 5) legendre_adj_df_k(LegArgs a, const double2* __restrict__ Gt,
                                                          float4* __restrict__ partial, int nitems, int64_t nalm) {
-  const int lane = threadIdx.x & 31;
-  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int it = blockIdx.x * 4 + warp;
   if (it >= nitems) return;
   int m, blk;
   item_of(a, it, m, blk);
@@ -519,10 +527,13 @@ __global__ void __launch_bounds__(128, 5) legendre_adj_df_k(LegArgs a, const dou
   const double2* row = Gt + (size_t)m * M;
   CH ch[LEG_K];
   // folded spectrum per chain as double-float (hi_re, lo_re, hi_im, lo_im),
-  // even / odd l - m; kept in shared memory to leave registers for occupancy
+  // even / odd l - m, and the per-degree sums of each lane (rows padded to
+  // 9 entries: conflict-free 16-byte stores)
   __shared__ float4 sS[2][LEG_K][128];
+  __shared__ float4 red[4][32][9];
   float4* SE = &sS[0][0][threadIdx.x];
   float4* SO = &sS[1][0][threadIdx.x];
+  float4(*rw)[9] = red[warp];
 #pragma unroll
   for (int k = 0; k < LEG_K; ++k) {
     const int jn = 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane;
@@ -546,56 +557,49 @@ __global__ void __launch_bounds__(128, 5) legendre_adj_df_k(LegArgs a, const dou
     SO[k * 128] = o4;
   }
   float4* out = partial + (size_t)blk * nalm + mb;
-  for (int base = m; base <= L; base += 8) {
-    float4 v[8];
+  // one degree: advance the chains to l, sum q_l S over the lane's chains
+  auto degree = [&](int l, const float4* S, float4* dst) {
+    if (l > m) {
+      const auto c = coef(a, mb + l, ch[0]);
+      const int rs = __ldg(a.dshift + mb + l);
 #pragma unroll
-    for (int st = 0; st < 8; ++st) {
-      v[st] = make_float4(0.f, 0.f, 0.f, 0.f);
-      const int l = base + st;
-      if (l <= L) {
-        if (l > m) {
-          const auto c = coef(a, mb + l, ch[0]);
-          const int rs = __ldg(a.dshift + mb + l);
+      for (int k = 0; k < LEG_K; ++k) chain_step(ch[k], c, rs);
+    }
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-          for (int k = 0; k < LEG_K; ++k) chain_step(ch[k], c, rs);
-        }
-#pragma unroll
-        for (int k = 0; k < LEG_K; ++k) {
-          if (ch[k].E == 0) {
-            float qh, ql;
-            qsplit(ch[k], qh, ql);
-            const float4 S = (st & 1) ? SO[k * 128] : SE[k * 128];
-            df_mac(v[st].x, v[st].y, S.x, S.y, qh, ql);
-            df_mac(v[st].z, v[st].w, S.z, S.w, qh, ql);
-          }
-        }
+    for (int k = 0; k < LEG_K; ++k) {
+      if (ch[k].E == 0) {
+        float qh, ql;
+        qsplit(ch[k], qh, ql);
+        const float4 Sv = S[k * 128];
+        df_mac(acc.x, acc.y, Sv.x, Sv.y, qh, ql);
+        df_mac(acc.z, acc.w, Sv.z, Sv.w, qh, ql);
       }
     }
-    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
-    float4 w4[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float4 send = u16 ? v[i] : v[i + 4];
-      w4[i] = u16 ? v[i + 4] : v[i];
-      df4_add(w4[i], shfl4(send, 16));
+    *dst = acc;
+  };
+  const int d = lane >> 2, cpt = (lane >> 1) & 1, half = lane & 1;
+  for (int base = m; base <= L; base += 8) {
+    const int nst = min(8, L - base + 1);
+#pragma unroll 1
+    for (int st = 0; st < nst; st += 2) {
+      degree(base + st, SE, &rw[lane][st]);
+      if (st + 1 < nst) degree(base + st + 1, SO, &rw[lane][st + 1]);
     }
-    float4 w2[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float4 send = u8 ? w4[i] : w4[i + 2];
-      w2[i] = u8 ? w4[i + 2] : w4[i];
-      df4_add(w2[i], shfl4(send, 8));
+    __syncwarp();
+    float sh = 0.f, sl = 0.f;
+    if (d < nst) {
+#pragma unroll 4
+      for (int i = 0; i < 16; ++i) {
+        const float2 x = reinterpret_cast<const float2*>(&rw[half * 16 + i][d])[cpt];
+        df_add(sh, sl, x.x, x.y);
+      }
     }
-    float4 z;
-    {
-      const float4 send = u4 ? w2[0] : w2[1];
-      z = u4 ? w2[1] : w2[0];
-      df4_add(z, shfl4(send, 4));
-    }
-    df4_add(z, shfl4(z, 2));
-    df4_add(z, shfl4(z, 1));
-    const int l = base + ((lane >> 2) & 7);
-    if ((lane & 3) == 0 && l <= L) out[l] = z;  // float pairs; adj_reduce_df_k converts
+    const float oh = __shfl_xor_sync(FULL, sh, 1), ol = __shfl_xor_sync(FULL, sl, 1);
+    df_add(sh, sl, oh, ol);
+    __syncwarp();  // the slots are rewritten by the next eight degrees
+    // float pairs; adj_reduce_df_k sums the ring blocks and converts
+    if (half == 0 && d < nst) reinterpret_cast<float2*>(out + base + d)[cpt] = make_float2(sh, sl);
   }
 }
 

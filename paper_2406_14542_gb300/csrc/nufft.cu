@@ -139,12 +139,13 @@ __global__ void gather_k(const double* __restrict__ pts, const int* __restrict__
 // ---------------------------------------------------------------------------
 // fine spectrum H[k1][m] (n1 x n2h) from the theta spectrum Ghat[m][kk] (M)
 template <typename T>
-__global__ void deconv_pad_k(const typename V2<T>::t* __restrict__ Gh, typename V2<T>::t* __restrict__ H, int lmax,
-                             int mmax, int M, int n1, int n2h, const double* __restrict__ d1,
-                             const double* __restrict__ d2) {
+__device__ __forceinline__ void deconv_pad_tile(const typename V2<T>::t* __restrict__ Gh,
+                                                typename V2<T>::t* __restrict__ H, int lmax, int mmax, int M, int n1,
+                                                int n2h, const double* __restrict__ d1,
+                                                const double* __restrict__ d2, int bx, int by) {
   using T2 = typename V2<T>::t;
   __shared__ T2 tile[32][33];
-  const int k0 = blockIdx.y * 32, m0 = blockIdx.x * 32;
+  const int k0 = by * 32, m0 = bx * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   // is this row tile entirely in the zero band lmax < k1 < n1 - lmax?
   const bool zero_rows = (k0 > lmax) && (k0 + 31 < n1 - lmax);
@@ -194,12 +195,13 @@ __global__ void deconv_pad_k(const typename V2<T>::t* __restrict__ Gh, typename 
 
 // theta spectrum Gt[m][kk] from the fine spectrum H[k1][m] (after the r2c FFT)
 template <typename T>
-__global__ void deconv_trunc_k(const typename V2<T>::t* __restrict__ H, typename V2<T>::t* __restrict__ Gt, int lmax,
-                               int mmax, int M, int n1, int n2h, const double* __restrict__ d1,
-                               const double* __restrict__ d2) {
+__device__ __forceinline__ void deconv_trunc_tile(const typename V2<T>::t* __restrict__ H,
+                                                  typename V2<T>::t* __restrict__ Gt, int lmax, int mmax, int M,
+                                                  int n1, int n2h, const double* __restrict__ d1,
+                                                  const double* __restrict__ d2, int bx, int by) {
   using T2 = typename V2<T>::t;
   __shared__ T2 tile[32][33];
-  const int kk0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
+  const int kk0 = bx * 32, m0 = by * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
   // load H[k1(kk0 + r)][m0 + tx]
   for (int r = ty; r < 32; r += 8) {
@@ -223,6 +225,20 @@ __global__ void deconv_trunc_k(const typename V2<T>::t* __restrict__ H, typename
     const int m = m0 + r, kk = kk0 + tx;
     if (m <= mmax && kk < M) Gt[(size_t)m * M + kk] = tile[tx][r];
   }
+}
+
+template <typename T>
+__global__ void deconv_pad_k(const typename V2<T>::t* __restrict__ Gh, typename V2<T>::t* __restrict__ H, int lmax,
+                             int mmax, int M, int n1, int n2h, const double* __restrict__ d1,
+                             const double* __restrict__ d2) {
+  deconv_pad_tile<T>(Gh, H, lmax, mmax, M, n1, n2h, d1, d2, blockIdx.x, blockIdx.y);
+}
+
+template <typename T>
+__global__ void deconv_trunc_k(const typename V2<T>::t* __restrict__ H, typename V2<T>::t* __restrict__ Gt, int lmax,
+                               int mmax, int M, int n1, int n2h, const double* __restrict__ d1,
+                               const double* __restrict__ d2) {
+  deconv_trunc_tile<T>(H, Gt, lmax, mmax, M, n1, n2h, d1, d2, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -927,9 +943,162 @@ void launch_interp_f(int nb, cudaStream_t s, const float* grid, int64_t stride, 
   interp_f_k<W><<<nb, 128, 0, s>>>(grid, stride, n1, n2, betaf, cell, offf, perm, npts, out);
 }
 
+// ---------------------------------------------------------------------------
+// The same mixed-precision kernels for every member of a batch in one launch:
+// a block finds its member by its first-block offset (binary search over the
+// member table) and then works as spread_pt_k / interp_f_k do on that
+// member's grid and points.
+// ---------------------------------------------------------------------------
+enum { MEMBER_BLK, MEMBER_SUB, MEMBER_ZERO, MEMBER_PAD, MEMBER_TRUNC };
+template <int KEY>
+__device__ __forceinline__ int nufft_member_of(const NufftMember* __restrict__ mem, int nm, int b) {
+  int lo = 0, hi = nm - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int f = KEY == MEMBER_BLK     ? mem[mid].blk0
+                  : KEY == MEMBER_SUB   ? mem[mid].sub0
+                  : KEY == MEMBER_ZERO  ? mem[mid].zero0
+                  : KEY == MEMBER_PAD   ? mem[mid].pad0
+                                        : mem[mid].trunc0;
+    if (f <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) zero_grids_k(const NufftMember* __restrict__ mem, int nm) {
+  const NufftMember& q = mem[nufft_member_of<MEMBER_ZERO>(mem, nm, blockIdx.x)];
+  const int64_t n = (int64_t)q.n1 * q.stride;
+  const int64_t i0 = (int64_t)(blockIdx.x - q.zero0) * ZERO_CHUNK;
+  const int64_t i1 = i0 + ZERO_CHUNK < n ? i0 + ZERO_CHUNK : n;
+  // the grid starts 256-byte aligned and i0 is a multiple of 4: 16-byte stores,
+  // the last partial vector element by element
+  float4* g4 = reinterpret_cast<float4*>(q.grid);
+  for (int64_t i = i0 + 4 * threadIdx.x; i < i1; i += 4 * blockDim.x) {
+    if (i + 4 <= i1)
+      g4[i >> 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    else
+      for (int64_t k = i; k < i1; ++k) q.grid[k] = 0.f;
+  }
+}
+
+// blocks b = blockIdx.x + base of the table slice `mem` (base: sub0 / blk0 of
+// its first member); maps[i] belongs to mem[i]
+template <int W>
+__global__ void __launch_bounds__(128) spread_many_k(const NufftMember* __restrict__ mem, int nm, int base,
+                                                     const float* const* __restrict__ maps) {
+  extern __shared__ unsigned char smem_raw[];
+  float* tile = reinterpret_cast<float*>(smem_raw);
+  const int b = blockIdx.x + base;
+  const int i = nufft_member_of<MEMBER_SUB>(mem, nm, b);
+  const NufftMember& q = mem[i];
+  const int* sb = q.sub + 3 * (b - q.sub0);
+  const int binsz = q.bin, tw = binsz + W - 1;
+  const int bin = sb[0], start = sb[1], cnt = sb[2];
+  const int r0 = (bin / q.nbins2) * binsz, c0 = (bin % q.nbins2) * binsz;
+  const float* f = maps[i];
+  for (int t = threadIdx.x; t < tw * tw; t += blockDim.x) tile[t] = 0.f;
+  __syncthreads();
+  const float scf = 2.0f / W;
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    const int64_t s = (int64_t)start + k;
+    const int lr = q.cell[2 * s] - r0, lc = q.cell[2 * s + 1] - c0;
+    const float fv = f[q.perm[s]];
+    const float o1 = q.off[2 * s], o2 = q.off[2 * s + 1];
+    float p1[W], p2[W];
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      p1[a] = fv * es_psif((o1 - a) * scf, q.beta);
+      p2[a] = es_psif((o2 - a) * scf, q.beta);
+    }
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      float* trow = tile + (lr + a) * tw + lc;
+#pragma unroll
+      for (int b = 0; b < W; ++b) atomicAdd(trow + b, p1[a] * p2[b]);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < tw * tw; t += blockDim.x) {
+    const float v = tile[t];
+    if (v != 0.f) {
+      int r = r0 + t / tw, c = c0 + t % tw;
+      while (r >= q.n1) r -= q.n1;
+      while (c >= q.n2) c -= q.n2;
+      atomicAdd(q.grid + (int64_t)r * q.stride + c, v);
+    }
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(128) interp_many_k(const NufftMember* __restrict__ mem, int nm, int base,
+                                                     float* const* __restrict__ maps) {
+  const int b = blockIdx.x + base;
+  const int i = nufft_member_of<MEMBER_BLK>(mem, nm, b);
+  const NufftMember& q = mem[i];
+  const int64_t s = (int64_t)(b - q.blk0) * 128 + threadIdx.x;
+  if (s >= q.npts) return;
+  const int i1 = q.cell[2 * s], i2 = q.cell[2 * s + 1];
+  const float o1 = q.off[2 * s], o2 = q.off[2 * s + 1];
+  const float scf = 2.0f / W;
+  float p1[W], p2[W];
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    p1[a] = es_psif((o1 - a) * scf, q.beta);
+    p2[a] = es_psif((o2 - a) * scf, q.beta);
+  }
+  const int n1 = q.n1, n2 = q.n2;
+  const bool wrap2 = i2 + W > n2;
+  float acc = 0.f;
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    int r = i1 + a;
+    if (r >= n1) r -= n1;
+    const float* row = q.grid + (int64_t)r * q.stride;
+    float in = 0.f;
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      int c = i2 + b;
+      if (wrap2 && c >= n2) c -= n2;
+      in = fmaf(p2[b], row[c], in);
+    }
+    acc = fmaf(p1[a], in, acc);
+  }
+  maps[i][q.perm[s]] = acc;
+}
+
+// deconv_pad_k / deconv_trunc_k of every member: the member's 2D tile grid
+// flattened, tiles in the same order
+__global__ void deconv_pad_many_k(const NufftMember* __restrict__ mem, int nm) {
+  const NufftMember& q = mem[nufft_member_of<MEMBER_PAD>(mem, nm, blockIdx.x)];
+  const int n2h = q.n2 / 2 + 1, gx = (n2h + 31) / 32;
+  const int t = blockIdx.x - q.pad0;
+  deconv_pad_tile<float>(q.Gh, reinterpret_cast<float2*>(q.grid), q.lmax, q.mmax, q.M, q.n1, n2h, q.d1, q.d2,
+                         t % gx, t / gx);
+}
+__global__ void deconv_trunc_many_k(const NufftMember* __restrict__ mem, int nm) {
+  const NufftMember& q = mem[nufft_member_of<MEMBER_TRUNC>(mem, nm, blockIdx.x)];
+  const int gx = (q.M + 31) / 32;
+  const int t = blockIdx.x - q.trunc0;
+  deconv_trunc_tile<float>(reinterpret_cast<const float2*>(q.grid), q.Gh, q.lmax, q.mmax, q.M, q.n1, q.n2 / 2 + 1,
+                           q.d1, q.d2, t % gx, t / gx);
+}
+
+template <int W>
+void launch_spread_many(const NufftBatch& nb, size_t sm, cudaStream_t s, const float* const* maps) {
+  spread_many_k<W><<<nb.nsub, 128, sm, s>>>(nb.mem, nb.nm, nb.sub_base, maps);
+}
+template <int W>
+void launch_interp_many(const NufftBatch& nb, cudaStream_t s, float* const* maps) {
+  interp_many_k<W><<<nb.nblk, 128, 0, s>>>(nb.mem, nb.nm, nb.blk_base, maps);
+}
+
 template <int W>
 void optin_f(int* st) {
-  if (cudaFuncSetAttribute(spread_pt_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 84 * 84 * 8) != cudaSuccess)
+  if (cudaFuncSetAttribute(spread_pt_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 84 * 84 * 8) != cudaSuccess ||
+      cudaFuncSetAttribute(spread_many_k<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 84 * 84 * 8) != cudaSuccess)
     *st = 1;
 }
 
@@ -1071,6 +1240,7 @@ int deconv_pad(nusht_plan_t p, cudaStream_t s) {
   // double-float FFT plans: deconvolution and zero-padding happen in the load
   // of the column pass, which this stage then runs
   if (p->dfft_fine) return dfft_cols_synth(p, s);
+  if (p->sfft_fine) return sfft_cols_synth(sfft_launch_of(p), s);
   const nusht_sizes& z = p->sz;
   const int n2h = z.n2 / 2 + 1;
   dim3 blk(32, 8), grd((n2h + 31) / 32, (z.n1 + 31) / 32);
@@ -1088,6 +1258,7 @@ int deconv_trunc(nusht_plan_t p, cudaStream_t s) {
   // double-float FFT plans: the column pass, with truncation and
   // deconvolution in its store
   if (p->dfft_fine) return dfft_cols_adjoint(p, s);
+  if (p->sfft_fine) return sfft_cols_adjoint(sfft_launch_of(p), s);
   const nusht_sizes& z = p->sz;
   const int n2h = z.n2 / 2 + 1;
   dim3 blk(32, 8), grd((z.M + 31) / 32, (z.mmax + 1 + 31) / 32);
@@ -1232,6 +1403,42 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
                                                            p->pts.binsub, (const float*)p->pts.tiles);
     NUSHT_CUDA(cudaGetLastError());
   }
+  return NUSHT_OK;
+}
+
+int zero_grids_many(const NufftBatch& nb, cudaStream_t s) {
+  if (nb.nzero <= 0) return NUSHT_OK;
+  zero_grids_k<<<nb.nzero, 256, 0, s>>>(nb.mem, nb.nm);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int spread_many(const NufftBatch& nb, const float* const* maps, cudaStream_t s) {
+  if (nb.nsub <= 0) return NUSHT_OK;
+  const int tw = nb.bin + nb.w - 1;
+  NUSHT_W_DISPATCH(nb.w, launch_spread_many, nb, (size_t)tw * tw * 4, s, maps);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int interp_many(const NufftBatch& nb, float* const* maps, cudaStream_t s) {
+  if (nb.nblk <= 0) return NUSHT_OK;
+  NUSHT_W_DISPATCH(nb.w, launch_interp_many, nb, s, maps);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int deconv_pad_many(const NufftBatch& nb, cudaStream_t s) {
+  if (nb.npad <= 0) return NUSHT_OK;
+  deconv_pad_many_k<<<nb.npad, dim3(32, 8), 0, s>>>(nb.mem, nb.nm);
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int deconv_trunc_many(const NufftBatch& nb, cudaStream_t s) {
+  if (nb.ntrunc <= 0) return NUSHT_OK;
+  deconv_trunc_many_k<<<nb.ntrunc, dim3(32, 8), 0, s>>>(nb.mem, nb.nm);
+  NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
 

@@ -116,6 +116,61 @@ struct DfftLen {
   int* rev = nullptr;
 };
 
+// One transform of the FP32 fine-grid FFT kernels (dfft.cu) of mixed plans;
+// a single plan has one, a batch one per member, so that each pass is one
+// launch for all members.  The order-major spectrum T sits between the
+// column pass (along theta, per order) and the row pass (along phi, per
+// pair of real rows).
+constexpr int SFFT_NMAX = 2 * DFFT_NMAX;  // longest line: float complex values in shared memory
+struct SfftMember {
+  float2* Gh = nullptr;        // theta spectrum [mmax + 1][M] (synthesis input, adjoint output)
+  float2* T = nullptr;         // [mmax + 1][n1]
+  float* grid = nullptr;       // fine grid, n1 rows of `stride` floats
+  const float* d1 = nullptr;   // theta deconvolution factors, k = -lmax..lmax (1/M included)
+  const float* d2 = nullptr;   // phi deconvolution factors, m = 0..mmax
+  int64_t stride = 0;
+  int lmax = 0, mmax = 0, M = 0, n1 = 0, n2 = 0;
+  int col0 = 0, row0 = 0;      // first CTA of this member in the column / row launches
+  DfftLen f1, f2;              // line tables of n1 and n2
+};
+
+// One transform of the mixed-precision NUFFT kernels that serve every member
+// of a batch in one launch (nufft.cu): the member's fine grid and sorted
+// points.  Interpolation blocks of 128 threads never straddle two members
+// (each member's points start at a multiple of 128 in the launch), spreading
+// blocks are the members' subproblems one after another.
+struct NufftMember {
+  float* grid = nullptr;       // n1 rows of `stride` floats
+  const int* cell = nullptr;   // sorted points: first tap (i1, i2)
+  const float* off = nullptr;  // sorted points: fractional offsets
+  const int* perm = nullptr;   // sorted index -> caller index
+  const int* sub = nullptr;    // spreading subproblems (bin, first point, count)
+  int64_t stride = 0;
+  int64_t npts = 0;
+  int n1 = 0, n2 = 0, nbins2 = 0, bin = 0;
+  int blk0 = 0;                // first interpolation block
+  int sub0 = 0;                // first spreading block
+  int zero0 = 0;               // first block of the grid zero fill
+  float beta = 0.f;
+  // deconvolution between the theta spectrum and the fine spectrum (the
+  // grid buffer seen as n1 x (n2/2 + 1) complex), 32 x 32 tiles
+  float2* Gh = nullptr;        // theta spectrum [mmax + 1][M]
+  const double* d1 = nullptr;  // k = -lmax..lmax
+  const double* d2 = nullptr;  // m = 0..mmax
+  int lmax = 0, mmax = 0, M = 0;
+  int pad0 = 0;                // first block of the padding launch
+  int trunc0 = 0;              // first block of the truncation launch
+};
+struct NufftBatch {
+  const NufftMember* mem = nullptr;  // device table (a slice of the batch's table)
+  int nm = 0, w = 0;
+  int nblk = 0, nsub = 0, nzero = 0; // blocks of the three launches
+  int blk_base = 0, sub_base = 0;    // blk0 / sub0 of the slice's first member
+  int npad = 0, ntrunc = 0;          // blocks of the deconvolution launches
+  int map_base = 0;                  // position of the slice in the batch's tables
+  int bin = 32;                      // largest bin edge (spreading tile size)
+};
+
 struct StageEvents {
   cudaEvent_t ev[8] = {};
   bool ready = false;
@@ -162,6 +217,14 @@ struct nusht_plan_s {
   void* tcols = nullptr;
   float2* deconv1f = nullptr;  // deconv1 / deconv2 as float pairs
   float2* deconv2f = nullptr;
+
+  // mixed plans: the fine-grid FFT as this library's FP32 line kernels
+  // (dfft.cu) with the deconvolution and padding / truncation fused into the
+  // column pass; tcols holds [mmax + 1][n1] float complex between the passes
+  bool sfft_fine = false;
+  float* deconv1s = nullptr;   // deconv1 / deconv2 as float
+  float* deconv2s = nullptr;
+  nusht::SfftMember* sfft_mem = nullptr;  // device copy of this plan's member entry
 
   size_t bytes = 0;
 
@@ -215,9 +278,24 @@ int interp_grad(nusht_plan_t p, void* d_dth, void* d_dph, const void* cot, doubl
 int interp_pointing(nusht_plan_t p, double* d_ptg, cudaStream_t s);
 int spread(nusht_plan_t p, const void* d_map, cudaStream_t s);
 int spread_smem_optin();
+// every member of a NufftBatch (mixed precision, atomics): zero the fine
+// grids, spread the maps (caller order, maps[i] of member i), interpolate
+int zero_grids_many(const NufftBatch& nb, cudaStream_t s);
+int spread_many(const NufftBatch& nb, const float* const* maps, cudaStream_t s);
+int interp_many(const NufftBatch& nb, float* const* maps, cudaStream_t s);
+// deconvolution + zero padding (theta spectrum -> fine spectrum) and
+// truncation + deconvolution (fine spectrum -> theta spectrum) of every member
+int deconv_pad_many(const NufftBatch& nb, cudaStream_t s);
+int deconv_trunc_many(const NufftBatch& nb, cudaStream_t s);
+constexpr int ZERO_CHUNK = 1 << 14;  // floats zeroed per block
 
 // autotuner (tune.cu)
 int tune_points(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s);
+// the tuner's cache (one "key value" line per entry, the last one wins) and
+// the device name used in its keys
+int tune_cache_get(const std::string& key);
+void tune_cache_put(const std::string& key, int value);
+std::string tune_device(int dev);
 // fine spectrum -> fine grid (inverse, both dimensions) and back (forward)
 int fine_fft_c2r(nusht_plan_t p, cudaStream_t s);
 int fine_fft_r2c(nusht_plan_t p, cudaStream_t s);
@@ -230,6 +308,24 @@ int dfft_cols_synth(nusht_plan_t p, cudaStream_t s);
 int dfft_rows_c2r(nusht_plan_t p, cudaStream_t s);
 int dfft_rows_r2c(nusht_plan_t p, cudaStream_t s);
 int dfft_cols_adjoint(nusht_plan_t p, cudaStream_t s);
+// FP32 fine-grid FFTs of mixed plans (dfft.cu): whether every length fits,
+// set-up (line tables, T, float deconvolution factors, the plan's member
+// entry), a member entry from a plan's buffers (col0 / row0 left 0), and the
+// passes for a device table of nm members with ncols / nrows CTAs in all
+bool sfft_fits(const nusht_sizes& z);
+int sfft_setup(nusht_plan_t p, const double* d1, const double* d2);
+void sfft_member(nusht_plan_t p, SfftMember& m);
+struct SfftLaunch {
+  const SfftMember* mem = nullptr;  // device table
+  int nm = 0, ncols = 0, nrows = 0;
+  int maxn1 = 0, maxn2 = 0;         // longest lines (shared memory per CTA)
+  bool wide = true;                 // every length has radices 2, 3, 4 only
+};
+int sfft_cols_synth(const SfftLaunch& l, cudaStream_t s);
+int sfft_rows_c2r(const SfftLaunch& l, cudaStream_t s);
+int sfft_rows_r2c(const SfftLaunch& l, cudaStream_t s);
+int sfft_cols_adjoint(const SfftLaunch& l, cudaStream_t s);
+SfftLaunch sfft_launch_of(nusht_plan_t p);
 // largest ES kernel width the spreading / interpolation kernels support
 constexpr int ES_WMAX = 20;
 // ES kernel width the accuracy formula asks for at NUFFT tolerance eps and

@@ -164,6 +164,10 @@ int tune_sigma(int lmax, int mmax, int64_t npts, const double* d_pts, double eps
   return NUSHT_OK;
 }
 
+int tune_cache_get(const std::string& key) { return cache_lookup(key); }
+void tune_cache_put(const std::string& key, int value) { cache_store(key, value); }
+std::string tune_device(int dev) { return device_name(dev); }
+
 int tune_points(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s) {
   const int mode = p->opts.tune;
   // untuned bin edge (plans whose caller fixed no bin come here once, at

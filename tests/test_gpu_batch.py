@@ -114,3 +114,35 @@ def test_batch64_members_against_oracle(env, tc, path):
         idx = np.concatenate([np.arange(oracle.lm_index(l, m, m), oracle.lm_index(l, l, m) + 1) for m in ms])
         got = cs[i].cpu().numpy().astype(np.complex128)
         assert oracle.eps_eff(ref[idx], got[idx]) <= TOL, (i, l)
+
+
+def test_batch_tuned_schedule(env, tmp_path, monkeypatch):
+    """opts.tune = 1 times the tensor-core contraction with 2, 4 and 8 degree
+    chunks per partial accumulation for each direction (and the members'
+    bin sizes), caches the choice, and tune = 2 takes it from the cache; the
+    tuned batch stays within the mixed tolerance against the oracle."""
+    torch, nu = env
+    monkeypatch.setenv("NUSHT_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    ls = [40, 100, 130, 200]
+    alms = [W.alm_gaussian(l, seed=80 + i, dtype=np.complex64) for i, l in enumerate(ls)]
+    pts = [W.points_uniform(2 * l * l, seed=90 + i) for i, l in enumerate(ls)]
+    dp = [torch.from_numpy(p).cuda() for p in pts]
+    bp = nu.BatchPlan(ls, dp, eps=1e-5, tune=1)
+    info = bp.info()
+    assert set(info["paths"]) == {2}
+    for cs, ca in info["schedule"]:
+        assert cs in (2, 4, 8) and ca in (2, 4, 8)
+    outs = bp.synth([torch.from_numpy(a).cuda() for a in alms])
+    ys = [np.random.default_rng(95 + i).standard_normal(p.shape[0]).astype(np.float32) for i, p in enumerate(pts)]
+    cs_ = bp.adjoint([torch.from_numpy(y).cuda() for y in ys])
+    bp.status()
+    for l, a, p, f, y, c in zip(ls, alms, pts, outs, ys, cs_):
+        sel = W.subset(p.shape[0], 2000, seed=l)
+        assert oracle.eps_eff(oracle.synth(a.astype(np.complex128), p[sel], l), f.double().cpu().numpy()[sel]) <= TOL
+        ref = oracle.adjoint(y.astype(np.float64), p, l)
+        assert oracle.eps_eff(ref, c.cpu().numpy().astype(np.complex128)) <= TOL
+    assert any(line.startswith("C:") for line in (tmp_path / "tune.txt").read_text().splitlines())
+    bp.close()
+    again = nu.BatchPlan(ls, dp, eps=1e-5, tune=2)
+    assert again.info()["schedule"] == info["schedule"]
+    again.close()

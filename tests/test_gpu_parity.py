@@ -473,3 +473,36 @@ def test_fp64_fft_kernels_theta_only(env):
     assert np.linalg.norm(c - c0) <= 1e-12 * np.linalg.norm(c0)
     sel = W.subset(pts.shape[0], 200, seed=64)
     assert oracle.eps_eff(oracle.synth(a, pts[sel], L), f[sel]) <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("L,npts,sigma", [(5, 3000, 0.0), (100, 20000, 0.0), (200, 40000, 1.5), (1023, 200000, 0.0)])
+def test_fp32_fft_kernels(env, L, npts, sigma):
+    """Mixed plans: this library's FP32 fine-grid FFT kernels (fft_kernels =
+    1, with the deconvolution fused into the column pass) against cuFFT's 2D
+    FP32 transforms and the separate deconvolution kernels (the default), on
+    lengths with every radix (n = 24 = 8 * 3, 420 = 4 * 3 * 5 * 7,
+    630 = 2 * 9 * 5 * 7 at sigma 1.5, 4096), the oracle on a seeded subset,
+    and the dot test (relative to |y| |f|, float rounding)."""
+    torch, nu = env
+    pts = W.points_uniform(npts, seed=71 + L)
+    a = W.alm_gaussian(L, seed=72 + L)
+    dp = dev(torch, pts)
+    own = nu.Plan(L, dp, eps=1e-5, precision="mixed", sigma=sigma, fft_kernels=1)
+    cuf = nu.Plan(L, dp, eps=1e-5, precision="mixed", sigma=sigma)
+    assert own.info()["n1"] == cuf.info()["n1"]
+    ad = dev(torch, a, torch.complex64)
+    f = own.synth(ad).double().cpu().numpy()
+    f0 = cuf.synth(ad).double().cpu().numpy()
+    assert np.linalg.norm(f - f0) <= 2e-6 * np.linalg.norm(f0)
+    y = np.random.default_rng(73 + L).standard_normal(npts).astype(np.float32)
+    yd = dev(torch, y)
+    c = own.adjoint(yd).cpu().numpy().astype(np.complex128)
+    c0 = cuf.adjoint(yd).cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(c - c0) <= 2e-6 * np.linalg.norm(c0)
+    sel = W.subset(npts, min(npts, 400), seed=74)
+    assert oracle.eps_eff(oracle.synth(a, pts[sel], L), f[sel]) <= TOL["mixed"]
+    if L <= 200:
+        assert oracle.eps_eff(oracle.adjoint(y.astype(np.float64), pts, L), c) <= TOL["mixed"]
+    lhs = float(np.dot(y.astype(np.float64), f))
+    rhs = oracle.alm_dot(c, a.astype(np.complex64).astype(np.complex128), L)
+    assert abs(lhs - rhs) <= 1e-6 * np.linalg.norm(y) * np.linalg.norm(f)
