@@ -14,7 +14,10 @@ packed m-major storage) are stated in the C file's header.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 against closed forms, the addition theorem, Gauss-Legendre orthogonality,
-scipy/mpmath, the reality symmetry, rotation invariance and the dot test.
+scipy/mpmath, the reality symmetry, rotation invariance and the dot test; the
+spin-weighted functions by ``tests/test_oracle_spin_pins.py`` (mpmath Wigner-d
+sums, the spin-0 harmonics and the analytic spin-0 gradient, the spin
+addition theorem, Gauss-Legendre orthogonality, the dot test).
 """
 from __future__ import annotations
 
@@ -62,6 +65,10 @@ def _load():
         lib.oracle_adjoint_m.argtypes = [ctypes.c_int, ctypes.c_int, i64, dp, dp, ctypes.c_int, ip, dp]
         lib.oracle_synth_grad.argtypes = [ctypes.c_int, ctypes.c_int, dp, i64, dp, dp, dp]
         lib.oracle_pointing.argtypes = [ctypes.c_int, ctypes.c_int, dp, i64, dp, dp]
+        lib.oracle_spin_lambda.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
+        lib.oracle_spin_synth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, i64, dp, dp, dp]
+        lib.oracle_spin_adjoint_m.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, dp, dp, dp, ctypes.c_int,
+                                              ip, dp, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
         return lib
@@ -175,6 +182,54 @@ def pointing(philm: np.ndarray, pts: np.ndarray, lmax: int, mmax: int | None = N
     out = np.empty((p.shape[0], 2), dtype=np.float64)
     _load().oracle_pointing(lmax, mmax, _dp(a), p.shape[0], _dp(p), _dp(out))
     return out
+
+
+def spin_lambda(lmax: int, spin: int, theta: float, mmax: int | None = None):
+    """(lambda^(+s), lambda^(-s)): sY_lm(theta, 0) and (-s)Y_lm(theta, 0) for all
+    packed (l, m), m >= 0 (entries with l < s are 0).  sY_lm =
+    (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) e^{i m phi}; spin 0 gives Pbar_lm."""
+    mmax = lmax if mmax is None else mmax
+    lp = np.zeros(nalm(lmax, mmax), dtype=np.float64)
+    lm = np.zeros(nalm(lmax, mmax), dtype=np.float64)
+    _load().oracle_spin_lambda(lmax, mmax, int(spin), float(theta), _dp(lp), _dp(lm))
+    return lp, lm
+
+
+def spin_synth(glm: np.ndarray, clm: np.ndarray, pts: np.ndarray, lmax: int, spin: int, mmax: int | None = None):
+    """Spin-s synthesis of two real fields, Q + i U = sum (G_lm + i C_lm) sY_lm
+    (G, C real-field coefficients in the packed layout); returns (Q, U)."""
+    mmax = lmax if mmax is None else mmax
+    g = _alm_pairs(glm, lmax, mmax)
+    c = _alm_pairs(clm, lmax, mmax)
+    p = _pts(pts)
+    q = np.empty(p.shape[0], dtype=np.float64)
+    u = np.empty(p.shape[0], dtype=np.float64)
+    _load().oracle_spin_synth(lmax, mmax, int(spin), _dp(g), _dp(c), p.shape[0], _dp(p), _dp(q), _dp(u))
+    return q, u
+
+
+def spin_adjoint(q: np.ndarray, u: np.ndarray, pts: np.ndarray, lmax: int, spin: int, mmax: int | None = None,
+                 mlist=None):
+    """Spin-s adjoint (type 1): the transpose of spin_synth; returns (G, C).
+    With ``mlist`` only those orders are computed (others NaN)."""
+    mmax = lmax if mmax is None else mmax
+    p = _pts(pts)
+    qv = np.ascontiguousarray(q, dtype=np.float64)
+    uv = np.ascontiguousarray(u, dtype=np.float64)
+    if qv.shape != (p.shape[0],) or uv.shape != (p.shape[0],):
+        raise ValueError("q and u must have one value per point")
+    if mlist is None:
+        ms = np.arange(mmax + 1, dtype=np.int32)
+        g = np.zeros(nalm(lmax, mmax), dtype=np.complex128)
+    else:
+        ms = np.unique(np.asarray(mlist, dtype=np.int32))
+        g = np.full(nalm(lmax, mmax), np.nan + 0j, dtype=np.complex128)
+    c = g.copy()
+    ms = np.ascontiguousarray(ms)
+    _load().oracle_spin_adjoint_m(lmax, mmax, int(spin), p.shape[0], _dp(p), _dp(qv), _dp(uv), int(ms.size),
+                                  ms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(g.view(np.float64)),
+                                  _dp(c.view(np.float64)))
+    return g, c
 
 
 def alm_dot(c: np.ndarray, a: np.ndarray, lmax: int, mmax: int | None = None) -> float:

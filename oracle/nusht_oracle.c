@@ -426,6 +426,255 @@ void oracle_pointing(int L, int mmax, const double* philm, int64_t npts, const d
   free(dph);
 }
 
+/*
+ * Spin-weighted harmonics (the spin-n generalisation named in the Conclusion,
+ * Sec. 5; the paper gives no formulas, so these are the standard ones).  For spin s >= 0 and m >= 0 (negative orders follow from the
+ * reality conditions below):
+ *   sY_lm(theta, phi) = (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) e^{i m phi},
+ * with d^l the Wigner small-d matrix.  For s = 0 this is Y_lm of the spin-0
+ * transform (Condon-Shortley phase), and 1Y_lm = (eth Y_lm) / sqrt(l(l+1))
+ * with eth = -(d/dtheta + (i / sin theta) d/dphi) on spin 0.
+ * lambda^(+s)_lm(theta) = sY_lm(theta, 0) uses d^l_{m,-s};
+ * lambda^(-s)_lm(theta) = (-s)Y_lm(theta, 0) uses d^l_{m,s}.
+ *
+ * d^l_{m,mp} for fixed (m, mp) from the three-term recurrence in l
+ *   (l-1) sqrt(l^2-m^2) sqrt(l^2-mp^2) d^l
+ *     = (2l-1) (l(l-1) cos(theta) - m mp) d^{l-1}
+ *       - l sqrt((l-1)^2-m^2) sqrt((l-1)^2-mp^2) d^{l-2},
+ * started at l0 = max(|m|, |mp|) from the closed forms
+ *   d^l_{l,mp}  = (-1)^{l-mp} sqrt(C(2l, l+mp)) cos^{l+mp}(theta/2) sin^{l-mp}(theta/2),
+ *   d^l_{m,l}   = sqrt(C(2l, l+m)) cos^{l+m}(theta/2) sin^{l-m}(theta/2),
+ *   d^l_{m,-l}  = (-1)^{l+m} sqrt(C(2l, l-m)) cos^{l-m}(theta/2) sin^{l+m}(theta/2).
+ * The start value and the pair (d^{l-1}, d^{l-2}) carry a separate binary
+ * exponent, as for the spin-0 columns.  The values are normalised by
+ * sqrt((2l+1)/(4 pi)) and multiplied by (-1)^s.
+ */
+/* value = p * 2^e of sqrt(C(2l, k)) cos^a(theta/2) sin^b(theta/2) */
+static xnum spin_start(int l, int k, int a, int b, double ch, double sh) {
+  xnum r = xnorm(1.0, 0);
+  /* C(2l, k) = prod_{i=1}^{k} (2l - k + i) / i, accumulated with exponents */
+  for (int i = 1; i <= k; ++i) r = xnorm(r.p * ((double)(2 * l - k + i) / (double)i), r.e);
+  /* square root of p * 2^e: make e even first */
+  if (r.e & 1) {
+    r.p *= 2.0;
+    r.e -= 1;
+  }
+  r = xnorm(sqrt(r.p), r.e / 2);
+  for (int i = 0; i < a; ++i) r = xnorm(r.p * ch, r.e);
+  for (int i = 0; i < b; ++i) r = xnorm(r.p * sh, r.e);
+  return r;
+}
+
+/* sqrt((2l+1)/(4 pi)) d^l_{m,mp}(theta) for l = l0..L into out[l - l0] (l0 = max(m, |mp|), m >= 0) */
+static void spin_column(int L, int m, int mp, double theta, double* out) {
+  const int amp = mp < 0 ? -mp : mp;
+  const int l0 = m > amp ? m : amp;
+  if (l0 > L) return;
+  const double ch = cos(0.5 * theta), sh = sin(0.5 * theta);
+  xnum st;
+  if (m >= amp) { /* d^{l0}_{l0, mp} */
+    st = spin_start(l0, l0 + mp, l0 + mp, l0 - mp, ch, sh);
+    if ((l0 - mp) & 1) st.p = -st.p;
+  } else if (mp > 0) { /* d^{l0}_{m, l0} */
+    st = spin_start(l0, l0 + m, l0 + m, l0 - m, ch, sh);
+  } else { /* d^{l0}_{m, -l0} */
+    st = spin_start(l0, l0 - m, l0 - m, l0 + m, ch, sh);
+    if ((l0 + m) & 1) st.p = -st.p;
+  }
+  /* cos(theta) as 1 - 2 sin^2(theta/2) or 2 cos^2(theta/2) - 1 (as for spin 0) */
+  double tc[2];
+  theta_cos(theta, tc);
+  const int north = tc[0] != 0.0;
+  const double w = tc[1];
+  double p1 = st.p, p2 = 0.0;
+  int e = st.e;
+  if (e > 0) {
+    p1 = ldexp(p1, e);
+    e = 0;
+  }
+  const double dm = (double)m, dmp = (double)mp;
+  out[0] = ldexp(p1, e) * sqrt((2.0 * l0 + 1.0) / (4.0 * M_PI));
+  for (int l = l0 + 1; l <= L; ++l) {
+    const double dl = (double)l;
+    const double xp1 = north ? (p1 - w * p1) : (w * p1 - p1); /* cos(theta) p1 */
+    double p;
+    if (l0 == 0 && l == 1) { /* m = mp = 0: the recurrence degenerates; d^1_00 = cos(theta) */
+      p = xp1;
+    } else {
+      const double den = (dl - 1.0) * sqrt((dl * dl - dm * dm) * (dl * dl - dmp * dmp));
+      p = (2.0 * dl - 1.0) * (dl * (dl - 1.0) * xp1 - dm * dmp * p1);
+      if (l - 2 >= l0)
+        p -= dl * sqrt(((dl - 1.0) * (dl - 1.0) - dm * dm) * ((dl - 1.0) * (dl - 1.0) - dmp * dmp)) * p2;
+      p /= den;
+    }
+    p2 = p1;
+    p1 = p;
+    if (e < 0 && p1 != 0.0) {
+      int k;
+      frexp(p1, &k);
+      int shift = k;
+      if (e + shift > 0) shift = -e;
+      p1 = ldexp(p1, -shift);
+      p2 = ldexp(p2, -shift);
+      e += shift;
+    }
+    out[l - l0] = ldexp(p1, e) * sqrt((2.0 * dl + 1.0) / (4.0 * M_PI));
+  }
+}
+
+/*
+ * lambda^(+s)_lm and lambda^(-s)_lm at theta for 0 <= m <= mmax, max(m, s) <= l <= L,
+ * in the packed layout (entries with l < s are 0).
+ */
+void oracle_spin_lambda(int L, int mmax, int s, double theta, double* lp, double* lm) {
+  const double sg = (s & 1) ? -1.0 : 1.0;
+  double* col = (double*)malloc(sizeof(double) * (size_t)(L + 1));
+  for (int m = 0; m <= mmax; ++m) {
+    const int l0 = m > s ? m : s;
+    for (int l = m; l <= L; ++l) lp[lm_index(L, l, m)] = lm[lm_index(L, l, m)] = 0.0;
+    if (l0 > L) continue;
+    spin_column(L, m, -s, theta, col);
+    for (int l = l0; l <= L; ++l) lp[lm_index(L, l, m)] = sg * col[l - l0];
+    spin_column(L, m, s, theta, col);
+    for (int l = l0; l <= L; ++l) lm[lm_index(L, l, m)] = sg * col[l - l0];
+  }
+  free(col);
+}
+
+/*
+ * Spin-s synthesis of two real fields:
+ *   Q + i U = sum_{l >= s} sum_{|m| <= l} (G_lm + i C_lm) sY_lm,
+ * G and C real-field coefficients (G_{l,-m} = (-1)^m conj(G_lm), same for C),
+ * stored for m >= 0 in the packed layout (entries with l < s ignored,
+ * Im of the m = 0 entries ignored).  With W = (lambda^(+s) + (-1)^s lambda^(-s)) / 2
+ * and X = (lambda^(+s) - (-1)^s lambda^(-s)) / 2 this is
+ *   Q = sum_l [ F_0 + 2 Re sum_{m>0} F_m e^{i m phi} ],  F_m = sum_l (G_lm W_lm + i C_lm X_lm),
+ *   U = the same with F_m = sum_l (C_lm W_lm - i G_lm X_lm).
+ */
+void oracle_spin_synth(int L, int mmax, int s, const double* glm, const double* clm, int64_t npts,
+                       const double* pts, double* q, double* u) {
+  const double sg = (s & 1) ? -1.0 : 1.0;
+#pragma omp parallel
+  {
+    double* cp = (double*)malloc(sizeof(double) * (size_t)(L + 1));
+    double* cn = (double*)malloc(sizeof(double) * (size_t)(L + 1));
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < npts; ++i) {
+      const double th = pts[2 * i], ph = pts[2 * i + 1];
+      double aq = 0.0, au = 0.0;
+      for (int m = 0; m <= mmax; ++m) {
+        const int l0 = m > s ? m : s;
+        if (l0 > L) break;
+        spin_column(L, m, -s, th, cp);
+        spin_column(L, m, s, th, cn);
+        double qr = 0.0, qi = 0.0, ur = 0.0, ui = 0.0;
+        for (int l = l0; l <= L; ++l) {
+          const double lpv = sg * cp[l - l0], lmv = sg * cn[l - l0];
+          const double W = 0.5 * (lpv + sg * lmv), X = 0.5 * (lpv - sg * lmv);
+          const double* g = glm + 2 * lm_index(L, l, m);
+          const double* c = clm + 2 * lm_index(L, l, m);
+          const double gi = (m == 0) ? 0.0 : g[1], ci = (m == 0) ? 0.0 : c[1];
+          /* G W + i C X */
+          qr += g[0] * W - ci * X;
+          qi += gi * W + c[0] * X;
+          /* C W - i G X */
+          ur += c[0] * W + gi * X;
+          ui += ci * W - g[0] * X;
+        }
+        if (m == 0) {
+          aq += qr;
+          au += ur;
+        } else {
+          const double cs = cos((double)m * ph), sn = sin((double)m * ph);
+          aq += 2.0 * (qr * cs - qi * sn);
+          au += 2.0 * (ur * cs - ui * sn);
+        }
+      }
+      q[i] = aq;
+      u[i] = au;
+    }
+    free(cp);
+    free(cn);
+  }
+}
+
+/*
+ * Spin-s adjoint (type 1): the transpose of oracle_spin_synth under the
+ * real inner product sum_l Re(.)_l0 + 2 sum_{l, m>0} Re(conj(.) .) applied to
+ * both G and C:
+ *   G_lm = sum_i (q_i W_lm + i u_i X_lm) e^{-i m phi_i},
+ *   C_lm = sum_i (u_i W_lm - i q_i X_lm) e^{-i m phi_i},
+ * for the orders in mlist (strictly increasing); entries with l < s are 0.
+ */
+void oracle_spin_adjoint_m(int L, int mmax, int s, int64_t npts, const double* pts, const double* q,
+                           const double* u, int nm, const int* mlist, double* outg, double* outc) {
+  const double sg = (s & 1) ? -1.0 : 1.0;
+  int nthreads = 1;
+#ifdef _OPENMP
+  nthreads = omp_get_max_threads();
+#endif
+  int64_t span = 0;
+  int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nm + 1));
+  for (int k = 0; k < nm; ++k) {
+    off[k] = span;
+    span += (L - mlist[k] + 1);
+  }
+  off[nm] = span;
+  /* per thread: G (re, im), C (re, im) per entry */
+  double* part = (double*)calloc((size_t)nthreads * (size_t)span * 4, sizeof(double));
+#pragma omp parallel num_threads(nthreads)
+  {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    double* acc = part + (size_t)t * (size_t)span * 4;
+    double* cp = (double*)malloc(sizeof(double) * (size_t)(L + 1));
+    double* cn = (double*)malloc(sizeof(double) * (size_t)(L + 1));
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < npts; ++i) {
+      const double th = pts[2 * i], ph = pts[2 * i + 1];
+      for (int k = 0; k < nm; ++k) {
+        const int m = mlist[k];
+        const int l0 = m > s ? m : s;
+        if (l0 > L) continue;
+        spin_column(L, m, -s, th, cp);
+        spin_column(L, m, s, th, cn);
+        const double cs = cos((double)m * ph), sn = -sin((double)m * ph); /* e^{-i m phi} */
+        for (int l = l0; l <= L; ++l) {
+          const double lpv = sg * cp[l - l0], lmv = sg * cn[l - l0];
+          const double W = 0.5 * (lpv + sg * lmv), X = 0.5 * (lpv - sg * lmv);
+          /* (q W + i u X)(cs + i sn) and (u W - i q X)(cs + i sn) */
+          const double gr = q[i] * W, gi = u[i] * X;
+          const double cr = u[i] * W, ci = -q[i] * X;
+          double* a = acc + 4 * (off[k] + (l - m));
+          a[0] += gr * cs - gi * sn;
+          a[1] += gr * sn + gi * cs;
+          a[2] += cr * cs - ci * sn;
+          a[3] += cr * sn + ci * cs;
+        }
+      }
+    }
+    free(cp);
+    free(cn);
+  }
+  for (int k = 0; k < nm; ++k) {
+    const int m = mlist[k];
+    for (int l = m; l <= L; ++l) {
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int t = 0; t < nthreads; ++t)
+        for (int c = 0; c < 4; ++c) v[c] += part[((size_t)t * span + off[k] + (l - m)) * 4 + c];
+      if (m == 0) v[1] = v[3] = 0.0;
+      outg[2 * lm_index(L, l, m)] = v[0];
+      outg[2 * lm_index(L, l, m) + 1] = v[1];
+      outc[2 * lm_index(L, l, m)] = v[2];
+      outc[2 * lm_index(L, l, m) + 1] = v[3];
+    }
+  }
+  free(part);
+  free(off);
+}
+
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
