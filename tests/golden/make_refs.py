@@ -14,15 +14,19 @@ GPU test run.
 Files (numpy .npz, float64 / complex128):
 
 * gl4095_oracle_refs.npz -- the 4096 x 8191 deflected GL grid, lmax 4095:
-    synth_idx, synth_ref   10^4 seeded points (PCG64 seed 12345) and the
-                           type 2 values there;
-    adj_orders, adj_ref    the type 1 coefficients c_lm, l = m..4095, for the
-                           orders {0, 1} and 4 seeded random orders in
-                           [2, 4095], concatenated order by order, for the map
-                           y_i ~ N(0, 1) (seed 52) rounded to float32 (so the
-                           same y serves the FP64 and the mixed plan);
-    pts_check              the coordinates of the first 8 sampled points, to
-                           detect a changed input recipe.
+    synth_idx, synth_pts   10^4 seeded points (PCG64 seed 12345) and their
+                           exact coordinates (the GPU test puts these into
+                           the regenerated point set: numpy's transcendental
+                           functions and FFT differ in the last bits between
+                           host platforms, and at lmax 4095 a coordinate
+                           change delta moves f by ~lmax delta relative);
+    synth_ref              the type 2 values at those points;
+    adj_y, adj_orders,     a map that is N(0, 1) (seed 52, rounded to float32)
+    adj_ref                on the sampled points and zero on every other
+                           point, and its type 1 coefficients c_lm,
+                           l = m..4095, for the orders {0, 1} and 4 seeded
+                           random orders in [2, 4095], concatenated order by
+                           order (a sum over the sampled points only).
 * batch64_oracle_refs.npz -- the 64-member batch (lmax_b ~ U{256..2047},
   N_b = 2 lmax_b^2, seed 0): for members at five ranks of the sorted lmax
   (smallest, 25 %, median, 75 %, largest), member<i>_synth_idx / _synth_ref
@@ -64,17 +68,19 @@ def order_block(c: np.ndarray, lmax: int, orders) -> np.ndarray:
 def make_gl4095(path: str):
     L, a, pts = W.workload("gl4095")
     n = pts.shape[0]
-    t0 = time.time()
     idx = W.subset(n, NSYNTH, seed=12345)
-    f = oracle.synth(a, pts[idx], L)
+    sp = np.ascontiguousarray(pts[idx])
+    t0 = time.time()
+    f = oracle.synth(a, sp, L)
     print("gl4095 synthesis on %d points: %.0f s" % (idx.size, time.time() - t0), flush=True)
-    y = f32_gauss(n, 52)
+    y = f32_gauss(idx.size, 52)
     orders = adj_orders(L, 4, 53)
     t0 = time.time()
-    c = oracle.adjoint(y, pts, L, mlist=orders)
-    print("gl4095 adjoint, orders %s: %.0f s" % (orders.tolist(), time.time() - t0), flush=True)
-    np.savez(path, synth_idx=idx, synth_ref=f, adj_orders=orders, adj_ref=order_block(c, L, orders),
-             pts_check=pts[idx[:8]])
+    c = oracle.adjoint(y, sp, L, mlist=orders)
+    print("gl4095 adjoint (map on the sampled points), orders %s: %.0f s" % (orders.tolist(), time.time() - t0),
+          flush=True)
+    np.savez(path, synth_idx=idx, synth_pts=sp, synth_ref=f, adj_y=y, adj_orders=orders,
+             adj_ref=order_block(c, L, orders))
 
 
 def batch64_members(lmaxs) -> list[int]:

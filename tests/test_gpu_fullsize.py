@@ -1,16 +1,36 @@
 """Parity at the benchmark's full size, in the configuration bench.py times:
 lmax = mmax = 4095 on the 4096 x 8191 deflected Gauss-Legendre grid
-(33,550,336 points), default plan options.
+(33,550,336 points).
 
-* synthesis on a seeded sample of points against the oracle's direct sum
-  (eps_eff <= 1e-10 in FP64, <= 1e-5 in mixed mode);
-* the adjoint through the full-size dot test <y, S a> = <S^H y, a>, since a
-  full-N oracle adjoint is O(L^2 N) = 5.6e14 operations.  For random y the
-  inner product is only ~ |y| |S a| / sqrt(N) (sqrt(N) = 5.8e3), so the
-  bound is taken relative to |y| |S a|: 1e-13 in FP64 (spreading and
-  interpolation use the same kernel values; only rounding differs),
-  1e-6 in mixed mode (float rounding).
+The expected values are the oracle's direct sums (Eq. SHTbase and Eq.
+adjointSHTbase), stored by tests/golden/make_refs.py, which calls only
+oracle/ on the seeded inputs of workloads/ (an O(lmax^2) sum per point takes
+minutes on host cores).  The file also stores the exact coordinates of the
+10^4 sampled points, and the test puts them into the regenerated point set
+before planning: numpy's transcendental functions and FFT differ in the last
+bits between host platforms, and at lmax 4095 a coordinate change delta
+moves f by ~lmax delta relative, more than the 1e-10 being tested.
+
+* synthesis at the 10^4 sampled points: eps_eff <= tol (relative l2 over
+  the sample, Sec. 4) and max_i |f_i - f_ref,i| <= tol max_i |f_ref,i|, so
+  that an error local to a few points (a pole ring, a bin edge, a skipped
+  item) is not diluted;
+* the adjoint of a map that is nonzero on the sampled points only (the GPU
+  path still spreads all 33.5M points), every degree of the orders {0, 1}
+  and four seeded random orders: eps_eff <= tol for each order on its own (a
+  wrong coefficient in one order fails even if the others are right);
+* the full-size dot test <y, S a> = <S^H y, a> for a dense map, relative to
+  |y| |S a| (1e-13 in FP64, where spreading and interpolation share their
+  kernel values; 1e-6 in mixed mode);
+* the same for the recurrence-table plans (FP64 legendre_table = 1) and for
+  the mixed plan that runs the recurrence every call (legendre_table = -1;
+  table mode is the mixed default).
+
+tol = 1e-10 in FP64 mode and 1e-5 in mixed mode.  Each test prints the
+measured errors.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -18,6 +38,8 @@ import oracle
 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+REFS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "gl4095_oracle_refs.npz")
 
 
 @pytest.fixture(scope="module")
@@ -31,26 +53,50 @@ def env():
     import paper_2406_14542_gb300 as nu
 
     L, a, pts = W.workload("gl4095")
-    return torch, nu, L, a, pts
+    refs = dict(np.load(REFS))
+    idx = refs["synth_idx"]
+    # same recipe and seeds: the regenerated sample agrees with the stored
+    # coordinates to rounding; the stored ones are used
+    assert np.allclose(pts[idx], refs["synth_pts"], rtol=0, atol=1e-9)
+    pts = pts.copy()
+    pts[idx] = refs["synth_pts"]
+    y = np.random.default_rng(52).standard_normal(pts.shape[0]).astype(np.float32).astype(np.float64)
+    ysp = np.zeros(pts.shape[0])
+    ysp[idx] = refs["adj_y"]
+    return torch, nu, L, a, pts, refs, y, ysp
 
 
-@pytest.mark.parametrize("prec,eps,tol,dot_tol", [("fp64", 1e-10, 1e-10, 1e-13), ("mixed", 1e-5, 1e-5, 1e-6)])
-def test_gl4095_synthesis_sample_and_dot(env, prec, eps, tol, dot_tol):
-    torch, nu, L, a, pts = env
+CASES = [("fp64", 1e-10, 1e-13, 0), ("mixed", 1e-5, 1e-6, 0), ("fp64", 1e-10, 1e-13, 1), ("mixed", 1e-5, 1e-6, -1)]
+
+
+@pytest.mark.parametrize("prec,tol,dot_tol,table", CASES)
+def test_gl4095_against_stored_oracle(env, prec, tol, dot_tol, table):
+    torch, nu, L, a, pts, refs, y, ysp = env
     n = pts.shape[0]
     cd = torch.complex128 if prec == "fp64" else torch.complex64
     rd = torch.float64 if prec == "fp64" else torch.float32
-    plan = nu.Plan(L, torch.from_numpy(pts).cuda(), eps=eps, precision=prec)
+    plan = nu.Plan(L, torch.from_numpy(pts).cuda(), eps=tol, precision=prec, legendre_table=table)
     ad = torch.from_numpy(a).to(cd).cuda()
     f = plan.synth(ad).double().cpu().numpy()
-    sel = W.subset(n, 256, seed=51)
-    assert oracle.eps_eff(oracle.synth(a, pts[sel], L), f[sel]) <= tol
-    y = np.random.default_rng(52).standard_normal(n)
-    if prec == "mixed":
-        y = y.astype(np.float32).astype(np.float64)
+    idx, fref = refs["synth_idx"], refs["synth_ref"]
+    e_syn = oracle.eps_eff(fref, f[idx])
+    e_max = float(np.max(np.abs(f[idx] - fref)) / np.max(np.abs(fref)))
+    csp = plan.adjoint(torch.from_numpy(ysp).to(rd).cuda()).cpu().numpy().astype(np.complex128)
     c = plan.adjoint(torch.from_numpy(y).to(rd).cuda()).cpu().numpy().astype(np.complex128)
+    e_orders = {}
+    pos = 0
+    for m in refs["adj_orders"].tolist():
+        k = L + 1 - m
+        ref = refs["adj_ref"][pos:pos + k]
+        pos += k
+        s = oracle.lm_index(L, m, m)
+        e_orders[m] = oracle.eps_eff(ref, csp[s:s + k])
     a_used = a.astype(np.complex64).astype(np.complex128) if prec == "mixed" else a
-    lhs = float(np.dot(y, f))
-    rhs = oracle.alm_dot(c, a_used, L)
-    assert abs(lhs - rhs) <= dot_tol * np.linalg.norm(y) * np.linalg.norm(f)
+    dot = abs(float(np.dot(y, f)) - oracle.alm_dot(c, a_used, L)) / (np.linalg.norm(y) * np.linalg.norm(f))
+    print("\n%s table=%d: synthesis eps_eff %.3g (max %.3g, 10^4 points); adjoint eps_eff by order %s; dot %.3g"
+          % (prec, table, e_syn, e_max, {m: "%.3g" % e for m, e in e_orders.items()}, dot))
     plan.close()
+    assert e_syn <= tol and e_max <= tol
+    assert all(e <= tol for e in e_orders.values()), e_orders
+    assert np.all(c[: L + 1].imag == 0) and np.all(csp[: L + 1].imag == 0)
+    assert dot <= dot_tol
