@@ -149,7 +149,10 @@ typedef struct {
                          library's FP32 line kernels for the fine grid (deconvolution fused
                          into the column pass; lengths up to 28672), slower than cuFFT on
                          GB300 and kept for comparison. */
-  int reserved[2];
+  int spin;           /* spin weight s >= 1 of nusht_synth_spin / nusht_adjoint_spin (NUSHT_FP64
+                         plans; the plan then holds the Wigner-d recurrence tables and two more
+                         ring maps); 0 = none */
+  int reserved;
 } nusht_opts;
 
 /* Sizes a plan uses; filled by nusht_plan_sizes (no GPU needed) and nusht_info. */
@@ -268,6 +271,39 @@ NUSHT_API int nusht_synth_grad_pts(nusht_plan_t p, const void* d_alm, const void
  * Asynchronous; allocates nothing; overwrites the plan's work buffers.
  */
 NUSHT_API int nusht_pointing(nusht_plan_t p, const void* d_philm, double* d_ptg, nusht_stream_t stream);
+
+/*
+ * nusht_synth_spin -- spin-weighted synthesis (the spin-n generalisation of
+ * the Conclusion, Sec. 5) of two real fields at the plan's points:
+ *     Q + i U = sum_{l >= s} sum_{|m| <= l} (G_lm + i C_lm) sY_lm,
+ *     sY_lm(theta, phi) = (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) e^{i m phi},
+ * for the plan's spin s = opts.spin >= 1, with d^l the Wigner small-d matrix
+ * (1Y_lm = eth Y_lm / sqrt(l (l+1)), eth = -(d/dtheta + (i/sin theta) d/dphi)).
+ * G and C are real-field coefficients (G_{l,-m} = (-1)^m conj(G_lm), same for
+ * C) in the packed m-major layout; entries with l < s and Im of the m = 0
+ * entries are ignored.  The same chain as nusht_synth (Eq. SHTfast) with a
+ * Wigner-d recurrence for S and the spin sign (-1)^s in the doubling.
+ *   d_glm, d_clm  device complex128[nalm]
+ *   d_q, d_u      device double[npts], caller's point order
+ * NUSHT_FP64 plans made with opts.spin >= 1 (NUSHT_EUNSUPPORTED otherwise).
+ * Asynchronous; allocates nothing.
+ */
+NUSHT_API int nusht_synth_spin(nusht_plan_t p, const void* d_glm, const void* d_clm, void* d_q, void* d_u,
+                               nusht_stream_t stream);
+
+/*
+ * nusht_adjoint_spin -- the adjoint (type 1) of nusht_synth_spin under
+ * <(G, C), (G', C')> = sum over both of the real-field inner product:
+ *     G_lm = sum_i (q_i W_lm + i u_i X_lm) e^{-i m phi_i},
+ *     C_lm = sum_i (u_i W_lm - i q_i X_lm) e^{-i m phi_i},
+ * W = (sY_lm + (-1)^s (-s)Y_lm) / 2, X = (sY_lm - (-1)^s (-s)Y_lm) / 2 at phi = 0.
+ *   d_q, d_u      device double[npts]
+ *   d_glm, d_clm  device complex128[nalm], overwritten (entries with l < s
+ *                 and Im of the m = 0 entries are 0)
+ * Asynchronous; allocates nothing.
+ */
+NUSHT_API int nusht_adjoint_spin(nusht_plan_t p, const void* d_q, const void* d_u, void* d_glm, void* d_clm,
+                                 nusht_stream_t stream);
 
 /*
  * nusht_adjoint_direct_noalloc -- type 1 transform (the adjoint, same result

@@ -19,7 +19,8 @@ Options (keyword arguments of Plan): sigma, kernel_width, tune (autotuner),
 deterministic (bit-reproducible adjoint), legendre_table (plan-time
 recurrence in HBM), fast_recurrence (double-float recurrence, opt-in),
 fp64_contraction, fft_kernels (-1: cuFFT FP64 instead of the double-float
-FFT kernels), profile (per-stage times, Plan.stage_times()).
+FFT kernels), profile (per-stage times, Plan.stage_times()), spin (spin-weighted
+transforms Plan.synth_spin / adjoint_spin, FP64).
 """
 from __future__ import annotations
 
@@ -38,7 +39,7 @@ EXPORTS = ("nusht_plan", "nusht_setpts", "nusht_synth", "nusht_adjoint", "nusht_
            "nusht_strerror", "nusht_last_error", "nusht_version", "nusht_adjoint_direct_noalloc",
            "nusht_plan_many", "nusht_synth_many", "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info",
            "nusht_plan_bin", "nusht_batch_status", "nusht_batch_path", "nusht_pointing", "nusht_adjoint_grad",
-           "nusht_synth_grad_pts", "nusht_batch_schedule")
+           "nusht_synth_grad_pts", "nusht_batch_schedule", "nusht_synth_spin", "nusht_adjoint_spin")
 
 
 class NushtError(RuntimeError):
@@ -52,7 +53,7 @@ class Opts(ctypes.Structure):
                 ("deterministic", ctypes.c_int), ("tune", ctypes.c_int), ("fp64_contraction", ctypes.c_int),
                 ("legendre_table", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("fast_recurrence", ctypes.c_int), ("fft_kernels", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("spin", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class Sizes(ctypes.Structure):
@@ -89,6 +90,8 @@ def load(path: str | None = None):
         lib.nusht_synth_grad.argtypes = [vp, vp, vp, vp, vp]
         lib.nusht_pointing.argtypes = [vp, vp, vp, vp]
         lib.nusht_adjoint_grad.argtypes = [vp, vp, vp, vp]
+        lib.nusht_synth_spin.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.nusht_adjoint_spin.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.nusht_synth_grad_pts.argtypes = [vp, vp, vp, vp, vp]
         lib.nusht_destroy.argtypes = [vp]
         lib.nusht_info.argtypes = [vp, ctypes.POINTER(Sizes)]
@@ -121,7 +124,8 @@ def load(path: str | None = None):
                      "nusht_adjoint_direct_noalloc", "nusht_plan_many", "nusht_synth_many",
                      "nusht_adjoint_many", "nusht_destroy_many", "nusht_batch_info", "nusht_plan_bin",
                      "nusht_batch_status", "nusht_batch_path", "nusht_pointing", "nusht_adjoint_grad",
-                     "nusht_synth_grad_pts", "nusht_batch_schedule"):
+                     "nusht_synth_grad_pts", "nusht_batch_schedule", "nusht_synth_spin",
+                     "nusht_adjoint_spin"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -140,8 +144,9 @@ def _check(code: int, where: str):
 
 
 def _opts(sigma=0.0, kernel_width=0, profile=False, fp64_contraction=False, legendre_table=0, tune=0,
-          tensor_cores=0, deterministic=False, fast_recurrence=False, fft_kernels=0) -> Opts:
+          tensor_cores=0, deterministic=False, fast_recurrence=False, fft_kernels=0, spin=0) -> Opts:
     o = Opts()
+    o.spin = int(spin)
     o.fft_kernels = int(fft_kernels)
     o.fast_recurrence = 1 if fast_recurrence else 0
     o.deterministic = 1 if deterministic else 0
@@ -257,7 +262,7 @@ class Plan:
     def __init__(self, lmax: int, pts, eps: float = 1e-10, precision="fp64", mmax: int | None = None,
                  sigma: float = 0.0, kernel_width: int = 0, profile: bool = False, fp64_contraction: bool = False,
                  legendre_table: int = 0, tune: int = 0, deterministic: bool = False,
-                 fast_recurrence: bool = False, fft_kernels: int = 0, stream=None):
+                 fast_recurrence: bool = False, fft_kernels: int = 0, spin: int = 0, stream=None):
         import torch
 
         self.lib = load()
@@ -272,7 +277,8 @@ class Plan:
         self.device = pts.device
         h = ctypes.c_void_p()
         o = _opts(sigma, kernel_width, profile, fp64_contraction, legendre_table, tune,
-                  deterministic=deterministic, fast_recurrence=fast_recurrence, fft_kernels=fft_kernels)
+                  deterministic=deterministic, fast_recurrence=fast_recurrence, fft_kernels=fft_kernels, spin=spin)
+        self.spin = int(spin)
         _check(self.lib.nusht_plan(ctypes.byref(h), self.lmax, self.mmax, self.npts,
                                    ctypes.c_void_p(pts.data_ptr() if self.npts else 0), self.eps, self.precision,
                                    ctypes.byref(o), _stream_ptr(stream)), "nusht_plan")
@@ -410,6 +416,31 @@ class Plan:
                                              ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(gp.data_ptr()),
                                              _stream_ptr(stream)), "nusht_synth_grad_pts")
         return gp
+
+    def synth_spin(self, glm, clm, stream=None):
+        """Spin-s synthesis (plan made with spin=s >= 1, FP64): Q + iU =
+        sum (G_lm + i C_lm) sY_lm at the points; returns (Q, U) float64."""
+        import torch
+
+        glm, clm = self._alm(glm), self._alm(clm)
+        q = torch.empty(self.npts, dtype=torch.float64, device=self.device)
+        u = torch.empty(self.npts, dtype=torch.float64, device=self.device)
+        _check(self.lib.nusht_synth_spin(self.handle, ctypes.c_void_p(glm.data_ptr()), ctypes.c_void_p(clm.data_ptr()),
+                                         ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                         _stream_ptr(stream)), "nusht_synth_spin")
+        return q, u
+
+    def adjoint_spin(self, q, u, stream=None):
+        """Adjoint of synth_spin: (G, C) complex128 coefficients."""
+        import torch
+
+        q, u = self._map(q), self._map(u)
+        g = torch.empty(self.nalm, dtype=torch.complex128, device=self.device)
+        c = torch.empty(self.nalm, dtype=torch.complex128, device=self.device)
+        _check(self.lib.nusht_adjoint_spin(self.handle, ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                           ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                           _stream_ptr(stream)), "nusht_adjoint_spin")
+        return g, c
 
     def pointing(self, philm, out=None, stream=None):
         """CMB lensing pointing (App. C): the deflected (theta', phi') of every

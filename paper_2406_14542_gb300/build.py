@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libnusht.so")
-SOURCES = ["plan.cu", "legendre.cu", "nufft.cu", "batch.cu", "tune.cu", "dfft.cu"]
+SOURCES = ["plan.cu", "legendre.cu", "nufft.cu", "batch.cu", "tune.cu", "dfft.cu", "spin.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -171,6 +171,24 @@ struct NufftBatch {
   int bin = 32;                      // largest bin edge (spreading tile size)
 };
 
+// Spin-weighted transforms (spin.cu): Wigner-d recurrence tables of the
+// plan's spin s (opts.spin), per packed (l, m), start values per order, the
+// two ring maps (Q and U; theta spectra in the adjoint) and the partial rows
+// of the adjoint
+struct SpinTables {
+  double* A = nullptr;        // sqrt((2l+1)(2l-1)) l / sqrt((l^2-m^2)(l^2-s^2))
+  double* Ab = nullptr;       // A m s / (l (l-1))
+  double* C = nullptr;        // the l-2 coefficient
+  double* st_mant = nullptr;  // start value at max(m, s) per (m, sign): mantissa ...
+  int* st_exp = nullptr;      // ... binary exponent ...
+  int* st_ab = nullptr;       // ... and powers of cos and sin of theta / 2 (a << 16 | b)
+  double2* GQ = nullptr;      // [mmax + 1][M]
+  double2* GU = nullptr;
+  double2* pg = nullptr;      // [nrows][nalm] partial sums of G and C
+  double2* pc = nullptr;
+  int nrows = 0;
+};
+
 struct StageEvents {
   cudaEvent_t ev[8] = {};
   bool ready = false;
@@ -227,6 +245,8 @@ struct nusht_plan_s {
   nusht::SfftMember* sfft_mem = nullptr;  // device copy of this plan's member entry
 
   size_t bytes = 0;
+
+  nusht::SpinTables spin;     // opts.spin > 0 (FP64 plans)
 
   // role inside a batch (see nusht::PlanRole); a standalone plan has all parts
   bool has_legendre = true, has_nufft = true, ghat_owned = true;
@@ -288,6 +308,12 @@ int interp_many(const NufftBatch& nb, float* const* maps, cudaStream_t s);
 int deconv_pad_many(const NufftBatch& nb, cudaStream_t s);
 int deconv_trunc_many(const NufftBatch& nb, cudaStream_t s);
 constexpr int ZERO_CHUNK = 1 << 14;  // floats zeroed per block
+
+// spin-weighted transforms (spin.cu)
+int spin_setup(nusht_plan_t p, cudaStream_t s);
+void spin_free(nusht_plan_t p);
+int spin_legendre_synth(nusht_plan_t p, const void* glm, const void* clm, cudaStream_t s);
+int spin_legendre_adjoint(nusht_plan_t p, void* glm, void* clm, cudaStream_t s);
 
 // autotuner (tune.cu)
 int tune_points(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s);

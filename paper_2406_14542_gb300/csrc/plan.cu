@@ -203,6 +203,7 @@ static void plan_free(nusht_plan_t p) {
   cudaGetDevice(&cur);
   cudaSetDevice(p->device);
   free_points(p);
+  spin_free(p);
   dev_free(p->leg.c);
   dev_free(p->leg.cdf);
   dev_free(p->leg.ahat);
@@ -392,6 +393,7 @@ static int plan_body(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStre
     NUSHT_TRY(legendre_build_tables(p, s));
     NUSHT_TRY(dev_alloc(&p->partial, (size_t)p->leg.blocks_per_m * p->nalm * cplx, &p->bytes));
     NUSHT_CUDA(cudaMemsetAsync(p->partial, 0, (size_t)p->leg.blocks_per_m * p->nalm * cplx, s));
+    if (p->opts.spin > 0) NUSHT_TRY(spin_setup(p, s));
   }
   NUSHT_TRY(make_ffts(p, d1.data(), d2.data()));
   NUSHT_TRY(spread_smem_optin());
@@ -443,6 +445,9 @@ int nusht::plan_create(nusht_plan_t* out, int lmax, int mmax, int64_t npts, cons
   }
   if (npts < 0 || npts > 0x7fffffffLL) return set_error(NUSHT_EINVAL, "npts must be in [0, 2^31)");
   if (npts > 0 && !d_pts) return set_error(NUSHT_EINVAL, "d_pts is NULL");
+  if (opts && (opts->spin < 0 || opts->spin > lmax)) return set_error(NUSHT_EINVAL, "spin must be in [0, lmax]");
+  if (opts && opts->spin > 0 && (precision != NUSHT_FP64 || !role.legendre || !role.nufft))
+    return set_error(NUSHT_EUNSUPPORTED, "spin transforms need a standalone NUSHT_FP64 plan");
   int dev = 0;
   NUSHT_TRY(check_device(&dev));
   const char* fa = std::getenv("NUSHT_FAIL_ALLOC_AFTER");
@@ -587,6 +592,42 @@ int nusht_synth_grad_pts(nusht_plan_t p, const void* d_alm, const void* d_cot, d
   NUSHT_TRY(deconv_pad(p, s));
   NUSHT_TRY(fine_fft_c2r(p, s));
   NUSHT_TRY(interp_grad(p, nullptr, nullptr, d_cot, d_gpts, s));
+  return NUSHT_OK;
+}
+
+int nusht_synth_spin(nusht_plan_t p, const void* d_glm, const void* d_clm, void* d_q, void* d_u,
+                     nusht_stream_t stream) {
+  if (!p) return set_error(NUSHT_EINVAL, "plan is NULL");
+  if (p->opts.spin <= 0 || !p->spin.A) return set_error(NUSHT_EUNSUPPORTED, "plan made without opts.spin");
+  if (!d_glm || !d_clm || (p->pts.npts > 0 && (!d_q || !d_u))) return set_error(NUSHT_EINVAL, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  // S for both fields at once (the Wigner-d recurrences are shared), then
+  // F and N for each
+  NUSHT_TRY(spin_legendre_synth(p, d_glm, d_clm, s));
+  for (int k = 0; k < 2; ++k) {
+    NUSHT_TRY(theta_fft(p, k ? p->spin.GU : p->spin.GQ, p->Ghat, -1, s));
+    NUSHT_TRY(deconv_pad(p, s));
+    NUSHT_TRY(fine_fft_c2r(p, s));
+    NUSHT_TRY(interp(p, k ? d_u : d_q, s));
+  }
+  return NUSHT_OK;
+}
+
+int nusht_adjoint_spin(nusht_plan_t p, const void* d_q, const void* d_u, void* d_glm, void* d_clm,
+                       nusht_stream_t stream) {
+  if (!p) return set_error(NUSHT_EINVAL, "plan is NULL");
+  if (p->opts.spin <= 0 || !p->spin.A) return set_error(NUSHT_EUNSUPPORTED, "plan made without opts.spin");
+  if (!d_glm || !d_clm || (p->pts.npts > 0 && (!d_q || !d_u))) return set_error(NUSHT_EINVAL, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  // N^dagger and F^dagger for each field into its theta-spectrum buffer, then
+  // D^dagger and S^dagger for both
+  for (int k = 0; k < 2; ++k) {
+    NUSHT_TRY(spread(p, k ? d_u : d_q, s));
+    NUSHT_TRY(fine_fft_r2c(p, s));
+    NUSHT_TRY(deconv_trunc(p, s));
+    NUSHT_TRY(theta_fft(p, p->Ghat, k ? p->spin.GU : p->spin.GQ, 1, s));
+  }
+  NUSHT_TRY(spin_legendre_adjoint(p, d_glm, d_clm, s));
   return NUSHT_OK;
 }
 
