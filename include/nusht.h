@@ -144,11 +144,13 @@ typedef struct {
                          run as this library's double-float kernels (one line per CTA in
                          shared memory, ~2^-47 relative per operation) when every length is
                          at most 14336; longer lengths use cuFFT's FP64 transforms;
-                         -1 = cuFFT's FP64 transforms always.  Mixed plans: 0 (default) or
-                         -1 = cuFFT FP32 (2D plans, separate deconvolution); 1 = this
-                         library's FP32 line kernels for the fine grid (deconvolution fused
-                         into the column pass; lengths up to 28672), slower than cuFFT on
-                         GB300 and kept for comparison. */
+                         -1 = cuFFT's FP64 transforms always.  Mixed plans: 1 = this
+                         library's FP32 line kernels for the fine grid (one line per CTA,
+                         deconvolution fused into the column pass; lengths whose line and
+                         twiddle table fit in 227 KB of shared memory, about 28,500),
+                         -1 = cuFFT FP32 (2D plans, separate deconvolution); 0 (default) =
+                         cuFFT for single plans, the FP32 line kernels for batched plans
+                         (where every member's column and row passes are one launch each). */
   int spin;           /* spin weight s >= 1 of nusht_synth_spin / nusht_adjoint_spin (NUSHT_FP64
                          plans; the plan then holds the Wigner-d recurrence tables and two more
                          ring maps); 0 = none */

@@ -1762,7 +1762,6 @@ int build_fused(nusht_batch_t p) {
       rows += (z.n1 + 1) / 2;
       sl.maxn1 = std::max(sl.maxn1, z.n1);
       sl.maxn2 = std::max(sl.maxn2, z.n2);
-      sl.wide = sl.wide && sfft_launch_of(q).wide;
     }
   }
   NUSHT_TRY(dev_alloc((void**)&p->d_nmem, nm.size() * sizeof(NufftMember), &p->bytes));
@@ -1898,6 +1897,10 @@ int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64
     }
     if (st != NUSHT_OK) break;
     p->sub.assign(nbatch, nullptr);
+    // members' fine-grid FFTs: by default this library's FP32 line kernels
+    // (two launches per direction for the whole batch); -1 keeps cuFFT
+    nusht_opts sub_opts = p->opts;
+    if (sub_opts.fft_kernels == 0) sub_opts.fft_kernels = 1;
     for (int i = 0; i < nbatch && st == NUSHT_OK; ++i) {
       const Bucket& b = p->buckets[p->bucket_of[i]];
       PlanRole role;
@@ -1905,7 +1908,7 @@ int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64
       role.nufft = true;
       role.M_override = b.M;
       role.ghat_external = b.Ghat + (size_t)p->slot_of[i] * (b.L + 1) * b.M;
-      st = plan_create(&p->sub[i], p->L[i], p->L[i], p->npts[i], d_pts[i], eps, precision, opts, s, role);
+      st = plan_create(&p->sub[i], p->L[i], p->L[i], p->npts[i], d_pts[i], eps, precision, &sub_opts, s, role);
       if (st == NUSHT_OK) p->bytes += p->sub[i]->bytes;
     }
     if (st != NUSHT_OK) break;

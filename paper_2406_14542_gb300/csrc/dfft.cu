@@ -162,9 +162,8 @@ __device__ __forceinline__ double2 c_value(float4 c) {
 }
 
 // ---------------------------------------------------------------------------
-// The line transform is written once for two complex types: CDF, the
-// float-pair complex above (FP64 plans), and CSF, plain float complex (mixed
-// plans; twiddles and odd-radix constants are the hi words of the table).
+// The float-pair line transform is written against a complex-type trait
+// (CDF: the float-pair complex above).
 // ---------------------------------------------------------------------------
 struct CDF {
   using V = float4;
@@ -183,25 +182,6 @@ struct CDF {
   static __device__ __forceinline__ void mac(V& acc, V a, float h, float l) { c_mac(acc, a, make_float2(h, l)); }
 };
 
-struct CSF {
-  using V = float2;
-  static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
-  static __device__ __forceinline__ V add(V a, V b) { return make_float2(a.x + b.x, a.y + b.y); }
-  static __device__ __forceinline__ V sub(V a, V b) { return make_float2(a.x - b.x, a.y - b.y); }
-  template <int SG>
-  static __device__ __forceinline__ V mul_i(V a) {
-    return SG > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
-  }
-  template <int SG>
-  static __device__ __forceinline__ V mul_tw(V a, float4 w) {
-    const float c = w.x, sn = SG > 0 ? w.z : -w.z;
-    return make_float2(fmaf(a.x, c, -a.y * sn), fmaf(a.x, sn, a.y * c));
-  }
-  static __device__ __forceinline__ void mac(V& acc, V a, float h, float) {
-    acc.x = fmaf(a.x, h, acc.x);
-    acc.y = fmaf(a.y, h, acc.y);
-  }
-};
 
 // ---------------------------------------------------------------------------
 // small DFTs of the butterflies (sign SG: +1 inverse, -1 forward)
@@ -476,9 +456,202 @@ __global__ void __launch_bounds__(NT) dfft_cols_adj_k(const float4* __restrict__
 // ---------------------------------------------------------------------------
 // FP32 fine-grid transforms of mixed plans, for one plan or every member of a
 // batch in one launch per pass: CTA b finds its member (the last one whose
-// first CTA is <= b) and the line it owns.  Same passes as above with plain
-// float complex values (8 bytes per value in shared memory).
+// first CTA is <= b) and the line it owns.
+//
+// The FP32 line transform is its own engine (the float-pair one above is
+// bound by its arithmetic, this one by shared-memory traffic): the odd
+// radices 3, 5, 7 first (so that every later pass has a power-of-two
+// stride), then radix-8 passes (three levels of the 2-power part each), then
+// one radix-4 or radix-2 pass; twiddles from a two-level table in shared
+// memory, W^k = C[k / 64] F[k % 64] (64 + N / 64 + 1 entries, 1.5 KB at
+// N = 8192), three table products per radix-8 butterfly and the other four
+// twiddles as products of those.  Value i of the line sits at
+// i ^ ((i >> 4 ^ i >> 8 ^ i >> 12) mod 16): a permutation inside each
+// aligned group of 16 that keeps contiguous and power-of-two-strided
+// accesses conflict-free and spreads the digit-reversed read of the output
+// over the banks (2 to 2.7 wavefronts per half-warp instead of 8).  512
+// threads per CTA, up to two CTAs per SM.
 // ---------------------------------------------------------------------------
+constexpr int SFFT_T = 512;
+
+__host__ __device__ __forceinline__ int spad(int i) { return i ^ (((i >> 4) ^ (i >> 8) ^ (i >> 12)) & 15); }
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 w) {
+  return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+__device__ __forceinline__ float2 caddf(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csubf(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+template <int SG>
+__device__ __forceinline__ float2 cmulif(float2 a) {  // a * (SG i)
+  return SG > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// e^(SG 2 pi i k / N) from the shared-memory table (fine 0..63, coarse after)
+template <int SG>
+__device__ __forceinline__ float2 stw(const float2* __restrict__ T, int k) {
+  const float2 w = cmulf(T[64 + (k >> 6)], T[k & 63]);
+  return SG > 0 ? w : make_float2(w.x, -w.y);
+}
+
+template <int SG>
+__device__ __forceinline__ void bfly4(float2* v) {
+  const float2 t0 = caddf(v[0], v[2]), t1 = csubf(v[0], v[2]);
+  const float2 t2 = caddf(v[1], v[3]), t3 = cmulif<SG>(csubf(v[1], v[3]));
+  v[0] = caddf(t0, t2);
+  v[2] = csubf(t0, t2);
+  v[1] = caddf(t1, t3);
+  v[3] = csubf(t1, t3);
+}
+
+// X_q = sum_r v_r e^(SG 2 pi i r q / 8): two 4-point DFTs of v_r + v_r+4 (even q)
+// and (v_r - v_r+4) e^(SG 2 pi i r / 8) (odd q)
+template <int SG>
+__device__ __forceinline__ void bfly8(float2* v) {
+  constexpr float H = 0.70710678118654752f;
+  float2 a[4], b[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    a[r] = caddf(v[r], v[r + 4]);
+    b[r] = csubf(v[r], v[r + 4]);
+  }
+  const float sg = (float)SG;
+  b[1] = make_float2(H * (b[1].x - sg * b[1].y), H * (b[1].y + sg * b[1].x));
+  b[2] = cmulif<SG>(b[2]);
+  b[3] = make_float2(H * (-b[3].x - sg * b[3].y), H * (-b[3].y + sg * b[3].x));
+  bfly4<SG>(a);
+  bfly4<SG>(b);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[2 * q] = a[q];
+    v[2 * q + 1] = b[q];
+  }
+}
+
+// odd R: X_q = v0 + sum_k cos(2 pi k q / R) (v_k + v_R-k) + SG i sin(...) (v_k - v_R-k),
+// cs[k - 1] = (cos, sin)(2 pi k / R), k = 1..R/2
+template <int R, int SG>
+__device__ __forceinline__ void bfly_odd(float2* v, const float2* cs) {
+  constexpr int Hh = R / 2;
+  float2 t[Hh], u[Hh], out[R];
+#pragma unroll
+  for (int k = 1; k <= Hh; ++k) {
+    t[k - 1] = caddf(v[k], v[R - k]);
+    u[k - 1] = csubf(v[k], v[R - k]);
+  }
+  out[0] = v[0];
+#pragma unroll
+  for (int k = 0; k < Hh; ++k) out[0] = caddf(out[0], t[k]);
+#pragma unroll
+  for (int q = 1; q <= Hh; ++q) {
+    float2 a = v[0], b = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 1; k <= Hh; ++k) {
+      const int m = (k * q) % R;
+      const float c = cs[(m <= Hh ? m : R - m) - 1].x;
+      const float sn = m <= Hh ? cs[m - 1].y : -cs[R - m - 1].y;
+      a = make_float2(fmaf(c, t[k - 1].x, a.x), fmaf(c, t[k - 1].y, a.y));
+      b = make_float2(fmaf(sn, u[k - 1].x, b.x), fmaf(sn, u[k - 1].y, b.y));
+    }
+    const float2 ib = cmulif<SG>(b);
+    out[q] = caddf(a, ib);
+    out[R - q] = csubf(a, ib);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = out[r];
+}
+
+// one in-place decimation-in-frequency pass of radix R over sub-blocks of
+// length L: butterfly (b, j) combines b L + j + r (L / R), output q times
+// W_L^(j q) = W_N^(j q N / L)
+template <int R, int SG>
+__device__ __forceinline__ void spass(float2* X, const float2* __restrict__ T, int N, int L) {
+  const int S = L / R, nb = N / R, mul = N / L;
+  const bool pow2 = (S & (S - 1)) == 0;
+  const int sh = __ffs(S) - 1;
+  float2 cs[R / 2 > 0 ? R / 2 : 1];
+  if constexpr (R == 3 || R == 5 || R == 7) {
+#pragma unroll
+    for (int k = 1; k <= R / 2; ++k) cs[k - 1] = stw<1>(T, k * (N / R));
+  }
+  for (int t = threadIdx.x; t < nb; t += SFFT_T) {
+    const int b = pow2 ? t >> sh : t / S;
+    const int j = t - b * S;
+    const int base = b * L + j;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = X[spad(base + r * S)];
+    if constexpr (R == 2) {
+      const float2 a = v[0];
+      v[0] = caddf(a, v[1]);
+      v[1] = csubf(a, v[1]);
+    } else if constexpr (R == 4) {
+      bfly4<SG>(v);
+    } else if constexpr (R == 8) {
+      bfly8<SG>(v);
+    } else {
+      bfly_odd<R, SG>(v, cs);
+    }
+    if (j != 0) {
+      const int k = mul * j;
+      const float2 w1 = stw<SG>(T, k);
+      v[1] = cmulf(v[1], w1);
+      if constexpr (R >= 3) {
+        const float2 w2 = stw<SG>(T, 2 * k);
+        v[2] = cmulf(v[2], w2);
+        if constexpr (R >= 4) {
+          const float2 w3 = cmulf(w1, w2);
+          v[3] = cmulf(v[3], w3);
+          if constexpr (R >= 5) {
+            const float2 w4 = stw<SG>(T, 4 * k);
+            v[4] = cmulf(v[4], w4);
+            if constexpr (R >= 7) {
+              v[5] = cmulf(v[5], cmulf(w1, w4));
+              v[6] = cmulf(v[6], cmulf(w2, w4));
+              if constexpr (R == 8) v[7] = cmulf(v[7], cmulf(w3, w4));
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) X[spad(base + r * S)] = v[r];
+  }
+}
+
+// the whole line: natural-order input in X (padded), output k at X[spad(rev[k])]
+template <int SG>
+__device__ void sline(float2* X, const float2* __restrict__ T, const DfftLen& f) {
+  int L = f.N;
+  for (int s = 0; s < f.npass; ++s) {
+    const int R = (int)((f.code >> (4 * s)) & 15u);
+    if (R == 8)
+      spass<8, SG>(X, T, f.N, L);
+    else if (R == 4)
+      spass<4, SG>(X, T, f.N, L);
+    else if (R == 2)
+      spass<2, SG>(X, T, f.N, L);
+    else if (R == 3)
+      spass<3, SG>(X, T, f.N, L);
+    else if (R == 5)
+      spass<5, SG>(X, T, f.N, L);
+    else
+      spass<7, SG>(X, T, f.N, L);
+    __syncthreads();
+    L /= R;
+  }
+}
+
+// shared memory of a CTA: the padded line, then the twiddle table
+__host__ __device__ __forceinline__ int sline_words(int n) { return (n + 15) & ~15; }
+__host__ __device__ __forceinline__ int stw_words(int n) { return 64 + n / 64 + 1; }
+
+__device__ __forceinline__ float2* stw_load(float2* Xs, int maxn, const DfftLen& f) {
+  float2* T = Xs + sline_words(maxn);
+  const int nt = stw_words(f.N);
+  for (int k = threadIdx.x; k < nt; k += SFFT_T) T[k] = __ldg(f.tw2 + k);
+  return T;
+}
+
 __device__ __forceinline__ int member_of(const SfftMember* __restrict__ mem, int nm, int b, bool rows) {
   int lo = 0, hi = nm - 1;
   while (lo < hi) {
@@ -493,15 +666,15 @@ __device__ __forceinline__ int member_of(const SfftMember* __restrict__ mem, int
 
 // synthesis, per (member, order m): deconvolve and zero-pad the theta
 // spectrum to n1, inverse DFT along theta, store T[m][.]
-template <int NT>
-__global__ void __launch_bounds__(NT) sfft_cols_synth_k(const SfftMember* __restrict__ mem, int nm) {
+__global__ void __launch_bounds__(SFFT_T, 2) sfft_cols_synth_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
   extern __shared__ float2 Xs[];
   const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, false)];
+  const float2* T = stw_load(Xs, maxn, q.f1);
   const int m = blockIdx.x - q.col0;
   const int n1 = q.n1, lmax = q.lmax, M = q.M;
   const float dm = q.d2[m];
   const float2* g = q.Gh + (int64_t)m * M;
-  for (int k1 = threadIdx.x; k1 < n1; k1 += NT) {
+  for (int k1 = threadIdx.x; k1 < n1; k1 += SFFT_T) {
     float2 v = make_float2(0.f, 0.f);
     const int k = k1 > lmax ? k1 - n1 : k1;
     if (k >= -lmax) {
@@ -509,84 +682,114 @@ __global__ void __launch_bounds__(NT) sfft_cols_synth_k(const SfftMember* __rest
       const float d = q.d1[k + lmax] * dm;
       v = make_float2(gv.x * d, gv.y * d);
     }
-    Xs[k1] = v;
+    Xs[spad(k1)] = v;
   }
   __syncthreads();
-  dif_line<1, NT, CSF>(Xs, q.f1);
+  sline<1>(Xs, T, q.f1);
   float2* dst = q.T + (int64_t)m * n1;
-  for (int j = threadIdx.x; j < n1; j += NT) dst[j] = Xs[__ldg(q.f1.rev + j)];
+  for (int j = threadIdx.x; j < n1; j += SFFT_T) dst[j] = Xs[spad(__ldg(q.f1.rev + j))];
 }
 
 // synthesis, per (member, row pair j, j + 1): the two Hermitian half spectra
 // packed as C = X_j + i X_j+1, one inverse DFT, x_j = Re, x_j+1 = Im
-template <int NT>
-__global__ void __launch_bounds__(NT) sfft_rows_c2r_k(const SfftMember* __restrict__ mem, int nm) {
+__global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_c2r_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
   extern __shared__ float2 Xs[];
   const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, true)];
+  const float2* T = stw_load(Xs, maxn, q.f2);
   const int j = 2 * (blockIdx.x - q.row0);
   const int n1 = q.n1, n2 = q.n2, mmax = q.mmax;
   const bool two = j + 1 < n1;
-  for (int k = mmax + 1 + threadIdx.x; k < n2 - mmax; k += NT) Xs[k] = make_float2(0.f, 0.f);
-  for (int m = threadIdx.x; m <= mmax; m += NT) {
-    const float2 a = q.T[(int64_t)m * n1 + j];
-    const float2 b = two ? q.T[(int64_t)m * n1 + j + 1] : make_float2(0.f, 0.f);
-    if (m == 0) {
-      Xs[0] = make_float2(a.x, b.x);  // a real transform takes only Re of m = 0
-    } else {
-      Xs[m] = make_float2(a.x - b.y, a.y + b.x);
-      Xs[n2 - m] = make_float2(a.x + b.y, b.x - a.y);
+  for (int k = mmax + 1 + threadIdx.x; k < n2 - mmax; k += SFFT_T) Xs[spad(k)] = make_float2(0.f, 0.f);
+  // the column pair of T: strided loads, four per thread in flight; with n1
+  // even (the fine-grid sizes are) T[m][j], T[m][j+1] are one aligned 16-byte load
+  const bool vec = (n1 & 1) == 0;
+  for (int m0 = threadIdx.x; m0 <= mmax; m0 += 4 * SFFT_T) {
+    float2 a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int m = m0 + u * SFFT_T;
+      a[u] = b[u] = make_float2(0.f, 0.f);
+      if (m <= mmax) {
+        const float2* t = q.T + (int64_t)m * n1 + j;
+        if (vec) {
+          const float4 ab = __ldg(reinterpret_cast<const float4*>(t));
+          a[u] = make_float2(ab.x, ab.y);
+          b[u] = make_float2(ab.z, ab.w);
+        } else {
+          a[u] = __ldg(t);
+          if (two) b[u] = __ldg(t + 1);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int m = m0 + u * SFFT_T;
+      if (m > mmax) break;
+      if (m == 0) {
+        Xs[spad(0)] = make_float2(a[u].x, b[u].x);  // a real transform takes only Re of m = 0
+      } else {
+        Xs[spad(m)] = make_float2(a[u].x - b[u].y, a[u].y + b[u].x);
+        Xs[spad(n2 - m)] = make_float2(a[u].x + b[u].y, b[u].x - a[u].y);
+      }
     }
   }
   __syncthreads();
-  dif_line<1, NT, CSF>(Xs, q.f2);
+  sline<1>(Xs, T, q.f2);
   float* r0 = q.grid + (int64_t)j * q.stride;
-  for (int n = threadIdx.x; n < n2; n += NT) {
-    const float2 c = Xs[__ldg(q.f2.rev + n)];
+  for (int n = threadIdx.x; n < n2; n += SFFT_T) {
+    const float2 c = Xs[spad(__ldg(q.f2.rev + n))];
     r0[n] = c.x;
     if (two) r0[q.stride + n] = c.y;
   }
 }
 
 // adjoint, per (member, row pair): spectra m <= mmax of rows j, j + 1 into T
-template <int NT>
-__global__ void __launch_bounds__(NT) sfft_rows_r2c_k(const SfftMember* __restrict__ mem, int nm) {
+__global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_r2c_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
   extern __shared__ float2 Xs[];
   const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, true)];
+  const float2* T = stw_load(Xs, maxn, q.f2);
   const int j = 2 * (blockIdx.x - q.row0);
   const int n1 = q.n1, n2 = q.n2, mmax = q.mmax;
   const bool two = j + 1 < n1;
   const float* r0 = q.grid + (int64_t)j * q.stride;
-  for (int n = threadIdx.x; n < n2; n += NT) Xs[n] = make_float2(r0[n], two ? r0[q.stride + n] : 0.f);
+  for (int n = threadIdx.x; n < n2; n += SFFT_T) Xs[spad(n)] = make_float2(r0[n], two ? r0[q.stride + n] : 0.f);
   __syncthreads();
-  dif_line<-1, NT, CSF>(Xs, q.f2);
-  for (int m = threadIdx.x; m <= mmax; m += NT) {
-    const float2 cm = Xs[__ldg(q.f2.rev + m)];
-    const float2 cn = Xs[__ldg(q.f2.rev + (m == 0 ? 0 : n2 - m))];
+  sline<-1>(Xs, T, q.f2);
+  for (int m = threadIdx.x; m <= mmax; m += SFFT_T) {
+    const float2 cm = Xs[spad(__ldg(q.f2.rev + m))];
+    const float2 cn = Xs[spad(__ldg(q.f2.rev + (m == 0 ? 0 : n2 - m)))];
     // X_j = (C[m] + conj C[n2-m]) / 2, X_j+1 = -i (C[m] - conj C[n2-m]) / 2
-    q.T[(int64_t)m * n1 + j] = make_float2(0.5f * (cm.x + cn.x), 0.5f * (cm.y - cn.y));
-    if (two) q.T[(int64_t)m * n1 + j + 1] = make_float2(0.5f * (cm.y + cn.y), 0.5f * (cn.x - cm.x));
+    const float2 xa = make_float2(0.5f * (cm.x + cn.x), 0.5f * (cm.y - cn.y));
+    const float2 xb = make_float2(0.5f * (cm.y + cn.y), 0.5f * (cn.x - cm.x));
+    float2* t = q.T + (int64_t)m * n1 + j;
+    if ((n1 & 1) == 0) {
+      *reinterpret_cast<float4*>(t) = make_float4(xa.x, xa.y, xb.x, xb.y);  // aligned: n1 and j even
+    } else {
+      t[0] = xa;
+      if (two) t[1] = xb;
+    }
   }
 }
 
 // adjoint, per (member, order m): forward DFT of T[m][.] along theta, then
 // Gh[m][kk] = H[k mod n1] d1[k] d2[m] for |k| <= lmax (k = kk or kk - M), else 0
-template <int NT>
-__global__ void __launch_bounds__(NT) sfft_cols_adj_k(const SfftMember* __restrict__ mem, int nm) {
+__global__ void __launch_bounds__(SFFT_T, 2) sfft_cols_adj_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
   extern __shared__ float2 Xs[];
   const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, false)];
+  const float2* T = stw_load(Xs, maxn, q.f1);
   const int m = blockIdx.x - q.col0;
   const int n1 = q.n1, lmax = q.lmax, M = q.M;
   const float2* src = q.T + (int64_t)m * n1;
-  for (int k = threadIdx.x; k < n1; k += NT) Xs[k] = src[k];
+  for (int k = threadIdx.x; k < n1; k += SFFT_T) Xs[spad(k)] = src[k];
   __syncthreads();
-  dif_line<-1, NT, CSF>(Xs, q.f1);
+  sline<-1>(Xs, T, q.f1);
   const float dm = q.d2[m];
   float2* g = const_cast<float2*>(q.Gh) + (int64_t)m * M;
-  for (int kk = threadIdx.x; kk < M; kk += NT) {
+  for (int kk = threadIdx.x; kk < M; kk += SFFT_T) {
     const int k = kk <= M / 2 ? kk : kk - M;
     float2 v = make_float2(0.f, 0.f);
     if (k >= -lmax && k <= lmax) {
-      const float2 c = Xs[__ldg(q.f1.rev + (k < 0 ? k + n1 : k))];
+      const float2 c = Xs[spad(__ldg(q.f1.rev + (k < 0 ? k + n1 : k)))];
       const float d = q.d1[k + lmax] * dm;
       v = make_float2(c.x * d, c.y * d);
     }
@@ -619,17 +822,32 @@ bool factor(int n, DfftLen& f) {
   return true;
 }
 
-int make_len(int N, DfftLen& f, size_t* bytes) {
-  f.N = N;
-  if (!factor(N, f)) return set_error(NUSHT_EUNSUPPORTED, "double-float FFT: length has a prime factor above 7");
-  std::vector<float4> tw(N);
-  for (int k = 0; k < N; ++k) {
-    const double a = 2.0 * M_PI * (double)k / (double)N;
-    const double c = std::cos(a), s = std::sin(a);
-    const float ch = (float)c, sh = (float)s;
-    tw[k] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
+// FP32 engine: the odd radices, then radix 8 while three factors of 2
+// remain, then one 4 or 2
+bool factor8(int n, DfftLen& f) {
+  std::vector<int> r;
+  for (int p : {7, 5, 3}) {
+    while (n % p == 0) {
+      r.push_back(p);
+      n /= p;
+    }
   }
-  // output k = k_1 + R_1 (k_2 + R_2 (...)) sits at sum_s k_s N / (R_1 ... R_s)
+  if ((n & (n - 1)) != 0) return false;
+  int e = 0;
+  while ((1 << e) < n) ++e;
+  for (int i = 0; i < e / 3; ++i) r.push_back(8);
+  if (e % 3 == 2) r.push_back(4);
+  if (e % 3 == 1) r.push_back(2);
+  if (r.empty() || (int)r.size() > DFFT_MAXPASS) return false;
+  f.npass = (int)r.size();
+  f.code = 0;
+  for (int i = 0; i < f.npass; ++i) f.code |= (unsigned long long)r[i] << (4 * i);
+  return true;
+}
+
+// digit-reversal table of a factorisation: output k = k_1 + R_1 (k_2 + R_2 (...))
+// sits at sum_s k_s N / (R_1 ... R_s)
+std::vector<int> rev_of(int N, const DfftLen& f) {
   std::vector<int> rev(N);
   for (int k = 0; k < N; ++k) {
     int kk = k, pos = 0, L = N;
@@ -642,6 +860,39 @@ int make_len(int N, DfftLen& f, size_t* bytes) {
     }
     rev[k] = pos;
   }
+  return rev;
+}
+
+// FP32 line of length N: factorisation, digit reversal and the two-level
+// twiddle table (F[k] = e^(2 pi i k / N), k < 64; C[c] = e^(2 pi i 64 c / N))
+int make_len_s(int N, DfftLen& f, size_t* bytes) {
+  f.N = N;
+  if (!factor8(N, f)) return set_error(NUSHT_EUNSUPPORTED, "FP32 FFT: length has a prime factor above 7");
+  const int nt = 64 + N / 64 + 1;
+  std::vector<float2> tw(nt);
+  for (int k = 0; k < nt; ++k) {
+    const double a = 2.0 * M_PI * (double)(k < 64 ? k : 64 * (k - 64)) / (double)N;
+    tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  const std::vector<int> rev = rev_of(N, f);
+  NUSHT_TRY(dev_alloc((void**)&f.tw2, (size_t)nt * sizeof(float2), bytes));
+  NUSHT_TRY(dev_alloc((void**)&f.rev, (size_t)N * sizeof(int), bytes));
+  NUSHT_CUDA(cudaMemcpy(f.tw2, tw.data(), (size_t)nt * sizeof(float2), cudaMemcpyHostToDevice));
+  NUSHT_CUDA(cudaMemcpy(f.rev, rev.data(), (size_t)N * sizeof(int), cudaMemcpyHostToDevice));
+  return NUSHT_OK;
+}
+
+int make_len(int N, DfftLen& f, size_t* bytes) {
+  f.N = N;
+  if (!factor(N, f)) return set_error(NUSHT_EUNSUPPORTED, "double-float FFT: length has a prime factor above 7");
+  std::vector<float4> tw(N);
+  for (int k = 0; k < N; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)N;
+    const double c = std::cos(a), s = std::sin(a);
+    const float ch = (float)c, sh = (float)s;
+    tw[k] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
+  }
+  const std::vector<int> rev = rev_of(N, f);
   NUSHT_TRY(dev_alloc((void**)&f.tw, (size_t)N * sizeof(float4), bytes));
   NUSHT_TRY(dev_alloc((void**)&f.rev, (size_t)N * sizeof(int), bytes));
   NUSHT_CUDA(cudaMemcpy(f.tw, tw.data(), (size_t)N * sizeof(float4), cudaMemcpyHostToDevice));
@@ -662,10 +913,6 @@ int optin_all(int b) {
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_r2c_k<NT>, a, b));
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k<false, NT>, a, b));
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_adj_k<true, NT>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_synth_k<NT>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_c2r_k<NT>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_r2c_k<NT>, a, b));
-  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_adj_k<NT>, a, b));
   return NUSHT_OK;
 }
 
@@ -684,6 +931,12 @@ int smem_optin() {
   const int b = DFFT_NMAX * (int)sizeof(float4);
   NUSHT_TRY(optin_all<DFFT_T_WIDE>(b));
   NUSHT_TRY(optin_all<DFFT_T_ODD>(b));
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  const int bs = SFFT_SMEM_MAX;
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_synth_k, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_c2r_k, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_r2c_k, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_adj_k, a, bs));
   done = 1;
   return NUSHT_OK;
 }
@@ -734,8 +987,10 @@ int dfft_setup(nusht_plan_t p, bool theta, bool fine, const double* d1, const do
 void dfft_free(nusht_plan_t p) {
   for (DfftLen* f : {&p->dft_theta, &p->dft_n1, &p->dft_n2}) {
     dev_free(f->tw);
+    dev_free(f->tw2);
     dev_free(f->rev);
     f->tw = nullptr;
+    f->tw2 = nullptr;
     f->rev = nullptr;
   }
   dev_free(p->tcols);
@@ -852,7 +1107,7 @@ int dfft_cols_adjoint(nusht_plan_t p, cudaStream_t s) {
 bool sfft_fits(const nusht_sizes& z) {
   auto ok = [](int n) {
     DfftLen f;
-    return n >= 2 && n <= SFFT_NMAX && factor(n, f);
+    return n >= 8 && n <= SFFT_NMAX && factor8(n, f) && sfft_smem(n) <= SFFT_SMEM_MAX;
   };
   return ok(z.n1) && ok(z.n2) && z.n2 % 2 == 0 && z.n1 > 2 * z.lmax && 2 * z.mmax < z.n2;
 }
@@ -860,8 +1115,8 @@ bool sfft_fits(const nusht_sizes& z) {
 int sfft_setup(nusht_plan_t p, const double* d1, const double* d2) {
   const nusht_sizes& z = p->sz;
   NUSHT_TRY(smem_optin());
-  NUSHT_TRY(make_len(z.n1, p->dft_n1, &p->bytes));
-  NUSHT_TRY(make_len(z.n2, p->dft_n2, &p->bytes));
+  NUSHT_TRY(make_len_s(z.n1, p->dft_n1, &p->bytes));
+  NUSHT_TRY(make_len_s(z.n2, p->dft_n2, &p->bytes));
   NUSHT_TRY(dev_alloc(&p->tcols, (size_t)(z.mmax + 1) * z.n1 * sizeof(float2), &p->bytes));
   std::vector<float> f1(2 * z.lmax + 1), f2(z.mmax + 1);
   for (size_t i = 0; i < f1.size(); ++i) f1[i] = (float)d1[i];
@@ -904,18 +1159,15 @@ SfftLaunch sfft_launch_of(nusht_plan_t p) {
   l.nrows = (p->sz.n1 + 1) / 2;
   l.maxn1 = p->sz.n1;
   l.maxn2 = p->sz.n2;
-  l.wide = wide(p->dft_n1) && wide(p->dft_n2);
   return l;
 }
+
+int sfft_smem(int n) { return (sline_words(n) + stw_words(n)) * (int)sizeof(float2); }
 
 #define NUSHT_SFFT_LAUNCH(KERNEL, NCTA, NMAXLEN)                                                       \
   do {                                                                                                 \
     if ((NCTA) <= 0) return NUSHT_OK;                                                                  \
-    const size_t sm = (size_t)(NMAXLEN) * sizeof(float2);                                              \
-    if (l.wide)                                                                                        \
-      KERNEL<DFFT_T_WIDE><<<(NCTA), DFFT_T_WIDE, sm, s>>>(l.mem, l.nm);                                \
-    else                                                                                               \
-      KERNEL<DFFT_T_ODD><<<(NCTA), DFFT_T_ODD, sm, s>>>(l.mem, l.nm);                                  \
+    KERNEL<<<(NCTA), SFFT_T, (size_t)sfft_smem(NMAXLEN), s>>>(l.mem, l.nm, (NMAXLEN));                 \
     NUSHT_CUDA(cudaGetLastError());                                                                    \
     return NUSHT_OK;                                                                                   \
   } while (0)

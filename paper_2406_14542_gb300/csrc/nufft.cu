@@ -47,9 +47,12 @@ __device__ __forceinline__ double es_psi(double z, double beta) {
   double r = 1.0 - z * z;
   return r > 0.0 ? exp(beta * (sqrt(r) - 1.0)) : 0.0;
 }
+// exp(beta (sqrt(1 - z^2) - 1)) as 2^(beta log2(e) (sqrt(1 - z^2) - 1)): exp2f
+// is the shorter of the two on the GPU; spreading and interpolation share it,
+// so the FP32 adjoint stays the exact transpose
 __device__ __forceinline__ float es_psif(float z, float beta) {
   float r = 1.0f - z * z;
-  return r > 0.0f ? expf(beta * (sqrtf(r) - 1.0f)) : 0.0f;
+  return r > 0.0f ? exp2f((beta * 1.44269504088896341f) * (sqrtf(r) - 1.0f)) : 0.0f;
 }
 // d psi / dz
 __device__ __forceinline__ double es_dpsi(double z, double beta) {
@@ -882,10 +885,14 @@ __global__ void __launch_bounds__(128) spread_pt_k(float* __restrict__ grid, int
     }
   }
   __syncthreads();
+  // tile row of t from a float reciprocal: (t + 1/2) / tw is at least
+  // 1 / (2 tw) from an integer, far above the rounding for t < tw^2 < 2^13
+  const float itw = 1.0f / (float)tw;
   for (int t = threadIdx.x; t < tw * tw; t += blockDim.x) {
     const float v = tile[t];
     if (v != 0.f) {
-      int r = r0 + t / tw, c = c0 + t % tw;
+      const int tr = __float2int_rz(((float)t + 0.5f) * itw);
+      int r = r0 + tr, c = c0 + (t - tr * tw);
       while (r >= n1) r -= n1;
       while (c >= n2) c -= n2;
       atomicAdd(grid + (int64_t)r * stride + c, v);
@@ -1021,10 +1028,12 @@ __global__ void __launch_bounds__(128) spread_many_k(const NufftMember* __restri
     }
   }
   __syncthreads();
+  const float itw = 1.0f / (float)tw;  // exact row of t, as in spread_pt_k
   for (int t = threadIdx.x; t < tw * tw; t += blockDim.x) {
     const float v = tile[t];
     if (v != 0.f) {
-      int r = r0 + t / tw, c = c0 + t % tw;
+      const int tr = __float2int_rz(((float)t + 0.5f) * itw);
+      int r = r0 + tr, c = c0 + (t - tr * tw);
       while (r >= q.n1) r -= q.n1;
       while (c >= q.n2) c -= q.n2;
       atomicAdd(q.grid + (int64_t)r * q.stride + c, v);

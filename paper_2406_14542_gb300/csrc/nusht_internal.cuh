@@ -112,7 +112,8 @@ constexpr int DFFT_MAXPASS = 16;
 struct DfftLen {
   int N = 0, npass = 0;
   unsigned long long code = 0;  // radix of pass s in bits [4s, 4s + 4)
-  float4* tw = nullptr;
+  float4* tw = nullptr;         // float-pair twiddles e^(2 pi i k / N), k < N (double-float engine)
+  float2* tw2 = nullptr;        // FP32 engine: e^(2 pi i k / N) for k < 64, then for k = 64 c
   int* rev = nullptr;
 };
 
@@ -345,8 +346,11 @@ struct SfftLaunch {
   const SfftMember* mem = nullptr;  // device table
   int nm = 0, ncols = 0, nrows = 0;
   int maxn1 = 0, maxn2 = 0;         // longest lines (shared memory per CTA)
-  bool wide = true;                 // every length has radices 2, 3, 4 only
 };
+// shared memory of an FP32 line kernel CTA for lines up to n values (padded
+// line + twiddle table), and its ceiling (the sm_103 per-CTA maximum)
+int sfft_smem(int n);
+constexpr int SFFT_SMEM_MAX = 227 * 1024;
 int sfft_cols_synth(const SfftLaunch& l, cudaStream_t s);
 int sfft_rows_c2r(const SfftLaunch& l, cudaStream_t s);
 int sfft_rows_r2c(const SfftLaunch& l, cudaStream_t s);

@@ -146,3 +146,35 @@ def test_batch_tuned_schedule(env, tmp_path, monkeypatch):
     again = nu.BatchPlan(ls, dp, eps=1e-5, tune=2)
     assert again.info()["schedule"] == info["schedule"]
     again.close()
+
+
+def test_batch_fp32_fft_kernels(env):
+    """The batch default (fft_kernels = 0): every member's fine-grid FFT by
+    this library's FP32 line kernels, two launches per direction for the
+    whole batch (radix 8, 4, 2 and odd 3 / 5 / 7 lengths among the members),
+    against cuFFT per member (fft_kernels = -1) and the oracle."""
+    torch, nu = env
+    ls = [3, 16, 40, 63, 100, 130, 7, 211]
+    alms = [W.alm_gaussian(l, seed=300 + 10 * i, dtype=np.complex64) for i, l in enumerate(ls)]
+    pts = [W.points_uniform(2 * l * l, seed=301 + 10 * i) for i, l in enumerate(ls)]
+    dpts = [torch.from_numpy(p).cuda() for p in pts]
+    own = nu.BatchPlan(ls, dpts, eps=1e-5)
+    cuf = nu.BatchPlan(ls, dpts, eps=1e-5, fft_kernels=-1)
+    da = [torch.from_numpy(a).cuda() for a in alms]
+    fo, fc = own.synth(da), cuf.synth(da)
+    rng = np.random.default_rng(302)
+    ys = [torch.from_numpy(rng.standard_normal(p.shape[0]).astype(np.float32)).cuda() for p in pts]
+    co, cc = own.adjoint(ys), cuf.adjoint(ys)
+    own.status()
+    for l, a, p, f1, f0, c1, c0, y in zip(ls, alms, pts, fo, fc, co, cc, ys):
+        f1, f0 = f1.double().cpu().numpy(), f0.double().cpu().numpy()
+        c1 = c1.cpu().numpy().astype(np.complex128)
+        c0 = c0.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(f1 - f0) <= 2e-6 * np.linalg.norm(f0), l
+        assert np.linalg.norm(c1 - c0) <= 2e-6 * np.linalg.norm(c0), l
+        sel = W.subset(p.shape[0], 2000, seed=l)
+        assert oracle.eps_eff(oracle.synth(a.astype(np.complex128), p[sel], l), f1[sel]) <= TOL, l
+        ref = oracle.adjoint(y.double().cpu().numpy(), p, l)
+        assert oracle.eps_eff(ref, c1) <= TOL, l
+    own.close()
+    cuf.close()
