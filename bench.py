@@ -246,6 +246,9 @@ def main():
                     help="skip the opt-in double-float recurrence (fast_recurrence=1) runs")
     ap.add_argument("--no-pointing", action="store_true", help="skip the lensing pointing measurement")
     ap.add_argument("--no-autograd", action="store_true", help="skip the differentiable-transform measurement")
+    ap.add_argument("--no-spin", action="store_true", help="skip the spin-2 transform measurement")
+    ap.add_argument("--sweep-workload", default="gl1023", choices=["gl1023", "gl2047", "gl4095"],
+                    help="workload of --sweep")
     ap.add_argument("--only-batch", action="store_true", help="run only the 64-transform batched measurement")
     ap.add_argument("--batch-n", type=int, default=64, help="transforms in the batched workload")
     ap.add_argument("--batch-lmax", type=int, default=2047, help="largest lmax of the batched workload")
@@ -399,6 +402,7 @@ def main():
         torch.cuda.empty_cache()
 
     pointing = None if args.no_pointing else run_pointing(torch, nu, args, dist, L)
+    spin = None if args.no_spin else run_spin(torch, nu, args, dist, rank, L, pts)
     autograd = None if args.no_autograd or args.workload != WORKLOAD else run_autograd(torch, nu, args, dist)
 
     batch = None
@@ -512,6 +516,8 @@ def main():
         line["pointing"] = pointing
     if autograd is not None:
         line["autograd"] = autograd
+    if spin is not None:
+        line["spin2"] = spin
     if batch is not None:
         line["batch64"] = batch
     if cpu is not None:
@@ -576,6 +582,55 @@ def run_pointing(torch, nu, args, dist, L):
             "rms_deflection_arcmin": float(np.sqrt(np.mean(moved**2)) * 180 * 60 / np.pi)}
 
 
+def run_spin(torch, nu, args, dist, rank, L, pts):
+    """Spin-2 synthesis + adjoint (Q + iU = sum (G + iC) 2Y_lm and its
+    transpose; the spin-n generalisation of the Conclusion, Sec. 5) on the
+    workload's points, FP64 at eps 1e-10: ms per step, and eps_eff of (Q, U)
+    against the oracle's direct sum on a seeded sample of points."""
+    npts = pts.shape[0]
+    g = W.alm_gaussian(L, seed=41, spectrum="inv_l1_sq")
+    c = W.alm_gaussian(L, seed=42, spectrum="inv_l1_sq")
+    dpts = torch.from_numpy(pts).cuda()
+    t0 = time.perf_counter()
+    plan = nu.Plan(L, dpts, eps=EPS["fp64"], precision="fp64", spin=2)
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t0
+    dg, dc = torch.from_numpy(g).cuda(), torch.from_numpy(c).cuda()
+    rng = np.random.default_rng(43)
+    yq = torch.from_numpy(rng.standard_normal(npts)).cuda()
+    yu = torch.from_numpy(rng.standard_normal(npts)).cuda()
+
+    def step():
+        plan.synth_spin(dg, dc)
+        plan.adjoint_spin(yq, yu)
+
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ms = max_over_ranks(dist, time_steps(torch, step, args.steps, args.warmup, dist))
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    q, u = plan.synth_spin(dg, dc)
+    e[1].record()
+    plan.adjoint_spin(yq, yu)
+    e[2].record()
+    torch.cuda.synchronize()
+    par = None
+    if rank == 0:
+        import oracle
+
+        sel = W.subset(npts, 200, seed=44)
+        rq, ru = oracle.spin_synth(g, c, pts[sel], L, 2)
+        got = np.concatenate([q.cpu().numpy()[sel], u.cpu().numpy()[sel]])
+        par = oracle.eps_eff(np.concatenate([rq, ru]), got)
+    nbytes = plan.info()["bytes_device"]
+    plan.close()
+    del dpts, dg, dc, yq, yu, q, u
+    torch.cuda.empty_cache()
+    return {"ms_per_step": ms, "synth_ms": e[0].elapsed_time(e[1]), "adjoint_ms": e[1].elapsed_time(e[2]),
+            "eps_eff": par, "eps_eff_sample": 200, "plan_s": t_plan, "plan_GB": nbytes / 1e9, "spin": 2,
+            "what": "FP64 Wigner-d recurrences (both +-s chains per ring pair) and FP64 sums; theta FFT, "
+                    "fine-grid FFT and NUFFT once per field (Q, U)", "clocks": clk.summary()}
+
+
 def run_autograd(torch, nu, args, dist):
     """The differentiable transform (autograd) on the lmax 2047 deflected GL
     grid (8,386,560 points), FP64 at eps 1e-10: one forward synthesis and the
@@ -605,15 +660,16 @@ def run_autograd(torch, nu, args, dist):
 
 def run_sweep(torch, nu, args):
     """eps in {1e-2, 1e-6, 1e-10} x sigma in {1.25, 1.5, 2} (FP64; mixed for
-    eps >= 1e-6) on the lmax 1023 deflected GL grid: eps_eff against the oracle
-    on a 3000-point subset, milliseconds per synthesis + adjoint and the
-    per-stage split, as the paper's accuracy/operator breakdown does."""
+    eps >= 1e-6) on a deflected GL grid (--sweep-workload, lmax 1023 by
+    default): eps_eff against the oracle on a seeded subset (3000 points, 600
+    at lmax 4095), milliseconds per synthesis + adjoint and the per-stage
+    split, as the paper's accuracy/operator breakdown does."""
     import oracle
 
-    L, a, pts = W.workload("gl1023")
+    L, a, pts = W.workload(args.sweep_workload)
     npts = pts.shape[0]
     dpts = torch.from_numpy(pts).cuda()
-    sel = W.subset(npts, 3000, seed=18)
+    sel = W.subset(npts, 3000 if L <= 2047 else 600, seed=18)
     f_ref = oracle.synth(a, pts[sel], L)
     y_host = np.random.default_rng(6).standard_normal(npts)
     out = []
@@ -645,7 +701,8 @@ def run_sweep(torch, nu, args):
                             "stages_ms": st})
                 plan.close()
                 torch.cuda.empty_cache()
-    return {"workload": "deflected GL grid 1024x2047 (%d pts), lmax=mmax=1023" % npts, "runs": out}
+    return {"workload": "deflected GL grid %dx%d (%d pts), lmax=mmax=%d" % (L + 1, 2 * L + 1, npts, L),
+            "oracle_sample": int(sel.size), "runs": out}
 
 
 def run_batch64(torch, nu, args, dist, rank, sequential=True):
