@@ -185,8 +185,10 @@ struct SpinTables {
   int* st_ab = nullptr;       // ... and powers of cos and sin of theta / 2 (a << 16 | b)
   double2* GQ = nullptr;      // [mmax + 1][M]
   double2* GU = nullptr;
-  double2* pg = nullptr;      // [nrows][nalm] partial sums of G and C
-  double2* pc = nullptr;
+  float4* ap = nullptr;       // per call: (G + iC) / 2 and (-1)^s (G - iC) / 2 as float pairs
+  float4* am = nullptr;
+  float4* pg = nullptr;       // [nrows][nalm] float-pair partial sums of G and C
+  float4* pc = nullptr;
   int nrows = 0;
 };
 

@@ -14,25 +14,37 @@
 // G(2 pi - theta) = (-1)^(m+s) F(theta).
 //
 // Legendre part.  For each (order m, ring pair theta, pi - theta) two Wigner-d
-// recurrences in l run in FP64 (sqrt((2l+1)/4pi) d^l_{m,-s} and d^l_{m,s}):
+// recurrences in l run in FP64 (pv = lambda+ ~ d^l_{m,-s}, nv = lambda- ~
+// d^l_{m,s}):
 //   v_l = A_l (x - b_l) v_{l-1} - C_l v_{l-2},  b_l = -/+ m s / (l (l-1)),
 // three FP64 operations per step with the plan-time tables A_l, A_l m s /
 // (l (l-1)) and C_l; started at l0 = max(m, s) from
 // sqrt(C(2 l0, k)) cos^a(theta/2) sin^b(theta/2) with an integer exponent
 // beside the mantissa (values below 2^-300 are carried scaled and not
 // accumulated, as in legendre.cu).  Since d^l_{m,-s}(pi - theta) =
-// (-1)^(l+m) d^l_{m,s}(theta), the two chains at theta give both rings: W
-// changes by (-1)^(l+m+s) and X by -(-1)^(l+m+s) at pi - theta.  One ring
-// pair per lane, four passes per warp over an item's 128 ring pairs; every
-// (order, ring block) is processed (the spin-0 polar-skip list does not
-// apply to spin functions).  The adjoint reduces each degree's products over
-// the warp's lanes and writes one partial row per (ring block, pass).
+// (-1)^(l+m) d^l_{m,s}(theta), the two chains at theta give both rings: with
+// p = (-1)^(l+m+s), pv(pi - theta) = p (-1)^s nv and nv(pi - theta) =
+// p (-1)^s pv.  In terms of A+ = (G + iC) / 2 and A- = (-1)^s (G - iC) / 2,
+//   north: F^Q = sum pv A+ + nv A-,   F^U = -i (sum pv A+ - nv A-),
+//   south: F^Q = (-1)^s sum p (nv A+ + pv A-),  F^U = (-1)^s i sum p (pv A- - nv A+),
+// four complex sums per ring pair, kept as float pairs on the FP32 pipe
+// (the FP64 pipe carries only the six recurrence operations per degree).
+// The adjoint is the transpose: with B+- = H^Q +- i H^U at each ring,
+// U1 = (B+_n + p B-_s) / 2, U2 = (-1)^s (B-_n + p B+_s) / 2 and V1, V2 with
+// -p, each degree adds G = pv U1 + nv U2 and C = i (nv V2 - pv V1) per ring
+// pair; the lanes' float-pair sums go to shared-memory slots and every four
+// degrees the warp reduces them through a transpose (lane t sums one float
+// pair over 16 lanes, one shuffle joins the halves).  One ring pair per
+// lane, four passes per warp over an item's 128 ring pairs; every (order,
+// ring block) is processed; one partial row per (ring block, pass), summed in
+// a fixed order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "nusht_internal.cuh"
 #include "recurrence.cuh"
 
@@ -110,9 +122,37 @@ __device__ __forceinline__ Ring ring_of(int j, int M) {
   return r;
 }
 
+// (G + iC) / 2 and (-1)^s (G - iC) / 2 per packed (l, m) as float pairs
+// (hi re, lo re, hi im, lo im); Im of the m = 0 entries is ignored
+__global__ void spin_scale_k(const double2* __restrict__ glm, const double2* __restrict__ clm, int64_t nalm, int L,
+                             int s, float4* __restrict__ ap, float4* __restrict__ am) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nalm) return;
+  double2 g = glm[i], c = clm[i];
+  if (i <= L) g.y = c.y = 0.0;
+  const double hs = (s & 1) ? -0.5 : 0.5;
+  float4 p, q;
+  df_of(0.5 * (g.x - c.y), p.x, p.y);
+  df_of(0.5 * (g.y + c.x), p.z, p.w);
+  df_of(hs * (g.x + c.y), q.x, q.y);
+  df_of(hs * (g.y - c.x), q.z, q.w);
+  ap[i] = p;
+  am[i] = q;
+}
+
+// acc += (float-pair complex a) * (float-pair real v)
+__device__ __forceinline__ void cmac(float4& acc, const float4 a, float vh, float vl) {
+  df_mac(acc.x, acc.y, a.x, a.y, vh, vl);
+  df_mac(acc.z, acc.w, a.z, a.w, vh, vl);
+}
+
+__device__ __forceinline__ double2 cval(const float4 v) {
+  return make_double2(df_value(v.x, v.y), df_value(v.z, v.w));
+}
+
 // synthesis: the Q and U ring maps, doubled, [m][M] complex each
-__global__ void __launch_bounds__(128) spin_synth_k(SpinArgs a, const double2* __restrict__ glm,
-                                                    const double2* __restrict__ clm, double2* __restrict__ GQ,
+__global__ void __launch_bounds__(128) spin_synth_k(SpinArgs a, const float4* __restrict__ ap,
+                                                    const float4* __restrict__ am, double2* __restrict__ GQ,
                                                     double2* __restrict__ GU) {
   const int lane = threadIdx.x & 31;
   const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -136,37 +176,34 @@ __global__ void __launch_bounds__(128) spin_synth_k(SpinArgs a, const double2* _
     SChain P, N;
     schain_init(P, mp, ep, abp >> 16, abp & 0xffff, rg.ch, rg.sh);
     schain_init(N, mn, en, abn >> 16, abn & 0xffff, rg.ch, rg.sh);
-    // sums by the parity p = (-1)^(l+m+s): Q (W part, X part), U (W part, X part)
-    double2 qw[2] = {{0, 0}, {0, 0}}, qx[2] = {{0, 0}, {0, 0}}, uw[2] = {{0, 0}, {0, 0}}, ux[2] = {{0, 0}, {0, 0}};
-    auto acc = [&](int l, int par) {
-      const double pv = sval(P), nv = sval(N);
-      const double W = 0.5 * (pv + sgs * nv), X = 0.5 * (pv - sgs * nv);
-      const double2 g = __ldg(glm + mb + l), c = __ldg(clm + mb + l);
-      const double gi = m == 0 ? 0.0 : g.y, ci = m == 0 ? 0.0 : c.y;
-      // G W + i C X  and  C W - i G X
-      qw[par].x = fma(g.x, W, qw[par].x);
-      qw[par].y = fma(gi, W, qw[par].y);
-      qx[par].x = fma(-ci, X, qx[par].x);
-      qx[par].y = fma(c.x, X, qx[par].y);
-      uw[par].x = fma(c.x, W, uw[par].x);
-      uw[par].y = fma(ci, W, uw[par].y);
-      ux[par].x = fma(gi, X, ux[par].x);
-      ux[par].y = fma(-g.x, X, ux[par].y);
+    // north: PA = sum pv A+, NA = sum nv A-; south: D1 = sum p nv A+, D2 = sum p pv A-
+    float4 PA = make_float4(0.f, 0.f, 0.f, 0.f), NA = PA, D1 = PA, D2 = PA;
+    auto acc = [&](int l) {
+      if (P.E != 0 && N.E != 0) return;
+      float ph, pl, nh, nl;
+      split_q(sval(P), ph, pl);
+      split_q(sval(N), nh, nl);
+      const float4 A = __ldg(ap + mb + l), B = __ldg(am + mb + l);
+      cmac(PA, A, ph, pl);
+      cmac(NA, B, nh, nl);
+      const bool neg = ((l + m + s) & 1) != 0;
+      cmac(D1, A, neg ? -nh : nh, neg ? -nl : nl);
+      cmac(D2, B, neg ? -ph : ph, neg ? -pl : pl);
     };
-    acc(l0, (l0 + m + s) & 1);
+    acc(l0);
     for (int l = l0 + 1; l <= L; ++l) {
       const double A = __ldg(a.A + mb + l), Ab = __ldg(a.Ab + mb + l), C = __ldg(a.Cc + mb + l);
       schain_step(P, fma(A, rg.x, Ab), C);   // lambda+: d^l_{m,-s}, b_l = -m s / (l (l-1))
       schain_step(N, fma(A, rg.x, -Ab), C);  // lambda-: d^l_{m,s}
-      acc(l, (l + m + s) & 1);
+      acc(l);
     }
     if (!valid) continue;
-    // north: all four sums; south: W parts times p, X parts times -p
+    const double2 pa = cval(PA), na = cval(NA), d1 = cval(D1), d2 = cval(D2);
+    const double2 fqn = make_double2(pa.x + na.x, pa.y + na.y);
+    const double2 fun = make_double2(pa.y - na.y, na.x - pa.x);              // -i (PA - NA)
+    const double2 fqs = make_double2(sgs * (d1.x + d2.x), sgs * (d1.y + d2.y));
+    const double2 fus = make_double2(sgs * (d1.y - d2.y), sgs * (d2.x - d1.x));  // (-1)^s i (D2 - D1)
     const int js = M / 2 - jn;
-    const double2 fqn = make_double2(qw[0].x + qw[1].x + qx[0].x + qx[1].x, qw[0].y + qw[1].y + qx[0].y + qx[1].y);
-    const double2 fun = make_double2(uw[0].x + uw[1].x + ux[0].x + ux[1].x, uw[0].y + uw[1].y + ux[0].y + ux[1].y);
-    const double2 fqs = make_double2(qw[0].x - qw[1].x - qx[0].x + qx[1].x, qw[0].y - qw[1].y - qx[0].y + qx[1].y);
-    const double2 fus = make_double2(uw[0].x - uw[1].x - ux[0].x + ux[1].x, uw[0].y - uw[1].y - ux[0].y + ux[1].y);
     rq[jn] = fqn;
     ru[jn] = fun;
     rq[M - jn] = make_double2(sgd * fqn.x, sgd * fqn.y);
@@ -229,33 +266,40 @@ __global__ void spin_poles_k(int L, int mmax, int s, int M, const double2* __res
   }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  return v;
-}
+// shared-memory slots of the adjoint: per warp, 4 degrees x 32 lanes x 8
+// floats (G and C as float pairs); a lane's 8 floats start at a multiple of
+// 12 floats (two conflict-free 16-byte stores per quarter warp) and the
+// degrees 392 = 8 (mod 32) floats apart, so that the transpose read (lane t:
+// degree t/4, float pair t mod 4 of one lane) hits distinct banks per half warp
+constexpr int SPIN_SL = 12, SPIN_SD = 32 * SPIN_SL + 8;
 
 // adjoint: from the theta spectra HQ, HU (inverse theta FFT done), fold with
-// the spin sign, then per degree G += W S^Q + i X D^U, C += W S^U - i X D^Q
-// over the warp's ring pairs; partial rows [(blk * 4 + pass)][nalm], G then C
+// the spin sign, then per degree G += pv U1 + nv U2, C += i (nv V2 - pv V1)
+// over the warp's ring pairs; partial rows [(blk * 4 + pass)][nalm] as float
+// pairs, G in pg and C in pc
 __global__ void __launch_bounds__(128) spin_adj_k(SpinArgs a, const double2* __restrict__ HQ,
-                                                  const double2* __restrict__ HU, double2* __restrict__ pg,
-                                                  double2* __restrict__ pc, int64_t nalm) {
+                                                  const double2* __restrict__ HU, float4* __restrict__ pg,
+                                                  float4* __restrict__ pc, int64_t nalm) {
+  __shared__ __align__(16) float slots[4][4 * SPIN_SD];
   const int lane = threadIdx.x & 31;
   const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (it >= (a.mmax + 1) * a.bpm) return;
+  float* sl = slots[threadIdx.x >> 5];
   const int m = it / a.bpm, blk = it % a.bpm;
   const int L = a.lmax, s = a.s, M = a.M;
   const int l0 = m > s ? m : s;
   if (l0 > L) return;
   const int mb = mbase_of(L, m);
-  const double sgs = (s & 1) ? -1.0 : 1.0;
+  const double hs = (s & 1) ? -0.5 : 0.5;  // (-1)^s / 2
   const double sgd = ((m + s) & 1) ? -1.0 : 1.0;
   const double mp = __ldg(a.st_mant + 2 * m), mn = __ldg(a.st_mant + 2 * m + 1);
   const int ep = __ldg(a.st_exp + 2 * m), en = __ldg(a.st_exp + 2 * m + 1);
   const int abp = __ldg(a.st_ab + 2 * m), abn = __ldg(a.st_ab + 2 * m + 1);
   const double2* hq = HQ + (size_t)m * M;
   const double2* hu = HU + (size_t)m * M;
+  // transpose-read role of this lane: float pair k = t mod 16 (degree k / 4,
+  // component k mod 4: G re, G im, C re, C im) summed over lanes 16 h .. 16 h + 15
+  const int tk = lane & 15, th = lane >> 4, td = tk >> 2, tc = tk & 3;
   for (int pass = 0; pass < 4; ++pass) {
     const int jn = 1 + blk * LEG_PAIRS_PER_WARP + pass * 32 + lane;
     const bool valid = jn <= a.npairs;
@@ -271,43 +315,73 @@ __global__ void __launch_bounds__(128) spin_adj_k(SpinArgs a, const double2* __r
         us = make_double2(hu[js].x + sgd * hu[M - js].x, hu[js].y + sgd * hu[M - js].y);
       }
     }
-    // parity p = +1 / -1: W multiplies north + p south, X multiplies north - p south
-    const double2 sq[2] = {make_double2(qn.x + qs.x, qn.y + qs.y), make_double2(qn.x - qs.x, qn.y - qs.y)};
-    const double2 dq[2] = {make_double2(qn.x - qs.x, qn.y - qs.y), make_double2(qn.x + qs.x, qn.y + qs.y)};
-    const double2 su[2] = {make_double2(un.x + us.x, un.y + us.y), make_double2(un.x - us.x, un.y - us.y)};
-    const double2 du[2] = {make_double2(un.x - us.x, un.y - us.y), make_double2(un.x + us.x, un.y + us.y)};
+    // B+ = H^Q + i H^U, B- = H^Q - i H^U at each ring; U1 +- = (B+_n +- B-_s) / 2,
+    // U2 +- = (-1)^s (B-_n +- B+_s) / 2 as float pairs
+    const double2 bpn = make_double2(qn.x - un.y, qn.y + un.x), bmn = make_double2(qn.x + un.y, qn.y - un.x);
+    const double2 bps = make_double2(qs.x - us.y, qs.y + us.x), bms = make_double2(qs.x + us.y, qs.y - us.x);
+    float4 u1p, u1m, u2p, u2m;
+    df_split(0.5 * (bpn.x + bms.x), u1p.x, u1p.y);
+    df_split(0.5 * (bpn.y + bms.y), u1p.z, u1p.w);
+    df_split(0.5 * (bpn.x - bms.x), u1m.x, u1m.y);
+    df_split(0.5 * (bpn.y - bms.y), u1m.z, u1m.w);
+    df_split(hs * (bmn.x + bps.x), u2p.x, u2p.y);
+    df_split(hs * (bmn.y + bps.y), u2p.z, u2p.w);
+    df_split(hs * (bmn.x - bps.x), u2m.x, u2m.y);
+    df_split(hs * (bmn.y - bps.y), u2m.z, u2m.w);
     SChain P, N;
     schain_init(P, mp, ep, abp >> 16, abp & 0xffff, rg.ch, rg.sh);
     schain_init(N, mn, en, abn >> 16, abn & 0xffff, rg.ch, rg.sh);
-    double2* og = pg + (size_t)(blk * 4 + pass) * nalm + mb;
-    double2* oc = pc + (size_t)(blk * 4 + pass) * nalm + mb;
+    float4* og = pg + (size_t)(blk * 4 + pass) * nalm + mb;
+    float4* oc = pc + (size_t)(blk * 4 + pass) * nalm + mb;
     for (int l = l0; l <= L; ++l) {
       if (l > l0) {
         const double A = __ldg(a.A + mb + l), Ab = __ldg(a.Ab + mb + l), C = __ldg(a.Cc + mb + l);
         schain_step(P, fma(A, rg.x, Ab), C);
         schain_step(N, fma(A, rg.x, -Ab), C);
       }
-      const int par = (l + m + s) & 1;
-      const double pv = sval(P), nv = sval(N);
-      const double W = 0.5 * (pv + sgs * nv), X = 0.5 * (pv - sgs * nv);
-      // G: W S^Q + i X D^U;  C: W S^U - i X D^Q
-      double gr = W * sq[par].x - X * du[par].y, gi = W * sq[par].y + X * du[par].x;
-      double cr = W * su[par].x + X * dq[par].y, ci = W * su[par].y - X * dq[par].x;
-      gr = warp_sum(gr);
-      gi = warp_sum(gi);
-      cr = warp_sum(cr);
-      ci = warp_sum(ci);
-      if (lane == 0) {
-        og[l] = make_double2(gr, gi);
-        oc[l] = make_double2(cr, ci);
+      float4 g = make_float4(0.f, 0.f, 0.f, 0.f), w = g;
+      if (P.E == 0 || N.E == 0) {
+        float ph, pl, nh, nl;
+        split_q(sval(P), ph, pl);
+        split_q(sval(N), nh, nl);
+        const bool even = ((l + m + s) & 1) == 0;
+        const float4 x1 = even ? u1p : u1m, x2 = even ? u2p : u2m;  // G: p = (-1)^(l+m+s)
+        const float4 y1 = even ? u1m : u1p, y2 = even ? u2m : u2p;  // C: -p
+        cmac(g, x1, ph, pl);
+        cmac(g, x2, nh, nl);
+        cmac(w, y2, nh, nl);
+        cmac(w, y1, -ph, -pl);
+      }
+      // C = i w = (-w.im, w.re)
+      const int slot = (l - l0) & 3;
+      float4* dst = reinterpret_cast<float4*>(sl + slot * SPIN_SD + lane * SPIN_SL);
+      dst[0] = g;
+      dst[1] = make_float4(-w.z, -w.w, w.x, w.y);
+      if (slot == 3 || l == L) {
+        __syncwarp();
+        const float* src = sl + td * SPIN_SD + (16 * th) * SPIN_SL + 2 * tc;
+        float sh = 0.f, slo = 0.f;
+#pragma unroll 4
+        for (int i = 0; i < 16; ++i) {
+          const float2 v = *reinterpret_cast<const float2*>(src + i * SPIN_SL);
+          df_add(sh, slo, v.x, v.y);
+        }
+        const float oh = __shfl_xor_sync(FULL, sh, 16), ol = __shfl_xor_sync(FULL, slo, 16);
+        df_add(sh, slo, oh, ol);
+        const int deg = l - slot + td;
+        if (th == 0 && deg <= l) {
+          float4* row = tc < 2 ? og : oc;
+          reinterpret_cast<float2*>(row + deg)[tc & 1] = make_float2(sh, slo);
+        }
+        __syncwarp();
       }
     }
   }
 }
 
-// c_lm = sum over the partial rows in a fixed order, plus the poles (order s);
-// entries with l < s are 0, Im of the m = 0 entries is 0
-__global__ void spin_adj_reduce_k(const double2* __restrict__ pg, const double2* __restrict__ pc, int nrows,
+// c_lm = sum over the partial rows in a fixed order (float pairs), plus the
+// poles (order s); entries with l < s are 0, Im of the m = 0 entries is 0
+__global__ void spin_adj_reduce_k(const float4* __restrict__ pg, const float4* __restrict__ pc, int nrows,
                                   int64_t nalm, int L, int mmax, int s, int M, const double2* __restrict__ HQ,
                                   const double2* __restrict__ HU, double2* __restrict__ og, double2* __restrict__ oc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -326,13 +400,18 @@ __global__ void spin_adj_reduce_k(const double2* __restrict__ pg, const double2*
   const int l = (int)(i - (int64_t)m * (2 * L + 1 - m) / 2);
   double g0 = 0, g1 = 0, c0 = 0, c1 = 0;
   if (l >= s) {
+    float4 sg = make_float4(0.f, 0.f, 0.f, 0.f), sc = sg;
     for (int r = 0; r < nrows; ++r) {
-      const double2 a = pg[(size_t)r * nalm + i], b = pc[(size_t)r * nalm + i];
-      g0 += a.x;
-      g1 += a.y;
-      c0 += b.x;
-      c1 += b.y;
+      const float4 a = pg[(size_t)r * nalm + i], b = pc[(size_t)r * nalm + i];
+      df_add(sg.x, sg.y, a.x, a.y);
+      df_add(sg.z, sg.w, a.z, a.w);
+      df_add(sc.x, sc.y, b.x, b.y);
+      df_add(sc.z, sc.w, b.z, b.w);
     }
+    g0 = df_value(sg.x, sg.y);
+    g1 = df_value(sg.z, sg.w);
+    c0 = df_value(sc.x, sc.y);
+    c1 = df_value(sc.z, sc.w);
     if (m == s) {
       // poles: F^Q, F^U at theta = 0 (index 0) and theta = pi (index M / 2),
       // each taken once (no fold partner)
@@ -462,8 +541,10 @@ int spin_setup(nusht_plan_t p, cudaStream_t s) {
   NUSHT_TRY(dev_alloc((void**)&t.GU, gbytes, &p->bytes));
   NUSHT_CUDA(cudaMemsetAsync(t.GQ, 0, gbytes, s));
   NUSHT_CUDA(cudaMemsetAsync(t.GU, 0, gbytes, s));
+  NUSHT_TRY(dev_alloc((void**)&t.ap, nalm * sizeof(float4), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&t.am, nalm * sizeof(float4), &p->bytes));
   t.nrows = 4 * p->leg.blocks_per_m;
-  const size_t pbytes = (size_t)t.nrows * nalm * sizeof(double2);
+  const size_t pbytes = (size_t)t.nrows * nalm * sizeof(float4);
   NUSHT_TRY(dev_alloc((void**)&t.pg, pbytes, &p->bytes));
   NUSHT_TRY(dev_alloc((void**)&t.pc, pbytes, &p->bytes));
   NUSHT_CUDA(cudaMemsetAsync(t.pg, 0, pbytes, s));
@@ -475,7 +556,7 @@ int spin_setup(nusht_plan_t p, cudaStream_t s) {
 void spin_free(nusht_plan_t p) {
   SpinTables& t = p->spin;
   for (void* q : {(void*)t.A, (void*)t.Ab, (void*)t.C, (void*)t.st_mant, (void*)t.st_exp, (void*)t.st_ab,
-                  (void*)t.GQ, (void*)t.GU, (void*)t.pg, (void*)t.pc})
+                  (void*)t.GQ, (void*)t.GU, (void*)t.ap, (void*)t.am, (void*)t.pg, (void*)t.pc})
     dev_free(q);
   t = SpinTables();
 }
@@ -483,8 +564,9 @@ void spin_free(nusht_plan_t p) {
 int spin_legendre_synth(nusht_plan_t p, const void* glm, const void* clm, cudaStream_t s) {
   const SpinArgs a = spin_args(p);
   const int nitems = (p->mmax + 1) * p->leg.blocks_per_m;
-  spin_synth_k<<<(nitems + 3) / 4, 128, 0, s>>>(a, (const double2*)glm, (const double2*)clm, p->spin.GQ,
-                                                p->spin.GU);
+  spin_scale_k<<<(int)((p->nalm + 255) / 256), 256, 0, s>>>((const double2*)glm, (const double2*)clm, p->nalm,
+                                                             p->lmax, p->opts.spin, p->spin.ap, p->spin.am);
+  spin_synth_k<<<(nitems + 3) / 4, 128, 0, s>>>(a, p->spin.ap, p->spin.am, p->spin.GQ, p->spin.GU);
   spin_poles_k<<<1, 256, 0, s>>>(p->lmax, p->mmax, p->opts.spin, p->sz.M, (const double2*)glm, (const double2*)clm,
                                  p->spin.GQ, p->spin.GU);
   NUSHT_CUDA(cudaGetLastError());
