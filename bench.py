@@ -627,8 +627,9 @@ def run_spin(torch, nu, args, dist, rank, L, pts):
     torch.cuda.empty_cache()
     return {"ms_per_step": ms, "synth_ms": e[0].elapsed_time(e[1]), "adjoint_ms": e[1].elapsed_time(e[2]),
             "eps_eff": par, "eps_eff_sample": 200, "plan_s": t_plan, "plan_GB": nbytes / 1e9, "spin": 2,
-            "what": "FP64 Wigner-d recurrences (both +-s chains per ring pair) and FP64 sums; theta FFT, "
-                    "fine-grid FFT and NUFFT once per field (Q, U)", "clocks": clk.summary()}
+            "what": "FP64 Wigner-d recurrences (both +-s chains per ring pair), float-pair sums on the FP32 pipe, "
+                    "passes whose values stay below 2^-300 skipped; theta FFT, fine-grid FFT and NUFFT once per "
+                    "field (Q, U)", "clocks": clk.summary()}
 
 
 def run_autograd(torch, nu, args, dist):

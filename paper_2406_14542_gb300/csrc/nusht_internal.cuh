@@ -189,6 +189,7 @@ struct SpinTables {
   float4* am = nullptr;
   float4* pg = nullptr;       // [nrows][nalm] float-pair partial sums of G and C
   float4* pc = nullptr;
+  unsigned char* keep = nullptr;  // per (order, ring block): bit k = pass k has a value above 2^-300
   int nrows = 0;
 };
 

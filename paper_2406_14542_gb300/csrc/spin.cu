@@ -37,7 +37,10 @@
 // pair over 16 lanes, one shuffle joins the halves).  One ring pair per
 // lane, four passes per warp over an item's 128 ring pairs; every (order,
 // ring block) is processed; one partial row per (ring block, pass), summed in
-// a fixed order.
+// a fixed order.  A plan-time probe runs the two chains of every pass once
+// and records the passes (32 ring pairs of an order) where some value rises
+// above 2^-300; the others contribute nothing and are skipped (synthesis
+// writes their rings as zeros).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,6 +66,7 @@ struct SpinArgs {
   const double* st_mant;  // per m and sign (2 m + 0: lambda+, 2 m + 1: lambda-): start mantissa
   const int* st_exp;      // start exponent (binary)
   const int* st_ab;       // per m and sign: powers a (cos) and b (sin) of theta / 2, packed a << 16 | b
+  const unsigned char* keep;  // per item: passes to run (bit k: pass k); null = all
 };
 
 // one Wigner-d chain: value = q1 * 2^-E
@@ -150,6 +154,42 @@ __device__ __forceinline__ double2 cval(const float4 v) {
   return make_double2(df_value(v.x, v.y), df_value(v.z, v.w));
 }
 
+// plan time: which passes of each (order, ring block) ever hold a value above
+// 2^-300 in either chain (the same chain steps as the transforms)
+__global__ void __launch_bounds__(128) spin_probe_k(SpinArgs a, unsigned char* __restrict__ keep) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= (a.mmax + 1) * a.bpm) return;
+  const int m = it / a.bpm, blk = it % a.bpm;
+  const int L = a.lmax, s = a.s, M = a.M;
+  const int l0 = m > s ? m : s;
+  unsigned bits = 0;
+  if (l0 <= L) {
+    const int mb = mbase_of(L, m);
+    const double mp = __ldg(a.st_mant + 2 * m), mn = __ldg(a.st_mant + 2 * m + 1);
+    const int ep = __ldg(a.st_exp + 2 * m), en = __ldg(a.st_exp + 2 * m + 1);
+    const int abp = __ldg(a.st_ab + 2 * m), abn = __ldg(a.st_ab + 2 * m + 1);
+    for (int pass = 0; pass < 4; ++pass) {
+      const int jn = 1 + blk * LEG_PAIRS_PER_WARP + pass * 32 + lane;
+      const bool valid = jn <= a.npairs;
+      const Ring rg = ring_of(valid ? jn : 1, M);
+      SChain P, N;
+      schain_init(P, mp, ep, abp >> 16, abp & 0xffff, rg.ch, rg.sh);
+      schain_init(N, mn, en, abn >> 16, abn & 0xffff, rg.ch, rg.sh);
+      // the pass is kept as soon as one lane's chain is ordinary (warp-uniform exit)
+      bool live = valid && (P.E == 0 || N.E == 0);
+      for (int l = l0 + 1; l <= L && !__any_sync(FULL, live); ++l) {
+        const double A = __ldg(a.A + mb + l), Ab = __ldg(a.Ab + mb + l), C = __ldg(a.Cc + mb + l);
+        schain_step(P, fma(A, rg.x, Ab), C);
+        schain_step(N, fma(A, rg.x, -Ab), C);
+        live = valid && (P.E == 0 || N.E == 0);
+      }
+      if (__any_sync(FULL, live)) bits |= 1u << pass;
+    }
+  }
+  if (lane == 0) keep[it] = (unsigned char)bits;
+}
+
 // synthesis: the Q and U ring maps, doubled, [m][M] complex each
 __global__ void __launch_bounds__(128) spin_synth_k(SpinArgs a, const float4* __restrict__ ap,
                                                     const float4* __restrict__ am, double2* __restrict__ GQ,
@@ -169,9 +209,20 @@ __global__ void __launch_bounds__(128) spin_synth_k(SpinArgs a, const float4* __
   const int abp = __ldg(a.st_ab + 2 * m), abn = __ldg(a.st_ab + 2 * m + 1);
   double2* rq = GQ + (size_t)m * M;
   double2* ru = GU + (size_t)m * M;
+  const unsigned kp = a.keep ? a.keep[it] : 15u;
   for (int pass = 0; pass < 4; ++pass) {
     const int jn = 1 + blk * LEG_PAIRS_PER_WARP + pass * 32 + lane;
     const bool valid = jn <= a.npairs;
+    if (!(kp & (1u << pass))) {
+      // every value of this pass stays below 2^-300: its rings are zero
+      if (valid) {
+        const double2 z = make_double2(0.0, 0.0);
+        const int js = M / 2 - jn;
+        rq[jn] = ru[jn] = rq[M - jn] = ru[M - jn] = z;
+        rq[js] = ru[js] = rq[M - js] = ru[M - js] = z;
+      }
+      continue;
+    }
     const Ring rg = ring_of(valid ? jn : 1, M);
     SChain P, N;
     schain_init(P, mp, ep, abp >> 16, abp & 0xffff, rg.ch, rg.sh);
@@ -300,7 +351,10 @@ __global__ void __launch_bounds__(128) spin_adj_k(SpinArgs a, const double2* __r
   // transpose-read role of this lane: float pair k = t mod 16 (degree k / 4,
   // component k mod 4: G re, G im, C re, C im) summed over lanes 16 h .. 16 h + 15
   const int tk = lane & 15, th = lane >> 4, td = tk >> 2, tc = tk & 3;
+  const unsigned kp = a.keep ? a.keep[it] : 15u;
   for (int pass = 0; pass < 4; ++pass) {
+    // a skipped pass adds nothing: its partial rows keep the zeros of the plan
+    if (!(kp & (1u << pass))) continue;
     const int jn = 1 + blk * LEG_PAIRS_PER_WARP + pass * 32 + lane;
     const bool valid = jn <= a.npairs;
     const Ring rg = ring_of(valid ? jn : 1, M);
@@ -464,6 +518,7 @@ SpinArgs spin_args(nusht_plan_t p) {
   a.st_mant = p->spin.st_mant;
   a.st_exp = p->spin.st_exp;
   a.st_ab = p->spin.st_ab;
+  a.keep = p->spin.keep;
   return a;
 }
 
@@ -549,6 +604,13 @@ int spin_setup(nusht_plan_t p, cudaStream_t s) {
   NUSHT_TRY(dev_alloc((void**)&t.pc, pbytes, &p->bytes));
   NUSHT_CUDA(cudaMemsetAsync(t.pg, 0, pbytes, s));
   NUSHT_CUDA(cudaMemsetAsync(t.pc, 0, pbytes, s));
+  // the passes that carry a value above 2^-300 (the probe runs with keep unset)
+  const int nitems = (mmax + 1) * p->leg.blocks_per_m;
+  unsigned char* keep = nullptr;
+  NUSHT_TRY(dev_alloc((void**)&keep, (size_t)nitems, &p->bytes));
+  spin_probe_k<<<(nitems + 3) / 4, 128, 0, s>>>(spin_args(p), keep);
+  NUSHT_CUDA(cudaGetLastError());
+  t.keep = keep;
   NUSHT_CUDA(cudaStreamSynchronize(s));
   return NUSHT_OK;
 }
@@ -556,7 +618,7 @@ int spin_setup(nusht_plan_t p, cudaStream_t s) {
 void spin_free(nusht_plan_t p) {
   SpinTables& t = p->spin;
   for (void* q : {(void*)t.A, (void*)t.Ab, (void*)t.C, (void*)t.st_mant, (void*)t.st_exp, (void*)t.st_ab,
-                  (void*)t.GQ, (void*)t.GU, (void*)t.ap, (void*)t.am, (void*)t.pg, (void*)t.pc})
+                  (void*)t.GQ, (void*)t.GU, (void*)t.ap, (void*)t.am, (void*)t.pg, (void*)t.pc, (void*)t.keep})
     dev_free(q);
   t = SpinTables();
 }
