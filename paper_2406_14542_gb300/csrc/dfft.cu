@@ -183,6 +183,16 @@ struct CDF {
 };
 
 
+// Shared-memory position of value i of a float-pair line (16 bytes per
+// value, 8 values per 128-byte bank row): i ^ ((i >> 3 ^ i >> 7 ^ i >> 11)
+// mod 8), a permutation inside each aligned group of 8 values.  The strided
+// butterfly accesses and the digit-reversed read of the output then spread
+// over the banks (1.2 wavefronts per quarter warp against the ideal 1, where
+// the plain layout takes 2.0, 8 for the reversed read alone).
+__device__ __forceinline__ int dsw(int i) { return i ^ (((i >> 3) ^ (i >> 7) ^ (i >> 11)) & 7); }
+// float4 slots of a line of n values
+__host__ __device__ __forceinline__ int dline_words(int n) { return (n + 7) & ~7; }
+
 // ---------------------------------------------------------------------------
 // small DFTs of the butterflies (sign SG: +1 inverse, -1 forward)
 // ---------------------------------------------------------------------------
@@ -249,10 +259,10 @@ __device__ __forceinline__ void dif_pass(typename C::V* X, const DfftLen& f, int
   for (int t = threadIdx.x; t < nb; t += blockDim.x) {
     const int b = pow2 ? (t >> sh) : t / S;
     const int j = t - b * S;
-    V* p = X + b * L + j;
+    const int base = b * L + j;
     V v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = p[r * S];
+    for (int r = 0; r < R; ++r) v[r] = X[dsw(base + r * S)];
     float4 wn[R - 1];
     {
       const int tn = t + blockDim.x < nb ? t + blockDim.x : t;
@@ -273,13 +283,13 @@ __device__ __forceinline__ void dif_pass(typename C::V* X, const DfftLen& f, int
 #pragma unroll
     for (int q = 1; q < R; ++q) v[q] = C::template mul_tw<SG>(v[q], w[q - 1]);
 #pragma unroll
-    for (int r = 0; r < R; ++r) p[r * S] = v[r];
+    for (int r = 0; r < R; ++r) X[dsw(base + r * S)] = v[r];
 #pragma unroll
     for (int q = 0; q < R - 1; ++q) w[q] = wn[q];
   }
 }
 
-// all passes; natural-order input in X, output k at X[f.rev[k]]
+// all passes; natural-order input in X (value i at dsw(i)), output k at X[dsw(f.rev[k])]
 template <int SG, int NT, class C = CDF>
 __device__ void dif_line(typename C::V* X, const DfftLen& f) {
   int L = f.N;
@@ -315,11 +325,11 @@ __global__ void __launch_bounds__(NT) dfft_lines_k(const void* in, void* out, in
   for (int line = blockIdx.x; line < nlines; line += gridDim.x) {
     const int64_t o = (int64_t)line * ld;
     for (int k = threadIdx.x; k < f.N; k += blockDim.x)
-      X[k] = INP ? static_cast<const float4*>(in)[o + k] : c_of(static_cast<const double2*>(in)[o + k]);
+      X[dsw(k)] = INP ? static_cast<const float4*>(in)[o + k] : c_of(static_cast<const double2*>(in)[o + k]);
     __syncthreads();
     dif_line<SG, NT>(X, f);
     for (int k = threadIdx.x; k < f.N; k += blockDim.x) {
-      const float4 c = X[__ldg(f.rev + k)];
+      const float4 c = X[dsw(__ldg(f.rev + k))];
       if (OUTP)
         static_cast<float4*>(out)[o + k] = c;
       else
@@ -352,12 +362,12 @@ __global__ void __launch_bounds__(NT) dfft_cols_synth_k(const void* __restrict__
       const float4 gv = INP ? static_cast<const float4*>(Gh)[i] : c_of(static_cast<const double2*>(Gh)[i]);
       v = c_scale(gv, df_mul(d1[k + lmax], dm));
     }
-    X[k1] = v;
+    X[dsw(k1)] = v;
   }
   __syncthreads();
   dif_line<1, NT>(X, f);
   float4* dst = T + (int64_t)m * n1;
-  for (int j = threadIdx.x; j < n1; j += blockDim.x) dst[j] = X[__ldg(f.rev + j)];
+  for (int j = threadIdx.x; j < n1; j += blockDim.x) dst[j] = X[dsw(__ldg(f.rev + j))];
 }
 
 // synthesis, per row pair (j, j + 1): the real rows of the fine grid
@@ -368,26 +378,26 @@ __global__ void __launch_bounds__(NT) dfft_rows_c2r_k(const float4* __restrict__
   const int n2 = f.N;
   const int j = 2 * blockIdx.x;
   const bool two = j + 1 < n1;
-  for (int k = mmax + 1 + threadIdx.x; k < n2 - mmax; k += blockDim.x) X[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = mmax + 1 + threadIdx.x; k < n2 - mmax; k += blockDim.x) X[dsw(k)] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int m = threadIdx.x; m <= mmax; m += blockDim.x) {
     const float4 a = T[(int64_t)m * n1 + j];
     const float4 b = two ? T[(int64_t)m * n1 + j + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
     if (m == 0) {
       // the imaginary parts of the m = 0 entries do not enter a real transform
-      X[0] = make_float4(a.x, a.y, b.x, b.y);
+      X[dsw(0)] = make_float4(a.x, a.y, b.x, b.y);
     } else {
       // C[m] = a + i b, C[n2 - m] = conj(a) + i conj(b)
       const float2 r1 = dd_add(a.x, a.y, -b.z, -b.w), i1 = dd_add(a.z, a.w, b.x, b.y);
       const float2 r2 = dd_add(a.x, a.y, b.z, b.w), i2 = dd_add(b.x, b.y, -a.z, -a.w);
-      X[m] = make_float4(r1.x, r1.y, i1.x, i1.y);
-      X[n2 - m] = make_float4(r2.x, r2.y, i2.x, i2.y);
+      X[dsw(m)] = make_float4(r1.x, r1.y, i1.x, i1.y);
+      X[dsw(n2 - m)] = make_float4(r2.x, r2.y, i2.x, i2.y);
     }
   }
   __syncthreads();
   dif_line<1, NT>(X, f);
   double* r0 = grid + (int64_t)j * stride;
   for (int n = threadIdx.x; n < n2; n += blockDim.x) {
-    const float4 c = X[__ldg(f.rev + n)];
+    const float4 c = X[dsw(__ldg(f.rev + n))];
     r0[n] = pair_to_double(c.x, c.y);
     if (two) r0[stride + n] = pair_to_double(c.z, c.w);
   }
@@ -410,13 +420,13 @@ __global__ void __launch_bounds__(NT) dfft_rows_r2c_k(const double* __restrict__
     } else {
       v.z = v.w = 0.f;
     }
-    X[n] = v;
+    X[dsw(n)] = v;
   }
   __syncthreads();
   dif_line<-1, NT>(X, f);
   for (int m = threadIdx.x; m <= mmax; m += blockDim.x) {
-    const float4 cm = X[__ldg(f.rev + m)];
-    const float4 cn = X[__ldg(f.rev + (m == 0 ? 0 : n2 - m))];
+    const float4 cm = X[dsw(__ldg(f.rev + m))];
+    const float4 cn = X[dsw(__ldg(f.rev + (m == 0 ? 0 : n2 - m)))];
     // X_j = (C[m] + conj C[n2-m]) / 2, X_j+1 = -i (C[m] - conj C[n2-m]) / 2
     const float2 ar = dd_add(cm.x, cm.y, cn.x, cn.y), ai = dd_add(cm.z, cm.w, -cn.z, -cn.w);
     const float2 br = dd_add(cm.z, cm.w, cn.z, cn.w), bi = dd_add(cn.x, cn.y, -cm.x, -cm.y);
@@ -434,7 +444,7 @@ __global__ void __launch_bounds__(NT) dfft_cols_adj_k(const float4* __restrict__
   extern __shared__ float4 X[];
   const int m = blockIdx.x, n1 = f.N;
   const float4* src = T + (int64_t)m * n1;
-  for (int k = threadIdx.x; k < n1; k += blockDim.x) X[k] = src[k];
+  for (int k = threadIdx.x; k < n1; k += blockDim.x) X[dsw(k)] = src[k];
   __syncthreads();
   dif_line<-1, NT>(X, f);
   const float2 dm = d2[m];
@@ -443,7 +453,7 @@ __global__ void __launch_bounds__(NT) dfft_cols_adj_k(const float4* __restrict__
     const int k = kk <= M / 2 ? kk : kk - M;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k >= -lmax && k <= lmax) {
-      const float4 c = X[__ldg(f.rev + (k < 0 ? k + n1 : k))];
+      const float4 c = X[dsw(__ldg(f.rev + (k < 0 ? k + n1 : k)))];
       v = c_scale(c, df_mul(d1[k + lmax], dm));
     }
     if (OUTP)
@@ -1012,7 +1022,7 @@ void dfft_free(nusht_plan_t p) {
 // DFT; the ring map G and the adjoint's final Ghat stay double2.
 int dfft_theta_exec(nusht_plan_t p, const void* src, void* dst, int sign, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
-  const size_t sm = (size_t)z.M * sizeof(float4);
+  const size_t sm = (size_t)dline_words(z.M) * sizeof(float4);
   const int nl = z.mmax + 1;
   const DfftLen& f = p->dft_theta;
   auto go = [&](auto kw, auto ko) {
@@ -1038,7 +1048,7 @@ int dfft_theta_exec(nusht_plan_t p, const void* src, void* dst, int sign, cudaSt
 
 int dfft_cols_synth(nusht_plan_t p, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
-  const size_t sm = (size_t)z.n1 * sizeof(float4);
+  const size_t sm = (size_t)dline_words(z.n1) * sizeof(float4);
   const DfftLen& f = p->dft_n1;
   auto go = [&](auto kw, auto ko) {
     if (wide(f))
@@ -1057,7 +1067,7 @@ int dfft_cols_synth(nusht_plan_t p, cudaStream_t s) {
 int dfft_rows_c2r(nusht_plan_t p, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const int64_t stride = 2 * (z.n2 / 2 + 1);
-  const size_t sm = (size_t)z.n2 * sizeof(float4);
+  const size_t sm = (size_t)dline_words(z.n2) * sizeof(float4);
   const DfftLen& f = p->dft_n2;
   if (wide(f))
     dfft_rows_c2r_k<DFFT_T_WIDE><<<(z.n1 + 1) / 2, DFFT_T_WIDE, sm, s>>>((const float4*)p->tcols, (double*)p->fine,
@@ -1072,7 +1082,7 @@ int dfft_rows_c2r(nusht_plan_t p, cudaStream_t s) {
 int dfft_rows_r2c(nusht_plan_t p, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   const int64_t stride = 2 * (z.n2 / 2 + 1);
-  const size_t sm = (size_t)z.n2 * sizeof(float4);
+  const size_t sm = (size_t)dline_words(z.n2) * sizeof(float4);
   const DfftLen& f = p->dft_n2;
   if (wide(f))
     dfft_rows_r2c_k<DFFT_T_WIDE><<<(z.n1 + 1) / 2, DFFT_T_WIDE, sm, s>>>((const double*)p->fine, (float4*)p->tcols,
@@ -1086,7 +1096,7 @@ int dfft_rows_r2c(nusht_plan_t p, cudaStream_t s) {
 
 int dfft_cols_adjoint(nusht_plan_t p, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
-  const size_t sm = (size_t)z.n1 * sizeof(float4);
+  const size_t sm = (size_t)dline_words(z.n1) * sizeof(float4);
   const DfftLen& f = p->dft_n1;
   auto go = [&](auto kw, auto ko) {
     if (wide(f))
