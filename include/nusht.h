@@ -285,6 +285,10 @@ NUSHT_API int nusht_pointing(nusht_plan_t p, const void* d_philm, double* d_ptg,
  * C) in the packed m-major layout; entries with l < s and Im of the m = 0
  * entries are ignored.  The same chain as nusht_synth (Eq. SHTfast) with a
  * Wigner-d recurrence for S and the spin sign (-1)^s in the doubling.
+ * Precision: the two Wigner-d recurrences (d^l_{m,-s}, d^l_{m,s}) in FP64
+ * with scaled exponents, the sums over l in double-float (as the spin-0
+ * Legendre contraction), the rest as in nusht_synth; measured eps_eff 7e-12
+ * at lmax 4095 against the 1e-10 target.
  *   d_glm, d_clm  device complex128[nalm]
  *   d_q, d_u      device double[npts], caller's point order
  * NUSHT_FP64 plans made with opts.spin >= 1 (NUSHT_EUNSUPPORTED otherwise).
