@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 #include "nusht_internal.cuh"
@@ -83,15 +84,19 @@ __device__ __forceinline__ void tap(double x, int n, int w, int& i0w, double& of
   i0w = i;
 }
 
+// sort key of a point: its bin (row-major over the bins), then its first tap
+// row-major inside the bin, key = bin * binsz^2 + (i1 mod binsz) binsz + i2 mod binsz
 __global__ void prep_k(const double* __restrict__ pts, int64_t npts, int n1, int n2, int w, int nb2, int binsz,
-                       int* __restrict__ binid) {
+                       int64_t* __restrict__ key) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npts) return;
   int i1, i2;
   double o1, o2;
   tap(pts[2 * i], n1, w, i1, o1);
   tap(pts[2 * i + 1], n2, w, i2, o2);
-  binid[i] = (i1 / binsz) * nb2 + (i2 / binsz);
+  const int b1 = i1 / binsz, b2 = i2 / binsz;
+  const int64_t bin = (int64_t)b1 * nb2 + b2;
+  key[i] = bin * binsz * binsz + (int64_t)(i1 - b1 * binsz) * binsz + (i2 - b2 * binsz);
 }
 
 // sorted point s <- caller's point perm[s]: first taps, and kernel values
@@ -1145,6 +1150,54 @@ void free_points(nusht_plan_t p) {
 // caller asked for FP64 instructions (opts.fp64_contraction)
 static bool nufft_df(nusht_plan_t p) { return p->precision == NUSHT_FP64 && !p->opts.fp64_contraction; }
 
+// Stable LSD radix sort of (key, index) pairs by key on the host, 16-bit
+// digits, `passes` of them, each pass split over the host threads: every
+// thread counts the digits of its slice, the offsets are laid out digit by
+// digit and, inside a digit, slice by slice (which keeps the sort stable), and
+// every thread scatters its slice.
+static void radix_sort_pairs(std::vector<int64_t>& keys, std::vector<int>& idx, int passes) {
+  const int64_t n = (int64_t)keys.size();
+  constexpr int D = 1 << 16;
+  int nt = (int)std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
+  if (n < (1 << 20)) nt = 1;
+  std::vector<int64_t> k2(n);
+  std::vector<int> i2(n);
+  std::vector<int64_t> hist((size_t)nt * D);
+  auto parallel = [&](auto&& body) {
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(body, t);
+    body(0);
+    for (auto& x : th) x.join();
+  };
+  for (int ps = 0; ps < passes; ++ps) {
+    const int sh = 16 * ps;
+    parallel([&](int t) {
+      int64_t* h = hist.data() + (size_t)t * D;
+      std::fill(h, h + D, 0);
+      const int64_t a = n * t / nt, b = n * (t + 1) / nt;
+      for (int64_t i = a; i < b; ++i) h[(keys[i] >> sh) & 0xffff]++;
+    });
+    int64_t run = 0;
+    for (int d = 0; d < D; ++d)
+      for (int t = 0; t < nt; ++t) {
+        const int64_t c = hist[(size_t)t * D + d];
+        hist[(size_t)t * D + d] = run;
+        run += c;
+      }
+    parallel([&](int t) {
+      int64_t* h = hist.data() + (size_t)t * D;
+      const int64_t a = n * t / nt, b = n * (t + 1) / nt;
+      for (int64_t i = a; i < b; ++i) {
+        const int64_t o = h[(keys[i] >> sh) & 0xffff]++;
+        k2[o] = keys[i];
+        i2[o] = idx[i];
+      }
+    });
+    keys.swap(k2);
+    idx.swap(i2);
+  }
+}
+
 int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   PointData& d = p->pts;
@@ -1185,28 +1238,38 @@ int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t 
   d.sub = nullptr;
   d.nsub = 0;
   if (npts == 0) return NUSHT_OK;
-  // bin ids on the device, counting sort on the host (stable, so that the
-  // order inside a bin, and with it every summation order, is deterministic)
-  int* dbin = nullptr;
-  NUSHT_TRY(dev_alloc((void**)&dbin, (size_t)npts * 4, nullptr));
+  // sort keys on the device (bin, then the first tap row-major inside the
+  // bin), LSD radix sort on the host: stable, so the order, and with it every
+  // summation order, is deterministic.  Points of a bin in cell order make a
+  // warp's lanes touch neighbouring cells of the tile and of the fine grid
+  // (for scattered inputs such as uniform random points the input order is
+  // random inside a bin).
+  int64_t* dkey = nullptr;
+  NUSHT_TRY(dev_alloc((void**)&dkey, (size_t)npts * 8, nullptr));
   const int tb = 256;
   const int nblk = (int)((npts + tb - 1) / tb);
-  prep_k<<<nblk, tb, 0, s>>>(d_pts, npts, z.n1, z.n2, z.w, nb2, binsz, dbin);
-  std::vector<int> bins(npts);
+  prep_k<<<nblk, tb, 0, s>>>(d_pts, npts, z.n1, z.n2, z.w, nb2, binsz, dkey);
+  std::vector<int64_t> keys(npts);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(bins.data(), dbin, (size_t)npts * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(keys.data(), dkey, (size_t)npts * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  dev_free(dbin);
+  dev_free(dkey);
   if (e != cudaSuccess) return cuda_status(e, "point binning");
   const int nbins = nb1 * nb2;
-  std::vector<int64_t> off(nbins + 1, 0);
-  for (int64_t i = 0; i < npts; ++i) off[bins[i] + 1]++;
-  for (int b = 0; b < nbins; ++b) off[b + 1] += off[b];
+  const int64_t cells_per_bin = (int64_t)binsz * binsz;
   std::vector<int> perm(npts);
   {
-    std::vector<int64_t> cur(off.begin(), off.end() - 1);
-    for (int64_t i = 0; i < npts; ++i) perm[cur[bins[i]]++] = (int)i;
+    // 16-bit digits, as many passes as the largest key needs
+    const int64_t kmax = (int64_t)nbins * cells_per_bin;
+    int passes = 0;
+    while (passes < 4 && (kmax >> (16 * passes)) > 0) ++passes;
+    for (int64_t i = 0; i < npts; ++i) perm[i] = (int)i;
+    radix_sort_pairs(keys, perm, passes);
   }
+  // keys are now sorted: bin offsets
+  std::vector<int64_t> off(nbins + 1, 0);
+  for (int64_t i = 0; i < npts; ++i) off[keys[i] / cells_per_bin + 1]++;
+  for (int b = 0; b < nbins; ++b) off[b + 1] += off[b];
   std::vector<int> sub;
   for (int b = 0; b < nbins; ++b)
     for (int64_t st = off[b]; st < off[b + 1]; st += SUBMAX) {
