@@ -1735,6 +1735,7 @@ int build_fused(nusht_batch_t p) {
     a.n2 = z.n2;
     a.nbins2 = q->pts.nbins2;
     a.bin = q->pts.bin > 0 ? q->pts.bin : 32;
+    a.spread_rows = q->pts.spread_rows;
     a.beta = (float)z.beta;
     a.Gh = static_cast<float2*>(q->Ghat);
     a.d1 = q->deconv1;

@@ -30,6 +30,12 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int SUBMAX = 256;   // points per spreading subproblem
+// FP32 spreading: the subproblem's points staged in shared memory after the
+// tile (float4 per point, one padding slot after every 8, so that lanes that
+// read every Lr-th point hit distinct banks)
+constexpr int SP_SLOTS = SUBMAX + SUBMAX / 8;
+__device__ __forceinline__ int sp_idx(int k) { return k + (k >> 3); }
+inline size_t spread_f_smem(int tw) { return (size_t)((tw * tw + 3) & ~3) * 4 + (size_t)SP_SLOTS * 16; }
 constexpr int WMAX = ES_WMAX;
 constexpr int NRMAX = (WMAX * WMAX + 31) / 32;  // rounds of 32 cells for a w x w footprint
 
@@ -855,38 +861,69 @@ void optin_df(int* st) {
     *st = 1;
 }
 
+// one point into the FP32 spreading tile: w x w native shared-memory float atomics
+template <int W>
+__device__ __forceinline__ void spread_point_f(float* tile, int tw, int lr, int lc, float o1, float o2, float fv,
+                                               float beta) {
+  const float scf = 2.0f / W;
+  float p1[W], p2[W];
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    p1[a] = fv * es_psif((o1 - a) * scf, beta);
+    p2[a] = es_psif((o2 - a) * scf, beta);
+  }
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    float* trow = tile + (lr + a) * tw + lc;
+#pragma unroll
+    for (int b = 0; b < W; ++b) atomicAdd(trow + b, p1[a] * p2[b]);
+  }
+}
+
 // Spreading in float (mixed mode): one thread per point of the subproblem,
 // kernel values evaluated on the fly from the FP32 offsets, w x w native
 // shared-memory float atomics into the bin's tile, one atomic flush.
+// Points are in cell order inside their bin.  rows = 0: consecutive points on
+// consecutive lanes (regular point sets, e.g. ring grids, whose neighbours sit
+// in distinct cells).  rows = 1 (scattered sets where neighbours often share a
+// cell): the subproblem's points are staged in shared memory with coalesced
+// loads, lane l of every warp takes the run l Lr .. l Lr + Lr - 1 and the
+// warps interleave inside it, so a warp's lanes sit about a tile row apart
+// and their atomics rarely share an address.
 template <int W>
 __global__ void __launch_bounds__(128) spread_pt_k(float* __restrict__ grid, int64_t stride, int n1, int n2, int nb2,
                                                    int binsz, float betaf, const int* __restrict__ sub,
                                                    const int* __restrict__ cell, const float* __restrict__ offf,
-                                                   const int* __restrict__ perm, const float* __restrict__ f) {
+                                                   const int* __restrict__ perm, const float* __restrict__ f,
+                                                   int rows) {
   extern __shared__ unsigned char smem_raw[];
   float* tile = reinterpret_cast<float*>(smem_raw);
   const int tw = binsz + W - 1;
   const int bin = sub[3 * blockIdx.x], start = sub[3 * blockIdx.x + 1], cnt = sub[3 * blockIdx.x + 2];
   const int r0 = (bin / nb2) * binsz, c0 = (bin % nb2) * binsz;
   for (int t = threadIdx.x; t < tw * tw; t += blockDim.x) tile[t] = 0.f;
-  __syncthreads();
-  const float scf = 2.0f / W;
-  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-    const int64_t s = (int64_t)start + q;
-    const int lr = cell[2 * s] - r0, lc = cell[2 * s + 1] - c0;
-    const float fv = f[perm[s]];
-    const float o1 = offf[2 * s], o2 = offf[2 * s + 1];
-    float p1[W], p2[W];
-#pragma unroll
-    for (int a = 0; a < W; ++a) {
-      p1[a] = fv * es_psif((o1 - a) * scf, betaf);
-      p2[a] = es_psif((o2 - a) * scf, betaf);
+  if (rows) {
+    float4* sp = reinterpret_cast<float4*>(tile + ((tw * tw + 3) & ~3));
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      const int64_t s = (int64_t)start + k;
+      const int lr = cell[2 * s] - r0, lc = cell[2 * s + 1] - c0;
+      sp[sp_idx(k)] = make_float4(__int_as_float((lr << 16) | lc), offf[2 * s], offf[2 * s + 1], f[perm[s]]);
     }
-#pragma unroll
-    for (int a = 0; a < W; ++a) {
-      float* trow = tile + (lr + a) * tw + lc;
-#pragma unroll
-      for (int b = 0; b < W; ++b) atomicAdd(trow + b, p1[a] * p2[b]);
+    __syncthreads();
+    const int Lr = (cnt + 31) >> 5, nwarp = (int)blockDim.x >> 5;
+    for (int j = (int)threadIdx.x >> 5; j < Lr; j += nwarp) {
+      const int q = ((int)threadIdx.x & 31) * Lr + j;
+      if (q >= cnt) continue;
+      const float4 pv = sp[sp_idx(q)];
+      const int pk = __float_as_int(pv.x);
+      spread_point_f<W>(tile, tw, pk >> 16, pk & 0xffff, pv.y, pv.z, pv.w, betaf);
+    }
+  } else {
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      const int64_t s = (int64_t)start + q;
+      spread_point_f<W>(tile, tw, cell[2 * s] - r0, cell[2 * s + 1] - c0, offf[2 * s], offf[2 * s + 1],
+                        f[perm[s]], betaf);
     }
   }
   __syncthreads();
@@ -945,8 +982,8 @@ __global__ void __launch_bounds__(128) interp_f_k(const float* __restrict__ grid
 template <int W>
 void launch_spread_f(int nsub, size_t sm, cudaStream_t s, float* grid, int64_t stride, int n1, int n2, int nb2,
                      int binsz, float betaf, const int* sub, const int* cell, const float* offf, const int* perm,
-                     const float* f) {
-  spread_pt_k<W><<<nsub, 128, sm, s>>>(grid, stride, n1, n2, nb2, binsz, betaf, sub, cell, offf, perm, f);
+                     const float* f, int rows) {
+  spread_pt_k<W><<<nsub, 128, sm, s>>>(grid, stride, n1, n2, nb2, binsz, betaf, sub, cell, offf, perm, f, rows);
 }
 
 template <int W>
@@ -1012,24 +1049,29 @@ __global__ void __launch_bounds__(128) spread_many_k(const NufftMember* __restri
   const int r0 = (bin / q.nbins2) * binsz, c0 = (bin % q.nbins2) * binsz;
   const float* f = maps[i];
   for (int t = threadIdx.x; t < tw * tw; t += blockDim.x) tile[t] = 0.f;
-  __syncthreads();
-  const float scf = 2.0f / W;
-  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-    const int64_t s = (int64_t)start + k;
-    const int lr = q.cell[2 * s] - r0, lc = q.cell[2 * s + 1] - c0;
-    const float fv = f[q.perm[s]];
-    const float o1 = q.off[2 * s], o2 = q.off[2 * s + 1];
-    float p1[W], p2[W];
-#pragma unroll
-    for (int a = 0; a < W; ++a) {
-      p1[a] = fv * es_psif((o1 - a) * scf, q.beta);
-      p2[a] = es_psif((o2 - a) * scf, q.beta);
+  // the two lane mappings of spread_pt_k, by the member's spread_rows
+  if (q.spread_rows) {
+    float4* sp = reinterpret_cast<float4*>(tile + ((tw * tw + 3) & ~3));
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      const int64_t s = (int64_t)start + k;
+      const int lr = q.cell[2 * s] - r0, lc = q.cell[2 * s + 1] - c0;
+      sp[sp_idx(k)] = make_float4(__int_as_float((lr << 16) | lc), q.off[2 * s], q.off[2 * s + 1], f[q.perm[s]]);
     }
-#pragma unroll
-    for (int a = 0; a < W; ++a) {
-      float* trow = tile + (lr + a) * tw + lc;
-#pragma unroll
-      for (int b = 0; b < W; ++b) atomicAdd(trow + b, p1[a] * p2[b]);
+    __syncthreads();
+    const int Lr = (cnt + 31) >> 5, nwarp = (int)blockDim.x >> 5;
+    for (int j = (int)threadIdx.x >> 5; j < Lr; j += nwarp) {
+      const int k = ((int)threadIdx.x & 31) * Lr + j;
+      if (k >= cnt) continue;
+      const float4 pv = sp[sp_idx(k)];
+      const int pk = __float_as_int(pv.x);
+      spread_point_f<W>(tile, tw, pk >> 16, pk & 0xffff, pv.y, pv.z, pv.w, q.beta);
+    }
+  } else {
+    __syncthreads();
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      const int64_t s = (int64_t)start + k;
+      spread_point_f<W>(tile, tw, q.cell[2 * s] - r0, q.cell[2 * s + 1] - c0, q.off[2 * s], q.off[2 * s + 1],
+                        f[q.perm[s]], q.beta);
     }
   }
   __syncthreads();
@@ -1266,9 +1308,17 @@ int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t 
     for (int64_t i = 0; i < npts; ++i) perm[i] = (int)i;
     radix_sort_pairs(keys, perm, passes);
   }
-  // keys are now sorted: bin offsets
+  // keys are now sorted: bin offsets, and how often a point shares its first
+  // tap with the one before it (ring grids: almost never; uniform random
+  // points at the fine grid's density: a large fraction), which picks the
+  // lane mapping of the FP32 spreading kernels
   std::vector<int64_t> off(nbins + 1, 0);
-  for (int64_t i = 0; i < npts; ++i) off[keys[i] / cells_per_bin + 1]++;
+  int64_t same = 0;
+  for (int64_t i = 0; i < npts; ++i) {
+    off[keys[i] / cells_per_bin + 1]++;
+    same += i > 0 && keys[i] == keys[i - 1];
+  }
+  d.spread_rows = same * 20 > npts ? 1 : 0;  // more than 5 % of the points
   for (int b = 0; b < nbins; ++b) off[b + 1] += off[b];
   std::vector<int> sub;
   for (int b = 0; b < nbins; ++b)
@@ -1437,7 +1487,8 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
   if (p->pts.nsub == 0) return NUSHT_OK;
   const int binsz = p->pts.bin > 0 ? p->pts.bin : 32;
   const int tw = binsz + z.w - 1;
-  const size_t sm = (size_t)tw * tw * es;
+  // FP32 spreading kernels stage the subproblem's points after the tile
+  const size_t sm = p->precision == NUSHT_FP64 ? (size_t)tw * tw * es : spread_f_smem(tw);
   if (nufft_df(p)) {
     const size_t smd = (size_t)tw * spread_df_stride(tw, z.w) * 8 + (size_t)SUBMAX * 16;
     NUSHT_W_DISPATCH(z.w, launch_spread_df, p->pts.nsub, smd, s, (double*)p->fine, stride, z.n1,
@@ -1457,7 +1508,8 @@ int spread(nusht_plan_t p, const void* d_map, cudaStream_t s) {
                                                 p->pts.perm, (const float*)d_map, (float*)p->pts.tiles);
   } else {
     NUSHT_W_DISPATCH(z.w, launch_spread_f, p->pts.nsub, sm, s, (float*)p->fine, stride, z.n1, z.n2, p->pts.nbins2,
-                     binsz, (float)z.beta, p->pts.sub, p->pts.cell, p->pts.off, p->pts.perm, (const float*)d_map);
+                     binsz, (float)z.beta, p->pts.sub, p->pts.cell, p->pts.off, p->pts.perm, (const float*)d_map,
+                     p->pts.spread_rows);
   }
   NUSHT_CUDA(cudaGetLastError());
   if (det) {
@@ -1488,7 +1540,7 @@ int zero_grids_many(const NufftBatch& nb, cudaStream_t s) {
 int spread_many(const NufftBatch& nb, const float* const* maps, cudaStream_t s) {
   if (nb.nsub <= 0) return NUSHT_OK;
   const int tw = nb.bin + nb.w - 1;
-  NUSHT_W_DISPATCH(nb.w, launch_spread_many, nb, (size_t)tw * tw * 4, s, maps);
+  NUSHT_W_DISPATCH(nb.w, launch_spread_many, nb, spread_f_smem(tw), s, maps);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }

@@ -95,6 +95,8 @@ struct PointData {
   int nsub = 0;
   int nbins1 = 0, nbins2 = 0;
   int bin = 32;               // bin edge in fine-grid cells (spreading tile = bin + w - 1)
+  int spread_rows = 0;        // FP32 spreading: 1 = lanes a tile row apart (scattered points, many
+                              // sharing a cell), 0 = consecutive points on consecutive lanes
   size_t bytes = 0;           // device bytes held for points (part of the plan's total)
   // opts.deterministic: every subproblem's tile is written here ([nsub][tile]),
   // then summed per grid cell in a fixed order (no atomics)
@@ -149,6 +151,7 @@ struct NufftMember {
   int64_t stride = 0;
   int64_t npts = 0;
   int n1 = 0, n2 = 0, nbins2 = 0, bin = 0;
+  int spread_rows = 0;         // as PointData::spread_rows
   int blk0 = 0;                // first interpolation block
   int sub0 = 0;                // first spreading block
   int zero0 = 0;               // first block of the grid zero fill
