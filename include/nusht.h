@@ -149,8 +149,10 @@ typedef struct {
                          deconvolution fused into the column pass; lengths whose line and
                          twiddle table fit in 227 KB of shared memory, about 28,500),
                          -1 = cuFFT FP32 (2D plans, separate deconvolution); 0 (default) =
-                         cuFFT for single plans, the FP32 line kernels for batched plans
-                         (where every member's column and row passes are one launch each). */
+                         the FP32 line kernels where the lengths fit, else cuFFT.  The line
+                         kernels transform only the row pairs some point's taps reach, and
+                         in a batch every member's column and row passes are one launch
+                         each. */
   int spin;           /* spin weight s >= 1 of nusht_synth_spin / nusht_adjoint_spin (NUSHT_FP64
                          plans; the plan then holds the Wigner-d recurrence tables and two more
                          ring maps); 0 = none */

@@ -1760,7 +1760,7 @@ int build_fused(nusht_batch_t p) {
       f.col0 = cols;
       f.row0 = rows;
       cols += z.mmax + 1;
-      rows += (z.n1 + 1) / 2;
+      rows += q->pts.nrowpairs;  // the row pairs the member's points reach
       sl.maxn1 = std::max(sl.maxn1, z.n1);
       sl.maxn2 = std::max(sl.maxn2, z.n2);
     }

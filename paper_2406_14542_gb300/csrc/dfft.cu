@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(NT) dfft_lines_k(const void* in, void* out, in
 template <bool INP, int NT>
 __global__ void __launch_bounds__(NT) dfft_cols_synth_k(const void* __restrict__ Gh, float4* __restrict__ T,
                                                             int lmax, int M, const float2* __restrict__ d1,
-                                                            const float2* __restrict__ d2, DfftLen f) {
+                                                            const float2* __restrict__ d2, DfftLen f,
+                                                            const unsigned char* __restrict__ rowmask) {
   extern __shared__ float4 X[];
   const int m = blockIdx.x, n1 = f.N;
   const float2 dm = d2[m];
@@ -366,17 +367,20 @@ __global__ void __launch_bounds__(NT) dfft_cols_synth_k(const void* __restrict__
   }
   __syncthreads();
   dif_line<1, NT>(X, f);
+  // only the rows some point reaches (the others of T stay zero)
   float4* dst = T + (int64_t)m * n1;
-  for (int j = threadIdx.x; j < n1; j += blockDim.x) dst[j] = X[dsw(__ldg(f.rev + j))];
+  for (int j = threadIdx.x; j < n1; j += blockDim.x)
+    if (__ldg(rowmask + j)) dst[j] = X[dsw(__ldg(f.rev + j))];
 }
 
 // synthesis, per row pair (j, j + 1): the real rows of the fine grid
 template <int NT>
 __global__ void __launch_bounds__(NT) dfft_rows_c2r_k(const float4* __restrict__ T, double* __restrict__ grid,
-                                                          int64_t stride, int n1, int mmax, DfftLen f) {
+                                                          int64_t stride, int n1, int mmax, DfftLen f,
+                                                          const int* __restrict__ rowpairs) {
   extern __shared__ float4 X[];
   const int n2 = f.N;
-  const int j = 2 * blockIdx.x;
+  const int j = 2 * __ldg(rowpairs + blockIdx.x);  // a row pair some point reaches
   const bool two = j + 1 < n1;
   for (int k = mmax + 1 + threadIdx.x; k < n2 - mmax; k += blockDim.x) X[dsw(k)] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int m = threadIdx.x; m <= mmax; m += blockDim.x) {
@@ -406,10 +410,11 @@ __global__ void __launch_bounds__(NT) dfft_rows_c2r_k(const float4* __restrict__
 // adjoint, per row pair: spectra m <= mmax of rows j, j + 1 into T[m][j], T[m][j + 1]
 template <int NT>
 __global__ void __launch_bounds__(NT) dfft_rows_r2c_k(const double* __restrict__ grid, float4* __restrict__ T,
-                                                          int64_t stride, int n1, int mmax, DfftLen f) {
+                                                          int64_t stride, int n1, int mmax, DfftLen f,
+                                                          const int* __restrict__ rowpairs) {
   extern __shared__ float4 X[];
   const int n2 = f.N;
-  const int j = 2 * blockIdx.x;
+  const int j = 2 * __ldg(rowpairs + blockIdx.x);  // a row pair some point reaches
   const bool two = j + 1 < n1;
   const double* r0 = grid + (int64_t)j * stride;
   for (int n = threadIdx.x; n < n2; n += blockDim.x) {
@@ -440,11 +445,14 @@ __global__ void __launch_bounds__(NT) dfft_rows_r2c_k(const double* __restrict__
 template <bool OUTP, int NT>
 __global__ void __launch_bounds__(NT) dfft_cols_adj_k(const float4* __restrict__ T, void* __restrict__ Gh,
                                                           int lmax, int M, const float2* __restrict__ d1,
-                                                          const float2* __restrict__ d2, DfftLen f) {
+                                                          const float2* __restrict__ d2, DfftLen f,
+                                                          const unsigned char* __restrict__ rowmask) {
   extern __shared__ float4 X[];
   const int m = blockIdx.x, n1 = f.N;
   const float4* src = T + (int64_t)m * n1;
-  for (int k = threadIdx.x; k < n1; k += blockDim.x) X[dsw(k)] = src[k];
+  // rows no point reaches hold zero spectra: not read
+  for (int k = threadIdx.x; k < n1; k += blockDim.x)
+    X[dsw(k)] = __ldg(rowmask + k) ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   dif_line<-1, NT>(X, f);
   const float2 dm = d2[m];
@@ -696,8 +704,10 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_cols_synth_k(const SfftMember*
   }
   __syncthreads();
   sline<1>(Xs, T, q.f1);
+  // only the rows some point reaches (the others of T stay zero)
   float2* dst = q.T + (int64_t)m * n1;
-  for (int j = threadIdx.x; j < n1; j += SFFT_T) dst[j] = Xs[spad(__ldg(q.f1.rev + j))];
+  for (int j = threadIdx.x; j < n1; j += SFFT_T)
+    if (__ldg(q.rowmask + j)) dst[j] = Xs[spad(__ldg(q.f1.rev + j))];
 }
 
 // synthesis, per (member, row pair j, j + 1): the two Hermitian half spectra
@@ -706,7 +716,7 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_c2r_k(const SfftMember* _
   extern __shared__ float2 Xs[];
   const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, true)];
   const float2* T = stw_load(Xs, maxn, q.f2);
-  const int j = 2 * (blockIdx.x - q.row0);
+  const int j = 2 * __ldg(q.rowpairs + (blockIdx.x - q.row0));  // a row pair some point reaches
   const int n1 = q.n1, n2 = q.n2, mmax = q.mmax;
   const bool two = j + 1 < n1;
   for (int k = mmax + 1 + threadIdx.x; k < n2 - mmax; k += SFFT_T) Xs[spad(k)] = make_float2(0.f, 0.f);
@@ -758,7 +768,7 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_r2c_k(const SfftMember* _
   extern __shared__ float2 Xs[];
   const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, true)];
   const float2* T = stw_load(Xs, maxn, q.f2);
-  const int j = 2 * (blockIdx.x - q.row0);
+  const int j = 2 * __ldg(q.rowpairs + (blockIdx.x - q.row0));  // a row pair some point reaches
   const int n1 = q.n1, n2 = q.n2, mmax = q.mmax;
   const bool two = j + 1 < n1;
   const float* r0 = q.grid + (int64_t)j * q.stride;
@@ -790,7 +800,8 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_cols_adj_k(const SfftMember* _
   const int m = blockIdx.x - q.col0;
   const int n1 = q.n1, lmax = q.lmax, M = q.M;
   const float2* src = q.T + (int64_t)m * n1;
-  for (int k = threadIdx.x; k < n1; k += SFFT_T) Xs[spad(k)] = src[k];
+  // rows no point reaches hold zero spectra: not read
+  for (int k = threadIdx.x; k < n1; k += SFFT_T) Xs[spad(k)] = __ldg(q.rowmask + k) ? src[k] : make_float2(0.f, 0.f);
   __syncthreads();
   sline<-1>(Xs, T, q.f1);
   const float dm = q.d2[m];
@@ -1052,9 +1063,11 @@ int dfft_cols_synth(nusht_plan_t p, cudaStream_t s) {
   const DfftLen& f = p->dft_n1;
   auto go = [&](auto kw, auto ko) {
     if (wide(f))
-      kw<<<z.mmax + 1, DFFT_T_WIDE, sm, s>>>(p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f, p->deconv2f, f);
+      kw<<<z.mmax + 1, DFFT_T_WIDE, sm, s>>>(p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f, p->deconv2f, f,
+                                             p->pts.rowmask);
     else
-      ko<<<z.mmax + 1, DFFT_T_ODD, sm, s>>>(p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f, p->deconv2f, f);
+      ko<<<z.mmax + 1, DFFT_T_ODD, sm, s>>>(p->Ghat, (float4*)p->tcols, z.lmax, z.M, p->deconv1f, p->deconv2f, f,
+                                            p->pts.rowmask);
   };
   if (p->dfft_theta)
     go(dfft_cols_synth_k<true, DFFT_T_WIDE>, dfft_cols_synth_k<true, DFFT_T_ODD>);
@@ -1069,12 +1082,14 @@ int dfft_rows_c2r(nusht_plan_t p, cudaStream_t s) {
   const int64_t stride = 2 * (z.n2 / 2 + 1);
   const size_t sm = (size_t)dline_words(z.n2) * sizeof(float4);
   const DfftLen& f = p->dft_n2;
+  const int np = p->pts.nrowpairs;  // only the row pairs some point reaches
+  if (np == 0) return NUSHT_OK;
   if (wide(f))
-    dfft_rows_c2r_k<DFFT_T_WIDE><<<(z.n1 + 1) / 2, DFFT_T_WIDE, sm, s>>>((const float4*)p->tcols, (double*)p->fine,
-                                                                        stride, z.n1, z.mmax, f);
+    dfft_rows_c2r_k<DFFT_T_WIDE><<<np, DFFT_T_WIDE, sm, s>>>((const float4*)p->tcols, (double*)p->fine, stride, z.n1,
+                                                            z.mmax, f, p->pts.rowpairs);
   else
-    dfft_rows_c2r_k<DFFT_T_ODD><<<(z.n1 + 1) / 2, DFFT_T_ODD, sm, s>>>((const float4*)p->tcols, (double*)p->fine,
-                                                                      stride, z.n1, z.mmax, f);
+    dfft_rows_c2r_k<DFFT_T_ODD><<<np, DFFT_T_ODD, sm, s>>>((const float4*)p->tcols, (double*)p->fine, stride, z.n1,
+                                                          z.mmax, f, p->pts.rowpairs);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
@@ -1084,12 +1099,14 @@ int dfft_rows_r2c(nusht_plan_t p, cudaStream_t s) {
   const int64_t stride = 2 * (z.n2 / 2 + 1);
   const size_t sm = (size_t)dline_words(z.n2) * sizeof(float4);
   const DfftLen& f = p->dft_n2;
+  const int np = p->pts.nrowpairs;  // rows no point reaches stay zero: their spectra in T are zero
+  if (np == 0) return NUSHT_OK;
   if (wide(f))
-    dfft_rows_r2c_k<DFFT_T_WIDE><<<(z.n1 + 1) / 2, DFFT_T_WIDE, sm, s>>>((const double*)p->fine, (float4*)p->tcols,
-                                                                        stride, z.n1, z.mmax, f);
+    dfft_rows_r2c_k<DFFT_T_WIDE><<<np, DFFT_T_WIDE, sm, s>>>((const double*)p->fine, (float4*)p->tcols, stride,
+                                                            z.n1, z.mmax, f, p->pts.rowpairs);
   else
-    dfft_rows_r2c_k<DFFT_T_ODD><<<(z.n1 + 1) / 2, DFFT_T_ODD, sm, s>>>((const double*)p->fine, (float4*)p->tcols,
-                                                                      stride, z.n1, z.mmax, f);
+    dfft_rows_r2c_k<DFFT_T_ODD><<<np, DFFT_T_ODD, sm, s>>>((const double*)p->fine, (float4*)p->tcols, stride, z.n1,
+                                                          z.mmax, f, p->pts.rowpairs);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }
@@ -1101,10 +1118,10 @@ int dfft_cols_adjoint(nusht_plan_t p, cudaStream_t s) {
   auto go = [&](auto kw, auto ko) {
     if (wide(f))
       kw<<<z.mmax + 1, DFFT_T_WIDE, sm, s>>>((const float4*)p->tcols, p->Ghat, z.lmax, z.M, p->deconv1f,
-                                             p->deconv2f, f);
+                                             p->deconv2f, f, p->pts.rowmask);
     else
       ko<<<z.mmax + 1, DFFT_T_ODD, sm, s>>>((const float4*)p->tcols, p->Ghat, z.lmax, z.M, p->deconv1f,
-                                            p->deconv2f, f);
+                                            p->deconv2f, f, p->pts.rowmask);
   };
   if (p->dfft_theta)
     go(dfft_cols_adj_k<true, DFFT_T_WIDE>, dfft_cols_adj_k<true, DFFT_T_ODD>);
@@ -1159,6 +1176,8 @@ void sfft_member(nusht_plan_t p, SfftMember& m) {
   m.col0 = m.row0 = 0;
   m.f1 = p->dft_n1;
   m.f2 = p->dft_n2;
+  m.rowpairs = p->pts.rowpairs;
+  m.rowmask = p->pts.rowmask;
 }
 
 SfftLaunch sfft_launch_of(nusht_plan_t p) {
@@ -1166,7 +1185,7 @@ SfftLaunch sfft_launch_of(nusht_plan_t p) {
   l.mem = p->sfft_mem;
   l.nm = 1;
   l.ncols = p->sz.mmax + 1;
-  l.nrows = (p->sz.n1 + 1) / 2;
+  l.nrows = p->pts.nrowpairs;
   l.maxn1 = p->sz.n1;
   l.maxn2 = p->sz.n2;
   return l;

@@ -1185,6 +1185,8 @@ void free_points(nusht_plan_t p) {
   dev_free(d.sub);
   dev_free(d.tiles);
   dev_free(d.binsub);
+  dev_free(d.rowmask);
+  dev_free(d.rowpairs);
   d = PointData();
 }
 
@@ -1240,6 +1242,60 @@ static void radix_sort_pairs(std::vector<int64_t>& keys, std::vector<int>& idx, 
   }
 }
 
+// The fine-grid rows that some point's taps reach (first tap row i1 and the
+// w - 1 rows after it, cyclically): the row FFT passes of this library's FFT
+// kernels transform only their row pairs, and the column pass stores T only
+// at those rows.  T's other entries are zeroed here and never written, so the
+// adjoint's column pass reads zeros there (the spectra of rows that
+// spreading leaves zero).  A superset is safe (an extra row is transformed
+// for nothing), so per bin the first tap rows from its first to its last
+// point (in cell order) are taken.  keys: the sorted point keys, off: the
+// bins' point offsets (null: no points).
+static int set_touched_rows(nusht_plan_t p, const std::vector<int64_t>* keys, const std::vector<int64_t>* off,
+                            int nb2, int binsz, cudaStream_t s) {
+  const nusht_sizes& z = p->sz;
+  PointData& d = p->pts;
+  const int n1 = z.n1;
+  std::vector<unsigned char> first(n1, 0), mask(n1, 0);
+  if (keys) {
+    const int64_t cpb = (int64_t)binsz * binsz;
+    const int nbins = (int)off->size() - 1;
+    for (int b = 0; b < nbins; ++b) {
+      const int64_t a0 = (*off)[b], a1 = (*off)[b + 1];
+      if (a0 == a1) continue;
+      const int base = (b / nb2) * binsz;
+      const int rlo = (int)(((*keys)[a0] % cpb) / binsz), rhi = (int)(((*keys)[a1 - 1] % cpb) / binsz);
+      for (int r = rlo; r <= rhi; ++r) first[base + r] = 1;
+    }
+  }
+  for (int r = 0; r < n1; ++r)
+    if (first[r])
+      for (int a = 0; a < z.w; ++a) mask[(r + a) % n1] = 1;
+  std::vector<int> pairs;
+  for (int j = 0; j < n1; j += 2)
+    if (mask[j] || (j + 1 < n1 && mask[j + 1])) pairs.push_back(j / 2);
+  if (!d.rowmask) {
+    NUSHT_TRY(dev_alloc((void**)&d.rowmask, (size_t)n1, &p->bytes));
+    NUSHT_TRY(dev_alloc((void**)&d.rowpairs, (size_t)(n1 + 1) / 2 * sizeof(int), &p->bytes));
+  }
+  NUSHT_CUDA(cudaMemcpyAsync(d.rowmask, mask.data(), (size_t)n1, cudaMemcpyHostToDevice, s));
+  if (!pairs.empty())
+    NUSHT_CUDA(cudaMemcpyAsync(d.rowpairs, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  d.nrowpairs = (int)pairs.size();
+  if (p->tcols) {
+    const size_t es = p->dfft_fine ? sizeof(float4) : sizeof(float2);
+    NUSHT_CUDA(cudaMemsetAsync(p->tcols, 0, (size_t)(z.mmax + 1) * n1 * es, s));
+  }
+  if (p->sfft_mem) {
+    // the plan's FP32 FFT member entry carries the row list and mask
+    SfftMember m;
+    sfft_member(p, m);
+    NUSHT_CUDA(cudaMemcpyAsync(p->sfft_mem, &m, sizeof(SfftMember), cudaMemcpyHostToDevice, s));
+  }
+  NUSHT_CUDA(cudaStreamSynchronize(s));
+  return NUSHT_OK;
+}
+
 int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t s) {
   const nusht_sizes& z = p->sz;
   PointData& d = p->pts;
@@ -1279,7 +1335,7 @@ int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t 
   dev_free(d.sub);
   d.sub = nullptr;
   d.nsub = 0;
-  if (npts == 0) return NUSHT_OK;
+  if (npts == 0) return set_touched_rows(p, nullptr, nullptr, nb2, binsz, s);
   // sort keys on the device (bin, then the first tap row-major inside the
   // bin), LSD radix sort on the host: stable, so the order, and with it every
   // summation order, is deterministic.  Points of a bin in cell order make a
@@ -1320,6 +1376,7 @@ int setpts_impl(nusht_plan_t p, int64_t npts, const double* d_pts, cudaStream_t 
   }
   d.spread_rows = same * 20 > npts ? 1 : 0;  // more than 5 % of the points
   for (int b = 0; b < nbins; ++b) off[b + 1] += off[b];
+  NUSHT_TRY(set_touched_rows(p, &keys, &off, nb2, binsz, s));
   std::vector<int> sub;
   for (int b = 0; b < nbins; ++b)
     for (int64_t st = off[b]; st < off[b + 1]; st += SUBMAX) {

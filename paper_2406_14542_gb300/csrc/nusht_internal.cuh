@@ -97,6 +97,12 @@ struct PointData {
   int bin = 32;               // bin edge in fine-grid cells (spreading tile = bin + w - 1)
   int spread_rows = 0;        // FP32 spreading: 1 = lanes a tile row apart (scattered points, many
                               // sharing a cell), 0 = consecutive points on consecutive lanes
+  // fine-grid rows some point's taps reach (the others are neither read by
+  // interpolation nor written by spreading): a flag per row and the list of
+  // row pairs (j / 2 for the pair j, j + 1) the row FFT passes transform
+  unsigned char* rowmask = nullptr;
+  int* rowpairs = nullptr;
+  int nrowpairs = 0;
   size_t bytes = 0;           // device bytes held for points (part of the plan's total)
   // opts.deterministic: every subproblem's tile is written here ([nsub][tile]),
   // then summed per grid cell in a fixed order (no atomics)
@@ -135,6 +141,8 @@ struct SfftMember {
   int lmax = 0, mmax = 0, M = 0, n1 = 0, n2 = 0;
   int col0 = 0, row0 = 0;      // first CTA of this member in the column / row launches
   DfftLen f1, f2;              // line tables of n1 and n2
+  const int* rowpairs = nullptr;           // row pairs (j / 2) some point reaches: the row launches
+  const unsigned char* rowmask = nullptr;  // per row: stored by the column pass
 };
 
 // One transform of the mixed-precision NUFFT kernels that serve every member

@@ -251,7 +251,7 @@ static int make_ffts(nusht_plan_t p, const double* d1, const double* d2) {
                                   z.mmax + 1, &ws));
   }
   if (!p->has_nufft || own_fine) return NUSHT_OK;
-  if (!dbl && p->opts.fft_kernels == 1 && sfft_fits(z)) {
+  if (!dbl && p->opts.fft_kernels >= 0 && sfft_fits(z)) {
     // FP32, opt-in: this library's line kernels, deconvolution fused into the
     // column pass (cuFFT's 2D plans measured 3-4x faster: the default)
     NUSHT_TRY(sfft_setup(p, d1, d2));

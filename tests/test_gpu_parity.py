@@ -478,8 +478,9 @@ def test_fp64_fft_kernels_theta_only(env):
 @pytest.mark.parametrize("L,npts,sigma", [(5, 3000, 0.0), (100, 20000, 0.0), (200, 40000, 1.5), (1023, 200000, 0.0)])
 def test_fp32_fft_kernels(env, L, npts, sigma):
     """Mixed plans: this library's FP32 fine-grid FFT kernels (fft_kernels =
-    1, with the deconvolution fused into the column pass) against cuFFT's 2D
-    FP32 transforms and the separate deconvolution kernels (the default), on
+    1, the default where the lengths fit; deconvolution fused into the column
+    pass; only the row pairs the points reach) against cuFFT's 2D FP32
+    transforms and the separate deconvolution kernels (fft_kernels = -1), on
     lengths with every radix (n = 24 = 8 * 3, 420 = 4 * 3 * 5 * 7,
     630 = 2 * 9 * 5 * 7 at sigma 1.5, 4096), the oracle on a seeded subset,
     and the dot test (relative to |y| |f|, float rounding)."""
@@ -488,7 +489,7 @@ def test_fp32_fft_kernels(env, L, npts, sigma):
     a = W.alm_gaussian(L, seed=72 + L)
     dp = dev(torch, pts)
     own = nu.Plan(L, dp, eps=1e-5, precision="mixed", sigma=sigma, fft_kernels=1)
-    cuf = nu.Plan(L, dp, eps=1e-5, precision="mixed", sigma=sigma)
+    cuf = nu.Plan(L, dp, eps=1e-5, precision="mixed", sigma=sigma, fft_kernels=-1)
     assert own.info()["n1"] == cuf.info()["n1"]
     ad = dev(torch, a, torch.complex64)
     f = own.synth(ad).double().cpu().numpy()
