@@ -487,10 +487,13 @@ __global__ void __launch_bounds__(NT) dfft_cols_adj_k(const float4* __restrict__
 // i ^ ((i >> 4 ^ i >> 8 ^ i >> 12) mod 16): a permutation inside each
 // aligned group of 16 that keeps contiguous and power-of-two-strided
 // accesses conflict-free and spreads the digit-reversed read of the output
-// over the banks (2 to 2.7 wavefronts per half-warp instead of 8).  512
-// threads per CTA, up to two CTAs per SM.
+// over the banks (2 to 2.7 wavefronts per half-warp instead of 8).  256
+// threads per CTA (four per SM) up to 8192 values, 1024 beyond.
 // ---------------------------------------------------------------------------
-constexpr int SFFT_T = 512;
+// threads per CTA: 256 (four CTAs per SM, each barrier waits on 8 warps)
+// for lines up to 8192; 1024 for longer lines, whose shared memory leaves
+// room for one CTA per SM
+constexpr int SFFT_T_SHORT = 256, SFFT_T_LONG = 1024, SFFT_SHORT_MAX = 8192;
 
 __host__ __device__ __forceinline__ int spad(int i) { return i ^ (((i >> 4) ^ (i >> 8) ^ (i >> 12)) & 15); }
 
@@ -591,7 +594,7 @@ __device__ __forceinline__ void spass(float2* X, const float2* __restrict__ T, i
 #pragma unroll
     for (int k = 1; k <= R / 2; ++k) cs[k - 1] = stw<1>(T, k * (N / R));
   }
-  for (int t = threadIdx.x; t < nb; t += SFFT_T) {
+  for (int t = threadIdx.x; t < nb; t += (int)blockDim.x) {
     const int b = pow2 ? t >> sh : t / S;
     const int j = t - b * S;
     const int base = b * L + j;
@@ -666,7 +669,7 @@ __host__ __device__ __forceinline__ int stw_words(int n) { return 64 + n / 64 + 
 __device__ __forceinline__ float2* stw_load(float2* Xs, int maxn, const DfftLen& f) {
   float2* T = Xs + sline_words(maxn);
   const int nt = stw_words(f.N);
-  for (int k = threadIdx.x; k < nt; k += SFFT_T) T[k] = __ldg(f.tw2 + k);
+  for (int k = threadIdx.x; k < nt; k += (int)blockDim.x) T[k] = __ldg(f.tw2 + k);
   return T;
 }
 
@@ -684,7 +687,8 @@ __device__ __forceinline__ int member_of(const SfftMember* __restrict__ mem, int
 
 // synthesis, per (member, order m): deconvolve and zero-pad the theta
 // spectrum to n1, inverse DFT along theta, store T[m][.]
-__global__ void __launch_bounds__(SFFT_T, 2) sfft_cols_synth_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) sfft_cols_synth_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
   extern __shared__ float2 Xs[];
   const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, false)];
   const float2* T = stw_load(Xs, maxn, q.f1);
@@ -692,7 +696,7 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_cols_synth_k(const SfftMember*
   const int n1 = q.n1, lmax = q.lmax, M = q.M;
   const float dm = q.d2[m];
   const float2* g = q.Gh + (int64_t)m * M;
-  for (int k1 = threadIdx.x; k1 < n1; k1 += SFFT_T) {
+  for (int k1 = threadIdx.x; k1 < n1; k1 += (int)blockDim.x) {
     float2 v = make_float2(0.f, 0.f);
     const int k = k1 > lmax ? k1 - n1 : k1;
     if (k >= -lmax) {
@@ -706,28 +710,29 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_cols_synth_k(const SfftMember*
   sline<1>(Xs, T, q.f1);
   // only the rows some point reaches (the others of T stay zero)
   float2* dst = q.T + (int64_t)m * n1;
-  for (int j = threadIdx.x; j < n1; j += SFFT_T)
+  for (int j = threadIdx.x; j < n1; j += (int)blockDim.x)
     if (__ldg(q.rowmask + j)) dst[j] = Xs[spad(__ldg(q.f1.rev + j))];
 }
 
 // synthesis, per (member, row pair j, j + 1): the two Hermitian half spectra
 // packed as C = X_j + i X_j+1, one inverse DFT, x_j = Re, x_j+1 = Im
-__global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_c2r_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) sfft_rows_c2r_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
   extern __shared__ float2 Xs[];
   const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, true)];
   const float2* T = stw_load(Xs, maxn, q.f2);
   const int j = 2 * __ldg(q.rowpairs + (blockIdx.x - q.row0));  // a row pair some point reaches
   const int n1 = q.n1, n2 = q.n2, mmax = q.mmax;
   const bool two = j + 1 < n1;
-  for (int k = mmax + 1 + threadIdx.x; k < n2 - mmax; k += SFFT_T) Xs[spad(k)] = make_float2(0.f, 0.f);
+  for (int k = mmax + 1 + threadIdx.x; k < n2 - mmax; k += (int)blockDim.x) Xs[spad(k)] = make_float2(0.f, 0.f);
   // the column pair of T: strided loads, four per thread in flight; with n1
   // even (the fine-grid sizes are) T[m][j], T[m][j+1] are one aligned 16-byte load
   const bool vec = (n1 & 1) == 0;
-  for (int m0 = threadIdx.x; m0 <= mmax; m0 += 4 * SFFT_T) {
+  for (int m0 = threadIdx.x; m0 <= mmax; m0 += 4 * (int)blockDim.x) {
     float2 a[4], b[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int m = m0 + u * SFFT_T;
+      const int m = m0 + u * (int)blockDim.x;
       a[u] = b[u] = make_float2(0.f, 0.f);
       if (m <= mmax) {
         const float2* t = q.T + (int64_t)m * n1 + j;
@@ -743,7 +748,7 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_c2r_k(const SfftMember* _
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int m = m0 + u * SFFT_T;
+      const int m = m0 + u * (int)blockDim.x;
       if (m > mmax) break;
       if (m == 0) {
         Xs[spad(0)] = make_float2(a[u].x, b[u].x);  // a real transform takes only Re of m = 0
@@ -756,7 +761,7 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_c2r_k(const SfftMember* _
   __syncthreads();
   sline<1>(Xs, T, q.f2);
   float* r0 = q.grid + (int64_t)j * q.stride;
-  for (int n = threadIdx.x; n < n2; n += SFFT_T) {
+  for (int n = threadIdx.x; n < n2; n += (int)blockDim.x) {
     const float2 c = Xs[spad(__ldg(q.f2.rev + n))];
     r0[n] = c.x;
     if (two) r0[q.stride + n] = c.y;
@@ -764,7 +769,8 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_c2r_k(const SfftMember* _
 }
 
 // adjoint, per (member, row pair): spectra m <= mmax of rows j, j + 1 into T
-__global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_r2c_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) sfft_rows_r2c_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
   extern __shared__ float2 Xs[];
   const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, true)];
   const float2* T = stw_load(Xs, maxn, q.f2);
@@ -772,10 +778,10 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_r2c_k(const SfftMember* _
   const int n1 = q.n1, n2 = q.n2, mmax = q.mmax;
   const bool two = j + 1 < n1;
   const float* r0 = q.grid + (int64_t)j * q.stride;
-  for (int n = threadIdx.x; n < n2; n += SFFT_T) Xs[spad(n)] = make_float2(r0[n], two ? r0[q.stride + n] : 0.f);
+  for (int n = threadIdx.x; n < n2; n += (int)blockDim.x) Xs[spad(n)] = make_float2(r0[n], two ? r0[q.stride + n] : 0.f);
   __syncthreads();
   sline<-1>(Xs, T, q.f2);
-  for (int m = threadIdx.x; m <= mmax; m += SFFT_T) {
+  for (int m = threadIdx.x; m <= mmax; m += (int)blockDim.x) {
     const float2 cm = Xs[spad(__ldg(q.f2.rev + m))];
     const float2 cn = Xs[spad(__ldg(q.f2.rev + (m == 0 ? 0 : n2 - m)))];
     // X_j = (C[m] + conj C[n2-m]) / 2, X_j+1 = -i (C[m] - conj C[n2-m]) / 2
@@ -793,7 +799,8 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_rows_r2c_k(const SfftMember* _
 
 // adjoint, per (member, order m): forward DFT of T[m][.] along theta, then
 // Gh[m][kk] = H[k mod n1] d1[k] d2[m] for |k| <= lmax (k = kk or kk - M), else 0
-__global__ void __launch_bounds__(SFFT_T, 2) sfft_cols_adj_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) sfft_cols_adj_k(const SfftMember* __restrict__ mem, int nm, int maxn) {
   extern __shared__ float2 Xs[];
   const SfftMember& q = mem[member_of(mem, nm, blockIdx.x, false)];
   const float2* T = stw_load(Xs, maxn, q.f1);
@@ -801,12 +808,12 @@ __global__ void __launch_bounds__(SFFT_T, 2) sfft_cols_adj_k(const SfftMember* _
   const int n1 = q.n1, lmax = q.lmax, M = q.M;
   const float2* src = q.T + (int64_t)m * n1;
   // rows no point reaches hold zero spectra: not read
-  for (int k = threadIdx.x; k < n1; k += SFFT_T) Xs[spad(k)] = __ldg(q.rowmask + k) ? src[k] : make_float2(0.f, 0.f);
+  for (int k = threadIdx.x; k < n1; k += (int)blockDim.x) Xs[spad(k)] = __ldg(q.rowmask + k) ? src[k] : make_float2(0.f, 0.f);
   __syncthreads();
   sline<-1>(Xs, T, q.f1);
   const float dm = q.d2[m];
   float2* g = const_cast<float2*>(q.Gh) + (int64_t)m * M;
-  for (int kk = threadIdx.x; kk < M; kk += SFFT_T) {
+  for (int kk = threadIdx.x; kk < M; kk += (int)blockDim.x) {
     const int k = kk <= M / 2 ? kk : kk - M;
     float2 v = make_float2(0.f, 0.f);
     if (k >= -lmax && k <= lmax) {
@@ -954,10 +961,14 @@ int smem_optin() {
   NUSHT_TRY(optin_all<DFFT_T_ODD>(b));
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   const int bs = SFFT_SMEM_MAX;
-  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_synth_k, a, bs));
-  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_c2r_k, a, bs));
-  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_r2c_k, a, bs));
-  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_adj_k, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_synth_k<SFFT_T_SHORT>, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_c2r_k<SFFT_T_SHORT>, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_r2c_k<SFFT_T_SHORT>, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_adj_k<SFFT_T_SHORT>, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_synth_k<SFFT_T_LONG>, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_c2r_k<SFFT_T_LONG>, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_rows_r2c_k<SFFT_T_LONG>, a, bs));
+  NUSHT_CUDA(cudaFuncSetAttribute(sfft_cols_adj_k<SFFT_T_LONG>, a, bs));
   done = 1;
   return NUSHT_OK;
 }
@@ -1196,7 +1207,10 @@ int sfft_smem(int n) { return (sline_words(n) + stw_words(n)) * (int)sizeof(floa
 #define NUSHT_SFFT_LAUNCH(KERNEL, NCTA, NMAXLEN)                                                       \
   do {                                                                                                 \
     if ((NCTA) <= 0) return NUSHT_OK;                                                                  \
-    KERNEL<<<(NCTA), SFFT_T, (size_t)sfft_smem(NMAXLEN), s>>>(l.mem, l.nm, (NMAXLEN));                 \
+    if ((NMAXLEN) <= SFFT_SHORT_MAX)                                                                   \
+      KERNEL<SFFT_T_SHORT><<<(NCTA), SFFT_T_SHORT, (size_t)sfft_smem(NMAXLEN), s>>>(l.mem, l.nm, (NMAXLEN)); \
+    else                                                                                               \
+      KERNEL<SFFT_T_LONG><<<(NCTA), SFFT_T_LONG, (size_t)sfft_smem(NMAXLEN), s>>>(l.mem, l.nm, (NMAXLEN));   \
     NUSHT_CUDA(cudaGetLastError());                                                                    \
     return NUSHT_OK;                                                                                   \
   } while (0)
