@@ -160,6 +160,43 @@ def test_setpts_replaces_points(env):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_setpts_changes_the_rows_reached(env, prec):
+    """The row passes of the fine-grid FFT transform only the rows the points'
+    taps reach, a set fixed by setpts (with T zeroed elsewhere).  A plan
+    re-pointed from a narrow theta band to another band, then to uniform
+    points half of which are given as their doubled-torus twins
+    (2 pi - theta, phi + pi) (rows in the other half of the grid), matches
+    the oracle after every change, synthesis and adjoint."""
+    torch, nu = env
+    L = 60
+    rng = np.random.default_rng(5)
+
+    def band(lo, hi, n):
+        return np.stack([rng.uniform(lo, hi, n), rng.uniform(0.0, 2 * np.pi, n)], 1)
+
+    a = W.alm_gaussian(L, seed=3)
+    p1, p2 = band(0.2, 0.5, 4000), band(2.0, 2.8, 5000)
+    p3 = W.points_uniform(6000, seed=4)
+    twin = p3.copy()
+    half = rng.random(p3.shape[0]) < 0.5
+    twin[half, 0] = 2 * np.pi - p3[half, 0]
+    twin[half, 1] = p3[half, 1] + np.pi
+    cd = torch.complex128 if prec == "fp64" else torch.complex64
+    rd = torch.float64 if prec == "fp64" else torch.float32
+    plan = nu.Plan(L, dev(torch, p1), eps=TOL[prec], precision=prec)
+    ad = dev(torch, a, cd)
+    for k, (given, ref_pts) in enumerate(((p1, p1), (p2, p2), (twin, p3))):
+        if k > 0:
+            plan.setpts(dev(torch, given))
+        f = plan.synth(ad).double().cpu().numpy()
+        assert oracle.eps_eff(oracle.synth(a, ref_pts, L), f) <= TOL[prec], k
+        y = rng.standard_normal(given.shape[0]).astype(np.float32).astype(np.float64)
+        c = plan.adjoint(dev(torch, y, rd)).cpu().numpy().astype(np.complex128)
+        assert oracle.eps_eff(oracle.adjoint(y, ref_pts, L), c) <= TOL[prec], k
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_gl1023_subset(env, prec):
     """lmax = 1023 on the 1024 x 2047 deflected GL grid; 10^4-point oracle subset."""
     torch, nu = env
