@@ -356,13 +356,20 @@ NUSHT_API int nusht_adjoint_direct_noalloc(int lmax, int mmax, int64_t npts, con
 
 /* ------------------------------------------------------------------------
  * Batched transforms: many independent transforms of uneven lmax and point
- * count in one plan (NUSHT_MIXED only; each lmax <= 4095).  Members are
+ * count in one plan (NUSHT_MIXED or NUSHT_FP64; each lmax <= 4095).  Members are
  * grouped into buckets of up to 64 that share one Clenshaw-Curtis ring set,
  * so one FP64 recurrence per (ring pair, l, m) serves every member of a
  * bucket (Sec. 3: the recurrence is the O(lmax^3) part); the contraction
  * over l (synthesis) or rings (adjoint) runs for all members at once, on the
  * tensor cores (Sec. 4's mixed-precision split: TF32 hi/lo operands, FP32
- * accumulation) or in FP32 on the CUDA cores (opts.tensor_cores).  The grouping minimises a cost model of recurrence and contraction
+ * accumulation) or in FP32 on the CUDA cores (opts.tensor_cores).  NUSHT_FP64
+ * plans split both operands of the contraction into five bf16 slices under
+ * one power of two (the recurrence values per order, the coefficients or
+ * folded spectrum per order and member) and run the 15 leading slice
+ * products on the tensor cores, exact in FP32 for the two leading levels
+ * (~38 significant bits against the largest terms: eps down to 1e-10);
+ * their members run the double-float FFT and NUFFT kernels of FP64 plans.
+ * The grouping minimises a cost model of recurrence and contraction
  * work.  Each direction's whole stage sequence is captured once into a CUDA
  * graph and replayed; it is re-captured when the buffer pointers change.
  * ------------------------------------------------------------------------ */
@@ -372,7 +379,10 @@ typedef struct nusht_batch_s* nusht_batch_t;
  * nusht_plan_many -- plan nbatch transforms.
  *   lmax[b]   band limit of member b (mmax = lmax), 0 <= lmax[b] <= 4095
  *   npts[b]   its number of points; d_pts[b] its device (theta, phi) pairs
- *   eps       accuracy, >= 1e-6 (mixed precision); precision must be NUSHT_MIXED
+ *   eps       accuracy, >= 1e-6 for NUSHT_MIXED, >= 1e-10 for NUSHT_FP64
+ *   precision NUSHT_MIXED or NUSHT_FP64 (NUSHT_ENOMEM when the FP64 split
+ *             tables, ~20 bytes per kept (ring pair, l, m), do not fit in
+ *             half the free device memory)
  * The host arrays lmax, npts, d_pts are read during the call only.
  * Synchronises `stream`.
  */
@@ -382,8 +392,10 @@ NUSHT_API int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, c
 
 /*
  * nusht_synth_many / nusht_adjoint_many -- all members at once.
- *   d_alm[b]  device complex64 coefficients of member b (its own m-major layout)
- *   d_map[b]  device float[npts[b]] values in member b's point order
+ *   d_alm[b]  device coefficients of member b (its own m-major layout):
+ *             complex64 (NUSHT_MIXED) or complex128 (NUSHT_FP64)
+ *   d_map[b]  device float[npts[b]] (NUSHT_MIXED) or double[npts[b]]
+ *             (NUSHT_FP64) values in member b's point order
  * The pointer arrays are host arrays read during the call.  The first call
  * with a given set of buffers captures a CUDA graph (this synchronises the
  * stream and writes the plan's device pointer tables); later calls with the
@@ -416,7 +428,8 @@ NUSHT_API int nusht_batch_status(nusht_batch_t p, nusht_stream_t stream);
 /*
  * nusht_batch_path -- the contraction path of bucket `bucket`: 2 = tensor
  * cores from the recurrence table, 1 = CUDA-core FP32 from the table,
- * 0 = CUDA-core FP32 with the recurrence run every call; -1 for a bad
+ * 0 = CUDA-core FP32 with the recurrence run every call, 3 = FP64 split
+ * bf16 contraction on the tensor cores; -1 for a bad
  * argument.
  */
 NUSHT_API int nusht_batch_path(nusht_batch_t p, int bucket);

@@ -486,16 +486,21 @@ class Plan:
 
 
 class BatchPlan:
-    """Many transforms of uneven lmax and point count in one plan (mixed
-    precision): complex64 a_lm, float32 maps.  ``pts_list[b]`` is a CUDA
-    float64 (N_b, 2) tensor; each lmax <= 4095."""
+    """Many transforms of uneven lmax and point count in one plan.
+    ``precision="mixed"``: complex64 a_lm, float32 maps; ``"fp64"``:
+    complex128 a_lm, float64 maps, the Legendre contraction split into bf16
+    slices on the tensor cores.  ``pts_list[b]`` is a CUDA float64 (N_b, 2)
+    tensor; each lmax <= 4095."""
 
     def __init__(self, lmaxs, pts_list, eps: float = 1e-5, sigma: float = 0.0, legendre_table: int = 0,
                  tune: int = 0, tensor_cores: int = 0, deterministic: bool = False, fft_kernels: int = 0,
-                 stream=None):
+                 stream=None, precision="mixed"):
         import torch
 
         self.lib = load()
+        self.precision = _prec(precision)
+        self._cdt = torch.complex128 if self.precision == FP64 else torch.complex64
+        self._rdt = torch.float64 if self.precision == FP64 else torch.float32
         self.lmaxs = [int(l) for l in lmaxs]
         n = len(self.lmaxs)
         if len(pts_list) != n:
@@ -509,8 +514,8 @@ class BatchPlan:
         o = _opts(sigma, legendre_table=legendre_table, tune=tune, tensor_cores=tensor_cores,
                   deterministic=deterministic, fft_kernels=fft_kernels)
         h = ctypes.c_void_p()
-        _check(self.lib.nusht_plan_many(ctypes.byref(h), n, larr, narr, parr, float(eps), MIXED, ctypes.byref(o),
-                                        _stream_ptr(stream)), "nusht_plan_many")
+        _check(self.lib.nusht_plan_many(ctypes.byref(h), n, larr, narr, parr, float(eps), self.precision,
+                                        ctypes.byref(o), _stream_ptr(stream)), "nusht_plan_many")
         self._h = h
         self.n = n
 
@@ -540,10 +545,10 @@ class BatchPlan:
         import torch
 
         if outs is None:
-            outs = [torch.empty(n, dtype=torch.float32, device=self.device) for n in self.npts]
+            outs = [torch.empty(n, dtype=self._rdt, device=self.device) for n in self.npts]
         for a, l in zip(alms, self.lmaxs):
-            if not (a.is_cuda and a.dtype == torch.complex64 and a.shape == (nalm(l),) and a.is_contiguous()):
-                raise ValueError("alm must be contiguous CUDA complex64 of length nalm(lmax)")
+            if not (a.is_cuda and a.dtype == self._cdt and a.shape == (nalm(l),) and a.is_contiguous()):
+                raise ValueError("alm must be contiguous CUDA %s of length nalm(lmax)" % self._cdt)
         ia = (ctypes.c_void_p * self.n)(*[a.data_ptr() for a in alms])
         oa = (ctypes.c_void_p * self.n)(*[o.data_ptr() for o in outs])
         _check(self.lib.nusht_synth_many(self._h, ia, oa, _stream_ptr(stream)), "nusht_synth_many")
@@ -553,10 +558,10 @@ class BatchPlan:
         import torch
 
         if outs is None:
-            outs = [torch.empty(nalm(l), dtype=torch.complex64, device=self.device) for l in self.lmaxs]
+            outs = [torch.empty(nalm(l), dtype=self._cdt, device=self.device) for l in self.lmaxs]
         for m, n in zip(maps, self.npts):
-            if not (m.is_cuda and m.dtype == torch.float32 and m.shape == (n,) and m.is_contiguous()):
-                raise ValueError("maps must be contiguous CUDA float32 of length npts")
+            if not (m.is_cuda and m.dtype == self._rdt and m.shape == (n,) and m.is_contiguous()):
+                raise ValueError("maps must be contiguous CUDA %s of length npts" % self._rdt)
         ia = (ctypes.c_void_p * self.n)(*[m.data_ptr() for m in maps])
         oa = (ctypes.c_void_p * self.n)(*[o.data_ptr() for o in outs])
         _check(self.lib.nusht_adjoint_many(self._h, ia, oa, _stream_ptr(stream)), "nusht_adjoint_many")

@@ -28,6 +28,7 @@
 
 #include "nusht_internal.cuh"
 #include "recurrence.cuh"
+#include "dfloat.cuh"
 
 struct nusht_batch_s;
 
@@ -1082,6 +1083,743 @@ __global__ void bucket_final_k(int L, int M, int B, const int* __restrict__ memb
   out[slot][idx_lm(Lb, l, m)] = make_float2(re, im);
 }
 
+// ---------------------------------------------------------------------------
+// FP64 batched plans: the split ("Ozaki") contraction on the tensor cores.
+//
+// The products per order m are those above, but every operand is an exact
+// sum of five bf16 slices under one power of two:
+//   x = 2^(e - 39) F,  F = round(x 2^(39 - e)) = sum_{i<5} d_i 256^(4 - i),
+// with |x| < 2^e and d_i the balanced base-256 digits of F (|d_i| <= 129), so
+// the representation error is at most 2^(e - 40).  Slice i is stored as
+// d_i 2^(-8 i) (at most 8 significant bits: exact in bf16), and then every
+// slice product d_i d_j 2^(-8 (i + j)) is exact in the tensor core's FP32
+// product.  The recurrence values Pbar_l^m(theta) are split at plan time
+// with one exponent per order (their largest magnitude over the bucket's
+// rings and degrees); the coefficients (synthesis) and the folded spectrum
+// (adjoint) are split per call with one exponent per (order, member column).
+// The 15 slice products with i + j <= 4 go to four accumulators per parity,
+// one per level i + j (the last one takes levels 3 and 4):
+//   D0 = sum d_0 d_0            integers below 2^14: exact while the sum stays
+//                               below 2^24 (1024 full-magnitude terms);
+//   D1 = sum over i + j = 1     multiples of 2^-8 below 2^6: exact while below
+//                               2^16 (random-sign sums of 1024 terms stay
+//                               near 2^11);
+//   D2 = sum over i + j = 2     multiples of 2^-16 below 2^-2: exact while
+//                               below 2^8;
+//   D3 = sum over i + j = 3, 4  rounded FP32 sums, ~2^-8 of D2.
+// The tensor core's FP32 accumulation aligns with truncation, so a rounded
+// accumulator's error grows with the number of MMAs folded into it; with one
+// accumulator for every level from 2 on, that error reached 2^-33 of the
+// result at 100 degrees.  With the exact levels apart, the dropped products
+// (i + j >= 5), the representation errors and D3's truncation stay near
+// 2^-38 of the product of the two operands' scales: D0 + D1 + D2 + D3 times
+// 2^(eA + eB - 14) has the accuracy class of the FP64 recurrence path.
+//
+// Block shapes: M = 128 rows, N = 64 columns (32 members, re / im), K = 16.
+//   synthesis: rows = the 128 ring pairs of a kept work item, K = 16 degrees
+//              of one parity (a chunk = 32 degrees);
+//   adjoint:   rows = 128 degrees of one parity (256 degrees per block),
+//              K = 16 ring pairs (8 chunks per kept work item).
+// A chunk is 10 A tiles (2 parities x 5 slices, 128 x 16 bf16 = 4 KB each)
+// and 10 B tiles (64 x 16 bf16 = 2 KB each) in the no-swizzle K-major
+// core-matrix layout of the TF32 kernel above (with 16-bit elements a core
+// matrix is 8 rows x 8 values), moved by two cp.async.bulk copies into a
+// ring of three 60 KB buffers; one thread issues the 30 MMAs of a chunk.
+// The eight accumulators (E, O) x (D0 .. D3) take all 512 TMEM columns.  The
+// synthesis epilogue forms north = E + O and south = E - O as float pairs
+// (the theta FFT of FP64 members reads float pairs); the adjoint's builds
+// each coefficient's double from a 64-bit fixed-point sum with integer
+// operations, so the FP64 pipe (1/64 of the FP32 rate on GB300) stays idle.
+// ---------------------------------------------------------------------------
+constexpr int OZ_NS = 5;                        // slices per operand
+constexpr int OZ_ATILE = 128 * 16 * 2;          // 128 rows x 16 bf16
+constexpr int OZ_BTILE = 64 * 16 * 2;           // 64 rows x 16 bf16
+constexpr int OZ_A = 2 * OZ_NS * OZ_ATILE;      // A half of a chunk (40 KB)
+constexpr int OZ_B = 2 * OZ_NS * OZ_BTILE;      // B half of a chunk (20 KB)
+constexpr int OZ_CHUNK = OZ_A + OZ_B;
+constexpr int OZ_NBUF = 3;
+constexpr int OZ_THREADS = 32 * 6;              // producer, MMA issuer, 4 epilogue warps
+constexpr int OZ_SMEM = OZ_NBUF * OZ_CHUNK + 256;
+constexpr int OZ_COLS = 128;                    // columns of eB per order (64 members, re / im)
+constexpr int OZ_LV = 4;                        // accumulator levels per parity
+// instruction descriptor: D f32 (bits 4-5 = 1), A and B bf16 (bits 7-9,
+// 10-12 = 1), both K-major, N = 64 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24)
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+static_assert(OZ_SMEM <= 227 * 1024, "three chunk buffers fit in shared memory");
+
+// byte offset of element (row, k) in a K-major tile of 16 bf16 per row
+__device__ __forceinline__ int oz_off(int row, int k) {
+  return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// balanced base-256 digits: F = sum_i d[i] 256^(4 - i), d[1..4] in [-128, 127]
+__device__ __forceinline__ void oz_digits(long long F, int (&d)[OZ_NS]) {
+#pragma unroll
+  for (int i = OZ_NS - 1; i > 0; --i) {
+    const long long r = ((F + 128) & 255) - 128;
+    d[i] = (int)r;
+    F = (F - r) >> 8;  // exact: F - r is a multiple of 256
+  }
+  d[0] = (int)F;
+}
+
+// bf16 bits of d 2^(-8 i): the float is exact and its low 16 bits are zero
+__device__ __forceinline__ uint32_t oz_bf16(int d, int i) {
+  return __float_as_uint((float)d * __int_as_float((127 - 8 * i) << 23)) >> 16;
+}
+
+// round(v 2^k) as a 64-bit integer (|v 2^k| < 2^52), integer operations only;
+// zero and subnormal v give 0
+__device__ __forceinline__ long long oz_fix_d(double v, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) return 0;
+  const long long mant = (long long)((b & 0xfffffffffffffull) | 0x10000000000000ull);
+  const int sh = ex - 1075 + k;  // v = mant 2^(ex - 1075)
+  long long r;
+  if (sh >= 0)
+    r = mant << (sh < 11 ? sh : 11);
+  else if (sh <= -54)
+    r = 0;
+  else
+    r = (mant + (1ll << (-sh - 1))) >> (-sh);
+  return (b >> 63) ? -r : r;
+}
+
+// round(v 2^k) for a float (|v 2^k| < 2^62)
+__device__ __forceinline__ long long oz_fix_f(float v, int k) {
+  const uint32_t b = __float_as_uint(v);
+  const int ex = (int)((b >> 23) & 0xff);
+  if (ex == 0) return 0;
+  const long long mant = (long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = ex - 150 + k;  // v = mant 2^(ex - 150)
+  long long r;
+  if (sh >= 0)
+    r = mant << (sh < 38 ? sh : 38);
+  else if (sh <= -25)
+    r = 0;
+  else
+    r = (mant + (1ll << (-sh - 1))) >> (-sh);
+  return (b >> 31) ? -r : r;
+}
+
+// N 2^k as a double (round half away from zero to 53 bits), integer
+// operations only; results below the normal range are 0
+__device__ __forceinline__ double oz_dbl(long long N, int k) {
+  if (N == 0) return 0.0;
+  const unsigned long long sgn = N < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = N < 0 ? (unsigned long long)(-N) : (unsigned long long)N;
+  const int top = 63 - __clzll((long long)u);  // index of the leading one
+  int e2 = top + k;
+  unsigned long long mnt;
+  if (top > 52) {
+    const int s = top - 52;
+    mnt = (u + (1ull << (s - 1))) >> s;
+    if (mnt >> 53) {
+      mnt >>= 1;
+      ++e2;
+    }
+  } else {
+    mnt = u << (52 - top);
+  }
+  if (e2 < -1022) return 0.0;
+  if (e2 > 1023) return __longlong_as_double((long long)(sgn | 0x7ff0000000000000ull));
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e2 + 1023) << 52) | (mnt & 0xfffffffffffffull)));
+}
+
+// 2^k as a float (0 below the normal range, saturated above)
+__device__ __forceinline__ float oz_pow2f(int k) {
+  k = k > 127 ? 127 : k;
+  return k < -126 ? 0.f : __int_as_float((k + 127) << 23);
+}
+
+// exponent e with |x| < 2^e of the double whose |bits| are b (0 for b = 0)
+__device__ __forceinline__ int oz_exp_of(unsigned long long b) { return b ? (int)(b >> 52) - 1022 : 0; }
+
+__device__ __forceinline__ unsigned long long oz_warp_max(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Plan time, pass 1: the largest |Pbar| of every order over the bucket's
+// rings and degrees, as the bits of a non-negative double (which order like
+// unsigned integers).  One warp per kept work item (order m, 128 ring pairs).
+__global__ void __launch_bounds__(128) oz_amax_k(BucketArgs a, const int* __restrict__ items, int nitems,
+                                                 const double* __restrict__ ahat,
+                                                 unsigned long long* __restrict__ amax) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  const int v = items[it];
+  const int m = v >> 16, blk = v & 0xffff;
+  const int L = a.lmax;
+  const int mb = idx_lm(L, 0, m);
+  Chain ch[LEG_K];
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) chain_init(ch[k], a, m, 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane);
+  unsigned long long mx = 0;
+  for (int l = m; l <= L; ++l) {
+    const bool step = l > m;
+    const double c = step ? __ldg(a.c + mb + l) : 0.0;
+    const int rs = step ? (int)__ldg(a.dshift + mb + l) : 0;
+    const double ah = __ldg(ahat + mb + l);
+#pragma unroll
+    for (int k = 0; k < LEG_K; ++k) {
+      if (step) chain_step(ch[k], c, rs);
+      if (ch[k].valid && ch[k].E == 0) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(ch[k].q1 * ah) & 0x7fffffffffffffffull;
+        mx = b > mx ? b : mx;
+      }
+    }
+  }
+  mx = oz_warp_max(mx);
+  if (lane == 0 && mx) atomicMax(amax + m, mx);
+}
+
+// Plan time, pass 2: the slices of Pbar = q Ahat into the synthesis table
+// (per item: [chunk of 32 degrees][parity][slice] tiles, rows = ring pairs,
+// k = degree / 2 within the chunk) and the adjoint table (per order:
+// [block of 256 degrees][item, 16-pair group][parity][slice] tiles, rows =
+// degree / 2 within the block, k = ring pair within the group).  The tables
+// are zero-filled beforehand; zero values are not written.
+__global__ void __launch_bounds__(128) oz_build_k(BucketArgs a, const int* __restrict__ items, int nitems,
+                                                  const int* __restrict__ mfirst, const double* __restrict__ ahat,
+                                                  const int* __restrict__ eA, const int64_t* __restrict__ soff,
+                                                  const int64_t* __restrict__ tbase, unsigned char* __restrict__ AS,
+                                                  unsigned char* __restrict__ AT) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (it >= nitems) return;
+  const int v = items[it];
+  const int m = v >> 16, blk = v & 0xffff;
+  const int L = a.lmax;
+  const int mb = idx_lm(L, 0, m);
+  const int j = it - mfirst[m], nim = mfirst[m + 1] - mfirst[m];
+  const int sh = 39 - eA[m];
+  unsigned char* sbase = AS + soff[it];
+  unsigned char* tb = AT + tbase[m];
+  Chain ch[LEG_K];
+#pragma unroll
+  for (int k = 0; k < LEG_K; ++k) chain_init(ch[k], a, m, 1 + blk * LEG_PAIRS_PER_WARP + k * 32 + lane);
+  for (int l = m; l <= L; ++l) {
+    const bool step = l > m;
+    const double c = step ? __ldg(a.c + mb + l) : 0.0;
+    const int rs = step ? (int)__ldg(a.dshift + mb + l) : 0;
+    const double ah = __ldg(ahat + mb + l);
+    const int r = l - m, par = r & 1;
+    unsigned char* ps = sbase + (size_t)(r >> 5) * OZ_A + par * OZ_NS * OZ_ATILE;
+    const int ks = (r & 31) >> 1;
+    unsigned char* pt = tb + (size_t)(r >> 8) * 8 * nim * OZ_A + par * OZ_NS * OZ_ATILE;
+    const int arow = (r & 255) >> 1;
+#pragma unroll
+    for (int k = 0; k < LEG_K; ++k) {
+      if (step) chain_step(ch[k], c, rs);
+      if (!(ch[k].valid && ch[k].E == 0)) continue;
+      const long long F = oz_fix_d(ch[k].q1 * ah, sh);
+      if (F == 0) continue;
+      int d[OZ_NS];
+      oz_digits(F, d);
+      const int row = k * 32 + lane;  // ring pair within the item
+      unsigned char* qs = ps + oz_off(row, ks);
+      unsigned char* qt = pt + (size_t)(8 * j + (row >> 4)) * OZ_A + oz_off(arow, row & 15);
+#pragma unroll
+      for (int i = 0; i < OZ_NS; ++i) {
+        const unsigned short bv = (unsigned short)oz_bf16(d[i], i);
+        *reinterpret_cast<unsigned short*>(qs + i * OZ_ATILE) = bv;
+        *reinterpret_cast<unsigned short*>(qt + i * OZ_ATILE) = bv;
+      }
+    }
+  }
+}
+
+// pack the 8 values of one 16-byte tile row piece (slice i of 8 consecutive k)
+__device__ __forceinline__ void oz_put(uint32_t (&w)[OZ_NS][4], int kk, const int (&d)[OZ_NS]) {
+#pragma unroll
+  for (int i = 0; i < OZ_NS; ++i) {
+    const uint32_t b = oz_bf16(d[i], i);
+    w[i][kk >> 1] = (kk & 1) ? (w[i][kk >> 1] | (b << 16)) : b;
+  }
+}
+
+__device__ __forceinline__ void oz_store(unsigned char* dst, const uint32_t (&w)[OZ_NS][4]) {
+#pragma unroll
+  for (int i = 0; i < OZ_NS; ++i)
+    *reinterpret_cast<uint4*>(dst + i * OZ_BTILE) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+}
+
+// Per call, synthesis: the members' coefficients of order m (one block per
+// order with kept items) as B slices [chunk of 32 degrees][column group]
+// [parity][slice] (rows = the group's 64 columns, k = degree / 2 in the
+// chunk), with eB[m][col] such that |a| < 2^eB over the order's degrees.
+// Coefficients past a member's lmax, and slots without a member, are zero;
+// m = 0 coefficients are real.
+__global__ void __launch_bounds__(256) oz_bs_k(int L, int B, int ncg, const int* __restrict__ memberL,
+                                               const double2* const* __restrict__ alm,
+                                               const int* __restrict__ mfirst, const int64_t* __restrict__ boff,
+                                               int* __restrict__ eB, unsigned char* __restrict__ Bt) {
+  const int m = blockIdx.x;
+  if (mfirst[m + 1] == mfirst[m]) return;
+  __shared__ double2 sa[32][65];  // [degree in the chunk][member slot]
+  __shared__ int se[OZ_COLS];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int slot = warp; slot < BK_MAXB; slot += 8) {
+    unsigned long long mr = 0, mi = 0;
+    const int Ls = slot < B ? memberL[slot] : -1;
+    if (m <= Ls) {
+      const double2* src = alm[slot] + idx_lm(Ls, 0, m);
+      for (int l = m + lane; l <= Ls; l += 32) {
+        const double2 v = src[l];
+        const unsigned long long br = (unsigned long long)__double_as_longlong(v.x) & 0x7fffffffffffffffull;
+        const unsigned long long bi = (unsigned long long)__double_as_longlong(v.y) & 0x7fffffffffffffffull;
+        mr = br > mr ? br : mr;
+        if (m > 0) mi = bi > mi ? bi : mi;
+      }
+    }
+    mr = oz_warp_max(mr);
+    mi = oz_warp_max(mi);
+    if (lane == 0) {
+      se[2 * slot] = oz_exp_of(mr);
+      se[2 * slot + 1] = oz_exp_of(mi);
+      eB[(size_t)m * OZ_COLS + 2 * slot] = oz_exp_of(mr);
+      eB[(size_t)m * OZ_COLS + 2 * slot + 1] = oz_exp_of(mi);
+    }
+  }
+  __syncthreads();
+  const int nch = (L - m + 1 + 31) >> 5;
+  const int row = t & 63, kh = (t >> 6) & 1, par = t >> 7;
+  for (int c = 0; c < nch; ++c) {
+    for (int idx = t; idx < 32 * BK_MAXB; idx += 256) {
+      const int slot = idx >> 5, li = idx & 31;
+      const int l = m + 32 * c + li;
+      double2 v = make_double2(0.0, 0.0);
+      const int Ls = slot < B ? memberL[slot] : -1;
+      if (m <= Ls && l <= Ls) {
+        v = alm[slot][idx_lm(Ls, l, m)];
+        if (m == 0) v.y = 0.0;
+      }
+      sa[li][slot] = v;
+    }
+    __syncthreads();
+    for (int cg = 0; cg < ncg; ++cg) {
+      const int col = cg * 64 + row, slot = col >> 1;
+      const int sh = 39 - se[col];
+      uint32_t w[OZ_NS][4];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const int li = 2 * (kh * 8 + kk) + par;
+        const double x = (col & 1) ? sa[li][slot].y : sa[li][slot].x;
+        int d[OZ_NS];
+        oz_digits(oz_fix_d(x, sh), d);
+        oz_put(w, kk, d);
+      }
+      oz_store(Bt + boff[m] + ((size_t)c * ncg + cg) * OZ_B + (size_t)par * OZ_NS * OZ_BTILE + (row >> 3) * 256 +
+                   kh * 128 + (row & 7) * 16,
+               w);
+    }
+    __syncthreads();
+  }
+}
+
+// the DFS fold of one ring pair of a member's theta-grid row (float pairs
+// hi_re, lo_re, hi_im, lo_im) in 2^k fixed point: e = S_E, o = S_O (re, im)
+__device__ __forceinline__ long long oz_fixp(float h, float l, int k) { return oz_fix_f(h, k) + oz_fix_f(l, k); }
+
+// Per call, adjoint: the members' folded spectrum of order m,
+//   fn = G[j] + (-1)^m G[M - j],  fs = G[M/2 - j] + (-1)^m G[M/2 + j]  (0 at the equator pair),
+//   S_E = fn + fs,  S_O = fn - fs,
+// as B slices [item][16-pair group][column group][parity][slice] (rows = the
+// group's 64 columns, k = ring pair in the group), with eB[m][col] such that
+// |S| < 2^eB over the order's kept ring pairs (from the high words: a value
+// may reach the digit 129, which bf16 holds exactly).
+__global__ void __launch_bounds__(256) oz_fold_k(int L, int M, int npairs, int B, int ncg,
+                                                 const int* __restrict__ memberL, const float4* const* __restrict__ gh,
+                                                 const int* __restrict__ items, const int* __restrict__ mfirst,
+                                                 const int64_t* __restrict__ boff, int* __restrict__ eB,
+                                                 unsigned char* __restrict__ Bt) {
+  const int m = blockIdx.x;
+  const int i0 = mfirst[m], nim = mfirst[m + 1] - i0;
+  if (nim == 0) return;
+  __shared__ long long sF[2][16][OZ_COLS + 1];  // [parity][ring pair in the group][column]
+  __shared__ int se[OZ_COLS];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const float sg = (m & 1) ? -1.f : 1.f;
+  for (int slot = warp; slot < BK_MAXB; slot += 8) {
+    float mr = 0.f, mi = 0.f;
+    const int Ls = slot < B ? memberL[slot] : -1;
+    if (m <= Ls) {
+      const float4* row = gh[slot] + (size_t)m * M;
+      for (int q = lane; q < nim * 128; q += 32) {
+        const int jn = 1 + (items[i0 + (q >> 7)] & 0xffff) * 128 + (q & 127);
+        if (jn > npairs) continue;
+        const int js = M / 2 - jn;
+        const float4 g0 = row[jn], g1 = row[M - jn];
+        float nr = g0.x + sg * g1.x, ni = g0.z + sg * g1.z, sr = 0.f, si = 0.f;
+        if (js != jn) {
+          const float4 h0 = row[js], h1 = row[M - js];
+          sr = h0.x + sg * h1.x;
+          si = h0.z + sg * h1.z;
+        }
+        mr = fmaxf(mr, fmaxf(fabsf(nr + sr), fabsf(nr - sr)));
+        mi = fmaxf(mi, fmaxf(fabsf(ni + si), fabsf(ni - si)));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+      mi = fmaxf(mi, __shfl_xor_sync(0xffffffffu, mi, o));
+    }
+    if (lane == 0) {
+      const int er = mr > 0.f ? ilogbf(mr) + 1 : 0, ei = mi > 0.f ? ilogbf(mi) + 1 : 0;
+      se[2 * slot] = er;
+      se[2 * slot + 1] = ei;
+      eB[(size_t)m * OZ_COLS + 2 * slot] = er;
+      eB[(size_t)m * OZ_COLS + 2 * slot + 1] = ei;
+    }
+  }
+  __syncthreads();
+  const int row = t & 63, kh = (t >> 6) & 1, par = t >> 7;
+  for (int tt = 0; tt < 8 * nim; ++tt) {
+    const int blk = items[i0 + (tt >> 3)] & 0xffff;
+    for (int idx = t; idx < 16 * BK_MAXB; idx += 256) {
+      const int slot = idx >> 4, kk = idx & 15;
+      const int jn = 1 + blk * 128 + (tt & 7) * 16 + kk;
+      long long er = 0, ei = 0, orr = 0, oi = 0;
+      const int Ls = slot < B ? memberL[slot] : -1;
+      if (m <= Ls && jn <= npairs) {
+        const int kr = 39 - se[2 * slot], ki = 39 - se[2 * slot + 1];
+        const float4* rw = gh[slot] + (size_t)m * M;
+        const int js = M / 2 - jn;
+        const float4 g0 = rw[jn], g1 = rw[M - jn];
+        long long nr = oz_fixp(g0.x, g0.y, kr), ni = oz_fixp(g0.z, g0.w, ki);
+        long long ur = oz_fixp(g1.x, g1.y, kr), ui = oz_fixp(g1.z, g1.w, ki);
+        if (m & 1) {
+          ur = -ur;
+          ui = -ui;
+        }
+        nr += ur;
+        ni += ui;
+        long long sr = 0, si = 0;
+        if (js != jn) {
+          const float4 h0 = rw[js], h1 = rw[M - js];
+          sr = oz_fixp(h0.x, h0.y, kr);
+          si = oz_fixp(h0.z, h0.w, ki);
+          long long vr = oz_fixp(h1.x, h1.y, kr), vi = oz_fixp(h1.z, h1.w, ki);
+          if (m & 1) {
+            vr = -vr;
+            vi = -vi;
+          }
+          sr += vr;
+          si += vi;
+        }
+        er = nr + sr;
+        ei = ni + si;
+        orr = nr - sr;
+        oi = ni - si;
+      }
+      sF[0][kk][2 * slot] = er;
+      sF[0][kk][2 * slot + 1] = ei;
+      sF[1][kk][2 * slot] = orr;
+      sF[1][kk][2 * slot + 1] = oi;
+    }
+    __syncthreads();
+    for (int cg = 0; cg < ncg; ++cg) {
+      const int col = cg * 64 + row;
+      uint32_t w[OZ_NS][4];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        int d[OZ_NS];
+        oz_digits(sF[par][kh * 8 + kk][col], d);
+        oz_put(w, kk, d);
+      }
+      oz_store(Bt + boff[m] + ((size_t)tt * ncg + cg) * OZ_B + (size_t)par * OZ_NS * OZ_BTILE + (row >> 3) * 256 +
+                   kh * 128 + (row & 7) * 16,
+               w);
+    }
+    __syncthreads();
+  }
+}
+
+// synthesis: F_0 at the poles of every member, G[0][0] and G[0][M/2], as float
+// pairs (every other pole entry stays 0)
+__global__ void __launch_bounds__(256) oz_poles_k(int M, const int* __restrict__ memberL,
+                                                  const double2* const* __restrict__ alm,
+                                                  const double* __restrict__ pole_norm, float4* const* __restrict__ gp) {
+  const int slot = blockIdx.x;
+  const int Ls = memberL[slot];
+  __shared__ double sn[256], ss[256];
+  double n = 0.0, s = 0.0;
+  for (int l = threadIdx.x; l <= Ls; l += blockDim.x) {
+    const double v = alm[slot][l].x * pole_norm[l];
+    n += v;
+    s += (l & 1) ? -v : v;
+  }
+  sn[threadIdx.x] = n;
+  ss[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sn[threadIdx.x] += sn[threadIdx.x + h];
+      ss[threadIdx.x] += ss[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    float h0, l0, h1, l1;
+    df_of(sn[0], h0, l0);
+    df_of(ss[0], h1, l1);
+    gp[slot][0] = make_float4(h0, l0, 0.f, 0.f);
+    gp[slot][M / 2] = make_float4(h1, l1, 0.f, 0.f);
+  }
+}
+
+// the poles' part of an m = 0 adjoint coefficient
+__device__ __forceinline__ double oz_pole_term(const float4* g, int M, const double* pole_norm, int l) {
+  const float4 n = g[0], s = g[M / 2];
+  const double np = (double)n.x + (double)n.y, sp = (double)s.x + (double)s.y;
+  return pole_norm[l] * (np + ((l & 1) ? -sp : sp));
+}
+
+// adjoint: the coefficients of orders without kept items (0, plus the poles at m = 0)
+__global__ void __launch_bounds__(128) oz_zero_k(int M, const int* __restrict__ memberL,
+                                                 const int* __restrict__ mfirst, const float4* const* __restrict__ gh,
+                                                 const double* __restrict__ pole_norm, double2* const* __restrict__ out) {
+  const int m = blockIdx.x, slot = blockIdx.y;
+  if (mfirst[m + 1] > mfirst[m]) return;
+  const int Ls = memberL[slot];
+  if (m > Ls) return;
+  double2* o = out[slot] + idx_lm(Ls, 0, m);
+  for (int l = m + threadIdx.x; l <= Ls; l += blockDim.x)
+    o[l] = make_double2(m == 0 ? oz_pole_term(gh[slot], M, pole_norm, l) : 0.0, 0.0);
+}
+
+struct OzArgs {
+  int L, M, npairs, B, ncg;
+  const int* memberL;
+  const int* items;          // kept work items (m << 16 | block of 128 ring pairs), by order
+  const int* mfirst;         // items of order m: [mfirst[m], mfirst[m + 1])
+  const int2* work;          // synthesis: (item, column group); adjoint: (m, block << 8 | column group)
+  const unsigned char* A;    // split recurrence table (synthesis or adjoint order)
+  const int64_t* aoff;       // synthesis: per item; adjoint: per order
+  const unsigned char* Bt;   // split coefficients / folded spectrum
+  const int64_t* boff;       // per order
+  const int* eA;             // per order
+  const int* eB;             // [order][128 columns]
+  float4* const* gout;       // synthesis: members' ring sums (float pairs)
+  const float4* const* gh;   // adjoint: members' theta spectra (the poles)
+  double2* const* aout;      // adjoint: members' coefficients
+  const double* pole_norm;
+};
+
+struct OzBars {
+  uint64_t full[OZ_NBUF], empty[OZ_NBUF], done;
+  uint32_t tslot;
+  int abort;
+};
+
+__device__ __forceinline__ void oz_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(OZ_IDESC), "r"(acc)
+      : "memory");
+}
+
+// One block: synthesis (ADJ = false) = (kept item, column group), chunks of
+// 32 degrees; adjoint = (order m, 256 degrees, column group), chunks of 16
+// ring pairs over the order's kept items.  Warp 0 lane 0 copies the chunks,
+// warp 1 lane 0 issues the MMAs, warps 2-5 (TMEM lanes 32 (warp % 4) ..) run
+// the epilogue once the last MMA has completed.  Every wait is bounded (one
+// second); a block that gives up flags the others, waits (bounded) for its
+// copies and MMAs in flight, sets *status and still frees its tensor memory.
+template <bool ADJ>
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_tc_k(OzArgs z, int nblk, int* __restrict__ status,
+                                                        int test_giveup) {
+  extern __shared__ __align__(1024) unsigned char oz_smem[];
+  OzBars* bars = reinterpret_cast<OzBars*>(oz_smem + OZ_NBUF * OZ_CHUNK);
+  if ((int)blockIdx.x >= nblk || *(volatile int*)status) return;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int2 wk = z.work[blockIdx.x];
+  int m, cg, nchunk, blk = 0, q = 0;
+  const unsigned char* Abase;
+  if (!ADJ) {
+    const int v = z.items[wk.x];
+    m = v >> 16;
+    blk = v & 0xffff;
+    cg = wk.y;
+    nchunk = (z.L - m + 1 + 31) >> 5;
+    Abase = z.A + z.aoff[wk.x];
+  } else {
+    m = wk.x;
+    q = wk.y >> 8;
+    cg = wk.y & 255;
+    nchunk = 8 * (z.mfirst[m + 1] - z.mfirst[m]);
+    Abase = z.A + z.aoff[m] + (size_t)q * nchunk * OZ_A;
+  }
+  const unsigned char* Bbase = z.Bt + z.boff[m] + (size_t)cg * OZ_B;
+  const size_t bstride = (size_t)z.ncg * OZ_B;
+  volatile int* abort = &bars->abort;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars->tslot)),
+                 "r"(TC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) {
+    for (int k = 0; k < OZ_NBUF; ++k) {
+      mbar_init(&bars->full[k], 1);
+      mbar_init(&bars->empty[k], 1);
+    }
+    mbar_init(&bars->done, 1);
+    bars->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = bars->tslot;
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int issued = 0;
+      for (int c = 0; c < nchunk && !*abort; ++c) {
+        const int s = c % OZ_NBUF;
+        if (c >= OZ_NBUF && !mbar_wait(smem_u32(&bars->empty[s]), (uint32_t)((c / OZ_NBUF - 1) & 1), abort)) {
+          *abort = 1;
+          break;
+        }
+        unsigned char* dst = oz_smem + s * OZ_CHUNK;
+        mbar_expect_tx(&bars->full[s], OZ_CHUNK);
+        bulk_g2s(dst, Abase + (size_t)c * OZ_A, OZ_A, &bars->full[s]);
+        bulk_g2s(dst + OZ_A, Bbase + (size_t)c * bstride, OZ_B, &bars->full[s]);
+        issued = c + 1;
+      }
+      if (*abort)  // wait (bounded) for the copies still in flight
+        for (int c = issued > OZ_NBUF ? issued - OZ_NBUF : 0; c < issued; ++c)
+          mbar_wait(smem_u32(&bars->full[c % OZ_NBUF]), (uint32_t)((c / OZ_NBUF) & 1));
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      int last = -1;
+      for (int c = 0; c < nchunk && !*abort; ++c) {
+        const int s = c % OZ_NBUF;
+        if (!mbar_wait(smem_u32(&bars->full[s]), (uint32_t)((c / OZ_NBUF) & 1), abort,
+                       (test_giveup && c == 0) ? 0 : (1 << 30))) {
+          *abort = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sb = smem_u32(oz_smem + s * OZ_CHUNK);
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int i = 0; i < OZ_NS; ++i)
+#pragma unroll
+            for (int j = 0; j < OZ_NS - i; ++j) {
+              const int lv = i + j < OZ_LV - 1 ? i + j : OZ_LV - 1;
+              // the first products into D0 .. D3 of chunk 0 are (0,0) .. (0,3)
+              const uint32_t acc = (c > 0 || i > 0 || j > OZ_LV - 1) ? 1u : 0u;
+              oz_mma(tmem + (uint32_t)((p * OZ_LV + lv) * 64), tc_desc(sb + (p * OZ_NS + i) * OZ_ATILE),
+                     tc_desc(sb + OZ_A + (p * OZ_NS + j) * OZ_BTILE), acc);
+            }
+        tc_commit(&bars->empty[s]);
+        last = c;
+      }
+      if (!*abort) {
+        tc_commit(&bars->done);
+      } else if (last >= 0) {
+        // MMAs already issued still write tensor memory: wait (bounded) for
+        // the commit that covers them before the block frees it
+        mbar_wait(smem_u32(&bars->empty[last % OZ_NBUF]), (uint32_t)((last / OZ_NBUF) & 1));
+      }
+    }
+  } else {  // epilogue: TMEM lanes 32 (warp % 4) .. + 31 = rows
+    const bool okw = mbar_wait(smem_u32(&bars->done), 0u, abort);
+    if (!__all_sync(0xffffffffu, okw)) {
+      *abort = 1;
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int q4 = warp & 3;
+      const int r = q4 * 32 + lane;
+      const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+      const int M = z.M;
+      const int ea = z.eA[m];
+      const int* eb = z.eB + (size_t)m * OZ_COLS + cg * 64;
+      const int jn = 1 + blk * 128 + r, js = M / 2 - jn;
+      for (int cc = 0; cc < 4; ++cc) {
+        uint32_t v[2 * OZ_LV][16];
+#pragma unroll
+        for (int a8 = 0; a8 < 2 * OZ_LV; ++a8) tc_ld16(tl + (uint32_t)(a8 * 64 + cc * 16), v[a8]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int mm = 0; mm < 8; ++mm) {
+          const int slot = cg * 32 + cc * 8 + mm;
+          const int Ls = slot < z.B ? z.memberL[slot] : -1;
+          if (m > Ls) continue;
+          const int c0 = 2 * mm;  // re column (im: c0 + 1) within the 16 loaded
+          if (!ADJ) {
+            if (jn > z.npairs) continue;
+            float o[2][2][2];  // [re, im][north, south][hi, lo]
+#pragma unroll
+            for (int ri = 0; ri < 2; ++ri) {
+              float eh = __uint_as_float(v[0][c0 + ri]), el = 0.f;
+              float oh = __uint_as_float(v[OZ_LV][c0 + ri]), ol = 0.f;
+#pragma unroll
+              for (int k = 1; k < OZ_LV; ++k) {
+                df_add(eh, el, __uint_as_float(v[k][c0 + ri]), 0.f);
+                df_add(oh, ol, __uint_as_float(v[OZ_LV + k][c0 + ri]), 0.f);
+              }
+              float nh = eh, nl = el, sh = eh, sl = el;
+              df_add(nh, nl, oh, ol);
+              df_add(sh, sl, -oh, -ol);
+              const float sc = oz_pow2f(ea + eb[cc * 16 + c0 + ri] - 14);
+              o[ri][0][0] = nh * sc;
+              o[ri][0][1] = nl * sc;
+              o[ri][1][0] = sh * sc;
+              o[ri][1][1] = sl * sc;
+            }
+            const float sg = (m & 1) ? -1.f : 1.f;
+            float4* row = z.gout[slot] + (size_t)m * M;
+            const float4 fn = make_float4(o[0][0][0], o[0][0][1], o[1][0][0], o[1][0][1]);
+            row[jn] = fn;
+            row[M - jn] = make_float4(sg * fn.x, sg * fn.y, sg * fn.z, sg * fn.w);
+            if (js != jn) {
+              const float4 fs = make_float4(o[0][1][0], o[0][1][1], o[1][1][0], o[1][1][1]);
+              row[js] = fs;
+              row[M - js] = make_float4(sg * fs.x, sg * fs.y, sg * fs.z, sg * fs.w);
+            }
+          } else {
+            double2* dst = z.aout[slot] + idx_lm(Ls, 0, m);
+#pragma unroll
+            for (int par = 0; par < 2; ++par) {
+              const int l = m + 256 * q + 2 * r + par;
+              if (l > Ls) continue;
+              double x[2];
+#pragma unroll
+              for (int ri = 0; ri < 2; ++ri) {
+                // 2^-36 fixed point: D0 < 2^25 stays below 2^61
+                long long N = 0;
+#pragma unroll
+                for (int k = 0; k < OZ_LV; ++k) N += oz_fix_f(__uint_as_float(v[OZ_LV * par + k][c0 + ri]), 36);
+                x[ri] = oz_dbl(N, ea + eb[cc * 16 + c0 + ri] - 14 - 36);
+              }
+              if (m == 0) {
+                x[0] += oz_pole_term(z.gh[slot], M, z.pole_norm, l);
+                x[1] = 0.0;
+              }
+              dst[l] = make_double2(x[0], x[1]);
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (*abort && t == 0) atomicExch(status, 1);
+  tc_teardown(tmem);
+}
+
 struct Bucket {
   int L = 0, M = 0, B = 0, npairs = 0, nt = 1;
   std::vector<int> members;
@@ -1126,6 +1864,29 @@ struct Bucket {
   int64_t* bs_off = nullptr;
   cufftHandle theta = 0;
   bool have_theta = false;
+  // FP64 plans: the split contraction (items / mfirst above hold the FP64
+  // probe's kept work items of 128 ring pairs)
+  bool oz = false;
+  int ncg = 1;                        // column groups of 32 members
+  int2* oz_ws = nullptr;              // synthesis blocks (item, column group)
+  int2* oz_wa = nullptr;              // adjoint blocks (m, block << 8 | column group)
+  int noz_s = 0, noz_a = 0;
+  unsigned char* OZS = nullptr;       // split table, synthesis order (per item)
+  unsigned char* OZT = nullptr;       // split table, adjoint order (per order)
+  int64_t* ozs_off = nullptr;         // per item
+  int64_t* ozt_base = nullptr;        // per order
+  unsigned char* OBS = nullptr;       // per call: split coefficients
+  unsigned char* OBA = nullptr;       // per call: split folded spectrum
+  int64_t* obs_off = nullptr;         // per order
+  int64_t* oba_off = nullptr;         // per order
+  int* eA = nullptr;                  // per order
+  int* eBs = nullptr;                 // [order][128]
+  int* eBa = nullptr;
+  float4* Gp = nullptr;               // members' ring sums (float pairs), [slot][(L_k + 1) M]
+  float4** gout = nullptr;            // device [BK_MAXB]
+  float4** gh = nullptr;              // device [BK_MAXB]: members' theta spectra
+  std::vector<float4*> gout_h;        // host copy of gout
+  size_t oz_bytes = 0;
 };
 
 int64_t tri_count(int L, int M) { return (int64_t)(M / 4) * (int64_t)(L + 1) * (L + 2) / 2; }
@@ -1200,6 +1961,22 @@ void bucket_free(Bucket& b) {
   dev_free(b.pa_off);
   dev_free(b.pt_off);
   dev_free(b.bs_off);
+  dev_free(b.oz_ws);
+  dev_free(b.oz_wa);
+  dev_free(b.OZS);
+  dev_free(b.OZT);
+  dev_free(b.ozs_off);
+  dev_free(b.ozt_base);
+  dev_free(b.OBS);
+  dev_free(b.OBA);
+  dev_free(b.obs_off);
+  dev_free(b.oba_off);
+  dev_free(b.eA);
+  dev_free(b.eBs);
+  dev_free(b.eBa);
+  dev_free(b.Gp);
+  dev_free(b.gout);
+  dev_free(b.gh);
   if (b.have_theta) cufftDestroy(b.theta);
   b = Bucket();
 }
@@ -1525,6 +2302,168 @@ int bucket_build(nusht_batch_t p, Bucket& b, cudaStream_t s) {
   return NUSHT_OK;
 }
 
+// FP64 bucket: the FP64 probe's kept work items, both split tables, the
+// per-call operand buffers and the members' ring-sum buffers.
+int bucket_build_oz(nusht_batch_t p, Bucket& b, cudaStream_t s) {
+  const int L = b.L;
+  nusht_sizes z;
+  NUSHT_TRY(choose_sizes(L, L, p->eps, NUSHT_FP64, &p->opts, &z));
+  b.M = z.M;
+  b.npairs = b.M / 4;
+  PlanRole role;
+  role.nufft = false;
+  role.legendre = true;
+  nusht_opts lo = p->opts;  // the FP64 chain's tables (no table mode, no double-float chain)
+  lo.legendre_table = -1;
+  lo.fast_recurrence = 0;
+  lo.spin = 0;
+  NUSHT_TRY(plan_create(&b.leg, L, L, 0, nullptr, p->eps, NUSHT_FP64, &lo, s, role));
+  std::vector<int> items(b.leg->leg.nitems);
+  if (!items.empty())
+    NUSHT_CUDA(cudaMemcpy(items.data(), b.leg->leg.items, items.size() * 4, cudaMemcpyDeviceToHost));
+  std::sort(items.begin(), items.end());  // by order, then ring block
+  b.nitems = (int)items.size();
+  std::vector<int> mf(L + 2, 0);
+  for (int v : items) mf[(v >> 16) + 1]++;
+  for (int m = 0; m <= L; ++m) mf[m + 1] += mf[m];
+  b.ncg = (b.B + 31) / 32;
+  std::vector<int64_t> soff(items.size()), tb(L + 1, 0), bso(L + 1, 0), bao(L + 1, 0);
+  int64_t sa = 0, ta = 0, bs = 0, ba = 0;
+  std::vector<int2> ws, wa;
+  for (size_t it = 0; it < items.size(); ++it) {
+    const int m = items[it] >> 16;
+    soff[it] = sa;
+    sa += (int64_t)((L - m + 1 + 31) / 32) * OZ_A;
+    for (int cg = 0; cg < b.ncg; ++cg) ws.push_back(make_int2((int)it, cg));
+  }
+  for (int m = 0; m <= L; ++m) {
+    const int nim = mf[m + 1] - mf[m];
+    tb[m] = ta;
+    bso[m] = bs;
+    bao[m] = ba;
+    if (nim == 0) continue;
+    const int nq = (L - m + 1 + 255) / 256;
+    ta += (int64_t)nq * 8 * nim * OZ_A;
+    bs += (int64_t)((L - m + 1 + 31) / 32) * b.ncg * OZ_B;
+    ba += (int64_t)8 * nim * b.ncg * OZ_B;
+    for (int q = 0; q < nq; ++q)
+      for (int cg = 0; cg < b.ncg; ++cg) wa.push_back(make_int2(m, (q << 8) | cg));
+  }
+  b.noz_s = (int)ws.size();
+  b.noz_a = (int)wa.size();
+  int64_t gsz = 0;
+  b.gout_h.assign(BK_MAXB, nullptr);
+  std::vector<int64_t> goff(b.B);
+  for (int k = 0; k < b.B; ++k) {
+    goff[k] = gsz;
+    gsz += (int64_t)(p->L[b.members[k]] + 1) * b.M;
+  }
+  const size_t need = (size_t)(sa + ta + bs + ba) + (size_t)gsz * sizeof(float4);
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  if (need >= freeb / 2)
+    return set_error(NUSHT_ENOMEM, "FP64 batched plan: the split recurrence tables do not fit in device memory");
+  b.oz_bytes = need;
+  NUSHT_TRY(dev_alloc((void**)&b.items, std::max<size_t>(1, items.size()) * 4, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.mfirst, mf.size() * 4, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.oz_ws, std::max<size_t>(1, ws.size()) * sizeof(int2), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.oz_wa, std::max<size_t>(1, wa.size()) * sizeof(int2), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.ozs_off, std::max<size_t>(1, soff.size()) * 8, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.ozt_base, tb.size() * 8, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.obs_off, bso.size() * 8, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.oba_off, bao.size() * 8, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.OZS, std::max<int64_t>(16, sa), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.OZT, std::max<int64_t>(16, ta), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.OBS, std::max<int64_t>(16, bs), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.OBA, std::max<int64_t>(16, ba), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.eA, (size_t)(L + 1) * 4, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.eBs, (size_t)(L + 1) * OZ_COLS * 4, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.eBa, (size_t)(L + 1) * OZ_COLS * 4, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.Gp, std::max<int64_t>(1, gsz) * sizeof(float4), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.gout, BK_MAXB * sizeof(void*), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.gh, BK_MAXB * sizeof(void*), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.memberL, BK_MAXB * 4, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.alm_ptrs, BK_MAXB * sizeof(void*), &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.out_ptrs, BK_MAXB * sizeof(void*), &p->bytes));
+  if (!items.empty()) {
+    NUSHT_CUDA(cudaMemcpy(b.items, items.data(), items.size() * 4, cudaMemcpyHostToDevice));
+    NUSHT_CUDA(cudaMemcpy(b.ozs_off, soff.data(), soff.size() * 8, cudaMemcpyHostToDevice));
+  }
+  NUSHT_CUDA(cudaMemcpy(b.mfirst, mf.data(), mf.size() * 4, cudaMemcpyHostToDevice));
+  if (!ws.empty()) NUSHT_CUDA(cudaMemcpy(b.oz_ws, ws.data(), ws.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  if (!wa.empty()) NUSHT_CUDA(cudaMemcpy(b.oz_wa, wa.data(), wa.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  NUSHT_CUDA(cudaMemcpy(b.ozt_base, tb.data(), tb.size() * 8, cudaMemcpyHostToDevice));
+  NUSHT_CUDA(cudaMemcpy(b.obs_off, bso.data(), bso.size() * 8, cudaMemcpyHostToDevice));
+  NUSHT_CUDA(cudaMemcpy(b.oba_off, bao.data(), bao.size() * 8, cudaMemcpyHostToDevice));
+  std::vector<int> ml(BK_MAXB, -1);
+  for (int k = 0; k < b.B; ++k) {
+    ml[k] = p->L[b.members[k]];
+    b.gout_h[k] = b.Gp + goff[k];
+  }
+  NUSHT_CUDA(cudaMemcpy(b.memberL, ml.data(), BK_MAXB * 4, cudaMemcpyHostToDevice));
+  NUSHT_CUDA(cudaMemcpy(b.gout, b.gout_h.data(), BK_MAXB * sizeof(void*), cudaMemcpyHostToDevice));
+  NUSHT_CUDA(cudaMemsetAsync(b.OZS, 0, std::max<int64_t>(16, sa), s));
+  NUSHT_CUDA(cudaMemsetAsync(b.OZT, 0, std::max<int64_t>(16, ta), s));
+  NUSHT_CUDA(cudaMemsetAsync(b.Gp, 0, std::max<int64_t>(1, gsz) * sizeof(float4), s));
+  // exponents of the recurrence values per order, then the tables
+  unsigned long long* amax = nullptr;
+  NUSHT_TRY(dev_alloc((void**)&amax, (size_t)(L + 1) * 8, nullptr));
+  int st = NUSHT_OK;
+  do {
+    const BucketArgs a = bucket_args(b);
+    cudaError_t e = cudaMemsetAsync(amax, 0, (size_t)(L + 1) * 8, s);
+    if (e == cudaSuccess && b.nitems > 0) {
+      oz_amax_k<<<(b.nitems + 3) / 4, 128, 0, s>>>(a, b.items, b.nitems, b.leg->leg.ahat, amax);
+      e = cudaGetLastError();
+    }
+    std::vector<unsigned long long> hm(L + 1, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), amax, (size_t)(L + 1) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = cuda_status(e, "split table exponents");
+      break;
+    }
+    std::vector<int> ea(L + 1);
+    for (int m = 0; m <= L; ++m) ea[m] = hm[m] ? (int)(hm[m] >> 52) - 1022 : 0;
+    e = cudaMemcpy(b.eA, ea.data(), (size_t)(L + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b.nitems > 0) {
+      oz_build_k<<<(b.nitems + 3) / 4, 128, 0, s>>>(a, b.items, b.nitems, b.mfirst, b.leg->leg.ahat, b.eA,
+                                                    b.ozs_off, b.ozt_base, b.OZS, b.OZT);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_status(e, "split table build");
+  } while (false);
+  dev_free(amax);
+  NUSHT_TRY(st);
+  b.oz = true;
+  return NUSHT_OK;
+}
+
+OzArgs oz_args(const Bucket& b, bool adj) {
+  OzArgs z;
+  z.L = b.L;
+  z.M = b.M;
+  z.npairs = b.npairs;
+  z.B = b.B;
+  z.ncg = b.ncg;
+  z.memberL = b.memberL;
+  z.items = b.items;
+  z.mfirst = b.mfirst;
+  z.work = adj ? b.oz_wa : b.oz_ws;
+  z.A = adj ? b.OZT : b.OZS;
+  z.aoff = adj ? b.ozt_base : b.ozs_off;
+  z.Bt = adj ? b.OBA : b.OBS;
+  z.boff = adj ? b.oba_off : b.obs_off;
+  z.eA = b.eA;
+  z.eB = adj ? b.eBa : b.eBs;
+  z.gout = b.gout;
+  z.gh = b.gh;
+  z.aout = reinterpret_cast<double2* const*>(b.out_ptrs);
+  z.pole_norm = b.leg->leg.pole_norm;
+  return z;
+}
+
 
 int launch_adj(const Bucket& b, cudaStream_t s) {
   const BucketArgs a = bucket_args(b);
@@ -1556,6 +2495,8 @@ int set_adj_smem() {
   NUSHT_CUDA(cudaFuncSetAttribute(bucket_adj_tab_k, cudaFuncAttributeMaxDynamicSharedMemorySize, smt));
   NUSHT_CUDA(cudaFuncSetAttribute(bucket_tc_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, T6_SMEM));
   NUSHT_CUDA(cudaFuncSetAttribute(bucket_tc_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, T6_SMEM));
+  NUSHT_CUDA(cudaFuncSetAttribute(oz_tc_k<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  NUSHT_CUDA(cudaFuncSetAttribute(oz_tc_k<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
   return NUSHT_OK;
 }
 
@@ -1680,6 +2621,61 @@ int enqueue_adjoint(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
     dim3 g((b.L + 1 + 3) / 4, b.L + 1);
     bucket_final_k<<<g, 256, 0, s>>>(b.L, b.M, b.B, b.memberL, b.cacc, b.leg->leg.ahat, b.leg->leg.pole_norm,
                                      b.Ghat, b.out_ptrs);
+    NUSHT_CUDA(cudaGetLastError());
+  }
+  return NUSHT_OK;
+}
+
+// FP64 batched synthesis: per bucket the split coefficients, the tensor-core
+// contraction into the members' ring sums and their poles; then every
+// member's theta FFT (float pairs in and out), deconvolution, fine-grid FFT
+// and interpolation on the forked streams.
+int enqueue_synth_oz(nusht_batch_t p, void* const* d_map, cudaStream_t s) {
+  for (auto& b : p->buckets) {
+    oz_bs_k<<<b.L + 1, 256, 0, s>>>(b.L, b.B, b.ncg, b.memberL, reinterpret_cast<const double2* const*>(b.alm_ptrs),
+                                    b.mfirst, b.obs_off, b.eBs, b.OBS);
+    if (b.noz_s > 0)
+      oz_tc_k<false><<<b.noz_s, OZ_THREADS, OZ_SMEM, s>>>(oz_args(b, false), b.noz_s, p->status, p->test_giveup);
+    oz_poles_k<<<b.B, 256, 0, s>>>(b.M, b.memberL, reinterpret_cast<const double2* const*>(b.alm_ptrs),
+                                   b.leg->leg.pole_norm, b.gout);
+    NUSHT_CUDA(cudaGetLastError());
+  }
+  NUSHT_TRY(fork(p, s));
+  for (int i = 0; i < p->nbatch; ++i) {
+    nusht_plan_t q = p->sub[i];
+    cudaStream_t ms = p->side[i % nusht_batch_s::NSIDE];
+    const Bucket& b = p->buckets[p->bucket_of[i]];
+    NUSHT_TRY(dfft_theta_pairs(q, b.gout_h[p->slot_of[i]], q->Ghat, -1, ms));
+    NUSHT_TRY(deconv_pad(q, ms));
+    NUSHT_TRY(fine_fft_c2r(q, ms));
+    NUSHT_TRY(interp(q, d_map[i], ms));
+  }
+  NUSHT_TRY(join(p, s));
+  return NUSHT_OK;
+}
+
+// FP64 batched adjoint: every member's spreading, fine-grid FFT, truncation
+// and inverse theta FFT (float pairs) on the forked streams; then per bucket
+// the folded split spectrum and the tensor-core contraction into the
+// members' coefficients.
+int enqueue_adjoint_oz(nusht_batch_t p, const void* const* d_map, cudaStream_t s) {
+  NUSHT_TRY(fork(p, s));
+  for (int i = 0; i < p->nbatch; ++i) {
+    nusht_plan_t q = p->sub[i];
+    cudaStream_t ms = p->side[i % nusht_batch_s::NSIDE];
+    NUSHT_TRY(spread(q, d_map[i], ms));
+    NUSHT_TRY(fine_fft_r2c(q, ms));
+    NUSHT_TRY(deconv_trunc(q, ms));
+    NUSHT_TRY(dfft_theta_pairs(q, q->Ghat, q->Ghat, 1, ms));
+  }
+  NUSHT_TRY(join(p, s));
+  for (auto& b : p->buckets) {
+    oz_fold_k<<<b.L + 1, 256, 0, s>>>(b.L, b.M, b.npairs, b.B, b.ncg, b.memberL, b.gh, b.items, b.mfirst, b.oba_off,
+                                      b.eBa, b.OBA);
+    oz_zero_k<<<dim3(b.L + 1, b.B), 128, 0, s>>>(b.M, b.memberL, b.mfirst, b.gh, b.leg->leg.pole_norm,
+                                                 reinterpret_cast<double2* const*>(b.out_ptrs));
+    if (b.noz_a > 0)
+      oz_tc_k<true><<<b.noz_a, OZ_THREADS, OZ_SMEM, s>>>(oz_args(b, true), b.noz_a, p->status, p->test_giveup);
     NUSHT_CUDA(cudaGetLastError());
   }
   return NUSHT_OK;
@@ -1838,8 +2834,8 @@ int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64
   *out = nullptr;
   if (nbatch < 1 || nbatch > 4096) return set_error(NUSHT_EINVAL, "nbatch must be in [1, 4096]");
   if (!lmax || !npts || !d_pts) return set_error(NUSHT_EINVAL, "null array argument");
-  if (precision != NUSHT_MIXED)
-    return set_error(NUSHT_EUNSUPPORTED, "batched transforms run in NUSHT_MIXED precision");
+  if (precision != NUSHT_MIXED && precision != NUSHT_FP64)
+    return set_error(NUSHT_EUNSUPPORTED, "batched transforms run in NUSHT_MIXED or NUSHT_FP64 precision");
   for (int i = 0; i < nbatch; ++i) {
     nusht_sizes z;
     NUSHT_TRY(choose_sizes(lmax[i], lmax[i], eps, precision, opts, &z));
@@ -1894,7 +2890,7 @@ int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64
         p->bucket_of[b.members[k]] = (int)g;
         p->slot_of[b.members[k]] = k;
       }
-      st = bucket_build(p, b, s);
+      st = (precision == NUSHT_FP64) ? bucket_build_oz(p, b, s) : bucket_build(p, b, s);
     }
     if (st != NUSHT_OK) break;
     p->sub.assign(nbatch, nullptr);
@@ -1908,11 +2904,28 @@ int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64
       role.legendre = false;
       role.nufft = true;
       role.M_override = b.M;
-      role.ghat_external = b.Ghat + (size_t)p->slot_of[i] * (b.L + 1) * b.M;
+      if (precision == NUSHT_FP64)
+        role.theta = true;  // own theta FFT and theta spectrum, float pairs
+      else
+        role.ghat_external = b.Ghat + (size_t)p->slot_of[i] * (b.L + 1) * b.M;
       st = plan_create(&p->sub[i], p->L[i], p->L[i], p->npts[i], d_pts[i], eps, precision, &sub_opts, s, role);
       if (st == NUSHT_OK) p->bytes += p->sub[i]->bytes;
+      if (st == NUSHT_OK && precision == NUSHT_FP64 && !(p->sub[i]->dfft_theta && p->sub[i]->dfft_fine))
+        st = set_error(NUSHT_EUNSUPPORTED, "FP64 batched plans need the double-float FFT kernels (fft_kernels >= 0)");
     }
     if (st != NUSHT_OK) break;
+    if (precision == NUSHT_FP64) {
+      for (auto& b : p->buckets) {
+        std::vector<const void*> gh(BK_MAXB, nullptr);
+        for (int k = 0; k < b.B; ++k) gh[k] = p->sub[b.members[k]]->Ghat;
+        cudaError_t e = cudaMemcpy(b.gh, gh.data(), BK_MAXB * sizeof(void*), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+          st = cuda_status(e, "member table upload");
+          break;
+        }
+      }
+      if (st != NUSHT_OK) break;
+    }
     if ((st = build_fused(p)) != NUSHT_OK) break;
     {
       cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
@@ -1953,7 +2966,11 @@ static int run_many(nusht_batch_t p, const void* const* in, void* const* out, nu
     NUSHT_TRY(set_tables(p, in, out, synth));
     cudaGraph_t g = nullptr;
     NUSHT_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
-    int st = synth ? enqueue_synth(p, out, p->cap) : enqueue_adjoint(p, in, p->cap);
+    int st;
+    if (p->precision == NUSHT_FP64)
+      st = synth ? enqueue_synth_oz(p, out, p->cap) : enqueue_adjoint_oz(p, in, p->cap);
+    else
+      st = synth ? enqueue_synth(p, out, p->cap) : enqueue_adjoint(p, in, p->cap);
     cudaError_t e = cudaStreamEndCapture(p->cap, &g);
     if (st != NUSHT_OK) {
       if (g) cudaGraphDestroy(g);
@@ -2010,7 +3027,7 @@ int nusht_batch_schedule(nusht_batch_t p, int bucket, int* chunks_synth, int* ch
 int nusht_batch_path(nusht_batch_t p, int bucket) {
   if (!p || bucket < 0 || bucket >= (int)p->buckets.size()) return -1;
   const nusht::Bucket& b = p->buckets[bucket];
-  return b.tc ? 2 : (b.table ? 1 : 0);
+  return b.oz ? 3 : (b.tc ? 2 : (b.table ? 1 : 0));
 }
 
 int nusht_batch_info(nusht_batch_t p, int* nbuckets, int* bucket_of, int* bucket_lmax, int64_t* bytes_device) {

@@ -935,6 +935,8 @@ int optin_all(int b) {
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<-1, false, true, NT>, a, b));
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1, false, false, NT>, a, b));
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1, true, false, NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<-1, true, true, NT>, a, b));
+  NUSHT_CUDA(cudaFuncSetAttribute(dfft_lines_k<1, true, true, NT>, a, b));
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_synth_k<false, NT>, a, b));
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_cols_synth_k<true, NT>, a, b));
   NUSHT_CUDA(cudaFuncSetAttribute(dfft_rows_c2r_k<NT>, a, b));
@@ -1064,6 +1066,26 @@ int dfft_theta_exec(nusht_plan_t p, const void* src, void* dst, int sign, cudaSt
     else
       go(dfft_lines_k<1, false, false, DFFT_T_WIDE>, dfft_lines_k<1, false, false, DFFT_T_ODD>);
   }
+  NUSHT_CUDA(cudaGetLastError());
+  return NUSHT_OK;
+}
+
+int dfft_theta_pairs(nusht_plan_t p, const void* src, void* dst, int sign, cudaStream_t s) {
+  if (!p->dfft_theta || !p->dfft_fine) return set_error(NUSHT_EUNSUPPORTED, "theta DFT on pairs needs both kernels");
+  const nusht_sizes& z = p->sz;
+  const size_t sm = (size_t)dline_words(z.M) * sizeof(float4);
+  const int nl = z.mmax + 1;
+  const DfftLen& f = p->dft_theta;
+  auto go = [&](auto kw, auto ko) {
+    if (wide(f))
+      kw<<<nl, DFFT_T_WIDE, sm, s>>>(src, dst, z.M, nl, f);
+    else
+      ko<<<nl, DFFT_T_ODD, sm, s>>>(src, dst, z.M, nl, f);
+  };
+  if (sign < 0)
+    go(dfft_lines_k<-1, true, true, DFFT_T_WIDE>, dfft_lines_k<-1, true, true, DFFT_T_ODD>);
+  else
+    go(dfft_lines_k<1, true, true, DFFT_T_WIDE>, dfft_lines_k<1, true, true, DFFT_T_ODD>);
   NUSHT_CUDA(cudaGetLastError());
   return NUSHT_OK;
 }

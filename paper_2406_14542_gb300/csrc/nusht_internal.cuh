@@ -265,6 +265,7 @@ struct nusht_plan_s {
 
   // role inside a batch (see nusht::PlanRole); a standalone plan has all parts
   bool has_legendre = true, has_nufft = true, ghat_owned = true;
+  bool theta_member = false;  // PlanRole::theta
 
   // profiling
   nusht::StageEvents ev_synth, ev_adj;
@@ -283,6 +284,7 @@ struct PlanRole {
   bool nufft = true;
   void* ghat_external = nullptr;
   int bin = 0;                // spreading bin edge chosen by the caller (0: opts.tune decides)
+  bool theta = false;         // a NUFFT-only member that runs its own theta FFT on float pairs
 };
 int plan_create(nusht_plan_t* out, int lmax, int mmax, int64_t npts, const double* d_pts, double eps, int precision,
                 const nusht_opts* opts, cudaStream_t s, const PlanRole& role);
@@ -345,6 +347,9 @@ bool dfft_fits(const nusht_sizes& z, bool theta, bool fine);
 int dfft_setup(nusht_plan_t p, bool theta, bool fine, const double* d1, const double* d2);
 void dfft_free(nusht_plan_t p);
 int dfft_theta_exec(nusht_plan_t p, const void* src, void* dst, int sign, cudaStream_t s);
+// the theta DFT with float-pair input and output in both directions (members
+// of FP64 batched plans; needs dfft_theta and dfft_fine)
+int dfft_theta_pairs(nusht_plan_t p, const void* src, void* dst, int sign, cudaStream_t s);
 int dfft_cols_synth(nusht_plan_t p, cudaStream_t s);
 int dfft_rows_c2r(nusht_plan_t p, cudaStream_t s);
 int dfft_rows_r2c(nusht_plan_t p, cudaStream_t s);

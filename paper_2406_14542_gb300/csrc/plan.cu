@@ -241,10 +241,11 @@ static int make_ffts(nusht_plan_t p, const double* d1, const double* d2) {
   size_t ws = 0;
   // FP64: double-float kernels for every length that fits in shared memory
   const bool own = dbl && p->opts.fft_kernels >= 0;
-  const bool own_theta = own && p->has_legendre && dfft_fits(z, true, false);
+  const bool want_theta = p->has_legendre || p->theta_member;
+  const bool own_theta = own && want_theta && dfft_fits(z, true, false);
   const bool own_fine = own && p->has_nufft && dfft_fits(z, false, true);
   if (own_theta || own_fine) NUSHT_TRY(dfft_setup(p, own_theta, own_fine, d1, d2));
-  if (p->has_legendre && !own_theta) {
+  if (want_theta && !own_theta) {
     NUSHT_CUFFT(cufftCreate(&p->fft_theta));
     p->have_theta = true;
     NUSHT_CUFFT(cufftMakePlanMany(p->fft_theta, 1, &M, nullptr, 1, M, nullptr, 1, M, dbl ? CUFFT_Z2Z : CUFFT_C2C,
@@ -465,6 +466,7 @@ int nusht::plan_create(nusht_plan_t* out, int lmax, int mmax, int64_t npts, cons
   p->nalm = (int64_t)(mmax + 1) * (lmax + 1) - (int64_t)mmax * (mmax + 1) / 2;
   p->has_legendre = role.legendre;
   p->has_nufft = role.nufft;
+  p->theta_member = role.theta;
   cudaStream_t s = stream;
   int st = plan_body(p, npts, d_pts, s, role);
   g_fail_after = -1;
