@@ -250,6 +250,12 @@ def main():
     ap.add_argument("--sweep-workload", default="gl1023", choices=["gl1023", "gl2047", "gl4095"],
                     help="workload of --sweep")
     ap.add_argument("--only-batch", action="store_true", help="run only the 64-transform batched measurement")
+    ap.add_argument("--batch-precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of --only-batch")
+    ap.add_argument("--no-batch-fp64", action="store_true",
+                    help="skip the 64-transform batched measurement in FP64 (eps 1e-10)")
+    ap.add_argument("--no-sequential", action="store_true",
+                    help="with --only-batch: skip the one-by-one comparison")
     ap.add_argument("--batch-n", type=int, default=64, help="transforms in the batched workload")
     ap.add_argument("--batch-lmax", type=int, default=2047, help="largest lmax of the batched workload")
     ap.add_argument("--workload", default=WORKLOAD, choices=["gl1023", "gl2047", "gl4095"],
@@ -270,9 +276,10 @@ def main():
             print(json.dumps({"sweep": run_sweep(torch, nu, args)}), flush=True)
         return
     if args.only_batch:
-        b = run_batch64(torch, nu, args, dist, rank, sequential=False)
+        b = run_batch64(torch, nu, args, dist, rank, sequential=not args.no_sequential,
+                        precision=args.batch_precision)
         if rank == 0:
-            print(json.dumps({"batch64": b}), flush=True)
+            print(json.dumps({"batch64" if args.batch_precision == "mixed" else "batch64_fp64": b}), flush=True)
         return
     L, a, pts = W.workload(args.workload)
     npts = pts.shape[0]
@@ -405,9 +412,11 @@ def main():
     spin = None if args.no_spin else run_spin(torch, nu, args, dist, rank, L, pts)
     autograd = None if args.no_autograd or args.workload != WORKLOAD else run_autograd(torch, nu, args, dist)
 
-    batch = None
+    batch = batch_fp64 = None
     if not args.no_batch and args.workload == WORKLOAD:
         batch = run_batch64(torch, nu, args, dist, rank)
+        if not args.no_batch_fp64:
+            batch_fp64 = run_batch64(torch, nu, args, dist, rank, precision="fp64")
 
     if rank != 0:
         if dist is not None:
@@ -520,6 +529,8 @@ def main():
         line["spin2"] = spin
     if batch is not None:
         line["batch64"] = batch
+    if batch_fp64 is not None:
+        line["batch64_fp64"] = batch_fp64
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -706,22 +717,28 @@ def run_sweep(torch, nu, args):
             "oracle_sample": int(sel.size), "runs": out}
 
 
-def run_batch64(torch, nu, args, dist, rank, sequential=True):
+def run_batch64(torch, nu, args, dist, rank, sequential=True, precision="mixed"):
     """64 independent transforms, lmax_b ~ U{256..2047}, N_b = 2 lmax_b^2 uniform
-    points, complex64 a_lm, eps 1e-5: one batched plan (shared-ring buckets,
-    graph replay) against the same transforms run one by one through
-    standalone mixed-precision plans."""
+    points: one batched plan (shared-ring buckets, graph replay) against the
+    same transforms run one by one through standalone plans of the same
+    precision.  "mixed": complex64 a_lm, float32 maps, eps 1e-5 (TF32-split
+    tensor-core contraction); "fp64": the same coefficients as complex128,
+    float64 maps, eps 1e-10 (bf16-sliced tensor-core contraction)."""
+    fp64 = precision == "fp64"
+    eps = 1e-10 if fp64 else 1e-5
+    cdt = torch.complex128 if fp64 else torch.complex64
+    rdt = torch.float64 if fp64 else torch.float32
     members = W.batch64(nbatch=args.batch_n, lmax=args.batch_lmax)
     ls = [m[0] for m in members]
     dpts = [torch.from_numpy(m[2]).cuda() for m in members]
-    alms = [torch.from_numpy(m[1]).cuda() for m in members]
-    ys = [torch.randn(d.shape[0], dtype=torch.float32, device="cuda") for d in dpts]
+    alms = [torch.from_numpy(m[1]).to(cdt).cuda() for m in members]
+    ys = [torch.randn(d.shape[0], dtype=rdt, device="cuda") for d in dpts]
     t0 = time.perf_counter()
-    bp = nu.BatchPlan(ls, dpts, eps=1e-5)
+    bp = nu.BatchPlan(ls, dpts, eps=eps, precision=precision)
     torch.cuda.synchronize()
     t_plan = time.perf_counter() - t0
-    fo = [torch.empty(d.shape[0], dtype=torch.float32, device="cuda") for d in dpts]
-    co = [torch.empty(nu.nalm(l), dtype=torch.complex64, device="cuda") for l in ls]
+    fo = [torch.empty(d.shape[0], dtype=rdt, device="cuda") for d in dpts]
+    co = [torch.empty(nu.nalm(l), dtype=cdt, device="cuda") for l in ls]
 
     def step():
         bp.synth(alms, fo)
@@ -747,7 +764,7 @@ def run_batch64(torch, nu, args, dist, rank, sequential=True):
     # the same transforms one by one (standalone plans, same eps / precision)
     seq = 0.0
     for i in range(len(ls) if sequential else 0):
-        pl = nu.Plan(ls[i], dpts[i], eps=1e-5, precision="mixed")
+        pl = nu.Plan(ls[i], dpts[i], eps=eps, precision=precision)
         f = torch.empty_like(fo[i])
         c = torch.empty_like(co[i])
 
@@ -759,8 +776,10 @@ def run_batch64(torch, nu, args, dist, rank, sequential=True):
         pl.close()
     torch.cuda.empty_cache()
     return {"workload": "%d transforms, lmax ~ U{256..%d} (seed 0), N_b = 2 lmax_b^2 uniform points "
-                        "(%d total), complex64, eps 1e-5" % (args.batch_n, args.batch_lmax,
-                                                             sum(int(d.shape[0]) for d in dpts)),
+                        "(%d total), %s, eps %g" % (args.batch_n, args.batch_lmax,
+                                                    sum(int(d.shape[0]) for d in dpts),
+                                                    "complex128" if fp64 else "complex64", eps),
+            "precision": precision,
             "ms_per_step": ms, "sequential_ms_per_step": seq if sequential else None,
             "speedup_vs_sequential": seq / ms if sequential else None,
             "buckets": info["nbuckets"], "bucket_lmax": info["bucket_lmax"], "plan_s": t_plan,
