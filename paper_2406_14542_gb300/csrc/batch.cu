@@ -1,5 +1,7 @@
 // batch.cu -- many transforms of uneven lmax and point counts in one plan
-// (mixed precision: FP64 recurrence, FP32 contraction / FFT / NUFFT).
+// (mixed precision: FP64 recurrence, FP32 contraction / FFT / NUFFT; FP64:
+// the contraction split into bf16 slices on the tensor cores, the members'
+// FFTs and NUFFT in double-float, see the split-contraction section below).
 //
 // Members are grouped into buckets of up to 64 transforms that share one
 // Clenshaw-Curtis ring set (the one of the bucket's largest lmax: more rings
