@@ -1089,18 +1089,18 @@ __global__ void bucket_final_k(int L, int M, int B, const int* __restrict__ memb
 // FP64 batched plans: the split ("Ozaki") contraction on the tensor cores.
 //
 // The products per order m are those above, but every operand is an exact
-// sum of five bf16 slices under one power of two:
-//   x = 2^(e - 39) F,  F = round(x 2^(39 - e)) = sum_{i<5} d_i 256^(4 - i),
+// sum of six bf16 slices under one power of two:
+//   x = 2^(e - 47) F,  F = round(x 2^(47 - e)) = sum_{i<6} d_i 256^(5 - i),
 // with |x| < 2^e and d_i the balanced base-256 digits of F (|d_i| <= 129), so
-// the representation error is at most 2^(e - 40).  Slice i is stored as
+// the representation error is at most 2^(e - 48).  Slice i is stored as
 // d_i 2^(-8 i) (at most 8 significant bits: exact in bf16), and then every
 // slice product d_i d_j 2^(-8 (i + j)) is exact in the tensor core's FP32
 // product.  The recurrence values Pbar_l^m(theta) are split at plan time
 // with one exponent per order (their largest magnitude over the bucket's
 // rings and degrees); the coefficients (synthesis) and the folded spectrum
 // (adjoint) are split per call with one exponent per (order, member column).
-// The 15 slice products with i + j <= 4 go to four accumulators per parity,
-// one per level i + j (the last one takes levels 3 and 4):
+// Synthesis: the 21 slice products with i + j <= 5 go to four accumulators
+// per parity, one per level i + j (the last one takes levels 3 to 5):
 //   D0 = sum d_0 d_0            integers below 2^14: exact while the sum stays
 //                               below 2^24 (1024 full-magnitude terms);
 //   D1 = sum over i + j = 1     multiples of 2^-8 below 2^6: exact while below
@@ -1108,38 +1108,58 @@ __global__ void bucket_final_k(int L, int M, int B, const int* __restrict__ memb
 //                               near 2^11);
 //   D2 = sum over i + j = 2     multiples of 2^-16 below 2^-2: exact while
 //                               below 2^8;
-//   D3 = sum over i + j = 3, 4  rounded FP32 sums, ~2^-8 of D2.
+//   D3 = sum over 3 <= i+j <= 5 rounded FP32 sums, ~2^-8 of D2.
 // The tensor core's FP32 accumulation aligns with truncation, so a rounded
 // accumulator's error grows with the number of MMAs folded into it; with one
 // accumulator for every level from 2 on, that error reached 2^-33 of the
 // result at 100 degrees.  With the exact levels apart, the dropped products
-// (i + j >= 5), the representation errors and D3's truncation stay near
-// 2^-38 of the product of the two operands' scales: D0 + D1 + D2 + D3 times
-// 2^(eA + eB - 14) has the accuracy class of the FP64 recurrence path.
+// (i + j >= 6), the representation errors and D3's truncation stay near
+// 2^-46 of the product of the two operands' scales.  Six slices rather than
+// five: the exponent is shared by a whole order, and at low orders the
+// largest |Pbar| (near the poles) is 16 times the rms, so five slices (40
+// bits) left the bulk of the values with ~36 bits and orders 0 and 1 of the
+// adjoint at 1-3e-10 at lmax 2043.  D0 + D1 + D2 + D3 times 2^(eA + eB - 14)
+// has the accuracy class of the FP64 recurrence path.
+// The rounded level still matters when the leading digits are small: its
+// magnitude comes from the full-range lower digits (|d| ~ 128), and its
+// truncation bias grows with the MMAs folded into it.  With one exponent per
+// order, the rings away from a low order's polar peak have leading digits
+// ~16 times below full range, and the adjoint (K = every kept ring pair,
+// 960 MMAs into the rounded level) lost 6e-11 to 1.6e-10 at orders 0-10.  So
+// the synthesis table takes one exponent per kept item (128 ring pairs: K
+// runs over degrees inside one item), and an adjoint block takes a single
+// parity: its six levels then each get an accumulator of their own (6 x 64
+// TMEM columns), all exact (level s: multiples of 2^-8s below 2^(14 - 8s),
+// random-sign sums far from 2^(24 - 8s)), and the split adds ~1e-12 against
+// standalone FP64 plans at every order.
 //
 // Block shapes: M = 128 rows, N = 64 columns (32 members, re / im), K = 16.
 //   synthesis: rows = the 128 ring pairs of a kept work item, K = 16 degrees
 //              of one parity (a chunk = 32 degrees);
 //   adjoint:   rows = 128 degrees of one parity (256 degrees per block),
 //              K = 16 ring pairs (8 chunks per kept work item).
-// A chunk is 10 A tiles (2 parities x 5 slices, 128 x 16 bf16 = 4 KB each)
-// and 10 B tiles (64 x 16 bf16 = 2 KB each) in the no-swizzle K-major
+// A chunk is 12 A tiles (2 parities x 6 slices, 128 x 16 bf16 = 4 KB each)
+// and 12 B tiles (64 x 16 bf16 = 2 KB each) in the no-swizzle K-major
 // core-matrix layout of the TF32 kernel above (with 16-bit elements a core
 // matrix is 8 rows x 8 values), moved by two cp.async.bulk copies into a
-// ring of three 60 KB buffers; one thread issues the 30 MMAs of a chunk.
-// The eight accumulators (E, O) x (D0 .. D3) take all 512 TMEM columns.  The
+// ring of three 72 KB buffers; one thread issues the 42 MMAs of a chunk.
+// The eight accumulators (E, O) x (D0 .. D3) take all 512 TMEM columns.  An
+// adjoint block moves half chunks (one parity, 36 KB) through six buffers.  The
 // synthesis epilogue forms north = E + O and south = E - O as float pairs
 // (the theta FFT of FP64 members reads float pairs); the adjoint's builds
 // each coefficient's double from a 64-bit fixed-point sum with integer
 // operations, so the FP64 pipe (1/64 of the FP32 rate on GB300) stays idle.
 // ---------------------------------------------------------------------------
-constexpr int OZ_NS = 5;                        // slices per operand
+constexpr int OZ_NS = 6;                        // slices per operand
+constexpr int OZ_FB = 8 * (OZ_NS - 1) + 7;      // F = round(x 2^(OZ_FB - e)), |F| < 2^47
 constexpr int OZ_ATILE = 128 * 16 * 2;          // 128 rows x 16 bf16
 constexpr int OZ_BTILE = 64 * 16 * 2;           // 64 rows x 16 bf16
-constexpr int OZ_A = 2 * OZ_NS * OZ_ATILE;      // A half of a chunk (40 KB)
-constexpr int OZ_B = 2 * OZ_NS * OZ_BTILE;      // B half of a chunk (20 KB)
-constexpr int OZ_CHUNK = OZ_A + OZ_B;
+constexpr int OZ_A = 2 * OZ_NS * OZ_ATILE;      // A half of a chunk (48 KB)
+constexpr int OZ_B = 2 * OZ_NS * OZ_BTILE;      // B half of a chunk (24 KB)
+constexpr int OZ_CHUNK = OZ_A + OZ_B;           // synthesis chunk: both parities
 constexpr int OZ_NBUF = 3;
+constexpr int OZ_CHUNK_P = OZ_CHUNK / 2;        // adjoint chunk: one parity
+constexpr int OZ_NBUF_P = 6;
 constexpr int OZ_THREADS = 32 * 6;              // producer, MMA issuer, 4 epilogue warps
 constexpr int OZ_SMEM = OZ_NBUF * OZ_CHUNK + 256;
 constexpr int OZ_COLS = 128;                    // columns of eB per order (64 members, re / im)
@@ -1148,13 +1168,14 @@ constexpr int OZ_LV = 4;                        // accumulator levels per parity
 // 10-12 = 1), both K-major, N = 64 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24)
 constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 static_assert(OZ_SMEM <= 227 * 1024, "three chunk buffers fit in shared memory");
+static_assert(OZ_NBUF_P * OZ_CHUNK_P == OZ_NBUF * OZ_CHUNK, "both directions use the same buffer space");
 
 // byte offset of element (row, k) in a K-major tile of 16 bf16 per row
 __device__ __forceinline__ int oz_off(int row, int k) {
   return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// balanced base-256 digits: F = sum_i d[i] 256^(4 - i), d[1..4] in [-128, 127]
+// balanced base-256 digits: F = sum_i d[i] 256^(OZ_NS - 1 - i), d[1..] in [-128, 127]
 __device__ __forceinline__ void oz_digits(long long F, int (&d)[OZ_NS]) {
 #pragma unroll
   for (int i = OZ_NS - 1; i > 0; --i) {
@@ -1248,11 +1269,13 @@ __device__ __forceinline__ unsigned long long oz_warp_max(unsigned long long v) 
 }
 
 // Plan time, pass 1: the largest |Pbar| of every order over the bucket's
-// rings and degrees, as the bits of a non-negative double (which order like
-// unsigned integers).  One warp per kept work item (order m, 128 ring pairs).
+// rings and degrees, and of every kept work item (order m, 128 ring pairs),
+// as the bits of a non-negative double (which order like unsigned integers).
+// One warp per item.
 __global__ void __launch_bounds__(128) oz_amax_k(BucketArgs a, const int* __restrict__ items, int nitems,
                                                  const double* __restrict__ ahat,
-                                                 unsigned long long* __restrict__ amax) {
+                                                 unsigned long long* __restrict__ amax,
+                                                 unsigned long long* __restrict__ amax_item) {
   const int lane = threadIdx.x & 31;
   const int it = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (it >= nitems) return;
@@ -1279,18 +1302,24 @@ __global__ void __launch_bounds__(128) oz_amax_k(BucketArgs a, const int* __rest
     }
   }
   mx = oz_warp_max(mx);
-  if (lane == 0 && mx) atomicMax(amax + m, mx);
+  if (lane == 0) {
+    amax_item[it] = mx;
+    if (mx) atomicMax(amax + m, mx);
+  }
 }
 
 // Plan time, pass 2: the slices of Pbar = q Ahat into the synthesis table
-// (per item: [chunk of 32 degrees][parity][slice] tiles, rows = ring pairs,
-// k = degree / 2 within the chunk) and the adjoint table (per order:
+// (per item, under the item's exponent eAi: [chunk of 32 degrees][parity]
+// [slice] tiles, rows = ring pairs, k = degree / 2 within the chunk) and the
+// adjoint table (per order, under the order's exponent eA, since an adjoint
+// block sums over all the order's items:
 // [block of 256 degrees][item, 16-pair group][parity][slice] tiles, rows =
 // degree / 2 within the block, k = ring pair within the group).  The tables
 // are zero-filled beforehand; zero values are not written.
 __global__ void __launch_bounds__(128) oz_build_k(BucketArgs a, const int* __restrict__ items, int nitems,
                                                   const int* __restrict__ mfirst, const double* __restrict__ ahat,
-                                                  const int* __restrict__ eA, const int64_t* __restrict__ soff,
+                                                  const int* __restrict__ eA, const int* __restrict__ eAi,
+                                                  const int64_t* __restrict__ soff,
                                                   const int64_t* __restrict__ tbase, unsigned char* __restrict__ AS,
                                                   unsigned char* __restrict__ AT) {
   const int lane = threadIdx.x & 31;
@@ -1301,7 +1330,7 @@ __global__ void __launch_bounds__(128) oz_build_k(BucketArgs a, const int* __res
   const int L = a.lmax;
   const int mb = idx_lm(L, 0, m);
   const int j = it - mfirst[m], nim = mfirst[m + 1] - mfirst[m];
-  const int sh = 39 - eA[m];
+  const int sh = OZ_FB - eA[m], shi = OZ_FB - eAi[it];
   unsigned char* sbase = AS + soff[it];
   unsigned char* tb = AT + tbase[m];
   Chain ch[LEG_K];
@@ -1321,18 +1350,23 @@ __global__ void __launch_bounds__(128) oz_build_k(BucketArgs a, const int* __res
     for (int k = 0; k < LEG_K; ++k) {
       if (step) chain_step(ch[k], c, rs);
       if (!(ch[k].valid && ch[k].E == 0)) continue;
-      const long long F = oz_fix_d(ch[k].q1 * ah, sh);
-      if (F == 0) continue;
-      int d[OZ_NS];
-      oz_digits(F, d);
+      const double pv = ch[k].q1 * ah;
       const int row = k * 32 + lane;  // ring pair within the item
-      unsigned char* qs = ps + oz_off(row, ks);
-      unsigned char* qt = pt + (size_t)(8 * j + (row >> 4)) * OZ_A + oz_off(arow, row & 15);
+      const long long Fs = oz_fix_d(pv, shi), Ft = oz_fix_d(pv, sh);
+      int d[OZ_NS];
+      if (Fs != 0) {
+        oz_digits(Fs, d);
+        unsigned char* qs = ps + oz_off(row, ks);
 #pragma unroll
-      for (int i = 0; i < OZ_NS; ++i) {
-        const unsigned short bv = (unsigned short)oz_bf16(d[i], i);
-        *reinterpret_cast<unsigned short*>(qs + i * OZ_ATILE) = bv;
-        *reinterpret_cast<unsigned short*>(qt + i * OZ_ATILE) = bv;
+        for (int i = 0; i < OZ_NS; ++i)
+          *reinterpret_cast<unsigned short*>(qs + i * OZ_ATILE) = (unsigned short)oz_bf16(d[i], i);
+      }
+      if (Ft != 0) {
+        oz_digits(Ft, d);
+        unsigned char* qt = pt + (size_t)(8 * j + (row >> 4)) * OZ_A + oz_off(arow, row & 15);
+#pragma unroll
+        for (int i = 0; i < OZ_NS; ++i)
+          *reinterpret_cast<unsigned short*>(qt + i * OZ_ATILE) = (unsigned short)oz_bf16(d[i], i);
       }
     }
   }
@@ -1408,7 +1442,7 @@ __global__ void __launch_bounds__(256) oz_bs_k(int L, int B, int ncg, const int*
     __syncthreads();
     for (int cg = 0; cg < ncg; ++cg) {
       const int col = cg * 64 + row, slot = col >> 1;
-      const int sh = 39 - se[col];
+      const int sh = OZ_FB - se[col];
       uint32_t w[OZ_NS][4];
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) {
@@ -1492,7 +1526,7 @@ __global__ void __launch_bounds__(256) oz_fold_k(int L, int M, int npairs, int B
       long long er = 0, ei = 0, orr = 0, oi = 0;
       const int Ls = slot < B ? memberL[slot] : -1;
       if (m <= Ls && jn <= npairs) {
-        const int kr = 39 - se[2 * slot], ki = 39 - se[2 * slot + 1];
+        const int kr = OZ_FB - se[2 * slot], ki = OZ_FB - se[2 * slot + 1];
         const float4* rw = gh[slot] + (size_t)m * M;
         const int js = M / 2 - jn;
         const float4 g0 = rw[jn], g1 = rw[M - jn];
@@ -1608,7 +1642,8 @@ struct OzArgs {
   const int64_t* aoff;       // synthesis: per item; adjoint: per order
   const unsigned char* Bt;   // split coefficients / folded spectrum
   const int64_t* boff;       // per order
-  const int* eA;             // per order
+  const int* eA;             // adjoint: per order
+  const int* eAi;            // synthesis: per kept item
   const int* eB;             // [order][128 columns]
   float4* const* gout;       // synthesis: members' ring sums (float pairs)
   const float4* const* gh;   // adjoint: members' theta spectra (the poles)
@@ -1617,7 +1652,7 @@ struct OzArgs {
 };
 
 struct OzBars {
-  uint64_t full[OZ_NBUF], empty[OZ_NBUF], done;
+  uint64_t full[OZ_NBUF_P], empty[OZ_NBUF_P], done;
   uint32_t tslot;
   int abort;
 };
@@ -1630,8 +1665,12 @@ __device__ __forceinline__ void oz_mma(uint32_t d, uint64_t a, uint64_t b, uint3
 }
 
 // One block: synthesis (ADJ = false) = (kept item, column group), chunks of
-// 32 degrees; adjoint = (order m, 256 degrees, column group), chunks of 16
-// ring pairs over the order's kept items.  Warp 0 lane 0 copies the chunks,
+// 32 degrees (both parities: 12 + 12 tiles, three 72 KB buffers, accumulators
+// (E, O) x (D0 .. D3)); adjoint = (order m, 256 degrees, column group,
+// parity), chunks of 16 ring pairs over the order's kept items (one parity:
+// 6 + 6 tiles, six 36 KB buffers, one accumulator per level i + j = 0 .. 5,
+// every one exact at these magnitudes, so the adjoint carries no truncated
+// accumulation at all).  Warp 0 lane 0 copies the chunks,
 // warp 1 lane 0 issues the MMAs, warps 2-5 (TMEM lanes 32 (warp % 4) ..) run
 // the epilogue once the last MMA has completed.  Every wait is bounded (one
 // second); a block that gives up flags the others, waits (bounded) for its
@@ -1639,12 +1678,16 @@ __device__ __forceinline__ void oz_mma(uint32_t d, uint64_t a, uint64_t b, uint3
 template <bool ADJ>
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_tc_k(OzArgs z, int nblk, int* __restrict__ status,
                                                         int test_giveup) {
+  constexpr int NB = ADJ ? OZ_NBUF_P : OZ_NBUF;
+  constexpr int CH = ADJ ? OZ_CHUNK_P : OZ_CHUNK;
+  constexpr int CA = CH * 2 / 3;  // A part of a chunk
+  constexpr int CB = CH - CA;     // B part
   extern __shared__ __align__(1024) unsigned char oz_smem[];
-  OzBars* bars = reinterpret_cast<OzBars*>(oz_smem + OZ_NBUF * OZ_CHUNK);
+  OzBars* bars = reinterpret_cast<OzBars*>(oz_smem + NB * CH);
   if ((int)blockIdx.x >= nblk || *(volatile int*)status) return;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int2 wk = z.work[blockIdx.x];
-  int m, cg, nchunk, blk = 0, q = 0;
+  int m, cg, nchunk, blk = 0, q = 0, par = 0;
   const unsigned char* Abase;
   if (!ADJ) {
     const int v = z.items[wk.x];
@@ -1656,11 +1699,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_tc_k(OzArgs z, int nblk, int
   } else {
     m = wk.x;
     q = wk.y >> 8;
-    cg = wk.y & 255;
+    par = (wk.y >> 4) & 1;
+    cg = wk.y & 15;
     nchunk = 8 * (z.mfirst[m + 1] - z.mfirst[m]);
-    Abase = z.A + z.aoff[m] + (size_t)q * nchunk * OZ_A;
+    Abase = z.A + z.aoff[m] + (size_t)q * nchunk * OZ_A + (size_t)par * OZ_NS * OZ_ATILE;
   }
-  const unsigned char* Bbase = z.Bt + z.boff[m] + (size_t)cg * OZ_B;
+  const unsigned char* Bbase = z.Bt + z.boff[m] + (size_t)cg * OZ_B + (size_t)par * OZ_NS * OZ_BTILE;
   const size_t bstride = (size_t)z.ncg * OZ_B;
   volatile int* abort = &bars->abort;
   if (warp == 0) {
@@ -1670,7 +1714,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_tc_k(OzArgs z, int nblk, int
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (t == 0) {
-    for (int k = 0; k < OZ_NBUF; ++k) {
+    for (int k = 0; k < NB; ++k) {
       mbar_init(&bars->full[k], 1);
       mbar_init(&bars->empty[k], 1);
     }
@@ -1686,45 +1730,56 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_tc_k(OzArgs z, int nblk, int
     if (lane == 0) {  // producer
       int issued = 0;
       for (int c = 0; c < nchunk && !*abort; ++c) {
-        const int s = c % OZ_NBUF;
-        if (c >= OZ_NBUF && !mbar_wait(smem_u32(&bars->empty[s]), (uint32_t)((c / OZ_NBUF - 1) & 1), abort)) {
+        const int s = c % NB;
+        if (c >= NB && !mbar_wait(smem_u32(&bars->empty[s]), (uint32_t)((c / NB - 1) & 1), abort)) {
           *abort = 1;
           break;
         }
-        unsigned char* dst = oz_smem + s * OZ_CHUNK;
-        mbar_expect_tx(&bars->full[s], OZ_CHUNK);
-        bulk_g2s(dst, Abase + (size_t)c * OZ_A, OZ_A, &bars->full[s]);
-        bulk_g2s(dst + OZ_A, Bbase + (size_t)c * bstride, OZ_B, &bars->full[s]);
+        unsigned char* dst = oz_smem + s * CH;
+        mbar_expect_tx(&bars->full[s], CH);
+        bulk_g2s(dst, Abase + (size_t)c * OZ_A, CA, &bars->full[s]);
+        bulk_g2s(dst + CA, Bbase + (size_t)c * bstride, CB, &bars->full[s]);
         issued = c + 1;
       }
       if (*abort)  // wait (bounded) for the copies still in flight
-        for (int c = issued > OZ_NBUF ? issued - OZ_NBUF : 0; c < issued; ++c)
-          mbar_wait(smem_u32(&bars->full[c % OZ_NBUF]), (uint32_t)((c / OZ_NBUF) & 1));
+        for (int c = issued > NB ? issued - NB : 0; c < issued; ++c)
+          mbar_wait(smem_u32(&bars->full[c % NB]), (uint32_t)((c / NB) & 1));
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       int last = -1;
       for (int c = 0; c < nchunk && !*abort; ++c) {
-        const int s = c % OZ_NBUF;
-        if (!mbar_wait(smem_u32(&bars->full[s]), (uint32_t)((c / OZ_NBUF) & 1), abort,
+        const int s = c % NB;
+        if (!mbar_wait(smem_u32(&bars->full[s]), (uint32_t)((c / NB) & 1), abort,
                        (test_giveup && c == 0) ? 0 : (1 << 30))) {
           *abort = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sb = smem_u32(oz_smem + s * OZ_CHUNK);
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
+        const uint32_t sb = smem_u32(oz_smem + s * CH);
+        if constexpr (ADJ) {
+          // one parity, one accumulator per level: the first product into
+          // level j of chunk 0 is (0, j)
 #pragma unroll
           for (int i = 0; i < OZ_NS; ++i)
 #pragma unroll
-            for (int j = 0; j < OZ_NS - i; ++j) {
-              const int lv = i + j < OZ_LV - 1 ? i + j : OZ_LV - 1;
-              // the first products into D0 .. D3 of chunk 0 are (0,0) .. (0,3)
-              const uint32_t acc = (c > 0 || i > 0 || j > OZ_LV - 1) ? 1u : 0u;
-              oz_mma(tmem + (uint32_t)((p * OZ_LV + lv) * 64), tc_desc(sb + (p * OZ_NS + i) * OZ_ATILE),
-                     tc_desc(sb + OZ_A + (p * OZ_NS + j) * OZ_BTILE), acc);
-            }
+            for (int j = 0; j < OZ_NS - i; ++j)
+              oz_mma(tmem + (uint32_t)((i + j) * 64), tc_desc(sb + i * OZ_ATILE), tc_desc(sb + CA + j * OZ_BTILE),
+                     (c > 0 || i > 0) ? 1u : 0u);
+        } else {
+#pragma unroll
+          for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int i = 0; i < OZ_NS; ++i)
+#pragma unroll
+              for (int j = 0; j < OZ_NS - i; ++j) {
+                const int lv = i + j < OZ_LV - 1 ? i + j : OZ_LV - 1;
+                // the first products into D0 .. D3 of chunk 0 are (0,0) .. (0,3)
+                const uint32_t acc = (c > 0 || i > 0 || j > OZ_LV - 1) ? 1u : 0u;
+                oz_mma(tmem + (uint32_t)((p * OZ_LV + lv) * 64), tc_desc(sb + (p * OZ_NS + i) * OZ_ATILE),
+                       tc_desc(sb + CA + (p * OZ_NS + j) * OZ_BTILE), acc);
+              }
+        }
         tc_commit(&bars->empty[s]);
         last = c;
       }
@@ -1733,7 +1788,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_tc_k(OzArgs z, int nblk, int
       } else if (last >= 0) {
         // MMAs already issued still write tensor memory: wait (bounded) for
         // the commit that covers them before the block frees it
-        mbar_wait(smem_u32(&bars->empty[last % OZ_NBUF]), (uint32_t)((last / OZ_NBUF) & 1));
+        mbar_wait(smem_u32(&bars->empty[last % NB]), (uint32_t)((last / NB) & 1));
       }
     }
   } else {  // epilogue: TMEM lanes 32 (warp % 4) .. + 31 = rows
@@ -1746,13 +1801,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_tc_k(OzArgs z, int nblk, int
       const int r = q4 * 32 + lane;
       const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
       const int M = z.M;
-      const int ea = z.eA[m];
+      const int ea = ADJ ? z.eA[m] : z.eAi[wk.x];
       const int* eb = z.eB + (size_t)m * OZ_COLS + cg * 64;
       const int jn = 1 + blk * 128 + r, js = M / 2 - jn;
+      constexpr int NACC = ADJ ? OZ_NS : 2 * OZ_LV;  // accumulators in use
       for (int cc = 0; cc < 4; ++cc) {
-        uint32_t v[2 * OZ_LV][16];
+        uint32_t v[NACC][16];
 #pragma unroll
-        for (int a8 = 0; a8 < 2 * OZ_LV; ++a8) tc_ld16(tl + (uint32_t)(a8 * 64 + cc * 16), v[a8]);
+        for (int a8 = 0; a8 < NACC; ++a8) tc_ld16(tl + (uint32_t)(a8 * 64 + cc * 16), v[a8]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int mm = 0; mm < 8; ++mm) {
@@ -1760,7 +1816,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_tc_k(OzArgs z, int nblk, int
           const int Ls = slot < z.B ? z.memberL[slot] : -1;
           if (m > Ls) continue;
           const int c0 = 2 * mm;  // re column (im: c0 + 1) within the 16 loaded
-          if (!ADJ) {
+          if constexpr (!ADJ) {
             if (jn > z.npairs) continue;
             float o[2][2][2];  // [re, im][north, south][hi, lo]
 #pragma unroll
@@ -1793,25 +1849,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_tc_k(OzArgs z, int nblk, int
             }
           } else {
             double2* dst = z.aout[slot] + idx_lm(Ls, 0, m);
+            const int l = m + 256 * q + 2 * r + par;
+            if (l > Ls) continue;
+            double x[2];
 #pragma unroll
-            for (int par = 0; par < 2; ++par) {
-              const int l = m + 256 * q + 2 * r + par;
-              if (l > Ls) continue;
-              double x[2];
+            for (int ri = 0; ri < 2; ++ri) {
+              // 2^-36 fixed point: D0 < 2^25 stays below 2^61
+              long long N = 0;
 #pragma unroll
-              for (int ri = 0; ri < 2; ++ri) {
-                // 2^-36 fixed point: D0 < 2^25 stays below 2^61
-                long long N = 0;
-#pragma unroll
-                for (int k = 0; k < OZ_LV; ++k) N += oz_fix_f(__uint_as_float(v[OZ_LV * par + k][c0 + ri]), 36);
-                x[ri] = oz_dbl(N, ea + eb[cc * 16 + c0 + ri] - 14 - 36);
-              }
-              if (m == 0) {
-                x[0] += oz_pole_term(z.gh[slot], M, z.pole_norm, l);
-                x[1] = 0.0;
-              }
-              dst[l] = make_double2(x[0], x[1]);
+              for (int k = 0; k < NACC; ++k) N += oz_fix_f(__uint_as_float(v[k][c0 + ri]), 36);
+              x[ri] = oz_dbl(N, ea + eb[cc * 16 + c0 + ri] - 14 - 36);
             }
+            if (m == 0) {
+              x[0] += oz_pole_term(z.gh[slot], M, z.pole_norm, l);
+              x[1] = 0.0;
+            }
+            dst[l] = make_double2(x[0], x[1]);
           }
         }
       }
@@ -1882,6 +1935,7 @@ struct Bucket {
   int64_t* obs_off = nullptr;         // per order
   int64_t* oba_off = nullptr;         // per order
   int* eA = nullptr;                  // per order
+  int* eAi = nullptr;                 // per kept item
   int* eBs = nullptr;                 // [order][128]
   int* eBa = nullptr;
   float4* Gp = nullptr;               // members' ring sums (float pairs), [slot][(L_k + 1) M]
@@ -1974,6 +2028,7 @@ void bucket_free(Bucket& b) {
   dev_free(b.obs_off);
   dev_free(b.oba_off);
   dev_free(b.eA);
+  dev_free(b.eAi);
   dev_free(b.eBs);
   dev_free(b.eBa);
   dev_free(b.Gp);
@@ -2349,7 +2404,8 @@ int bucket_build_oz(nusht_batch_t p, Bucket& b, cudaStream_t s) {
     bs += (int64_t)((L - m + 1 + 31) / 32) * b.ncg * OZ_B;
     ba += (int64_t)8 * nim * b.ncg * OZ_B;
     for (int q = 0; q < nq; ++q)
-      for (int cg = 0; cg < b.ncg; ++cg) wa.push_back(make_int2(m, (q << 8) | cg));
+      for (int cg = 0; cg < b.ncg; ++cg)
+        for (int par = 0; par < 2; ++par) wa.push_back(make_int2(m, (q << 8) | (par << 4) | cg));
   }
   b.noz_s = (int)ws.size();
   b.noz_a = (int)wa.size();
@@ -2379,6 +2435,7 @@ int bucket_build_oz(nusht_batch_t p, Bucket& b, cudaStream_t s) {
   NUSHT_TRY(dev_alloc((void**)&b.OBS, std::max<int64_t>(16, bs), &p->bytes));
   NUSHT_TRY(dev_alloc((void**)&b.OBA, std::max<int64_t>(16, ba), &p->bytes));
   NUSHT_TRY(dev_alloc((void**)&b.eA, (size_t)(L + 1) * 4, &p->bytes));
+  NUSHT_TRY(dev_alloc((void**)&b.eAi, std::max<size_t>(1, items.size()) * 4, &p->bytes));
   NUSHT_TRY(dev_alloc((void**)&b.eBs, (size_t)(L + 1) * OZ_COLS * 4, &p->bytes));
   NUSHT_TRY(dev_alloc((void**)&b.eBa, (size_t)(L + 1) * OZ_COLS * 4, &p->bytes));
   NUSHT_TRY(dev_alloc((void**)&b.Gp, std::max<int64_t>(1, gsz) * sizeof(float4), &p->bytes));
@@ -2409,27 +2466,33 @@ int bucket_build_oz(nusht_batch_t p, Bucket& b, cudaStream_t s) {
   NUSHT_CUDA(cudaMemsetAsync(b.Gp, 0, std::max<int64_t>(1, gsz) * sizeof(float4), s));
   // exponents of the recurrence values per order, then the tables
   unsigned long long* amax = nullptr;
-  NUSHT_TRY(dev_alloc((void**)&amax, (size_t)(L + 1) * 8, nullptr));
+  NUSHT_TRY(dev_alloc((void**)&amax, (size_t)(L + 1 + std::max(1, b.nitems)) * 8, nullptr));
+  unsigned long long* amax_item = amax + L + 1;
   int st = NUSHT_OK;
   do {
     const BucketArgs a = bucket_args(b);
     cudaError_t e = cudaMemsetAsync(amax, 0, (size_t)(L + 1) * 8, s);
     if (e == cudaSuccess && b.nitems > 0) {
-      oz_amax_k<<<(b.nitems + 3) / 4, 128, 0, s>>>(a, b.items, b.nitems, b.leg->leg.ahat, amax);
+      oz_amax_k<<<(b.nitems + 3) / 4, 128, 0, s>>>(a, b.items, b.nitems, b.leg->leg.ahat, amax, amax_item);
       e = cudaGetLastError();
     }
-    std::vector<unsigned long long> hm(L + 1, 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), amax, (size_t)(L + 1) * 8, cudaMemcpyDeviceToHost, s);
+    std::vector<unsigned long long> hm(L + 1 + std::max(1, b.nitems), 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), amax, hm.size() * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
       st = cuda_status(e, "split table exponents");
       break;
     }
-    std::vector<int> ea(L + 1);
+    std::vector<int> ea(L + 1), eai(std::max(1, b.nitems), 0);
     for (int m = 0; m <= L; ++m) ea[m] = hm[m] ? (int)(hm[m] >> 52) - 1022 : 0;
+    for (int it = 0; it < b.nitems; ++it) {
+      const unsigned long long v = hm[L + 1 + it];
+      eai[it] = v ? (int)(v >> 52) - 1022 : 0;
+    }
     e = cudaMemcpy(b.eA, ea.data(), (size_t)(L + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b.eAi, eai.data(), eai.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && b.nitems > 0) {
-      oz_build_k<<<(b.nitems + 3) / 4, 128, 0, s>>>(a, b.items, b.nitems, b.mfirst, b.leg->leg.ahat, b.eA,
+      oz_build_k<<<(b.nitems + 3) / 4, 128, 0, s>>>(a, b.items, b.nitems, b.mfirst, b.leg->leg.ahat, b.eA, b.eAi,
                                                     b.ozs_off, b.ozt_base, b.OZS, b.OZT);
       e = cudaGetLastError();
     }
@@ -2458,6 +2521,7 @@ OzArgs oz_args(const Bucket& b, bool adj) {
   z.Bt = adj ? b.OBA : b.OBS;
   z.boff = adj ? b.oba_off : b.obs_off;
   z.eA = b.eA;
+  z.eAi = b.eAi;
   z.eB = adj ? b.eBa : b.eBs;
   z.gout = b.gout;
   z.gh = b.gh;
