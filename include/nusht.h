@@ -363,12 +363,14 @@ NUSHT_API int nusht_adjoint_direct_noalloc(int lmax, int mmax, int64_t npts, con
  * over l (synthesis) or rings (adjoint) runs for all members at once, on the
  * tensor cores (Sec. 4's mixed-precision split: TF32 hi/lo operands, FP32
  * accumulation) or in FP32 on the CUDA cores (opts.tensor_cores).  NUSHT_FP64
- * plans split both operands of the contraction into five bf16 slices under
- * one power of two (the recurrence values per order, the coefficients or
- * folded spectrum per order and member) and run the 15 leading slice
- * products on the tensor cores, exact in FP32 for the two leading levels
- * (~38 significant bits against the largest terms: eps down to 1e-10);
- * their members run the double-float FFT and NUFFT kernels of FP64 plans.
+ * plans split both operands of the contraction into six bf16 slices under
+ * one power of two (the recurrence values per 128-ring-pair block or per
+ * order, the coefficients or folded spectrum per order and member) and run
+ * the 21 leading slice products on the tensor cores, every level but the
+ * synthesis's last summed exactly in FP32 (~46 significant bits against
+ * the largest terms; eps down to 1e-10, the same per-order errors as
+ * standalone FP64 plans); their members run the double-float FFT and NUFFT
+ * kernels of FP64 plans.
  * The grouping minimises a cost model of recurrence and contraction
  * work.  Each direction's whole stage sequence is captured once into a CUDA
  * graph and replayed; it is re-captured when the buffer pointers change.
@@ -381,7 +383,7 @@ typedef struct nusht_batch_s* nusht_batch_t;
  *   npts[b]   its number of points; d_pts[b] its device (theta, phi) pairs
  *   eps       accuracy, >= 1e-6 for NUSHT_MIXED, >= 1e-10 for NUSHT_FP64
  *   precision NUSHT_MIXED or NUSHT_FP64 (NUSHT_ENOMEM when the FP64 split
- *             tables, ~20 bytes per kept (ring pair, l, m), do not fit in
+ *             tables, ~24 bytes per kept (ring pair, l, m), do not fit in
  *             half the free device memory)
  * The host arrays lmax, npts, d_pts are read during the call only.
  * Synchronises `stream`.
