@@ -31,6 +31,7 @@
 #include "nusht_internal.cuh"
 #include "recurrence.cuh"
 #include "dfloat.cuh"
+#include "ozsplit.cuh"
 
 struct nusht_batch_s;
 
@@ -1150,8 +1151,6 @@ __global__ void bucket_final_k(int L, int M, int B, const int* __restrict__ memb
 // each coefficient's double from a 64-bit fixed-point sum with integer
 // operations, so the FP64 pipe (1/64 of the FP32 rate on GB300) stays idle.
 // ---------------------------------------------------------------------------
-constexpr int OZ_NS = 6;                        // slices per operand
-constexpr int OZ_FB = 8 * (OZ_NS - 1) + 7;      // F = round(x 2^(OZ_FB - e)), |F| < 2^47
 constexpr int OZ_ATILE = 128 * 16 * 2;          // 128 rows x 16 bf16
 constexpr int OZ_BTILE = 64 * 16 * 2;           // 64 rows x 16 bf16
 constexpr int OZ_A = 2 * OZ_NS * OZ_ATILE;      // A half of a chunk (48 KB)
@@ -1174,90 +1173,6 @@ static_assert(OZ_NBUF_P * OZ_CHUNK_P == OZ_NBUF * OZ_CHUNK, "both directions use
 __device__ __forceinline__ int oz_off(int row, int k) {
   return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
-
-// balanced base-256 digits: F = sum_i d[i] 256^(OZ_NS - 1 - i), d[1..] in [-128, 127]
-__device__ __forceinline__ void oz_digits(long long F, int (&d)[OZ_NS]) {
-#pragma unroll
-  for (int i = OZ_NS - 1; i > 0; --i) {
-    const long long r = ((F + 128) & 255) - 128;
-    d[i] = (int)r;
-    F = (F - r) >> 8;  // exact: F - r is a multiple of 256
-  }
-  d[0] = (int)F;
-}
-
-// bf16 bits of d 2^(-8 i): the float is exact and its low 16 bits are zero
-__device__ __forceinline__ uint32_t oz_bf16(int d, int i) {
-  return __float_as_uint((float)d * __int_as_float((127 - 8 * i) << 23)) >> 16;
-}
-
-// round(v 2^k) as a 64-bit integer (|v 2^k| < 2^52), integer operations only;
-// zero and subnormal v give 0
-__device__ __forceinline__ long long oz_fix_d(double v, int k) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int ex = (int)((b >> 52) & 0x7ff);
-  if (ex == 0) return 0;
-  const long long mant = (long long)((b & 0xfffffffffffffull) | 0x10000000000000ull);
-  const int sh = ex - 1075 + k;  // v = mant 2^(ex - 1075)
-  long long r;
-  if (sh >= 0)
-    r = mant << (sh < 11 ? sh : 11);
-  else if (sh <= -54)
-    r = 0;
-  else
-    r = (mant + (1ll << (-sh - 1))) >> (-sh);
-  return (b >> 63) ? -r : r;
-}
-
-// round(v 2^k) for a float (|v 2^k| < 2^62)
-__device__ __forceinline__ long long oz_fix_f(float v, int k) {
-  const uint32_t b = __float_as_uint(v);
-  const int ex = (int)((b >> 23) & 0xff);
-  if (ex == 0) return 0;
-  const long long mant = (long long)((b & 0x7fffffu) | 0x800000u);
-  const int sh = ex - 150 + k;  // v = mant 2^(ex - 150)
-  long long r;
-  if (sh >= 0)
-    r = mant << (sh < 38 ? sh : 38);
-  else if (sh <= -25)
-    r = 0;
-  else
-    r = (mant + (1ll << (-sh - 1))) >> (-sh);
-  return (b >> 31) ? -r : r;
-}
-
-// N 2^k as a double (round half away from zero to 53 bits), integer
-// operations only; results below the normal range are 0
-__device__ __forceinline__ double oz_dbl(long long N, int k) {
-  if (N == 0) return 0.0;
-  const unsigned long long sgn = N < 0 ? (1ull << 63) : 0ull;
-  unsigned long long u = N < 0 ? (unsigned long long)(-N) : (unsigned long long)N;
-  const int top = 63 - __clzll((long long)u);  // index of the leading one
-  int e2 = top + k;
-  unsigned long long mnt;
-  if (top > 52) {
-    const int s = top - 52;
-    mnt = (u + (1ull << (s - 1))) >> s;
-    if (mnt >> 53) {
-      mnt >>= 1;
-      ++e2;
-    }
-  } else {
-    mnt = u << (52 - top);
-  }
-  if (e2 < -1022) return 0.0;
-  if (e2 > 1023) return __longlong_as_double((long long)(sgn | 0x7ff0000000000000ull));
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e2 + 1023) << 52) | (mnt & 0xfffffffffffffull)));
-}
-
-// 2^k as a float (0 below the normal range, saturated above)
-__device__ __forceinline__ float oz_pow2f(int k) {
-  k = k > 127 ? 127 : k;
-  return k < -126 ? 0.f : __int_as_float((k + 127) << 23);
-}
-
-// exponent e with |x| < 2^e of the double whose |bits| are b (0 for b = 0)
-__device__ __forceinline__ int oz_exp_of(unsigned long long b) { return b ? (int)(b >> 52) - 1022 : 0; }
 
 __device__ __forceinline__ unsigned long long oz_warp_max(unsigned long long v) {
 #pragma unroll
