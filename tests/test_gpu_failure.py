@@ -77,8 +77,10 @@ def test_injected_allocation_failures(env, prec, eps):
     assert oracle.eps_eff(oracle.synth(a, pts, L), f) <= (1e-10 if prec == 0 else 1e-5)
 
 
-def test_tensor_core_wait_runs_out_and_reports_timeout(env):
-    """The tensor-core contraction's bounded waits.  With the test hook
+@pytest.mark.parametrize("precision,eps,path", [("mixed", 1e-5, 2), ("fp64", 1e-10, 3)])
+def test_tensor_core_wait_runs_out_and_reports_timeout(env, precision, eps, path):
+    """The tensor-core contractions' bounded waits (the TF32 split of mixed
+    plans and the bf16 split of FP64 plans).  With the test hook
     NUSHT_TEST_TC_GIVEUP=1 at plan time the MMA thread's first wait for data
     has a limit of zero polls, so it runs out before any MMA is issued; the
     block's other roles stop waiting, the copies already issued are waited
@@ -88,31 +90,33 @@ def test_tensor_core_wait_runs_out_and_reports_timeout(env):
     the hook is correct against the oracle (the context stays usable)."""
     torch, nu = env
     ls = [40, 63, 100]
-    alms = [W.alm_gaussian(l, seed=i, dtype=np.complex64) for i, l in enumerate(ls)]
+    cdt = np.complex128 if precision == "fp64" else np.complex64
+    rdt = torch.float64 if precision == "fp64" else torch.float32
+    alms = [W.alm_gaussian(l, seed=i, dtype=cdt) for i, l in enumerate(ls)]
     pts = [W.points_uniform(2 * l * l, seed=10 + i) for i, l in enumerate(ls)]
     dpts = [torch.from_numpy(p).cuda() for p in pts]
     dalm = [torch.from_numpy(a).cuda() for a in alms]
     os.environ["NUSHT_TEST_TC_GIVEUP"] = "1"
     try:
-        bp = nu.BatchPlan(ls, dpts, eps=1e-5)
+        bp = nu.BatchPlan(ls, dpts, eps=eps, precision=precision)
     finally:
         del os.environ["NUSHT_TEST_TC_GIVEUP"]
-    assert set(bp.info()["paths"]) == {2}
+    assert set(bp.info()["paths"]) == {path}
     bp.synth(dalm)
     with pytest.raises(nu.NushtError) as ex:
         bp.status()
     assert ex.value.code == nu.NUSHT_ETIMEOUT
     bp.status()  # cleared
-    bp.adjoint([torch.ones(p.shape[0], dtype=torch.float32, device="cuda") for p in pts])
+    bp.adjoint([torch.ones(p.shape[0], dtype=rdt, device="cuda") for p in pts])
     with pytest.raises(nu.NushtError) as ex:
         bp.status()
     assert ex.value.code == nu.NUSHT_ETIMEOUT
     bp.close()
-    good = nu.BatchPlan(ls, dpts, eps=1e-5)
+    good = nu.BatchPlan(ls, dpts, eps=eps, precision=precision)
     outs = good.synth(dalm)
     good.status()
     for l, a, p, f in zip(ls, alms, pts, outs):
         sel = W.subset(p.shape[0], 2000, seed=l)
         ref = oracle.synth(a.astype(np.complex128), p[sel], l)
-        assert oracle.eps_eff(ref, f.double().cpu().numpy()[sel]) <= 1e-5
+        assert oracle.eps_eff(ref, f.double().cpu().numpy()[sel]) <= eps
     good.close()
