@@ -14,6 +14,9 @@ GB300 (sm_103a) the calls raise.  PyTorch provides device memory and streams.
                                                  # (theta', phi') per point, (N, 2)
     batch = nu.BatchPlan(lmaxs, pts_list, eps=1e-5)   # many transforms of uneven lmax
     maps = batch.synth(alm_list)                 # one CUDA graph per direction
+    batch64 = nu.BatchPlan(lmaxs, pts_list, eps=1e-10, precision="fp64")
+                                                 # the same in FP64: complex128 / float64,
+                                                 # bf16-sliced tensor-core contraction
 
 Options (keyword arguments of Plan): sigma, kernel_width, tune (autotuner),
 deterministic (bit-reproducible adjoint), legendre_table (plan-time
