@@ -2930,8 +2930,13 @@ int nusht_plan_many(nusht_batch_t* out, int nbatch, const int* lmax, const int64
 static int run_many(nusht_batch_t p, const void* const* in, void* const* out, nusht_stream_t stream, bool synth) {
   if (!p) return set_error(NUSHT_EINVAL, "batch plan is NULL");
   if (!in || !out) return set_error(NUSHT_EINVAL, "null pointer array");
-  for (int i = 0; i < p->nbatch; ++i)
-    if (!in[i] || (!out[i] && p->npts[i] > 0)) return set_error(NUSHT_EINVAL, "null member buffer");
+  // a member without points may pass NULL for its map (input of the
+  // adjoint, output of the synthesis)
+  for (int i = 0; i < p->nbatch; ++i) {
+    const bool has_pts = p->npts[i] > 0;
+    const bool bad = synth ? (!in[i] || (!out[i] && has_pts)) : ((!in[i] && has_pts) || !out[i]);
+    if (bad) return set_error(NUSHT_EINVAL, "null member buffer");
+  }
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<const void*> vin(in, in + p->nbatch);
   std::vector<void*> vout(out, out + p->nbatch);

@@ -157,3 +157,25 @@ def test_batch_fp64_deterministic_adjoint(env):
     for l, p, y, a, b in zip(ls, pts, ys, c1, c2):
         assert torch.equal(a, b)
         assert oracle.eps_eff(oracle.adjoint(y.cpu().numpy(), p, l), a.cpu().numpy()) <= TOL
+
+
+def test_batch_fp64_empty_member(env):
+    """A member without points sits in the batch with the others: its
+    synthesis writes nothing, its adjoint gives zeros, and the other members
+    still match the oracle."""
+    torch, nu = env
+    ls = [50, 30, 70]
+    npts = [3000, 0, 3000]
+    alms = [W.alm_gaussian(l, seed=80 + i) for i, l in enumerate(ls)]
+    pts = [W.points_uniform(max(n, 1), seed=90 + i)[:n] for i, n in enumerate(npts)]
+    bp = nu.BatchPlan(ls, [torch.from_numpy(p).cuda() for p in pts], eps=1e-10, precision="fp64")
+    outs = bp.synth([torch.from_numpy(a).cuda() for a in alms])
+    ys = [torch.from_numpy(np.random.default_rng(95 + i).standard_normal(n)).cuda() for i, n in enumerate(npts)]
+    cs = bp.adjoint(ys)
+    torch.cuda.synchronize()
+    bp.status()
+    assert outs[1].numel() == 0
+    assert float(cs[1].abs().max()) == 0.0
+    for i in (0, 2):
+        assert oracle.eps_eff(oracle.synth(alms[i], pts[i], ls[i]), outs[i].cpu().numpy()) <= TOL
+        assert oracle.eps_eff(oracle.adjoint(ys[i].cpu().numpy(), pts[i], ls[i]), cs[i].cpu().numpy()) <= TOL
