@@ -178,3 +178,27 @@ def test_batch_fp32_fft_kernels(env):
         assert oracle.eps_eff(ref, c1) <= TOL, l
     own.close()
     cuf.close()
+
+
+def test_batch_empty_member(env):
+    """Mixed precision: a member without points (NULL map pointers) beside
+    others; its adjoint is zero and the others match the oracle."""
+    torch, nu = env
+    ls = [50, 30, 70]
+    npts = [3000, 0, 3000]
+    alms = [W.alm_gaussian(l, seed=80 + i, dtype=np.complex64) for i, l in enumerate(ls)]
+    pts = [W.points_uniform(max(n, 1), seed=90 + i)[:n] for i, n in enumerate(npts)]
+    bp = nu.BatchPlan(ls, [torch.from_numpy(p).cuda() for p in pts], eps=1e-5)
+    outs = bp.synth([torch.from_numpy(a).cuda() for a in alms])
+    ys = [torch.from_numpy(np.random.default_rng(95 + i).standard_normal(n).astype(np.float32)).cuda()
+          for i, n in enumerate(npts)]
+    cs = bp.adjoint(ys)
+    torch.cuda.synchronize()
+    bp.status()
+    assert outs[1].numel() == 0
+    assert float(cs[1].abs().max()) == 0.0
+    for i in (0, 2):
+        ref = oracle.synth(alms[i].astype(np.complex128), pts[i], ls[i])
+        assert oracle.eps_eff(ref, outs[i].double().cpu().numpy()) <= TOL
+        cref = oracle.adjoint(ys[i].double().cpu().numpy(), pts[i], ls[i])
+        assert oracle.eps_eff(cref, cs[i].cpu().numpy().astype(np.complex128)) <= TOL
