@@ -384,7 +384,8 @@ typedef struct nusht_batch_s* nusht_batch_t;
  *   eps       accuracy, >= 1e-6 for NUSHT_MIXED, >= 1e-10 for NUSHT_FP64
  *   precision NUSHT_MIXED or NUSHT_FP64 (NUSHT_ENOMEM when the FP64 split
  *             tables, ~24 bytes per kept (ring pair, l, m), do not fit in
- *             half the free device memory).  For NUSHT_FP64 the contraction
+ *             half the free device memory: on a 288 GB GB300 a bucket up to
+ *             lmax ~3000).  For NUSHT_FP64 the contraction
  *             is always the split one (opts.legendre_table and
  *             opts.tensor_cores do not apply) and opts.fft_kernels must be
  *             >= 0 (NUSHT_EUNSUPPORTED otherwise: the members pass float
